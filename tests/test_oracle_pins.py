@@ -1,0 +1,368 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+Each test names the passage of arXiv:1709.05458 it checks.  None of them
+re-types an oracle formula: they compare the oracle against printed values
+(tests/golden), closed forms, invariants, exact polynomial reproduction, an
+independent exact-rational restatement and measured convergence order.
+"""
+from fractions import Fraction as Fr
+import os
+
+import numpy as np
+import pytest
+
+from oracle import dugks_oracle as O
+from oracle import exact_rational as X
+from oracle import tgv
+from oracle import velocity_sets as V
+import workloads
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _setup(nx, ny, vel, tau, dt, bc, RT=1.0 / 3.0, **kw):
+    xi, W, RT = vel(RT) if callable(vel) else vel
+    return O.Setup(nx, ny, 1.0 / nx, 1.0 / ny, xi, W, RT, tau, dt, bc, **kw)
+
+
+PER = [(O.PERIODIC, 0.0, 0.0)] * 4
+
+
+# ---------------------------------------------------------- velocity sets
+def test_d2q9_matches_printed_table():
+    """Sec. 2.2: the D2Q9 velocities and 2-D weights as printed."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "d2q9_table.txt"))
+            if l.strip() and not l.startswith("#")]
+    RT = 0.7
+    xi, W, RT2 = V.d2q9(RT)
+    c = np.sqrt(3 * RT)
+    assert RT2 == RT
+    for k, (ex, ey, w) in enumerate(rows):
+        assert xi[k, 0] == pytest.approx(float(ex) * c, abs=1e-15)
+        assert xi[k, 1] == pytest.approx(float(ey) * c, abs=1e-15)
+        assert W[k] == pytest.approx(float(Fr(w)), rel=1e-15)
+    # Gauss-Hermite exactness: the discrete moments up to order 5 equal those
+    # of the Maxwellian weight (mean 0, variance RT per direction)
+    assert W.sum() == pytest.approx(1.0, rel=1e-15)
+    assert np.sum(W * xi[:, 0] ** 2) == pytest.approx(RT, rel=1e-14)
+    assert np.sum(W * xi[:, 0] ** 2 * xi[:, 1] ** 2) == pytest.approx(RT * RT, rel=1e-14)
+    assert np.sum(W * xi[:, 0] ** 4) == pytest.approx(3 * RT * RT, rel=1e-14)
+
+
+@pytest.mark.parametrize("n,deg", [(5, 5), (9, 5), (4, 3), (64, 3), (7, 3), (6, 3), (11, 3)])
+def test_newton_cotes_rule_exactness(n, deg):
+    """Composite closed Newton-Cotes rules integrate polynomials up to their
+    degree exactly (Boole: 5, Simpson 3/8 and 1/3: 3)."""
+    x, w = V.newton_cotes_1d(n, -1.3, 2.1)
+    for p in range(deg + 1):
+        exact = (2.1 ** (p + 1) - (-1.3) ** (p + 1)) / (p + 1)
+        assert np.sum(w * x ** p) == pytest.approx(exact, rel=1e-12, abs=1e-12)
+
+
+def test_newton_cotes_maxwellian_moments():
+    """Sec. 2.2 (rarefied): with raw weights the grid reproduces the
+    Maxwellian moments up to the truncation of [-4,4] sqrt(RT) and the
+    quadrature error; normalised weights are exact by construction."""
+    RT = 0.5
+    xi, W, RT_raw = V.newton_cotes_2d(64, RT, normalize=False)
+    assert RT_raw == RT
+    # truncation at 4 sigma leaves erfc(4/sqrt 2) ~ 6.3e-5 per dimension
+    assert abs(W.sum() - 1.0) < 2e-4
+    assert abs(np.sum(W * xi[:, 0] ** 2) / RT - 1.0) < 3e-3
+    assert abs(np.sum(W * xi[:, 0])) < 1e-15
+    xi, W, RT_eff = V.newton_cotes_2d(64, RT, normalize=True)
+    assert W.sum() == pytest.approx(1.0, rel=1e-14)
+    assert np.sum(W * xi[:, 1] ** 2) == pytest.approx(RT_eff, rel=1e-13)
+    assert np.all(V.opposite_index(xi) >= 0)
+
+
+# ------------------------------------------------- time-scheme constants
+def test_scheme_coefficients_satisfy_order_conditions():
+    """Sec. 2.1.1: with A = 1/6, K = 3/4 the L-coefficients solve eq. Para_L
+    to third order; a = 1/3 gives P_n = 0, P' = 3/4, P_{n+1} = 1/4 summing
+    to one; A = a/2 and A = (3K-2)/(6K-3)."""
+    A, K, a = Fr(1, 6), Fr(3, 4), Fr(1, 3)
+    B1 = 3 * (2 * K - 1) ** 2 / (4 * (3 * K * K - 3 * K + 1))
+    B2 = 1 / (4 * (3 * K * K - 3 * K + 1))
+    assert (B1, B2) == (Fr(3, 7), Fr(4, 7))
+    assert B1 + B2 == 1
+    assert A * B1 + K * B2 == Fr(1, 2)
+    assert A * A * B1 + K * K * B2 == Fr(1, 3)
+    assert A == a / 2 == (3 * K - 2) / (6 * K - 3)
+    Pn = (1 - 4 * a + 3 * a * a) / (6 * a * (a - 1))
+    Pp = -1 / (6 * a * (a - 1))
+    Pn1 = (-2 * a + 3 * a * a) / (6 * a * (a - 1))
+    assert (Pn, Pp, Pn1) == (0, Fr(3, 4), Fr(1, 4))
+    for key, val in dict(a=a, A=A, K=K, B1=B1, B2=B2, Pn=Pn, Pp=Pp, Pn1=Pn1).items():
+        assert O.SCHEME[key] == float(val)
+
+
+def test_remark1_t2s2_is_second_order_special_case():
+    """Remark I: A = 0, K = 1/2, B~2 = 1, B-bar0 = B-bar3 = 1/2 satisfy the
+    second-order conditions but not the third-order one."""
+    A, K = Fr(0), Fr(1, 2)
+    Bt = [0, 0, 1, 0]
+    Bb = [Fr(1, 2), 0, 0, Fr(1, 2)]
+    for B in (Bt, Bb):
+        assert sum(B) == 1
+        assert A * B[1] + K * B[2] + B[3] == Fr(1, 2)
+    assert A * A * Bt[1] + K * K * Bt[2] + Bt[3] != Fr(1, 3)
+
+
+# ----------------------------------------------------- cell-local chain
+@pytest.mark.parametrize("D", [0.0, 0.5, 1.0, 2.0, 4.0, 8.0, 12.0, 20.0])
+def test_uniform_nonequilibrium_decay_equals_printed_stability_factor(D):
+    """Sec. 2.1.1: for a spatially uniform state (L = 0) the non-equilibrium
+    part is multiplied each step by the printed P^_n(a = 1/3, D), |P^_n| <= 1
+    iff D <= 12.  This exercises every cell-local transform of Steps (1)-(4)."""
+    tau = 0.01
+    s = _setup(4, 3, V.d2q9, tau, D * tau if D > 0 else 1e-300, PER)
+    rho = np.full((3, 4), 1.1)
+    ux, uy = np.full((3, 4), 0.03), np.full((3, 4), -0.02)
+    feq = O.equilibrium(rho, ux, uy, s)
+    # a non-equilibrium perturbation with zero mass and momentum
+    eps = np.array([1, 0, -1, 0, 0, 0, -1, 0, 1], float) * 1e-3
+    eps += np.array([0, 1, 0, 1, -4, 1, 0, 1, 0], float) * 2e-4
+    f0 = feq + eps[:, None, None]
+    f1 = O.t3s3_step(f0, s)
+    a = Fr(1, 3)
+    Dq = Fr(D)
+    G = abs((-3 * a * a * Dq * Dq + 13 * a * Dq * Dq + 10 * a * Dq - 22 * Dq + 32)
+            / (4 * (a * Dq + 2) * (Dq + 4)))
+    ratio = (f1 - feq) / eps[:, None, None]
+    np.testing.assert_allclose(ratio[np.abs(eps) > 0], float(G), rtol=2e-12)
+    assert (float(G) <= 1 + 1e-15) == (D <= 12)
+    # local truncation of the collision integration: G - exp(-D) = D^4/144 + ...
+    if 0 < D <= 0.5:
+        assert abs(float(G) - np.exp(-D) - D ** 4 / 144) < 0.01 * D ** 4
+
+
+def test_uniform_flow_is_invariant():
+    """A uniform equilibrium flow on a periodic domain is a steady state."""
+    for vel in (V.d2q9, lambda RT: V.newton_cotes_2d(12, RT)):
+        s = _setup(6, 5, vel, 0.02, 0.03, PER, RT=0.5)
+        f0 = O.equilibrium_state(np.full((5, 6), 0.9), np.full((5, 6), 0.05),
+                                 np.full((5, 6), -0.04), s)
+        f = O.t3s3_run(f0, s, 3)
+        np.testing.assert_allclose(f, f0, rtol=1e-13, atol=1e-15)
+
+
+def test_conservation_periodic():
+    """Sum over cells of rho and rho u is constant on a periodic domain
+    (telescoping fluxes, conservative collision; Sec. 2.1.2 and 2.2)."""
+    xi, W, RT = V.d2q9(1 / 3)
+    s = O.Setup(12, 10, 1 / 12, 1 / 10, xi, W, RT, 0.01, 0.03, PER)
+    f = workloads.near_equilibrium_state(W, 10, 12, amp=0.2)
+    m0 = [a.sum() for a in O.moments(f, s)]
+    f = O.t3s3_run(f, s, 5)
+    m1 = [a.sum() for a in O.moments(f, s)]
+    assert abs(m1[0] - m0[0]) < 1e-13 * abs(m0[0])
+    assert abs(m1[1] - m0[1]) < 1e-13 * abs(m0[0])
+    assert abs(m1[2] - m0[2]) < 1e-13 * abs(m0[0])
+
+
+@pytest.mark.parametrize("kind", [O.BOUNCEBACK, O.DIFFUSE])
+def test_mass_conservation_with_walls(kind):
+    """Bounce-back (eq. BB, tangential wall velocity) and diffuse scattering
+    (zero net mass flux through the wall) keep the total mass."""
+    vel = V.d2q9 if kind == O.BOUNCEBACK else (lambda RT: V.newton_cotes_2d(10, RT))
+    bc = [(kind, 0, 0), (kind, 0, 0), (kind, 0, 0), (kind, 0.05, 0)]
+    xi, W, RT = vel(0.5)
+    s = O.Setup(8, 7, 1 / 8, 1 / 7, xi, W, RT, 0.02, 0.01, bc)
+    f = workloads.near_equilibrium_state(W, 7, 8, amp=0.1)
+    m0 = f.sum()
+    f = O.t3s3_run(f, s, 4)
+    assert abs(f.sum() - m0) < 1e-13 * m0
+
+
+# ---------------------------------------------------------- reconstruction
+def test_reconstruction_exact_on_quadratics():
+    """eq. flux_DS (with Q2, Q3, Q16): a quadratic g is reproduced exactly
+    at the characteristic foot x_b - xi h of every interior face and every
+    wall face (incoming velocities), including ghost extrapolation."""
+    xi, W, RT = V.newton_cotes_2d(6, 0.5)
+    bc = [(O.BOUNCEBACK, 0, 0)] * 4
+    nx, ny = 7, 6
+    s = O.Setup(nx, ny, 0.3, 0.2, xi, W, RT, 0.1, 0.05, bc)
+    r = np.random.default_rng(3)
+    co = r.standard_normal((len(xi), 6))
+
+    def G(x, y):
+        c = co[:, :, None, None]
+        return (c[:, 0] + c[:, 1] * x + c[:, 2] * y + c[:, 3] * x * x
+                + c[:, 4] * x * y + c[:, 5] * y * y)
+
+    X, Y = np.meshgrid((np.arange(nx) + .5) * s.dx, (np.arange(ny) + .5) * s.dy)
+    g = G(X, Y)
+    h = 0.07
+    fbx, fby = O.interface_fbar(g, h, np.ones((ny, nx)), s)
+    xf, yc = np.meshgrid(np.arange(nx + 1) * s.dx, (np.arange(ny) + .5) * s.dy)
+    ex = G(xf[None] - s.cx * h, yc[None] - s.cy * h)
+    xc, yf = np.meshgrid((np.arange(nx) + .5) * s.dx, np.arange(ny + 1) * s.dy)
+    ey = G(xc[None] - s.cx * h, yf[None] - s.cy * h)
+    # interior faces: every velocity
+    np.testing.assert_allclose(fbx[:, :, 1:-1], ex[:, :, 1:-1], rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(fby[:, 1:-1, :], ey[:, 1:-1, :], rtol=1e-11, atol=1e-11)
+    # wall faces: velocities not leaving the wall come from the fluid side
+    inc_w = s.xi[:, 0] <= 0
+    inc_e = s.xi[:, 0] >= 0
+    np.testing.assert_allclose(fbx[inc_w, :, 0], ex[inc_w, :, 0], rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(fbx[inc_e, :, nx], ex[inc_e, :, nx], rtol=1e-11, atol=1e-11)
+    inc_s = s.xi[:, 1] <= 0
+    inc_n = s.xi[:, 1] >= 0
+    np.testing.assert_allclose(fby[inc_s, 0, :], ey[inc_s, 0, :], rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(fby[inc_n, ny, :], ey[inc_n, ny, :], rtol=1e-11, atol=1e-11)
+
+
+def test_bounceback_reflects_with_wall_momentum():
+    """eq. BB on f-bar at a wall face: leaving velocities equal the reversed
+    incoming ones plus 2 rho_w W_i xi_i.u_w / RT."""
+    xi, W, RT = V.d2q9(1 / 3)
+    uw = 0.07
+    bc = [(O.PERIODIC, 0, 0)] * 2 + [(O.BOUNCEBACK, 0, 0), (O.BOUNCEBACK, uw, 0)]
+    s = O.Setup(5, 4, .2, .25, xi, W, RT, .1, .05, bc)
+    g = workloads.near_equilibrium_state(W, 4, 5)
+    rho = np.full((4, 5), 1.3)
+    _, fby = O.interface_fbar(g, 0.02, rho, s)
+    top = fby[:, 4, :]
+    for k in range(9):
+        if xi[k, 1] < 0:          # leaves the north wall
+            kk = s.opp[k]
+            np.testing.assert_allclose(top[k], top[kk] + 2 * 1.3 * W[k] * xi[k, 0] * uw / RT,
+                                       rtol=1e-14)
+    # zero net mass flux through each wall at the f-bar level
+    assert np.abs((xi[:, 1][:, None] * top).sum(axis=0)).max() < 1e-15
+    bot = fby[:, 0, :]
+    assert np.abs((xi[:, 1][:, None] * bot).sum(axis=0)).max() < 1e-15
+
+
+# ------------------------------------------------- brute force, exact
+D2Q9_RAT = ([(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1)],
+            [Fr(1, 36), Fr(1, 9), Fr(1, 36), Fr(1, 9), Fr(4, 9), Fr(1, 9),
+             Fr(1, 36), Fr(1, 9), Fr(1, 36)])
+
+
+@pytest.mark.parametrize("bc", [
+    [(0, 0, 0)] * 4,
+    [(1, 0, 0), (1, 0, 0), (1, 0, 0), (1, Fr(1, 10), 0)],
+    [(2, 0, 0), (2, 0, 0), (2, Fr(-1, 20), 0), (2, Fr(1, 10), 0)],
+    [(0, 0, 0), (0, 0, 0), (2, Fr(-1, 10), 0), (1, Fr(1, 10), 0)],
+], ids=["periodic", "bounceback", "diffuse", "mixed"])
+def test_exact_rational_brute_force_4x4(bc):
+    """One full T3S3 step on a 4x4 D2Q9 grid (RT = 1/3, rational tau, dt and
+    state) in exact rational arithmetic with scalar loops agrees with the
+    vectorised FP64 oracle to round-off."""
+    nx = ny = 4
+    tau, dt = Fr(1, 50), Fr(1, 20)
+    r = workloads.rng(7)
+    xir, Wr = D2Q9_RAT
+    f0 = [[[Wr[k] * (1 + Fr(int(r.integers(-60, 61)), 500)) for _ in range(nx)]
+           for _ in range(ny)] for k in range(9)]
+    es = X.ExactSetup(nx, ny, Fr(1, 4), Fr(1, 4), xir, Wr, Fr(1, 3), tau, dt, bc)
+    ex = np.array(X.t3s3_step(es, f0), dtype=float)
+    s = O.Setup(nx, ny, .25, .25, np.array(xir, float), np.array(Wr, float), 1 / 3,
+                float(tau), float(dt), [(b[0], float(b[1]), float(b[2])) for b in bc])
+    out = O.t3s3_step(np.array(f0, dtype=float), s)
+    assert np.abs(out - ex).max() <= 1e-14 * np.abs(ex).max()
+
+
+# ------------------------------------------------------- Remark I in use
+def test_intermediate_state_is_t2_step_of_dt_over_3():
+    """Step (2): f~(t') is one original-DUGKS step of size dt/3 from t_n
+    (Remark I with h = dt/6, Q5, Q7)."""
+    xi, W, RT = V.d2q9(1 / 3)
+    s = O.Setup(10, 8, .1, .125, xi, W, RT, 0.004, 0.01, PER)
+    fhat = workloads.near_equilibrium_state(W, 8, 10, amp=0.2)
+    tr = {}
+    O.t3s3_step(fhat, s, trace=tr)
+    f = O.f_from_fhat(fhat, s)
+    feq, _ = O.equilibrium_of(f, s)
+    ftilde = f + (s.dt / 6) / s.tau * (f - feq)          # f~ = f - dt/6 Omega
+    ref = O.t2_step(ftilde, s, s.dt / 3)
+    np.testing.assert_allclose(tr["ft_prime"], ref, rtol=1e-13, atol=1e-16)
+    # and f^+ (eq. fhp) is the plain f at t_n
+    np.testing.assert_allclose(tr["fhat_plus"], f, rtol=1e-14)
+
+
+# ------------------------------------------------------ accuracy order
+def _tgv_error(N, fbp="derived"):
+    RT, nu, u0, dt, T = 100.0, 0.01, 1.0, 2e-4, 0.04
+    xi, W, RT = V.d2q9(RT)
+    s = O.Setup(N, N, 1 / N, 1 / N, xi, W, RT, nu / RT, dt, PER, fbp=fbp)
+    f = tgv.chapman_enskog_fhat(s, u0, nu)
+    n = int(round(T / dt))
+    f = O.t3s3_run(f, s, n)
+    return tgv.error_L2(f, s, n * dt, u0, nu)
+
+
+def test_taylor_green_third_order():
+    """Sec. 3.1 / Table 1: E(u) against the analytic Taylor vortex decays at
+    third order under grid refinement at fixed small dt (dt/tau = 2)."""
+    e = [_tgv_error(N) for N in (16, 32, 64)]
+    orders = [np.log2(e[i] / e[i + 1]) for i in range(2)]
+    assert all(2.7 < p < 3.8 for p in orders), (e, orders)
+
+
+def test_printed_eq_fbp_5_12_breaks_convergence():
+    """Reading Q6: the printed coefficients of eq. fbp_5_12 do not converge
+    (error at 64^2 above 32^2), the consistent ones do."""
+    e32, e64 = _tgv_error(32, "printed"), _tgv_error(64, "printed")
+    assert e64 > e32
+
+
+# ----------------------------------------------------- diffuse walls
+def test_free_molecular_couette_is_a_fixed_point():
+    """Diffuse scattering (Sec. 2.3, Q15) with 1/tau -> 0: between plates at
+    -u_w (south) and +u_w (north) the exact discrete steady state is, in each
+    half space, the emitting wall's discrete Maxwellian with the same rho_w."""
+    RT = 0.5
+    xi, W, RT = V.newton_cotes_2d(16, RT)
+    uw = 0.1
+    bc = [(O.PERIODIC, 0, 0)] * 2 + [(O.DIFFUSE, -uw, 0), (O.DIFFUSE, uw, 0)]
+    s = O.Setup(4, 6, .25, 1 / 6, xi, W, RT, 1e200, 0.005, bc)
+
+    def maxw(u):
+        eu = xi[:, 0] * u
+        return W * (1 + eu / RT + eu * eu / (2 * RT * RT) - u * u / (2 * RT))
+
+    f_half = np.where(xi[:, 1] > 0, maxw(-uw), maxw(uw))
+    f0 = np.broadcast_to(f_half[:, None, None], (len(W), 6, 4)).copy()
+    f = O.t3s3_run(f0, s, 3)
+    np.testing.assert_allclose(f, f0, rtol=1e-12, atol=1e-15)
+    # the shear stress is the discrete free-molecular value -2 (u_w/RT) sum_{xi_y>0} W xi_x^2 xi_y
+    pxy = (xi[:, 0] * xi[:, 1])[:, None, None] * f
+    expect = -2 * uw / RT * np.sum((W * xi[:, 0] ** 2 * xi[:, 1])[xi[:, 1] > 0])
+    np.testing.assert_allclose(pxy.sum(axis=0), expect, rtol=1e-12)
+
+
+def test_bounceback_couette_linear_profile():
+    """Bounce-back with a moving wall (eq. BB): steady plane Couette flow has
+    the linear profile u = U (y / H) (walls on the faces, Q12)."""
+    xi, W, RT = V.d2q9(1 / 3)
+    ny, U = 8, 0.02
+    bc = [(O.PERIODIC, 0, 0)] * 2 + [(O.BOUNCEBACK, 0, 0), (O.BOUNCEBACK, U, 0)]
+    nu = 0.05
+    tau = nu / RT
+    dt = 0.5 / ny
+    s = O.Setup(3, ny, 1 / 3, 1 / ny, xi, W, RT, tau, dt, bc)
+    f = O.equilibrium_state(*workloads.rest_fields(3, ny), s)
+    f = O.t3s3_run(f, s, int(3.0 / (nu * dt)))
+    _, u, v = O.velocity(f, s)
+    y = (np.arange(ny) + 0.5) / ny
+    np.testing.assert_allclose(u[:, 1], U * y, atol=0.01 * U)
+    assert np.abs(v).max() < 1e-3 * U
+
+
+# ------------------------------------------------------ Table 1 (slow)
+@pytest.mark.slow
+def test_table1_taylor_vortex_32():
+    """Table 1, T3S3 row, N = 32: E(u) at t = 1 s (1e5 steps)."""
+    rows = {int(a): float(b) for a, b in (l.split() for l in
+            open(os.path.join(GOLD, "table1_tgv_t3s3.txt")) if l.strip() and l[0] != "#")}
+    dt, nu, u0 = 1e-5, 0.01, 1.0
+    tau = dt / 4
+    xi, W, RT = V.d2q9(nu / tau)
+    s = O.Setup(32, 32, 1 / 32, 1 / 32, xi, W, RT, tau, dt, PER)
+    f = O.t3s3_run(tgv.chapman_enskog_fhat(s, u0, nu), s, 100000)
+    e = tgv.error_L2(f, s, 1.0, u0, nu)
+    assert rows[32] / 1.5 < e < rows[32] * 1.5
