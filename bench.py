@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput of the third-order DUGKS (T3S3) step on GB300.
+
+Metric: G cell-velocity updates/s (cells x velocities x steps / device time)
+of the full T3S3 step (Sec. 2.1.3 of arXiv:1709.05458) on the lid-driven
+cavity workload ``cavity256``: 256^2 cells, D2Q9 Gauss-Hermite, Re = 1000,
+lid Ma = 0.1, bounce-back/moving walls, FP64.  One bench step = one T3S3
+time step of the whole grid; the L2 cache is flushed (a 256 MiB write)
+before every timed step, and each step is timed with CUDA events on the
+solver's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the CPU oracle (plain FP64 numpy restatement of
+the paper) on the host cores on the same workload; N > 1 runs independent
+replicas (one per rank, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "cavity256"
+L2_FLUSH_BYTES = 256 << 20
+
+# Algorithmic FP64 flops (FMA = 2) per unit of each kernel, from the
+# arithmetic of the method (counted in the design notes): per cell-velocity
+# for cell/update kernels, per face-velocity for face kernels.
+FLOPS_PER_UNIT = {
+    "cell_stage1": 17, "cell_stage2": 17,
+    "face_x_stage1": 34, "face_y_stage1": 34, "face_x_stage2": 34, "face_y_stage2": 34,
+    "update_stage1": 17, "update_stage2": 21,
+}
+# Algorithmic DRAM bytes per unit (FP64 values each kernel must read/write once).
+BYTES_PER_UNIT = {
+    "cell_stage1": 16, "cell_stage2": 16,              # read f, write g
+    "face_x_stage1": 16, "face_y_stage1": 16,          # read g (upwind), write f_b
+    "face_x_stage2": 16, "face_y_stage2": 16,
+    "update_stage1": 48,                               # read f^, g, 2 faces; write f~', acc (per cell: 6 values)
+    "update_stage2": 40,                               # read f~', acc, 2 faces; write f^
+}
+
+
+def fp64_peak_tflops():
+    """Nominal GB300 FP64 vector peak from unit counts and clock:
+    152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz = 1.258 TFLOP/s."""
+    return 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_solver(P, PV, WL, stream):
+    c = WL.config(WORKLOAD)
+    xi, W, RT = PV.d2q9(c["RT"])
+    n = c["nx"]
+    s = P.Solver(n, n, 1.0 / n, 1.0 / n, xi, W, RT, c["tau"], c["dt"], c["bc"], stream=stream)
+    s.set_equilibrium(*WL.rest_fields(n, n))
+    return s, c, len(W)
+
+
+def cpu_oracle_rate(steps, budget_s=20.0):
+    """The oracle as it stands on this host: T3S3 steps of the full cavity256
+    grid from rest.  Returns (updates/s, steps run, seconds, cores)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import dugks_oracle as O
+    from oracle import velocity_sets as OV
+    import workloads as WL
+    c = WL.config(WORKLOAD)
+    xi, W, RT = OV.d2q9(c["RT"])
+    n = c["nx"]
+    s = O.Setup(n, n, 1.0 / n, 1.0 / n, xi, W, RT, c["tau"], c["dt"], c["bc"])
+    f = O.equilibrium_state(*WL.rest_fields(n, n), s)
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        f = O.t3s3_step(f, s)
+        done += 1
+        if budget_s is not None and time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n * n * len(W) * done / dt, done, dt, 1
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import workloads as WL
+    c = WL.config(WORKLOAD)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(1, None)
+    rate, done, secs, cores = cpu_oracle_rate(args.steps, None)
+    units = c["nx"] * c["ny"] * 9
+    val = rate / 1e9
+    line = {
+        "impl": "reference", "metric": "G cell-velocity updates/s (T3S3 step)",
+        "value": val, "unit": "G updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * secs / done, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": f"{c['nx']}x{c['ny']}", "velocities": "D2Q9",
+                   "bc": "bounce-back, moving lid", "units_per_step": units},
+        "cpu_baseline": {"value": val, "unit": "G updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{done} full T3S3 steps of {WORKLOAD} from rest (numpy FP64 oracle)"},
+        "e2e": {"value": val, "unit": "G updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1709_05458_gb300 as P
+    from paper_1709_05458_gb300 import velocity_sets as PV
+    import workloads as WL
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev_index = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    P.load()
+    solver, c, nv = make_solver(P, PV, WL, stream)
+    units = c["nx"] * c["ny"] * nv
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # warm-up
+    for _ in range(max(args.warmup, 0)):
+        solver.step(1)
+    solver.synchronize()
+    assert solver.check() == P.DUGKS_OK, "warm-up produced an unstable state"
+
+    # device-timed region: flush L2, then one T3S3 step between two events
+    clocks = Clocks(dev_index) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    P.dugks_profile(solver.ctx, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for a, b in evs:
+            flush.fill_(1.0)
+            a.record(stream)
+            solver.step(1)
+            b.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    prof = P.dugks_profile_read(solver.ctx)
+    P.dugks_profile(solver.ctx, False)
+    clk = clocks.stop() if clocks else None
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ok = solver.check() == P.DUGKS_OK
+
+    # end to end through the C ABI with host buffers: upload f^ from pinned
+    # host memory, one step, read the moments back, every step
+    import numpy as np
+    f_host = torch.empty((nv, c["ny"], c["nx"]), dtype=torch.float64).pin_memory()
+    mom_host = [torch.empty((c["ny"], c["nx"]), dtype=torch.float64).pin_memory() for _ in range(3)]
+    P.dugks_get_state(solver.ctx, f_host.numpy())
+    fh = f_host.numpy()
+    mh = [m.numpy() for m in mom_host]
+    for _ in range(2):
+        P.dugks_set_state(solver.ctx, fh)
+        solver.step(1)
+        P.dugks_moments(solver.ctx, *mh)
+    e2e_steps = max(1, min(args.steps, 200))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        P.dugks_set_state(solver.ctx, fh)
+        solver.step(1)
+        P.dugks_moments(solver.ctx, *mh)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    if rank != 0:
+        return 0
+
+    value = units * args.steps * world / (ms * 1e-3) / 1e9
+    e2e = units * e2e_steps * world / e2e_s / 1e9
+
+    # roofline of the dominant kernel (largest share of device time)
+    name, (nl, kms) = max(((k, v) for k, v in prof.items() if k in FLOPS_PER_UNIT),
+                          key=lambda kv: kv[1][1])
+    nx, ny = c["nx"], c["ny"]
+    per_launch_units = {
+        "face_x": nv * ny * (nx + 1), "face_y": nv * (ny + 1) * nx,
+    }.get(name[:6], nv * nx * ny)
+    flops = FLOPS_PER_UNIT[name] * per_launch_units
+    avg_s = kms * 1e-3 / max(nl, 1)
+    achieved = flops / avg_s / 1e12
+    peak = fp64_peak_tflops()
+    launches = sum(v[0] for k, v in prof.items())
+    line = {
+        "metric": "G cell-velocity updates/s (T3S3 step)", "value": value,
+        "unit": "G updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": f"{nx}x{ny}", "velocities": "D2Q9",
+                   "bc": "bounce-back walls, moving lid", "Re": 1000, "Ma": 0.1,
+                   "units_per_step": units, "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": "nominal FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                     "kernel_ms_per_launch": avg_s * 1e3,
+                     "kernel_share": kms / sum(v[1] for v in prof.values())},
+        "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items() if v[0]},
+        "e2e": {"value": e2e, "unit": "G updates/s",
+                "h2d_bytes_per_step": int(fh.nbytes), "d2h_bytes_per_step": int(sum(m.nbytes for m in mh))},
+        "gpu_launches": int(launches), "stable": ok, "wall_s": t_wall,
+    }
+    if clk:
+        line["clocks"] = clk
+    if not args.no_cpu_baseline and world == 1:
+        rate, done, secs, cores = cpu_oracle_rate(10_000, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": rate / 1e9, "unit": "G updates/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"{done} full T3S3 steps of {WORKLOAD} from rest, {secs:.1f} s"}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

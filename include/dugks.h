@@ -1,0 +1,152 @@
+/*
+ * dugks.h -- C ABI of the GB300 (sm_103a) third-order DUGKS library.
+ *
+ * The library advances the isothermal BGK-Boltzmann equation
+ *     df/dt = L(f) + Omega(f),  L = -xi . grad f,  Omega = -(f - feq)/tau
+ * (arXiv:1709.05458, Sec. 2.1.1, eq. BE) on a uniform 2-D cell-centred
+ * finite-volume mesh with a discrete velocity set, using the two-stage
+ * third-order DUGKS time step of Sec. 2.1.3 (Steps (1)-(4), eq.
+ * feqIntD3rdHat2_DS).  Every step of that path runs in the library's own
+ * CUDA kernels on the stream given at init.
+ *
+ * Conventions shared by all calls
+ *   - Status: every function returns an int, DUGKS_OK (0) on success or a
+ *     negative DUGKS_E* code.  Nothing throws or exits across the ABI.
+ *     dugks_last_error() returns a thread-local message for the last
+ *     failing call on the calling thread (or a warning set by dugks_init).
+ *   - Layout of per-(velocity, cell) arrays: structure of arrays
+ *     f[k][j][i], velocity k = 0..nv-1 slowest, cell row j = 0..ny-1 (y),
+ *     cell column i = 0..nx-1 (x) fastest; cell (i, j) is centred at
+ *     ((i + 1/2) dx, (j + 1/2) dy).  Per-cell arrays are [j][i].
+ *   - Memory: the context owns its device state.  Pointers passed in are
+ *     borrowed for the duration of the call only.  With on_device = 0 they
+ *     are host pointers (pageable or pinned); with on_device = 1 they are
+ *     device pointers on the context's device, read or written on the
+ *     context's stream (the caller keeps them alive until that stream
+ *     reaches the call; device-side calls are asynchronous).
+ *   - Threading: one context per stream; a context is not thread-safe.
+ */
+#ifndef DUGKS_H
+#define DUGKS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DUGKS_OK          0
+#define DUGKS_EINVAL     (-1)  /* bad argument (sizes, tau, dt, boundary set, ...) */
+#define DUGKS_ECUDA      (-2)  /* a CUDA runtime error; message in dugks_last_error */
+#define DUGKS_ENOMEM     (-3)  /* device allocation failed */
+#define DUGKS_EUNSTABLE  (-4)  /* non-finite or non-positive density detected */
+#define DUGKS_ENOTIMPL   (-5)  /* option not provided by this build */
+
+/* boundary kinds (Sec. 2.3) and side order of the bc[4] array */
+enum { DUGKS_BC_PERIODIC = 0,   /* index wrap; opposite sides must both be periodic */
+       DUGKS_BC_BOUNCEBACK = 1, /* eq. BB, wall velocity (uw_x, uw_y) */
+       DUGKS_BC_DIFFUSE = 2 };  /* diffuse scattering, wall velocity (uw_x, uw_y) */
+enum { DUGKS_WEST = 0, DUGKS_EAST = 1, DUGKS_SOUTH = 2, DUGKS_NORTH = 3 };
+
+/* storage form of the distribution */
+enum { DUGKS_FP64 = 0 };
+
+typedef struct dugks_ctx dugks_ctx;   /* opaque, owned by the library */
+
+/* Uniform Cartesian mesh of nx * ny cells of size dx * dy (Sec. 2.1.2). */
+typedef struct { int nx, ny; double dx, dy; } dugks_mesh;
+
+/* Discrete velocity set (Sec. 2.2): nv velocities (xi_x[k], xi_y[k]) and the
+ * weights W_k of the equilibrium feq_k = W_k rho [1 + xi.u/RT
+ * + (xi.u)^2/(2 RT^2) - |u|^2/(2 RT)] (second-order expansion, Sec. 2.1.1).
+ * For D2Q9 these are the Gauss-Hermite weights; for a Newton-Cotes grid
+ * W_k is the quadrature weight times the Maxwellian factor.  Host arrays,
+ * copied at dugks_init. */
+typedef struct { int nv; const double* xi_x; const double* xi_y; const double* w; double RT; } dugks_velset;
+
+/* One side of the domain: kind and wall velocity (ignored for periodic). */
+typedef struct { int kind; double uw_x, uw_y; } dugks_bc;
+
+/*
+ * dugks_init -- validate the problem and allocate device state.
+ *   mesh, vel   : problem definition (copied).
+ *   tau, dt     : relaxation time and time step, both > 0.  dt/tau > 12
+ *                 exceeds the stability bound of Sec. 2.1.1 (P^_n <= 1 at
+ *                 a = 1/3): accepted, with a warning in dugks_last_error.
+ *   bc[4]       : sides in the order WEST, EAST, SOUTH, NORTH.  A wall
+ *                 direction needs at least 3 cells across (the stencil ghost
+ *                 extrapolation uses three cells); bounce-back needs -xi_k in
+ *                 the set for every velocity leaving that wall; diffuse walls
+ *                 need at least one velocity leaving the wall.
+ *   storage     : DUGKS_FP64.
+ *   cuda_stream : cudaStream_t (may be NULL = legacy default stream) on which
+ *                 every later call of this context runs.
+ *   out         : receives the new context.
+ * The state is zero until dugks_set_state or dugks_set_equilibrium.
+ * Errors: EINVAL, ENOTIMPL, ENOMEM, ECUDA.
+ */
+int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, double dt,
+               const dugks_bc bc[4], int storage, void* cuda_stream, dugks_ctx** out);
+
+/*
+ * dugks_set_equilibrium -- f^ = feq(rho, u) in every cell (the paper's
+ * initialisation, Sec. 3: f = feq, hence f^ = f - dt/4 Omega = feq).
+ *   rho, ux, uy : per-cell arrays [ny][nx], rho > 0.
+ */
+int dugks_set_equilibrium(dugks_ctx* ctx, const double* rho, const double* ux,
+                          const double* uy, int on_device);
+
+/* dugks_set_state -- copy f^ = f - dt/4 Omega (eq. feqIntD3rdHat2), array
+ * [nv][ny][nx], into the context. */
+int dugks_set_state(dugks_ctx* ctx, const double* fhat, int on_device);
+
+/* dugks_get_state -- copy the current f^ [nv][ny][nx] out.  With
+ * on_device = 0 the call waits for the context's stream. */
+int dugks_get_state(dugks_ctx* ctx, double* fhat, int on_device);
+
+/*
+ * dugks_step -- advance n >= 0 T3S3 steps (Sec. 2.1.3, Steps (1)-(4)):
+ *   (1) moments of f^, feq, f-bar^{+,dt/6} (eq. f_bar_1_6), interface values
+ *       at t* = t_n + dt/6 by eqs. interfaceEvof/flux_DS with walls (Sec.
+ *       2.3), f-bar -> f (eq. recover2f), micro-flux L* (eq. microflux);
+ *   (2) f~(t') = f~+(t_n) + dt/3 L* (eqs. f_tilde_1_3, feqIntD2nd_Explicit),
+ *       its moments and dt Omega(f') (eq. collisionterm);
+ *   (3) f-bar^{+,5dt/12}(t') and L** at t** = t_n + 3dt/4;
+ *   (4) f^^{n+1} = f^+ + 3/4 dt Omega' + dt/7 (3 L* + 4 L**).
+ * Asynchronous on the context's stream; returns ECUDA if a launch failed.
+ */
+int dugks_step(dugks_ctx* ctx, int n);
+
+/* dugks_moments -- rho = sum_k f_k, (ux, uy) = sum_k xi_k f_k / rho of the
+ * current state (Sec. 2.2; the moments of f^ equal those of f because the
+ * collision conserves them).  Any output pointer may be NULL.  With
+ * on_device = 0 the call waits for the context's stream. */
+int dugks_moments(dugks_ctx* ctx, double* rho, double* ux, double* uy, int on_device);
+
+/* dugks_check -- scan the state for non-finite values or rho <= 0 (waits
+ * for the stream).  Returns DUGKS_OK or DUGKS_EUNSTABLE. */
+int dugks_check(dugks_ctx* ctx);
+
+/* dugks_synchronize -- wait for all work queued on the context's stream. */
+int dugks_synchronize(dugks_ctx* ctx);
+
+/*
+ * Launch profiling.  dugks_profile(ctx, 1) brackets every kernel launch of
+ * the context with CUDA events on its stream; dugks_profile_read waits for
+ * the stream and returns, for kernel id 0..n-1, the number of launches and
+ * the summed device time in ms since profiling was enabled.  Names of the
+ * ids come from dugks_kernel_name.  Returns the number of kernel ids.
+ */
+int dugks_profile(dugks_ctx* ctx, int enable);
+int dugks_profile_read(dugks_ctx* ctx, long long* launches, double* ms, int n);
+const char* dugks_kernel_name(int id);
+
+/* dugks_destroy -- free the context (NULL is accepted). */
+int dugks_destroy(dugks_ctx* ctx);
+
+/* dugks_last_error -- message of the last error or warning on this thread. */
+const char* dugks_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DUGKS_H */

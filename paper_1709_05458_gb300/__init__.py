@@ -1,0 +1,233 @@
+"""Python binding of the GB300 third-order DUGKS library (``libdugks.so``).
+
+Argument marshalling only: every step of the DUGKS path runs in the
+library's CUDA kernels (see ``include/dugks.h``).  The functions keep the
+C-ABI names (``dugks_init``, ``dugks_step``, ...); :class:`Solver` is a small
+convenience wrapper that owns one context.  PyTorch is used only for device
+buffers and streams.
+
+The library must have been built (``paper_1709_05458_gb300.build``); there is
+no fallback: loading fails loudly if ``libdugks.so`` is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import velocity_sets  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdugks.so")
+
+DUGKS_OK, DUGKS_EINVAL, DUGKS_ECUDA, DUGKS_ENOMEM, DUGKS_EUNSTABLE, DUGKS_ENOTIMPL = 0, -1, -2, -3, -4, -5
+PERIODIC, BOUNCEBACK, DIFFUSE = 0, 1, 2
+WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
+FP64 = 0
+
+# every symbol include/dugks.h declares
+EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_state",
+           "dugks_step", "dugks_moments", "dugks_check", "dugks_synchronize",
+           "dugks_profile", "dugks_profile_read", "dugks_kernel_name", "dugks_destroy",
+           "dugks_last_error")
+
+
+class DugksError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dugks error {code}: {msg}")
+        self.code = code
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("dx", C.c_double), ("dy", C.c_double)]
+
+
+class VelSet(C.Structure):
+    _fields_ = [("nv", C.c_int), ("xi_x", C.POINTER(C.c_double)), ("xi_y", C.POINTER(C.c_double)),
+                ("w", C.POINTER(C.c_double)), ("RT", C.c_double)]
+
+
+class BC(C.Structure):
+    _fields_ = [("kind", C.c_int), ("uw_x", C.c_double), ("uw_y", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load ``libdugks.so`` (raises if it is absent: no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not built; run python -m paper_1709_05458_gb300.build")
+    lib = C.CDLL(path)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    sig = {
+        "dugks_init": (I, [C.POINTER(Mesh), C.POINTER(VelSet), D, D, C.POINTER(BC), I, P, C.POINTER(P)]),
+        "dugks_set_equilibrium": (I, [P, P, P, P, I]),
+        "dugks_set_state": (I, [P, P, I]),
+        "dugks_get_state": (I, [P, P, I]),
+        "dugks_step": (I, [P, I]),
+        "dugks_moments": (I, [P, P, P, P, I]),
+        "dugks_check": (I, [P]),
+        "dugks_synchronize": (I, [P]),
+        "dugks_profile": (I, [P, I]),
+        "dugks_profile_read": (I, [P, C.POINTER(C.c_longlong), C.POINTER(C.c_double), I]),
+        "dugks_kernel_name": (C.c_char_p, [I]),
+        "dugks_destroy": (I, [P]),
+        "dugks_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != DUGKS_OK:
+        raise DugksError(rc, load().dugks_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    """Pointer of a numpy array (host) or a torch tensor (device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+        return a.ctypes.data_as(C.c_void_p)
+    assert a.is_contiguous()
+    return C.c_void_p(a.data_ptr())
+
+
+def _on_device(a):
+    return 0 if (a is None or isinstance(a, np.ndarray)) else int(a.is_cuda)
+
+
+# ------------------------------------------------- C-ABI mirrors
+def dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, storage=FP64, stream=None):
+    """Returns an opaque context handle (int).  ``bc``: four (kind, uw_x, uw_y)
+    in the order west, east, south, north; ``stream``: a torch.cuda.Stream,
+    a raw cudaStream_t int, or None."""
+    lib = load()
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    xx = np.ascontiguousarray(xi[:, 0])
+    xy = np.ascontiguousarray(xi[:, 1])
+    w = np.ascontiguousarray(W, dtype=np.float64)
+    vs = VelSet(len(w), xx.ctypes.data_as(C.POINTER(C.c_double)),
+                xy.ctypes.data_as(C.POINTER(C.c_double)),
+                w.ctypes.data_as(C.POINTER(C.c_double)), float(RT))
+    bcs = (BC * 4)(*[BC(int(b[0]), float(b[1]), float(b[2])) for b in bc])
+    mesh = Mesh(int(nx), int(ny), float(dx), float(dy))
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    out = C.c_void_p()
+    _check(lib.dugks_init(C.byref(mesh), C.byref(vs), float(tau), float(dt), bcs, int(storage),
+                          C.c_void_p(s), C.byref(out)))
+    return out.value
+
+
+def dugks_set_equilibrium(ctx, rho, ux, uy):
+    return _check(load().dugks_set_equilibrium(ctx, _ptr(rho), _ptr(ux), _ptr(uy), _on_device(rho)))
+
+
+def dugks_set_state(ctx, fhat):
+    return _check(load().dugks_set_state(ctx, _ptr(fhat), _on_device(fhat)))
+
+
+def dugks_get_state(ctx, out):
+    return _check(load().dugks_get_state(ctx, _ptr(out), _on_device(out)))
+
+
+def dugks_step(ctx, n=1):
+    return _check(load().dugks_step(ctx, int(n)))
+
+
+def dugks_moments(ctx, rho=None, ux=None, uy=None):
+    ref = next((a for a in (rho, ux, uy) if a is not None), None)
+    return _check(load().dugks_moments(ctx, _ptr(rho), _ptr(ux), _ptr(uy), _on_device(ref)))
+
+
+def dugks_check(ctx):
+    return load().dugks_check(ctx)
+
+
+def dugks_synchronize(ctx):
+    return _check(load().dugks_synchronize(ctx))
+
+
+def dugks_profile(ctx, enable=True):
+    return _check(load().dugks_profile(ctx, int(bool(enable))))
+
+
+def dugks_profile_read(ctx):
+    """{kernel name: (launches, total ms)} since profiling was enabled."""
+    lib = load()
+    n = 32
+    la = (C.c_longlong * n)()
+    ms = (C.c_double * n)()
+    k = lib.dugks_profile_read(ctx, la, ms, n)
+    if k < 0:
+        _check(k)
+    return {lib.dugks_kernel_name(i).decode(): (int(la[i]), float(ms[i])) for i in range(k)}
+
+
+def dugks_destroy(ctx):
+    return _check(load().dugks_destroy(ctx))
+
+
+def dugks_last_error():
+    return load().dugks_last_error().decode()
+
+
+class Solver:
+    """One DUGKS context: ``Solver(nx, ny, dx, dy, xi, W, RT, tau, dt, bc)``."""
+
+    def __init__(self, nx, ny, dx, dy, xi, W, RT, tau, dt, bc, stream=None):
+        self.nx, self.ny, self.nv = int(nx), int(ny), len(W)
+        self.ctx = dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, FP64, stream)
+        self.warning = dugks_last_error()
+
+    def set_equilibrium(self, rho, ux, uy):
+        a = [np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x
+             for x in (rho, ux, uy)]
+        dugks_set_equilibrium(self.ctx, *a)
+
+    def set_state(self, fhat):
+        if isinstance(fhat, np.ndarray):
+            fhat = np.ascontiguousarray(fhat, dtype=np.float64)
+        dugks_set_state(self.ctx, fhat)
+
+    def state(self, out=None):
+        if out is None:
+            out = np.empty((self.nv, self.ny, self.nx))
+        dugks_get_state(self.ctx, out)
+        return out
+
+    def step(self, n=1):
+        dugks_step(self.ctx, n)
+
+    def moments(self):
+        r, u, v = (np.empty((self.ny, self.nx)) for _ in range(3))
+        dugks_moments(self.ctx, r, u, v)
+        return r, u, v
+
+    def check(self):
+        return dugks_check(self.ctx)
+
+    def synchronize(self):
+        dugks_synchronize(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            dugks_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

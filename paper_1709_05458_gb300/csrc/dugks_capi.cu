@@ -1,0 +1,449 @@
+// C-ABI host side of the DUGKS library: validation, device state, launch
+// sequencing of the T3S3 step (Sec. 2.1.3 of arXiv:1709.05458), copies and
+// launch profiling.  Declarations and argument contracts: include/dugks.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dugks.h"
+#include "dugks_internal.cuh"
+
+using namespace dugks;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(DUGKS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+const char* kNames[K_NUM] = {
+    "cell_stage1", "face_x_stage1", "face_y_stage1", "update_stage1",
+    "cell_stage2", "face_x_stage2", "face_y_stage2", "update_stage2",
+    "moments",     "set_equilibrium", "check"};
+
+struct Pending {
+  int id;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct dugks_ctx {
+  DevParams p{};
+  cudaStream_t stream = nullptr;
+  int groups = 1;
+  StageCoef s1{}, s2{};
+  double c_om = 0.0;            // dt Omega(f') = c_om (f~' - feq'), eq. collisionterm
+  // device buffers
+  double* fhat = nullptr;       // state f^ [nv][N]
+  double* ftp = nullptr;        // f~(t') [nv][N]
+  double* acc = nullptr;        // f^+ + 3dt/7 L* [nv][N]
+  double* g = nullptr;          // f-bar^{+,h} of the current stage [nv][N]
+  double* fbx = nullptr;        // x-face f [nv][ny][nx+1]
+  double* fby = nullptr;        // y-face f [nv][ny+1][nx]
+  double* mom = nullptr;        // rho, ux, uy [3][N]
+  double* vel = nullptr;        // xi_x, xi_y, w, feq_wall[4]  ([7][nv])
+  int* opp = nullptr;           // [nv]
+  int* flag = nullptr;          // [1]
+  // profiling
+  bool prof = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  long long launches[K_NUM] = {0};
+  double ms[K_NUM] = {0.0};
+
+  cudaEvent_t ev() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drain() {
+    for (auto& q : pending) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, q.a, q.b) == cudaSuccess) {
+        ms[q.id] += t;
+        launches[q.id] += 1;
+      }
+      pool.push_back(q.a);
+      pool.push_back(q.b);
+    }
+    pending.clear();
+  }
+};
+
+namespace {
+
+// Bracket one launch with profiling events when enabled.
+template <typename F>
+int launch(dugks_ctx* c, int id, F&& f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->prof) {
+    if (c->pending.size() > 200000) {  // bound host memory: fold finished ones
+      cudaStreamSynchronize(c->stream);
+      c->drain();
+    }
+    a = c->ev();
+    b = c->ev();
+    cudaEventRecord(a, c->stream);
+  }
+  cudaError_t e = f();
+  if (c->prof) {
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({id, a, b});
+  }
+  if (e != cudaSuccess) return cuda_fail(e, kNames[id]);
+  return DUGKS_OK;
+}
+
+#define TRY(x)                        \
+  do {                                \
+    int rc__ = (x);                   \
+    if (rc__ != DUGKS_OK) return rc__; \
+  } while (0)
+
+int copy_in(dugks_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, n * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy to device");
+  if (!on_device) {  // host buffer may be freed by the caller after return
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy to device");
+  }
+  return DUGKS_OK;
+}
+
+int copy_out(dugks_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, n * sizeof(double),
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy from device");
+  if (!on_device) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy from device");
+  }
+  return DUGKS_OK;
+}
+
+void free_all(dugks_ctx* c) {
+  double* bufs[] = {c->fhat, c->ftp, c->acc, c->g, c->fbx, c->fby, c->mom, c->vel};
+  for (double* b : bufs)
+    if (b) cudaFree(b);
+  if (c->opp) cudaFree(c->opp);
+  if (c->flag) cudaFree(c->flag);
+  for (auto& q : c->pending) {
+    cudaEventDestroy(q.a);
+    cudaEventDestroy(q.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+}
+
+int one_step(dugks_ctx* c) {
+  const DevParams& p = c->p;
+  cudaStream_t s = c->stream;
+  const int G = c->groups;
+  // Step (1): moments of f^, g1 = f-bar^{+,dt/6}; faces at t*; L*; Step (2): f~(t')
+  TRY(launch(c, K_CELL_STAGE1, [&] { return launch_cell(p, G, 1, c->fhat, c->g, c->mom, c->s1.a, c->s1.b, s); }));
+  TRY(launch(c, K_FACE_X_STAGE1, [&] { return launch_face(p, G, 0, c->g, c->mom, c->fbx, c->s1, s); }));
+  TRY(launch(c, K_FACE_Y_STAGE1, [&] { return launch_face(p, G, 1, c->g, c->mom, c->fby, c->s1, s); }));
+  TRY(launch(c, K_UPDATE_STAGE1, [&] { return launch_update1(p, c->fhat, c->g, c->fbx, c->fby, c->ftp, c->acc, s); }));
+  // Step (2) collision at t' and Step (3): g2 = f-bar^{+,5dt/12}(t'); faces at t**; Step (4)
+  TRY(launch(c, K_CELL_STAGE2, [&] { return launch_cell(p, G, 2, c->ftp, c->g, c->mom, c->s2.a, c->s2.b, s); }));
+  TRY(launch(c, K_FACE_X_STAGE2, [&] { return launch_face(p, G, 0, c->g, c->mom, c->fbx, c->s2, s); }));
+  TRY(launch(c, K_FACE_Y_STAGE2, [&] { return launch_face(p, G, 1, c->g, c->mom, c->fby, c->s2, s); }));
+  TRY(launch(c, K_UPDATE_STAGE2, [&] { return launch_update2(p, c->ftp, c->acc, c->mom, c->fbx, c->fby, c->fhat, c->c_om, s); }));
+  return DUGKS_OK;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* dugks_last_error(void) { return g_err.c_str(); }
+
+const char* dugks_kernel_name(int id) {
+  return (id >= 0 && id < K_NUM) ? kNames[id] : "";
+}
+
+int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, double dt,
+               const dugks_bc bc[4], int storage, void* cuda_stream, dugks_ctx** out) {
+  g_err.clear();
+  if (!out) return fail(DUGKS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !vel || !bc) return fail(DUGKS_EINVAL, "NULL mesh, velocity set or bc");
+  if (storage != DUGKS_FP64) return fail(DUGKS_ENOTIMPL, "only DUGKS_FP64 storage is provided");
+  if (mesh->nx < 1 || mesh->ny < 1) return fail(DUGKS_EINVAL, "nx, ny must be >= 1");
+  if ((long long)mesh->nx * mesh->ny > (1LL << 31) - 1)
+    return fail(DUGKS_EINVAL, "too many cells");
+  if (!finite_pos(mesh->dx) || !finite_pos(mesh->dy)) return fail(DUGKS_EINVAL, "dx, dy must be > 0");
+  if (!finite_pos(tau) || !finite_pos(dt)) return fail(DUGKS_EINVAL, "tau, dt must be > 0 and finite");
+  const int nv = vel->nv;
+  if (nv < 1 || !vel->xi_x || !vel->xi_y || !vel->w) return fail(DUGKS_EINVAL, "empty velocity set");
+  if (!finite_pos(vel->RT)) return fail(DUGKS_EINVAL, "RT must be > 0");
+  if ((long long)nv * mesh->nx * mesh->ny * 8LL > (1LL << 40))
+    return fail(DUGKS_EINVAL, "state larger than 1 TiB");
+  for (int k = 0; k < nv; ++k)
+    if (!std::isfinite(vel->xi_x[k]) || !std::isfinite(vel->xi_y[k]) || !std::isfinite(vel->w[k]))
+      return fail(DUGKS_EINVAL, "non-finite velocity or weight");
+  for (int s = 0; s < 4; ++s) {
+    if (bc[s].kind < 0 || bc[s].kind > 2) return fail(DUGKS_EINVAL, "unknown boundary kind");
+    if (!std::isfinite(bc[s].uw_x) || !std::isfinite(bc[s].uw_y))
+      return fail(DUGKS_EINVAL, "non-finite wall velocity");
+  }
+  const bool px = bc[DUGKS_WEST].kind == DUGKS_BC_PERIODIC;
+  const bool py = bc[DUGKS_SOUTH].kind == DUGKS_BC_PERIODIC;
+  if (px != (bc[DUGKS_EAST].kind == DUGKS_BC_PERIODIC))
+    return fail(DUGKS_EINVAL, "west and east must both be periodic or both walls");
+  if (py != (bc[DUGKS_NORTH].kind == DUGKS_BC_PERIODIC))
+    return fail(DUGKS_EINVAL, "south and north must both be periodic or both walls");
+  if (!px && mesh->nx < 3) return fail(DUGKS_EINVAL, "walls in x need nx >= 3");
+  if (!py && mesh->ny < 3) return fail(DUGKS_EINVAL, "walls in y need ny >= 3");
+
+  // opposite velocities (bounce-back) and wall equilibria (diffuse)
+  std::vector<int> opp(nv, -1);
+  double vmax = 0.0;
+  for (int k = 0; k < nv; ++k) vmax = std::fmax(vmax, std::fabs(vel->xi_x[k]) + std::fabs(vel->xi_y[k]));
+  for (int k = 0; k < nv; ++k)
+    for (int q = 0; q < nv; ++q)
+      if (std::fabs(vel->xi_x[q] + vel->xi_x[k]) + std::fabs(vel->xi_y[q] + vel->xi_y[k]) <=
+          1e-12 * (1.0 + vmax)) {
+        opp[k] = q;
+        break;
+      }
+  std::vector<double> host(7 * (size_t)nv, 0.0);
+  for (int k = 0; k < nv; ++k) {
+    host[k] = vel->xi_x[k];
+    host[nv + k] = vel->xi_y[k];
+    host[2 * nv + k] = vel->w[k];
+  }
+  DevParams p{};
+  const double invRT = 1.0 / vel->RT;
+  for (int s = 0; s < 4; ++s) {
+    p.bc_kind[s] = bc[s].kind;
+    p.uw_x[s] = bc[s].uw_x;
+    p.uw_y[s] = bc[s].uw_y;
+    if (bc[s].kind == DUGKS_BC_PERIODIC) continue;
+    const double nxs = (s == DUGKS_WEST) ? -1.0 : (s == DUGKS_EAST) ? 1.0 : 0.0;
+    const double nys = (s == DUGKS_SOUTH) ? -1.0 : (s == DUGKS_NORTH) ? 1.0 : 0.0;
+    double den = 0.0;
+    int nout = 0;
+    for (int k = 0; k < nv; ++k) {
+      const double eu = (vel->xi_x[k] * bc[s].uw_x + vel->xi_y[k] * bc[s].uw_y) * invRT;
+      const double uu = (bc[s].uw_x * bc[s].uw_x + bc[s].uw_y * bc[s].uw_y) * invRT;
+      const double fw = vel->w[k] * (1.0 + eu + 0.5 * eu * eu - 0.5 * uu);
+      host[(3 + s) * (size_t)nv + k] = fw;
+      const double xn = vel->xi_x[k] * nxs + vel->xi_y[k] * nys;
+      if (xn < 0.0) {
+        ++nout;
+        den -= xn * fw;
+        if (bc[s].kind == DUGKS_BC_BOUNCEBACK && opp[k] < 0)
+          return fail(DUGKS_EINVAL, "bounce-back needs -xi_k in the velocity set");
+      }
+    }
+    if (bc[s].kind == DUGKS_BC_DIFFUSE && (nout == 0 || !(den > 0.0)))
+      return fail(DUGKS_EINVAL, "diffuse wall without velocities leaving it");
+    p.ds_den[s] = den;
+    if (bc[s].kind == DUGKS_BC_DIFFUSE) p.has_ds = 1;
+  }
+
+  dugks_ctx* c = new dugks_ctx();
+  c->stream = (cudaStream_t)cuda_stream;
+  c->groups = nv <= 32 ? 1 : 8;
+  p.nx = mesh->nx;
+  p.ny = mesh->ny;
+  p.nv = nv;
+  p.N = mesh->nx * mesh->ny;
+  p.px = px;
+  p.py = py;
+  p.dx = mesh->dx;
+  p.dy = mesh->dy;
+  p.inv_dx = 1.0 / mesh->dx;
+  p.inv_dy = 1.0 / mesh->dy;
+  p.tau = tau;
+  p.dt = dt;
+  p.RT = vel->RT;
+  p.inv_RT = invRT;
+
+  const size_t nvN = (size_t)nv * p.N;
+  const size_t nfx = (size_t)nv * p.ny * (p.nx + 1), nfy = (size_t)nv * (p.ny + 1) * p.nx;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](double** ptr, size_t n) {
+    if (e == cudaSuccess) e = cudaMalloc((void**)ptr, n * sizeof(double));
+  };
+  alloc(&c->fhat, nvN);
+  alloc(&c->ftp, nvN);
+  alloc(&c->acc, nvN);
+  alloc(&c->g, nvN);
+  alloc(&c->fbx, nfx);
+  alloc(&c->fby, nfy);
+  alloc(&c->mom, 3 * (size_t)p.N);
+  alloc(&c->vel, host.size());
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->opp, nv * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->flag, sizeof(int));
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? DUGKS_ENOMEM : DUGKS_ECUDA,
+                std::string("device allocation: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(c->vel, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->opp, opp.data(), nv * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->fhat, 0, nvN * sizeof(double), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return cuda_fail(e, "dugks_init");
+  }
+  p.xi_x = c->vel;
+  p.xi_y = c->vel + nv;
+  p.w = c->vel + 2 * (size_t)nv;
+  p.feq_wall = c->vel + 3 * (size_t)nv;
+  p.opp = c->opp;
+  c->p = p;
+
+  // Stage coefficients (Sec. 2.1.3; readings in the oracle's header):
+  //   g1 = ((12 tau - dt) f^ + 4 dt feq) / (12 tau + 3 dt)          eq. f_bar_1_6
+  //   g2 = ((24 tau - 5 dt) f~' + 9 dt feq') / (24 tau + 4 dt)      eq. fbp_5_12 (derived form)
+  //   f  = (2 tau f-bar + h feq) / (2 tau + h)                     eq. recover2f
+  //   dt Omega' = -6 dt / (6 tau + dt) (f~' - feq')                eq. collisionterm
+  const double T = tau;
+  c->s1.a = (12.0 * T - dt) / (12.0 * T + 3.0 * dt);
+  c->s1.b = 4.0 * dt / (12.0 * T + 3.0 * dt);
+  c->s1.h = dt / 6.0;
+  c->s2.a = (24.0 * T - 5.0 * dt) / (24.0 * T + 4.0 * dt);
+  c->s2.b = 9.0 * dt / (24.0 * T + 4.0 * dt);
+  c->s2.h = 5.0 * dt / 12.0;
+  for (StageCoef* s : {&c->s1, &c->s2}) {
+    s->alpha = 2.0 * T / (2.0 * T + s->h);
+    s->beta = s->h / (2.0 * T + s->h);
+  }
+  c->c_om = -6.0 * dt / (6.0 * T + dt);
+  *out = c;
+  if (dt / tau > 12.0)
+    g_err = "warning: dt/tau > 12 exceeds the stability bound of the scheme";
+  return DUGKS_OK;
+}
+
+int dugks_set_equilibrium(dugks_ctx* c, const double* rho, const double* ux, const double* uy,
+                          int on_device) {
+  if (!c || !rho || !ux || !uy) return fail(DUGKS_EINVAL, "NULL argument");
+  const size_t N = c->p.N;
+  const double *r = rho, *u = ux, *v = uy;
+  if (!on_device) {  // stage through the moment buffer
+    TRY(copy_in(c, c->mom, rho, N, 0));
+    TRY(copy_in(c, c->mom + N, ux, N, 0));
+    TRY(copy_in(c, c->mom + 2 * N, uy, N, 0));
+    r = c->mom;
+    u = c->mom + N;
+    v = c->mom + 2 * N;
+  }
+  TRY(launch(c, K_SET_EQ, [&] { return launch_set_eq(c->p, r, u, v, c->fhat, c->stream); }));
+  return DUGKS_OK;
+}
+
+int dugks_set_state(dugks_ctx* c, const double* fhat, int on_device) {
+  if (!c || !fhat) return fail(DUGKS_EINVAL, "NULL argument");
+  return copy_in(c, c->fhat, fhat, (size_t)c->p.nv * c->p.N, on_device);
+}
+
+int dugks_get_state(dugks_ctx* c, double* fhat, int on_device) {
+  if (!c || !fhat) return fail(DUGKS_EINVAL, "NULL argument");
+  return copy_out(c, fhat, c->fhat, (size_t)c->p.nv * c->p.N, on_device);
+}
+
+int dugks_step(dugks_ctx* c, int n) {
+  if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  if (n < 0) return fail(DUGKS_EINVAL, "n must be >= 0");
+  for (int i = 0; i < n; ++i) TRY(one_step(c));
+  return DUGKS_OK;
+}
+
+int dugks_moments(dugks_ctx* c, double* rho, double* ux, double* uy, int on_device) {
+  if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  TRY(launch(c, K_MOMENTS, [&] {
+    return launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
+  }));
+  const size_t N = c->p.N;
+  if (rho) TRY(copy_out(c, rho, c->mom, N, on_device));
+  if (ux) TRY(copy_out(c, ux, c->mom + N, N, on_device));
+  if (uy) TRY(copy_out(c, uy, c->mom + 2 * N, N, on_device));
+  return DUGKS_OK;
+}
+
+int dugks_check(dugks_ctx* c) {
+  if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  cudaError_t e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dugks_check");
+  TRY(launch(c, K_MOMENTS, [&] {
+    return launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
+  }));
+  TRY(launch(c, K_CHECK, [&] { return launch_check(c->p, c->mom, c->flag, c->stream); }));
+  int h = 0;
+  e = cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dugks_check");
+  if (h) return fail(DUGKS_EUNSTABLE, "non-finite or non-positive density in the state");
+  return DUGKS_OK;
+}
+
+int dugks_synchronize(dugks_ctx* c) {
+  if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dugks_synchronize");
+  return DUGKS_OK;
+}
+
+int dugks_profile(dugks_ctx* c, int enable) {
+  if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dugks_profile");
+  c->drain();
+  for (int i = 0; i < K_NUM; ++i) {
+    c->launches[i] = 0;
+    c->ms[i] = 0.0;
+  }
+  c->prof = enable != 0;
+  return DUGKS_OK;
+}
+
+int dugks_profile_read(dugks_ctx* c, long long* launches, double* ms, int n) {
+  if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "dugks_profile_read");
+  c->drain();
+  for (int i = 0; i < n && i < K_NUM; ++i) {
+    if (launches) launches[i] = c->launches[i];
+    if (ms) ms[i] = c->ms[i];
+  }
+  return K_NUM;
+}
+
+int dugks_destroy(dugks_ctx* c) {
+  if (!c) return DUGKS_OK;
+  cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+  return DUGKS_OK;
+}
+
+}  // extern "C"
