@@ -238,17 +238,16 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers: upload f^ from pinned
     # host memory, one step, read the moments back, every step
-    import numpy as np
     f_host = torch.empty((nv, c["ny"], c["nx"]), dtype=torch.float64).pin_memory()
     mom_host = [torch.empty((c["ny"], c["nx"]), dtype=torch.float64).pin_memory() for _ in range(3)]
     P.dugks_get_state(solver.ctx, f_host.numpy())
     fh = f_host.numpy()
     mh = [m.numpy() for m in mom_host]
-    for _ in range(2):
+    for _ in range(0 if args.no_e2e else 2):
         P.dugks_set_state(solver.ctx, fh)
         solver.step(1)
         P.dugks_moments(solver.ctx, *mh)
-    e2e_steps = max(1, min(args.steps, 200))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 200))
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -269,7 +268,7 @@ def run_ours(args):
         return 0
 
     value = units * args.steps * world / (ms * 1e-3) / 1e9
-    e2e = units * e2e_steps * world / e2e_s / 1e9
+    e2e = units * e2e_steps * world / e2e_s / 1e9 if e2e_steps else None
 
     # roofline of the dominant kernel (largest share of device time)
     name, (nl, kms) = max(((k, v) for k, v in prof.items() if k in FLOPS_PER_UNIT),
@@ -321,7 +320,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="cavityN (N^2 D2Q9 cavity); the default is the reported workload")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
+    globals()["WORKLOAD"] = args.workload
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
