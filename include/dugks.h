@@ -140,6 +140,37 @@ int dugks_profile(dugks_ctx* ctx, int enable);
 int dugks_profile_read(dugks_ctx* ctx, long long* launches, double* ms, int n);
 const char* dugks_kernel_name(int id);
 
+/*
+ * dugks_step_static -- advance nsteps T3S3 steps exactly as dugks_step does,
+ * without allocating any device memory.  The paper has no counterpart: this
+ * is a facility for callers that may not allocate device memory, such as a
+ * plugin inside an application that owns all device memory through its own
+ * pool, or a latency-critical loop that cannot accept the implicit device
+ * synchronisation of cudaMalloc/cudaFree.
+ *   mesh, vel, tau, dt, bc : as for dugks_init (host structures, read during
+ *                  the call).
+ *   fhat_in      : device pointer, f^ [nv][ny][nx] at t_n (not modified
+ *                  unless it equals fhat_out).
+ *   fhat_out     : device pointer, receives f^ after nsteps (may equal
+ *                  fhat_in for an in-place update).
+ *   nsteps       : >= 0.
+ *   cuda_stream  : cudaStream_t for every copy and launch (NULL = legacy
+ *                  default stream); the call is asynchronous on it.
+ * All intermediates live in one fixed 32 MiB device array inside the
+ * library (held on every GPU that loads the library until the process
+ * exits).  A problem needing more than 32 MiB of intermediates (about
+ * 5 * nv * nx * ny doubles, e.g. more than a 256^2 D2Q9 grid) is rejected
+ * with DUGKS_EINVAL and a message giving the size.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make it before any stream capture.  Calls share the
+ * array and it keeps the last call's contents (nothing needs to start at
+ * zero); calls that overlap on the GPU race on it and must be serialised.
+ * Errors: EINVAL, ECUDA (message in dugks_last_error).
+ */
+int dugks_step_static(const dugks_mesh* mesh, const dugks_velset* vel, double tau, double dt,
+                      const dugks_bc bc[4], const double* fhat_in, double* fhat_out,
+                      int nsteps, void* cuda_stream);
+
 /* dugks_destroy -- free the context (NULL is accepted). */
 int dugks_destroy(dugks_ctx* ctx);
 

@@ -30,7 +30,7 @@ FP64 = 0
 EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_state",
            "dugks_step", "dugks_moments", "dugks_check", "dugks_synchronize",
            "dugks_profile", "dugks_profile_read", "dugks_kernel_name", "dugks_destroy",
-           "dugks_last_error")
+           "dugks_last_error", "dugks_step_static")
 
 
 class DugksError(RuntimeError):
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
         "dugks_kernel_name": (C.c_char_p, [I]),
         "dugks_destroy": (I, [P]),
         "dugks_last_error": (C.c_char_p, []),
+        "dugks_step_static": (I, [C.POINTER(Mesh), C.POINTER(VelSet), D, D, C.POINTER(BC), P, P, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -181,6 +182,26 @@ def dugks_destroy(ctx):
 
 def dugks_last_error():
     return load().dugks_last_error().decode()
+
+
+def dugks_step_static(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, fhat_in, fhat_out, nsteps,
+                      stream=None):
+    """T3S3 steps with no device allocation (library-internal fixed 32 MiB
+    scratch); ``fhat_in``/``fhat_out`` are CUDA tensors [nv][ny][nx]
+    (may be the same tensor).  For callers that may not allocate device
+    memory; calls must not overlap on the GPU."""
+    lib = load()
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    xx, xy = np.ascontiguousarray(xi[:, 0]), np.ascontiguousarray(xi[:, 1])
+    w = np.ascontiguousarray(W, dtype=np.float64)
+    vs = VelSet(len(w), xx.ctypes.data_as(C.POINTER(C.c_double)),
+                xy.ctypes.data_as(C.POINTER(C.c_double)),
+                w.ctypes.data_as(C.POINTER(C.c_double)), float(RT))
+    bcs = (BC * 4)(*[BC(int(b[0]), float(b[1]), float(b[2])) for b in bc])
+    mesh = Mesh(int(nx), int(ny), float(dx), float(dy))
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    return _check(lib.dugks_step_static(C.byref(mesh), C.byref(vs), float(tau), float(dt), bcs,
+                                        _ptr(fhat_in), _ptr(fhat_out), int(nsteps), C.c_void_p(s)))
 
 
 class Solver:

@@ -39,6 +39,8 @@ struct Pending {
 
 }  // namespace
 
+void dugks::set_last_error(const std::string& msg) { g_err = msg; }
+
 struct dugks_ctx {
   DevParams p{};
   cudaStream_t stream = nullptr;

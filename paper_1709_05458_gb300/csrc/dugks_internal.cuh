@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace dugks {
 
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
@@ -49,6 +51,9 @@ struct StageCoef {
   double h;                     // interface time step of the stage
   double alpha, beta;           // f = alpha f-bar + beta feq at a face
 };
+
+// Sets the message returned by dugks_last_error() on the calling thread.
+void set_last_error(const std::string& msg);
 
 // Launchers (dugks_kernels.cu).  All asynchronous on `s`.
 cudaError_t launch_cell(const DevParams& p, int groups, int stage, const double* src,
