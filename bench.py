@@ -40,6 +40,12 @@ FLOPS_PER_UNIT = {
     "cell_stage1": 17, "cell_stage2": 17,
     "face_x_stage1": 34, "face_y_stage1": 34, "face_x_stage2": 34, "face_y_stage2": 34,
     "update_stage1": 17, "update_stage2": 21,
+    # fused D2Q9 kernels, per cell-velocity: two faces (2 x 23.2: the 70
+    # non-zero stencil products of the nine velocities, face moments, one
+    # reciprocal, the nine equilibrium polynomials, f-bar -> f) plus the cell
+    # part (stage 1: L*, f~', moments, feq', dt Omega', g2, X = 25.9;
+    # stage 2: L**, f^, moments, feq, g1 = 13.8)
+    "d2q9_stage1": 72.3, "d2q9_stage2": 60.2,
 }
 # Algorithmic DRAM bytes per unit (FP64 values each kernel must read/write once).
 BYTES_PER_UNIT = {
@@ -48,6 +54,15 @@ BYTES_PER_UNIT = {
     "face_x_stage2": 16, "face_y_stage2": 16,
     "update_stage1": 48,                               # read f^, g, 2 faces; write f~', acc (per cell: 6 values)
     "update_stage2": 40,                               # read f~', acc, 2 faces; write f^
+}
+
+
+# DRAM bytes (read + write) per unit measured by ncu for the kernels named,
+# from profiles/d2q9_stage_kernels_cavity1024.md (1024^2 capture, scaled to
+# a launch by the units it processes); kept only while the kernel is unchanged.
+TRAFFIC_BYTES_PER_UNIT = {
+    "d2q9_stage1": (151.361536e6 + 114.549504e6) / (1024 * 1024 * 9),
+    "d2q9_stage2": (151.355904e6 + 115.911424e6) / (1024 * 1024 * 9),
 }
 
 
@@ -271,7 +286,8 @@ def run_ours(args):
     e2e = units * e2e_steps * world / e2e_s / 1e9 if e2e_steps else None
 
     # roofline of the dominant kernel (largest share of device time)
-    name, (nl, kms) = max(((k, v) for k, v in prof.items() if k in FLOPS_PER_UNIT),
+    name, (nl, kms) = max(((k, v) for k, v in prof.items()
+                           if k in FLOPS_PER_UNIT and v[0] > 0 and v[1] > 0),
                           key=lambda kv: kv[1][1])
     nx, ny = c["nx"], c["ny"]
     per_launch_units = {
@@ -292,7 +308,9 @@ def run_ours(args):
                    "units_per_step": units, "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": (TRAFFIC_BYTES_PER_UNIT[name] * per_launch_units
+                                 if name in TRAFFIC_BYTES_PER_UNIT else None),
                      "peak_source": "nominal FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
                      "kernel_ms_per_launch": avg_s * 1e3,
                      "kernel_share": kms / sum(v[1] for v in prof.values())},

@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -30,7 +31,8 @@ int cuda_fail(cudaError_t e, const char* where) {
 const char* kNames[K_NUM] = {
     "cell_stage1", "face_x_stage1", "face_y_stage1", "update_stage1",
     "cell_stage2", "face_x_stage2", "face_y_stage2", "update_stage2",
-    "moments",     "set_equilibrium", "check"};
+    "moments",     "set_equilibrium", "check",
+    "d2q9_prologue", "d2q9_stage1", "d2q9_stage2"};
 
 struct Pending {
   int id;
@@ -58,6 +60,12 @@ struct dugks_ctx {
   double* vel = nullptr;        // xi_x, xi_y, w, feq_wall[4]  ([7][nv])
   int* opp = nullptr;           // [nv]
   int* flag = nullptr;          // [1]
+  // fused D2Q9 path: buffers fhat = f^, g = g1, ftp = g2, acc = X, mom[0..N) and
+  // mom[N..2N) = rho of the two stage base states
+  bool d2q9 = false;
+  bool g1_valid = false;
+  D2Q9Params dp{};
+  D2Q9Stage ds1{}, ds2{};
   // profiling
   bool prof = false;
   std::vector<Pending> pending;
@@ -154,6 +162,89 @@ void free_all(dugks_ctx* c) {
     cudaEventDestroy(q.b);
   }
   for (auto e : c->pool) cudaEventDestroy(e);
+}
+
+// Quadratic Taylor weights about one cell centre for the foot offset
+// (a dx, b dy): T[dy+1][dx+1] (eq. flux_DS with central differences).
+void taylor_weights(double a, double b, double T[3][3]) {
+  T[0][0] = a * b / 4;  T[0][1] = (b * b - b) / 2;  T[0][2] = -a * b / 4;
+  T[1][0] = (a * a - a) / 2;  T[1][1] = 1 - a * a - b * b;  T[1][2] = (a * a + a) / 2;
+  T[2][0] = -a * b / 4;  T[2][1] = (b * b + b) / 2;  T[2][2] = a * b / 4;
+}
+
+// Interface weight tables of one stage (interface step h, flux factor fac).
+void d2q9_stage_tables(D2Q9Stage& S, double c, double dx, double dy, double tau, double h,
+                       double fac) {
+  std::memset(&S, 0, sizeof(S));
+  const double alpha = 2 * tau / (2 * tau + h);
+  S.gamma = h / (2 * tau);
+  for (int k = 0; k < 9; ++k) {
+    const int ex = k / 3 - 1, ey = k % 3 - 1;
+    const double cx = c * ex, cy = c * ey;
+    double TL[3][3], TR[3][3], TB[3][3], TT[3][3];
+    taylor_weights((0.5 * dx - cx * h) / dx, (-cy * h) / dy, TL);    // from cell fi-1
+    taylor_weights((-0.5 * dx - cx * h) / dx, (-cy * h) / dy, TR);   // from cell fi
+    taylor_weights((-cx * h) / dx, (0.5 * dy - cy * h) / dy, TB);    // from cell fj-1
+    taylor_weights((-cx * h) / dx, (-0.5 * dy - cy * h) / dy, TT);   // from cell fj
+    const double wl = ex > 0 ? 1.0 : (ex < 0 ? 0.0 : 0.5), wr = ex < 0 ? 1.0 : (ex > 0 ? 0.0 : 0.5);
+    const double wb = ey > 0 ? 1.0 : (ey < 0 ? 0.0 : 0.5), wt = ey < 0 ? 1.0 : (ey > 0 ? 0.0 : 0.5);
+    for (int r = 0; r < 3; ++r)
+      for (int q = 0; q < 3; ++q) {
+        S.wx[k][r][q] += wl * TL[r][q];
+        S.wx[k][r][q + 1] += wr * TR[r][q];
+        S.wy[k][r][q] += wb * TB[r][q];
+        S.wy[k][r + 1][q] += wt * TT[r][q];
+        S.wxL[k][r][q] = TL[r][q];
+        S.wxR[k][r][q] = TR[r][q];
+        S.wyB[k][r][q] = TB[r][q];
+        S.wyT[k][r][q] = TT[r][q];
+      }
+    S.kx[k] = -fac * alpha * cx / dx;
+    S.ky[k] = -fac * alpha * cy / dy;
+  }
+}
+
+// Is the velocity set xi_k = c (k/3 - 1, k%3 - 1)?  Returns c (> 0) or 0.
+double d2q9_speed(const dugks_velset* v) {
+  if (v->nv != 9) return 0.0;
+  const double c = v->xi_x[6];
+  if (!(c > 0.0)) return 0.0;
+  for (int k = 0; k < 9; ++k)
+    if (v->xi_x[k] != c * (k / 3 - 1) || v->xi_y[k] != c * (k % 3 - 1)) return 0.0;
+  return c;
+}
+
+// Tile height: the number of 32 x ty tiles per SM wave times the work per
+// tile (ty + 1 face rows) is minimised over ty in [4, 16].
+int d2q9_tile_height(int nx, int ny, int sms) {
+  int best = 8;
+  double bestc = 1e300;
+  for (int ty = 4; ty <= 16; ++ty) {
+    const long tiles = (long)((nx + 31) / 32) * ((ny + ty - 1) / ty);
+    const long waves = (tiles + sms - 1) / sms;
+    const double cost = (double)waves * (ty + 1);
+    if (cost < bestc - 1e-9) {
+      bestc = cost;
+      best = ty;
+    }
+  }
+  return best;
+}
+
+int one_step_d2q9(dugks_ctx* c) {
+  cudaStream_t s = c->stream;
+  const size_t N = c->p.N;
+  if (!c->g1_valid) {
+    TRY(launch(c, K_D2Q9_PROLOGUE, [&] { return launch_cell(c->p, 1, 1, c->fhat, c->g, c->mom, c->s1.a, c->s1.b, s); }));
+    c->g1_valid = true;
+  }
+  TRY(launch(c, K_D2Q9_STAGE1, [&] {
+    return launch_d2q9_stage(c->dp, c->ds1, 1, c->g, c->fhat, c->mom, c->ftp, c->acc, c->mom + N, s);
+  }));
+  TRY(launch(c, K_D2Q9_STAGE2, [&] {
+    return launch_d2q9_stage(c->dp, c->ds2, 2, c->ftp, c->acc, c->mom + N, c->fhat, c->g, c->mom, s);
+  }));
+  return DUGKS_OK;
 }
 
 int one_step(dugks_ctx* c) {
@@ -340,6 +431,51 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     s->beta = s->h / (2.0 * T + s->h);
   }
   c->c_om = -6.0 * dt / (6.0 * T + dt);
+
+  // fused D2Q9 path
+  const double cd = d2q9_speed(vel);
+  const char* force = std::getenv("DUGKS_FORCE_GENERIC");
+  if (cd > 0.0 && !(force && force[0] == '1')) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    D2Q9Params& q = c->dp;
+    q.nx = p.nx;
+    q.ny = p.ny;
+    q.N = p.N;
+    q.px = p.px;
+    q.py = p.py;
+    q.ty = d2q9_tile_height(p.nx, p.ny, sms);
+    for (int k = 0; k < 9; ++k) q.W[k] = vel->w[k];
+    q.c3 = cd * cd / vel->RT;
+    q.base_div = 0.5 / q.c3;
+    q.c_over_RT = cd / vel->RT;
+    q.c = cd;
+    q.a1 = c->s1.a;
+    q.b1 = c->s1.b;
+    q.a2 = c->s2.a;
+    q.b2 = c->s2.b;
+    q.c_om34 = 0.75 * c->c_om;
+    q.r37 = 9.0 / 7.0;
+    for (int s4 = 0; s4 < 4; ++s4) {
+      q.bc_kind[s4] = bc[s4].kind;
+      q.ds_den[s4] = p.ds_den[s4];
+      for (int k = 0; k < 9; ++k) {
+        q.feq_wall[s4][k] = host[(3 + s4) * (size_t)nv + k];
+        q.bb[s4][k] = 2.0 * vel->w[k] *
+                      (vel->xi_x[k] * bc[s4].uw_x + vel->xi_y[k] * bc[s4].uw_y) * invRT;
+      }
+    }
+    d2q9_stage_tables(c->ds1, cd, p.dx, p.dy, T, c->s1.h, dt / 3.0);
+    d2q9_stage_tables(c->ds2, cd, p.dx, p.dy, T, c->s2.h, 4.0 * dt / 7.0);
+    e = d2q9_prepare(q.ty);
+    if (e != cudaSuccess) {
+      free_all(c);
+      delete c;
+      return cuda_fail(e, "dugks_init (fused D2Q9 set-up)");
+    }
+    c->d2q9 = true;
+  }
   *out = c;
   if (dt / tau > 12.0)
     g_err = "warning: dt/tau > 12 exceeds the stability bound of the scheme";
@@ -360,11 +496,13 @@ int dugks_set_equilibrium(dugks_ctx* c, const double* rho, const double* ux, con
     v = c->mom + 2 * N;
   }
   TRY(launch(c, K_SET_EQ, [&] { return launch_set_eq(c->p, r, u, v, c->fhat, c->stream); }));
+  c->g1_valid = false;
   return DUGKS_OK;
 }
 
 int dugks_set_state(dugks_ctx* c, const double* fhat, int on_device) {
   if (!c || !fhat) return fail(DUGKS_EINVAL, "NULL argument");
+  c->g1_valid = false;
   return copy_in(c, c->fhat, fhat, (size_t)c->p.nv * c->p.N, on_device);
 }
 
@@ -376,7 +514,7 @@ int dugks_get_state(dugks_ctx* c, double* fhat, int on_device) {
 int dugks_step(dugks_ctx* c, int n) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
   if (n < 0) return fail(DUGKS_EINVAL, "n must be >= 0");
-  for (int i = 0; i < n; ++i) TRY(one_step(c));
+  for (int i = 0; i < n; ++i) TRY(c->d2q9 ? one_step_d2q9(c) : one_step(c));
   return DUGKS_OK;
 }
 

@@ -25,6 +25,9 @@ enum KernelId {
   K_MOMENTS,
   K_SET_EQ,
   K_CHECK,
+  K_D2Q9_PROLOGUE,     // fused D2Q9 path: g1 from f^ after a new state
+  K_D2Q9_STAGE1,       // fused D2Q9 path: whole stage 1 (+ cell part of stage 2)
+  K_D2Q9_STAGE2,       // fused D2Q9 path: whole stage 2 (+ cell part of next stage 1)
   K_NUM
 };
 
@@ -51,6 +54,47 @@ struct StageCoef {
   double h;                     // interface time step of the stage
   double alpha, beta;           // f = alpha f-bar + beta feq at a face
 };
+
+// Fused D2Q9 path (dugks_d2q9.cu).  Velocities must be
+// xi_k = c (ex_k, ey_k) with ex_k = k/3 - 1, ey_k = k%3 - 1 (the paper's
+// listing order); the weights W_k are arbitrary.
+//
+// Per-stage interface tables.  x-face stencil columns q = 0..3 are the cells
+// fi-2 .. fi+1 around face fi, rows r = 0..2 the cells j-1 .. j+1; y-faces
+// swap the roles.  The one-sided tables (wall faces, tangential velocities)
+// use only the fluid cell's 3x3 neighbourhood.
+struct D2Q9Stage {
+  double wx[9][3][4];        // x-face weights [k][row][col q]
+  double wy[9][4][3];        // y-face weights [k][row q][col]
+  double wxL[9][3][3];       // x-face from the left cell only (cols q = 0..2)
+  double wxR[9][3][3];       // x-face from the right cell only (cols q = 1..3)
+  double wyB[9][3][3];       // y-face from the cell below only (rows q = 0..2)
+  double wyT[9][3][3];       // y-face from the cell above only (rows q = 1..3)
+  double gamma;              // beta/alpha = h / (2 tau): f / alpha = f-bar + gamma feq
+  double kx[9], ky[9];       // flux scale -(stage factor) alpha xi/dx, .../dy
+};
+
+struct D2Q9Params {
+  int nx, ny, N, px, py, ty;  // ty = tile height (tile width is 32)
+  double W[9];
+  double c3;                  // c^2/RT (= 3 for the Gauss-Hermite set)
+  double base_div;            // RT / c^2 / 2 ... |u|^2/(2RT) = (ut_x^2 + ut_y^2) * base_div
+  double c_over_RT;           // c / RT: ut = c u / RT
+  double c;                   // lattice speed: xi = c (ex, ey)
+  double a1, b1, a2, b2;      // g1 = a1 f^ + b1 feq, g2 = a2 f~' + b2 feq'
+  double c_om34;              // 3/4 * (-6 dt / (6 tau + dt))
+  double r37;                 // (3 dt/7) / (dt/3) = 9/7
+  int bc_kind[4];
+  double ds_den[4];
+  double feq_wall[4][9];      // W_k P(xi_k; u_w)
+  double bb[4][9];            // 2 W_k xi_k.u_w / RT
+};
+
+cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage,
+                              const double* gin, const double* own, const double* rho_in,
+                              double* out0, double* out1, double* rho_out, cudaStream_t st);
+size_t d2q9_smem_bytes(int ty);
+cudaError_t d2q9_prepare(int ty);
 
 // Sets the message returned by dugks_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
