@@ -137,11 +137,12 @@ def dist_setup():
     return world, rank, local
 
 
-def make_solver(P, PV, WL, stream):
+def make_solver(P, PV, WL, stream, storage=0):
     c = WL.config(WORKLOAD)
     xi, W, RT = PV.d2q9(c["RT"])
     n = c["nx"]
-    s = P.Solver(n, n, 1.0 / n, 1.0 / n, xi, W, RT, c["tau"], c["dt"], c["bc"], stream=stream)
+    s = P.Solver(n, n, 1.0 / n, 1.0 / n, xi, W, RT, c["tau"], c["dt"], c["bc"], stream=stream,
+                 storage=storage)
     s.set_equilibrium(*WL.rest_fields(n, n))
     return s, c, len(W)
 
@@ -196,7 +197,27 @@ def run_reference(args):
     return 0
 
 
+def timed_steps(P, solver, stream, flush, steps):
+    """K T3S3 steps, each after an L2 flush, each timed with CUDA events on
+    the solver's stream.  Returns (total ms, per-kernel profile)."""
+    import torch
+    P.dugks_profile(solver.ctx, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for a, b in evs:
+            flush.fill_(1.0)
+            a.record(stream)
+            solver.step(1)
+            b.record(stream)
+    torch.cuda.synchronize()
+    prof = P.dugks_profile_read(solver.ctx)
+    P.dugks_profile(solver.ctx, False)
+    return sum(a.elapsed_time(b) for a, b in evs), prof
+
+
 def run_ours(args):
+    import numpy as np
     import torch
     import paper_1709_05458_gb300 as P
     from paper_1709_05458_gb300 import velocity_sets as PV
@@ -225,31 +246,20 @@ def run_ours(args):
     solver.synchronize()
     assert solver.check() == P.DUGKS_OK, "warm-up produced an unstable state"
 
-    # device-timed region: flush L2, then one T3S3 step between two events
+    # device-timed region (FP64 form)
     clocks = Clocks(dev_index) if rank == 0 else None
     if clocks:
         clocks.start()
         time.sleep(0.3)
-    P.dugks_profile(solver.ctx, True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for a, b in evs:
-            flush.fill_(1.0)
-            a.record(stream)
-            solver.step(1)
-            b.record(stream)
-    torch.cuda.synchronize()
+    ms, prof = timed_steps(P, solver, stream, flush, args.steps)
     barrier()
     t_wall = time.perf_counter() - t_wall
-    prof = P.dugks_profile_read(solver.ctx)
-    P.dugks_profile(solver.ctx, False)
     clk = clocks.stop() if clocks else None
-    ms = sum(a.elapsed_time(b) for a, b in evs)
     ok = solver.check() == P.DUGKS_OK
+    _, u64, v64 = solver.moments()
 
     # end to end through the C ABI with host buffers: upload f^ from pinned
     # host memory, one step, read the moments back, every step
@@ -273,6 +283,25 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
+
+    # the FP32 and BF16 deviation-storage forms on the same workload and
+    # protocol; E(u) against the FP64 run after the same W + K steps
+    forms = {}
+    if not args.no_forms:
+        for label, st in (("fp32", P.G_FP32), ("bf16", P.G_BF16)):
+            s2, _, _ = make_solver(P, PV, WL, stream, storage=st)
+            for _ in range(max(args.warmup, 0)):
+                s2.step(1)
+            fms, fprof = timed_steps(P, s2, stream, flush, args.steps)
+            _, u2, v2 = s2.moments()
+            num = np.sqrt(((u2 - u64) ** 2 + (v2 - v64) ** 2).sum())
+            den = np.sqrt((u64 ** 2 + v64 ** 2).sum())
+            forms[label] = {"value": units * args.steps * world / (fms * 1e-3) / 1e9,
+                            "ms_per_step": fms / args.steps,
+                            "E_u_vs_fp64": float(num / den),
+                            "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)}
+                                        for k, v in fprof.items() if v[0]}}
+            s2.close()
 
     if world > 1:
         import torch.distributed as dist
@@ -319,6 +348,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(fh.nbytes), "d2h_bytes_per_step": int(sum(m.nbytes for m in mh))},
         "gpu_launches": int(launches), "stable": ok, "wall_s": t_wall,
     }
+    if forms:
+        line["forms"] = forms
     if clk:
         line["clocks"] = clk
     if not args.no_cpu_baseline and world == 1:
@@ -341,6 +372,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="cavityN (N^2 D2Q9 cavity); the default is the reported workload")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32/BF16 deviation-storage forms")
     args = ap.parse_args()
     globals()["WORKLOAD"] = args.workload
     if args.impl == "reference":

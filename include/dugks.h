@@ -47,8 +47,18 @@ enum { DUGKS_BC_PERIODIC = 0,   /* index wrap; opposite sides must both be perio
        DUGKS_BC_DIFFUSE = 2 };  /* diffuse scattering, wall velocity (uw_x, uw_y) */
 enum { DUGKS_WEST = 0, DUGKS_EAST = 1, DUGKS_SOUTH = 2, DUGKS_NORTH = 3 };
 
-/* storage form of the distribution */
-enum { DUGKS_FP64 = 0 };
+/* Storage and arithmetic form of the distribution.
+ *   DUGKS_FP64   : FP64 storage and arithmetic throughout (any velocity set).
+ *   DUGKS_G_FP32 : per-(cell, velocity) arrays hold the deviation
+ *                  d = f - W_k rho0 (rho0 = 1) in FP32; interface stencils,
+ *                  fluxes and the per-velocity equilibrium assembly run in
+ *                  FP32, the moment sums (Sec. 2.2), 1/rho and the
+ *                  equilibrium parameters u/RT, |u|^2/(2RT) in FP64.
+ *   DUGKS_G_BF16 : as DUGKS_G_FP32 with the deviations stored in BF16.
+ * The deviation forms need the D2Q9 listing order of Sec. 2.2 (xi_k =
+ * c (k/3 - 1, k%3 - 1)); other sets return DUGKS_ENOTIMPL.  States cross the
+ * ABI in FP64 for every form. */
+enum { DUGKS_FP64 = 0, DUGKS_G_FP32 = 1, DUGKS_G_BF16 = 2 };
 
 typedef struct dugks_ctx dugks_ctx;   /* opaque, owned by the library */
 
@@ -77,7 +87,7 @@ typedef struct { int kind; double uw_x, uw_y; } dugks_bc;
  *                 extrapolation uses three cells); bounce-back needs -xi_k in
  *                 the set for every velocity leaving that wall; diffuse walls
  *                 need at least one velocity leaving the wall.
- *   storage     : DUGKS_FP64.
+ *   storage     : DUGKS_FP64, DUGKS_G_FP32 or DUGKS_G_BF16 (see above).
  *   cuda_stream : cudaStream_t (may be NULL = legacy default stream) on which
  *                 every later call of this context runs.
  *   out         : receives the new context.

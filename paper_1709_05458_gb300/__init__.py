@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libdugks.so")
 DUGKS_OK, DUGKS_EINVAL, DUGKS_ECUDA, DUGKS_ENOMEM, DUGKS_EUNSTABLE, DUGKS_ENOTIMPL = 0, -1, -2, -3, -4, -5
 PERIODIC, BOUNCEBACK, DIFFUSE = 0, 1, 2
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
-FP64 = 0
+FP64, G_FP32, G_BF16 = 0, 1, 2
 
 # every symbol include/dugks.h declares
 EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_state",
@@ -207,9 +207,10 @@ def dugks_step_static(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, fhat_in, fhat_out,
 class Solver:
     """One DUGKS context: ``Solver(nx, ny, dx, dy, xi, W, RT, tau, dt, bc)``."""
 
-    def __init__(self, nx, ny, dx, dy, xi, W, RT, tau, dt, bc, stream=None):
+    def __init__(self, nx, ny, dx, dy, xi, W, RT, tau, dt, bc, stream=None, storage=FP64):
         self.nx, self.ny, self.nv = int(nx), int(ny), len(W)
-        self.ctx = dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, FP64, stream)
+        self.ctx = None
+        self.ctx = dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, storage, stream)
         self.warning = dugks_last_error()
 
     def set_equilibrium(self, rho, ux, uy):

@@ -32,7 +32,8 @@ const char* kNames[K_NUM] = {
     "cell_stage1", "face_x_stage1", "face_y_stage1", "update_stage1",
     "cell_stage2", "face_x_stage2", "face_y_stage2", "update_stage2",
     "moments",     "set_equilibrium", "check",
-    "d2q9_prologue", "d2q9_stage1", "d2q9_stage2"};
+    "d2q9_prologue", "d2q9_stage1", "d2q9_stage2",
+    "d2q9m_stage1", "d2q9m_stage2", "convert"};
 
 struct Pending {
   int id;
@@ -66,6 +67,11 @@ struct dugks_ctx {
   bool g1_valid = false;
   D2Q9Params dp{};
   D2Q9Stage ds1{}, ds2{};
+  // deviation storage (store 1 = FP32, 2 = BF16): fhat, g, ftp, acc hold
+  // typed deviations d = f - W rho0; fbx is the FP64 staging buffer
+  int store = 0;
+  double rho0 = 1.0;
+  D2Q9StageF df1{}, df2{};
   // profiling
   bool prof = false;
   std::vector<Pending> pending;
@@ -247,6 +253,26 @@ int one_step_d2q9(dugks_ctx* c) {
   return DUGKS_OK;
 }
 
+int one_step_d2q9m(dugks_ctx* c) {
+  cudaStream_t s = c->stream;
+  const size_t N = c->p.N;
+  if (!c->g1_valid) {
+    TRY(launch(c, K_D2Q9_PROLOGUE, [&] {
+      return launch_dev_cell(c->p, c->store, c->rho0, c->fhat, c->g, c->mom, c->s1.a, c->s1.b, 1, s);
+    }));
+    c->g1_valid = true;
+  }
+  TRY(launch(c, K_D2Q9M_STAGE1, [&] {
+    return launch_d2q9m_stage(c->dp, c->df1, c->store, 1, c->rho0, c->g, c->fhat, c->mom, c->ftp,
+                              c->acc, c->mom + N, s);
+  }));
+  TRY(launch(c, K_D2Q9M_STAGE2, [&] {
+    return launch_d2q9m_stage(c->dp, c->df2, c->store, 2, c->rho0, c->ftp, c->acc, c->mom + N,
+                              c->fhat, c->g, c->mom, s);
+  }));
+  return DUGKS_OK;
+}
+
 int one_step(dugks_ctx* c) {
   const DevParams& p = c->p;
   cudaStream_t s = c->stream;
@@ -282,7 +308,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
   if (!out) return fail(DUGKS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!mesh || !vel || !bc) return fail(DUGKS_EINVAL, "NULL mesh, velocity set or bc");
-  if (storage != DUGKS_FP64) return fail(DUGKS_ENOTIMPL, "only DUGKS_FP64 storage is provided");
+  if (storage < DUGKS_FP64 || storage > DUGKS_G_BF16) return fail(DUGKS_ENOTIMPL, "unknown storage form");
   if (mesh->nx < 1 || mesh->ny < 1) return fail(DUGKS_EINVAL, "nx, ny must be >= 1");
   if ((long long)mesh->nx * mesh->ny > (1LL << 31) - 1)
     return fail(DUGKS_EINVAL, "too many cells");
@@ -307,6 +333,8 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     return fail(DUGKS_EINVAL, "west and east must both be periodic or both walls");
   if (py != (bc[DUGKS_NORTH].kind == DUGKS_BC_PERIODIC))
     return fail(DUGKS_EINVAL, "south and north must both be periodic or both walls");
+  if (storage != DUGKS_FP64 && !(d2q9_speed(vel) > 0.0))
+    return fail(DUGKS_ENOTIMPL, "deviation storage needs the D2Q9 velocity set");
   if (!px && mesh->nx < 3) return fail(DUGKS_EINVAL, "walls in x need nx >= 3");
   if (!py && mesh->ny < 3) return fail(DUGKS_EINVAL, "walls in y need ny >= 3");
 
@@ -435,7 +463,12 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
   // fused D2Q9 path
   const double cd = d2q9_speed(vel);
   const char* force = std::getenv("DUGKS_FORCE_GENERIC");
-  if (cd > 0.0 && !(force && force[0] == '1')) {
+  if (storage != DUGKS_FP64 && !(cd > 0.0)) {
+    free_all(c);
+    delete c;
+    return fail(DUGKS_ENOTIMPL, "deviation storage needs the D2Q9 velocity set");
+  }
+  if (cd > 0.0 && (storage != DUGKS_FP64 || !(force && force[0] == '1'))) {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -469,6 +502,12 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     d2q9_stage_tables(c->ds1, cd, p.dx, p.dy, T, c->s1.h, dt / 3.0);
     d2q9_stage_tables(c->ds2, cd, p.dx, p.dy, T, c->s2.h, 4.0 * dt / 7.0);
     e = d2q9_prepare(q.ty);
+    if (e == cudaSuccess && storage != DUGKS_FP64) {
+      c->store = storage;
+      d2q9_stage_to_float(c->ds1, c->df1);
+      d2q9_stage_to_float(c->ds2, c->df2);
+      e = d2q9m_prepare();
+    }
     if (e != cudaSuccess) {
       free_all(c);
       delete c;
@@ -495,7 +534,10 @@ int dugks_set_equilibrium(dugks_ctx* c, const double* rho, const double* ux, con
     u = c->mom + N;
     v = c->mom + 2 * N;
   }
-  TRY(launch(c, K_SET_EQ, [&] { return launch_set_eq(c->p, r, u, v, c->fhat, c->stream); }));
+  if (c->store)
+    TRY(launch(c, K_SET_EQ, [&] { return launch_dev_set_eq(c->p, c->store, c->rho0, r, u, v, c->fhat, c->stream); }));
+  else
+    TRY(launch(c, K_SET_EQ, [&] { return launch_set_eq(c->p, r, u, v, c->fhat, c->stream); }));
   c->g1_valid = false;
   return DUGKS_OK;
 }
@@ -503,25 +545,42 @@ int dugks_set_equilibrium(dugks_ctx* c, const double* rho, const double* ux, con
 int dugks_set_state(dugks_ctx* c, const double* fhat, int on_device) {
   if (!c || !fhat) return fail(DUGKS_EINVAL, "NULL argument");
   c->g1_valid = false;
+  if (c->store) {
+    const double* src = fhat;
+    if (!on_device) {
+      TRY(copy_in(c, c->fbx, fhat, (size_t)c->p.nv * c->p.N, 0));
+      src = c->fbx;
+    }
+    TRY(launch(c, K_CONVERT, [&] { return launch_dev_from_f64(c->p, c->store, c->rho0, src, c->fhat, c->stream); }));
+    return DUGKS_OK;
+  }
   return copy_in(c, c->fhat, fhat, (size_t)c->p.nv * c->p.N, on_device);
 }
 
 int dugks_get_state(dugks_ctx* c, double* fhat, int on_device) {
   if (!c || !fhat) return fail(DUGKS_EINVAL, "NULL argument");
+  if (c->store) {
+    double* dst = on_device ? fhat : c->fbx;
+    TRY(launch(c, K_CONVERT, [&] { return launch_f64_from_dev(c->p, c->store, c->rho0, c->fhat, dst, c->stream); }));
+    if (on_device) return DUGKS_OK;
+    return copy_out(c, fhat, c->fbx, (size_t)c->p.nv * c->p.N, 0);
+  }
   return copy_out(c, fhat, c->fhat, (size_t)c->p.nv * c->p.N, on_device);
 }
 
 int dugks_step(dugks_ctx* c, int n) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
   if (n < 0) return fail(DUGKS_EINVAL, "n must be >= 0");
-  for (int i = 0; i < n; ++i) TRY(c->d2q9 ? one_step_d2q9(c) : one_step(c));
+  for (int i = 0; i < n; ++i)
+    TRY(c->store ? one_step_d2q9m(c) : c->d2q9 ? one_step_d2q9(c) : one_step(c));
   return DUGKS_OK;
 }
 
 int dugks_moments(dugks_ctx* c, double* rho, double* ux, double* uy, int on_device) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
   TRY(launch(c, K_MOMENTS, [&] {
-    return launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
+    return c->store ? launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, c->mom, 0.0, 0.0, 0, c->stream)
+                    : launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
   }));
   const size_t N = c->p.N;
   if (rho) TRY(copy_out(c, rho, c->mom, N, on_device));
@@ -535,7 +594,8 @@ int dugks_check(dugks_ctx* c) {
   cudaError_t e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "dugks_check");
   TRY(launch(c, K_MOMENTS, [&] {
-    return launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
+    return c->store ? launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, c->mom, 0.0, 0.0, 0, c->stream)
+                    : launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
   }));
   TRY(launch(c, K_CHECK, [&] { return launch_check(c->p, c->mom, c->flag, c->stream); }));
   int h = 0;

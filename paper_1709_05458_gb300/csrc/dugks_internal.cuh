@@ -28,6 +28,9 @@ enum KernelId {
   K_D2Q9_PROLOGUE,     // fused D2Q9 path: g1 from f^ after a new state
   K_D2Q9_STAGE1,       // fused D2Q9 path: whole stage 1 (+ cell part of stage 2)
   K_D2Q9_STAGE2,       // fused D2Q9 path: whole stage 2 (+ cell part of next stage 1)
+  K_D2Q9M_STAGE1,      // deviation-storage (FP32/BF16) D2Q9 path, stage 1
+  K_D2Q9M_STAGE2,      // deviation-storage D2Q9 path, stage 2
+  K_CONVERT,           // FP64 <-> deviation storage
   K_NUM
 };
 
@@ -89,6 +92,34 @@ struct D2Q9Params {
   double feq_wall[4][9];      // W_k P(xi_k; u_w)
   double bb[4][9];            // 2 W_k xi_k.u_w / RT
 };
+
+// Mixed-precision D2Q9 path (dugks_d2q9_mixed.cu): arrays hold deviations
+// d = f - W_k rho0 in FP32 (store = 1) or BF16 (store = 2); reconstruction,
+// fluxes and per-velocity equilibrium assembly in FP32, moment sums and the
+// equilibrium parameters (rho, u, polynomial coefficients) in FP64.
+struct D2Q9StageF {
+  float wx[9][3][4];
+  float wy[9][4][3];
+  float wxL[9][3][3], wxR[9][3][3], wyB[9][3][3], wyT[9][3][3];
+  float gamma;
+  float kx[9], ky[9];
+};
+void d2q9_stage_to_float(const D2Q9Stage& s, D2Q9StageF& f);
+cudaError_t launch_d2q9m_stage(const D2Q9Params& p, const D2Q9StageF& s, int store, int stage,
+                               double rho0, const void* gin, const void* own,
+                               const double* rho_in, void* out0, void* out1, double* rho_out,
+                               cudaStream_t st);
+// conversions between FP64 f^ and the deviation storage; moments; equilibrium
+cudaError_t launch_dev_from_f64(const DevParams& p, int store, double rho0, const double* f,
+                                void* d, cudaStream_t st);
+cudaError_t launch_f64_from_dev(const DevParams& p, int store, double rho0, const void* d,
+                                double* f, cudaStream_t st);
+cudaError_t launch_dev_cell(const DevParams& p, int store, double rho0, const void* d,
+                            void* g, double* mom, double a, double b, int write_g,
+                            cudaStream_t st);
+cudaError_t launch_dev_set_eq(const DevParams& p, int store, double rho0, const double* rho,
+                              const double* ux, const double* uy, void* d, cudaStream_t st);
+cudaError_t d2q9m_prepare();
 
 cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage,
                               const double* gin, const double* own, const double* rho_in,
