@@ -46,6 +46,8 @@ FLOPS_PER_UNIT = {
     # part (stage 1: L*, f~', moments, feq', dt Omega', g2, X = 25.9;
     # stage 2: L**, f^, moments, feq, g1 = 13.8)
     "d2q9_stage1": 72.3, "d2q9_stage2": 60.2,
+    # deviation forms: the same arithmetic, mostly in FP32; counted the same way
+    "d2q9m_stage1": 72.3, "d2q9m_stage2": 60.2,
 }
 # Algorithmic DRAM bytes per unit (FP64 values each kernel must read/write once).
 BYTES_PER_UNIT = {
@@ -231,7 +233,8 @@ def run_ours(args):
     dev_index = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     P.load()
-    solver, c, nv = make_solver(P, PV, WL, stream)
+    main_storage = {"fp64": P.FP64, "fp32": P.G_FP32, "bf16": P.G_BF16}[args.storage]
+    solver, c, nv = make_solver(P, PV, WL, stream, storage=main_storage)
     units = c["nx"] * c["ny"] * nv
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -287,7 +290,7 @@ def run_ours(args):
     # the FP32 and BF16 deviation-storage forms on the same workload and
     # protocol; E(u) against the FP64 run after the same W + K steps
     forms = {}
-    if not args.no_forms:
+    if not args.no_forms and args.storage == "fp64":
         for label, st in (("fp32", P.G_FP32), ("bf16", P.G_BF16)):
             s2, _, _ = make_solver(P, PV, WL, stream, storage=st)
             for _ in range(max(args.warmup, 0)):
@@ -317,7 +320,7 @@ def run_ours(args):
     # roofline of the dominant kernel (largest share of device time)
     name, (nl, kms) = max(((k, v) for k, v in prof.items()
                            if k in FLOPS_PER_UNIT and v[0] > 0 and v[1] > 0),
-                          key=lambda kv: kv[1][1])
+                          key=lambda kv: kv[1][1], default=("d2q9_stage1", (1, 0.0)))
     nx, ny = c["nx"], c["ny"]
     per_launch_units = {
         "face_x": nv * ny * (nx + 1), "face_y": nv * (ny + 1) * nx,
@@ -331,7 +334,10 @@ def run_ours(args):
         "metric": "G cell-velocity updates/s (T3S3 step)", "value": value,
         "unit": "G updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32 deviation storage, f64 moment sums",
+                  "bf16": "bf16 deviation storage, f32 arithmetic, f64 moment sums"}[args.storage],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": f"{nx}x{ny}", "velocities": "D2Q9",
                    "bc": "bounce-back walls, moving lid", "Re": 1000, "Ma": 0.1,
                    "units_per_step": units, "l2": "flushed (256 MiB write) before every timed step",
@@ -372,6 +378,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="cavityN (N^2 D2Q9 cavity); the default is the reported workload")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--storage", default="fp64", choices=["fp64", "fp32", "bf16"],
+                    help="storage form of the measured line (default FP64)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32/BF16 deviation-storage forms")
     args = ap.parse_args()

@@ -52,8 +52,12 @@ enum { DUGKS_WEST = 0, DUGKS_EAST = 1, DUGKS_SOUTH = 2, DUGKS_NORTH = 3 };
  *   DUGKS_G_FP32 : per-(cell, velocity) arrays hold the deviation
  *                  d = f - W_k rho0 (rho0 = 1) in FP32; interface stencils,
  *                  fluxes and the per-velocity equilibrium assembly run in
- *                  FP32, the moment sums (Sec. 2.2), 1/rho and the
- *                  equilibrium parameters u/RT, |u|^2/(2RT) in FP64.
+ *                  FP32; the moment sums (Sec. 2.2) are accumulated exactly
+ *                  in 64-bit fixed point (2^-56 resolution) and rounded to
+ *                  FP64; 1/rho and the equilibrium parameters u/RT,
+ *                  |u|^2/(2RT) are FP64.  Deviations must stay below 8 in
+ *                  magnitude (rho below ~18); larger ones turn the moment
+ *                  into NaN, which dugks_check reports as DUGKS_EUNSTABLE.
  *   DUGKS_G_BF16 : as DUGKS_G_FP32 with the deviations stored in BF16.
  * The deviation forms need the D2Q9 listing order of Sec. 2.2 (xi_k =
  * c (k/3 - 1, k%3 - 1)); other sets return DUGKS_ENOTIMPL.  States cross the

@@ -15,6 +15,8 @@
 // |u|^2 / (2 RT) run in FP64 (Sec. 2.2 moments; Sec. 2.1.1 equilibrium).
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "dugks_internal.cuh"
 
 namespace dugks {
@@ -42,10 +44,14 @@ struct MixedConst {
   double rho0;          // reference density of the deviations
   double rho0W;         // rho0 * sum_k W_k
   double sxW, syW;      // rho0 * (sum_{ex=1} W - sum_{ex=-1} W), same for y
+  long long fr0W;       // rho0 sum W in 56-fraction-bit fixed point
+  long long fdr0;       // rho0 (sum W - 1), fixed point
+  long long fsxW, fsyW; // sxW, syW, fixed point
   double inW[4];        // rho0 * sum of W over the velocities hitting each wall
   float W[9];
   float bb[4][9];       // bounce-back: rho_w * bb + (W_opp - W_k) rho0
   float bbc[4][9];
+  float r37, com, a1, b1, a2, b2;   // FP32 copies of the stage coefficients
 };
 
 template <int K> struct Vel {
@@ -82,28 +88,104 @@ __device__ __forceinline__ float yface_valf(const float* __restrict__ s, const D
   return wdotf<q0, q1, c0, c1, 3>(s, &S.wy[K][0][0]);
 }
 
-// FP64 moments of deviations: rho = rho0W + sum d, sx, sy as in the FP64 path
+// Exact FP32 -> FP64 conversion with integer operations.  GB300 executes the
+// F2F conversion instructions on its FP64 pipe (2 per SM per clock), the
+// same pipe the moment sums need; the bit manipulation runs on the integer
+// pipe instead.  Zero and FP32 denormals map to 0, inf/NaN stay inf/NaN.
+__device__ __forceinline__ double f2d_bits(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned em = b & 0x7fffffffu;
+  unsigned hi = (em >> 3) + 0x38000000u;          // exponent rebias 127 -> 1023
+  unsigned lo = em << 29;
+  hi = (em >= 0x7f800000u) ? (0x7ff00000u | ((em & 0x7fffffu) >> 3)) : hi;
+  const bool tiny = em < 0x00800000u;
+  hi = tiny ? 0u : hi;
+  lo = tiny ? 0u : lo;
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
+}
+
+// FP64 -> FP32 with round-to-nearest (ties away) by integer operations, for
+// normal values in FP32 range (the equilibrium parameters); values below the
+// FP32 normal range map to 0, NaN, inf and values beyond the FP32 range to
+// NaN (so that a flagged moment reaches the state and dugks_check).
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int E = (int)((hi >> 20) & 0x7ffu) - 896;
+  unsigned mag = ((unsigned)E << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  mag += (lo >> 28) & 1u;
+  mag = (E <= 0) ? 0u : mag;
+  mag = (E >= 255) ? 0x7fc00000u : mag;
+  return __uint_as_float(mag | (hi & 0x80000000u));
+}
+
+// FP32 value -> signed fixed point with 56 fraction bits (resolution
+// 1.4e-17, comparable to the FP64 rounding of O(0.1) terms).  `bad` is set
+// for |x| >= 8, inf or NaN (nine such terms keep the sum below 2^7), which
+// the caller turns into a NaN moment so that dugks_check reports it.
+__device__ __forceinline__ long long f2fix(float x, unsigned& bad) {
+  const unsigned b = __float_as_uint(x);
+  const int e = (int)((b >> 23) & 0xffu);
+  const unsigned long long m = (unsigned long long)((b & 0x7fffffu) | 0x800000u);
+  const int sh = e - 94;                          // x * 2^56 = m * 2^(e - 94)
+  unsigned long long v = sh >= 0 ? (m << (sh & 63)) : (m >> ((-sh) & 63));
+  v = (sh < -63 || e == 0) ? 0ull : v;
+  bad |= (unsigned)(e >= 130);
+  return (b >> 31) ? -(long long)v : (long long)v;
+}
+
+// fixed point (56 fraction bits) -> FP64, round to nearest, integer pipe only
+__device__ __forceinline__ double fix2d(long long v) {
+  const unsigned long long s = v < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  const unsigned long long n = a << (lz & 63);    // leading one at bit 63
+  const unsigned long long bits =
+      ((unsigned long long)(1023 + 7 - lz) << 52) + ((n >> 11) & 0xfffffffffffffull) +
+      ((n >> 10) & 1ull);
+  return __longlong_as_double((long long)(a == 0 ? 0ull : (bits | s)));
+}
+
+// Moments of f = W rho0 + d (Sec. 2.2): the sums over the nine velocities,
+// including the reference part rho0 W, are accumulated exactly in 64-bit
+// fixed point on the integer pipe and rounded once to FP64 (absolute error
+// <= 1.2e-16, the order of FP64 summation of O(0.1) terms).  dr = rho - rho0.
 __device__ __forceinline__ void dev_sums(const float (&d)[9], const MixedConst& M, double& rho,
-                                         double& sx, double& sy) {
-  double v[9];
+                                         double& dr, double& sx, double& sy) {
+  unsigned bad = 0u;
+  long long v[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) v[k] = (double)d[k];
-  const double a = v[0] + v[1] + v[2];
-  const double b = v[6] + v[7] + v[8];
-  rho = M.rho0W + ((a + b) + (v[3] + v[4] + v[5]));
-  sx = M.sxW + (b - a);
-  sy = M.syW + ((v[2] + v[5] + v[8]) - (v[0] + v[3] + v[6]));
+  for (int k = 0; k < 9; ++k) v[k] = f2fix(d[k], bad);
+  const long long a = v[0] + v[1] + v[2];
+  const long long b = v[6] + v[7] + v[8];
+  const long long r = a + b + (v[3] + v[4] + v[5]);
+  const long long y = (v[2] + v[5] + v[8]) - (v[0] + v[3] + v[6]);
+  rho = bad ? __longlong_as_double(0x7ff8000000000000ll) : fix2d(r + M.fr0W);
+  dr = fix2d(r + M.fdr0);
+  sx = fix2d(b - a + M.fsxW);
+  sy = fix2d(y + M.fsyW);
+}
+
+// 1/x for x in the FP32 normal range: FP32 seed (rcp.approx, integer-pipe
+// conversions) and two FP64 Newton steps, error ~2^-92 before rounding.
+__device__ __forceinline__ double rcp64(double x) {
+  float sf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sf) : "f"(d2f_bits(x)));
+  double r = f2d_bits(sf);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
 }
 
 // Equilibrium deviations W_k (rho P_k - rho0) from FP64 moments: u/RT and the
 // constant part in FP64, per-velocity assembly in FP32.
-__device__ __forceinline__ void dev_feq(double rho, double sx, double sy, const D2Q9Params& P,
-                                        const MixedConst& M, float (&fe)[9]) {
-  const double rinv = 1.0 / rho;
-  const double utx = P.c3 * sx * rinv, uty = P.c3 * sy * rinv;
+__device__ __forceinline__ void dev_feq(double rho, double drho, double sx, double sy,
+                                        const D2Q9Params& P, const MixedConst& M, float (&fe)[9]) {
+  const double rc = P.c3 * rcp64(rho);
+  const double utx = sx * rc, uty = sy * rc;
   const double bm1 = -fma(utx, utx, uty * uty) * P.base_div;     // P - 1 at rest velocity
-  const float ux = (float)utx, uy = (float)uty, b1 = (float)bm1;
-  const float r = (float)rho, dr = (float)(rho - M.rho0);
+  const float ux = d2f_bits(utx), uy = d2f_bits(uty), b1 = d2f_bits(bm1);
+  const float r = d2f_bits(rho), dr = d2f_bits(drho);
   const float sp = ux + uy, sm = ux - uy;
   float p1[9];                                                  // P_k - 1
   p1[4] = b1;
@@ -177,10 +259,10 @@ __device__ __forceinline__ void wall_dev(float (&fb)[9], const float* __restrict
 
 __device__ __forceinline__ void face_recover_dev(float (&fb)[9], const D2Q9StageF& S,
                                                  const D2Q9Params& P, const MixedConst& M) {
-  double rho, sx, sy;
-  dev_sums(fb, M, rho, sx, sy);
+  double rho, dr, sx, sy;
+  dev_sums(fb, M, rho, dr, sx, sy);
   float fe[9];
-  dev_feq(rho, sx, sy, P, M, fe);
+  dev_feq(rho, dr, sx, sy, P, M, fe);
 #pragma unroll
   for (int k = 0; k < 9; ++k) fb[k] = fmaf(S.gamma, fe[k], fb[k]);
 }
@@ -300,13 +382,13 @@ k_d2q9m(D2Q9Params P, D2Q9StageF S, MixedConst M, const T* __restrict__ gin,
         const float g1 = sg[k * stride + (r + HALO) * SW + c + HALO];
         const float fh = ld(own + (size_t)k * N + cell);
         ft[k] = fmaf(1.25f, g1, fmaf(-0.25f, fh, L[k]));
-        X[k] = fmaf(0.25f, fh, fmaf(0.75f, g1, (float)P.r37 * L[k]));
+        X[k] = fmaf(0.25f, fh, fmaf(0.75f, g1, M.r37 * L[k]));
       }
-      double rho, sx, sy;
-      dev_sums(ft, M, rho, sx, sy);
+      double rho, dr, sx, sy;
+      dev_sums(ft, M, rho, dr, sx, sy);
       float fe[9];
-      dev_feq(rho, sx, sy, P, M, fe);
-      const float com = (float)P.c_om34, a2 = (float)P.a2, b2 = (float)P.b2;
+      dev_feq(rho, dr, sx, sy, P, M, fe);
+      const float com = M.com, a2 = M.a2, b2 = M.b2;
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         st(out0 + (size_t)k * N + cell, fmaf(b2, fe[k], a2 * ft[k]));
@@ -317,11 +399,11 @@ k_d2q9m(D2Q9Params P, D2Q9StageF S, MixedConst M, const T* __restrict__ gin,
       float fh[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) fh[k] = ld(own + (size_t)k * N + cell) + L[k];
-      double rho, sx, sy;
-      dev_sums(fh, M, rho, sx, sy);
+      double rho, dr, sx, sy;
+      dev_sums(fh, M, rho, dr, sx, sy);
       float fe[9];
-      dev_feq(rho, sx, sy, P, M, fe);
-      const float a1 = (float)P.a1, b1 = (float)P.b1;
+      dev_feq(rho, dr, sx, sy, P, M, fe);
+      const float a1 = M.a1, b1 = M.b1;
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         st(out0 + (size_t)k * N + cell, fh[k]);
@@ -408,6 +490,16 @@ MixedConst mixed_const(const D2Q9Params& P, double rho0) {
     M.W[k] = (float)P.W[k];
   }
   M.rho0W = rho0 * sw;
+  M.fr0W = llrint(std::ldexp(rho0 * sw, 56));
+  M.fdr0 = llrint(std::ldexp(rho0 * (sw - 1.0), 56));
+  M.fsxW = llrint(std::ldexp(rho0 * sxp, 56));
+  M.fsyW = llrint(std::ldexp(rho0 * syp, 56));
+  M.r37 = (float)P.r37;
+  M.com = (float)P.c_om34;
+  M.a1 = (float)P.a1;
+  M.b1 = (float)P.b1;
+  M.a2 = (float)P.a2;
+  M.b2 = (float)P.b2;
   M.sxW = rho0 * sxp;
   M.syW = rho0 * syp;
   for (int s = 0; s < 4; ++s) {

@@ -85,3 +85,19 @@ def test_state_roundtrip_and_walls(cuda, storage):
     o = O.Setup(nx, ny, 1 / nx, 1 / ny, po[0], po[1], po[2], 0.004, 0.008, bc)
     fo = O.t3s3_run(f0, o, 5)
     assert np.abs(g.state() - fo).max() / np.abs(fo).max() <= 10 * BOUND[storage]["f"]
+
+
+@pytest.mark.parametrize("storage", [P.G_FP32, P.G_BF16], ids=["fp32", "bf16"])
+def test_out_of_range_state_is_reported(cuda, storage):
+    """A deviation beyond the documented range (|f - W rho0| >= 8) must not be
+    laundered into a finite state: the step turns it into NaN and
+    dugks_check reports DUGKS_EUNSTABLE."""
+    xi, W, RT = PV.d2q9(1 / 3)
+    n = 40
+    g = P.Solver(n, n, 1 / n, 1 / n, xi, W, RT, 0.01, 0.01, [(P.PERIODIC, 0, 0)] * 4,
+                 storage=storage)
+    f0 = WL.near_equilibrium_state(OV.d2q9(1 / 3)[1], n, n, amp=0.05, seed=2)
+    f0[4, 20, 20] = 50.0
+    g.set_state(f0)
+    g.step(2)
+    assert g.check() == P.DUGKS_EUNSTABLE
