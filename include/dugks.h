@@ -155,6 +155,45 @@ int dugks_profile_read(dugks_ctx* ctx, long long* launches, double* ms, int n);
 const char* dugks_kernel_name(int id);
 
 /*
+ * Adjoint (reverse-mode derivative) of the T3S3 step, FP64 storage only
+ * (DUGKS_ENOTIMPL otherwise).  It is the exact transpose of the linearised
+ * step of dugks_step (Sec. 2.1.3, Steps (1)-(4)): equilibrium Jacobians of
+ * the cell and face moments, the transposed upwind reconstruction (eq.
+ * flux_DS) and micro-flux (eq. microflux), the bounce-back (eq. BB) and
+ * diffuse-scattering wall rules, and the derivatives of every coefficient
+ * with respect to tau.  Parameter adjoints are ADDED to the caller's
+ * accumulators: dJ_dtau[0], and dJ_duw[8] = (d/d uw_x, d/d uw_y) for the
+ * sides WEST, EAST, SOUTH, NORTH.  Gradient arrays are host pointers.
+ *
+ * dugks_adjoint_step -- lam_out = (d f^^{n+1} / d f^^n)^T lam_in for the step
+ *   taken from the context's current state f^^n (set it first); the
+ *   forward intermediates are recomputed.  lam_in/lam_out [nv][ny][nx].
+ */
+int dugks_adjoint_step(dugks_ctx* ctx, const double* lam_in, double* lam_out, double* dJ_dtau,
+                       double* dJ_duw, int on_device);
+
+/*
+ * dugks_adjoint_run -- run nsteps forward from fhat0, keeping a checkpoint
+ * every `every` steps in device memory (ceil(nsteps/every) + every + 1
+ * state-sized buffers, kept by the context), then sweep backwards from
+ * lam_final = dJ/df^^N, recomputing each segment from its checkpoint.
+ * lam0 receives dJ/df^^0; the parameter adjoints are added as above.  On
+ * return the context's state is f^^N.
+ */
+int dugks_adjoint_run(dugks_ctx* ctx, const double* fhat0, int nsteps, int every,
+                      const double* lam_final, double* lam0, double* dJ_dtau, double* dJ_duw,
+                      int on_device);
+
+/*
+ * dugks_adjoint_equilibrium -- adjoint of dugks_set_equilibrium
+ * (f^ = feq(rho, u), Sec. 2.1.1): from lam = dJ/df^ [nv][ny][nx] writes
+ * dJ/drho, dJ/dux, dJ/duy [ny][nx] (any may be NULL).
+ */
+int dugks_adjoint_equilibrium(dugks_ctx* ctx, const double* rho, const double* ux,
+                              const double* uy, const double* lam, double* drho, double* dux,
+                              double* duy, int on_device);
+
+/*
  * dugks_step_static -- advance nsteps T3S3 steps exactly as dugks_step does,
  * without allocating any device memory.  The paper has no counterpart: this
  * is a facility for callers that may not allocate device memory, such as a

@@ -30,7 +30,8 @@ FP64, G_FP32, G_BF16 = 0, 1, 2
 EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_state",
            "dugks_step", "dugks_moments", "dugks_check", "dugks_synchronize",
            "dugks_profile", "dugks_profile_read", "dugks_kernel_name", "dugks_destroy",
-           "dugks_last_error", "dugks_step_static")
+           "dugks_last_error", "dugks_step_static", "dugks_adjoint_step", "dugks_adjoint_run",
+           "dugks_adjoint_equilibrium")
 
 
 class DugksError(RuntimeError):
@@ -79,6 +80,9 @@ def load(path: str = LIB_PATH):
         "dugks_destroy": (I, [P]),
         "dugks_last_error": (C.c_char_p, []),
         "dugks_step_static": (I, [C.POINTER(Mesh), C.POINTER(VelSet), D, D, C.POINTER(BC), P, P, I, P]),
+        "dugks_adjoint_step": (I, [P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double), I]),
+        "dugks_adjoint_run": (I, [P, P, I, I, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double), I]),
+        "dugks_adjoint_equilibrium": (I, [P, P, P, P, P, P, P, P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -182,6 +186,30 @@ def dugks_destroy(ctx):
 
 def dugks_last_error():
     return load().dugks_last_error().decode()
+
+
+def dugks_adjoint_step(ctx, lam_in, lam_out):
+    """lam_out = (d step / d f^)^T lam_in at the current state; returns
+    (dJ/dtau, dJ/duw[4][2]) contributions of this step."""
+    t = (C.c_double * 1)(0.0)
+    u = (C.c_double * 8)(*([0.0] * 8))
+    _check(load().dugks_adjoint_step(ctx, _ptr(lam_in), _ptr(lam_out), t, u, _on_device(lam_in)))
+    return t[0], np.array(list(u)).reshape(4, 2)
+
+
+def dugks_adjoint_run(ctx, fhat0, nsteps, every, lam_final, lam0):
+    """Checkpointed forward + reverse sweep; returns (dJ/dtau, dJ/duw[4][2])."""
+    t = (C.c_double * 1)(0.0)
+    u = (C.c_double * 8)(*([0.0] * 8))
+    _check(load().dugks_adjoint_run(ctx, _ptr(fhat0), int(nsteps), int(every), _ptr(lam_final),
+                                    _ptr(lam0), t, u, _on_device(fhat0)))
+    return t[0], np.array(list(u)).reshape(4, 2)
+
+
+def dugks_adjoint_equilibrium(ctx, rho, ux, uy, lam, drho=None, dux=None, duy=None):
+    return _check(load().dugks_adjoint_equilibrium(ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(lam),
+                                                   _ptr(drho), _ptr(dux), _ptr(duy),
+                                                   _on_device(lam)))
 
 
 def dugks_step_static(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, fhat_in, fhat_out, nsteps,

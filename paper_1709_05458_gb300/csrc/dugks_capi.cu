@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -72,6 +73,12 @@ struct dugks_ctx {
   int store = 0;
   double rho0 = 1.0;
   D2Q9StageF df1{}, df2{};
+  // adjoint (allocated on first use): forward intermediates and adjoint fields
+  double *a_g1 = nullptr, *a_g2 = nullptr, *a_ftp = nullptr, *a_acc = nullptr;
+  double *a_mom1 = nullptr, *a_mom2 = nullptr, *a_tbar = nullptr, *a_gbar = nullptr;
+  double *a_lam = nullptr, *a_out = nullptr, *a_phix = nullptr, *a_phiy = nullptr;
+  double *a_rhob = nullptr, *a_grads = nullptr;
+  std::vector<double*> ckpt;    // checkpoint store for dugks_adjoint_run
   // profiling
   bool prof = false;
   std::vector<Pending> pending;
@@ -158,8 +165,12 @@ int copy_out(dugks_ctx* c, double* dst, const double* src, size_t n, int on_devi
 }
 
 void free_all(dugks_ctx* c) {
-  double* bufs[] = {c->fhat, c->ftp, c->acc, c->g, c->fbx, c->fby, c->mom, c->vel};
+  double* bufs[] = {c->fhat, c->ftp, c->acc, c->g, c->fbx, c->fby, c->mom, c->vel,
+                    c->a_g1, c->a_g2, c->a_ftp, c->a_acc, c->a_mom1, c->a_mom2, c->a_tbar,
+                    c->a_gbar, c->a_lam, c->a_out, c->a_phix, c->a_phiy, c->a_rhob, c->a_grads};
   for (double* b : bufs)
+    if (b) cudaFree(b);
+  for (double* b : c->ckpt)
     if (b) cudaFree(b);
   if (c->opp) cudaFree(c->opp);
   if (c->flag) cudaFree(c->flag);
@@ -291,6 +302,94 @@ int one_step(dugks_ctx* c) {
 }
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int advance(dugks_ctx* c) {
+  return c->store ? one_step_d2q9m(c) : c->d2q9 ? one_step_d2q9(c) : one_step(c);
+}
+
+int ensure_adjoint(dugks_ctx* c) {
+  if (c->a_grads) return DUGKS_OK;
+  const size_t nvN = (size_t)c->p.nv * c->p.N, N = c->p.N;
+  const size_t nfx = (size_t)c->p.nv * c->p.ny * (c->p.nx + 1);
+  const size_t nfy = (size_t)c->p.nv * (c->p.ny + 1) * c->p.nx;
+  cudaError_t e = cudaSuccess;
+  auto al = [&](double** p, size_t n) {
+    if (e == cudaSuccess) e = cudaMalloc((void**)p, n * sizeof(double));
+  };
+  al(&c->a_g1, nvN); al(&c->a_g2, nvN); al(&c->a_ftp, nvN); al(&c->a_acc, nvN);
+  al(&c->a_mom1, 3 * N); al(&c->a_mom2, 3 * N); al(&c->a_tbar, nvN); al(&c->a_gbar, nvN);
+  al(&c->a_lam, nvN); al(&c->a_out, nvN); al(&c->a_phix, nfx); al(&c->a_phiy, nfy);
+  al(&c->a_rhob, N); al(&c->a_grads, 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? DUGKS_ENOMEM : DUGKS_ECUDA,
+                std::string("adjoint buffers: ") + cudaGetErrorString(e));
+  }
+  return DUGKS_OK;
+}
+
+#define CK(x)                                       \
+  do {                                              \
+    cudaError_t e__ = (x);                          \
+    if (e__ != cudaSuccess) return cuda_fail(e__, "adjoint"); \
+  } while (0)
+
+// Adjoint of one T3S3 step taken from the current state c->fhat:
+// a_lam = lambda^{n+1} in, a_out = lambda^n out, a_grads[0..8] += parameter
+// adjoints.  Forward intermediates are recomputed by the generic kernels.
+int adjoint_core(dugks_ctx* c) {
+  const DevParams& p = c->p;
+  cudaStream_t s = c->stream;
+  const int G = c->groups;
+  const size_t nvN = (size_t)p.nv * p.N;
+  const double tau = p.tau, dt = p.dt;
+  // forward recomputation
+  CK(launch_cell(p, G, 1, c->fhat, c->a_g1, c->a_mom1, c->s1.a, c->s1.b, s));
+  CK(launch_face(p, G, 0, c->a_g1, c->a_mom1, c->fbx, c->s1, s));
+  CK(launch_face(p, G, 1, c->a_g1, c->a_mom1, c->fby, c->s1, s));
+  CK(launch_update1(p, c->fhat, c->a_g1, c->fbx, c->fby, c->a_ftp, c->a_acc, s));
+  CK(launch_cell(p, G, 2, c->a_ftp, c->a_g2, c->a_mom2, c->s2.a, c->s2.b, s));
+  // tau-derivatives of the coefficients
+  const double c34 = 0.75 * c->c_om;
+  const double da1 = 48.0 * dt / ((12 * tau + 3 * dt) * (12 * tau + 3 * dt));
+  const double da2 = 216.0 * dt / ((24 * tau + 4 * dt) * (24 * tau + 4 * dt));
+  const double dc = 27.0 * dt / ((6 * tau + dt) * (6 * tau + dt));
+  const double dal1 = 2 * c->s1.h / ((2 * tau + c->s1.h) * (2 * tau + c->s1.h));
+  const double dal2 = 2 * c->s2.h / ((2 * tau + c->s2.h) * (2 * tau + c->s2.h));
+  const size_t N = p.N;
+  // stage 2: f^^{n+1} = X + c (f~' - feq') + 4dt/7 L**
+  CK(launch_axpby(nvN, c->a_lam, c34, nullptr, 0.0, c->a_tbar, s));
+  CK(launch_flux_T(p, 0, c->a_lam, 4.0 * dt / 7.0, nullptr, 0.0, c->a_phix, s));
+  CK(launch_flux_T(p, 1, c->a_lam, 4.0 * dt / 7.0, nullptr, 0.0, c->a_phiy, s));
+  CK(cudaMemsetAsync(c->a_gbar, 0, nvN * sizeof(double), s));
+  CK(cudaMemsetAsync(c->a_rhob, 0, N * sizeof(double), s));
+  CK(launch_face_T(p, 0, c->a_g2, c->a_mom2, c->a_phix, c->a_gbar, c->a_rhob, c->a_grads, c->s2, dal2, s));
+  CK(launch_face_T(p, 1, c->a_g2, c->a_mom2, c->a_phiy, c->a_gbar, c->a_rhob, c->a_grads, c->s2, dal2, s));
+  CK(launch_cell_T(p, c->a_ftp, c->a_gbar, c->a_lam, c->a_rhob, c->a_tbar, c->s2.a, c->s2.b, c34,
+                   da2, dc, c->a_grads, s));
+  // stage 1: f~' = 5/4 g1 - 1/4 f^ + dt/3 L*,  X = 1/4 f^ + 3/4 g1 + 3dt/7 L*
+  CK(launch_axpby(nvN, c->a_tbar, 1.25, c->a_lam, 0.75, c->a_gbar, s));
+  CK(launch_axpby(nvN, c->a_tbar, -0.25, c->a_lam, 0.25, c->a_out, s));
+  CK(launch_flux_T(p, 0, c->a_tbar, dt / 3.0, c->a_lam, 3.0 * dt / 7.0, c->a_phix, s));
+  CK(launch_flux_T(p, 1, c->a_tbar, dt / 3.0, c->a_lam, 3.0 * dt / 7.0, c->a_phiy, s));
+  CK(cudaMemsetAsync(c->a_rhob, 0, N * sizeof(double), s));
+  CK(launch_face_T(p, 0, c->a_g1, c->a_mom1, c->a_phix, c->a_gbar, c->a_rhob, c->a_grads, c->s1, dal1, s));
+  CK(launch_face_T(p, 1, c->a_g1, c->a_mom1, c->a_phiy, c->a_gbar, c->a_rhob, c->a_grads, c->s1, dal1, s));
+  CK(launch_cell_T(p, c->fhat, c->a_gbar, nullptr, c->a_rhob, c->a_out, c->s1.a, c->s1.b, 0.0,
+                   da1, 0.0, c->a_grads, s));
+  return DUGKS_OK;
+}
+
+int read_grads(dugks_ctx* c, double* dJ_dtau, double* dJ_duw) {
+  double h[9];
+  cudaError_t e = cudaMemcpyAsync(h, c->a_grads, 9 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint gradients");
+  if (dJ_dtau) *dJ_dtau += h[0];
+  if (dJ_duw)
+    for (int i = 0; i < 8; ++i) dJ_duw[i] += h[1 + i];
+  return DUGKS_OK;
+}
 
 }  // namespace
 
@@ -636,6 +735,94 @@ int dugks_profile_read(dugks_ctx* c, long long* launches, double* ms, int n) {
     if (ms) ms[i] = c->ms[i];
   }
   return K_NUM;
+}
+
+int dugks_adjoint_step(dugks_ctx* c, const double* lam_in, double* lam_out, double* dJ_dtau,
+                       double* dJ_duw, int on_device) {
+  if (!c || !lam_in || !lam_out) return fail(DUGKS_EINVAL, "NULL argument");
+  if (c->store) return fail(DUGKS_ENOTIMPL, "the adjoint needs DUGKS_FP64 storage");
+  TRY(ensure_adjoint(c));
+  const size_t nvN = (size_t)c->p.nv * c->p.N;
+  CK(cudaMemsetAsync(c->a_grads, 0, 16 * sizeof(double), c->stream));
+  TRY(copy_in(c, c->a_lam, lam_in, nvN, on_device));
+  TRY(adjoint_core(c));
+  TRY(copy_out(c, lam_out, c->a_out, nvN, on_device));
+  return read_grads(c, dJ_dtau, dJ_duw);
+}
+
+int dugks_adjoint_run(dugks_ctx* c, const double* fhat0, int nsteps, int every,
+                      const double* lam_final, double* lam0, double* dJ_dtau, double* dJ_duw,
+                      int on_device) {
+  if (!c || !fhat0 || !lam_final || !lam0) return fail(DUGKS_EINVAL, "NULL argument");
+  if (nsteps < 0 || every < 1) return fail(DUGKS_EINVAL, "nsteps >= 0 and every >= 1 required");
+  if (c->store) return fail(DUGKS_ENOTIMPL, "the adjoint needs DUGKS_FP64 storage");
+  TRY(ensure_adjoint(c));
+  const size_t nvN = (size_t)c->p.nv * c->p.N;
+  const int nseg = (nsteps + every - 1) / every;
+  const size_t need = (size_t)nseg + (size_t)every + 1;   // checkpoints + one segment + f^N
+  while (c->ckpt.size() < need) {
+    double* b = nullptr;
+    cudaError_t e = cudaMalloc((void**)&b, nvN * sizeof(double));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DUGKS_ENOMEM, "checkpoint store: " + std::string(cudaGetErrorString(e)));
+    }
+    c->ckpt.push_back(b);
+  }
+  double** cp = c->ckpt.data();               // cp[0..nseg): checkpoints
+  double** seg = cp + nseg;                   // seg[0..every): states of one segment
+  double* fin = cp[need - 1];                 // f^N
+  auto set_dev = [&](const double* src) {
+    c->g1_valid = false;
+    return cudaMemcpyAsync(c->fhat, src, nvN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+  };
+  // forward with checkpoints
+  TRY(copy_in(c, c->fhat, fhat0, nvN, on_device));
+  c->g1_valid = false;
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % every == 0)
+      CK(cudaMemcpyAsync(cp[n / every], c->fhat, nvN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    TRY(advance(c));
+  }
+  CK(cudaMemcpyAsync(fin, c->fhat, nvN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  // reverse sweep, recomputing each segment from its checkpoint
+  CK(cudaMemsetAsync(c->a_grads, 0, 16 * sizeof(double), c->stream));
+  TRY(copy_in(c, c->a_lam, lam_final, nvN, on_device));
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int start = sg * every, len = std::min(every, nsteps - start);
+    CK(set_dev(cp[sg]));
+    for (int m = 0; m < len; ++m) {
+      CK(cudaMemcpyAsync(seg[m], c->fhat, nvN * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      if (m + 1 < len) TRY(advance(c));
+    }
+    for (int m = len - 1; m >= 0; --m) {
+      CK(set_dev(seg[m]));
+      TRY(adjoint_core(c));
+      std::swap(c->a_lam, c->a_out);
+    }
+  }
+  TRY(copy_out(c, lam0, c->a_lam, nvN, on_device));
+  CK(set_dev(fin));
+  return read_grads(c, dJ_dtau, dJ_duw);
+}
+
+int dugks_adjoint_equilibrium(dugks_ctx* c, const double* rho, const double* ux,
+                              const double* uy, const double* lam, double* drho, double* dux,
+                              double* duy, int on_device) {
+  if (!c || !rho || !ux || !uy || !lam) return fail(DUGKS_EINVAL, "NULL argument");
+  TRY(ensure_adjoint(c));
+  const size_t N = c->p.N, nvN = (size_t)c->p.nv * N;
+  // stage everything through adjoint buffers (a_mom1: rho, ux, uy; a_lam; a_mom2: outputs)
+  TRY(copy_in(c, c->a_mom1, rho, N, on_device));
+  TRY(copy_in(c, c->a_mom1 + N, ux, N, on_device));
+  TRY(copy_in(c, c->a_mom1 + 2 * N, uy, N, on_device));
+  TRY(copy_in(c, c->a_lam, lam, nvN, on_device));
+  CK(launch_eq_T(c->p, c->a_mom1, c->a_mom1 + N, c->a_mom1 + 2 * N, c->a_lam, c->a_mom2,
+                 c->a_mom2 + N, c->a_mom2 + 2 * N, c->stream));
+  if (drho) TRY(copy_out(c, drho, c->a_mom2, N, on_device));
+  if (dux) TRY(copy_out(c, dux, c->a_mom2 + N, N, on_device));
+  if (duy) TRY(copy_out(c, duy, c->a_mom2 + 2 * N, N, on_device));
+  return DUGKS_OK;
 }
 
 int dugks_destroy(dugks_ctx* c) {

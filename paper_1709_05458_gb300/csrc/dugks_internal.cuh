@@ -127,6 +127,22 @@ cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage
 size_t d2q9_smem_bytes(int ty);
 cudaError_t d2q9_prepare(int ty);
 
+// Adjoint kernels (dugks_adjoint.cu); grads = [tau, uw_x(W), uw_y(W), uw_x(E), ...].
+cudaError_t launch_flux_T(const DevParams& p, int dir, const double* A, double sa,
+                          const double* B, double sb, double* phi, cudaStream_t s);
+cudaError_t launch_face_T(const DevParams& p, int dir, const double* g, const double* mom,
+                          double* phi, double* gbar, double* rhobar, double* grads,
+                          const StageCoef& c, double dalpha, cudaStream_t s);
+cudaError_t launch_cell_T(const DevParams& p, const double* x, const double* gbar,
+                          const double* lam, const double* rhobar, double* xbar, double a,
+                          double b, double c_extra, double da, double dc, double* grads,
+                          cudaStream_t s);
+cudaError_t launch_axpby(size_t n, const double* A, double sa, const double* B, double sb,
+                         double* out, cudaStream_t s);
+cudaError_t launch_eq_T(const DevParams& p, const double* rho, const double* ux,
+                        const double* uy, const double* lam, double* drho, double* dux,
+                        double* duy, cudaStream_t s);
+
 // Sets the message returned by dugks_last_error() on the calling thread.
 void set_last_error(const std::string& msg);
 
