@@ -155,6 +155,37 @@ int dugks_profile_read(dugks_ctx* ctx, long long* launches, double* ms, int n);
 const char* dugks_kernel_name(int id);
 
 /*
+ * dugks_autotune -- choose the tile height of the fused D2Q9 kernels for this
+ * problem by timing `trials` steps for every height 4..16 on the context's
+ * own stream and state (f^ is saved and restored; the state is unchanged on
+ * return).  The chosen height is kept by the context and written to *ty_out.
+ * Other velocity sets: DUGKS_ENOTIMPL.  Results of later steps are
+ * identical for every tile height (same arithmetic per face and cell).
+ */
+int dugks_autotune(dugks_ctx* ctx, int trials, int* ty_out);
+
+/*
+ * Batched stepping of many independent problems (contexts) in one CUDA
+ * graph.  All FP64 D2Q9 contexts of the batch advance together through one
+ * persistent launch per stage whose blocks take (instance, tile) work items
+ * from an atomic counter, so uneven grid sizes and parameters share the
+ * GPU; the other contexts (Newton-Cotes sets, deviation storage) run their
+ * own launches inside the same graph.  The contexts must share one
+ * non-default stream; their parameters and tile heights are read at
+ * dugks_batch_create (autotune before creating the batch).
+ *   dugks_batch_create  -- ctxs[n] (borrowed; keep them alive while the
+ *                          batch exists) -> *out.
+ *   dugks_batch_step    -- advance every context nsteps steps: the graph for
+ *                          this nsteps is captured on first use and replayed
+ *                          afterwards (asynchronous on the stream).
+ *   dugks_batch_destroy -- free the batch (not the contexts).
+ */
+typedef struct dugks_batch dugks_batch;
+int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out);
+int dugks_batch_step(dugks_batch* batch, int nsteps);
+int dugks_batch_destroy(dugks_batch* batch);
+
+/*
  * Adjoint (reverse-mode derivative) of the T3S3 step, FP64 storage only
  * (DUGKS_ENOTIMPL otherwise).  It is the exact transpose of the linearised
  * step of dugks_step (Sec. 2.1.3, Steps (1)-(4)): equilibrium Jacobians of

@@ -31,7 +31,8 @@ EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_
            "dugks_step", "dugks_moments", "dugks_check", "dugks_synchronize",
            "dugks_profile", "dugks_profile_read", "dugks_kernel_name", "dugks_destroy",
            "dugks_last_error", "dugks_step_static", "dugks_adjoint_step", "dugks_adjoint_run",
-           "dugks_adjoint_equilibrium")
+           "dugks_adjoint_equilibrium", "dugks_autotune", "dugks_batch_create",
+           "dugks_batch_step", "dugks_batch_destroy")
 
 
 class DugksError(RuntimeError):
@@ -83,6 +84,10 @@ def load(path: str = LIB_PATH):
         "dugks_adjoint_step": (I, [P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double), I]),
         "dugks_adjoint_run": (I, [P, P, I, I, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double), I]),
         "dugks_adjoint_equilibrium": (I, [P, P, P, P, P, P, P, P, I]),
+        "dugks_autotune": (I, [P, I, C.POINTER(C.c_int)]),
+        "dugks_batch_create": (I, [C.POINTER(P), I, C.POINTER(P)]),
+        "dugks_batch_step": (I, [P, I]),
+        "dugks_batch_destroy": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -210,6 +215,53 @@ def dugks_adjoint_equilibrium(ctx, rho, ux, uy, lam, drho=None, dux=None, duy=No
     return _check(load().dugks_adjoint_equilibrium(ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(lam),
                                                    _ptr(drho), _ptr(dux), _ptr(duy),
                                                    _on_device(lam)))
+
+
+def dugks_autotune(ctx, trials=3):
+    """Time tile heights 4..16 for this context's fused D2Q9 kernels and keep
+    the fastest (state unchanged); returns the chosen height."""
+    ty = C.c_int(0)
+    _check(load().dugks_autotune(ctx, int(trials), C.byref(ty)))
+    return ty.value
+
+
+def dugks_batch_create(ctxs):
+    arr = (C.c_void_p * len(ctxs))(*ctxs)
+    out = C.c_void_p()
+    _check(load().dugks_batch_create(arr, len(ctxs), C.byref(out)))
+    return out.value
+
+
+def dugks_batch_step(batch, nsteps=1):
+    return _check(load().dugks_batch_step(batch, int(nsteps)))
+
+
+def dugks_batch_destroy(batch):
+    return _check(load().dugks_batch_destroy(batch))
+
+
+class Batch:
+    """Many Solvers advanced together (one persistent launch per stage for
+    the FP64 D2Q9 ones, everything inside one CUDA graph per step count).
+    The solvers must share one non-default stream."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.handle = dugks_batch_create([s.ctx for s in self.solvers])
+
+    def step(self, n=1):
+        dugks_batch_step(self.handle, n)
+
+    def close(self):
+        if self.handle:
+            dugks_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def dugks_step_static(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, fhat_in, fhat_out, nsteps,

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -108,6 +109,17 @@ struct dugks_ctx {
     }
     pending.clear();
   }
+};
+
+struct dugks_batch {
+  std::vector<dugks_ctx*> ctxs;
+  std::vector<dugks_ctx*> own;      // instances run by their own launches
+  cudaStream_t stream = nullptr;
+  D2Q9BatchItem* items = nullptr;   // device
+  int* tile_start = nullptr;        // device, nitems + 1
+  int* counters = nullptr;          // device, 2
+  int nitems = 0, max_ty = 1, blocks = 0;
+  std::map<int, cudaGraphExec_t> graphs;
 };
 
 namespace {
@@ -305,6 +317,22 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 int advance(dugks_ctx* c) {
   return c->store ? one_step_d2q9m(c) : c->d2q9 ? one_step_d2q9(c) : one_step(c);
+}
+
+// g1 of the current state for the fused paths (run eagerly before capture)
+int ensure_g1(dugks_ctx* c) {
+  if (!c->d2q9 || c->g1_valid) return DUGKS_OK;
+  cudaStream_t s = c->stream;
+  if (c->store)
+    TRY(launch(c, K_D2Q9_PROLOGUE, [&] {
+      return launch_dev_cell(c->p, c->store, c->rho0, c->fhat, c->g, c->mom, c->s1.a, c->s1.b, 1, s);
+    }));
+  else
+    TRY(launch(c, K_D2Q9_PROLOGUE, [&] {
+      return launch_cell(c->p, 1, 1, c->fhat, c->g, c->mom, c->s1.a, c->s1.b, s);
+    }));
+  c->g1_valid = true;
+  return DUGKS_OK;
 }
 
 int ensure_adjoint(dugks_ctx* c) {
@@ -822,6 +850,166 @@ int dugks_adjoint_equilibrium(dugks_ctx* c, const double* rho, const double* ux,
   if (drho) TRY(copy_out(c, drho, c->a_mom2, N, on_device));
   if (dux) TRY(copy_out(c, dux, c->a_mom2 + N, N, on_device));
   if (duy) TRY(copy_out(c, duy, c->a_mom2 + 2 * N, N, on_device));
+  return DUGKS_OK;
+}
+
+int dugks_autotune(dugks_ctx* c, int trials, int* ty_out) {
+  if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  if (!c->d2q9) return fail(DUGKS_ENOTIMPL, "tile autotuning applies to the D2Q9 kernels");
+  if (trials < 1) trials = 3;
+  const size_t bytes = (size_t)c->p.nv * c->p.N * sizeof(double);
+  cudaStream_t s = c->stream;
+  const bool prof = c->prof;
+  c->prof = false;
+  CK(cudaMemcpyAsync(c->fbx, c->fhat, bytes, cudaMemcpyDeviceToDevice, s));   // save f^
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  int best = c->dp.ty;
+  float best_ms = 1e30f;
+  for (int ty = 4; ty <= 16; ++ty) {
+    c->dp.ty = ty;
+    c->g1_valid = false;
+    int rc = advance(c);                                  // warm-up incl. the prologue
+    if (rc == DUGKS_OK) rc = cudaEventRecord(a, s) == cudaSuccess ? DUGKS_OK : DUGKS_ECUDA;
+    for (int i = 0; i < trials && rc == DUGKS_OK; ++i) rc = advance(c);
+    if (rc == DUGKS_OK) rc = cudaEventRecord(b, s) == cudaSuccess ? DUGKS_OK : DUGKS_ECUDA;
+    float ms = 0.f;
+    if (rc == DUGKS_OK && cudaEventSynchronize(b) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, a, b) == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best = ty;
+    }
+    CK(cudaMemcpyAsync(c->fhat, c->fbx, bytes, cudaMemcpyDeviceToDevice, s));  // restore f^
+    if (rc != DUGKS_OK) {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      c->prof = prof;
+      return rc;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  c->dp.ty = best;
+  c->g1_valid = false;
+  c->prof = prof;
+  if (ty_out) *ty_out = best;
+  return dugks_synchronize(c);
+}
+
+int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
+  if (!out) return fail(DUGKS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctxs || n < 1) return fail(DUGKS_EINVAL, "empty batch");
+  for (int i = 0; i < n; ++i) {
+    if (!ctxs[i]) return fail(DUGKS_EINVAL, "NULL context in the batch");
+    if (ctxs[i]->stream != ctxs[0]->stream)
+      return fail(DUGKS_EINVAL, "batched contexts must share one stream");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(DUGKS_EINVAL, "a context appears twice in the batch");
+  }
+  if (!ctxs[0]->stream) return fail(DUGKS_EINVAL, "batching needs a non-default stream (graph capture)");
+  dugks_batch* b = new dugks_batch();
+  b->stream = ctxs[0]->stream;
+  std::vector<D2Q9BatchItem> items;
+  std::vector<int> start(1, 0);
+  for (int i = 0; i < n; ++i) {
+    dugks_ctx* c = ctxs[i];
+    b->ctxs.push_back(c);
+    if (!(c->d2q9 && c->store == 0)) {
+      b->own.push_back(c);
+      continue;
+    }
+    D2Q9BatchItem it{};
+    it.P = c->dp;
+    it.S1 = c->ds1;
+    it.S2 = c->ds2;
+    it.fhat = c->fhat;
+    it.g1 = c->g;
+    it.g2 = c->ftp;
+    it.X = c->acc;
+    it.mom = c->mom;
+    it.tiles_x = (c->p.nx + 31) / 32;
+    const int tiles = it.tiles_x * ((c->p.ny + c->dp.ty - 1) / c->dp.ty);
+    start.push_back(start.back() + tiles);
+    b->max_ty = std::max(b->max_ty, c->dp.ty);
+    items.push_back(it);
+  }
+  b->nitems = (int)items.size();
+  cudaError_t e = cudaSuccess;
+  if (b->nitems) {
+    e = cudaMalloc((void**)&b->items, items.size() * sizeof(D2Q9BatchItem));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->tile_start, start.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->counters, 2 * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->items, items.data(), items.size() * sizeof(D2Q9BatchItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(b->tile_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice);
+    int dev = 0, sms = 152;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->blocks = sms * d2q9_batch_blocks_per_sm(b->max_ty);
+  }
+  if (e != cudaSuccess) {
+    dugks_batch_destroy(b);
+    return cuda_fail(e, "dugks_batch_create");
+  }
+  *out = b;
+  return DUGKS_OK;
+}
+
+int dugks_batch_step(dugks_batch* b, int nsteps) {
+  if (!b) return fail(DUGKS_EINVAL, "NULL batch");
+  if (nsteps < 0) return fail(DUGKS_EINVAL, "nsteps must be >= 0");
+  if (nsteps == 0) return DUGKS_OK;
+  for (dugks_ctx* c : b->ctxs) TRY(ensure_g1(c));
+  auto found = b->graphs.find(nsteps);
+  if (found == b->graphs.end()) {
+    std::vector<bool> prof;
+    for (dugks_ctx* c : b->ctxs) {
+      prof.push_back(c->prof);
+      c->prof = false;
+    }
+    cudaStream_t s = b->stream;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? DUGKS_OK : cuda_fail(e, "begin capture");
+    for (int i = 0; i < nsteps && rc == DUGKS_OK; ++i) {
+      if (b->nitems) {
+        e = cudaMemsetAsync(b->counters, 0, 2 * sizeof(int), s);
+        if (e == cudaSuccess)
+          e = launch_d2q9_batch(1, b->items, b->tile_start, b->nitems, b->max_ty, b->counters, b->blocks, s);
+        if (e == cudaSuccess)
+          e = launch_d2q9_batch(2, b->items, b->tile_start, b->nitems, b->max_ty, b->counters + 1, b->blocks, s);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batched launch");
+      }
+      for (size_t k = 0; k < b->own.size() && rc == DUGKS_OK; ++k) rc = advance(b->own[k]);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    for (size_t k = 0; k < b->ctxs.size(); ++k) b->ctxs[k]->prof = prof[k];
+    if (rc == DUGKS_OK && e != cudaSuccess) rc = cuda_fail(e, "end capture");
+    cudaGraphExec_t x = nullptr;
+    if (rc == DUGKS_OK) {
+      e = cudaGraphInstantiate(&x, g, 0);
+      if (e != cudaSuccess) rc = cuda_fail(e, "graph instantiate");
+    }
+    if (g) cudaGraphDestroy(g);
+    if (rc != DUGKS_OK) return rc;
+    found = b->graphs.emplace(nsteps, x).first;
+  }
+  cudaError_t e = cudaGraphLaunch(found->second, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+  return DUGKS_OK;
+}
+
+int dugks_batch_destroy(dugks_batch* b) {
+  if (!b) return DUGKS_OK;
+  cudaStreamSynchronize(b->stream);
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  if (b->items) cudaFree(b->items);
+  if (b->tile_start) cudaFree(b->tile_start);
+  if (b->counters) cudaFree(b->counters);
+  delete b;
   return DUGKS_OK;
 }
 

@@ -131,12 +131,16 @@ __device__ __forceinline__ int resolve1(int x, int n, bool per, int (&i)[3], dou
 }
 
 // ---------------------------------------------------------------- kernel
+// One 32 x P.ty tile of one stage (all phases); every thread of the block
+// takes part (blockDim.x >= 32 (P.ty + 1)).
 template <int STAGE>
-__global__ void __launch_bounds__(kMaxThreads)
-k_d2q9(D2Q9Params P, D2Q9Stage S, const double* __restrict__ gin,
-       const double* __restrict__ own, const double* __restrict__ rho_in,
-       double* __restrict__ out0, double* __restrict__ out1, double* __restrict__ rho_out) {
-  extern __shared__ double smem[];
+__device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& S,
+                                          const double* __restrict__ gin,
+                                          const double* __restrict__ own,
+                                          const double* __restrict__ rho_in,
+                                          double* __restrict__ out0, double* __restrict__ out1,
+                                          double* __restrict__ rho_out, int x0, int y0,
+                                          double* __restrict__ smem) {
   const int TY = P.ty;
   const int SH = TY + 2 * HALO;
   double* sg = smem;                               // [9][SH][SW]
@@ -144,7 +148,6 @@ k_d2q9(D2Q9Params P, D2Q9Stage S, const double* __restrict__ gin,
   double* sfy = sfx + 9 * TY * (TX + 1);           // [9][TY+1][TX]
   const int nx = P.nx, ny = P.ny, N = P.N;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
 
   // phase 0: g tile with a 2-cell halo (wrap or wall ghosts)
   for (int p = tid; p < SH * SW; p += nthr) {
@@ -357,6 +360,53 @@ k_d2q9(D2Q9Params P, D2Q9Stage S, const double* __restrict__ gin,
   }
 }
 
+template <int STAGE>
+__global__ void __launch_bounds__(kMaxThreads)
+k_d2q9(D2Q9Params P, D2Q9Stage S, const double* __restrict__ gin,
+       const double* __restrict__ own, const double* __restrict__ rho_in,
+       double* __restrict__ out0, double* __restrict__ out1, double* __restrict__ rho_out) {
+  extern __shared__ double smem[];
+  d2q9_tile<STAGE>(P, S, gin, own, rho_in, out0, out1, rho_out, blockIdx.x * TX,
+                   blockIdx.y * P.ty, smem);
+}
+
+// Persistent batched stage kernel: blocks take (instance, tile) work items
+// from an atomic counter until all tiles of all instances are done (no
+// waiting on other blocks).  Instance parameters and stage tables are read
+// through the read-only cache.
+template <int STAGE>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+k_d2q9_batch(const D2Q9BatchItem* __restrict__ items, const int* __restrict__ tile_start,
+             int nitems, int* __restrict__ counter) {
+  extern __shared__ double smem[];
+  __shared__ int s_tile, s_item;
+  const int total = tile_start[nitems];
+  for (int guard = 0; guard < (1 << 30); ++guard) {
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(counter, 1);
+      int lo = 0, hi = nitems - 1;
+      while (lo < hi) {                 // last item with tile_start <= t
+        const int mid = (lo + hi + 1) >> 1;
+        if (tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+      }
+      s_tile = t;
+      s_item = lo;
+    }
+    __syncthreads();
+    const int t = s_tile, it = s_item;
+    __syncthreads();
+    if (t >= total) break;
+    const D2Q9BatchItem& I = items[it];
+    const int local = t - tile_start[it];
+    const int bx = local % I.tiles_x, by = local / I.tiles_x;
+    if constexpr (STAGE == 1)
+      d2q9_tile<1>(I.P, I.S1, I.g1, I.fhat, I.mom, I.g2, I.X, I.mom + I.P.N, bx * TX, by * I.P.ty, smem);
+    else
+      d2q9_tile<2>(I.P, I.S2, I.g2, I.X, I.mom + I.P.N, I.fhat, I.g1, I.mom, bx * TX, by * I.P.ty, smem);
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 size_t d2q9_smem_bytes(int ty) {
@@ -371,7 +421,27 @@ cudaError_t d2q9_prepare(int ty) {
   cudaError_t e = cudaFuncSetAttribute(k_d2q9<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_d2q9<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_d2q9_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_d2q9_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;
+}
+
+cudaError_t launch_d2q9_batch(int stage, const D2Q9BatchItem* items, const int* tile_start,
+                              int nitems, int max_ty, int* counter, int blocks, cudaStream_t st) {
+  const int threads = TX * (max_ty + 1);
+  const size_t bytes = d2q9_smem_bytes(max_ty);
+  if (stage == 1) k_d2q9_batch<1><<<blocks, threads, bytes, st>>>(items, tile_start, nitems, counter);
+  else k_d2q9_batch<2><<<blocks, threads, bytes, st>>>(items, tile_start, nitems, counter);
+  return cudaGetLastError();
+}
+
+int d2q9_batch_blocks_per_sm(int max_ty) {
+  int n = 0;
+  const int threads = TX * (max_ty + 1);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_d2q9_batch<1>, threads, d2q9_smem_bytes(max_ty));
+  return n < 1 ? 1 : n;
 }
 
 cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage,

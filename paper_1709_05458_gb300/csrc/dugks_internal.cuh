@@ -121,6 +121,17 @@ cudaError_t launch_dev_set_eq(const DevParams& p, int store, double rho0, const 
                               const double* ux, const double* uy, void* d, cudaStream_t st);
 cudaError_t d2q9m_prepare();
 
+// One instance of a batched D2Q9 FP64 launch (device memory).
+struct D2Q9BatchItem {
+  D2Q9Params P;
+  D2Q9Stage S1, S2;
+  double *fhat, *g1, *g2, *X, *mom;
+  int tiles_x, pad;
+};
+cudaError_t launch_d2q9_batch(int stage, const D2Q9BatchItem* items, const int* tile_start,
+                              int nitems, int max_ty, int* counter, int blocks, cudaStream_t st);
+int d2q9_batch_blocks_per_sm(int max_ty);
+
 cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage,
                               const double* gin, const double* own, const double* rho_in,
                               double* out0, double* out1, double* rho_out, cudaStream_t st);

@@ -1,0 +1,85 @@
+"""Batched stepping (one persistent launch per stage for the FP64 D2Q9
+instances, CUDA graph per step count) and tile autotuning.  The batched
+results must be bit-for-bit those of stepping each problem alone (the same
+per-face and per-cell arithmetic), and the autotuner must leave the state
+and the later results unchanged."""
+import numpy as np
+import pytest
+
+import paper_1709_05458_gb300 as P
+from paper_1709_05458_gb300 import velocity_sets as PV
+from oracle import dugks_oracle as O
+from oracle import velocity_sets as OV
+import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+def specs():
+    """(nx, ny, velocity set, tau, dt, bc, storage) of uneven instances."""
+    d2 = PV.d2q9(1 / 3)
+    nc = PV.newton_cotes(16, 0.5)
+    per = [(P.PERIODIC, 0, 0)] * 4
+    cav = [(P.BOUNCEBACK, 0, 0)] * 3 + [(P.BOUNCEBACK, 0.05, 0)]
+    ds = [(P.DIFFUSE, 0, 0)] * 3 + [(P.DIFFUSE, 0.1, 0)]
+    return [
+        (32, 32, d2, 0.004, 0.01, per, P.FP64),
+        (70, 45, d2, 0.003, 0.006, cav, P.FP64),
+        (129, 64, d2, 0.002, 0.004, per, P.FP64),
+        (40, 33, d2, 0.005, 0.01, cav, P.G_FP32),
+        (20, 17, nc, 0.5, 0.002, ds, P.FP64),
+        (256, 7, d2, 0.01, 0.02, per, P.FP64),
+    ]
+
+
+def make(spec, stream):
+    nx, ny, (xi, W, RT), tau, dt, bc, st = spec
+    s = P.Solver(nx, ny, 1 / nx, 1 / ny, xi, W, RT, tau, dt, bc, stream=stream, storage=st)
+    f0 = WL.near_equilibrium_state(W, ny, nx, amp=0.1, seed=nx * 1000 + ny)
+    s.set_state(f0)
+    return s, f0
+
+
+def test_batch_equals_individual_runs(cuda):
+    torch = cuda
+    stream = torch.cuda.Stream()
+    sols, f0s = zip(*[make(sp, stream) for sp in specs()])
+    b = P.Batch(sols)
+    b.step(3)
+    b.step(3)            # graph for nsteps = 3 is replayed
+    b.step(2)
+    out = [s.state() for s in sols]
+    for sp, f0, fb in zip(specs(), f0s, out):
+        ref, _ = make(sp, stream)
+        ref.set_state(f0)
+        ref.step(8)
+        np.testing.assert_array_equal(fb, ref.state())
+    b.close()
+    # one batched instance against the oracle
+    nx, ny, _, tau, dt, bc, _ = specs()[1]
+    po = OV.d2q9(1 / 3)
+    o = O.Setup(nx, ny, 1 / nx, 1 / ny, po[0], po[1], po[2], tau, dt, bc)
+    fo = O.t3s3_run(f0s[1], o, 8)
+    assert np.abs(out[1] - fo).max() <= 1e-12 * np.abs(fo).max()
+
+
+def test_autotune_keeps_state_and_results(cuda):
+    torch = cuda
+    stream = torch.cuda.Stream()
+    sp = specs()[2]
+    a, f0 = make(sp, stream)
+    ty = P.dugks_autotune(a.ctx, trials=2)
+    assert 4 <= ty <= 16
+    np.testing.assert_array_equal(a.state(), f0)
+    a.step(4)
+    ref, _ = make(sp, stream)
+    ref.step(4)
+    np.testing.assert_array_equal(a.state(), ref.state())
+
+
+def test_batch_needs_a_stream(cuda):
+    xi, W, RT = PV.d2q9(1 / 3)
+    s = P.Solver(8, 8, 1 / 8, 1 / 8, xi, W, RT, 0.01, 0.01, [(P.PERIODIC, 0, 0)] * 4)
+    with pytest.raises(P.DugksError) as e:
+        P.Batch([s])
+    assert e.value.code == P.DUGKS_EINVAL

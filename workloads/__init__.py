@@ -128,4 +128,35 @@ def config(name: str) -> dict:
                     tau=tau, dt=dt, steps=5000, U=uw,
                     bc=[(DIFFUSE, 0, 0), (DIFFUSE, 0, 0),
                         (DIFFUSE, 0, 0), (DIFFUSE, uw, 0)])
+    if name == "batched64":
+        return dict(name=name, instances=batched_instances(64))
     raise KeyError(name)
+
+
+def batched_instances(n: int, seed: int = SEED):
+    """Seeded mix of uneven instances: kind TGV or cavity (p = 1/2), N in
+    {32, 64, ..., 512}; D2Q9 (p = 1/2) with Re log-uniform in [100, 1000] and
+    dt/tau = 4, else a Newton-Cotes grid n in {16, 22, 28, 32} with Kn
+    log-uniform in [0.1, 10] (CFL 0.25)."""
+    r = rng(seed)
+    out = []
+    for _ in range(n):
+        kind = "tgv" if r.uniform() < 0.5 else "cavity"
+        N = int(32 * r.integers(1, 17))
+        if r.uniform() < 0.5:
+            RT = 1.0 / 3.0
+            C = math.sqrt(3 * RT)
+            U = 0.05 * C
+            Re = float(np.exp(r.uniform(np.log(100.0), np.log(1000.0))))
+            nu = U / Re
+            tau = nu / RT
+            out.append(dict(kind=kind, N=N, vel="d2q9", RT=RT, U=U, tau=tau, dt=4 * tau))
+        else:
+            nv1 = int(r.choice([16, 22, 28, 32]))
+            RT = 0.5
+            Kn = float(np.exp(r.uniform(np.log(0.1), np.log(10.0))))
+            tau = Kn / math.sqrt(math.pi * RT / 2)
+            dt = 0.25 * (1.0 / N) / (4 * math.sqrt(RT))
+            out.append(dict(kind=kind, N=N, vel="nc", nv1=nv1, RT=RT, U=0.1 * math.sqrt(RT),
+                            tau=tau, dt=dt, Kn=Kn))
+    return out
