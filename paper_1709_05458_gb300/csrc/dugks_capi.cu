@@ -62,6 +62,8 @@ struct dugks_ctx {
   double* mom = nullptr;        // rho, ux, uy [3][N]
   double* vel = nullptr;        // xi_x, xi_y, w, feq_wall[4]  ([7][nv])
   int* opp = nullptr;           // [nv]
+  double* part = nullptr;       // partial face moments of the large-set face kernels
+  int nchx = 0, nchy = 0;       // velocity chunks of those kernels (0: not used)
   int* flag = nullptr;          // [1]
   // fused D2Q9 path: buffers fhat = f^, g = g1, ftp = g2, acc = X, mom[0..N) and
   // mom[N..2N) = rho of the two stage base states
@@ -177,7 +179,7 @@ int copy_out(dugks_ctx* c, double* dst, const double* src, size_t n, int on_devi
 }
 
 void free_all(dugks_ctx* c) {
-  double* bufs[] = {c->fhat, c->ftp, c->acc, c->g, c->fbx, c->fby, c->mom, c->vel,
+  double* bufs[] = {c->fhat, c->ftp, c->acc, c->g, c->fbx, c->fby, c->mom, c->vel, c->part,
                     c->a_g1, c->a_g2, c->a_ftp, c->a_acc, c->a_mom1, c->a_mom2, c->a_tbar,
                     c->a_gbar, c->a_lam, c->a_out, c->a_phix, c->a_phiy, c->a_rhob, c->a_grads};
   for (double* b : bufs)
@@ -296,19 +298,32 @@ int one_step_d2q9m(dugks_ctx* c) {
   return DUGKS_OK;
 }
 
+// faces of one direction and stage for the generic path: the large-set
+// kernels for interior faces plus the generic kernel for wall faces, or the
+// generic kernel for all faces
+cudaError_t faces(dugks_ctx* c, int dir, const StageCoef& sc, double* fb) {
+  const DevParams& p = c->p;
+  const int nch = dir == 0 ? c->nchx : c->nchy;
+  if (!nch) return launch_face(p, c->groups, dir, c->g, c->mom, fb, sc, c->stream);
+  cudaError_t e = launch_nc_faces(p, dir, c->g, fb, c->part, nch, sc, c->stream);
+  if (e == cudaSuccess && !(dir == 0 ? p.px : p.py))
+    e = launch_face(p, c->groups, dir, c->g, c->mom, fb, sc, c->stream, 1);
+  return e;
+}
+
 int one_step(dugks_ctx* c) {
   const DevParams& p = c->p;
   cudaStream_t s = c->stream;
   const int G = c->groups;
   // Step (1): moments of f^, g1 = f-bar^{+,dt/6}; faces at t*; L*; Step (2): f~(t')
   TRY(launch(c, K_CELL_STAGE1, [&] { return launch_cell(p, G, 1, c->fhat, c->g, c->mom, c->s1.a, c->s1.b, s); }));
-  TRY(launch(c, K_FACE_X_STAGE1, [&] { return launch_face(p, G, 0, c->g, c->mom, c->fbx, c->s1, s); }));
-  TRY(launch(c, K_FACE_Y_STAGE1, [&] { return launch_face(p, G, 1, c->g, c->mom, c->fby, c->s1, s); }));
+  TRY(launch(c, K_FACE_X_STAGE1, [&] { return faces(c, 0, c->s1, c->fbx); }));
+  TRY(launch(c, K_FACE_Y_STAGE1, [&] { return faces(c, 1, c->s1, c->fby); }));
   TRY(launch(c, K_UPDATE_STAGE1, [&] { return launch_update1(p, c->fhat, c->g, c->fbx, c->fby, c->ftp, c->acc, s); }));
   // Step (2) collision at t' and Step (3): g2 = f-bar^{+,5dt/12}(t'); faces at t**; Step (4)
   TRY(launch(c, K_CELL_STAGE2, [&] { return launch_cell(p, G, 2, c->ftp, c->g, c->mom, c->s2.a, c->s2.b, s); }));
-  TRY(launch(c, K_FACE_X_STAGE2, [&] { return launch_face(p, G, 0, c->g, c->mom, c->fbx, c->s2, s); }));
-  TRY(launch(c, K_FACE_Y_STAGE2, [&] { return launch_face(p, G, 1, c->g, c->mom, c->fby, c->s2, s); }));
+  TRY(launch(c, K_FACE_X_STAGE2, [&] { return faces(c, 0, c->s2, c->fbx); }));
+  TRY(launch(c, K_FACE_Y_STAGE2, [&] { return faces(c, 1, c->s2, c->fby); }));
   TRY(launch(c, K_UPDATE_STAGE2, [&] { return launch_update2(p, c->ftp, c->acc, c->mom, c->fbx, c->fby, c->fhat, c->c_om, s); }));
   return DUGKS_OK;
 }
@@ -543,6 +558,15 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
   alloc(&c->fbx, nfx);
   alloc(&c->fby, nfy);
   alloc(&c->mom, 3 * (size_t)p.N);
+  if (c->groups > 1) {          // large velocity sets: interior-face kernels of dugks_nc.cu
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->nchx = nc_chunks(p, 0, sms);
+    c->nchy = nc_chunks(p, 1, sms);
+    const size_t nfmax = std::max((size_t)p.ny * (p.nx + 1), (size_t)(p.ny + 1) * p.nx);
+    alloc(&c->part, (size_t)std::max(c->nchx, c->nchy) * 3 * nfmax);
+  }
   alloc(&c->vel, host.size());
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->opp, nv * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->flag, sizeof(int));

@@ -160,8 +160,16 @@ void set_last_error(const std::string& msg);
 // Launchers (dugks_kernels.cu).  All asynchronous on `s`.
 cudaError_t launch_cell(const DevParams& p, int groups, int stage, const double* src,
                         double* g, double* mom, double a, double b, cudaStream_t s);
+// walls_only = 1: only the wall faces of direction dir (non-periodic sides)
 cudaError_t launch_face(const DevParams& p, int groups, int dir, const double* g,
-                        const double* mom, double* fb, const StageCoef& c, cudaStream_t s);
+                        const double* mom, double* fb, const StageCoef& c, cudaStream_t s,
+                        int walls_only = 0);
+// Interior faces of large velocity sets (dugks_nc.cu): pass 1 (stencils,
+// partial face moments per velocity chunk into part[nchunk][3][nf]) and
+// pass 2 (f = alpha f-bar + beta feq).  Wall faces: launch_face(walls_only).
+int nc_chunks(const DevParams& p, int dir, int sms);
+cudaError_t launch_nc_faces(const DevParams& p, int dir, const double* g, double* fb,
+                            double* part, int nchunk, const StageCoef& c, cudaStream_t s);
 cudaError_t launch_update1(const DevParams& p, const double* fhat, const double* g1,
                            const double* fbx, const double* fby, double* ftp, double* acc,
                            cudaStream_t s);

@@ -145,11 +145,15 @@ k_cell(DevParams p, const double* __restrict__ src, double* __restrict__ g,
     mom[2 * p.N + cell] = uy;
   }
   if constexpr (STAGE > 0) {
+    // feq_k = W_k rho (base + e (1 + e/2)), e = xi_k.u/RT, base = 1 - |u|^2/(2RT)
+    const double vx = ux * p.inv_RT, vy = uy * p.inv_RT;
+    const double base = 1.0 - 0.5 * fma(ux, vx, uy * vy);
+    const double br = b * rho;
     for (int k = ty; k < p.nv; k += G) {
       const size_t idx = (size_t)k * p.N + cell;
-      const double feq = __ldg(p.w + k) * rho *
-                         feq_poly(__ldg(p.xi_x + k), __ldg(p.xi_y + k), ux, uy, p.inv_RT);
-      g[idx] = a * src[idx] + b * feq;
+      const double e = fma(__ldg(p.xi_x + k), vx, __ldg(p.xi_y + k) * vy);
+      const double P = fma(e, fma(0.5, e, 1.0), base);
+      g[idx] = fma(br * __ldg(p.w + k), P, a * src[idx]);
     }
   }
 }
@@ -157,17 +161,25 @@ k_cell(DevParams p, const double* __restrict__ src, double* __restrict__ g,
 // ---------------------------------------------------------------- faces
 // DIR 0: x-faces, DIR 1: y-faces.  "lower" cell = the one with the smaller
 // index along the face normal (left / below), "upper" = right / above.
+// walls_only: the launch covers only the wall faces (2 per row or column),
+// indexed compactly: DIR 0 id -> row id/2, face 0 or nx; DIR 1 likewise.
 template <int G, int DIR>
 __global__ void __launch_bounds__(kThreads)
 k_face(DevParams p, const double* __restrict__ g, const double* __restrict__ mom,
-       double* __restrict__ fb, StageCoef c) {
+       double* __restrict__ fb, StageCoef c, int walls_only) {
   constexpr int TX = kThreads / G;
   __shared__ double red[4 * G * TX];
   const int nx = p.nx, ny = p.ny, N = p.N;
   const int nf = (DIR == 0) ? ny * (nx + 1) : (ny + 1) * nx;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int face = blockIdx.x * TX + tx;
-  const bool valid = face < nf;
+  int face = blockIdx.x * TX + tx;
+  bool valid = face < nf;
+  if (walls_only) {
+    const int id = face;
+    valid = id < 2 * (DIR == 0 ? ny : nx);
+    face = (DIR == 0) ? (id >> 1) * (nx + 1) + ((id & 1) ? nx : 0)
+                      : ((id & 1) ? ny : 0) * nx + (id >> 1);
+  }
 
   int li = 0, lj = 0, ui = 0, uj = 0, side = -1;
   if (valid) {
@@ -332,9 +344,11 @@ k_update2(DevParams p, const double* __restrict__ ftp, const double* __restrict_
   const int j = cell / p.nx, i = cell - j * p.nx;
   const double L = microflux(p, fbx, fby, k, i, j);
   const double rho = mom[cell], ux = mom[p.N + cell], uy = mom[2 * p.N + cell];
-  const double feq = __ldg(p.w + k) * rho *
-                     feq_poly(__ldg(p.xi_x + k), __ldg(p.xi_y + k), ux, uy, p.inv_RT);
-  fhat[t] = acc[t] + c_om34 * (ftp[t] - feq) + dt47 * L;
+  const double vx = ux * p.inv_RT, vy = uy * p.inv_RT;
+  const double e = fma(__ldg(p.xi_x + k), vx, __ldg(p.xi_y + k) * vy);
+  const double P = fma(e, fma(0.5, e, 1.0), 1.0 - 0.5 * fma(ux, vx, uy * vy));
+  const double feq = __ldg(p.w + k) * rho * P;
+  fhat[t] = fma(dt47, L, fma(c_om34, ftp[t] - feq, acc[t]));
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -370,12 +384,13 @@ cudaError_t cell_launch_g(const DevParams& p, int stage, const double* src, doub
 
 template <int G>
 cudaError_t face_launch_g(const DevParams& p, int dir, const double* g, const double* mom,
-                          double* fb, const StageCoef& c, cudaStream_t s) {
+                          double* fb, const StageCoef& c, int walls_only, cudaStream_t s) {
   constexpr int TX = kThreads / G;
-  const int nf = dir == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
+  const int nf = walls_only ? 2 * (dir == 0 ? p.ny : p.nx)
+                            : (dir == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx);
   dim3 block(TX, G), grid((nf + TX - 1) / TX);
-  if (dir == 0) k_face<G, 0><<<grid, block, 0, s>>>(p, g, mom, fb, c);
-  else k_face<G, 1><<<grid, block, 0, s>>>(p, g, mom, fb, c);
+  if (dir == 0) k_face<G, 0><<<grid, block, 0, s>>>(p, g, mom, fb, c, walls_only);
+  else k_face<G, 1><<<grid, block, 0, s>>>(p, g, mom, fb, c, walls_only);
   return cudaGetLastError();
 }
 
@@ -390,9 +405,12 @@ cudaError_t launch_cell(const DevParams& p, int groups, int stage, const double*
 }
 
 cudaError_t launch_face(const DevParams& p, int groups, int dir, const double* g,
-                        const double* mom, double* fb, const StageCoef& c, cudaStream_t s) {
-  return groups == 1 ? face_launch_g<1>(p, dir, g, mom, fb, c, s)
-                     : face_launch_g<8>(p, dir, g, mom, fb, c, s);
+                        const double* mom, double* fb, const StageCoef& c, cudaStream_t s,
+                        int walls_only) {
+  if (groups == 1) return face_launch_g<1>(p, dir, g, mom, fb, c, walls_only, s);
+  // the few wall faces of a large velocity set: 32 velocity groups per face
+  if (walls_only && p.nv > 256) return face_launch_g<32>(p, dir, g, mom, fb, c, walls_only, s);
+  return face_launch_g<8>(p, dir, g, mom, fb, c, walls_only, s);
 }
 
 cudaError_t launch_update1(const DevParams& p, const double* fhat, const double* g1,
