@@ -48,6 +48,19 @@ FLOPS_PER_UNIT = {
     "d2q9_stage1": 72.3, "d2q9_stage2": 60.2,
     # deviation forms: the same arithmetic, mostly in FP32; counted the same way
     "d2q9m_stage1": 72.3, "d2q9m_stage2": 60.2,
+    # deviation forms on the generic kernels: the FP64 part is the moment
+    # sums (one add and two FMAs = 5 flops per cell- or face-velocity); at
+    # the FP64 peak it takes longer than the kernels' algorithmic bytes at
+    # the HBM peak, so it is their bound
+    "gdev_cell": 5, "gdev_face_x": 5, "gdev_face_y": 5,
+}
+# Kernels bound by HBM instead: algorithmic bytes per cell-velocity by
+# storage form (FP32 / BF16 per-cell arrays; face values are FP32 in both).
+HBM_BYTES_PER_UNIT = {
+    # read f^, g1, x and y faces; write f~', acc
+    "gdev_update_stage1": {"fp32": 24, "bf16": 16},
+    # read f~', acc, x and y faces; write f^
+    "gdev_update_stage2": {"fp32": 20, "bf16": 14},
 }
 # Algorithmic DRAM bytes per unit (FP64 values each kernel must read/write once).
 BYTES_PER_UNIT = {
@@ -393,16 +406,27 @@ def run_ours(args):
 
     # roofline of the dominant kernel (largest share of device time)
     name, (nl, kms) = max(((k, v) for k, v in prof.items()
-                           if k in FLOPS_PER_UNIT and v[0] > 0 and v[1] > 0),
-                          key=lambda kv: kv[1][1], default=("d2q9_stage1", (1, 0.0)))
+                           if (k in FLOPS_PER_UNIT or k in HBM_BYTES_PER_UNIT)
+                           and v[0] > 0 and v[1] > 0),
+                          key=lambda kv: kv[1][1])
     nx, ny = c["nx"], c["ny"]
+    face = name.replace("gdev_", "")[:6]
     per_launch_units = {
         "face_x": nv * ny * (nx + 1), "face_y": nv * (ny + 1) * nx,
-    }.get(name[:6], nv * nx * ny)
-    flops = FLOPS_PER_UNIT[name] * per_launch_units
+    }.get(face, nv * nx * ny)
+    # gdev face and cell entries cover both stages: two launches per step
     avg_s = kms * 1e-3 / max(nl, 1)
-    achieved = flops / avg_s / 1e12
-    peak = fp64_peak_tflops()
+    if name in HBM_BYTES_PER_UNIT:
+        bound, unit = "hbm", "GB/s"
+        achieved = HBM_BYTES_PER_UNIT[name][args.storage] * per_launch_units / avg_s / 1e9
+        peak = measured_peaks().get("hbm_gbs", 6800.0)
+        peak_source = ("measured copy bandwidth" if "hbm_gbs" in measured_peaks()
+                       else "fallback 6.8 TB/s")
+    else:
+        bound, unit = "alu", "TFLOP/s"
+        achieved = FLOPS_PER_UNIT[name] * per_launch_units / avg_s / 1e12
+        peak = fp64_peak_tflops()
+        peak_source = "nominal FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"
     launches = sum(v[0] for k, v in prof.items())
     line = {
         "metric": "G cell-velocity updates/s (T3S3 step)", "value": value,
@@ -420,11 +444,11 @@ def run_ours(args):
                    **({"Re": 1000, "Ma": 0.1} if c.get("vel") != "nc" else {"Kn": c.get("Kn")}),
                    "units_per_step": units, "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas{world}" if world > 1 else "single"},
-        "roofline": {"bound": "alu", "kernel": name, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak,
+        "roofline": {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
+                     "unit": unit, "frac": achieved / peak,
                      "traffic": (TRAFFIC_BYTES_PER_UNIT[name] * per_launch_units
                                  if name in TRAFFIC_BYTES_PER_UNIT else None),
-                     "peak_source": "nominal FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz",
+                     "peak_source": peak_source,
                      "kernel_ms_per_launch": avg_s * 1e3,
                      "kernel_share": kms / sum(v[1] for v in prof.values())},
         "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items() if v[0]},

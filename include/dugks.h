@@ -59,9 +59,14 @@ enum { DUGKS_WEST = 0, DUGKS_EAST = 1, DUGKS_SOUTH = 2, DUGKS_NORTH = 3 };
  *                  magnitude (rho below ~18); larger ones turn the moment
  *                  into NaN, which dugks_check reports as DUGKS_EUNSTABLE.
  *   DUGKS_G_BF16 : as DUGKS_G_FP32 with the deviations stored in BF16.
- * The deviation forms need the D2Q9 listing order of Sec. 2.2 (xi_k =
- * c (k/3 - 1, k%3 - 1)); other sets return DUGKS_ENOTIMPL.  States cross the
- * ABI in FP64 for every form. */
+ * The description above is that of the fused D2Q9 kernels, taken when the
+ * set is in the D2Q9 listing order of Sec. 2.2 (xi_k = c (k/3 - 1, k%3 - 1)).
+ * Any other velocity set (Newton-Cotes grids) runs the deviation forms on
+ * the generic kernels: the same FP32/BF16 storage and FP32 stencils, FP32
+ * face values, moment sums of every cell and face accumulated in FP64 from
+ * the exactly converted FP32 terms (no magnitude limit; a non-finite
+ * deviation gives a non-finite moment).  States cross the ABI in FP64 for
+ * every form. */
 enum { DUGKS_FP64 = 0, DUGKS_G_FP32 = 1, DUGKS_G_BF16 = 2 };
 
 typedef struct dugks_ctx dugks_ctx;   /* opaque, owned by the library */

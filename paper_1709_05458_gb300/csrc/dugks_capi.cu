@@ -35,7 +35,8 @@ const char* kNames[K_NUM] = {
     "cell_stage2", "face_x_stage2", "face_y_stage2", "update_stage2",
     "moments",     "set_equilibrium", "check",
     "d2q9_prologue", "d2q9_stage1", "d2q9_stage2",
-    "d2q9m_stage1", "d2q9m_stage2", "convert"};
+    "d2q9m_stage1", "d2q9m_stage2", "convert",
+    "gdev_cell", "gdev_face_x", "gdev_face_y", "gdev_update_stage1", "gdev_update_stage2"};
 
 struct Pending {
   int id;
@@ -76,6 +77,12 @@ struct dugks_ctx {
   int store = 0;
   double rho0 = 1.0;
   D2Q9StageF df1{}, df2{};
+  // deviation storage on the generic path (any velocity set): launch set-up
+  // and the FP32 equilibrium parameters of the last cell pass ([5][N])
+  bool gdev = false;
+  GDevStep gs{};
+  float* eqp = nullptr;
+  float* vf = nullptr;          // FP32 velocity tables [GV_N][nv]
   // adjoint (allocated on first use): forward intermediates and adjoint fields
   double *a_g1 = nullptr, *a_g2 = nullptr, *a_ftp = nullptr, *a_acc = nullptr;
   double *a_mom1 = nullptr, *a_mom2 = nullptr, *a_tbar = nullptr, *a_gbar = nullptr;
@@ -188,6 +195,8 @@ void free_all(dugks_ctx* c) {
     if (b) cudaFree(b);
   if (c->opp) cudaFree(c->opp);
   if (c->flag) cudaFree(c->flag);
+  if (c->eqp) cudaFree(c->eqp);
+  if (c->vf) cudaFree(c->vf);
   for (auto& q : c->pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -328,10 +337,26 @@ int one_step(dugks_ctx* c) {
   return DUGKS_OK;
 }
 
+// Deviation storage on the generic path: the same eight launch groups as
+// one_step, FP32/BF16 arrays, FP64 moment sums.
+int one_step_gdev(dugks_ctx* c) {
+  const GDevStep& g = c->gs;
+  cudaStream_t s = c->stream;
+  for (int stage = 1; stage <= 2; ++stage) {
+    TRY(launch(c, K_GDEV_CELL, [&] { return launch_gdev_cell(g, stage, s); }));
+    TRY(launch(c, K_GDEV_FACE_X, [&] { return launch_gdev_faces(g, stage, 0, s); }));
+    TRY(launch(c, K_GDEV_FACE_Y, [&] { return launch_gdev_faces(g, stage, 1, s); }));
+    TRY(launch(c, stage == 1 ? K_GDEV_UPDATE1 : K_GDEV_UPDATE2,
+               [&] { return launch_gdev_update(g, stage, s); }));
+  }
+  return DUGKS_OK;
+}
+
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 int advance(dugks_ctx* c) {
-  return c->store ? one_step_d2q9m(c) : c->d2q9 ? one_step_d2q9(c) : one_step(c);
+  if (c->store) return c->gdev ? one_step_gdev(c) : one_step_d2q9m(c);
+  return c->d2q9 ? one_step_d2q9(c) : one_step(c);
 }
 
 // g1 of the current state for the fused paths (run eagerly before capture)
@@ -475,8 +500,6 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     return fail(DUGKS_EINVAL, "west and east must both be periodic or both walls");
   if (py != (bc[DUGKS_NORTH].kind == DUGKS_BC_PERIODIC))
     return fail(DUGKS_EINVAL, "south and north must both be periodic or both walls");
-  if (storage != DUGKS_FP64 && !(d2q9_speed(vel) > 0.0))
-    return fail(DUGKS_ENOTIMPL, "deviation storage needs the D2Q9 velocity set");
   if (!px && mesh->nx < 3) return fail(DUGKS_EINVAL, "walls in x need nx >= 3");
   if (!py && mesh->ny < 3) return fail(DUGKS_EINVAL, "walls in y need ny >= 3");
 
@@ -614,12 +637,71 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
   // fused D2Q9 path
   const double cd = d2q9_speed(vel);
   const char* force = std::getenv("DUGKS_FORCE_GENERIC");
-  if (storage != DUGKS_FP64 && !(cd > 0.0)) {
-    free_all(c);
-    delete c;
-    return fail(DUGKS_ENOTIMPL, "deviation storage needs the D2Q9 velocity set");
+  const bool forced = force && force[0] == '1';
+  if (storage != DUGKS_FP64 && !(cd > 0.0 && !forced)) {
+    // deviation storage on the generic kernels (any velocity set)
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    GDevStep& g = c->gs;
+    g.p = c->p;
+    g.store = storage;
+    g.ref.rho0 = c->rho0;
+    for (int k = 0; k < nv; ++k) {
+      g.ref.W += c->rho0 * vel->w[k];
+      g.ref.Wx += c->rho0 * vel->w[k] * vel->xi_x[k];
+      g.ref.Wy += c->rho0 * vel->w[k] * vel->xi_y[k];
+    }
+    g.s1 = c->s1;
+    g.s2 = c->s2;
+    g.c_om = c->c_om;
+    g.nchx = gdev_chunks(p, 0, sms);
+    g.nchy = gdev_chunks(p, 1, sms);
+    if (c->part && (c->nchx < g.nchx || c->nchy < g.nchy)) {
+      cudaFree(c->part);
+      c->part = nullptr;
+    }
+    const size_t nfmax = std::max((size_t)p.ny * (p.nx + 1), (size_t)(p.ny + 1) * p.nx);
+    if (!c->part)
+      e = cudaMalloc((void**)&c->part, (size_t)std::max(g.nchx, g.nchy) * 3 * nfmax * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->eqp, 5 * (size_t)p.N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->vf, (size_t)GV_N * nv * sizeof(float));
+    if (e == cudaSuccess) {
+      std::vector<float> t((size_t)GV_N * nv);
+      for (int k = 0; k < nv; ++k) {
+        const double x = vel->xi_x[k], y = vel->xi_y[k];
+        const float xh = (float)x, yh = (float)y;
+        t[GV_XH * nv + k] = xh;
+        t[GV_YH * nv + k] = yh;
+        t[GV_XL * nv + k] = (float)(x - (double)xh);
+        t[GV_YL * nv + k] = (float)(y - (double)yh);
+        t[GV_W * nv + k] = (float)vel->w[k];
+        t[GV_KX * nv + k] = (float)(x / mesh->dx);
+        t[GV_KY * nv + k] = (float)(y / mesh->dy);
+      }
+      e = cudaMemcpy(c->vf, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+      free_all(c);
+      delete c;
+      cudaGetLastError();
+      return fail(e == cudaErrorMemoryAllocation ? DUGKS_ENOMEM : DUGKS_ECUDA,
+                  std::string("device allocation: ") + cudaGetErrorString(e));
+    }
+    g.fhat = c->fhat;
+    g.g = c->g;
+    g.ftp = c->ftp;
+    g.acc = c->acc;
+    g.fbx = (float*)c->fbx;
+    g.fby = (float*)c->fby;
+    g.eqp = c->eqp;
+    g.vf = c->vf;
+    g.mom = c->mom;
+    g.part = c->part;
+    c->store = storage;
+    c->gdev = true;
   }
-  if (cd > 0.0 && (storage != DUGKS_FP64 || !(force && force[0] == '1'))) {
+  if (cd > 0.0 && !forced) {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -722,8 +804,7 @@ int dugks_get_state(dugks_ctx* c, double* fhat, int on_device) {
 int dugks_step(dugks_ctx* c, int n) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
   if (n < 0) return fail(DUGKS_EINVAL, "n must be >= 0");
-  for (int i = 0; i < n; ++i)
-    TRY(c->store ? one_step_d2q9m(c) : c->d2q9 ? one_step_d2q9(c) : one_step(c));
+  for (int i = 0; i < n; ++i) TRY(advance(c));
   return DUGKS_OK;
 }
 

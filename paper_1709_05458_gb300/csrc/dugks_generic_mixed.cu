@@ -1,0 +1,697 @@
+// Deviation-storage (FP32 / BF16) form of the generic path: any velocity
+// set (Newton-Cotes grids in particular), periodic / bounce-back / diffuse
+// walls.  Same step structure as the FP64 generic path:
+//   cell(stage) -> faces x, y (interior slab kernels + wall faces) -> update.
+// Every per-(cell, velocity) array holds d = f - W_k rho0; face values are
+// FP32 deviations.  Stencils, fluxes, the stage transforms and the
+// per-velocity equilibrium assembly W_k((rho - rho0) + rho (P_k - 1)) run in
+// FP32.  The moment sums of every cell and face (Sec. 2.2) are carried per
+// thread as unevaluated FP32 pairs (hi + lo) updated by error-free
+// transformations -- TwoSum for each term, and the exact FMA residual of
+// xi_hi d plus xi_lo d for the momentum, xi = xi_hi + xi_lo -- so a partial
+// sum keeps ~48 significant bits; the partials are combined across threads,
+// warps and velocity chunks in FP64, and rho, u/RT and |u|^2/(2RT) are FP64
+// before they are rounded for the assembly (Sec. 2.1.1 equilibrium).  No
+// FP64 arithmetic or FP64<->FP32 conversion sits in an inner loop: GB300 runs
+// both on its 2-lane-per-clock FP64 pipe.  The maps of the step (eqs.
+// f_bar_1_6, fbp_5_12, recover2f, f_tilde_1_3, fhp, feqIntD3rdHat2_DS) are
+// affine with coefficients summing to one and the flux divergence of a
+// uniform field vanishes, so they act on deviations unchanged.
+#include <cuda_bf16.h>
+
+#include "dugks_internal.cuh"
+
+namespace dugks {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int NW = 8, R = 8, LANES = 32;
+
+template <typename T> __device__ __forceinline__ float ldv(const T* p);
+template <> __device__ __forceinline__ float ldv<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+template <typename T> __device__ __forceinline__ void stv(T* p, float v);
+template <> __device__ __forceinline__ void stv<float>(float* p, float v) { *p = v; }
+template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16* p, float v) {
+  *p = __float2bfloat16_rn(v);
+}
+
+// exact FP32 -> FP64 on the integer pipe; zero and denormals -> 0, inf and
+// NaN kept
+__device__ __forceinline__ double f2d(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned em = b & 0x7fffffffu;
+  unsigned hi = (em >> 3) + 0x38000000u;
+  unsigned lo = em << 29;
+  hi = (em >= 0x7f800000u) ? (0x7ff00000u | ((em & 0x7fffffu) >> 3)) : hi;
+  const bool tiny = em < 0x00800000u;
+  hi = tiny ? 0u : hi;
+  lo = tiny ? 0u : lo;
+  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
+}
+
+// FP64 -> FP32, round half up on the magnitude, on the integer pipe; values
+// below the FP32 normal range -> 0; NaN, inf and overflow -> NaN
+__device__ __forceinline__ float d2f(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int E = (int)((hi >> 20) & 0x7ffu) - 896;
+  unsigned mag = ((unsigned)E << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+  mag += (lo >> 28) & 1u;
+  mag = (E <= 0) ? 0u : mag;
+  mag = (E >= 255) ? 0x7fc00000u : mag;
+  return __uint_as_float(mag | (hi & 0x80000000u));
+}
+
+// ---- compensated FP32-pair accumulation (error-free transformations) ----
+// s = hi + lo.  add: TwoSum(hi, x), the rounding error goes to lo.
+// addprod: x (ah + al) with ah x split exactly into p + pe by an FMA.  The
+// _rn intrinsics keep the compiler from contracting or reassociating.
+struct Acc {
+  float hi, lo;
+};
+__device__ __forceinline__ void acc_add(Acc& a, float x) {
+  const float s = __fadd_rn(a.hi, x);
+  const float bp = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, e);
+}
+__device__ __forceinline__ void acc_addprod(Acc& a, float ah, float al, float x) {
+  const float p = __fmul_rn(ah, x);
+  const float pe = __fmaf_rn(ah, x, -p);
+  const float s = __fadd_rn(a.hi, p);
+  const float bp = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(e, __fmaf_rn(al, x, pe)));
+}
+__device__ __forceinline__ double acc_value(const Acc& a) { return f2d(a.hi) + f2d(a.lo); }
+
+// per-velocity FP32 tables, [GV_N][nv]
+__device__ __forceinline__ float vt(const float* vf, int nv, int row, int k) {
+  return __ldg(vf + row * nv + k);
+}
+
+// FP32 equilibrium-assembly parameters of one cell or face
+struct EqF {
+  float vx, vy, bm1, r, dr;   // u/RT, -|u|^2/(2RT), rho, rho - rho0
+};
+__device__ __forceinline__ EqF eq_params_u(double rho, double ux, double uy, double inv_RT,
+                                           double rho0) {
+  const double vx = ux * inv_RT, vy = uy * inv_RT;
+  EqF q;
+  q.vx = d2f(vx);
+  q.vy = d2f(vy);
+  q.bm1 = d2f(-0.5 * fma(ux, vx, uy * vy));
+  q.r = d2f(rho);
+  q.dr = d2f(rho - rho0);
+  return q;
+}
+// from the sums (rho, jx, jy): one FP64 reciprocal
+__device__ __forceinline__ EqF eq_params_j(double rho, double jx, double jy, double inv_RT,
+                                           double rho0) {
+  const double rinv = 1.0 / rho;
+  return eq_params_u(rho, jx * rinv, jy * rinv, inv_RT, rho0);
+}
+// W_k (rho P_k - rho0) = W_k ((rho - rho0) + rho (P_k - 1)),
+// P_k - 1 = e (1 + e/2) - |u|^2/(2RT), e = xi_k.u/RT
+__device__ __forceinline__ float feq_dev(const EqF& q, float cx, float cy, float w) {
+  const float e = fmaf(cx, q.vx, cy * q.vy);
+  const float p1 = fmaf(e, fmaf(0.5f, e, 1.0f), q.bm1);
+  return w * fmaf(q.r, p1, q.dr);
+}
+
+// Sum M values over the threads of a block (warp shuffles, then the warps'
+// totals in a fixed order); every thread gets the totals.  sm: [32][M].
+template <int M>
+__device__ __forceinline__ void block_sum(double (&v)[M], double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+  if (lane == 0)
+#pragma unroll
+    for (int m = 0; m < M; ++m) sm[warp * M + m] = v[m];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sm[w * M + m];
+    v[m] = s;
+  }
+  __syncthreads();
+}
+
+// Sum over the G velocity groups (threadIdx.y) of a block column.
+template <int G, int TX, int M>
+__device__ __forceinline__ void group_sum(double (&v)[M], double* red) {
+  if constexpr (G > 1) {
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int m = 0; m < M; ++m) red[(m * G + ty) * TX + tx] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < G; ++q) s += red[(m * G + q) * TX + tx];
+      v[m] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- cell
+// Moments of src -> mom (rho, ux, uy, FP64) and the FP32 assembly
+// parameters eqp[5][N]; g = a src + b feq as a deviation.
+template <typename T, int G>
+__global__ void __launch_bounds__(kThreads)
+k_gcell(DevParams p, GDevRef ref, const float* __restrict__ vf, const T* __restrict__ src,
+        T* __restrict__ g, double* __restrict__ mom, float* __restrict__ eqp, float a, float b) {
+  constexpr int TX = kThreads / G;
+  __shared__ double red[G > 1 ? 3 * G * TX : 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int cell = blockIdx.x * TX + tx;
+  const bool valid = cell < p.N;
+  const int nv = p.nv;
+  Acc s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
+  if (valid)
+    for (int k = ty; k < nv; k += G) {
+      const float d = ldv(src + (size_t)k * p.N + cell);
+      acc_add(s0, d);
+      acc_addprod(s1, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_XL, k), d);
+      acc_addprod(s2, vt(vf, nv, GV_YH, k), vt(vf, nv, GV_YL, k), d);
+    }
+  double v[3] = {acc_value(s0), acc_value(s1), acc_value(s2)};
+  group_sum<G, TX, 3>(v, red);
+  if (!valid) return;
+  const double rho = ref.W + v[0];
+  const double rinv = 1.0 / rho;
+  const double ux = (ref.Wx + v[1]) * rinv, uy = (ref.Wy + v[2]) * rinv;
+  const EqF q = eq_params_u(rho, ux, uy, p.inv_RT, ref.rho0);
+  if (ty == 0) {
+    mom[cell] = rho;
+    mom[p.N + cell] = ux;
+    mom[2 * p.N + cell] = uy;
+    eqp[cell] = q.vx;
+    eqp[p.N + cell] = q.vy;
+    eqp[2 * p.N + cell] = q.bm1;
+    eqp[3 * p.N + cell] = q.r;
+    eqp[4 * p.N + cell] = q.dr;
+  }
+  for (int k = ty; k < nv; k += G) {
+    const size_t idx = (size_t)k * p.N + cell;
+    const float fe = feq_dev(q, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_YH, k), vt(vf, nv, GV_W, k));
+    stv(g + idx, fmaf(b, fe, a * ldv(src + idx)));
+  }
+}
+
+// ---------------------------------------------------------- interior faces
+// g at (gx, gy): interior, periodic wrap, one ghost layer of quadratic
+// extrapolation (g_-1 = 3 g_0 - 3 g_1 + g_2); positions further out are
+// clamped (their values feed no face).
+template <typename T>
+__device__ __forceinline__ float gfetch(const T* __restrict__ gk, const DevParams& p, int gx,
+                                        int gy) {
+  if (gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny) return ldv(gk + gy * p.nx + gx);
+  if (p.px) gx = ((gx % p.nx) + p.nx) % p.nx;
+  else gx = gx < -1 ? -1 : (gx > p.nx ? p.nx : gx);
+  if (p.py) gy = ((gy % p.ny) + p.ny) % p.ny;
+  else gy = gy < -1 ? -1 : (gy > p.ny ? p.ny : gy);
+  auto col = [&](int x, int y) {
+    if (y < 0 || y >= p.ny) {
+      const int b = y < 0 ? 0 : p.ny - 1, s = y < 0 ? 1 : -1;
+      return 3.f * ldv(gk + b * p.nx + x) - 3.f * ldv(gk + (b + s) * p.nx + x) +
+             ldv(gk + (b + 2 * s) * p.nx + x);
+    }
+    return ldv(gk + y * p.nx + x);
+  };
+  if (gx < 0 || gx >= p.nx) {
+    const int b = gx < 0 ? 0 : p.nx - 1, s = gx < 0 ? 1 : -1;
+    return 3.f * col(b, gy) - 3.f * col(b + s, gy) + col(b + 2 * s, gy);
+  }
+  return col(gx, gy);
+}
+
+// quadratic Taylor weights about a cell for the foot offset (a dx, b dy),
+// central differences on the 3x3 neighbourhood: T[(dy+1)*3 + dx+1]
+__device__ __forceinline__ void taylor9f(float a, float b, float (&T)[9]) {
+  const float ab = 0.25f * a * b;
+  T[0] = ab;                   T[1] = 0.5f * (b * b - b);  T[2] = -ab;
+  T[3] = 0.5f * (a * a - a);   T[4] = 1.f - a * a - b * b; T[5] = 0.5f * (a * a + a);
+  T[6] = -ab;                  T[7] = 0.5f * (b * b + b);  T[8] = ab;
+}
+
+// Pass 1: lanes over 32 faces, warps over velocities, R face rows per block;
+// FP32 stencils from a per-warp slab of g in shared memory, compensated
+// partial face moments, combined in FP64 per velocity chunk into
+// part[chunk][3][nf].
+template <typename T, int DIR>
+__global__ void __launch_bounds__(LANES * NW)
+k_gfaces1(DevParams p, const float* __restrict__ vf, const T* __restrict__ g,
+          float* __restrict__ fb, double* __restrict__ part, float h, int kchunk) {
+  constexpr int SR = DIR == 0 ? R + 2 : R + 3;
+  constexpr int SC = DIR == 0 ? 36 : 34;
+  // the warps' slabs, later reused for the reduction
+  __shared__ double smem[NW * R * LANES * 3];
+  static_assert(NW * SR * SC * sizeof(float) <= sizeof(smem), "slab too large");
+  auto red = [&](int w, int r, int l, int m) -> double& {
+    return smem[((w * R + r) * LANES + l) * 3 + m];
+  };
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nx = p.nx, ny = p.ny, nv = p.nv;
+  const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
+  const int c0 = blockIdx.x * LANES, r0 = blockIdx.y * R;
+  const int k0 = blockIdx.z * kchunk, k1 = min(nv, k0 + kchunk);
+  const int ox = DIR == 0 ? c0 - 2 : c0 - 1;
+  const int oy = DIR == 0 ? r0 - 1 : r0 - 2;
+  const float dx = (float)p.dx, dy = (float)p.dy;
+  const float idx_ = (float)p.inv_dx, idy = (float)p.inv_dy;
+  Acc acc[R][3];
+  bool ok[R];
+  const int col = c0 + lane;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) acc[r][m] = Acc{0.f, 0.f};
+    if (DIR == 0) {
+      const int j = r0 + r;
+      ok[r] = j < ny && col <= nx && (p.px || (col >= 1 && col <= nx - 1));
+    } else {
+      const int fj = r0 + r;
+      ok[r] = col < nx && fj <= ny && (p.py || (fj >= 1 && fj <= ny - 1));
+    }
+  }
+  float* sl = reinterpret_cast<float*>(smem) + warp * SR * SC;
+  for (int k = k0 + warp; k < k1; k += NW) {
+    const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k);
+    const float cxl = vt(vf, nv, GV_XL, k), cyl = vt(vf, nv, GV_YL, k);
+    const float cn = DIR == 0 ? cx : cy;
+    float TL[9], TU[9];
+    const bool lo = cn >= 0.f, hi = cn <= 0.f;     // uniform across the warp
+    if (DIR == 0) {
+      const float bb = -cy * h * idy;
+      if (lo) taylor9f((0.5f * dx - cx * h) * idx_, bb, TL);
+      if (hi) taylor9f((-0.5f * dx - cx * h) * idx_, bb, TU);
+    } else {
+      const float aa = -cx * h * idx_;
+      if (lo) taylor9f(aa, (0.5f * dy - cy * h) * idy, TL);
+      if (hi) taylor9f(aa, (-0.5f * dy - cy * h) * idy, TU);
+    }
+    const T* gk = g + (size_t)k * p.N;
+    __syncwarp();
+    for (int e = lane; e < SR * SC; e += LANES) {
+      const int rr = e / SC, cc = e - rr * SC;
+      sl[e] = gfetch(gk, p, ox + cc, oy + rr);
+    }
+    __syncwarp();
+    float* fbk = fb + (size_t)k * nf;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!ok[r]) continue;
+      const float* s0 = sl + r * SC + lane;
+      float vl = 0.f, vu = 0.f;
+      if (lo) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) vl = fmaf(TL[a * 3 + q], s0[a * SC + q], vl);
+      }
+      if (hi) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int q = 0; q < 3; ++q)
+            vu = fmaf(TU[a * 3 + q], DIR == 0 ? s0[a * SC + q + 1] : s0[(a + 1) * SC + q], vu);
+      }
+      const float v = (lo && hi) ? 0.5f * (vl + vu) : (lo ? vl : vu);
+      const int face = DIR == 0 ? (r0 + r) * (nx + 1) + col : (r0 + r) * nx + col;
+      fbk[face] = v;
+      acc_add(acc[r][0], v);
+      acc_addprod(acc[r][1], cx, cxl, v);
+      acc_addprod(acc[r][2], cy, cyl, v);
+    }
+  }
+  __syncthreads();                                  // all slabs done: reuse the memory
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int m = 0; m < 3; ++m) red(warp, r, lane, m) = acc_value(acc[r][m]);
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * LANES; e += LANES * NW) {
+    const int r = e / LANES, l = e - r * LANES;
+    const int cc = c0 + l;
+    bool okf;
+    int face;
+    if (DIR == 0) {
+      okf = (r0 + r) < ny && cc <= nx && (p.px || (cc >= 1 && cc <= nx - 1));
+      face = (r0 + r) * (nx + 1) + cc;
+    } else {
+      okf = cc < nx && (r0 + r) <= ny && (p.py || ((r0 + r) >= 1 && (r0 + r) <= ny - 1));
+      face = (r0 + r) * nx + cc;
+    }
+    if (!okf) continue;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      s0 += red(w, r, l, 0);
+      s1 += red(w, r, l, 1);
+      s2 += red(w, r, l, 2);
+    }
+    double* pc = part + (size_t)blockIdx.z * 3 * nf;
+    pc[face] = s0;
+    pc[nf + face] = s1;
+    pc[2 * nf + face] = s2;
+  }
+}
+
+// Pass 2: face moments (FP64, chunks summed in order) -> face equilibrium
+// (eq. recover2f) -> f = alpha f-bar + beta feq.  Wall faces are skipped.
+// blockIdx.y strides the velocities; four are in flight per thread.
+template <int DIR>
+__global__ void __launch_bounds__(256)
+k_gfaces2(DevParams p, GDevRef ref, const float* __restrict__ vf, float* __restrict__ fb,
+          const double* __restrict__ part, int nchunk, float alpha, float beta) {
+  const int nx = p.nx, ny = p.ny, nv = p.nv;
+  const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
+  const int face = blockIdx.x * blockDim.x + threadIdx.x;
+  if (face >= nf) return;
+  if (DIR == 0) {
+    const int fi = face % (nx + 1);
+    if (!p.px && (fi == 0 || fi == nx)) return;
+  } else {
+    const int fj = face / nx;
+    if (!p.py && (fj == 0 || fj == ny)) return;
+  }
+  double r = ref.W, jx = ref.Wx, jy = ref.Wy;
+  for (int c = 0; c < nchunk; ++c) {
+    const double* pc = part + (size_t)c * 3 * nf;
+    r += pc[face];
+    jx += pc[nf + face];
+    jy += pc[2 * nf + face];
+  }
+  const EqF q = eq_params_j(r, jx, jy, p.inv_RT, ref.rho0);
+  const int ks = gridDim.y;
+  int k = blockIdx.y;
+  for (; k + 3 * ks < nv; k += 4 * ks) {
+    float f[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) f[u] = fb[(size_t)(k + u * ks) * nf + face];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = k + u * ks;
+      const float fe = feq_dev(q, vt(vf, nv, GV_XH, kk), vt(vf, nv, GV_YH, kk), vt(vf, nv, GV_W, kk));
+      fb[(size_t)kk * nf + face] = fmaf(alpha, f[u], beta * fe);
+    }
+  }
+  for (; k < nv; k += ks) {
+    const size_t idx = (size_t)k * nf + face;
+    const float fe = feq_dev(q, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_YH, k), vt(vf, nv, GV_W, k));
+    fb[idx] = fmaf(alpha, fb[idx], beta * fe);
+  }
+}
+
+// -------------------------------------------------------------- wall faces
+// One wall face per block, the threads over the velocity set: fluid-side
+// reconstruction (velocities leaving the fluid or along the wall), the wall
+// rule of Sec. 2.3 for velocities entering the fluid (bounce-back with the
+// moving-wall term, or diffuse scattering with the density that balances
+// the outgoing flux), face moments (FP64, few terms per thread), then
+// f = alpha f-bar + beta feq.  Faces: id = 2 line + (0: W/S wall, 1: E/N).
+template <typename T>
+__device__ __forceinline__ float taylor_at(const T* __restrict__ gk, const DevParams& p, int ci,
+                                           int cj, float X, float Y) {
+  float Tw[9];
+  taylor9f(X * (float)p.inv_dx, Y * (float)p.inv_dy, Tw);
+  float v = 0.f;
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx)
+      v = fmaf(Tw[(dy + 1) * 3 + dx + 1], gfetch(gk, p, ci + dx, cj + dy), v);
+  return v;
+}
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(kThreads)
+k_gwall(DevParams p, GDevRef ref, const float* __restrict__ vf, const T* __restrict__ g,
+        const double* __restrict__ mom, float* __restrict__ fb, float h, float alpha,
+        float beta) {
+  __shared__ double sm[32 * 4];
+  const int nx = p.nx, ny = p.ny, N = p.N, nv = p.nv;
+  const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
+  const int id = blockIdx.x;
+  const bool upper_wall = id & 1;                 // east / north
+  const int line = id >> 1;
+  const int face = DIR == 0 ? line * (nx + 1) + (upper_wall ? nx : 0)
+                            : (upper_wall ? ny : 0) * nx + line;
+  const int side = DIR == 0 ? (upper_wall ? SIDE_E : SIDE_W) : (upper_wall ? SIDE_N : SIDE_S);
+  // the fluid cell lies on the +normal side of W/S walls; xi.n with n the
+  // fluid's outward normal is -xi_n there and +xi_n at E/N walls
+  const bool fluid_hi = !upper_wall;
+  const float nsg = fluid_hi ? -1.f : 1.f;
+  const int ci = DIR == 0 ? (fluid_hi ? 0 : nx - 1) : line;
+  const int cj = DIR == 0 ? line : (fluid_hi ? 0 : ny - 1);
+  const int kind = p.bc_kind[side];
+  const float half = 0.5f * (float)(DIR == 0 ? p.dx : p.dy);
+  const float off = fluid_hi ? -half : half;      // face centre from the fluid cell centre
+  const float rho_w = (float)mom[cj * nx + ci];
+  const float uwx = (float)p.uw_x[side], uwy = (float)p.uw_y[side];
+  const float irt = (float)p.inv_RT;
+  auto recon = [&](int k) {
+    const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k);
+    const float X = DIR == 0 ? off - cx * h : -cx * h;
+    const float Y = DIR == 0 ? -cy * h : off - cy * h;
+    return taylor_at(g + (size_t)k * N, p, ci, cj, X, Y);
+  };
+  double v[4] = {0.0, 0.0, 0.0, 0.0};            // moments of f-bar, diffuse numerator
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k);
+    const float xn = nsg * (DIR == 0 ? cx : cy);
+    float fbar;
+    if (xn >= 0.f) {                               // hits the wall or runs along it
+      fbar = recon(k);
+      if (xn > 0.f) {
+        const double xnd = (double)nsg * (DIR == 0 ? __ldg(p.xi_x + k) : __ldg(p.xi_y + k));
+        v[3] = fma(xnd, f2d(fbar) + __ldg(p.w + k) * ref.rho0, v[3]);
+      }
+    } else if (kind == BC_BOUNCEBACK) {
+      const int kk = __ldg(p.opp + k);
+      const float wk = vt(vf, nv, GV_W, k);
+      const float bbk = 2.f * wk * fmaf(cx, uwx, cy * uwy) * irt;
+      const float shift = (vt(vf, nv, GV_W, kk) - wk) * (float)ref.rho0;
+      fbar = fmaf(rho_w, bbk, recon(kk) + shift);
+    } else {
+      continue;                                    // diffuse: after the reduction
+    }
+    fb[(size_t)k * nf + face] = fbar;
+    const double fd = f2d(fbar);
+    v[0] += fd;
+    v[1] = fma(__ldg(p.xi_x + k), fd, v[1]);
+    v[2] = fma(__ldg(p.xi_y + k), fd, v[2]);
+  }
+  block_sum<4>(v, sm);
+  if (kind == BC_DIFFUSE) {                        // uniform over the block
+    double w2[3] = {0.0, 0.0, 0.0};
+    const double rho_ds = v[3] / p.ds_den[side];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+      const float xn = nsg * (DIR == 0 ? vt(vf, nv, GV_XH, k) : vt(vf, nv, GV_YH, k));
+      if (xn < 0.f) {
+        const float fbar =
+            d2f(fma(rho_ds, __ldg(p.feq_wall + side * nv + k), -__ldg(p.w + k) * ref.rho0));
+        fb[(size_t)k * nf + face] = fbar;
+        const double fd = f2d(fbar);
+        w2[0] += fd;
+        w2[1] = fma(__ldg(p.xi_x + k), fd, w2[1]);
+        w2[2] = fma(__ldg(p.xi_y + k), fd, w2[2]);
+      }
+    }
+    block_sum<3>(w2, sm);
+    v[0] += w2[0];
+    v[1] += w2[1];
+    v[2] += w2[2];
+  }
+  const EqF q = eq_params_j(ref.W + v[0], ref.Wx + v[1], ref.Wy + v[2], p.inv_RT, ref.rho0);
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
+    const size_t idx = (size_t)k * nf + face;
+    const float fe = feq_dev(q, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_YH, k), vt(vf, nv, GV_W, k));
+    fb[idx] = fmaf(alpha, fb[idx], beta * fe);
+  }
+}
+
+// ---------------------------------------------------------------- updates
+// L = -(xi_x (f_e - f_w)/dx + xi_y (f_n - f_s)/dy)   (eq. microflux)
+__device__ __forceinline__ float lflux(const DevParams& p, const float* __restrict__ vf,
+                                       const float* __restrict__ fbx,
+                                       const float* __restrict__ fby, int k, int i, int j) {
+  const int nx = p.nx, ny = p.ny;
+  const size_t bx = (size_t)k * ny * (nx + 1) + (size_t)j * (nx + 1) + i;
+  const size_t by = (size_t)k * (ny + 1) * nx + (size_t)j * nx + i;
+  return -fmaf(vt(vf, p.nv, GV_KX, k), __ldg(fbx + bx + 1) - __ldg(fbx + bx),
+               vt(vf, p.nv, GV_KY, k) * (__ldg(fby + by + nx) - __ldg(fby + by)));
+}
+
+// f~(t') = 5/4 g1 - 1/4 f^ + dt/3 L*,  acc = 1/4 f^ + 3/4 g1 + 3dt/7 L*
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gupdate1(DevParams p, const float* __restrict__ vf, const T* __restrict__ fhat,
+           const T* __restrict__ g1, const float* __restrict__ fbx,
+           const float* __restrict__ fby, T* __restrict__ ftp, T* __restrict__ acc, float dt3,
+           float dt37) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)p.nv * p.N) return;
+  const int k = (int)(t / p.N);
+  const int cell = (int)(t - (size_t)k * p.N);
+  const int j = cell / p.nx, i = cell - j * p.nx;
+  const float L = lflux(p, vf, fbx, fby, k, i, j);
+  const float fh = ldv(fhat + t), g = ldv(g1 + t);
+  stv(ftp + t, fmaf(1.25f, g, fmaf(-0.25f, fh, dt3 * L)));
+  stv(acc + t, fmaf(0.25f, fh, fmaf(0.75f, g, dt37 * L)));
+}
+
+// f^^{n+1} = acc + 3/4 dt Omega' + 4dt/7 L**,  dt Omega' = c_om (f~' - feq')
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gupdate2(DevParams p, const float* __restrict__ vf, const T* __restrict__ ftp,
+           const T* __restrict__ acc, const float* __restrict__ eqp,
+           const float* __restrict__ fbx, const float* __restrict__ fby, T* __restrict__ fhat,
+           float c_om34, float dt47) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)p.nv * p.N) return;
+  const int k = (int)(t / p.N);
+  const int cell = (int)(t - (size_t)k * p.N);
+  const int j = cell / p.nx, i = cell - j * p.nx;
+  const float L = lflux(p, vf, fbx, fby, k, i, j);
+  EqF q;
+  q.vx = __ldg(eqp + cell);
+  q.vy = __ldg(eqp + p.N + cell);
+  q.bm1 = __ldg(eqp + 2 * p.N + cell);
+  q.r = __ldg(eqp + 3 * p.N + cell);
+  q.dr = __ldg(eqp + 4 * p.N + cell);
+  const float fe =
+      feq_dev(q, vt(vf, p.nv, GV_XH, k), vt(vf, p.nv, GV_YH, k), vt(vf, p.nv, GV_W, k));
+  stv(fhat + t, fmaf(dt47, L, fmaf(c_om34, ldv(ftp + t) - fe, ldv(acc + t))));
+}
+
+unsigned nblk(size_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+template <typename T>
+cudaError_t cell_t(const GDevStep& s, const void* src, const StageCoef& c, cudaStream_t st) {
+  const DevParams& p = s.p;
+  if (p.nv > 32) {
+    constexpr int G = 8, TX = kThreads / G;
+    k_gcell<T, G><<<(p.N + TX - 1) / TX, dim3(TX, G), 0, st>>>(
+        p, s.ref, s.vf, (const T*)src, (T*)s.g, s.mom, s.eqp, (float)c.a, (float)c.b);
+  } else {
+    k_gcell<T, 1><<<(p.N + kThreads - 1) / kThreads, dim3(kThreads, 1), 0, st>>>(
+        p, s.ref, s.vf, (const T*)src, (T*)s.g, s.mom, s.eqp, (float)c.a, (float)c.b);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int DIR>
+cudaError_t faces_t(const GDevStep& s, const StageCoef& c, cudaStream_t st) {
+  const DevParams& p = s.p;
+  float* fb = DIR == 0 ? s.fbx : s.fby;
+  const int nch = DIR == 0 ? s.nchx : s.nchy;
+  const int kchunk = (p.nv + nch - 1) / nch;
+  const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
+  const dim3 grid(DIR == 0 ? (p.nx + 1 + LANES - 1) / LANES : (p.nx + LANES - 1) / LANES,
+                  DIR == 0 ? (p.ny + R - 1) / R : (p.ny + 1 + R - 1) / R, nch);
+  k_gfaces1<T, DIR><<<grid, LANES * NW, 0, st>>>(p, s.vf, (const T*)s.g, fb, s.part, (float)c.h,
+                                                kchunk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // velocity groups of pass 2: each thread forms its face equilibrium once
+  // and serves about nv / gy velocities
+  const int gy = p.nv < 128 ? (p.nv + 7) / 8 : 16;
+  const dim3 g2((nf + 255) / 256, gy);
+  k_gfaces2<DIR><<<g2, 256, 0, st>>>(p, s.ref, s.vf, fb, s.part, nch, (float)c.alpha,
+                                     (float)c.beta);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || (DIR == 0 ? p.px : p.py)) return e;
+  const int nw = 2 * (DIR == 0 ? p.ny : p.nx);
+  const int threads = p.nv >= kThreads ? kThreads : ((p.nv + 31) / 32) * 32;
+  k_gwall<T, DIR><<<nw, threads, 0, st>>>(p, s.ref, s.vf, (const T*)s.g, s.mom, fb, (float)c.h,
+                                          (float)c.alpha, (float)c.beta);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Velocity chunks of the interior-face pass 1: the grid of (face columns x
+// face rows x chunks) blocks is sized to fill whole waves of resident blocks
+// (time ~ waves / chunks), with a small charge per chunk for the partial
+// moments that pass 2 reads back.
+int gdev_chunks(const DevParams& p, int dir, int sms) {
+  int occ = 0;
+  const cudaError_t e = dir == 0
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gfaces1<float, 0>, LANES * NW, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gfaces1<float, 1>, LANES * NW, 0);
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const long slots = (long)occ * (sms > 0 ? sms : 1);
+  const long base = dir == 0 ? (long)((p.nx + LANES) / LANES) * ((p.ny + R - 1) / R)
+                             : (long)((p.nx + LANES - 1) / LANES) * ((p.ny + R) / R);
+  const int maxc = p.nv < 64 ? p.nv : 64;
+  int best = 1;
+  double bestc = 1e300;
+  for (int c = 1; c <= maxc; ++c) {
+    const long waves = (base * c + slots - 1) / slots;
+    const double cost = (double)waves / c + 0.002 * c;
+    if (cost < bestc - 1e-12) {
+      bestc = cost;
+      best = c;
+    }
+  }
+  return best;
+}
+
+cudaError_t launch_gdev_cell(const GDevStep& s, int stage, cudaStream_t st) {
+  const void* src = stage == 1 ? s.fhat : s.ftp;
+  const StageCoef& c = stage == 1 ? s.s1 : s.s2;
+  return s.store == 1 ? cell_t<float>(s, src, c, st) : cell_t<__nv_bfloat16>(s, src, c, st);
+}
+
+cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_t st) {
+  const StageCoef& c = stage == 1 ? s.s1 : s.s2;
+  if (s.store == 1)
+    return dir == 0 ? faces_t<float, 0>(s, c, st) : faces_t<float, 1>(s, c, st);
+  return dir == 0 ? faces_t<__nv_bfloat16, 0>(s, c, st) : faces_t<__nv_bfloat16, 1>(s, c, st);
+}
+
+cudaError_t launch_gdev_update(const GDevStep& s, int stage, cudaStream_t st) {
+  const DevParams& p = s.p;
+  const size_t n = (size_t)p.nv * p.N;
+  if (stage == 1) {
+    const float dt3 = (float)(p.dt / 3.0), dt37 = (float)(3.0 * p.dt / 7.0);
+    if (s.store == 1)
+      k_gupdate1<float><<<nblk(n), kThreads, 0, st>>>(p, s.vf, (const float*)s.fhat,
+                                                      (const float*)s.g, s.fbx, s.fby,
+                                                      (float*)s.ftp, (float*)s.acc, dt3, dt37);
+    else
+      k_gupdate1<__nv_bfloat16><<<nblk(n), kThreads, 0, st>>>(
+          p, s.vf, (const __nv_bfloat16*)s.fhat, (const __nv_bfloat16*)s.g, s.fbx, s.fby,
+          (__nv_bfloat16*)s.ftp, (__nv_bfloat16*)s.acc, dt3, dt37);
+  } else {
+    const float c34 = (float)(0.75 * s.c_om), dt47 = (float)(4.0 * p.dt / 7.0);
+    if (s.store == 1)
+      k_gupdate2<float><<<nblk(n), kThreads, 0, st>>>(p, s.vf, (const float*)s.ftp,
+                                                      (const float*)s.acc, s.eqp, s.fbx, s.fby,
+                                                      (float*)s.fhat, c34, dt47);
+    else
+      k_gupdate2<__nv_bfloat16><<<nblk(n), kThreads, 0, st>>>(
+          p, s.vf, (const __nv_bfloat16*)s.ftp, (const __nv_bfloat16*)s.acc, s.eqp, s.fbx,
+          s.fby, (__nv_bfloat16*)s.fhat, c34, dt47);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dugks

@@ -31,6 +31,11 @@ enum KernelId {
   K_D2Q9M_STAGE1,      // deviation-storage (FP32/BF16) D2Q9 path, stage 1
   K_D2Q9M_STAGE2,      // deviation-storage D2Q9 path, stage 2
   K_CONVERT,           // FP64 <-> deviation storage
+  K_GDEV_CELL,         // deviation-storage generic path: cell pass (both stages)
+  K_GDEV_FACE_X,       // x faces (interior passes + walls, both stages)
+  K_GDEV_FACE_Y,       // y faces
+  K_GDEV_UPDATE1,      // L*, f~(t'), accumulator
+  K_GDEV_UPDATE2,      // L**, dt Omega', f^^{n+1}
   K_NUM
 };
 
@@ -120,6 +125,34 @@ cudaError_t launch_dev_cell(const DevParams& p, int store, double rho0, const vo
 cudaError_t launch_dev_set_eq(const DevParams& p, int store, double rho0, const double* rho,
                               const double* ux, const double* uy, void* d, cudaStream_t st);
 cudaError_t d2q9m_prepare();
+
+// Deviation-storage form of the generic path (dugks_generic_mixed.cu), any
+// velocity set.  fhat/g/ftp/acc hold typed deviations d = f - W rho0 (store
+// 1 = FP32, 2 = BF16), fbx/fby FP32 face deviations, mom FP64 (rho, ux, uy)
+// of the last cell pass, eqp [5][N] its FP32 equilibrium parameters.
+struct GDevRef {
+  double rho0, W, Wx, Wy;       // rho0, rho0 sum W_k, rho0 sum W_k xi_x, rho0 sum W_k xi_y
+};
+// FP32 per-velocity tables of that path, rows of vf[GV_N][nv]:
+// xi rounded to FP32 and its remainder (xi = xh + xl to ~2^-48), W_k, and
+// the flux factors xi_x/dx, xi_y/dy.
+enum { GV_XH = 0, GV_YH, GV_XL, GV_YL, GV_W, GV_KX, GV_KY, GV_N };
+struct GDevStep {
+  DevParams p;
+  GDevRef ref;
+  int store;
+  StageCoef s1, s2;
+  double c_om;
+  void *fhat, *g, *ftp, *acc;
+  float *fbx, *fby, *eqp;
+  const float* vf;
+  double *mom, *part;           // part: [nch][3][nf] partial face moments
+  int nchx, nchy;
+};
+int gdev_chunks(const DevParams& p, int dir, int sms);
+cudaError_t launch_gdev_cell(const GDevStep& s, int stage, cudaStream_t st);
+cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_t st);
+cudaError_t launch_gdev_update(const GDevStep& s, int stage, cudaStream_t st);
 
 // One instance of a batched D2Q9 FP64 launch (device memory).
 struct D2Q9BatchItem {

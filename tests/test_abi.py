@@ -82,10 +82,3 @@ def test_product_velocity_sets_match_oracle():
     a, b = PV.d2q9(0.4), V.d2q9(0.4)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
-
-
-def test_deviation_storage_needs_d2q9(lib):
-    xi, W, RT = PV.newton_cotes(8, 0.5)
-    with pytest.raises(P.DugksError) as e:
-        P.dugks_init(8, 8, .1, .1, xi, W, RT, .1, .1, [(P.PERIODIC, 0, 0)] * 4, storage=P.G_FP32)
-    assert e.value.code == P.DUGKS_ENOTIMPL
