@@ -83,6 +83,8 @@ struct dugks_ctx {
   GDevStep gs{};
   float* eqp = nullptr;
   float* vf = nullptr;          // FP32 velocity tables [GV_N][nv]
+  void* gpad = nullptr;         // padded stage field of that path
+  float* fpar = nullptr;        // face equilibrium parameters of that path
   // adjoint (allocated on first use): forward intermediates and adjoint fields
   double *a_g1 = nullptr, *a_g2 = nullptr, *a_ftp = nullptr, *a_acc = nullptr;
   double *a_mom1 = nullptr, *a_mom2 = nullptr, *a_tbar = nullptr, *a_gbar = nullptr;
@@ -197,6 +199,8 @@ void free_all(dugks_ctx* c) {
   if (c->flag) cudaFree(c->flag);
   if (c->eqp) cudaFree(c->eqp);
   if (c->vf) cudaFree(c->vf);
+  if (c->gpad) cudaFree(c->gpad);
+  if (c->fpar) cudaFree(c->fpar);
   for (auto& q : c->pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -664,7 +668,11 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     const size_t nfmax = std::max((size_t)p.ny * (p.nx + 1), (size_t)(p.ny + 1) * p.nx);
     if (!c->part)
       e = cudaMalloc((void**)&c->part, (size_t)std::max(g.nchx, g.nchy) * 3 * nfmax * sizeof(double));
+    g.pitch = gdev_pitch(p.nx);
+    g.plane = (size_t)(p.ny + 4) * g.pitch;
+    if (e == cudaSuccess) e = cudaMalloc(&c->gpad, g.plane * nv * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->eqp, 5 * (size_t)p.N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->fpar, 5 * 2 * nfmax * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->vf, (size_t)GV_N * nv * sizeof(float));
     if (e == cudaSuccess) {
       std::vector<float> t((size_t)GV_N * nv);
@@ -689,12 +697,14 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
                   std::string("device allocation: ") + cudaGetErrorString(e));
     }
     g.fhat = c->fhat;
-    g.g = c->g;
+    g.g = c->gpad;
     g.ftp = c->ftp;
     g.acc = c->acc;
     g.fbx = (float*)c->fbx;
     g.fby = (float*)c->fby;
     g.eqp = c->eqp;
+    g.fpx = c->fpar;
+    g.fpy = c->fpar + 5 * nfmax;
     g.vf = c->vf;
     g.mom = c->mom;
     g.part = c->part;

@@ -1,7 +1,8 @@
 // Deviation-storage (FP32 / BF16) form of the generic path: any velocity
 // set (Newton-Cotes grids in particular), periodic / bounce-back / diffuse
 // walls.  Same step structure as the FP64 generic path:
-//   cell(stage) -> faces x, y (interior slab kernels + wall faces) -> update.
+//   cell(stage) -> ghosts -> faces x, y (interior slab kernels + wall
+//   faces) -> update.
 // Every per-(cell, velocity) array holds d = f - W_k rho0; face values are
 // FP32 deviations.  Stencils, fluxes, the stage transforms and the
 // per-velocity equilibrium assembly W_k((rho - rho0) + rho (P_k - 1)) run in
@@ -17,6 +18,14 @@
 // f_bar_1_6, fbp_5_12, recover2f, f_tilde_1_3, fhp, feqIntD3rdHat2_DS) are
 // affine with coefficients summing to one and the flux divergence of a
 // uniform field vanishes, so they act on deviations unchanged.
+//
+// The stage field g = f-bar^{+,h} lives in a padded layout
+// g[k][ny + 4][pitch], cell (i, j) at row j + 2, column i + 2, with two
+// ghost layers: periodic copies, or the quadratic extrapolation across a
+// wall (g_-1 = 3 g_0 - 3 g_1 + g_2; the second layer repeats the first and
+// feeds no face).  The pitch is a multiple of 8 elements with room for a
+// 16-byte chunk past column nx + 1, so the face kernels stage their slabs
+// with aligned 16-byte asynchronous copies and no boundary logic.
 #include <cuda_bf16.h>
 
 #include "dugks_internal.cuh"
@@ -33,11 +42,25 @@ template <> __device__ __forceinline__ float ldv<float>(const float* p) { return
 template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16* p) {
   return __bfloat162float(__ldg(p));
 }
+template <typename T> __device__ __forceinline__ float lds(const T* p);
+template <> __device__ __forceinline__ float lds<float>(const float* p) { return *p; }
+template <> __device__ __forceinline__ float lds<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
 template <typename T> __device__ __forceinline__ void stv(T* p, float v);
 template <> __device__ __forceinline__ void stv<float>(float* p, float v) { *p = v; }
 template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16* p, float v) {
   *p = __float2bfloat16_rn(v);
 }
+
+// asynchronous 16-byte global -> shared copy (bypassing L1) and its groups
+__device__ __forceinline__ void cp16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // exact FP32 -> FP64 on the integer pipe; zero and denormals -> 0, inf and
 // NaN kept
@@ -147,95 +170,155 @@ __device__ __forceinline__ void block_sum(double (&v)[M], double* sm) {
   __syncthreads();
 }
 
-// Sum over the G velocity groups (threadIdx.y) of a block column.
-template <int G, int TX, int M>
-__device__ __forceinline__ void group_sum(double (&v)[M], double* red) {
-  if constexpr (G > 1) {
-    const int tx = threadIdx.x, ty = threadIdx.y;
-#pragma unroll
-    for (int m = 0; m < M; ++m) red[(m * G + ty) * TX + tx] = v[m];
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-      double s = 0.0;
-#pragma unroll
-      for (int q = 0; q < G; ++q) s += red[(m * G + q) * TX + tx];
-      v[m] = s;
-    }
-    __syncthreads();
-  }
+// padded offset of cell (i, j) (ghosts: -2 <= i <= nx + 1, -2 <= j <= ny + 1)
+__device__ __forceinline__ size_t gp_at(const GDevStep& s, int k, int i, int j) {
+  return (size_t)k * s.plane + (size_t)(j + 2) * s.pitch + (i + 2);
 }
 
 // ---------------------------------------------------------------- cell
-// Moments of src -> mom (rho, ux, uy, FP64) and the FP32 assembly
-// parameters eqp[5][N]; g = a src + b feq as a deviation.
+// Per cell: moments of src over the velocity set (G groups of velocities per
+// column of TX cells, eight loads in flight per thread); one thread per cell
+// forms rho, u (FP64, into mom) and the FP32 assembly parameters (into eqp
+// and shared memory); then g = a src + b feq as a deviation, in the padded
+// layout.
 template <typename T, int G>
 __global__ void __launch_bounds__(kThreads)
-k_gcell(DevParams p, GDevRef ref, const float* __restrict__ vf, const T* __restrict__ src,
-        T* __restrict__ g, double* __restrict__ mom, float* __restrict__ eqp, float a, float b) {
+k_gcell(GDevStep s, const T* __restrict__ src, float a, float b) {
   constexpr int TX = kThreads / G;
+  constexpr int U = 8;
   __shared__ double red[G > 1 ? 3 * G * TX : 1];
+  __shared__ float eqs[5][TX];
+  const DevParams& p = s.p;
+  const float* __restrict__ vf = s.vf;
+  T* __restrict__ g = (T*)s.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int cell = blockIdx.x * TX + tx;
   const bool valid = cell < p.N;
   const int nv = p.nv;
   Acc s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
-  if (valid)
-    for (int k = ty; k < nv; k += G) {
+  if (valid) {
+    int k = ty;
+    for (; k + (U - 1) * G < nv; k += U * G) {
+      float d[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) d[u] = ldv(src + (size_t)(k + u * G) * p.N + cell);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int kk = k + u * G;
+        acc_add(s0, d[u]);
+        acc_addprod(s1, vt(vf, nv, GV_XH, kk), vt(vf, nv, GV_XL, kk), d[u]);
+        acc_addprod(s2, vt(vf, nv, GV_YH, kk), vt(vf, nv, GV_YL, kk), d[u]);
+      }
+    }
+    for (; k < nv; k += G) {
       const float d = ldv(src + (size_t)k * p.N + cell);
       acc_add(s0, d);
       acc_addprod(s1, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_XL, k), d);
       acc_addprod(s2, vt(vf, nv, GV_YH, k), vt(vf, nv, GV_YL, k), d);
     }
-  double v[3] = {acc_value(s0), acc_value(s1), acc_value(s2)};
-  group_sum<G, TX, 3>(v, red);
-  if (!valid) return;
-  const double rho = ref.W + v[0];
-  const double rinv = 1.0 / rho;
-  const double ux = (ref.Wx + v[1]) * rinv, uy = (ref.Wy + v[2]) * rinv;
-  const EqF q = eq_params_u(rho, ux, uy, p.inv_RT, ref.rho0);
-  if (ty == 0) {
-    mom[cell] = rho;
-    mom[p.N + cell] = ux;
-    mom[2 * p.N + cell] = uy;
-    eqp[cell] = q.vx;
-    eqp[p.N + cell] = q.vy;
-    eqp[2 * p.N + cell] = q.bm1;
-    eqp[3 * p.N + cell] = q.r;
-    eqp[4 * p.N + cell] = q.dr;
   }
-  for (int k = ty; k < nv; k += G) {
-    const size_t idx = (size_t)k * p.N + cell;
+  double v[3] = {acc_value(s0), acc_value(s1), acc_value(s2)};
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) red[(m * G + ty) * TX + tx] = v[m];
+    __syncthreads();
+    if (ty == 0)
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        double t = 0.0;
+#pragma unroll
+        for (int q = 0; q < G; ++q) t += red[(m * G + q) * TX + tx];
+        v[m] = t;
+      }
+  }
+  if (ty == 0 && valid) {
+    const GDevRef& ref = s.ref;
+    const double rho = ref.W + v[0];
+    const double rinv = 1.0 / rho;
+    const double ux = (ref.Wx + v[1]) * rinv, uy = (ref.Wy + v[2]) * rinv;
+    const EqF q = eq_params_u(rho, ux, uy, p.inv_RT, ref.rho0);
+    s.mom[cell] = rho;
+    s.mom[p.N + cell] = ux;
+    s.mom[2 * p.N + cell] = uy;
+    const float qv[5] = {q.vx, q.vy, q.bm1, q.r, q.dr};
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      s.eqp[m * p.N + cell] = qv[m];
+      eqs[m][tx] = qv[m];
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  const EqF q{eqs[0][tx], eqs[1][tx], eqs[2][tx], eqs[3][tx], eqs[4][tx]};
+  const int j = cell / p.nx, i = cell - j * p.nx;
+  int k = ty;
+  for (; k + 3 * G < nv; k += 4 * G) {
+    float d[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[u] = ldv(src + (size_t)(k + u * G) * p.N + cell);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = k + u * G;
+      const float fe =
+          feq_dev(q, vt(vf, nv, GV_XH, kk), vt(vf, nv, GV_YH, kk), vt(vf, nv, GV_W, kk));
+      stv(g + gp_at(s, kk, i, j), fmaf(b, fe, a * d[u]));
+    }
+  }
+  for (; k < nv; k += G) {
     const float fe = feq_dev(q, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_YH, k), vt(vf, nv, GV_W, k));
-    stv(g + idx, fmaf(b, fe, a * ldv(src + idx)));
+    stv(g + gp_at(s, k, i, j), fmaf(b, fe, a * ldv(src + (size_t)k * p.N + cell)));
   }
 }
 
-// ---------------------------------------------------------- interior faces
-// g at (gx, gy): interior, periodic wrap, one ghost layer of quadratic
-// extrapolation (g_-1 = 3 g_0 - 3 g_1 + g_2); positions further out are
-// clamped (their values feed no face).
+// ---------------------------------------------------------------- ghosts
+// The two ghost layers of every velocity plane of g.  Positions are
+// periodic copies, or one layer of quadratic extrapolation across a wall
+// (along x of the y-extrapolated columns at corners); the second layer
+// beyond a wall repeats the first.  Reads interior cells only.
 template <typename T>
-__device__ __forceinline__ float gfetch(const T* __restrict__ gk, const DevParams& p, int gx,
-                                        int gy) {
-  if (gx >= 0 && gx < p.nx && gy >= 0 && gy < p.ny) return ldv(gk + gy * p.nx + gx);
-  if (p.px) gx = ((gx % p.nx) + p.nx) % p.nx;
-  else gx = gx < -1 ? -1 : (gx > p.nx ? p.nx : gx);
-  if (p.py) gy = ((gy % p.ny) + p.ny) % p.ny;
-  else gy = gy < -1 ? -1 : (gy > p.ny ? p.ny : gy);
-  auto col = [&](int x, int y) {
-    if (y < 0 || y >= p.ny) {
-      const int b = y < 0 ? 0 : p.ny - 1, s = y < 0 ? 1 : -1;
-      return 3.f * ldv(gk + b * p.nx + x) - 3.f * ldv(gk + (b + s) * p.nx + x) +
-             ldv(gk + (b + 2 * s) * p.nx + x);
-    }
-    return ldv(gk + y * p.nx + x);
-  };
-  if (gx < 0 || gx >= p.nx) {
-    const int b = gx < 0 ? 0 : p.nx - 1, s = gx < 0 ? 1 : -1;
-    return 3.f * col(b, gy) - 3.f * col(b + s, gy) + col(b + 2 * s, gy);
+__global__ void __launch_bounds__(kThreads)
+k_gghost(GDevStep s) {
+  const DevParams& p = s.p;
+  const int nx = p.nx, ny = p.ny;
+  const int W = nx + 4;
+  const int per = 4 * W + 4 * ny;                 // rows -2,-1,ny,ny+1 (all columns) + 4 columns
+  const int k = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per) return;
+  int x, y;
+  if (t < 4 * W) {
+    const int rsel = t / W;
+    x = t - rsel * W - 2;
+    y = rsel < 2 ? rsel - 2 : ny + rsel - 2;
+  } else {
+    const int u = t - 4 * W;
+    const int csel = u / ny;
+    y = u - csel * ny;
+    x = csel < 2 ? csel - 2 : nx + csel - 2;
   }
-  return col(gx, gy);
+  T* __restrict__ g = (T*)s.g;
+  const T* gk = g + (size_t)k * s.plane;
+  int xx = x, yy = y;
+  if (p.px) xx = (xx + nx) % nx;
+  else xx = xx < -1 ? -1 : (xx > nx ? nx : xx);
+  if (p.py) yy = (yy + ny) % ny;
+  else yy = yy < -1 ? -1 : (yy > ny ? ny : yy);
+  auto at = [&](int i, int j) { return ldv(gk + (size_t)(j + 2) * s.pitch + (i + 2)); };
+  auto col = [&](int i, int j) {
+    if (j < 0 || j >= ny) {
+      const int b = j < 0 ? 0 : ny - 1, sg = j < 0 ? 1 : -1;
+      return 3.f * at(i, b) - 3.f * at(i, b + sg) + at(i, b + 2 * sg);
+    }
+    return at(i, j);
+  };
+  float v;
+  if (xx < 0 || xx >= nx) {
+    const int b = xx < 0 ? 0 : nx - 1, sg = xx < 0 ? 1 : -1;
+    v = 3.f * col(b, yy) - 3.f * col(b + sg, yy) + col(b + 2 * sg, yy);
+  } else {
+    v = col(xx, yy);
+  }
+  stv(g + gp_at(s, k, x, y), v);
 }
 
 // quadratic Taylor weights about a cell for the foot offset (a dx, b dy),
@@ -247,29 +330,49 @@ __device__ __forceinline__ void taylor9f(float a, float b, float (&T)[9]) {
   T[6] = -ab;                  T[7] = 0.5f * (b * b + b);  T[8] = ab;
 }
 
-// Pass 1: lanes over 32 faces, warps over velocities, R face rows per block;
-// FP32 stencils from a per-warp slab of g in shared memory, compensated
-// partial face moments, combined in FP64 per velocity chunk into
-// part[chunk][3][nf].
+// ---------------------------------------------------------- interior faces
+// Pass 1: lanes over 32 faces, warps over velocities, R face rows per block.
+// Each warp stages the slab of g its velocity needs (SR rows x SW columns,
+// from padded column c0) in shared memory with 16-byte asynchronous copies,
+// double-buffered so the next velocity's slab loads while the current one
+// is used; FP32 stencils, compensated partial face moments, combined in
+// FP64 per velocity chunk into part[chunk][3][nf].
 template <typename T, int DIR>
-__global__ void __launch_bounds__(LANES * NW)
-k_gfaces1(DevParams p, const float* __restrict__ vf, const T* __restrict__ g,
-          float* __restrict__ fb, double* __restrict__ part, float h, int kchunk) {
-  constexpr int SR = DIR == 0 ? R + 2 : R + 3;
-  constexpr int SC = DIR == 0 ? 36 : 34;
-  // the warps' slabs, later reused for the reduction
-  __shared__ double smem[NW * R * LANES * 3];
-  static_assert(NW * SR * SC * sizeof(float) <= sizeof(smem), "slab too large");
+struct Slab {
+  static constexpr int SR = DIR == 0 ? R + 2 : R + 3;          // rows
+  static constexpr int SW = sizeof(T) == 4 ? 36 : 40;          // columns (x 16-byte chunks)
+  static constexpr int EPC = 16 / sizeof(T);                   // elements per chunk
+  static constexpr int CPR = SW / EPC;                         // chunks per row
+  static constexpr int NCH = SR * CPR;
+  static constexpr int ELEMS = SR * SW;
+};
+
+template <typename T, int DIR>
+__global__ void __launch_bounds__(LANES * NW, 2)
+k_gfaces1(GDevStep s, float* __restrict__ fb, float h, int kchunk) {
+  using S = Slab<T, DIR>;
+  constexpr int SW = S::SW;
+  // the stencil reads rows r .. r + 2 (+1 for y faces) and columns
+  // lane .. lane + 3 of the slab
+  static_assert(S::SR >= R + (DIR == 0 ? 2 : 3) && SW >= LANES + 3, "slab too small");
+  // the warps' double-buffered slabs, later reused for the reduction
+  __shared__ __align__(16) double smem[NW * R * LANES * 3];
+  static_assert(NW * 2 * S::ELEMS * sizeof(T) <= sizeof(smem), "slab too large");
   auto red = [&](int w, int r, int l, int m) -> double& {
     return smem[((w * R + r) * LANES + l) * 3 + m];
   };
+  const DevParams& p = s.p;
+  const float* __restrict__ vf = s.vf;
+  const T* __restrict__ g = (const T*)s.g;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nx = p.nx, ny = p.ny, nv = p.nv;
   const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
   const int c0 = blockIdx.x * LANES, r0 = blockIdx.y * R;
   const int k0 = blockIdx.z * kchunk, k1 = min(nv, k0 + kchunk);
-  const int ox = DIR == 0 ? c0 - 2 : c0 - 1;
-  const int oy = DIR == 0 ? r0 - 1 : r0 - 2;
+  // slab origin in padded coordinates: column c0 (cell c0 - 2); first row
+  // cell r0 - 1 (x faces) or r0 - 2 (y faces)
+  const int prow0 = DIR == 0 ? r0 + 1 : r0;
+  const int prows = ny + 4;
   const float dx = (float)p.dx, dy = (float)p.dy;
   const float idx_ = (float)p.inv_dx, idy = (float)p.inv_dy;
   Acc acc[R][3];
@@ -287,8 +390,25 @@ k_gfaces1(DevParams p, const float* __restrict__ vf, const T* __restrict__ g,
       ok[r] = col < nx && fj <= ny && (p.py || (fj >= 1 && fj <= ny - 1));
     }
   }
-  float* sl = reinterpret_cast<float*>(smem) + warp * SR * SC;
+  T* slab = reinterpret_cast<T*>(smem) + warp * 2 * S::ELEMS;
+  // issue the copies of velocity k's slab into buffer b (chunks beyond the
+  // padded plane feed no face and are skipped)
+  auto issue = [&](int k, int b) {
+    const T* gk = g + (size_t)k * s.plane;
+    T* dst = slab + b * S::ELEMS;
+    for (int e = lane; e < S::NCH; e += LANES) {
+      const int rr = e / S::CPR, cc = (e - rr * S::CPR) * S::EPC;
+      const int pr = prow0 + rr, pc = c0 + cc;
+      if (pr < prows && pc + S::EPC <= s.pitch)
+        cp16(dst + rr * SW + cc, gk + (size_t)pr * s.pitch + pc);
+    }
+  };
+  int b = 0;
+  if (k0 + warp < k1) issue(k0 + warp, 0);
+  cp_commit();
   for (int k = k0 + warp; k < k1; k += NW) {
+    if (k + NW < k1) issue(k + NW, b ^ 1);
+    cp_commit();
     const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k);
     const float cxl = vt(vf, nv, GV_XL, k), cyl = vt(vf, nv, GV_YL, k);
     const float cn = DIR == 0 ? cx : cy;
@@ -303,31 +423,30 @@ k_gfaces1(DevParams p, const float* __restrict__ vf, const T* __restrict__ g,
       if (lo) taylor9f(aa, (0.5f * dy - cy * h) * idy, TL);
       if (hi) taylor9f(aa, (-0.5f * dy - cy * h) * idy, TU);
     }
-    const T* gk = g + (size_t)k * p.N;
+    cp_wait1();                                    // this velocity's slab has landed
     __syncwarp();
-    for (int e = lane; e < SR * SC; e += LANES) {
-      const int rr = e / SC, cc = e - rr * SC;
-      sl[e] = gfetch(gk, p, ox + cc, oy + rr);
-    }
-    __syncwarp();
+    const T* sl = slab + b * S::ELEMS;
     float* fbk = fb + (size_t)k * nf;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if (!ok[r]) continue;
-      const float* s0 = sl + r * SC + lane;
+      // x faces: rows r..r+2 (cells j-1..j+1), columns lane+q (cells fi-2+q);
+      // y faces: rows r+q (cells fj-2+q), columns lane+1+q (cells i-1+q)
+      const T* s0 = sl + r * SW + lane + (DIR == 0 ? 0 : 1);
       float vl = 0.f, vu = 0.f;
       if (lo) {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int q = 0; q < 3; ++q) vl = fmaf(TL[a * 3 + q], s0[a * SC + q], vl);
+          for (int q = 0; q < 3; ++q) vl = fmaf(TL[a * 3 + q], lds(s0 + a * SW + q), vl);
       }
       if (hi) {
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
           for (int q = 0; q < 3; ++q)
-            vu = fmaf(TU[a * 3 + q], DIR == 0 ? s0[a * SC + q + 1] : s0[(a + 1) * SC + q], vu);
+            vu = fmaf(TU[a * 3 + q], lds(DIR == 0 ? s0 + a * SW + q + 1 : s0 + (a + 1) * SW + q),
+                      vu);
       }
       const float v = (lo && hi) ? 0.5f * (vl + vu) : (lo ? vl : vu);
       const int face = DIR == 0 ? (r0 + r) * (nx + 1) + col : (r0 + r) * nx + col;
@@ -336,8 +455,11 @@ k_gfaces1(DevParams p, const float* __restrict__ vf, const T* __restrict__ g,
       acc_addprod(acc[r][1], cx, cxl, v);
       acc_addprod(acc[r][2], cy, cyl, v);
     }
+    __syncwarp();                                  // buffer b is refilled two velocities on
+    b ^= 1;
   }
-  __syncthreads();                                  // all slabs done: reuse the memory
+  cp_wait_all();
+  __syncthreads();                                 // all slabs done: reuse the memory
 #pragma unroll
   for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -363,21 +485,22 @@ k_gfaces1(DevParams p, const float* __restrict__ vf, const T* __restrict__ g,
       s1 += red(w, r, l, 1);
       s2 += red(w, r, l, 2);
     }
-    double* pc = part + (size_t)blockIdx.z * 3 * nf;
+    double* pc = s.part + (size_t)blockIdx.z * 3 * nf;
     pc[face] = s0;
     pc[nf + face] = s1;
     pc[2 * nf + face] = s2;
   }
 }
 
-// Pass 2: face moments (FP64, chunks summed in order) -> face equilibrium
-// (eq. recover2f) -> f = alpha f-bar + beta feq.  Wall faces are skipped.
-// blockIdx.y strides the velocities; four are in flight per thread.
+// Face parameters of the interior faces: the face moments (FP64, velocity
+// chunks summed in order) and the FP32 assembly parameters of the face
+// equilibrium, fpar[5][nf] (eq. recover2f is applied where the update reads
+// the face values: f = alpha f-bar + beta feq).  Wall faces are skipped.
 template <int DIR>
 __global__ void __launch_bounds__(256)
-k_gfaces2(DevParams p, GDevRef ref, const float* __restrict__ vf, float* __restrict__ fb,
-          const double* __restrict__ part, int nchunk, float alpha, float beta) {
-  const int nx = p.nx, ny = p.ny, nv = p.nv;
+k_gfacepar(GDevStep s, float* __restrict__ fpar, int nchunk) {
+  const DevParams& p = s.p;
+  const int nx = p.nx, ny = p.ny;
   const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
   const int face = blockIdx.x * blockDim.x + threadIdx.x;
   if (face >= nf) return;
@@ -388,32 +511,19 @@ k_gfaces2(DevParams p, GDevRef ref, const float* __restrict__ vf, float* __restr
     const int fj = face / nx;
     if (!p.py && (fj == 0 || fj == ny)) return;
   }
-  double r = ref.W, jx = ref.Wx, jy = ref.Wy;
+  double r = s.ref.W, jx = s.ref.Wx, jy = s.ref.Wy;
   for (int c = 0; c < nchunk; ++c) {
-    const double* pc = part + (size_t)c * 3 * nf;
+    const double* pc = s.part + (size_t)c * 3 * nf;
     r += pc[face];
     jx += pc[nf + face];
     jy += pc[2 * nf + face];
   }
-  const EqF q = eq_params_j(r, jx, jy, p.inv_RT, ref.rho0);
-  const int ks = gridDim.y;
-  int k = blockIdx.y;
-  for (; k + 3 * ks < nv; k += 4 * ks) {
-    float f[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) f[u] = fb[(size_t)(k + u * ks) * nf + face];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int kk = k + u * ks;
-      const float fe = feq_dev(q, vt(vf, nv, GV_XH, kk), vt(vf, nv, GV_YH, kk), vt(vf, nv, GV_W, kk));
-      fb[(size_t)kk * nf + face] = fmaf(alpha, f[u], beta * fe);
-    }
-  }
-  for (; k < nv; k += ks) {
-    const size_t idx = (size_t)k * nf + face;
-    const float fe = feq_dev(q, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_YH, k), vt(vf, nv, GV_W, k));
-    fb[idx] = fmaf(alpha, fb[idx], beta * fe);
-  }
+  const EqF q = eq_params_j(r, jx, jy, p.inv_RT, s.ref.rho0);
+  fpar[face] = q.vx;
+  fpar[nf + face] = q.vy;
+  fpar[2 * nf + face] = q.bm1;
+  fpar[3 * nf + face] = q.r;
+  fpar[4 * nf + face] = q.dr;
 }
 
 // -------------------------------------------------------------- wall faces
@@ -421,29 +531,32 @@ k_gfaces2(DevParams p, GDevRef ref, const float* __restrict__ vf, float* __restr
 // reconstruction (velocities leaving the fluid or along the wall), the wall
 // rule of Sec. 2.3 for velocities entering the fluid (bounce-back with the
 // moving-wall term, or diffuse scattering with the density that balances
-// the outgoing flux), face moments (FP64, few terms per thread), then
-// f = alpha f-bar + beta feq.  Faces: id = 2 line + (0: W/S wall, 1: E/N).
+// the outgoing flux), f-bar into fb, the face moments (FP64, few terms per
+// thread) and the face's assembly parameters into fpar.  Faces:
+// id = 2 line + (0: W/S wall, 1: E/N).
 template <typename T>
-__device__ __forceinline__ float taylor_at(const T* __restrict__ gk, const DevParams& p, int ci,
-                                           int cj, float X, float Y) {
+__device__ __forceinline__ float taylor_at(const GDevStep& s, const T* __restrict__ g, int k,
+                                           int ci, int cj, float X, float Y) {
   float Tw[9];
-  taylor9f(X * (float)p.inv_dx, Y * (float)p.inv_dy, Tw);
+  taylor9f(X * (float)s.p.inv_dx, Y * (float)s.p.inv_dy, Tw);
   float v = 0.f;
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx)
-      v = fmaf(Tw[(dy + 1) * 3 + dx + 1], gfetch(gk, p, ci + dx, cj + dy), v);
+      v = fmaf(Tw[(dy + 1) * 3 + dx + 1], ldv(g + gp_at(s, k, ci + dx, cj + dy)), v);
   return v;
 }
 
 template <typename T, int DIR>
 __global__ void __launch_bounds__(kThreads)
-k_gwall(DevParams p, GDevRef ref, const float* __restrict__ vf, const T* __restrict__ g,
-        const double* __restrict__ mom, float* __restrict__ fb, float h, float alpha,
-        float beta) {
+k_gwall(GDevStep s, float* __restrict__ fb, float* __restrict__ fpar, float h) {
   __shared__ double sm[32 * 4];
-  const int nx = p.nx, ny = p.ny, N = p.N, nv = p.nv;
+  const DevParams& p = s.p;
+  const GDevRef& ref = s.ref;
+  const float* __restrict__ vf = s.vf;
+  const T* __restrict__ g = (const T*)s.g;
+  const int nx = p.nx, ny = p.ny, nv = p.nv;
   const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
   const int id = blockIdx.x;
   const bool upper_wall = id & 1;                 // east / north
@@ -460,14 +573,14 @@ k_gwall(DevParams p, GDevRef ref, const float* __restrict__ vf, const T* __restr
   const int kind = p.bc_kind[side];
   const float half = 0.5f * (float)(DIR == 0 ? p.dx : p.dy);
   const float off = fluid_hi ? -half : half;      // face centre from the fluid cell centre
-  const float rho_w = (float)mom[cj * nx + ci];
+  const float rho_w = (float)s.mom[cj * nx + ci];
   const float uwx = (float)p.uw_x[side], uwy = (float)p.uw_y[side];
   const float irt = (float)p.inv_RT;
   auto recon = [&](int k) {
     const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k);
     const float X = DIR == 0 ? off - cx * h : -cx * h;
     const float Y = DIR == 0 ? -cy * h : off - cy * h;
-    return taylor_at(g + (size_t)k * N, p, ci, cj, X, Y);
+    return taylor_at(s, g, k, ci, cj, X, Y);
   };
   double v[4] = {0.0, 0.0, 0.0, 0.0};            // moments of f-bar, diffuse numerator
   for (int k = threadIdx.x; k < nv; k += blockDim.x) {
@@ -516,81 +629,147 @@ k_gwall(DevParams p, GDevRef ref, const float* __restrict__ vf, const T* __restr
     v[1] += w2[1];
     v[2] += w2[2];
   }
-  const EqF q = eq_params_j(ref.W + v[0], ref.Wx + v[1], ref.Wy + v[2], p.inv_RT, ref.rho0);
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-    const size_t idx = (size_t)k * nf + face;
-    const float fe = feq_dev(q, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_YH, k), vt(vf, nv, GV_W, k));
-    fb[idx] = fmaf(alpha, fb[idx], beta * fe);
+  if (threadIdx.x == 0) {
+    const EqF q = eq_params_j(ref.W + v[0], ref.Wx + v[1], ref.Wy + v[2], p.inv_RT, ref.rho0);
+    fpar[face] = q.vx;
+    fpar[nf + face] = q.vy;
+    fpar[2 * nf + face] = q.bm1;
+    fpar[3 * nf + face] = q.r;
+    fpar[4 * nf + face] = q.dr;
   }
 }
 
 // ---------------------------------------------------------------- updates
-// L = -(xi_x (f_e - f_w)/dx + xi_y (f_n - f_s)/dy)   (eq. microflux)
-__device__ __forceinline__ float lflux(const DevParams& p, const float* __restrict__ vf,
-                                       const float* __restrict__ fbx,
-                                       const float* __restrict__ fby, int k, int i, int j) {
-  const int nx = p.nx, ny = p.ny;
-  const size_t bx = (size_t)k * ny * (nx + 1) + (size_t)j * (nx + 1) + i;
-  const size_t by = (size_t)k * (ny + 1) * nx + (size_t)j * nx + i;
-  return -fmaf(vt(vf, p.nv, GV_KX, k), __ldg(fbx + bx + 1) - __ldg(fbx + bx),
-               vt(vf, p.nv, GV_KY, k) * (__ldg(fby + by + nx) - __ldg(fby + by)));
+// One thread per cell and KB consecutive velocities: the assembly
+// parameters of the cell and of its four faces are read once; the face
+// values f = alpha f-bar + beta feq (eq. recover2f) are formed here, and
+// L = -(xi_x (f_e - f_w)/dx + xi_y (f_n - f_s)/dy) (eq. microflux).
+constexpr int KB = 8;
+
+__device__ __forceinline__ EqF load_par(const float* __restrict__ fp, int n, int i) {
+  return EqF{__ldg(fp + i), __ldg(fp + n + i), __ldg(fp + 2 * n + i), __ldg(fp + 3 * n + i),
+             __ldg(fp + 4 * n + i)};
+}
+
+struct FaceCtx {
+  EqF w, e, so, no;                      // parameters of the W, E, S, N faces
+  size_t bx, by;                         // fbx / fby index of the W / S face, velocity 0
+  int nfx, nfy, nx;
+};
+__device__ __forceinline__ FaceCtx face_ctx(const GDevStep& s, int i, int j) {
+  const int nx = s.p.nx, ny = s.p.ny;
+  FaceCtx c;
+  c.nx = nx;
+  c.nfx = ny * (nx + 1);
+  c.nfy = (ny + 1) * nx;
+  const int fx = j * (nx + 1) + i, fy = j * nx + i;
+  c.w = load_par(s.fpx, c.nfx, fx);
+  c.e = load_par(s.fpx, c.nfx, fx + 1);
+  c.so = load_par(s.fpy, c.nfy, fy);
+  c.no = load_par(s.fpy, c.nfy, fy + nx);
+  c.bx = fx;
+  c.by = fy;
+  return c;
+}
+// raw face values of velocity k: W, E, S, N
+__device__ __forceinline__ void face_vals(const GDevStep& s, const FaceCtx& c, int k, float (&f)[4]) {
+  const size_t bx = (size_t)k * c.nfx + c.bx, by = (size_t)k * c.nfy + c.by;
+  f[0] = __ldg(s.fbx + bx);
+  f[1] = __ldg(s.fbx + bx + 1);
+  f[2] = __ldg(s.fby + by);
+  f[3] = __ldg(s.fby + by + c.nx);
+}
+__device__ __forceinline__ float flux(const GDevStep& s, const FaceCtx& c, int k,
+                                      const float (&f)[4], float alpha, float beta) {
+  const float* vf = s.vf;
+  const int nv = s.p.nv;
+  const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k), w = vt(vf, nv, GV_W, k);
+  const float dxf = fmaf(alpha, f[1] - f[0], beta * (feq_dev(c.e, cx, cy, w) - feq_dev(c.w, cx, cy, w)));
+  const float dyf = fmaf(alpha, f[3] - f[2], beta * (feq_dev(c.no, cx, cy, w) - feq_dev(c.so, cx, cy, w)));
+  return -fmaf(vt(vf, nv, GV_KX, k), dxf, vt(vf, nv, GV_KY, k) * dyf);
 }
 
 // f~(t') = 5/4 g1 - 1/4 f^ + dt/3 L*,  acc = 1/4 f^ + 3/4 g1 + 3dt/7 L*
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gupdate1(DevParams p, const float* __restrict__ vf, const T* __restrict__ fhat,
-           const T* __restrict__ g1, const float* __restrict__ fbx,
-           const float* __restrict__ fby, T* __restrict__ ftp, T* __restrict__ acc, float dt3,
-           float dt37) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)p.nv * p.N) return;
-  const int k = (int)(t / p.N);
-  const int cell = (int)(t - (size_t)k * p.N);
+k_gupdate1(GDevStep s, float alpha, float beta, float dt3, float dt37) {
+  const DevParams& p = s.p;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= p.N) return;
   const int j = cell / p.nx, i = cell - j * p.nx;
-  const float L = lflux(p, vf, fbx, fby, k, i, j);
-  const float fh = ldv(fhat + t), g = ldv(g1 + t);
-  stv(ftp + t, fmaf(1.25f, g, fmaf(-0.25f, fh, dt3 * L)));
-  stv(acc + t, fmaf(0.25f, fh, fmaf(0.75f, g, dt37 * L)));
+  const FaceCtx c = face_ctx(s, i, j);
+  const int kb = blockIdx.y * KB;
+  float fh[KB], gg[KB], fv[KB][4];
+#pragma unroll
+  for (int u = 0; u < KB; ++u) {
+    const int k = kb + u;
+    if (k < p.nv) {
+      fh[u] = ldv((const T*)s.fhat + (size_t)k * p.N + cell);
+      gg[u] = ldv((const T*)s.g + gp_at(s, k, i, j));
+      face_vals(s, c, k, fv[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < KB; ++u) {
+    const int k = kb + u;
+    if (k < p.nv) {
+      const float L = flux(s, c, k, fv[u], alpha, beta);
+      const size_t t = (size_t)k * p.N + cell;
+      stv((T*)s.ftp + t, fmaf(1.25f, gg[u], fmaf(-0.25f, fh[u], dt3 * L)));
+      stv((T*)s.acc + t, fmaf(0.25f, fh[u], fmaf(0.75f, gg[u], dt37 * L)));
+    }
+  }
 }
 
 // f^^{n+1} = acc + 3/4 dt Omega' + 4dt/7 L**,  dt Omega' = c_om (f~' - feq')
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gupdate2(DevParams p, const float* __restrict__ vf, const T* __restrict__ ftp,
-           const T* __restrict__ acc, const float* __restrict__ eqp,
-           const float* __restrict__ fbx, const float* __restrict__ fby, T* __restrict__ fhat,
-           float c_om34, float dt47) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)p.nv * p.N) return;
-  const int k = (int)(t / p.N);
-  const int cell = (int)(t - (size_t)k * p.N);
+k_gupdate2(GDevStep s, float alpha, float beta, float c_om34, float dt47) {
+  const DevParams& p = s.p;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= p.N) return;
   const int j = cell / p.nx, i = cell - j * p.nx;
-  const float L = lflux(p, vf, fbx, fby, k, i, j);
-  EqF q;
-  q.vx = __ldg(eqp + cell);
-  q.vy = __ldg(eqp + p.N + cell);
-  q.bm1 = __ldg(eqp + 2 * p.N + cell);
-  q.r = __ldg(eqp + 3 * p.N + cell);
-  q.dr = __ldg(eqp + 4 * p.N + cell);
-  const float fe =
-      feq_dev(q, vt(vf, p.nv, GV_XH, k), vt(vf, p.nv, GV_YH, k), vt(vf, p.nv, GV_W, k));
-  stv(fhat + t, fmaf(dt47, L, fmaf(c_om34, ldv(ftp + t) - fe, ldv(acc + t))));
+  const FaceCtx c = face_ctx(s, i, j);
+  const EqF q = load_par(s.eqp, p.N, cell);
+  const int kb = blockIdx.y * KB;
+  float ft[KB], ac[KB], fv[KB][4];
+#pragma unroll
+  for (int u = 0; u < KB; ++u) {
+    const int k = kb + u;
+    if (k < p.nv) {
+      const size_t t = (size_t)k * p.N + cell;
+      ft[u] = ldv((const T*)s.ftp + t);
+      ac[u] = ldv((const T*)s.acc + t);
+      face_vals(s, c, k, fv[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < KB; ++u) {
+    const int k = kb + u;
+    if (k < p.nv) {
+      const float L = flux(s, c, k, fv[u], alpha, beta);
+      const float fe = feq_dev(q, vt(s.vf, p.nv, GV_XH, k), vt(s.vf, p.nv, GV_YH, k),
+                               vt(s.vf, p.nv, GV_W, k));
+      stv((T*)s.fhat + (size_t)k * p.N + cell, fmaf(dt47, L, fmaf(c_om34, ft[u] - fe, ac[u])));
+    }
+  }
 }
-
-unsigned nblk(size_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
 
 template <typename T>
 cudaError_t cell_t(const GDevStep& s, const void* src, const StageCoef& c, cudaStream_t st) {
   const DevParams& p = s.p;
   if (p.nv > 32) {
-    constexpr int G = 8, TX = kThreads / G;
-    k_gcell<T, G><<<(p.N + TX - 1) / TX, dim3(TX, G), 0, st>>>(
-        p, s.ref, s.vf, (const T*)src, (T*)s.g, s.mom, s.eqp, (float)c.a, (float)c.b);
+    constexpr int G = 16, TX = kThreads / G;
+    k_gcell<T, G><<<(p.N + TX - 1) / TX, dim3(TX, G), 0, st>>>(s, (const T*)src, (float)c.a,
+                                                              (float)c.b);
   } else {
     k_gcell<T, 1><<<(p.N + kThreads - 1) / kThreads, dim3(kThreads, 1), 0, st>>>(
-        p, s.ref, s.vf, (const T*)src, (T*)s.g, s.mom, s.eqp, (float)c.a, (float)c.b);
+        s, (const T*)src, (float)c.a, (float)c.b);
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int per = 4 * (p.nx + 4) + 4 * p.ny;
+  k_gghost<T><<<dim3((per + kThreads - 1) / kThreads, p.nv), kThreads, 0, st>>>(s);
   return cudaGetLastError();
 }
 
@@ -598,31 +777,30 @@ template <typename T, int DIR>
 cudaError_t faces_t(const GDevStep& s, const StageCoef& c, cudaStream_t st) {
   const DevParams& p = s.p;
   float* fb = DIR == 0 ? s.fbx : s.fby;
+  float* fpar = DIR == 0 ? s.fpx : s.fpy;
   const int nch = DIR == 0 ? s.nchx : s.nchy;
   const int kchunk = (p.nv + nch - 1) / nch;
   const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
   const dim3 grid(DIR == 0 ? (p.nx + 1 + LANES - 1) / LANES : (p.nx + LANES - 1) / LANES,
                   DIR == 0 ? (p.ny + R - 1) / R : (p.ny + 1 + R - 1) / R, nch);
-  k_gfaces1<T, DIR><<<grid, LANES * NW, 0, st>>>(p, s.vf, (const T*)s.g, fb, s.part, (float)c.h,
-                                                kchunk);
+  k_gfaces1<T, DIR><<<grid, LANES * NW, 0, st>>>(s, fb, (float)c.h, kchunk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  // velocity groups of pass 2: each thread forms its face equilibrium once
-  // and serves about nv / gy velocities
-  const int gy = p.nv < 128 ? (p.nv + 7) / 8 : 16;
-  const dim3 g2((nf + 255) / 256, gy);
-  k_gfaces2<DIR><<<g2, 256, 0, st>>>(p, s.ref, s.vf, fb, s.part, nch, (float)c.alpha,
-                                     (float)c.beta);
+  k_gfacepar<DIR><<<(nf + 255) / 256, 256, 0, st>>>(s, fpar, nch);
   e = cudaGetLastError();
   if (e != cudaSuccess || (DIR == 0 ? p.px : p.py)) return e;
   const int nw = 2 * (DIR == 0 ? p.ny : p.nx);
   const int threads = p.nv >= kThreads ? kThreads : ((p.nv + 31) / 32) * 32;
-  k_gwall<T, DIR><<<nw, threads, 0, st>>>(p, s.ref, s.vf, (const T*)s.g, s.mom, fb, (float)c.h,
-                                          (float)c.alpha, (float)c.beta);
+  k_gwall<T, DIR><<<nw, threads, 0, st>>>(s, fb, fpar, (float)c.h);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+// Padded g layout: the row pitch leaves a whole 16-byte chunk (8 BF16 /
+// 4 FP32 elements) past the last ghost column nx + 1 and is a multiple of 8
+// elements, so every chunk the face kernels copy is aligned and in bounds.
+int gdev_pitch(int nx) { return ((nx + 10 + 7) / 8) * 8; }
 
 // Velocity chunks of the interior-face pass 1: the grid of (face columns x
 // face rows x chunks) blocks is sized to fill whole waves of resident blocks
@@ -669,27 +847,17 @@ cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_
 
 cudaError_t launch_gdev_update(const GDevStep& s, int stage, cudaStream_t st) {
   const DevParams& p = s.p;
-  const size_t n = (size_t)p.nv * p.N;
+  const dim3 grid((p.N + kThreads - 1) / kThreads, (p.nv + KB - 1) / KB);
+  const StageCoef& c = stage == 1 ? s.s1 : s.s2;
+  const float al = (float)c.alpha, be = (float)c.beta;
   if (stage == 1) {
     const float dt3 = (float)(p.dt / 3.0), dt37 = (float)(3.0 * p.dt / 7.0);
-    if (s.store == 1)
-      k_gupdate1<float><<<nblk(n), kThreads, 0, st>>>(p, s.vf, (const float*)s.fhat,
-                                                      (const float*)s.g, s.fbx, s.fby,
-                                                      (float*)s.ftp, (float*)s.acc, dt3, dt37);
-    else
-      k_gupdate1<__nv_bfloat16><<<nblk(n), kThreads, 0, st>>>(
-          p, s.vf, (const __nv_bfloat16*)s.fhat, (const __nv_bfloat16*)s.g, s.fbx, s.fby,
-          (__nv_bfloat16*)s.ftp, (__nv_bfloat16*)s.acc, dt3, dt37);
+    if (s.store == 1) k_gupdate1<float><<<grid, kThreads, 0, st>>>(s, al, be, dt3, dt37);
+    else k_gupdate1<__nv_bfloat16><<<grid, kThreads, 0, st>>>(s, al, be, dt3, dt37);
   } else {
     const float c34 = (float)(0.75 * s.c_om), dt47 = (float)(4.0 * p.dt / 7.0);
-    if (s.store == 1)
-      k_gupdate2<float><<<nblk(n), kThreads, 0, st>>>(p, s.vf, (const float*)s.ftp,
-                                                      (const float*)s.acc, s.eqp, s.fbx, s.fby,
-                                                      (float*)s.fhat, c34, dt47);
-    else
-      k_gupdate2<__nv_bfloat16><<<nblk(n), kThreads, 0, st>>>(
-          p, s.vf, (const __nv_bfloat16*)s.ftp, (const __nv_bfloat16*)s.acc, s.eqp, s.fbx,
-          s.fby, (__nv_bfloat16*)s.fhat, c34, dt47);
+    if (s.store == 1) k_gupdate2<float><<<grid, kThreads, 0, st>>>(s, al, be, c34, dt47);
+    else k_gupdate2<__nv_bfloat16><<<grid, kThreads, 0, st>>>(s, al, be, c34, dt47);
   }
   return cudaGetLastError();
 }

@@ -128,8 +128,10 @@ cudaError_t d2q9m_prepare();
 
 // Deviation-storage form of the generic path (dugks_generic_mixed.cu), any
 // velocity set.  fhat/g/ftp/acc hold typed deviations d = f - W rho0 (store
-// 1 = FP32, 2 = BF16), fbx/fby FP32 face deviations, mom FP64 (rho, ux, uy)
-// of the last cell pass, eqp [5][N] its FP32 equilibrium parameters.
+// 1 = FP32, 2 = BF16), fbx/fby FP32 face deviations of f-bar with the face
+// equilibrium parameters in fpx/fpy (the update forms f = alpha f-bar +
+// beta feq), mom FP64 (rho, ux, uy) of the last cell pass, eqp [5][N] its
+// FP32 equilibrium parameters.
 struct GDevRef {
   double rho0, W, Wx, Wy;       // rho0, rho0 sum W_k, rho0 sum W_k xi_x, rho0 sum W_k xi_y
 };
@@ -143,12 +145,17 @@ struct GDevStep {
   int store;
   StageCoef s1, s2;
   double c_om;
-  void *fhat, *g, *ftp, *acc;
-  float *fbx, *fby, *eqp;
+  void *fhat, *ftp, *acc;       // [nv][ny][nx]
+  void* g;                      // stage field, padded: [nv][ny + 4][pitch], cell (i, j) at (j+2, i+2)
+  int pitch;                    // gdev_pitch(nx)
+  size_t plane;                 // (ny + 4) * pitch
+  float *fbx, *fby, *eqp;       // faces hold f-bar; eqp [5][N]
+  float *fpx, *fpy;             // face assembly parameters [5][nf] of x / y faces
   const float* vf;
   double *mom, *part;           // part: [nch][3][nf] partial face moments
   int nchx, nchy;
 };
+int gdev_pitch(int nx);
 int gdev_chunks(const DevParams& p, int dir, int sms);
 cudaError_t launch_gdev_cell(const GDevStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_t st);
