@@ -36,7 +36,8 @@ const char* kNames[K_NUM] = {
     "moments",     "set_equilibrium", "check",
     "d2q9_prologue", "d2q9_stage1", "d2q9_stage2",
     "d2q9m_stage1", "d2q9m_stage2", "convert",
-    "gdev_cell", "gdev_face_x", "gdev_face_y", "gdev_update_stage1", "gdev_update_stage2"};
+    "gdev_cell", "gdev_face_x", "gdev_face_y", "gdev_walls", "gdev_update_stage1",
+    "gdev_update_stage2"};
 
 struct Pending {
   int id;
@@ -350,6 +351,7 @@ int one_step_gdev(dugks_ctx* c) {
     TRY(launch(c, K_GDEV_CELL, [&] { return launch_gdev_cell(g, stage, s); }));
     TRY(launch(c, K_GDEV_FACE_X, [&] { return launch_gdev_faces(g, stage, 0, s); }));
     TRY(launch(c, K_GDEV_FACE_Y, [&] { return launch_gdev_faces(g, stage, 1, s); }));
+    TRY(launch(c, K_GDEV_WALLS, [&] { return launch_gdev_walls(g, stage, s); }));
     TRY(launch(c, stage == 1 ? K_GDEV_UPDATE1 : K_GDEV_UPDATE2,
                [&] { return launch_gdev_update(g, stage, s); }));
   }
@@ -656,6 +658,16 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
       g.ref.Wx += c->rho0 * vel->w[k] * vel->xi_x[k];
       g.ref.Wy += c->rho0 * vel->w[k] * vel->xi_y[k];
     }
+    for (int sd = 0; sd < 4; ++sd) {     // outgoing flux of the reference state per wall
+      const double nxs = sd == DUGKS_WEST ? -1.0 : sd == DUGKS_EAST ? 1.0 : 0.0;
+      const double nys = sd == DUGKS_SOUTH ? -1.0 : sd == DUGKS_NORTH ? 1.0 : 0.0;
+      double o = 0.0;
+      for (int k = 0; k < nv; ++k) {
+        const double xn = vel->xi_x[k] * nxs + vel->xi_y[k] * nys;
+        if (xn > 0.0) o += xn * vel->w[k];
+      }
+      g.ds_out[sd] = c->rho0 * o;
+    }
     g.s1 = c->s1;
     g.s2 = c->s2;
     g.c_om = c->c_om;
@@ -673,9 +685,11 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     if (e == cudaSuccess) e = cudaMalloc(&c->gpad, g.plane * nv * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->eqp, 5 * (size_t)p.N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->fpar, 5 * 2 * nfmax * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->vf, (size_t)GV_N * nv * sizeof(float));
+    // FP32 tables, then (16-byte aligned) the packed float4 rows
+    const size_t off4 = (((size_t)GV_N * nv + 3) / 4) * 4;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->vf, (off4 + 8 * (size_t)nv) * sizeof(float));
     if (e == cudaSuccess) {
-      std::vector<float> t((size_t)GV_N * nv);
+      std::vector<float> t(off4 + 8 * (size_t)nv, 0.f);
       for (int k = 0; k < nv; ++k) {
         const double x = vel->xi_x[k], y = vel->xi_y[k];
         const float xh = (float)x, yh = (float)y;
@@ -686,6 +700,15 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
         t[GV_W * nv + k] = (float)vel->w[k];
         t[GV_KX * nv + k] = (float)(x / mesh->dx);
         t[GV_KY * nv + k] = (float)(y / mesh->dy);
+        float* q = t.data() + off4;
+        q[4 * k + 0] = xh;
+        q[4 * k + 1] = t[GV_XL * nv + k];
+        q[4 * k + 2] = yh;
+        q[4 * k + 3] = t[GV_YL * nv + k];
+        q[4 * ((size_t)nv + k) + 0] = xh;
+        q[4 * ((size_t)nv + k) + 1] = yh;
+        q[4 * ((size_t)nv + k) + 2] = (float)vel->w[k];
+        q[4 * ((size_t)nv + k) + 3] = 0.f;
       }
       e = cudaMemcpy(c->vf, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
@@ -706,6 +729,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     g.fpx = c->fpar;
     g.fpy = c->fpar + 5 * nfmax;
     g.vf = c->vf;
+    g.vq = reinterpret_cast<const float4*>(c->vf + off4);
     g.mom = c->mom;
     g.part = c->part;
     c->store = storage;

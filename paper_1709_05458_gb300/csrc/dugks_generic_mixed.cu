@@ -53,6 +53,12 @@ template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16* p,
   *p = __float2bfloat16_rn(v);
 }
 
+// raw loads (no conversion), so a batch of loads is issued before the
+// first value is used; tof converts afterwards
+template <typename T> __device__ __forceinline__ T ldr(const T* p) { return __ldg(p); }
+__device__ __forceinline__ float tof(float v) { return v; }
+__device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
+
 // asynchronous 16-byte global -> shared copy (bypassing L1) and its groups
 __device__ __forceinline__ void cp16(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -199,22 +205,25 @@ k_gcell(GDevStep s, const T* __restrict__ src, float a, float b) {
   if (valid) {
     int k = ty;
     for (; k + (U - 1) * G < nv; k += U * G) {
-      float d[U];
+      T d[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) d[u] = ldv(src + (size_t)(k + u * G) * p.N + cell);
+      for (int u = 0; u < U; ++u) d[u] = ldr(src + (size_t)(k + u * G) * p.N + cell);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int kk = k + u * G;
-        acc_add(s0, d[u]);
-        acc_addprod(s1, vt(vf, nv, GV_XH, kk), vt(vf, nv, GV_XL, kk), d[u]);
-        acc_addprod(s2, vt(vf, nv, GV_YH, kk), vt(vf, nv, GV_YL, kk), d[u]);
+        const float4 xq = __ldg(s.vq + kk);
+        const float du = tof(d[u]);
+        acc_add(s0, du);
+        acc_addprod(s1, xq.x, xq.y, du);
+        acc_addprod(s2, xq.z, xq.w, du);
       }
     }
     for (; k < nv; k += G) {
       const float d = ldv(src + (size_t)k * p.N + cell);
+      const float4 xq = __ldg(s.vq + k);
       acc_add(s0, d);
-      acc_addprod(s1, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_XL, k), d);
-      acc_addprod(s2, vt(vf, nv, GV_YH, k), vt(vf, nv, GV_YL, k), d);
+      acc_addprod(s1, xq.x, xq.y, d);
+      acc_addprod(s2, xq.z, xq.w, d);
     }
   }
   double v[3] = {acc_value(s0), acc_value(s1), acc_value(s2)};
@@ -253,19 +262,20 @@ k_gcell(GDevStep s, const T* __restrict__ src, float a, float b) {
   const int j = cell / p.nx, i = cell - j * p.nx;
   int k = ty;
   for (; k + 3 * G < nv; k += 4 * G) {
-    float d[4];
+    T d[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) d[u] = ldv(src + (size_t)(k + u * G) * p.N + cell);
+    for (int u = 0; u < 4; ++u) d[u] = ldr(src + (size_t)(k + u * G) * p.N + cell);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int kk = k + u * G;
-      const float fe =
-          feq_dev(q, vt(vf, nv, GV_XH, kk), vt(vf, nv, GV_YH, kk), vt(vf, nv, GV_W, kk));
-      stv(g + gp_at(s, kk, i, j), fmaf(b, fe, a * d[u]));
+      const float4 e4 = __ldg(s.vq + nv + kk);
+      const float fe = feq_dev(q, e4.x, e4.y, e4.z);
+      stv(g + gp_at(s, kk, i, j), fmaf(b, fe, a * tof(d[u])));
     }
   }
   for (; k < nv; k += G) {
-    const float fe = feq_dev(q, vt(vf, nv, GV_XH, k), vt(vf, nv, GV_YH, k), vt(vf, nv, GV_W, k));
+    const float4 e4 = __ldg(s.vq + nv + k);
+    const float fe = feq_dev(q, e4.x, e4.y, e4.z);
     stv(g + gp_at(s, k, i, j), fmaf(b, fe, a * ldv(src + (size_t)k * p.N + cell)));
   }
 }
@@ -362,7 +372,6 @@ k_gfaces1(GDevStep s, float* __restrict__ fb, float h, int kchunk) {
     return smem[((w * R + r) * LANES + l) * 3 + m];
   };
   const DevParams& p = s.p;
-  const float* __restrict__ vf = s.vf;
   const T* __restrict__ g = (const T*)s.g;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nx = p.nx, ny = p.ny, nv = p.nv;
@@ -409,51 +418,62 @@ k_gfaces1(GDevStep s, float* __restrict__ fb, float h, int kchunk) {
   for (int k = k0 + warp; k < k1; k += NW) {
     if (k + NW < k1) issue(k + NW, b ^ 1);
     cp_commit();
-    const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k);
-    const float cxl = vt(vf, nv, GV_XL, k), cyl = vt(vf, nv, GV_YL, k);
+    const float4 xq = __ldg(s.vq + k);             // xi_x hi, lo, xi_y hi, lo
+    const float cx = xq.x, cxl = xq.y, cy = xq.z, cyl = xq.w;
     const float cn = DIR == 0 ? cx : cy;
-    float TL[9], TU[9];
-    const bool lo = cn >= 0.f, hi = cn <= 0.f;     // uniform across the warp
-    if (DIR == 0) {
-      const float bb = -cy * h * idy;
-      if (lo) taylor9f((0.5f * dx - cx * h) * idx_, bb, TL);
-      if (hi) taylor9f((-0.5f * dx - cx * h) * idx_, bb, TU);
-    } else {
-      const float aa = -cx * h * idx_;
-      if (lo) taylor9f(aa, (0.5f * dy - cy * h) * idy, TL);
-      if (hi) taylor9f(aa, (-0.5f * dy - cy * h) * idy, TU);
-    }
+    // the upwind cell is the lower one (slab offset 0) for xi.n > 0 and the
+    // upper one (one column / row on) for xi.n < 0; xi.n = 0 averages both
+    // (uniform across the warp)
+    const bool up = cn < 0.f, tie = cn == 0.f;
+    const float sh = up ? -0.5f : 0.5f;
+    float Tw[9];
+    if (DIR == 0) taylor9f((sh * dx - cx * h) * idx_, -cy * h * idy, Tw);
+    else taylor9f(-cx * h * idx_, (sh * dy - cy * h) * idy, Tw);
     cp_wait1();                                    // this velocity's slab has landed
     __syncwarp();
-    const T* sl = slab + b * S::ELEMS;
+    // x faces: rows r..r+2 (cells j-1..j+1), columns lane+q (cells fi-2+q);
+    // y faces: rows r+q (cells fj-2+q), columns lane+1+q (cells i-1+q)
+    const T* sl = slab + b * S::ELEMS + lane + (DIR == 0 ? 0 : 1);
+    const int uoff = DIR == 0 ? 1 : SW;            // lower -> upper cell
     float* fbk = fb + (size_t)k * nf;
+    if (!tie) {
+      const T* sb = sl + (up ? uoff : 0);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      if (!ok[r]) continue;
-      // x faces: rows r..r+2 (cells j-1..j+1), columns lane+q (cells fi-2+q);
-      // y faces: rows r+q (cells fj-2+q), columns lane+1+q (cells i-1+q)
-      const T* s0 = sl + r * SW + lane + (DIR == 0 ? 0 : 1);
-      float vl = 0.f, vu = 0.f;
-      if (lo) {
+      for (int r = 0; r < R; ++r) {
+        const T* s0 = sb + r * SW;
+        float v = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int q = 0; q < 3; ++q) vl = fmaf(TL[a * 3 + q], lds(s0 + a * SW + q), vl);
+          for (int q = 0; q < 3; ++q) v = fmaf(Tw[a * 3 + q], lds(s0 + a * SW + q), v);
+        const int face = DIR == 0 ? (r0 + r) * (nx + 1) + col : (r0 + r) * nx + col;
+        if (ok[r]) fbk[face] = v;
+        acc_add(acc[r][0], v);                     // rows without a face are never stored
+        acc_addprod(acc[r][1], cx, cxl, v);
+        acc_addprod(acc[r][2], cy, cyl, v);
       }
-      if (hi) {
+    } else {
+      float Tu[9];
+      if (DIR == 0) taylor9f((-0.5f * dx - cx * h) * idx_, -cy * h * idy, Tu);
+      else taylor9f(-cx * h * idx_, (-0.5f * dy - cy * h) * idy, Tu);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const T* s0 = sl + r * SW;
+        float vl = 0.f, vu = 0.f;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int q = 0; q < 3; ++q)
-            vu = fmaf(TU[a * 3 + q], lds(DIR == 0 ? s0 + a * SW + q + 1 : s0 + (a + 1) * SW + q),
-                      vu);
+          for (int q = 0; q < 3; ++q) {
+            vl = fmaf(Tw[a * 3 + q], lds(s0 + a * SW + q), vl);
+            vu = fmaf(Tu[a * 3 + q], lds(s0 + uoff + a * SW + q), vu);
+          }
+        const float v = 0.5f * (vl + vu);
+        const int face = DIR == 0 ? (r0 + r) * (nx + 1) + col : (r0 + r) * nx + col;
+        if (ok[r]) fbk[face] = v;
+        acc_add(acc[r][0], v);
+        acc_addprod(acc[r][1], cx, cxl, v);
+        acc_addprod(acc[r][2], cy, cyl, v);
       }
-      const float v = (lo && hi) ? 0.5f * (vl + vu) : (lo ? vl : vu);
-      const int face = DIR == 0 ? (r0 + r) * (nx + 1) + col : (r0 + r) * nx + col;
-      fbk[face] = v;
-      acc_add(acc[r][0], v);
-      acc_addprod(acc[r][1], cx, cxl, v);
-      acc_addprod(acc[r][2], cy, cyl, v);
     }
     __syncwarp();                                  // buffer b is refilled two velocities on
     b ^= 1;
@@ -527,12 +547,13 @@ k_gfacepar(GDevStep s, float* __restrict__ fpar, int nchunk) {
 }
 
 // -------------------------------------------------------------- wall faces
-// One wall face per block, the threads over the velocity set: fluid-side
-// reconstruction (velocities leaving the fluid or along the wall), the wall
-// rule of Sec. 2.3 for velocities entering the fluid (bounce-back with the
-// moving-wall term, or diffuse scattering with the density that balances
-// the outgoing flux), f-bar into fb, the face moments (FP64, few terms per
-// thread) and the face's assembly parameters into fpar.  Faces:
+// One wall face per block (both directions in one launch), the threads over
+// the velocity set: fluid-side reconstruction (velocities leaving the fluid
+// or along the wall), the wall rule of Sec. 2.3 for velocities entering the
+// fluid (bounce-back with the moving-wall term, or diffuse scattering with
+// the density that balances the outgoing flux), f-bar into fb, the face
+// moments (compensated FP32 partials per thread, FP64 across the block) and
+// the face's assembly parameters into fpar.  Per direction, face
 // id = 2 line + (0: W/S wall, 1: E/N).
 template <typename T>
 __device__ __forceinline__ float taylor_at(const GDevStep& s, const T* __restrict__ g, int k,
@@ -549,16 +570,14 @@ __device__ __forceinline__ float taylor_at(const GDevStep& s, const T* __restric
 }
 
 template <typename T, int DIR>
-__global__ void __launch_bounds__(kThreads)
-k_gwall(GDevStep s, float* __restrict__ fb, float* __restrict__ fpar, float h) {
-  __shared__ double sm[32 * 4];
+__device__ __forceinline__ void wall_face(const GDevStep& s, int id, float h, double* sm) {
   const DevParams& p = s.p;
   const GDevRef& ref = s.ref;
-  const float* __restrict__ vf = s.vf;
   const T* __restrict__ g = (const T*)s.g;
+  float* __restrict__ fb = DIR == 0 ? s.fbx : s.fby;
+  float* __restrict__ fpar = DIR == 0 ? s.fpx : s.fpy;
   const int nx = p.nx, ny = p.ny, nv = p.nv;
   const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
-  const int id = blockIdx.x;
   const bool upper_wall = id & 1;                 // east / north
   const int line = id >> 1;
   const int face = DIR == 0 ? line * (nx + 1) + (upper_wall ? nx : 0)
@@ -577,53 +596,57 @@ k_gwall(GDevStep s, float* __restrict__ fb, float* __restrict__ fpar, float h) {
   const float uwx = (float)p.uw_x[side], uwy = (float)p.uw_y[side];
   const float irt = (float)p.inv_RT;
   auto recon = [&](int k) {
-    const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k);
-    const float X = DIR == 0 ? off - cx * h : -cx * h;
-    const float Y = DIR == 0 ? -cy * h : off - cy * h;
+    const float4 e4 = __ldg(s.vq + nv + k);
+    const float X = DIR == 0 ? off - e4.x * h : -e4.x * h;
+    const float Y = DIR == 0 ? -e4.y * h : off - e4.y * h;
     return taylor_at(s, g, k, ci, cj, X, Y);
   };
-  double v[4] = {0.0, 0.0, 0.0, 0.0};            // moments of f-bar, diffuse numerator
+  // moments of f-bar (deviations) and the outgoing flux sum(xi.n f-bar_dev)
+  Acc a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
   for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-    const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k);
+    const float4 xq = __ldg(s.vq + k);
+    const float cx = xq.x, cy = xq.z;
     const float xn = nsg * (DIR == 0 ? cx : cy);
     float fbar;
     if (xn >= 0.f) {                               // hits the wall or runs along it
       fbar = recon(k);
-      if (xn > 0.f) {
-        const double xnd = (double)nsg * (DIR == 0 ? __ldg(p.xi_x + k) : __ldg(p.xi_y + k));
-        v[3] = fma(xnd, f2d(fbar) + __ldg(p.w + k) * ref.rho0, v[3]);
-      }
+      if (xn > 0.f)
+        acc_addprod(a3, DIR == 0 ? nsg * xq.x : nsg * xq.z, DIR == 0 ? nsg * xq.y : nsg * xq.w,
+                    fbar);
     } else if (kind == BC_BOUNCEBACK) {
       const int kk = __ldg(p.opp + k);
-      const float wk = vt(vf, nv, GV_W, k);
+      const float wk = __ldg(s.vq + nv + k).z;
       const float bbk = 2.f * wk * fmaf(cx, uwx, cy * uwy) * irt;
-      const float shift = (vt(vf, nv, GV_W, kk) - wk) * (float)ref.rho0;
+      const float shift = (__ldg(s.vq + nv + kk).z - wk) * (float)ref.rho0;
       fbar = fmaf(rho_w, bbk, recon(kk) + shift);
     } else {
       continue;                                    // diffuse: after the reduction
     }
     fb[(size_t)k * nf + face] = fbar;
-    const double fd = f2d(fbar);
-    v[0] += fd;
-    v[1] = fma(__ldg(p.xi_x + k), fd, v[1]);
-    v[2] = fma(__ldg(p.xi_y + k), fd, v[2]);
+    acc_add(a0, fbar);
+    acc_addprod(a1, xq.x, xq.y, fbar);
+    acc_addprod(a2, xq.z, xq.w, fbar);
   }
+  double v[4] = {acc_value(a0), acc_value(a1), acc_value(a2), acc_value(a3)};
   block_sum<4>(v, sm);
   if (kind == BC_DIFFUSE) {                        // uniform over the block
-    double w2[3] = {0.0, 0.0, 0.0};
-    const double rho_ds = v[3] / p.ds_den[side];
+    // rho_ds: the outgoing flux of f = W rho0 + d over the wall's flux
+    // normaliser (Sec. 2.3 diffuse scattering)
+    const double rho_ds = (s.ds_out[side] + v[3]) / p.ds_den[side];
+    Acc b0{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f};
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-      const float xn = nsg * (DIR == 0 ? vt(vf, nv, GV_XH, k) : vt(vf, nv, GV_YH, k));
+      const float4 xq = __ldg(s.vq + k);
+      const float xn = nsg * (DIR == 0 ? xq.x : xq.z);
       if (xn < 0.f) {
         const float fbar =
             d2f(fma(rho_ds, __ldg(p.feq_wall + side * nv + k), -__ldg(p.w + k) * ref.rho0));
         fb[(size_t)k * nf + face] = fbar;
-        const double fd = f2d(fbar);
-        w2[0] += fd;
-        w2[1] = fma(__ldg(p.xi_x + k), fd, w2[1]);
-        w2[2] = fma(__ldg(p.xi_y + k), fd, w2[2]);
+        acc_add(b0, fbar);
+        acc_addprod(b1, xq.x, xq.y, fbar);
+        acc_addprod(b2, xq.z, xq.w, fbar);
       }
     }
+    double w2[3] = {acc_value(b0), acc_value(b1), acc_value(b2)};
     block_sum<3>(w2, sm);
     v[0] += w2[0];
     v[1] += w2[1];
@@ -637,6 +660,15 @@ k_gwall(GDevStep s, float* __restrict__ fb, float* __restrict__ fpar, float h) {
     fpar[3 * nf + face] = q.r;
     fpar[4 * nf + face] = q.dr;
   }
+}
+
+// blocks [0, nwx): x-direction walls (W/E), then y-direction walls (S/N)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gwalls(GDevStep s, float h, int nwx) {
+  __shared__ double sm[32 * 4];
+  if ((int)blockIdx.x < nwx) wall_face<T, 0>(s, blockIdx.x, h, sm);
+  else wall_face<T, 1>(s, blockIdx.x - nwx, h, sm);
 }
 
 // ---------------------------------------------------------------- updates
@@ -683,7 +715,8 @@ __device__ __forceinline__ float flux(const GDevStep& s, const FaceCtx& c, int k
                                       const float (&f)[4], float alpha, float beta) {
   const float* vf = s.vf;
   const int nv = s.p.nv;
-  const float cx = vt(vf, nv, GV_XH, k), cy = vt(vf, nv, GV_YH, k), w = vt(vf, nv, GV_W, k);
+  const float4 e4 = __ldg(s.vq + nv + k);
+  const float cx = e4.x, cy = e4.y, w = e4.z;
   const float dxf = fmaf(alpha, f[1] - f[0], beta * (feq_dev(c.e, cx, cy, w) - feq_dev(c.w, cx, cy, w)));
   const float dyf = fmaf(alpha, f[3] - f[2], beta * (feq_dev(c.no, cx, cy, w) - feq_dev(c.so, cx, cy, w)));
   return -fmaf(vt(vf, nv, GV_KX, k), dxf, vt(vf, nv, GV_KY, k) * dyf);
@@ -699,13 +732,14 @@ k_gupdate1(GDevStep s, float alpha, float beta, float dt3, float dt37) {
   const int j = cell / p.nx, i = cell - j * p.nx;
   const FaceCtx c = face_ctx(s, i, j);
   const int kb = blockIdx.y * KB;
-  float fh[KB], gg[KB], fv[KB][4];
+  T fh[KB], gg[KB];
+  float fv[KB][4];
 #pragma unroll
   for (int u = 0; u < KB; ++u) {
     const int k = kb + u;
     if (k < p.nv) {
-      fh[u] = ldv((const T*)s.fhat + (size_t)k * p.N + cell);
-      gg[u] = ldv((const T*)s.g + gp_at(s, k, i, j));
+      fh[u] = ldr((const T*)s.fhat + (size_t)k * p.N + cell);
+      gg[u] = ldr((const T*)s.g + gp_at(s, k, i, j));
       face_vals(s, c, k, fv[u]);
     }
   }
@@ -715,8 +749,9 @@ k_gupdate1(GDevStep s, float alpha, float beta, float dt3, float dt37) {
     if (k < p.nv) {
       const float L = flux(s, c, k, fv[u], alpha, beta);
       const size_t t = (size_t)k * p.N + cell;
-      stv((T*)s.ftp + t, fmaf(1.25f, gg[u], fmaf(-0.25f, fh[u], dt3 * L)));
-      stv((T*)s.acc + t, fmaf(0.25f, fh[u], fmaf(0.75f, gg[u], dt37 * L)));
+      const float f0 = tof(fh[u]), g0 = tof(gg[u]);
+      stv((T*)s.ftp + t, fmaf(1.25f, g0, fmaf(-0.25f, f0, dt3 * L)));
+      stv((T*)s.acc + t, fmaf(0.25f, f0, fmaf(0.75f, g0, dt37 * L)));
     }
   }
 }
@@ -732,14 +767,15 @@ k_gupdate2(GDevStep s, float alpha, float beta, float c_om34, float dt47) {
   const FaceCtx c = face_ctx(s, i, j);
   const EqF q = load_par(s.eqp, p.N, cell);
   const int kb = blockIdx.y * KB;
-  float ft[KB], ac[KB], fv[KB][4];
+  T ft[KB], ac[KB];
+  float fv[KB][4];
 #pragma unroll
   for (int u = 0; u < KB; ++u) {
     const int k = kb + u;
     if (k < p.nv) {
       const size_t t = (size_t)k * p.N + cell;
-      ft[u] = ldv((const T*)s.ftp + t);
-      ac[u] = ldv((const T*)s.acc + t);
+      ft[u] = ldr((const T*)s.ftp + t);
+      ac[u] = ldr((const T*)s.acc + t);
       face_vals(s, c, k, fv[u]);
     }
   }
@@ -750,7 +786,8 @@ k_gupdate2(GDevStep s, float alpha, float beta, float c_om34, float dt47) {
       const float L = flux(s, c, k, fv[u], alpha, beta);
       const float fe = feq_dev(q, vt(s.vf, p.nv, GV_XH, k), vt(s.vf, p.nv, GV_YH, k),
                                vt(s.vf, p.nv, GV_W, k));
-      stv((T*)s.fhat + (size_t)k * p.N + cell, fmaf(dt47, L, fmaf(c_om34, ft[u] - fe, ac[u])));
+      stv((T*)s.fhat + (size_t)k * p.N + cell,
+          fmaf(dt47, L, fmaf(c_om34, tof(ft[u]) - fe, tof(ac[u]))));
     }
   }
 }
@@ -787,11 +824,6 @@ cudaError_t faces_t(const GDevStep& s, const StageCoef& c, cudaStream_t st) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_gfacepar<DIR><<<(nf + 255) / 256, 256, 0, st>>>(s, fpar, nch);
-  e = cudaGetLastError();
-  if (e != cudaSuccess || (DIR == 0 ? p.px : p.py)) return e;
-  const int nw = 2 * (DIR == 0 ? p.ny : p.nx);
-  const int threads = p.nv >= kThreads ? kThreads : ((p.nv + 31) / 32) * 32;
-  k_gwall<T, DIR><<<nw, threads, 0, st>>>(s, fb, fpar, (float)c.h);
   return cudaGetLastError();
 }
 
@@ -843,6 +875,17 @@ cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_
   if (s.store == 1)
     return dir == 0 ? faces_t<float, 0>(s, c, st) : faces_t<float, 1>(s, c, st);
   return dir == 0 ? faces_t<__nv_bfloat16, 0>(s, c, st) : faces_t<__nv_bfloat16, 1>(s, c, st);
+}
+
+cudaError_t launch_gdev_walls(const GDevStep& s, int stage, cudaStream_t st) {
+  const DevParams& p = s.p;
+  const int nwx = p.px ? 0 : 2 * p.ny, nwy = p.py ? 0 : 2 * p.nx;
+  if (nwx + nwy == 0) return cudaSuccess;
+  const float h = (float)(stage == 1 ? s.s1.h : s.s2.h);
+  const int threads = p.nv >= kThreads ? kThreads : ((p.nv + 31) / 32) * 32;
+  if (s.store == 1) k_gwalls<float><<<nwx + nwy, threads, 0, st>>>(s, h, nwx);
+  else k_gwalls<__nv_bfloat16><<<nwx + nwy, threads, 0, st>>>(s, h, nwx);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gdev_update(const GDevStep& s, int stage, cudaStream_t st) {

@@ -32,8 +32,9 @@ enum KernelId {
   K_D2Q9M_STAGE2,      // deviation-storage D2Q9 path, stage 2
   K_CONVERT,           // FP64 <-> deviation storage
   K_GDEV_CELL,         // deviation-storage generic path: cell pass (both stages)
-  K_GDEV_FACE_X,       // x faces (interior passes + walls, both stages)
+  K_GDEV_FACE_X,       // interior x faces (both stages)
   K_GDEV_FACE_Y,       // y faces
+  K_GDEV_WALLS,        // wall faces of both directions
   K_GDEV_UPDATE1,      // L*, f~(t'), accumulator
   K_GDEV_UPDATE2,      // L**, dt Omega', f^^{n+1}
   K_NUM
@@ -152,13 +153,16 @@ struct GDevStep {
   float *fbx, *fby, *eqp;       // faces hold f-bar; eqp [5][N]
   float *fpx, *fpy;             // face assembly parameters [5][nf] of x / y faces
   const float* vf;
+  const float4* vq;             // [2][nv]: (xh, xl, yh, yl), (xh, yh, W, 0)
   double *mom, *part;           // part: [nch][3][nf] partial face moments
   int nchx, nchy;
+  double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
 };
 int gdev_pitch(int nx);
 int gdev_chunks(const DevParams& p, int dir, int sms);
 cudaError_t launch_gdev_cell(const GDevStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_t st);
+cudaError_t launch_gdev_walls(const GDevStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gdev_update(const GDevStep& s, int stage, cudaStream_t st);
 
 // One instance of a batched D2Q9 FP64 launch (device memory).
