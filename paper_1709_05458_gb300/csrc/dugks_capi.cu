@@ -83,7 +83,7 @@ struct dugks_ctx {
   bool gdev = false;
   GDevStep gs{};
   float* eqp = nullptr;
-  float* vf = nullptr;          // FP32 velocity tables [GV_N][nv]
+  float* vf = nullptr;          // FP32 velocity table (float4 rows [3][nv])
   void* gpad = nullptr;         // padded stage field of that path
   float* fpar = nullptr;        // face equilibrium parameters of that path
   // adjoint (allocated on first use): forward intermediates and adjoint fields
@@ -685,30 +685,27 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     if (e == cudaSuccess) e = cudaMalloc(&c->gpad, g.plane * nv * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->eqp, 5 * (size_t)p.N * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->fpar, 5 * 2 * nfmax * sizeof(float));
-    // FP32 tables, then (16-byte aligned) the packed float4 rows
-    const size_t off4 = (((size_t)GV_N * nv + 3) / 4) * 4;
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->vf, (off4 + 8 * (size_t)nv) * sizeof(float));
+    // FP32 velocity table, float4 rows [3][nv]: (xi_x hi, lo, xi_y hi, lo),
+    // (xi_x, xi_y, W_k, 0), (xi_x/dx, xi_y/dy, 0, 0); hi = xi rounded to
+    // FP32, lo = the FP32 rounding of the remainder
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->vf, 12 * (size_t)nv * sizeof(float));
     if (e == cudaSuccess) {
-      std::vector<float> t(off4 + 8 * (size_t)nv, 0.f);
+      std::vector<float> t(12 * (size_t)nv, 0.f);
       for (int k = 0; k < nv; ++k) {
         const double x = vel->xi_x[k], y = vel->xi_y[k];
         const float xh = (float)x, yh = (float)y;
-        t[GV_XH * nv + k] = xh;
-        t[GV_YH * nv + k] = yh;
-        t[GV_XL * nv + k] = (float)(x - (double)xh);
-        t[GV_YL * nv + k] = (float)(y - (double)yh);
-        t[GV_W * nv + k] = (float)vel->w[k];
-        t[GV_KX * nv + k] = (float)(x / mesh->dx);
-        t[GV_KY * nv + k] = (float)(y / mesh->dy);
-        float* q = t.data() + off4;
-        q[4 * k + 0] = xh;
-        q[4 * k + 1] = t[GV_XL * nv + k];
-        q[4 * k + 2] = yh;
-        q[4 * k + 3] = t[GV_YL * nv + k];
-        q[4 * ((size_t)nv + k) + 0] = xh;
-        q[4 * ((size_t)nv + k) + 1] = yh;
-        q[4 * ((size_t)nv + k) + 2] = (float)vel->w[k];
-        q[4 * ((size_t)nv + k) + 3] = 0.f;
+        float* r0 = t.data() + 4 * (size_t)k;
+        float* r1 = t.data() + 4 * ((size_t)nv + k);
+        float* r2 = t.data() + 4 * (2 * (size_t)nv + k);
+        r0[0] = xh;
+        r0[1] = (float)(x - (double)xh);
+        r0[2] = yh;
+        r0[3] = (float)(y - (double)yh);
+        r1[0] = xh;
+        r1[1] = yh;
+        r1[2] = (float)vel->w[k];
+        r2[0] = (float)(x / mesh->dx);
+        r2[1] = (float)(y / mesh->dy);
       }
       e = cudaMemcpy(c->vf, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
@@ -728,8 +725,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     g.eqp = c->eqp;
     g.fpx = c->fpar;
     g.fpy = c->fpar + 5 * nfmax;
-    g.vf = c->vf;
-    g.vq = reinterpret_cast<const float4*>(c->vf + off4);
+    g.vq = reinterpret_cast<const float4*>(c->vf);
     g.mom = c->mom;
     g.part = c->part;
     c->store = storage;

@@ -119,11 +119,6 @@ __device__ __forceinline__ void acc_addprod(Acc& a, float ah, float al, float x)
 }
 __device__ __forceinline__ double acc_value(const Acc& a) { return f2d(a.hi) + f2d(a.lo); }
 
-// per-velocity FP32 tables, [GV_N][nv]
-__device__ __forceinline__ float vt(const float* vf, int nv, int row, int k) {
-  return __ldg(vf + row * nv + k);
-}
-
 // FP32 equilibrium-assembly parameters of one cell or face
 struct EqF {
   float vx, vy, bm1, r, dr;   // u/RT, -|u|^2/(2RT), rho, rho - rho0
@@ -195,7 +190,6 @@ k_gcell(GDevStep s, const T* __restrict__ src, float a, float b) {
   __shared__ double red[G > 1 ? 3 * G * TX : 1];
   __shared__ float eqs[5][TX];
   const DevParams& p = s.p;
-  const float* __restrict__ vf = s.vf;
   T* __restrict__ g = (T*)s.g;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int cell = blockIdx.x * TX + tx;
@@ -672,122 +666,167 @@ k_gwalls(GDevStep s, float h, int nwx) {
 }
 
 // ---------------------------------------------------------------- updates
-// One thread per cell and KB consecutive velocities: the assembly
-// parameters of the cell and of its four faces are read once; the face
-// values f = alpha f-bar + beta feq (eq. recover2f) are formed here, and
-// L = -(xi_x (f_e - f_w)/dx + xi_y (f_n - f_s)/dy) (eq. microflux).
-constexpr int KB = 8;
+// One thread per cell and KB consecutive velocities (batches of KH loads in
+// flight).  Face values are f = alpha f-bar + beta feq (eq. recover2f) and
+// L = -(xi_x (f_e - f_w)/dx + xi_y (f_n - f_s)/dy) (eq. microflux).  Every
+// equilibrium entering the update -- the four faces' in L, and the cell's
+// in the collision term -- is W_k P(xi_k) with P quadratic in xi:
+// P = (r bm1 + dr) + r (u.xi/RT) + (r/2)(u.xi/RT)^2 from the assembly
+// parameters.  Their combination is W_k S(xi_k) with S a cubic in
+// (xi_x, xi_y), whose ten coefficients each thread forms once for its cell.
+constexpr int KB = 16, KH = 8;
 
-__device__ __forceinline__ EqF load_par(const float* __restrict__ fp, int n, int i) {
-  return EqF{__ldg(fp + i), __ldg(fp + n + i), __ldg(fp + 2 * n + i), __ldg(fp + 3 * n + i),
-             __ldg(fp + 4 * n + i)};
-}
-
-struct FaceCtx {
-  EqF w, e, so, no;                      // parameters of the W, E, S, N faces
-  size_t bx, by;                         // fbx / fby index of the W / S face, velocity 0
-  int nfx, nfy, nx;
+struct Quad {                    // P(xi) = c0 + cx x + cy y + cxx x^2 + cxy x y + cyy y^2
+  float c0, cx, cy, cxx, cxy, cyy;
 };
-__device__ __forceinline__ FaceCtx face_ctx(const GDevStep& s, int i, int j) {
+__device__ __forceinline__ Quad quad(const float* __restrict__ fp, int n, int i) {
+  const float vx = __ldg(fp + i), vy = __ldg(fp + n + i), bm1 = __ldg(fp + 2 * n + i);
+  const float r = __ldg(fp + 3 * n + i), dr = __ldg(fp + 4 * n + i);
+  Quad o;
+  o.c0 = fmaf(r, bm1, dr);
+  o.cx = r * vx;
+  o.cy = r * vy;
+  o.cxx = 0.5f * o.cx * vx;
+  o.cxy = o.cx * vy;
+  o.cyy = 0.5f * o.cy * vy;
+  return o;
+}
+struct Cubic {                   // 1, x, y, xx, xy, yy, xxx, xxy, xyy, yyy
+  float c[10];
+};
+__device__ __forceinline__ float cubic(const Cubic& S, float x, float y) {
+  const float t1 = fmaf(x, S.c[6], fmaf(y, S.c[7], S.c[3]));
+  const float t2 = fmaf(y, S.c[8], S.c[4]);
+  const float t3 = fmaf(y, S.c[9], S.c[5]);
+  const float X = fmaf(x, t1, fmaf(y, t2, S.c[1]));
+  const float Y = fmaf(y, t3, S.c[2]);
+  return fmaf(x, X, fmaf(y, Y, S.c[0]));
+}
+// F(xi) = (x/dx)(P_E - P_W) + (y/dy)(P_N - P_S) for the faces of cell (i, j),
+// scaled by sc
+__device__ __forceinline__ Cubic flux_cubic(const GDevStep& s, int i, int j, float sc) {
   const int nx = s.p.nx, ny = s.p.ny;
-  FaceCtx c;
-  c.nx = nx;
-  c.nfx = ny * (nx + 1);
-  c.nfy = (ny + 1) * nx;
+  const int nfx = ny * (nx + 1), nfy = (ny + 1) * nx;
   const int fx = j * (nx + 1) + i, fy = j * nx + i;
-  c.w = load_par(s.fpx, c.nfx, fx);
-  c.e = load_par(s.fpx, c.nfx, fx + 1);
-  c.so = load_par(s.fpy, c.nfy, fy);
-  c.no = load_par(s.fpy, c.nfy, fy + nx);
-  c.bx = fx;
-  c.by = fy;
-  return c;
-}
-// raw face values of velocity k: W, E, S, N
-__device__ __forceinline__ void face_vals(const GDevStep& s, const FaceCtx& c, int k, float (&f)[4]) {
-  const size_t bx = (size_t)k * c.nfx + c.bx, by = (size_t)k * c.nfy + c.by;
-  f[0] = __ldg(s.fbx + bx);
-  f[1] = __ldg(s.fbx + bx + 1);
-  f[2] = __ldg(s.fby + by);
-  f[3] = __ldg(s.fby + by + c.nx);
-}
-__device__ __forceinline__ float flux(const GDevStep& s, const FaceCtx& c, int k,
-                                      const float (&f)[4], float alpha, float beta) {
-  const float* vf = s.vf;
-  const int nv = s.p.nv;
-  const float4 e4 = __ldg(s.vq + nv + k);
-  const float cx = e4.x, cy = e4.y, w = e4.z;
-  const float dxf = fmaf(alpha, f[1] - f[0], beta * (feq_dev(c.e, cx, cy, w) - feq_dev(c.w, cx, cy, w)));
-  const float dyf = fmaf(alpha, f[3] - f[2], beta * (feq_dev(c.no, cx, cy, w) - feq_dev(c.so, cx, cy, w)));
-  return -fmaf(vt(vf, nv, GV_KX, k), dxf, vt(vf, nv, GV_KY, k) * dyf);
+  const Quad w = quad(s.fpx, nfx, fx), e = quad(s.fpx, nfx, fx + 1);
+  const Quad so = quad(s.fpy, nfy, fy), no = quad(s.fpy, nfy, fy + nx);
+  const float ax = sc * (float)s.p.inv_dx, ay = sc * (float)s.p.inv_dy;
+  Cubic F;
+  F.c[0] = 0.f;
+  F.c[1] = ax * (e.c0 - w.c0);
+  F.c[2] = ay * (no.c0 - so.c0);
+  F.c[3] = ax * (e.cx - w.cx);
+  F.c[4] = fmaf(ax, e.cy - w.cy, ay * (no.cx - so.cx));
+  F.c[5] = ay * (no.cy - so.cy);
+  F.c[6] = ax * (e.cxx - w.cxx);
+  F.c[7] = fmaf(ax, e.cxy - w.cxy, ay * (no.cxx - so.cxx));
+  F.c[8] = fmaf(ax, e.cyy - w.cyy, ay * (no.cxy - so.cxy));
+  F.c[9] = ay * (no.cyy - so.cyy);
+  return F;
 }
 
-// f~(t') = 5/4 g1 - 1/4 f^ + dt/3 L*,  acc = 1/4 f^ + 3/4 g1 + 3dt/7 L*
+// kx (f-bar_e - f-bar_w) + ky (f-bar_n - f-bar_s) of velocity k
+__device__ __forceinline__ float lbar(const float (&f)[4], float kx, float ky) {
+  return fmaf(kx, f[1] - f[0], ky * (f[3] - f[2]));
+}
+
+// f~(t') = 5/4 g1 - 1/4 f^ + dt/3 L*,  acc = 1/4 f^ + 3/4 g1 + 3dt/7 L*,
+// L* = -alpha lbar + W S(xi), S = -beta F
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_gupdate1(GDevStep s, float alpha, float beta, float dt3, float dt37) {
   const DevParams& p = s.p;
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.N) return;
-  const int j = cell / p.nx, i = cell - j * p.nx;
-  const FaceCtx c = face_ctx(s, i, j);
-  const int kb = blockIdx.y * KB;
-  T fh[KB], gg[KB];
-  float fv[KB][4];
+  const int nx = p.nx, ny = p.ny, nv = p.nv;
+  const int j = cell / nx, i = cell - j * nx;
+  const Cubic S = flux_cubic(s, i, j, -beta);
+  const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
+  const float* fbx = s.fbx + (size_t)j * (nx + 1) + i;
+  const float* fby = s.fby + (size_t)j * nx + i;
+  for (int h = 0; h < KB; h += KH) {
+    const int kb = blockIdx.y * KB + h;
+    T fh[KH], gg[KH];
+    float fv[KH][4];
 #pragma unroll
-  for (int u = 0; u < KB; ++u) {
-    const int k = kb + u;
-    if (k < p.nv) {
-      fh[u] = ldr((const T*)s.fhat + (size_t)k * p.N + cell);
-      gg[u] = ldr((const T*)s.g + gp_at(s, k, i, j));
-      face_vals(s, c, k, fv[u]);
+    for (int u = 0; u < KH; ++u) {
+      const int k = kb + u;
+      if (k < nv) {
+        fh[u] = ldr((const T*)s.fhat + (size_t)k * p.N + cell);
+        gg[u] = ldr((const T*)s.g + gp_at(s, k, i, j));
+        fv[u][0] = __ldg(fbx + k * nfx);
+        fv[u][1] = __ldg(fbx + k * nfx + 1);
+        fv[u][2] = __ldg(fby + k * nfy);
+        fv[u][3] = __ldg(fby + k * nfy + nx);
+      }
     }
-  }
 #pragma unroll
-  for (int u = 0; u < KB; ++u) {
-    const int k = kb + u;
-    if (k < p.nv) {
-      const float L = flux(s, c, k, fv[u], alpha, beta);
-      const size_t t = (size_t)k * p.N + cell;
-      const float f0 = tof(fh[u]), g0 = tof(gg[u]);
-      stv((T*)s.ftp + t, fmaf(1.25f, g0, fmaf(-0.25f, f0, dt3 * L)));
-      stv((T*)s.acc + t, fmaf(0.25f, f0, fmaf(0.75f, g0, dt37 * L)));
+    for (int u = 0; u < KH; ++u) {
+      const int k = kb + u;
+      if (k < nv) {
+        const float4 e4 = __ldg(s.vq + nv + k);
+        const float4 k4 = __ldg(s.vq + 2 * nv + k);
+        const float L = fmaf(-alpha, lbar(fv[u], k4.x, k4.y), e4.z * cubic(S, e4.x, e4.y));
+        const size_t t = (size_t)k * p.N + cell;
+        const float f0 = tof(fh[u]), g0 = tof(gg[u]);
+        stv((T*)s.ftp + t, fmaf(1.25f, g0, fmaf(-0.25f, f0, dt3 * L)));
+        stv((T*)s.acc + t, fmaf(0.25f, f0, fmaf(0.75f, g0, dt37 * L)));
+      }
     }
   }
 }
 
-// f^^{n+1} = acc + 3/4 dt Omega' + 4dt/7 L**,  dt Omega' = c_om (f~' - feq')
+// f^^{n+1} = acc + 3/4 dt Omega' + 4dt/7 L**,  dt Omega' = c_om (f~' - feq');
+// = acc + c34 f~' - (4dt/7) alpha lbar + W S(xi),
+// S = -c34 P_cell - (4dt/7) beta F
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_gupdate2(GDevStep s, float alpha, float beta, float c_om34, float dt47) {
   const DevParams& p = s.p;
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.N) return;
-  const int j = cell / p.nx, i = cell - j * p.nx;
-  const FaceCtx c = face_ctx(s, i, j);
-  const EqF q = load_par(s.eqp, p.N, cell);
-  const int kb = blockIdx.y * KB;
-  T ft[KB], ac[KB];
-  float fv[KB][4];
-#pragma unroll
-  for (int u = 0; u < KB; ++u) {
-    const int k = kb + u;
-    if (k < p.nv) {
-      const size_t t = (size_t)k * p.N + cell;
-      ft[u] = ldr((const T*)s.ftp + t);
-      ac[u] = ldr((const T*)s.acc + t);
-      face_vals(s, c, k, fv[u]);
-    }
+  const int nx = p.nx, ny = p.ny, nv = p.nv;
+  const int j = cell / nx, i = cell - j * nx;
+  Cubic S = flux_cubic(s, i, j, -dt47 * beta);
+  {
+    const Quad c = quad(s.eqp, p.N, cell);
+    S.c[0] = fmaf(-c_om34, c.c0, S.c[0]);
+    S.c[1] = fmaf(-c_om34, c.cx, S.c[1]);
+    S.c[2] = fmaf(-c_om34, c.cy, S.c[2]);
+    S.c[3] = fmaf(-c_om34, c.cxx, S.c[3]);
+    S.c[4] = fmaf(-c_om34, c.cxy, S.c[4]);
+    S.c[5] = fmaf(-c_om34, c.cyy, S.c[5]);
   }
+  const float adt = dt47 * alpha;
+  const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
+  const float* fbx = s.fbx + (size_t)j * (nx + 1) + i;
+  const float* fby = s.fby + (size_t)j * nx + i;
+  for (int h = 0; h < KB; h += KH) {
+    const int kb = blockIdx.y * KB + h;
+    T ft[KH], ac[KH];
+    float fv[KH][4];
 #pragma unroll
-  for (int u = 0; u < KB; ++u) {
-    const int k = kb + u;
-    if (k < p.nv) {
-      const float L = flux(s, c, k, fv[u], alpha, beta);
-      const float fe = feq_dev(q, vt(s.vf, p.nv, GV_XH, k), vt(s.vf, p.nv, GV_YH, k),
-                               vt(s.vf, p.nv, GV_W, k));
-      stv((T*)s.fhat + (size_t)k * p.N + cell,
-          fmaf(dt47, L, fmaf(c_om34, tof(ft[u]) - fe, tof(ac[u]))));
+    for (int u = 0; u < KH; ++u) {
+      const int k = kb + u;
+      if (k < nv) {
+        const size_t t = (size_t)k * p.N + cell;
+        ft[u] = ldr((const T*)s.ftp + t);
+        ac[u] = ldr((const T*)s.acc + t);
+        fv[u][0] = __ldg(fbx + k * nfx);
+        fv[u][1] = __ldg(fbx + k * nfx + 1);
+        fv[u][2] = __ldg(fby + k * nfy);
+        fv[u][3] = __ldg(fby + k * nfy + nx);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < KH; ++u) {
+      const int k = kb + u;
+      if (k < nv) {
+        const float4 e4 = __ldg(s.vq + nv + k);
+        const float4 k4 = __ldg(s.vq + 2 * nv + k);
+        const float src = fmaf(-adt, lbar(fv[u], k4.x, k4.y), e4.z * cubic(S, e4.x, e4.y));
+        stv((T*)s.fhat + (size_t)k * p.N + cell, fmaf(c_om34, tof(ft[u]), tof(ac[u]) + src));
+      }
     }
   }
 }

@@ -136,10 +136,6 @@ cudaError_t d2q9m_prepare();
 struct GDevRef {
   double rho0, W, Wx, Wy;       // rho0, rho0 sum W_k, rho0 sum W_k xi_x, rho0 sum W_k xi_y
 };
-// FP32 per-velocity tables of that path, rows of vf[GV_N][nv]:
-// xi rounded to FP32 and its remainder (xi = xh + xl to ~2^-48), W_k, and
-// the flux factors xi_x/dx, xi_y/dy.
-enum { GV_XH = 0, GV_YH, GV_XL, GV_YL, GV_W, GV_KX, GV_KY, GV_N };
 struct GDevStep {
   DevParams p;
   GDevRef ref;
@@ -152,8 +148,7 @@ struct GDevStep {
   size_t plane;                 // (ny + 4) * pitch
   float *fbx, *fby, *eqp;       // faces hold f-bar; eqp [5][N]
   float *fpx, *fpy;             // face assembly parameters [5][nf] of x / y faces
-  const float* vf;
-  const float4* vq;             // [2][nv]: (xh, xl, yh, yl), (xh, yh, W, 0)
+  const float4* vq;             // [3][nv]: (xh, xl, yh, yl), (xh, yh, W, 0), (kx, ky, 0, 0)
   double *mom, *part;           // part: [nch][3][nf] partial face moments
   int nchx, nchy;
   double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
