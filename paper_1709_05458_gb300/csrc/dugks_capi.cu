@@ -673,13 +673,16 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     g.c_om = c->c_om;
     g.nchx = gdev_chunks(p, 0, sms);
     g.nchy = gdev_chunks(p, 1, sms);
-    if (c->part && (c->nchx < g.nchx || c->nchy < g.nchy)) {
+    g.mch = nv > 32 ? 4 : 1;
+    // partial moments of this path's face and cell passes (the FP64 path's
+    // buffer, if any, is not used by it)
+    if (c->part) {
       cudaFree(c->part);
       c->part = nullptr;
     }
     const size_t nfmax = std::max((size_t)p.ny * (p.nx + 1), (size_t)(p.ny + 1) * p.nx);
-    if (!c->part)
-      e = cudaMalloc((void**)&c->part, (size_t)std::max(g.nchx, g.nchy) * 3 * nfmax * sizeof(double));
+    const int pch = std::max(std::max(g.nchx, g.nchy), g.mch);
+    e = cudaMalloc((void**)&c->part, (size_t)pch * 3 * nfmax * sizeof(double));
     g.pitch = gdev_pitch(p.nx);
     g.plane = (size_t)(p.ny + 4) * g.pitch;
     if (e == cudaSuccess) e = cudaMalloc(&c->gpad, g.plane * nv * sizeof(float));

@@ -176,101 +176,169 @@ __device__ __forceinline__ size_t gp_at(const GDevStep& s, int k, int i, int j) 
   return (size_t)k * s.plane + (size_t)(j + 2) * s.pitch + (i + 2);
 }
 
+// Equilibrium of a cell or face as a quadratic in xi from its assembly
+// parameters: feq_k = W_k P(xi_k).
+struct Quad {                    // P(xi) = c0 + cx x + cy y + cxx x^2 + cxy x y + cyy y^2
+  float c0, cx, cy, cxx, cxy, cyy;
+};
+__device__ __forceinline__ Quad quad(const float* __restrict__ fp, int n, int i) {
+  const float vx = __ldg(fp + i), vy = __ldg(fp + n + i), bm1 = __ldg(fp + 2 * n + i);
+  const float r = __ldg(fp + 3 * n + i), dr = __ldg(fp + 4 * n + i);
+  Quad o;
+  o.c0 = fmaf(r, bm1, dr);
+  o.cx = r * vx;
+  o.cy = r * vy;
+  o.cxx = 0.5f * o.cx * vx;
+  o.cxy = o.cx * vy;
+  o.cyy = 0.5f * o.cy * vy;
+  return o;
+}
 // ---------------------------------------------------------------- cell
-// Per cell: moments of src over the velocity set (G groups of velocities per
-// column of TX cells, eight loads in flight per thread); one thread per cell
-// forms rho, u (FP64, into mom) and the FP32 assembly parameters (into eqp
-// and shared memory); then g = a src + b feq as a deviation, in the padded
-// layout.
-template <typename T, int G>
+// The cell pass of a stage: moments of src (f^ or f~') -> rho, u (FP64, into
+// mom) and the FP32 assembly parameters (eqp [5][N]); g = a src + b feq as
+// a deviation, into the padded layout.
+//
+// Small velocity sets: one thread per cell does both sweeps.
+template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gcell(GDevStep s, const T* __restrict__ src, float a, float b) {
-  constexpr int TX = kThreads / G;
-  constexpr int U = 8;
-  __shared__ double red[G > 1 ? 3 * G * TX : 1];
-  __shared__ float eqs[5][TX];
+k_gcell1(GDevStep s, const T* __restrict__ src, float a, float b) {
   const DevParams& p = s.p;
   T* __restrict__ g = (T*)s.g;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int cell = blockIdx.x * TX + tx;
-  const bool valid = cell < p.N;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= p.N) return;
   const int nv = p.nv;
   Acc s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
+  for (int k = 0; k < nv; ++k) {
+    const float d = ldv(src + (size_t)k * p.N + cell);
+    const float4 xq = __ldg(s.vq + k);
+    acc_add(s0, d);
+    acc_addprod(s1, xq.x, xq.y, d);
+    acc_addprod(s2, xq.z, xq.w, d);
+  }
+  const GDevRef& ref = s.ref;
+  const double rho = ref.W + acc_value(s0);
+  const double rinv = 1.0 / rho;
+  const double ux = (ref.Wx + acc_value(s1)) * rinv, uy = (ref.Wy + acc_value(s2)) * rinv;
+  const EqF q = eq_params_u(rho, ux, uy, p.inv_RT, ref.rho0);
+  s.mom[cell] = rho;
+  s.mom[p.N + cell] = ux;
+  s.mom[2 * p.N + cell] = uy;
+  const float qv[5] = {q.vx, q.vy, q.bm1, q.r, q.dr};
+#pragma unroll
+  for (int m = 0; m < 5; ++m) s.eqp[m * p.N + cell] = qv[m];
+  const int j = cell / p.nx, i = cell - j * p.nx;
+  for (int k = 0; k < nv; ++k) {
+    const float4 e4 = __ldg(s.vq + nv + k);
+    const float fe = feq_dev(q, e4.x, e4.y, e4.z);
+    stv(g + gp_at(s, k, i, j), fmaf(b, fe, a * ldv(src + (size_t)k * p.N + cell)));
+  }
+}
+
+// Large velocity sets, three kernels.  (1) Partial moments: 32 cells per
+// block, 8 warps over a velocity chunk (eight loads in flight per thread),
+// compensated FP32 partials combined in FP64, into part[chunk][3][N].
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gmom(GDevStep s, const T* __restrict__ src, int kchunk) {
+  constexpr int TX = 32, G = kThreads / TX, U = 8;
+  __shared__ double red[3][G][TX];
+  const DevParams& p = s.p;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int cell = blockIdx.x * TX + tx;
+  const bool valid = cell < p.N;
+  const int k0 = blockIdx.y * kchunk, k1 = min(p.nv, k0 + kchunk);
+  Acc s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
   if (valid) {
-    int k = ty;
-    for (; k + (U - 1) * G < nv; k += U * G) {
+    int k = k0 + ty;
+    for (; k + (U - 1) * G < k1; k += U * G) {
       T d[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) d[u] = ldr(src + (size_t)(k + u * G) * p.N + cell);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int kk = k + u * G;
-        const float4 xq = __ldg(s.vq + kk);
+        const float4 xq = __ldg(s.vq + k + u * G);
         const float du = tof(d[u]);
         acc_add(s0, du);
         acc_addprod(s1, xq.x, xq.y, du);
         acc_addprod(s2, xq.z, xq.w, du);
       }
     }
-    for (; k < nv; k += G) {
-      const float d = ldv(src + (size_t)k * p.N + cell);
+    for (; k < k1; k += G) {
+      const float du = ldv(src + (size_t)k * p.N + cell);
       const float4 xq = __ldg(s.vq + k);
-      acc_add(s0, d);
-      acc_addprod(s1, xq.x, xq.y, d);
-      acc_addprod(s2, xq.z, xq.w, d);
+      acc_add(s0, du);
+      acc_addprod(s1, xq.x, xq.y, du);
+      acc_addprod(s2, xq.z, xq.w, du);
     }
   }
-  double v[3] = {acc_value(s0), acc_value(s1), acc_value(s2)};
-  if constexpr (G > 1) {
-#pragma unroll
-    for (int m = 0; m < 3; ++m) red[(m * G + ty) * TX + tx] = v[m];
-    __syncthreads();
-    if (ty == 0)
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        double t = 0.0;
-#pragma unroll
-        for (int q = 0; q < G; ++q) t += red[(m * G + q) * TX + tx];
-        v[m] = t;
-      }
-  }
-  if (ty == 0 && valid) {
-    const GDevRef& ref = s.ref;
-    const double rho = ref.W + v[0];
-    const double rinv = 1.0 / rho;
-    const double ux = (ref.Wx + v[1]) * rinv, uy = (ref.Wy + v[2]) * rinv;
-    const EqF q = eq_params_u(rho, ux, uy, p.inv_RT, ref.rho0);
-    s.mom[cell] = rho;
-    s.mom[p.N + cell] = ux;
-    s.mom[2 * p.N + cell] = uy;
-    const float qv[5] = {q.vx, q.vy, q.bm1, q.r, q.dr};
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      s.eqp[m * p.N + cell] = qv[m];
-      eqs[m][tx] = qv[m];
-    }
-  }
+  red[0][ty][tx] = acc_value(s0);
+  red[1][ty][tx] = acc_value(s1);
+  red[2][ty][tx] = acc_value(s2);
   __syncthreads();
-  if (!valid) return;
-  const EqF q{eqs[0][tx], eqs[1][tx], eqs[2][tx], eqs[3][tx], eqs[4][tx]};
-  const int j = cell / p.nx, i = cell - j * p.nx;
-  int k = ty;
-  for (; k + 3 * G < nv; k += 4 * G) {
-    T d[4];
+  if (ty < 3 && valid) {
+    double t = 0.0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) d[u] = ldr(src + (size_t)(k + u * G) * p.N + cell);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int kk = k + u * G;
-      const float4 e4 = __ldg(s.vq + nv + kk);
-      const float fe = feq_dev(q, e4.x, e4.y, e4.z);
-      stv(g + gp_at(s, kk, i, j), fmaf(b, fe, a * tof(d[u])));
-    }
+    for (int q = 0; q < G; ++q) t += red[ty][q][tx];
+    s.part[((size_t)blockIdx.y * 3 + ty) * p.N + cell] = t;
   }
-  for (; k < nv; k += G) {
-    const float4 e4 = __ldg(s.vq + nv + k);
-    const float fe = feq_dev(q, e4.x, e4.y, e4.z);
-    stv(g + gp_at(s, k, i, j), fmaf(b, fe, a * ldv(src + (size_t)k * p.N + cell)));
+}
+
+// (2) Per cell: the chunks' partials in order -> rho, u, mom, eqp.
+__global__ void __launch_bounds__(kThreads)
+k_gmomfin(GDevStep s, int nchunk) {
+  const DevParams& p = s.p;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= p.N) return;
+  double v0 = s.ref.W, v1 = s.ref.Wx, v2 = s.ref.Wy;
+  for (int c = 0; c < nchunk; ++c) {
+    const double* pc = s.part + (size_t)c * 3 * p.N;
+    v0 += pc[cell];
+    v1 += pc[p.N + cell];
+    v2 += pc[2 * p.N + cell];
+  }
+  const double rinv = 1.0 / v0;
+  const double ux = v1 * rinv, uy = v2 * rinv;
+  const EqF q = eq_params_u(v0, ux, uy, p.inv_RT, s.ref.rho0);
+  s.mom[cell] = v0;
+  s.mom[p.N + cell] = ux;
+  s.mom[2 * p.N + cell] = uy;
+  s.eqp[cell] = q.vx;
+  s.eqp[p.N + cell] = q.vy;
+  s.eqp[2 * p.N + cell] = q.bm1;
+  s.eqp[3 * p.N + cell] = q.r;
+  s.eqp[4 * p.N + cell] = q.dr;
+}
+
+// (3) g = a src + b W_k P(xi_k): one thread per cell and 16 consecutive
+// velocities (two batches of eight loads in flight), P the cell's
+// equilibrium quadratic in xi.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gcellg(GDevStep s, const T* __restrict__ src, float a, float b) {
+  constexpr int CB = 16, CH = 8;
+  const DevParams& p = s.p;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= p.N) return;
+  const int nv = p.nv;
+  const int j = cell / p.nx, i = cell - j * p.nx;
+  const Quad P = quad(s.eqp, p.N, cell);
+  T* __restrict__ g = (T*)s.g;
+  for (int h = 0; h < CB; h += CH) {
+    const int kb = blockIdx.y * CB + h;
+    T d[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+      if (kb + u < nv) d[u] = ldr(src + (size_t)(kb + u) * p.N + cell);
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int k = kb + u;
+      if (k < nv) {
+        const float4 e4 = __ldg(s.vq + nv + k);
+        const float x = e4.x, y = e4.y;
+        const float pk = fmaf(x, fmaf(x, P.cxx, fmaf(y, P.cxy, P.cx)), fmaf(y, fmaf(y, P.cyy, P.cy), P.c0));
+        stv(g + gp_at(s, k, i, j), fmaf(b * e4.z, pk, a * tof(d[u])));
+      }
+    }
   }
 }
 
@@ -676,21 +744,6 @@ k_gwalls(GDevStep s, float h, int nwx) {
 // (xi_x, xi_y), whose ten coefficients each thread forms once for its cell.
 constexpr int KB = 16, KH = 8;
 
-struct Quad {                    // P(xi) = c0 + cx x + cy y + cxx x^2 + cxy x y + cyy y^2
-  float c0, cx, cy, cxx, cxy, cyy;
-};
-__device__ __forceinline__ Quad quad(const float* __restrict__ fp, int n, int i) {
-  const float vx = __ldg(fp + i), vy = __ldg(fp + n + i), bm1 = __ldg(fp + 2 * n + i);
-  const float r = __ldg(fp + 3 * n + i), dr = __ldg(fp + 4 * n + i);
-  Quad o;
-  o.c0 = fmaf(r, bm1, dr);
-  o.cx = r * vx;
-  o.cy = r * vy;
-  o.cxx = 0.5f * o.cx * vx;
-  o.cxy = o.cx * vy;
-  o.cyy = 0.5f * o.cy * vy;
-  return o;
-}
 struct Cubic {                   // 1, x, y, xx, xy, yy, xxx, xxy, xyy, yyy
   float c[10];
 };
@@ -834,12 +887,18 @@ k_gupdate2(GDevStep s, float alpha, float beta, float c_om34, float dt47) {
 template <typename T>
 cudaError_t cell_t(const GDevStep& s, const void* src, const StageCoef& c, cudaStream_t st) {
   const DevParams& p = s.p;
-  if (p.nv > 32) {
-    constexpr int G = 16, TX = kThreads / G;
-    k_gcell<T, G><<<(p.N + TX - 1) / TX, dim3(TX, G), 0, st>>>(s, (const T*)src, (float)c.a,
-                                                              (float)c.b);
+  if (s.mch <= 1) {
+    k_gcell1<T><<<(p.N + kThreads - 1) / kThreads, kThreads, 0, st>>>(s, (const T*)src, (float)c.a,
+                                                                    (float)c.b);
   } else {
-    k_gcell<T, 1><<<(p.N + kThreads - 1) / kThreads, dim3(kThreads, 1), 0, st>>>(
+    const int kchunk = (p.nv + s.mch - 1) / s.mch;
+    k_gmom<T><<<dim3((p.N + 31) / 32, s.mch), kThreads, 0, st>>>(s, (const T*)src, kchunk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gmomfin<<<(p.N + kThreads - 1) / kThreads, kThreads, 0, st>>>(s, s.mch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_gcellg<T><<<dim3((p.N + kThreads - 1) / kThreads, (p.nv + 15) / 16), kThreads, 0, st>>>(
         s, (const T*)src, (float)c.a, (float)c.b);
   }
   cudaError_t e = cudaGetLastError();

@@ -149,8 +149,9 @@ struct GDevStep {
   float *fbx, *fby, *eqp;       // faces hold f-bar; eqp [5][N]
   float *fpx, *fpy;             // face assembly parameters [5][nf] of x / y faces
   const float4* vq;             // [3][nv]: (xh, xl, yh, yl), (xh, yh, W, 0), (kx, ky, 0, 0)
-  double *mom, *part;           // part: [nch][3][nf] partial face moments
+  double *mom, *part;           // part: [nch][3][nf] partial face moments, or [mch][3][N] cell ones
   int nchx, nchy;
+  int mch;                      // velocity chunks of the cell moments (1: one thread per cell)
   double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
 };
 int gdev_pitch(int nx);
