@@ -53,6 +53,12 @@ marked ``Qn`` where it is used):
       [ - sum_{xi.n<0} (xi.n) feq(xi; 1, u_w) ].
 * Q16 stencil ghosts beyond a wall: quadratic extrapolation along the wall
       normal, g_{-1} = 3 g_0 - 3 g_1 + g_2 (corners: both directions).
+* Q26 T2S2 (Sec. 3, the second-order-in-space comparison method, whose
+      reconstruction is not printed): eq. flux_DS taken to first order, the
+      "desired order" its text allows -- f-bar^+(x_b - xi h) =
+      g_U + (x_b - xi h - x_U).grad g_U from the upwind cell U, gradient by
+      central differences (Q3), walls and ties as for T3S3.  T2S3 is the same
+      T2 step with the full quadratic expansion.
 """
 from __future__ import annotations
 
@@ -201,15 +207,26 @@ def _wall(fluid, rho_adj, xn, s: Setup, bc):
     return fb
 
 
-def interface_fbar(g, h, rho_base, s: Setup):
+def taylor_linear(d, dX, dY):
+    """First-order Taylor expansion about a cell centre (eq. flux_DS to the
+    gradient term, Q26)."""
+    C, gx, gy = d[0], d[1], d[2]
+    return C + dX * gx + dY * gy
+
+
+def interface_fbar(g, h, rho_base, s: Setup, recon="quadratic"):
     """f-bar(x_b, t+h) = f-bar^{+,h}(x_b - xi h, t) on every face
     (eqs. interfaceEvof and flux_DS), given g = f-bar^{+,h}(t) at the cells.
 
     Returns (fbx, fby): x-faces (nv, ny, nx+1) at x = i dx and y-faces
     (nv, ny+1, nx) at y = j dy.  The upwind cell is chosen by the sign of
-    xi.n (eq. flux_DS); Q4 for xi.n == 0.
+    xi.n (eq. flux_DS); Q4 for xi.n == 0.  ``recon="linear"``: the
+    expansion truncated after the gradient term instead (T2S2, Q26).
     """
     nx, ny = s.nx, s.ny
+    if recon not in ("quadratic", "linear"):
+        raise ValueError(recon)
+    taylor_ = taylor if recon == "quadratic" else taylor_linear
     d = cell_derivatives(g, s)
 
     # x-faces: face i lies between cell i-1 (left) and cell i (right)
@@ -217,8 +234,8 @@ def interface_fbar(g, h, rho_base, s: Setup):
     ri = np.arange(nx + 1) % nx
     dL = tuple(a[:, :, li] for a in d)
     dR = tuple(a[:, :, ri] for a in d)
-    fromL = taylor(dL, 0.5 * s.dx - s.cx * h, -s.cy * h)
-    fromR = taylor(dR, -0.5 * s.dx - s.cx * h, -s.cy * h)
+    fromL = taylor_(dL, 0.5 * s.dx - s.cx * h, -s.cy * h)
+    fromR = taylor_(dR, -0.5 * s.dx - s.cx * h, -s.cy * h)
     fbx = np.where(s.cx > 0, fromL, np.where(s.cx < 0, fromR, 0.5 * (fromL + fromR)))
     if not s.periodic_x:
         fbx[:, :, 0] = _wall(fromR[:, :, 0], rho_base[:, 0], -s.xi[:, 0], s, s.bc[WEST])
@@ -229,8 +246,8 @@ def interface_fbar(g, h, rho_base, s: Setup):
     rj = np.arange(ny + 1) % ny
     dB = tuple(a[:, lj, :] for a in d)
     dT = tuple(a[:, rj, :] for a in d)
-    fromB = taylor(dB, -s.cx * h, 0.5 * s.dy - s.cy * h)
-    fromT = taylor(dT, -s.cx * h, -0.5 * s.dy - s.cy * h)
+    fromB = taylor_(dB, -s.cx * h, 0.5 * s.dy - s.cy * h)
+    fromT = taylor_(dT, -s.cx * h, -0.5 * s.dy - s.cy * h)
     fby = np.where(s.cy > 0, fromB, np.where(s.cy < 0, fromT, 0.5 * (fromB + fromT)))
     if not s.periodic_y:
         fby[:, 0, :] = _wall(fromT[:, 0, :], rho_base[0, :], -s.xi[:, 1], s, s.bc[SOUTH])
@@ -251,9 +268,9 @@ def microflux(fx, fy, s: Setup):
              + s.cy * (fy[:, 1:, :] - fy[:, :-1, :]) / s.dy)
 
 
-def flux_from_g(g, h, rho_base, s: Setup):
+def flux_from_g(g, h, rho_base, s: Setup, recon="quadratic"):
     """The DUGKS reconstruction chain: g -> f-bar(x_b) -> f(x_b) -> L."""
-    fbx, fby = interface_fbar(g, h, rho_base, s)
+    fbx, fby = interface_fbar(g, h, rho_base, s, recon)
     return microflux(recover_f(fbx, h, s), recover_f(fby, h, s), s)
 
 
@@ -298,10 +315,11 @@ def t3s3_run(fhat, s: Setup, nsteps: int):
 
 
 # ------------------------------------------------ T2 step (Remark I)
-def t2_step(ftilde, s: Setup, delta: float):
+def t2_step(ftilde, s: Setup, delta: float, recon="quadratic"):
     """Original DUGKS time step of size ``delta`` (Remark I, eq.
-    feqIntD2nd_Explicit with Q7), with this file's quadratic reconstruction
-    at h = delta/2:  f~^{n+1} = f~^{+,n} + delta * L(t_n + delta/2).
+    feqIntD2nd_Explicit with Q7) at h = delta/2:
+    f~^{n+1} = f~^{+,n} + delta * L(t_n + delta/2); the quadratic
+    reconstruction gives T2S3, ``recon="linear"`` (Q26) gives T2S2.
 
     Works on f~ = f - delta/2 Omega.
     """
@@ -311,9 +329,23 @@ def t2_step(ftilde, s: Setup, delta: float):
     # f-bar^{+,h} from f~ (x = f - (h) Omega here since delta/2 = h):
     # f~ - feq = (f - feq)(1 + h/tau);  f-bar^{+,h} - feq = (f - feq)(1 - h/(2 tau))
     gbar = ((2.0 * tau - h) * ftilde + 3.0 * h * feq) / (2.0 * tau + 2.0 * h)
-    L = flux_from_g(gbar, h, rho, s)
+    L = flux_from_g(gbar, h, rho, s, recon)
     ft_plus = ((2.0 * tau - delta) * ftilde + 2.0 * delta * feq) / (2.0 * tau + delta)
     return ft_plus + delta * L
+
+
+def t2_run(ftilde, s: Setup, nsteps: int, recon="quadratic"):
+    """nsteps T2 steps of size s.dt (T2S3, or T2S2 with recon="linear")."""
+    f = np.array(ftilde, dtype=np.float64, copy=True)
+    for _ in range(nsteps):
+        f = t2_step(f, s, s.dt, recon)
+    return f
+
+
+def ftilde_from_f(f, s: Setup):
+    """f~ = f - dt/2 Omega(f) = f + dt/(2 tau) (f - feq(f)), the T2 state."""
+    feq, _ = equilibrium_of(f, s)
+    return f + s.dt / (2.0 * s.tau) * (f - feq)
 
 
 # ---------------------------------------------------------- conversions

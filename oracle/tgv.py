@@ -50,10 +50,15 @@ def cell_centres(s: O.Setup):
 
 
 def chapman_enskog_fhat(s: O.Setup, u0, nu):
-    """Initial f^ from f = feq - tau (d_t feq + xi . grad feq) (Sec. 3.1).
+    """Initial f^ = f - dt/4 Omega(f) of the Chapman-Enskog state below."""
+    return O.fhat_from_f(chapman_enskog_f(s, u0, nu), s)
+
+
+def chapman_enskog_f(s: O.Setup, u0, nu):
+    """Initial f = feq - tau (d_t feq + xi . grad feq) (Sec. 3.1).
 
     The derivatives of feq follow from the chain rule through (rho, u) of
-    the analytic solution; f^ = f - dt/4 Omega(f).
+    the analytic solution.
     """
     X, Y = cell_centres(s)
     rho, u, v, d = fields(X, Y, 0.0, u0, nu, s.RT)
@@ -71,8 +76,7 @@ def chapman_enskog_fhat(s: O.Setup, u0, nu):
     ft = dfeq(d["rho_t"], d["u_t"], d["v_t"])
     fx = dfeq(d["rho_x"], d["u_x"], d["v_x"])
     fy = dfeq(d["rho_y"], d["u_y"], d["v_y"])
-    f = feq - s.tau * (ft + cx * fx + cy * fy)
-    return O.fhat_from_f(f, s)
+    return feq - s.tau * (ft + cx * fx + cy * fy)
 
 
 def error_L2(fhat, s: O.Setup, t, u0, nu):
