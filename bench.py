@@ -53,7 +53,10 @@ FLOPS_PER_UNIT = {
     # the FP64 peak it takes longer than the kernels' algorithmic bytes at
     # the HBM peak, so it is their bound
     "gdev_cell": 5, "gdev_face_x": 5, "gdev_face_y": 5,
+    # T2 schemes on the generic kernels (counted as the T3S3 generic ones)
+    "t2_cell": 17, "t2_face_x": 34, "t2_face_y": 34, "t2_update": 19,
 }
+SCHEMES = {"t3s3": 0, "t2s3": 1, "t2s2": 2}
 # Kernels bound by HBM instead: algorithmic bytes per cell-velocity by
 # storage form (FP32 / BF16 per-cell arrays; face values are FP32 in both).
 HBM_BYTES_PER_UNIT = {
@@ -152,7 +155,7 @@ def dist_setup():
     return world, rank, local
 
 
-def make_solver(P, PV, WL, stream, storage=0):
+def make_solver(P, PV, WL, stream, storage=0, scheme="t3s3"):
     c = WL.config(WORKLOAD)
     if c.get("vel") == "nc":
         xi, W, RT = PV.newton_cotes(c["nv1"], c["RT"])
@@ -160,7 +163,7 @@ def make_solver(P, PV, WL, stream, storage=0):
         xi, W, RT = PV.d2q9(c["RT"])
     n = c["nx"]
     s = P.Solver(n, n, 1.0 / n, 1.0 / n, xi, W, RT, c["tau"], c["dt"], c["bc"], stream=stream,
-                 storage=storage)
+                 storage=storage, scheme=SCHEMES[scheme])
     s.set_equilibrium(*WL.rest_fields(n, n))
     return s, c, len(W)
 
@@ -321,7 +324,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     P.load()
     main_storage = {"fp64": P.FP64, "fp32": P.G_FP32, "bf16": P.G_BF16}[args.storage]
-    solver, c, nv = make_solver(P, PV, WL, stream, storage=main_storage)
+    solver, c, nv = make_solver(P, PV, WL, stream, storage=main_storage, scheme=args.scheme)
     units = c["nx"] * c["ny"] * nv
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -377,7 +380,7 @@ def run_ours(args):
     # the FP32 and BF16 deviation-storage forms on the same workload and
     # protocol; E(u) against the FP64 run after the same W + K steps
     forms = {}
-    if not args.no_forms and args.storage == "fp64":
+    if not args.no_forms and args.storage == "fp64" and args.scheme == "t3s3":
         for label, st in (("fp32", P.G_FP32), ("bf16", P.G_BF16)):
             s2, _, _ = make_solver(P, PV, WL, stream, storage=st)
             for _ in range(max(args.warmup, 0)):
@@ -436,7 +439,7 @@ def run_ours(args):
         "dtype": {"fp64": "f64", "fp32": "f32 deviation storage, f64 moment sums",
                   "bf16": "bf16 deviation storage, f32 arithmetic, f64 moment sums"}[args.storage],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": f"{nx}x{ny}",
+        "config": {"workload": WORKLOAD, "cells": f"{nx}x{ny}", "scheme": args.scheme.upper(),
                    "velocities": ("D2Q9" if c.get("vel") != "nc"
                                   else f"Newton-Cotes {c['nv1']}x{c['nv1']}"),
                    "bc": ("bounce-back walls, moving lid" if c.get("vel") != "nc"
@@ -480,6 +483,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="cavityN (N^2 D2Q9 cavity); the default is the reported workload")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--scheme", default="t3s3", choices=list(SCHEMES),
+                    help="time scheme (T2S3/T2S2: the second-order comparison schemes, "
+                         "generic FP64 kernels; the step they time is a T2 step)")
     ap.add_argument("--storage", default="fp64", choices=["fp64", "fp32", "bf16"],
                     help="storage form of the measured line (default FP64)")
     ap.add_argument("--no-forms", action="store_true",

@@ -260,6 +260,27 @@ int dugks_step_static(const dugks_mesh* mesh, const dugks_velset* vel, double ta
                       const dugks_bc bc[4], const double* fhat_in, double* fhat_out,
                       int nsteps, void* cuda_stream);
 
+/* Time schemes.  DUGKS_T3S3 (default) is the paper's two-stage third-order
+ * step (Sec. 2.1.3).  DUGKS_T2S3 and DUGKS_T2S2 are the second-order
+ * comparison methods of Sec. 3 (Remark I, eq. feqIntD2nd_Explicit):
+ * f~^{n+1} = f~^{+,n} + dt L(t_n + dt/2) on f~ = f - dt/2 Omega, with the
+ * face values at t_n + dt/2 from the quadratic upwind expansion of eq.
+ * flux_DS (T2S3) or that expansion truncated after the gradient term (T2S2;
+ * the paper does not print its reconstruction, this is the reading used). */
+enum { DUGKS_T3S3 = 0, DUGKS_T2S3 = 1, DUGKS_T2S2 = 2 };
+
+/* dugks_set_scheme -- select the time scheme of later dugks_step calls.
+ *   scheme: DUGKS_T3S3, DUGKS_T2S3 or DUGKS_T2S2.
+ * The state is not converted: under a T2 scheme the array that
+ * dugks_set_state / dugks_get_state move (and that dugks_set_equilibrium
+ * fills) is f~ = f - dt/2 Omega instead of f^ = f - dt/4 Omega; at
+ * equilibrium both equal feq.  The T2 schemes run on the generic kernels
+ * with DUGKS_FP64 storage (other storage: DUGKS_ENOTIMPL); the adjoint
+ * entry points are those of T3S3 and return DUGKS_ENOTIMPL under a T2
+ * scheme.  A context that belongs to a batch cannot change scheme.
+ * Errors: EINVAL (unknown scheme, NULL, batched context), ENOTIMPL. */
+int dugks_set_scheme(dugks_ctx* ctx, int scheme);
+
 /* dugks_destroy -- free the context (NULL is accepted). */
 int dugks_destroy(dugks_ctx* ctx);
 

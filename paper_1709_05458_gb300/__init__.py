@@ -25,6 +25,7 @@ DUGKS_OK, DUGKS_EINVAL, DUGKS_ECUDA, DUGKS_ENOMEM, DUGKS_EUNSTABLE, DUGKS_ENOTIM
 PERIODIC, BOUNCEBACK, DIFFUSE = 0, 1, 2
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 FP64, G_FP32, G_BF16 = 0, 1, 2
+T3S3, T2S3, T2S2 = 0, 1, 2
 
 # every symbol include/dugks.h declares
 EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_state",
@@ -32,7 +33,7 @@ EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_
            "dugks_profile", "dugks_profile_read", "dugks_kernel_name", "dugks_destroy",
            "dugks_last_error", "dugks_step_static", "dugks_adjoint_step", "dugks_adjoint_run",
            "dugks_adjoint_equilibrium", "dugks_autotune", "dugks_batch_create",
-           "dugks_batch_step", "dugks_batch_destroy")
+           "dugks_batch_step", "dugks_batch_destroy", "dugks_set_scheme")
 
 
 class DugksError(RuntimeError):
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH):
         "dugks_batch_create": (I, [C.POINTER(P), I, C.POINTER(P)]),
         "dugks_batch_step": (I, [P, I]),
         "dugks_batch_destroy": (I, [P]),
+        "dugks_set_scheme": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,6 +191,11 @@ def dugks_destroy(ctx):
     return _check(load().dugks_destroy(ctx))
 
 
+def dugks_set_scheme(ctx, scheme):
+    """T3S3 (default), T2S3 or T2S2; under a T2 scheme the state is f~."""
+    return _check(load().dugks_set_scheme(ctx, int(scheme)))
+
+
 def dugks_last_error():
     return load().dugks_last_error().decode()
 
@@ -287,11 +294,14 @@ def dugks_step_static(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, fhat_in, fhat_out,
 class Solver:
     """One DUGKS context: ``Solver(nx, ny, dx, dy, xi, W, RT, tau, dt, bc)``."""
 
-    def __init__(self, nx, ny, dx, dy, xi, W, RT, tau, dt, bc, stream=None, storage=FP64):
+    def __init__(self, nx, ny, dx, dy, xi, W, RT, tau, dt, bc, stream=None, storage=FP64,
+                 scheme=T3S3):
         self.nx, self.ny, self.nv = int(nx), int(ny), len(W)
         self.ctx = None
         self.ctx = dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, storage, stream)
         self.warning = dugks_last_error()
+        if scheme != T3S3:
+            dugks_set_scheme(self.ctx, scheme)
 
     def set_equilibrium(self, rho, ux, uy):
         a = [np.ascontiguousarray(x, dtype=np.float64) if isinstance(x, np.ndarray) else x

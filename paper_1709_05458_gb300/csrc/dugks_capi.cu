@@ -37,7 +37,7 @@ const char* kNames[K_NUM] = {
     "d2q9_prologue", "d2q9_stage1", "d2q9_stage2",
     "d2q9m_stage1", "d2q9m_stage2", "convert",
     "gdev_cell", "gdev_face_x", "gdev_face_y", "gdev_walls", "gdev_update_stage1",
-    "gdev_update_stage2"};
+    "gdev_update_stage2", "t2_cell", "t2_face_x", "t2_face_y", "t2_update"};
 
 struct Pending {
   int id;
@@ -86,6 +86,12 @@ struct dugks_ctx {
   float* vf = nullptr;          // FP32 velocity table (float4 rows [3][nv])
   void* gpad = nullptr;         // padded stage field of that path
   float* fpar = nullptr;        // face equilibrium parameters of that path
+  // time scheme (dugks_set_scheme): 0 T3S3; 1 T2S3, 2 T2S2 on the generic
+  // kernels with the T2 stage coefficients below
+  int scheme = DUGKS_T3S3;
+  StageCoef t2{};               // g = a f~ + b feq, h = dt/2, f = alpha f-bar + beta feq
+  double t2a = 0.0, t2b = 0.0;  // f~^+ = t2a f~ + t2b feq
+  int batched = 0;              // number of batches holding this context
   // adjoint (allocated on first use): forward intermediates and adjoint fields
   double *a_g1 = nullptr, *a_g2 = nullptr, *a_ftp = nullptr, *a_acc = nullptr;
   double *a_mom1 = nullptr, *a_mom2 = nullptr, *a_tbar = nullptr, *a_gbar = nullptr;
@@ -358,9 +364,24 @@ int one_step_gdev(dugks_ctx* c) {
   return DUGKS_OK;
 }
 
+// One T2 step of size dt (Remark I, eq. feqIntD2nd_Explicit with Q7) on the
+// generic kernels: g = f-bar^{+,dt/2} from f~, faces at t_n + dt/2 with the
+// quadratic (T2S3) or first-order (T2S2) expansion, f~^{n+1} = f~^+ + dt L.
+int one_step_t2(dugks_ctx* c) {
+  const DevParams& p = c->p;
+  cudaStream_t s = c->stream;
+  const int G = c->groups;
+  TRY(launch(c, K_T2_CELL, [&] { return launch_cell(p, G, 1, c->fhat, c->g, c->mom, c->t2.a, c->t2.b, s); }));
+  TRY(launch(c, K_T2_FACE_X, [&] { return faces(c, 0, c->t2, c->fbx); }));
+  TRY(launch(c, K_T2_FACE_Y, [&] { return faces(c, 1, c->t2, c->fby); }));
+  TRY(launch(c, K_T2_UPDATE, [&] { return launch_update_t2(p, c->mom, c->fbx, c->fby, c->fhat, c->t2a, c->t2b, s); }));
+  return DUGKS_OK;
+}
+
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 int advance(dugks_ctx* c) {
+  if (c->scheme != DUGKS_T3S3) return one_step_t2(c);
   if (c->store) return c->gdev ? one_step_gdev(c) : one_step_d2q9m(c);
   return c->d2q9 ? one_step_d2q9(c) : one_step(c);
 }
@@ -639,6 +660,16 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     s->beta = s->h / (2.0 * T + s->h);
   }
   c->c_om = -6.0 * dt / (6.0 * T + dt);
+  // T2 schemes (Remark I): h = dt/2; f-bar^{+,h} from f~ = f - dt/2 Omega
+  // (the same map as the oracle's t2_step), f~^+ = ((2 tau - dt) f~ +
+  // 2 dt feq)/(2 tau + dt)
+  c->t2.h = 0.5 * dt;
+  c->t2.a = (2.0 * T - c->t2.h) / (2.0 * T + 2.0 * c->t2.h);
+  c->t2.b = 3.0 * c->t2.h / (2.0 * T + 2.0 * c->t2.h);
+  c->t2.alpha = 2.0 * T / (2.0 * T + c->t2.h);
+  c->t2.beta = c->t2.h / (2.0 * T + c->t2.h);
+  c->t2a = (2.0 * T - dt) / (2.0 * T + dt);
+  c->t2b = 2.0 * dt / (2.0 * T + dt);
 
   // fused D2Q9 path
   const double cd = d2q9_speed(vel);
@@ -907,6 +938,7 @@ int dugks_adjoint_step(dugks_ctx* c, const double* lam_in, double* lam_out, doub
                        double* dJ_duw, int on_device) {
   if (!c || !lam_in || !lam_out) return fail(DUGKS_EINVAL, "NULL argument");
   if (c->store) return fail(DUGKS_ENOTIMPL, "the adjoint needs DUGKS_FP64 storage");
+  if (c->scheme != DUGKS_T3S3) return fail(DUGKS_ENOTIMPL, "the adjoint is that of the T3S3 step");
   TRY(ensure_adjoint(c));
   const size_t nvN = (size_t)c->p.nv * c->p.N;
   CK(cudaMemsetAsync(c->a_grads, 0, 16 * sizeof(double), c->stream));
@@ -922,6 +954,7 @@ int dugks_adjoint_run(dugks_ctx* c, const double* fhat0, int nsteps, int every,
   if (!c || !fhat0 || !lam_final || !lam0) return fail(DUGKS_EINVAL, "NULL argument");
   if (nsteps < 0 || every < 1) return fail(DUGKS_EINVAL, "nsteps >= 0 and every >= 1 required");
   if (c->store) return fail(DUGKS_ENOTIMPL, "the adjoint needs DUGKS_FP64 storage");
+  if (c->scheme != DUGKS_T3S3) return fail(DUGKS_ENOTIMPL, "the adjoint is that of the T3S3 step");
   TRY(ensure_adjoint(c));
   const size_t nvN = (size_t)c->p.nv * c->p.N;
   const int nseg = (nsteps + every - 1) / every;
@@ -1054,7 +1087,8 @@ int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
   for (int i = 0; i < n; ++i) {
     dugks_ctx* c = ctxs[i];
     b->ctxs.push_back(c);
-    if (!(c->d2q9 && c->store == 0)) {
+    c->batched += 1;
+    if (!(c->d2q9 && c->store == 0 && c->scheme == DUGKS_T3S3)) {
       b->own.push_back(c);
       continue;
     }
@@ -1143,11 +1177,24 @@ int dugks_batch_step(dugks_batch* b, int nsteps) {
 int dugks_batch_destroy(dugks_batch* b) {
   if (!b) return DUGKS_OK;
   cudaStreamSynchronize(b->stream);
+  for (dugks_ctx* c : b->ctxs) c->batched -= 1;
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   if (b->items) cudaFree(b->items);
   if (b->tile_start) cudaFree(b->tile_start);
   if (b->counters) cudaFree(b->counters);
   delete b;
+  return DUGKS_OK;
+}
+
+int dugks_set_scheme(dugks_ctx* c, int scheme) {
+  if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  if (scheme < DUGKS_T3S3 || scheme > DUGKS_T2S2) return fail(DUGKS_EINVAL, "unknown scheme");
+  if (c->batched) return fail(DUGKS_EINVAL, "the context belongs to a batch");
+  if (scheme != DUGKS_T3S3 && c->store)
+    return fail(DUGKS_ENOTIMPL, "the T2 schemes run with DUGKS_FP64 storage");
+  c->scheme = scheme;
+  c->p.recon = scheme == DUGKS_T2S2 ? 1 : 0;
+  c->g1_valid = false;
   return DUGKS_OK;
 }
 

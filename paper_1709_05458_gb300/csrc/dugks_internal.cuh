@@ -37,6 +37,10 @@ enum KernelId {
   K_GDEV_WALLS,        // wall faces of both directions
   K_GDEV_UPDATE1,      // L*, f~(t'), accumulator
   K_GDEV_UPDATE2,      // L**, dt Omega', f^^{n+1}
+  K_T2_CELL,           // T2 schemes: moments, g = f-bar^{+,dt/2}
+  K_T2_FACE_X,
+  K_T2_FACE_Y,
+  K_T2_UPDATE,         // f~^{n+1} = f~^{+,n} + dt L
   K_NUM
 };
 
@@ -55,6 +59,7 @@ struct DevParams {
   int bc_kind[4];
   double uw_x[4], uw_y[4];
   double ds_den[4];             // -sum_{xi.n<0} (xi.n) W_k P(xi_k; u_w) per side
+  int recon;                    // face expansion: 0 quadratic (eq. flux_DS), 1 first order (T2S2)
 };
 
 // Per-stage scalar coefficients (host-computed once at init).
@@ -216,6 +221,9 @@ cudaError_t launch_update1(const DevParams& p, const double* fhat, const double*
 cudaError_t launch_update2(const DevParams& p, const double* ftp, const double* acc,
                            const double* mom, const double* fbx, const double* fby,
                            double* fhat, double c_om, cudaStream_t s);
+// T2 step update (Remark I): ft <- a ft + b feq(mom) + dt L
+cudaError_t launch_update_t2(const DevParams& p, const double* mom, const double* fbx,
+                            const double* fby, double* ft, double a, double b, cudaStream_t s);
 cudaError_t launch_set_eq(const DevParams& p, const double* rho, const double* ux,
                           const double* uy, double* fhat, cudaStream_t s);
 cudaError_t launch_check(const DevParams& p, const double* mom, int* flag, cudaStream_t s);

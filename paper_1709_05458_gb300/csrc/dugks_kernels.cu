@@ -70,7 +70,8 @@ __device__ __forceinline__ double g_at(const double* __restrict__ gk, const DevP
 
 // Quadratic Taylor expansion of g about the centre of cell (ci, cj), evaluated
 // at offset (dX, dY): value + d.grad + 1/2 d^T H d, derivatives by central
-// differences on the 3x3 neighbourhood (eq. flux_DS).
+// differences on the 3x3 neighbourhood (eq. flux_DS).  p.recon = 1: the
+// expansion stops after the gradient term (the T2S2 reconstruction).
 __device__ __forceinline__ double taylor(const double* __restrict__ gk, const DevParams& p,
                                          int ci, int cj, double dX, double dY) {
   double C, E, W, N, S, NE, NW, SE, SW;
@@ -90,6 +91,7 @@ __device__ __forceinline__ double taylor(const double* __restrict__ gk, const De
   }
   const double gx = (E - W) * (0.5 * p.inv_dx);
   const double gy = (N - S) * (0.5 * p.inv_dy);
+  if (p.recon) return C + dX * gx + dY * gy;   // first order (T2S2)
   const double gxx = (E - 2.0 * C + W) * (p.inv_dx * p.inv_dx);
   const double gyy = (N - 2.0 * C + S) * (p.inv_dy * p.inv_dy);
   const double gxy = (NE - NW - SE + SW) * (0.25 * p.inv_dx * p.inv_dy);
@@ -351,6 +353,26 @@ k_update2(DevParams p, const double* __restrict__ ftp, const double* __restrict_
   fhat[t] = fma(dt47, L, fma(c_om34, ftp[t] - feq, acc[t]));
 }
 
+// T2 step (Remark I, eq. feqIntD2nd_Explicit):
+// f~^{n+1} = ((2 tau - dt) f~ + 2 dt feq) / (2 tau + dt) + dt L(t_n + dt/2)
+__global__ void __launch_bounds__(kThreads)
+k_update_t2(DevParams p, const double* __restrict__ mom, const double* __restrict__ fbx,
+            const double* __restrict__ fby, double* __restrict__ ft, double a, double b) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t total = (size_t)p.nv * p.N;
+  if (t >= total) return;
+  const int k = (int)(t / p.N);
+  const int cell = (int)(t - (size_t)k * p.N);
+  const int j = cell / p.nx, i = cell - j * p.nx;
+  const double L = microflux(p, fbx, fby, k, i, j);
+  const double rho = mom[cell], ux = mom[p.N + cell], uy = mom[2 * p.N + cell];
+  const double vx = ux * p.inv_RT, vy = uy * p.inv_RT;
+  const double e = fma(__ldg(p.xi_x + k), vx, __ldg(p.xi_y + k) * vy);
+  const double P = fma(e, fma(0.5, e, 1.0), 1.0 - 0.5 * fma(ux, vx, uy * vy));
+  const double feq = __ldg(p.w + k) * rho * P;
+  ft[t] = fma(p.dt, L, fma(a, ft[t], b * feq));
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_set_eq(DevParams p, const double* __restrict__ rho, const double* __restrict__ ux,
          const double* __restrict__ uy, double* __restrict__ fhat) {
@@ -419,6 +441,13 @@ cudaError_t launch_update1(const DevParams& p, const double* fhat, const double*
   const size_t n = (size_t)p.nv * p.N;
   k_update1<<<blocks_for(n), kThreads, 0, s>>>(p, fhat, g1, fbx, fby, ftp, acc, p.dt / 3.0,
                                                3.0 * p.dt / 7.0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_t2(const DevParams& p, const double* mom, const double* fbx,
+                            const double* fby, double* ft, double a, double b, cudaStream_t s) {
+  const size_t n = (size_t)p.nv * p.N;
+  k_update_t2<<<blocks_for(n), kThreads, 0, s>>>(p, mom, fbx, fby, ft, a, b);
   return cudaGetLastError();
 }
 

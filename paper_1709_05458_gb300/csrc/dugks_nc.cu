@@ -58,6 +58,19 @@ __device__ __forceinline__ void taylor9(double a, double b, double (&T)[9]) {
   T[6] = -ab;                 T[7] = 0.5 * (b * b + b); T[8] = ab;
 }
 
+// the expansion's weights: quadratic (eq. flux_DS), or stopped after the
+// gradient term when p.recon = 1 (the T2S2 reconstruction)
+__device__ __forceinline__ void weights9(const DevParams& p, double a, double b,
+                                         double (&T)[9]) {
+  if (p.recon) {
+    T[0] = 0.0;      T[1] = -0.5 * b; T[2] = 0.0;
+    T[3] = -0.5 * a; T[4] = 1.0;      T[5] = 0.5 * a;
+    T[6] = 0.0;      T[7] = 0.5 * b;  T[8] = 0.0;
+  } else {
+    taylor9(a, b, T);
+  }
+}
+
 // Pass 1.  DIR 0: x-faces (lanes over fi, rows j); DIR 1: y-faces (lanes
 // over i, rows fj).  part[chunk][3][nf]: partial face moments of the chunk.
 template <int DIR>
@@ -105,12 +118,12 @@ k_nc_faces1(DevParams p, const double* __restrict__ g, double* __restrict__ fb,
     const bool lo = cn >= 0.0, hi = cn <= 0.0;     // uniform across the warp
     if (DIR == 0) {
       const double b = -cy * h * p.inv_dy;
-      if (lo) taylor9((0.5 * p.dx - cx * h) * p.inv_dx, b, TL);
-      if (hi) taylor9((-0.5 * p.dx - cx * h) * p.inv_dx, b, TU);
+      if (lo) weights9(p, (0.5 * p.dx - cx * h) * p.inv_dx, b, TL);
+      if (hi) weights9(p, (-0.5 * p.dx - cx * h) * p.inv_dx, b, TU);
     } else {
       const double a = -cx * h * p.inv_dx;
-      if (lo) taylor9(a, (0.5 * p.dy - cy * h) * p.inv_dy, TL);
-      if (hi) taylor9(a, (-0.5 * p.dy - cy * h) * p.inv_dy, TU);
+      if (lo) weights9(p, a, (0.5 * p.dy - cy * h) * p.inv_dy, TL);
+      if (hi) weights9(p, a, (-0.5 * p.dy - cy * h) * p.inv_dy, TU);
     }
     const double* gk = g + (size_t)k * p.N;
     __syncwarp();

@@ -82,3 +82,9 @@ def test_product_velocity_sets_match_oracle():
     a, b = PV.d2q9(0.4), V.d2q9(0.4)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_set_scheme_needs_a_context(lib):
+    with pytest.raises(P.DugksError) as e:
+        P.dugks_set_scheme(None, P.T2S2)
+    assert e.value.code == P.DUGKS_EINVAL
