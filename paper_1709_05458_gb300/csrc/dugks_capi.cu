@@ -779,6 +779,9 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     for (int k = 0; k < 9; ++k) q.W[k] = vel->w[k];
     q.c3 = cd * cd / vel->RT;
     q.base_div = 0.5 / q.c3;
+    q.half_mb = 0.5 - q.base_div;
+    q.wsym = vel->w[1] == vel->w[3] && vel->w[1] == vel->w[5] && vel->w[1] == vel->w[7] &&
+             vel->w[0] == vel->w[2] && vel->w[0] == vel->w[6] && vel->w[0] == vel->w[8];
     q.c_over_RT = cd / vel->RT;
     q.c = cd;
     q.a1 = c->s1.a;

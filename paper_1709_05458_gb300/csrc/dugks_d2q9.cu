@@ -23,6 +23,9 @@
 // pattern of those weights is fixed at compile time per velocity.  The face
 // value is kept as f/alpha = f-bar + gamma feq (alpha is folded into the
 // flux scale), and equilibria use P = B +- e with B = base + e^2/2.
+#include <type_traits>
+
+#include "dugks_fp.cuh"
 #include "dugks_internal.cuh"
 
 namespace dugks {
@@ -75,19 +78,62 @@ __device__ __forceinline__ double yface_val(const double* __restrict__ s, const 
 }
 
 // Equilibrium polynomials P_k = 1 + e + e^2/2 - |ut|^2 base_div for the nine
-// velocities, e = ex ut_x + ey ut_y, with the pair form P(+-e) = B +- e.
-__device__ __forceinline__ void d2q9_poly(double utx, double uty, double base_div, double (&P)[9]) {
-  const double base = 1.0 - fma(utx, utx, uty * uty) * base_div;
-  const double bx = fma(0.5 * utx, utx, base);
-  const double by = fma(0.5 * uty, uty, base);
+// velocities, e = ex ut_x + ey ut_y, in the pair form P(+-e) = B +- e with
+// the B of the four velocity pairs from uu = |ut|^2, xx = ut_x^2 and
+// p = ut_x ut_y:  B_x = base + xx/2, B_y = base + (uu - xx)/2,
+// B_(+-1,+-1) = base + uu/2 + p, B_(+-1,-+1) = base + uu/2 - p.
+__device__ __forceinline__ void d2q9_poly(double utx, double uty, const D2Q9Params& Q,
+                                          double (&P)[9]) {
+  const double xx = utx * utx;
+  const double uu = fma(uty, uty, xx);
+  const double base = fma(uu, -Q.base_div, 1.0);
+  const double bh = fma(uu, Q.half_mb, 1.0);            // base + uu/2
+  const double pxy = utx * uty;
+  const double bx = fma(0.5, xx, base);
+  const double by = fma(-0.5, xx, bh);
+  const double bs = bh + pxy, bd = bh - pxy;
   const double sp = utx + uty, sm = utx - uty;
-  const double bs = fma(0.5 * sp, sp, base);
-  const double bd = fma(0.5 * sm, sm, base);
   P[4] = base;
   P[7] = bx + utx;  P[1] = bx - utx;          // (+-1, 0)
   P[5] = by + uty;  P[3] = by - uty;          // (0, +-1)
   P[8] = bs + sp;   P[0] = bs - sp;           // (+1,+1), (-1,-1)
   P[6] = bd + sm;   P[2] = bd - sm;           // (+1,-1), (-1,+1)
+}
+
+// s W_k of velocity K.  WS: the weights depend only on |e_k|^2 (rest,
+// axis, diagonal), and ws = (s W_rest, s W_axis, s W_diagonal) precomputed;
+// otherwise one product per velocity.
+template <bool WS, int K>
+__device__ __forceinline__ double wk(const D2Q9Params& P, double s, const double (&ws)[3]) {
+  if constexpr (WS) return K == 4 ? ws[0] : ((K & 1) ? ws[1] : ws[2]);
+  else return s * P.W[K];
+}
+template <bool WS>
+__device__ __forceinline__ void wclasses(const D2Q9Params& P, double s, double (&ws)[3]) {
+  if constexpr (WS) {
+    ws[0] = s * P.W[4];
+    ws[1] = s * P.W[1];
+    ws[2] = s * P.W[0];
+  } else {
+    ws[0] = ws[1] = ws[2] = 0.0;
+  }
+}
+
+// unrolled loop over the nine velocities with a compile-time index
+template <int K = 0, typename F>
+__device__ __forceinline__ void for9(F&& f) {
+  if constexpr (K < 9) {
+    f(std::integral_constant<int, K>{});
+    for9<K + 1>(f);
+  }
+}
+
+// ut = c u / RT from the sums: (c^2/RT) (sx, sy) / rho
+__device__ __forceinline__ void d2q9_ut(double rho, double sx, double sy, const D2Q9Params& P,
+                                        double& utx, double& uty) {
+  const double rc = P.c3 * rcp_fast(rho);
+  utx = sx * rc;
+  uty = sy * rc;
 }
 
 // rho, sx = sum_{ex=1} f - sum_{ex=-1} f, sy likewise
@@ -100,17 +146,21 @@ __device__ __forceinline__ void d2q9_sums(const double (&f)[9], double& rho, dou
 }
 
 // f/alpha = f-bar + gamma feq(moments of f-bar) for one face, in place
+template <bool WS>
 __device__ __forceinline__ void face_recover(double (&fb)[9], const D2Q9Stage& S,
                                              const D2Q9Params& P) {
   double rho, sx, sy;
   d2q9_sums(fb, rho, sx, sy);
-  const double rinv = 1.0 / rho;
-  const double utx = P.c3 * sx * rinv, uty = P.c3 * sy * rinv;
-  double Pk[9];
-  d2q9_poly(utx, uty, P.base_div, Pk);
+  double utx, uty;
+  d2q9_ut(rho, sx, sy, P, utx, uty);
+  double Pk[9], ws[3];
+  d2q9_poly(utx, uty, P, Pk);
   const double gr = S.gamma * rho;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) fb[k] = fma(gr * P.W[k], Pk[k], fb[k]);
+  wclasses<WS>(P, gr, ws);
+  for9([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    fb[k] = fma(wk<WS, k>(P, gr, ws), Pk[k], fb[k]);
+  });
 }
 
 // Resolve a (possibly ghost) cell to a combination of interior cells:
@@ -133,7 +183,7 @@ __device__ __forceinline__ int resolve1(int x, int n, bool per, int (&i)[3], dou
 // ---------------------------------------------------------------- kernel
 // One 32 x P.ty tile of one stage (all phases); every thread of the block
 // takes part (blockDim.x >= 32 (P.ty + 1)).
-template <int STAGE>
+template <int STAGE, bool WS>
 __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& S,
                                           const double* __restrict__ gin,
                                           const double* __restrict__ own,
@@ -228,7 +278,7 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
 #pragma unroll
       for (int k = 0; k < 9; ++k) fb[k] = fw[k];
     }
-    face_recover(fb, S, P);
+    face_recover<WS>(fb, S, P);
 #pragma unroll
     for (int k = 0; k < 9; ++k) sfx[(k * TY + r) * (TX + 1) + fc] = fb[k];
   }
@@ -287,7 +337,7 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
 #pragma unroll
       for (int k = 0; k < 9; ++k) fb[k] = fw[k];
     }
-    face_recover(fb, S, P);
+    face_recover<WS>(fb, S, P);
 #pragma unroll
     for (int k = 0; k < 9; ++k) sfy[(k * (TY + 1) + fr) * TX + c] = fb[k];
   }
@@ -314,29 +364,36 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
     }
     if (STAGE == 1) {
       // L[k] = dt/3 L*.  f~' = 5/4 g1 - 1/4 f^ + dt/3 L*;  X0 = 1/4 f^ + 3/4 g1 + 3dt/7 L*
+      // X0 = f^+ + 3dt/7 L* with L* written through f~' (dt/3 L* = f~' -
+      // 5/4 g1 + 1/4 f^):  X0 = r37 f~' + Xg,  Xg = (3/4 - 5/4 r37) g1 +
+      // (1/4 + 1/4 r37) f^;  the r37 f~' part joins the c_om34 f~' term below
+      const double cg = 0.75 - 1.25 * P.r37, cf = 0.25 + 0.25 * P.r37;
+      const double cft = P.c_om34 + P.r37;
       double ft[9], X[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         const double g1 = sg[(k * SH + r + HALO) * SW + c + HALO];
         const double fh = __ldg(own + (size_t)k * N + cell);
         ft[k] = fma(1.25, g1, fma(-0.25, fh, L[k]));
-        X[k] = fma(0.25, fh, fma(0.75, g1, P.r37 * L[k]));
+        X[k] = fma(cf, fh, cg * g1);
       }
       double rho, sx, sy;
       d2q9_sums(ft, rho, sx, sy);
-      const double rinv = 1.0 / rho;
-      double Pk[9];
-      d2q9_poly(P.c3 * sx * rinv, P.c3 * sy * rinv, P.base_div, Pk);
+      double utx, uty;
+      d2q9_ut(rho, sx, sy, P, utx, uty);
+      double Pk[9], rcw[3], rbw[3];
+      d2q9_poly(utx, uty, P, Pk);
       // X += 3/4 dt Omega' = c_om34 (f~' - feq');  g2 = a2 f~' + b2 feq'
-      const double rc = P.c_om34 * rho, rb = P.b2 * rho;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        const double q = P.W[k] * Pk[k];
-        const double xk = fma(P.c_om34, ft[k], fma(-rc, q, X[k]));
-        const double g2 = fma(rb, q, P.a2 * ft[k]);
+      const double rc = -P.c_om34 * rho, rb = P.b2 * rho;
+      wclasses<WS>(P, rc, rcw);
+      wclasses<WS>(P, rb, rbw);
+      for9([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const double xk = fma(cft, ft[k], fma(wk<WS, k>(P, rc, rcw), Pk[k], X[k]));
+        const double g2 = fma(wk<WS, k>(P, rb, rbw), Pk[k], P.a2 * ft[k]);
         out0[(size_t)k * N + cell] = g2;
         out1[(size_t)k * N + cell] = xk;
-      }
+      });
       rho_out[cell] = rho;
     } else {
       // L[k] = 4dt/7 L**.  f^^{n+1} = X + 4dt/7 L**; then g1 of the next step
@@ -345,29 +402,31 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
       for (int k = 0; k < 9; ++k) fh[k] = __ldg(own + (size_t)k * N + cell) + L[k];
       double rho, sx, sy;
       d2q9_sums(fh, rho, sx, sy);
-      const double rinv = 1.0 / rho;
-      double Pk[9];
-      d2q9_poly(P.c3 * sx * rinv, P.c3 * sy * rinv, P.base_div, Pk);
+      double utx, uty;
+      d2q9_ut(rho, sx, sy, P, utx, uty);
+      double Pk[9], rbw[3];
+      d2q9_poly(utx, uty, P, Pk);
       const double rb = P.b1 * rho;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        const double g1 = fma(rb, P.W[k] * Pk[k], P.a1 * fh[k]);
+      wclasses<WS>(P, rb, rbw);
+      for9([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        const double g1 = fma(wk<WS, k>(P, rb, rbw), Pk[k], P.a1 * fh[k]);
         out0[(size_t)k * N + cell] = fh[k];
         out1[(size_t)k * N + cell] = g1;
-      }
+      });
       rho_out[cell] = rho;
     }
   }
 }
 
-template <int STAGE>
+template <int STAGE, bool WS>
 __global__ void __launch_bounds__(kMaxThreads)
 k_d2q9(D2Q9Params P, D2Q9Stage S, const double* __restrict__ gin,
        const double* __restrict__ own, const double* __restrict__ rho_in,
        double* __restrict__ out0, double* __restrict__ out1, double* __restrict__ rho_out) {
   extern __shared__ double smem[];
-  d2q9_tile<STAGE>(P, S, gin, own, rho_in, out0, out1, rho_out, blockIdx.x * TX,
-                   blockIdx.y * P.ty, smem);
+  d2q9_tile<STAGE, WS>(P, S, gin, own, rho_in, out0, out1, rho_out, blockIdx.x * TX,
+                       blockIdx.y * P.ty, smem);
 }
 
 // Persistent batched stage kernel: blocks take (instance, tile) work items
@@ -400,9 +459,11 @@ k_d2q9_batch(const D2Q9BatchItem* __restrict__ items, const int* __restrict__ ti
     const int local = t - tile_start[it];
     const int bx = local % I.tiles_x, by = local / I.tiles_x;
     if constexpr (STAGE == 1)
-      d2q9_tile<1>(I.P, I.S1, I.g1, I.fhat, I.mom, I.g2, I.X, I.mom + I.P.N, bx * TX, by * I.P.ty, smem);
+      d2q9_tile<1, false>(I.P, I.S1, I.g1, I.fhat, I.mom, I.g2, I.X, I.mom + I.P.N, bx * TX,
+                          by * I.P.ty, smem);
     else
-      d2q9_tile<2>(I.P, I.S2, I.g2, I.X, I.mom + I.P.N, I.fhat, I.g1, I.mom, bx * TX, by * I.P.ty, smem);
+      d2q9_tile<2, false>(I.P, I.S2, I.g2, I.X, I.mom + I.P.N, I.fhat, I.g1, I.mom, bx * TX,
+                          by * I.P.ty, smem);
     __syncthreads();
   }
 }
@@ -418,9 +479,13 @@ cudaError_t d2q9_prepare(int ty) {
   // contexts with different tile heights can coexist
   (void)ty;
   const int bytes = (int)d2q9_smem_bytes(kMaxTY);
-  cudaError_t e = cudaFuncSetAttribute(k_d2q9<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(k_d2q9<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_d2q9<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    e = cudaFuncSetAttribute(k_d2q9<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_d2q9<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_d2q9<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_d2q9_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -451,10 +516,17 @@ cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + p.ty - 1) / p.ty);
   const int threads = TX * (p.ty + 1);
   const size_t bytes = d2q9_smem_bytes(p.ty);
-  if (stage == 1)
-    k_d2q9<1><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
-  else
-    k_d2q9<2><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
+  if (p.wsym) {
+    if (stage == 1)
+      k_d2q9<1, true><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
+    else
+      k_d2q9<2, true><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
+  } else {
+    if (stage == 1)
+      k_d2q9<1, false><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
+    else
+      k_d2q9<2, false><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
+  }
   return cudaGetLastError();
 }
 

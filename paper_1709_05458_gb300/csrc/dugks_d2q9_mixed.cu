@@ -17,6 +17,7 @@
 
 #include <cmath>
 
+#include "dugks_fp.cuh"
 #include "dugks_internal.cuh"
 
 namespace dugks {
@@ -88,35 +89,6 @@ __device__ __forceinline__ float yface_valf(const float* __restrict__ s, const D
   return wdotf<q0, q1, c0, c1, 3>(s, &S.wy[K][0][0]);
 }
 
-// Exact FP32 -> FP64 conversion with integer operations.  GB300 executes the
-// F2F conversion instructions on its FP64 pipe (2 per SM per clock), the
-// same pipe the moment sums need; the bit manipulation runs on the integer
-// pipe instead.  Zero and FP32 denormals map to 0, inf/NaN stay inf/NaN.
-__device__ __forceinline__ double f2d_bits(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned em = b & 0x7fffffffu;
-  unsigned hi = (em >> 3) + 0x38000000u;          // exponent rebias 127 -> 1023
-  unsigned lo = em << 29;
-  hi = (em >= 0x7f800000u) ? (0x7ff00000u | ((em & 0x7fffffu) >> 3)) : hi;
-  const bool tiny = em < 0x00800000u;
-  hi = tiny ? 0u : hi;
-  lo = tiny ? 0u : lo;
-  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
-}
-
-// FP64 -> FP32 with round-to-nearest (ties away) by integer operations, for
-// normal values in FP32 range (the equilibrium parameters); values below the
-// FP32 normal range map to 0, NaN, inf and values beyond the FP32 range to
-// NaN (so that a flagged moment reaches the state and dugks_check).
-__device__ __forceinline__ float d2f_bits(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const int E = (int)((hi >> 20) & 0x7ffu) - 896;
-  unsigned mag = ((unsigned)E << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  mag += (lo >> 28) & 1u;
-  mag = (E <= 0) ? 0u : mag;
-  mag = (E >= 255) ? 0x7fc00000u : mag;
-  return __uint_as_float(mag | (hi & 0x80000000u));
-}
 
 // FP32 value -> signed fixed point with 56 fraction bits (resolution
 // 1.4e-17, comparable to the FP64 rounding of O(0.1) terms).  `bad` is set
@@ -165,17 +137,6 @@ __device__ __forceinline__ void dev_sums(const float (&d)[9], const MixedConst& 
   sy = fix2d(y + M.fsyW);
 }
 
-// 1/x for x in the FP32 normal range: FP32 seed (rcp.approx, integer-pipe
-// conversions) and two FP64 Newton steps, error ~2^-92 before rounding.
-__device__ __forceinline__ double rcp64(double x) {
-  float sf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(sf) : "f"(d2f_bits(x)));
-  double r = f2d_bits(sf);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
 
 // Equilibrium deviations W_k (rho P_k - rho0) from FP64 moments: u/RT and the
 // constant part in FP64, per-velocity assembly in FP32.

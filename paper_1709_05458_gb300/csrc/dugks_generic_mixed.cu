@@ -28,6 +28,7 @@
 // with aligned 16-byte asynchronous copies and no boundary logic.
 #include <cuda_bf16.h>
 
+#include "dugks_fp.cuh"
 #include "dugks_internal.cuh"
 
 namespace dugks {
@@ -68,31 +69,9 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// exact FP32 -> FP64 on the integer pipe; zero and denormals -> 0, inf and
-// NaN kept
-__device__ __forceinline__ double f2d(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned em = b & 0x7fffffffu;
-  unsigned hi = (em >> 3) + 0x38000000u;
-  unsigned lo = em << 29;
-  hi = (em >= 0x7f800000u) ? (0x7ff00000u | ((em & 0x7fffffu) >> 3)) : hi;
-  const bool tiny = em < 0x00800000u;
-  hi = tiny ? 0u : hi;
-  lo = tiny ? 0u : lo;
-  return __hiloint2double((int)(hi | (b & 0x80000000u)), (int)lo);
-}
-
-// FP64 -> FP32, round half up on the magnitude, on the integer pipe; values
-// below the FP32 normal range -> 0; NaN, inf and overflow -> NaN
-__device__ __forceinline__ float d2f(double x) {
-  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-  const int E = (int)((hi >> 20) & 0x7ffu) - 896;
-  unsigned mag = ((unsigned)E << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
-  mag += (lo >> 28) & 1u;
-  mag = (E <= 0) ? 0u : mag;
-  mag = (E >= 255) ? 0x7fc00000u : mag;
-  return __uint_as_float(mag | (hi & 0x80000000u));
-}
+// FP32 <-> FP64 conversions on the integer pipe (dugks_fp.cuh)
+__device__ __forceinline__ double f2d(float x) { return f2d_bits(x); }
+__device__ __forceinline__ float d2f(double x) { return d2f_bits(x); }
 
 // ---- compensated FP32-pair accumulation (error-free transformations) ----
 // s = hi + lo.  add: TwoSum(hi, x), the rounding error goes to lo.

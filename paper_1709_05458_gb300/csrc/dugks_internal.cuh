@@ -93,6 +93,8 @@ struct D2Q9Params {
   double W[9];
   double c3;                  // c^2/RT (= 3 for the Gauss-Hermite set)
   double base_div;            // RT / c^2 / 2 ... |u|^2/(2RT) = (ut_x^2 + ut_y^2) * base_div
+  double half_mb;             // 1/2 - base_div
+  int wsym;                   // W_k depends only on |e_k|^2 (W[1] = W[3] = W[5] = W[7], corners equal)
   double c_over_RT;           // c / RT: ut = c u / RT
   double c;                   // lattice speed: xi = c (ex, ey)
   double a1, b1, a2, b2;      // g1 = a1 f^ + b1 feq, g2 = a2 f~' + b2 feq'
