@@ -79,8 +79,8 @@ BYTES_PER_UNIT = {
 # from profiles/d2q9_stage_kernels_cavity1024.md (1024^2 capture, scaled to
 # a launch by the units it processes); kept only while the kernel is unchanged.
 TRAFFIC_BYTES_PER_UNIT = {
-    "d2q9_stage1": (151.361536e6 + 114.549504e6) / (1024 * 1024 * 9),
-    "d2q9_stage2": (151.355904e6 + 115.911424e6) / (1024 * 1024 * 9),
+    "d2q9_stage1": (151.407104e6 + 114.269952e6) / (1024 * 1024 * 9),
+    "d2q9_stage2": (151.355392e6 + 115.520256e6) / (1024 * 1024 * 9),
 }
 
 
