@@ -57,6 +57,14 @@ FLOPS_PER_UNIT = {
     "t2_cell": 17, "t2_face_x": 34, "t2_face_y": 34, "t2_update": 19,
 }
 SCHEMES = {"t3s3": 0, "t2s3": 1, "t2s2": 2}
+# The same kernels in FP64 (dugks_generic_mixed.cu with FP64 storage): all
+# their arithmetic is FP64 -- cell: moment sums 5 + g from the equilibrium
+# quadratic 12; face: 9-point stencil 18 + moment sums 5; updates: the
+# cubic equilibrium term 20 + face differences 5 + the stage maps 10 / 5.
+FLOPS_PER_UNIT_GDEV_FP64 = {
+    "gdev_cell": 17, "gdev_face_x": 23, "gdev_face_y": 23,
+    "gdev_update_stage1": 35, "gdev_update_stage2": 30,
+}
 # Kernels bound by HBM instead: algorithmic bytes per cell-velocity by
 # storage form (FP32 / BF16 per-cell arrays; face values are FP32 in both).
 HBM_BYTES_PER_UNIT = {
@@ -408,8 +416,14 @@ def run_ours(args):
     e2e = units * e2e_steps * world / e2e_s / 1e9 if e2e_steps else None
 
     # roofline of the dominant kernel (largest share of device time)
+    flops_per_unit = dict(FLOPS_PER_UNIT)
+    hbm_per_unit = dict(HBM_BYTES_PER_UNIT)
+    if args.storage == "fp64":
+        flops_per_unit.update(FLOPS_PER_UNIT_GDEV_FP64)
+        for k in FLOPS_PER_UNIT_GDEV_FP64:
+            hbm_per_unit.pop(k, None)
     name, (nl, kms) = max(((k, v) for k, v in prof.items()
-                           if (k in FLOPS_PER_UNIT or k in HBM_BYTES_PER_UNIT)
+                           if (k in flops_per_unit or k in hbm_per_unit)
                            and v[0] > 0 and v[1] > 0),
                           key=lambda kv: kv[1][1])
     nx, ny = c["nx"], c["ny"]
@@ -419,15 +433,15 @@ def run_ours(args):
     }.get(face, nv * nx * ny)
     # gdev face and cell entries cover both stages: two launches per step
     avg_s = kms * 1e-3 / max(nl, 1)
-    if name in HBM_BYTES_PER_UNIT:
+    if name in hbm_per_unit:
         bound, unit = "hbm", "GB/s"
-        achieved = HBM_BYTES_PER_UNIT[name][args.storage] * per_launch_units / avg_s / 1e9
+        achieved = hbm_per_unit[name][args.storage] * per_launch_units / avg_s / 1e9
         peak = measured_peaks().get("hbm_gbs", 6800.0)
         peak_source = ("measured copy bandwidth" if "hbm_gbs" in measured_peaks()
                        else "fallback 6.8 TB/s")
     else:
         bound, unit = "alu", "TFLOP/s"
-        achieved = FLOPS_PER_UNIT[name] * per_launch_units / avg_s / 1e12
+        achieved = flops_per_unit[name] * per_launch_units / avg_s / 1e12
         peak = fp64_peak_tflops()
         peak_source = "nominal FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"
     launches = sum(v[0] for k, v in prof.items())

@@ -82,10 +82,10 @@ struct dugks_ctx {
   // and the FP32 equilibrium parameters of the last cell pass ([5][N])
   bool gdev = false;
   GDevStep gs{};
-  float* eqp = nullptr;
-  float* vf = nullptr;          // FP32 velocity table (float4 rows [3][nv])
+  void* eqp = nullptr;
+  void* vf = nullptr;           // velocity table of that path (4-vector rows [3][nv])
   void* gpad = nullptr;         // padded stage field of that path
-  float* fpar = nullptr;        // face equilibrium parameters of that path
+  void* fpar = nullptr;         // face equilibrium parameters of that path
   // time scheme (dugks_set_scheme): 0 T3S3; 1 T2S3, 2 T2S2 on the generic
   // kernels with the T2 stage coefficients below
   int scheme = DUGKS_T3S3;
@@ -382,7 +382,8 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 int advance(dugks_ctx* c) {
   if (c->scheme != DUGKS_T3S3) return one_step_t2(c);
-  if (c->store) return c->gdev ? one_step_gdev(c) : one_step_d2q9m(c);
+  if (c->gdev) return one_step_gdev(c);
+  if (c->store) return one_step_d2q9m(c);
   return c->d2q9 ? one_step_d2q9(c) : one_step(c);
 }
 
@@ -675,19 +676,28 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
   const double cd = d2q9_speed(vel);
   const char* force = std::getenv("DUGKS_FORCE_GENERIC");
   const bool forced = force && force[0] == '1';
-  if (storage != DUGKS_FP64 && !(cd > 0.0 && !forced)) {
-    // deviation storage on the generic kernels (any velocity set)
+  // The optimised generic kernels (dugks_generic_mixed.cu) step every
+  // context that the fused D2Q9 kernels do not take: any velocity set, FP64
+  // or deviation storage.  DUGKS_LEGACY_GENERIC=1 keeps FP64 contexts on the
+  // first generic kernels (dugks_kernels.cu, dugks_nc.cu), which also run
+  // the T2 schemes.
+  const char* legacy = std::getenv("DUGKS_LEGACY_GENERIC");
+  const bool generic = !(cd > 0.0 && !forced);
+  if (generic && (storage != DUGKS_FP64 || !(legacy && legacy[0] == '1'))) {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const bool f64 = storage == DUGKS_FP64;
+    const double rho0 = f64 ? 0.0 : c->rho0;         // FP64: the arrays hold f itself
+    const size_t csz = f64 ? sizeof(double) : sizeof(float);   // compute type
     GDevStep& g = c->gs;
     g.p = c->p;
     g.store = storage;
-    g.ref.rho0 = c->rho0;
+    g.ref.rho0 = rho0;
     for (int k = 0; k < nv; ++k) {
-      g.ref.W += c->rho0 * vel->w[k];
-      g.ref.Wx += c->rho0 * vel->w[k] * vel->xi_x[k];
-      g.ref.Wy += c->rho0 * vel->w[k] * vel->xi_y[k];
+      g.ref.W += rho0 * vel->w[k];
+      g.ref.Wx += rho0 * vel->w[k] * vel->xi_x[k];
+      g.ref.Wy += rho0 * vel->w[k] * vel->xi_y[k];
     }
     for (int sd = 0; sd < 4; ++sd) {     // outgoing flux of the reference state per wall
       const double nxs = sd == DUGKS_WEST ? -1.0 : sd == DUGKS_EAST ? 1.0 : 0.0;
@@ -697,69 +707,76 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
         const double xn = vel->xi_x[k] * nxs + vel->xi_y[k] * nys;
         if (xn > 0.0) o += xn * vel->w[k];
       }
-      g.ds_out[sd] = c->rho0 * o;
+      g.ds_out[sd] = rho0 * o;
     }
     g.s1 = c->s1;
     g.s2 = c->s2;
     g.c_om = c->c_om;
-    g.nchx = gdev_chunks(p, 0, sms);
-    g.nchy = gdev_chunks(p, 1, sms);
+    e = gdev_prepare(storage);
+    g.nchx = gdev_chunks(p, 0, sms, storage);
+    g.nchy = gdev_chunks(p, 1, sms, storage);
     g.mch = nv > 32 ? 4 : 1;
-    // partial moments of this path's face and cell passes (the FP64 path's
-    // buffer, if any, is not used by it)
+    // partial moments: this path's face and cell passes and (FP64) the
+    // first generic kernels share one buffer, used at different times
     if (c->part) {
       cudaFree(c->part);
       c->part = nullptr;
     }
     const size_t nfmax = std::max((size_t)p.ny * (p.nx + 1), (size_t)(p.ny + 1) * p.nx);
-    const int pch = std::max(std::max(g.nchx, g.nchy), g.mch);
-    e = cudaMalloc((void**)&c->part, (size_t)pch * 3 * nfmax * sizeof(double));
+    const int pch = std::max(std::max(std::max(g.nchx, g.nchy), g.mch), std::max(c->nchx, c->nchy));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, (size_t)pch * 3 * nfmax * sizeof(double));
     g.pitch = gdev_pitch(p.nx);
     g.plane = (size_t)(p.ny + 4) * g.pitch;
-    if (e == cudaSuccess) e = cudaMalloc(&c->gpad, g.plane * nv * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->eqp, 5 * (size_t)p.N * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->fpar, 5 * 2 * nfmax * sizeof(float));
-    // FP32 velocity table, float4 rows [3][nv]: (xi_x hi, lo, xi_y hi, lo),
-    // (xi_x, xi_y, W_k, 0), (xi_x/dx, xi_y/dy, 0, 0); hi = xi rounded to
-    // FP32, lo = the FP32 rounding of the remainder
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->vf, 12 * (size_t)nv * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->gpad, g.plane * nv * csz);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->eqp, 5 * (size_t)p.N * csz);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->fpar, 5 * 2 * nfmax * csz);
+    // velocity table in the compute type, 4-vector rows [3][nv]:
+    // (xi_x hi, lo, xi_y hi, lo), (xi_x, xi_y, W_k, 0), (xi_x/dx, xi_y/dy, 0, 0);
+    // FP32: hi = xi rounded to FP32, lo = the FP32 rounding of the remainder;
+    // FP64: hi = xi, lo = 0
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->vf, 12 * (size_t)nv * csz);
     if (e == cudaSuccess) {
-      std::vector<float> t(12 * (size_t)nv, 0.f);
+      std::vector<double> t(12 * (size_t)nv, 0.0);
       for (int k = 0; k < nv; ++k) {
         const double x = vel->xi_x[k], y = vel->xi_y[k];
-        const float xh = (float)x, yh = (float)y;
-        float* r0 = t.data() + 4 * (size_t)k;
-        float* r1 = t.data() + 4 * ((size_t)nv + k);
-        float* r2 = t.data() + 4 * (2 * (size_t)nv + k);
+        const double xh = f64 ? x : (double)(float)x, yh = f64 ? y : (double)(float)y;
+        double* r0 = t.data() + 4 * (size_t)k;
+        double* r1 = t.data() + 4 * ((size_t)nv + k);
+        double* r2 = t.data() + 4 * (2 * (size_t)nv + k);
         r0[0] = xh;
-        r0[1] = (float)(x - (double)xh);
+        r0[1] = x - xh;
         r0[2] = yh;
-        r0[3] = (float)(y - (double)yh);
+        r0[3] = y - yh;
         r1[0] = xh;
         r1[1] = yh;
-        r1[2] = (float)vel->w[k];
-        r2[0] = (float)(x / mesh->dx);
-        r2[1] = (float)(y / mesh->dy);
+        r1[2] = vel->w[k];
+        r2[0] = x / mesh->dx;
+        r2[1] = y / mesh->dy;
       }
-      e = cudaMemcpy(c->vf, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice);
+      if (f64) {
+        e = cudaMemcpy(c->vf, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice);
+      } else {
+        std::vector<float> tf(t.begin(), t.end());
+        e = cudaMemcpy(c->vf, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
+      }
     }
     if (e != cudaSuccess) {
       free_all(c);
       delete c;
       cudaGetLastError();
       return fail(e == cudaErrorMemoryAllocation ? DUGKS_ENOMEM : DUGKS_ECUDA,
-                  std::string("device allocation: ") + cudaGetErrorString(e));
+                  std::string("generic path set-up: ") + cudaGetErrorString(e));
     }
     g.fhat = c->fhat;
     g.g = c->gpad;
     g.ftp = c->ftp;
     g.acc = c->acc;
-    g.fbx = (float*)c->fbx;
-    g.fby = (float*)c->fby;
+    g.fbx = c->fbx;
+    g.fby = c->fby;
     g.eqp = c->eqp;
     g.fpx = c->fpar;
-    g.fpy = c->fpar + 5 * nfmax;
-    g.vq = reinterpret_cast<const float4*>(c->vf);
+    g.fpy = (char*)c->fpar + 5 * nfmax * csz;
+    g.vq = c->vf;
     g.mom = c->mom;
     g.part = c->part;
     c->store = storage;

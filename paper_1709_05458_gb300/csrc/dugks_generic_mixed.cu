@@ -1,23 +1,26 @@
-// Deviation-storage (FP32 / BF16) form of the generic path: any velocity
-// set (Newton-Cotes grids in particular), periodic / bounce-back / diffuse
-// walls.  Same step structure as the FP64 generic path:
-//   cell(stage) -> ghosts -> faces x, y (interior slab kernels + wall
-//   faces) -> update.
-// Every per-(cell, velocity) array holds d = f - W_k rho0; face values are
-// FP32 deviations.  Stencils, fluxes, the stage transforms and the
-// per-velocity equilibrium assembly W_k((rho - rho0) + rho (P_k - 1)) run in
-// FP32.  The moment sums of every cell and face (Sec. 2.2) are carried per
-// thread as unevaluated FP32 pairs (hi + lo) updated by error-free
-// transformations -- TwoSum for each term, and the exact FMA residual of
-// xi_hi d plus xi_lo d for the momentum, xi = xi_hi + xi_lo -- so a partial
-// sum keeps ~48 significant bits; the partials are combined across threads,
-// warps and velocity chunks in FP64, and rho, u/RT and |u|^2/(2RT) are FP64
-// before they are rounded for the assembly (Sec. 2.1.1 equilibrium).  No
-// FP64 arithmetic or FP64<->FP32 conversion sits in an inner loop: GB300 runs
-// both on its 2-lane-per-clock FP64 pipe.  The maps of the step (eqs.
-// f_bar_1_6, fbp_5_12, recover2f, f_tilde_1_3, fhp, feqIntD3rdHat2_DS) are
-// affine with coefficients summing to one and the flux divergence of a
-// uniform field vanishes, so they act on deviations unchanged.
+// Optimised generic path of the T3S3 step for any velocity set (Newton-Cotes
+// grids in particular), periodic / bounce-back / diffuse walls, in three
+// storage forms: FP64, and the FP32 / BF16 deviation forms.  Per stage:
+//   cell pass -> ghosts -> interior faces x, y (stencils + face moments)
+//   -> face parameters -> wall faces -> update.
+//
+// Storage T and compute type C: T = double computes in FP64 (plain FP64
+// sums; reference density rho0 = 0, so the arrays hold f itself).  T =
+// float / bf16 hold the deviation d = f - W_k rho0 and compute stencils,
+// face values, stage transforms and the per-velocity equilibrium assembly
+// W_k((rho - rho0) + rho (P_k - 1)) in FP32; their moment sums (Sec. 2.2)
+// are carried per thread as unevaluated FP32 pairs (hi + lo) updated by
+// error-free transformations -- TwoSum for each term, and the exact FMA
+// residual of xi_hi d plus xi_lo d for the momentum, xi = xi_hi + xi_lo -- so
+// a partial keeps ~48 significant bits; partials are combined across
+// threads, warps and velocity chunks in FP64, and rho, u/RT and |u|^2/(2RT)
+// are FP64 before they are rounded for the assembly (Sec. 2.1.1
+// equilibrium).  No FP64 arithmetic or conversion sits in an inner loop of
+// the FP32 forms: GB300 runs both on its 2-lane-per-clock FP64 pipe.  The
+// maps of the step (eqs. f_bar_1_6, fbp_5_12, recover2f, f_tilde_1_3, fhp,
+// feqIntD3rdHat2_DS) are affine with coefficients summing to one and the
+// flux divergence of a uniform field vanishes, so they act on deviations
+// unchanged.
 //
 // The stage field g = f-bar^{+,h} lives in a padded layout
 // g[k][ny + 4][pitch], cell (i, j) at row j + 2, column i + 2, with two
@@ -38,20 +41,26 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int NW = 8, R = 8, LANES = 32;
 
-template <typename T> __device__ __forceinline__ float ldv(const T* p);
-template <> __device__ __forceinline__ float ldv<float>(const float* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float ldv<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(__ldg(p));
-}
-template <typename T> __device__ __forceinline__ float lds(const T* p);
-template <> __device__ __forceinline__ float lds<float>(const float* p) { return *p; }
-template <> __device__ __forceinline__ float lds<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(*p);
-}
-template <typename T> __device__ __forceinline__ void stv(T* p, float v);
-template <> __device__ __forceinline__ void stv<float>(float* p, float v) { *p = v; }
-template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16* p, float v) {
-  *p = __float2bfloat16_rn(v);
+// ------------------------------------------------------------ precision
+struct __align__(16) D4 {
+  double x, y, z, w;
+};
+template <typename T> struct Prec {            // FP32 and BF16 storage
+  using C = float;
+  using V4 = float4;
+  static constexpr int KH = 8;                  // loads in flight per batch in the updates
+};
+template <> struct Prec<double> {
+  using C = double;
+  using V4 = D4;
+  static constexpr int KH = 4;
+};
+
+__device__ __forceinline__ float4 ld4(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ D4 ld4(const D4* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return D4{a.x, a.y, b.x, b.y};
 }
 
 // raw loads (no conversion), so a batch of loads is issued before the
@@ -59,6 +68,21 @@ template <> __device__ __forceinline__ void stv<__nv_bfloat16>(__nv_bfloat16* p,
 template <typename T> __device__ __forceinline__ T ldr(const T* p) { return __ldg(p); }
 __device__ __forceinline__ float tof(float v) { return v; }
 __device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double tof(double v) { return v; }
+template <typename T> __device__ __forceinline__ auto ldv(const T* p) { return tof(__ldg(p)); }
+template <typename T> __device__ __forceinline__ auto lds(const T* p) { return tof(*p); }
+__device__ __forceinline__ void stv(float* p, float v) { *p = v; }
+__device__ __forceinline__ void stv(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void stv(double* p, double v) { *p = v; }
+
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+
+// FP64 -> C (FP32 on the integer pipe) and C -> FP64
+template <typename C> __device__ __forceinline__ C to_c(double x);
+template <> __device__ __forceinline__ float to_c<float>(double x) { return d2f_bits(x); }
+template <> __device__ __forceinline__ double to_c<double>(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return f2d_bits(x); }
 
 // asynchronous 16-byte global -> shared copy (bypassing L1) and its groups
 __device__ __forceinline__ void cp16(void* smem_dst, const void* gsrc) {
@@ -69,25 +93,26 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// FP32 <-> FP64 conversions on the integer pipe (dugks_fp.cuh)
-__device__ __forceinline__ double f2d(float x) { return f2d_bits(x); }
-__device__ __forceinline__ float d2f(double x) { return d2f_bits(x); }
-
-// ---- compensated FP32-pair accumulation (error-free transformations) ----
-// s = hi + lo.  add: TwoSum(hi, x), the rounding error goes to lo.
-// addprod: x (ah + al) with ah x split exactly into p + pe by an FMA.  The
-// _rn intrinsics keep the compiler from contracting or reassociating.
-struct Acc {
+// ---- moment accumulators ----
+// FP32: compensated pair s = hi + lo (error-free transformations).  add:
+// TwoSum(hi, x), the rounding error goes to lo; addprod: x (ah + al) with
+// ah x split exactly into p + pe by an FMA.  The _rn intrinsics keep the
+// compiler from contracting or reassociating.  FP64: a plain sum (al = 0).
+template <typename C> struct Acc;
+template <> struct Acc<float> {
   float hi, lo;
 };
-__device__ __forceinline__ void acc_add(Acc& a, float x) {
+template <> struct Acc<double> {
+  double s;
+};
+__device__ __forceinline__ void acc_add(Acc<float>& a, float x) {
   const float s = __fadd_rn(a.hi, x);
   const float bp = __fsub_rn(s, a.hi);
   const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
   a.hi = s;
   a.lo = __fadd_rn(a.lo, e);
 }
-__device__ __forceinline__ void acc_addprod(Acc& a, float ah, float al, float x) {
+__device__ __forceinline__ void acc_addprod(Acc<float>& a, float ah, float al, float x) {
   const float p = __fmul_rn(ah, x);
   const float pe = __fmaf_rn(ah, x, -p);
   const float s = __fadd_rn(a.hi, p);
@@ -96,35 +121,74 @@ __device__ __forceinline__ void acc_addprod(Acc& a, float ah, float al, float x)
   a.hi = s;
   a.lo = __fadd_rn(a.lo, __fadd_rn(e, __fmaf_rn(al, x, pe)));
 }
-__device__ __forceinline__ double acc_value(const Acc& a) { return f2d(a.hi) + f2d(a.lo); }
+__device__ __forceinline__ double acc_value(const Acc<float>& a) {
+  return to_d(a.hi) + to_d(a.lo);
+}
+__device__ __forceinline__ void acc_add(Acc<double>& a, double x) { a.s += x; }
+__device__ __forceinline__ void acc_addprod(Acc<double>& a, double ah, double, double x) {
+  a.s = fma(ah, x, a.s);
+}
+__device__ __forceinline__ double acc_value(const Acc<double>& a) { return a.s; }
 
-// FP32 equilibrium-assembly parameters of one cell or face
-struct EqF {
-  float vx, vy, bm1, r, dr;   // u/RT, -|u|^2/(2RT), rho, rho - rho0
+// ---- equilibrium ----
+// assembly parameters of one cell or face
+template <typename C> struct EqF {
+  C vx, vy, bm1, r, dr;          // u/RT, -|u|^2/(2RT), rho, rho - rho0
 };
-__device__ __forceinline__ EqF eq_params_u(double rho, double ux, double uy, double inv_RT,
-                                           double rho0) {
+template <typename C>
+__device__ __forceinline__ EqF<C> eq_params_u(double rho, double ux, double uy, double inv_RT,
+                                              double rho0) {
   const double vx = ux * inv_RT, vy = uy * inv_RT;
-  EqF q;
-  q.vx = d2f(vx);
-  q.vy = d2f(vy);
-  q.bm1 = d2f(-0.5 * fma(ux, vx, uy * vy));
-  q.r = d2f(rho);
-  q.dr = d2f(rho - rho0);
+  EqF<C> q;
+  q.vx = to_c<C>(vx);
+  q.vy = to_c<C>(vy);
+  q.bm1 = to_c<C>(-0.5 * fma(ux, vx, uy * vy));
+  q.r = to_c<C>(rho);
+  q.dr = to_c<C>(rho - rho0);
   return q;
 }
 // from the sums (rho, jx, jy): one FP64 reciprocal
-__device__ __forceinline__ EqF eq_params_j(double rho, double jx, double jy, double inv_RT,
-                                           double rho0) {
+template <typename C>
+__device__ __forceinline__ EqF<C> eq_params_j(double rho, double jx, double jy, double inv_RT,
+                                              double rho0) {
   const double rinv = 1.0 / rho;
-  return eq_params_u(rho, jx * rinv, jy * rinv, inv_RT, rho0);
+  return eq_params_u<C>(rho, jx * rinv, jy * rinv, inv_RT, rho0);
 }
 // W_k (rho P_k - rho0) = W_k ((rho - rho0) + rho (P_k - 1)),
 // P_k - 1 = e (1 + e/2) - |u|^2/(2RT), e = xi_k.u/RT
-__device__ __forceinline__ float feq_dev(const EqF& q, float cx, float cy, float w) {
-  const float e = fmaf(cx, q.vx, cy * q.vy);
-  const float p1 = fmaf(e, fmaf(0.5f, e, 1.0f), q.bm1);
-  return w * fmaf(q.r, p1, q.dr);
+template <typename C>
+__device__ __forceinline__ C feq_dev(const EqF<C>& q, C cx, C cy, C w) {
+  const C e = fmx(cx, q.vx, cy * q.vy);
+  const C p1 = fmx(e, fmx(C(0.5), e, C(1)), q.bm1);
+  return w * fmx(q.r, p1, q.dr);
+}
+template <typename C>
+__device__ __forceinline__ void store_par(C* __restrict__ fp, int n, int i, const EqF<C>& q) {
+  fp[i] = q.vx;
+  fp[n + i] = q.vy;
+  fp[2 * n + i] = q.bm1;
+  fp[3 * n + i] = q.r;
+  fp[4 * n + i] = q.dr;
+}
+
+// Equilibrium of a cell or face as a quadratic in xi from its assembly
+// parameters: W_k P(xi_k) = W_k (rho P_k - rho0) (the equilibrium itself
+// when rho0 = 0), P(xi) = c0 + cx x + cy y + cxx x^2 + cxy x y + cyy y^2.
+template <typename C> struct Quad {
+  C c0, cx, cy, cxx, cxy, cyy;
+};
+template <typename C>
+__device__ __forceinline__ Quad<C> quad(const C* __restrict__ fp, int n, int i) {
+  const C vx = __ldg(fp + i), vy = __ldg(fp + n + i), bm1 = __ldg(fp + 2 * n + i);
+  const C r = __ldg(fp + 3 * n + i), dr = __ldg(fp + 4 * n + i);
+  Quad<C> o;
+  o.c0 = fmx(r, bm1, dr);
+  o.cx = r * vx;
+  o.cy = r * vy;
+  o.cxx = C(0.5) * o.cx * vx;
+  o.cxy = o.cx * vy;
+  o.cyy = C(0.5) * o.cy * vy;
+  return o;
 }
 
 // Sum M values over the threads of a block (warp shuffles, then the warps'
@@ -155,41 +219,27 @@ __device__ __forceinline__ size_t gp_at(const GDevStep& s, int k, int i, int j) 
   return (size_t)k * s.plane + (size_t)(j + 2) * s.pitch + (i + 2);
 }
 
-// Equilibrium of a cell or face as a quadratic in xi from its assembly
-// parameters: feq_k = W_k P(xi_k).
-struct Quad {                    // P(xi) = c0 + cx x + cy y + cxx x^2 + cxy x y + cyy y^2
-  float c0, cx, cy, cxx, cxy, cyy;
-};
-__device__ __forceinline__ Quad quad(const float* __restrict__ fp, int n, int i) {
-  const float vx = __ldg(fp + i), vy = __ldg(fp + n + i), bm1 = __ldg(fp + 2 * n + i);
-  const float r = __ldg(fp + 3 * n + i), dr = __ldg(fp + 4 * n + i);
-  Quad o;
-  o.c0 = fmaf(r, bm1, dr);
-  o.cx = r * vx;
-  o.cy = r * vy;
-  o.cxx = 0.5f * o.cx * vx;
-  o.cxy = o.cx * vy;
-  o.cyy = 0.5f * o.cy * vy;
-  return o;
-}
 // ---------------------------------------------------------------- cell
 // The cell pass of a stage: moments of src (f^ or f~') -> rho, u (FP64, into
-// mom) and the FP32 assembly parameters (eqp [5][N]); g = a src + b feq as
-// a deviation, into the padded layout.
+// mom) and the assembly parameters (eqp [5][N]); g = a src + b feq, into the
+// padded layout.
 //
 // Small velocity sets: one thread per cell does both sweeps.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gcell1(GDevStep s, const T* __restrict__ src, float a, float b) {
+k_gcell1(GDevStep s, const T* __restrict__ src, typename Prec<T>::C a, typename Prec<T>::C b) {
+  using C = typename Prec<T>::C;
+  using V4 = typename Prec<T>::V4;
   const DevParams& p = s.p;
+  const V4* vq = (const V4*)s.vq;
   T* __restrict__ g = (T*)s.g;
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.N) return;
   const int nv = p.nv;
-  Acc s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
+  Acc<C> s0{}, s1{}, s2{};
   for (int k = 0; k < nv; ++k) {
-    const float d = ldv(src + (size_t)k * p.N + cell);
-    const float4 xq = __ldg(s.vq + k);
+    const C d = ldv(src + (size_t)k * p.N + cell);
+    const V4 xq = ld4(vq + k);
     acc_add(s0, d);
     acc_addprod(s1, xq.x, xq.y, d);
     acc_addprod(s2, xq.z, xq.w, d);
@@ -198,35 +248,36 @@ k_gcell1(GDevStep s, const T* __restrict__ src, float a, float b) {
   const double rho = ref.W + acc_value(s0);
   const double rinv = 1.0 / rho;
   const double ux = (ref.Wx + acc_value(s1)) * rinv, uy = (ref.Wy + acc_value(s2)) * rinv;
-  const EqF q = eq_params_u(rho, ux, uy, p.inv_RT, ref.rho0);
+  const EqF<C> q = eq_params_u<C>(rho, ux, uy, p.inv_RT, ref.rho0);
   s.mom[cell] = rho;
   s.mom[p.N + cell] = ux;
   s.mom[2 * p.N + cell] = uy;
-  const float qv[5] = {q.vx, q.vy, q.bm1, q.r, q.dr};
-#pragma unroll
-  for (int m = 0; m < 5; ++m) s.eqp[m * p.N + cell] = qv[m];
+  store_par((C*)s.eqp, p.N, cell, q);
   const int j = cell / p.nx, i = cell - j * p.nx;
   for (int k = 0; k < nv; ++k) {
-    const float4 e4 = __ldg(s.vq + nv + k);
-    const float fe = feq_dev(q, e4.x, e4.y, e4.z);
-    stv(g + gp_at(s, k, i, j), fmaf(b, fe, a * ldv(src + (size_t)k * p.N + cell)));
+    const V4 e4 = ld4(vq + nv + k);
+    const C fe = feq_dev<C>(q, e4.x, e4.y, e4.z);
+    stv(g + gp_at(s, k, i, j), fmx(b, fe, a * ldv(src + (size_t)k * p.N + cell)));
   }
 }
 
 // Large velocity sets, three kernels.  (1) Partial moments: 32 cells per
 // block, 8 warps over a velocity chunk (eight loads in flight per thread),
-// compensated FP32 partials combined in FP64, into part[chunk][3][N].
+// per-thread partials combined in FP64, into part[chunk][3][N].
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_gmom(GDevStep s, const T* __restrict__ src, int kchunk) {
+  using C = typename Prec<T>::C;
+  using V4 = typename Prec<T>::V4;
   constexpr int TX = 32, G = kThreads / TX, U = 8;
   __shared__ double red[3][G][TX];
   const DevParams& p = s.p;
+  const V4* vq = (const V4*)s.vq;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int cell = blockIdx.x * TX + tx;
   const bool valid = cell < p.N;
   const int k0 = blockIdx.y * kchunk, k1 = min(p.nv, k0 + kchunk);
-  Acc s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f};
+  Acc<C> s0{}, s1{}, s2{};
   if (valid) {
     int k = k0 + ty;
     for (; k + (U - 1) * G < k1; k += U * G) {
@@ -235,16 +286,16 @@ k_gmom(GDevStep s, const T* __restrict__ src, int kchunk) {
       for (int u = 0; u < U; ++u) d[u] = ldr(src + (size_t)(k + u * G) * p.N + cell);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const float4 xq = __ldg(s.vq + k + u * G);
-        const float du = tof(d[u]);
+        const V4 xq = ld4(vq + k + u * G);
+        const C du = tof(d[u]);
         acc_add(s0, du);
         acc_addprod(s1, xq.x, xq.y, du);
         acc_addprod(s2, xq.z, xq.w, du);
       }
     }
     for (; k < k1; k += G) {
-      const float du = ldv(src + (size_t)k * p.N + cell);
-      const float4 xq = __ldg(s.vq + k);
+      const C du = ldv(src + (size_t)k * p.N + cell);
+      const V4 xq = ld4(vq + k);
       acc_add(s0, du);
       acc_addprod(s1, xq.x, xq.y, du);
       acc_addprod(s2, xq.z, xq.w, du);
@@ -263,6 +314,7 @@ k_gmom(GDevStep s, const T* __restrict__ src, int kchunk) {
 }
 
 // (2) Per cell: the chunks' partials in order -> rho, u, mom, eqp.
+template <typename C>
 __global__ void __launch_bounds__(kThreads)
 k_gmomfin(GDevStep s, int nchunk) {
   const DevParams& p = s.p;
@@ -277,15 +329,11 @@ k_gmomfin(GDevStep s, int nchunk) {
   }
   const double rinv = 1.0 / v0;
   const double ux = v1 * rinv, uy = v2 * rinv;
-  const EqF q = eq_params_u(v0, ux, uy, p.inv_RT, s.ref.rho0);
+  const EqF<C> q = eq_params_u<C>(v0, ux, uy, p.inv_RT, s.ref.rho0);
   s.mom[cell] = v0;
   s.mom[p.N + cell] = ux;
   s.mom[2 * p.N + cell] = uy;
-  s.eqp[cell] = q.vx;
-  s.eqp[p.N + cell] = q.vy;
-  s.eqp[2 * p.N + cell] = q.bm1;
-  s.eqp[3 * p.N + cell] = q.r;
-  s.eqp[4 * p.N + cell] = q.dr;
+  store_par((C*)s.eqp, p.N, cell, q);
 }
 
 // (3) g = a src + b W_k P(xi_k): one thread per cell and 16 consecutive
@@ -293,14 +341,17 @@ k_gmomfin(GDevStep s, int nchunk) {
 // equilibrium quadratic in xi.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gcellg(GDevStep s, const T* __restrict__ src, float a, float b) {
+k_gcellg(GDevStep s, const T* __restrict__ src, typename Prec<T>::C a, typename Prec<T>::C b) {
+  using C = typename Prec<T>::C;
+  using V4 = typename Prec<T>::V4;
   constexpr int CB = 16, CH = 8;
   const DevParams& p = s.p;
+  const V4* vq = (const V4*)s.vq;
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.N) return;
   const int nv = p.nv;
   const int j = cell / p.nx, i = cell - j * p.nx;
-  const Quad P = quad(s.eqp, p.N, cell);
+  const Quad<C> P = quad((const C*)s.eqp, p.N, cell);   // W_k P: W_k (rho P_k - rho0)
   T* __restrict__ g = (T*)s.g;
   for (int h = 0; h < CB; h += CH) {
     const int kb = blockIdx.y * CB + h;
@@ -312,10 +363,10 @@ k_gcellg(GDevStep s, const T* __restrict__ src, float a, float b) {
     for (int u = 0; u < CH; ++u) {
       const int k = kb + u;
       if (k < nv) {
-        const float4 e4 = __ldg(s.vq + nv + k);
-        const float x = e4.x, y = e4.y;
-        const float pk = fmaf(x, fmaf(x, P.cxx, fmaf(y, P.cxy, P.cx)), fmaf(y, fmaf(y, P.cyy, P.cy), P.c0));
-        stv(g + gp_at(s, k, i, j), fmaf(b * e4.z, pk, a * tof(d[u])));
+        const V4 e4 = ld4(vq + nv + k);
+        const C x = e4.x, y = e4.y;
+        const C pk = fmx(x, fmx(x, P.cxx, fmx(y, P.cxy, P.cx)), fmx(y, fmx(y, P.cyy, P.cy), P.c0));
+        stv(g + gp_at(s, k, i, j), fmx(b * e4.z, pk, a * tof(d[u])));
       }
     }
   }
@@ -329,6 +380,7 @@ k_gcellg(GDevStep s, const T* __restrict__ src, float a, float b) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_gghost(GDevStep s) {
+  using C = typename Prec<T>::C;
   const DevParams& p = s.p;
   const int nx = p.nx, ny = p.ny;
   const int W = nx + 4;
@@ -354,18 +406,18 @@ k_gghost(GDevStep s) {
   else xx = xx < -1 ? -1 : (xx > nx ? nx : xx);
   if (p.py) yy = (yy + ny) % ny;
   else yy = yy < -1 ? -1 : (yy > ny ? ny : yy);
-  auto at = [&](int i, int j) { return ldv(gk + (size_t)(j + 2) * s.pitch + (i + 2)); };
-  auto col = [&](int i, int j) {
+  auto at = [&](int i, int j) -> C { return ldv(gk + (size_t)(j + 2) * s.pitch + (i + 2)); };
+  auto col = [&](int i, int j) -> C {
     if (j < 0 || j >= ny) {
       const int b = j < 0 ? 0 : ny - 1, sg = j < 0 ? 1 : -1;
-      return 3.f * at(i, b) - 3.f * at(i, b + sg) + at(i, b + 2 * sg);
+      return C(3) * at(i, b) - C(3) * at(i, b + sg) + at(i, b + 2 * sg);
     }
     return at(i, j);
   };
-  float v;
+  C v;
   if (xx < 0 || xx >= nx) {
     const int b = xx < 0 ? 0 : nx - 1, sg = xx < 0 ? 1 : -1;
-    v = 3.f * col(b, yy) - 3.f * col(b + sg, yy) + col(b + 2 * sg, yy);
+    v = C(3) * col(b, yy) - C(3) * col(b + sg, yy) + col(b + 2 * sg, yy);
   } else {
     v = col(xx, yy);
   }
@@ -374,11 +426,12 @@ k_gghost(GDevStep s) {
 
 // quadratic Taylor weights about a cell for the foot offset (a dx, b dy),
 // central differences on the 3x3 neighbourhood: T[(dy+1)*3 + dx+1]
-__device__ __forceinline__ void taylor9f(float a, float b, float (&T)[9]) {
-  const float ab = 0.25f * a * b;
-  T[0] = ab;                   T[1] = 0.5f * (b * b - b);  T[2] = -ab;
-  T[3] = 0.5f * (a * a - a);   T[4] = 1.f - a * a - b * b; T[5] = 0.5f * (a * a + a);
-  T[6] = -ab;                  T[7] = 0.5f * (b * b + b);  T[8] = ab;
+template <typename C>
+__device__ __forceinline__ void taylor9(C a, C b, C (&T)[9]) {
+  const C ab = C(0.25) * a * b;
+  T[0] = ab;                      T[1] = C(0.5) * (b * b - b);      T[2] = -ab;
+  T[3] = C(0.5) * (a * a - a);    T[4] = C(1) - a * a - b * b;      T[5] = C(0.5) * (a * a + a);
+  T[6] = -ab;                     T[7] = C(0.5) * (b * b + b);      T[8] = ab;
 }
 
 // ---------------------------------------------------------- interior faces
@@ -386,33 +439,39 @@ __device__ __forceinline__ void taylor9f(float a, float b, float (&T)[9]) {
 // Each warp stages the slab of g its velocity needs (SR rows x SW columns,
 // from padded column c0) in shared memory with 16-byte asynchronous copies,
 // double-buffered so the next velocity's slab loads while the current one
-// is used; FP32 stencils, compensated partial face moments, combined in
-// FP64 per velocity chunk into part[chunk][3][nf].
+// is used; stencils in C, per-thread partial face moments, combined in FP64
+// per velocity chunk into part[chunk][3][nf].
 template <typename T, int DIR>
 struct Slab {
   static constexpr int SR = DIR == 0 ? R + 2 : R + 3;          // rows
-  static constexpr int SW = sizeof(T) == 4 ? 36 : 40;          // columns (x 16-byte chunks)
-  static constexpr int EPC = 16 / sizeof(T);                   // elements per chunk
+  static constexpr int SW = sizeof(T) == 2 ? 40 : 36;          // columns (x 16-byte chunks)
+  static constexpr int EPC = 16 / (int)sizeof(T);              // elements per chunk
   static constexpr int CPR = SW / EPC;                         // chunks per row
   static constexpr int NCH = SR * CPR;
   static constexpr int ELEMS = SR * SW;
+  // dynamic shared memory: the warps' double-buffered slabs, later reused
+  // for the cross-warp reduction of the face moments
+  static constexpr size_t SLAB_BYTES = (size_t)NW * 2 * ELEMS * sizeof(T);
+  static constexpr size_t RED_BYTES = (size_t)NW * R * LANES * 3 * sizeof(double);
+  static constexpr size_t BYTES = SLAB_BYTES > RED_BYTES ? SLAB_BYTES : RED_BYTES;
 };
 
 template <typename T, int DIR>
 __global__ void __launch_bounds__(LANES * NW, 2)
-k_gfaces1(GDevStep s, float* __restrict__ fb, float h, int kchunk) {
+k_gfaces1(GDevStep s, typename Prec<T>::C* __restrict__ fb, typename Prec<T>::C h, int kchunk) {
+  using C = typename Prec<T>::C;
+  using V4 = typename Prec<T>::V4;
   using S = Slab<T, DIR>;
   constexpr int SW = S::SW;
   // the stencil reads rows r .. r + 2 (+1 for y faces) and columns
   // lane .. lane + 3 of the slab
   static_assert(S::SR >= R + (DIR == 0 ? 2 : 3) && SW >= LANES + 3, "slab too small");
-  // the warps' double-buffered slabs, later reused for the reduction
-  __shared__ __align__(16) double smem[NW * R * LANES * 3];
-  static_assert(NW * 2 * S::ELEMS * sizeof(T) <= sizeof(smem), "slab too large");
+  extern __shared__ __align__(16) double smem[];
   auto red = [&](int w, int r, int l, int m) -> double& {
     return smem[((w * R + r) * LANES + l) * 3 + m];
   };
   const DevParams& p = s.p;
+  const V4* vq = (const V4*)s.vq;
   const T* __restrict__ g = (const T*)s.g;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nx = p.nx, ny = p.ny, nv = p.nv;
@@ -423,15 +482,15 @@ k_gfaces1(GDevStep s, float* __restrict__ fb, float h, int kchunk) {
   // cell r0 - 1 (x faces) or r0 - 2 (y faces)
   const int prow0 = DIR == 0 ? r0 + 1 : r0;
   const int prows = ny + 4;
-  const float dx = (float)p.dx, dy = (float)p.dy;
-  const float idx_ = (float)p.inv_dx, idy = (float)p.inv_dy;
-  Acc acc[R][3];
+  const C dx = (C)p.dx, dy = (C)p.dy;
+  const C idx_ = (C)p.inv_dx, idy = (C)p.inv_dy;
+  Acc<C> acc[R][3];
   bool ok[R];
   const int col = c0 + lane;
 #pragma unroll
   for (int r = 0; r < R; ++r) {
 #pragma unroll
-    for (int m = 0; m < 3; ++m) acc[r][m] = Acc{0.f, 0.f};
+    for (int m = 0; m < 3; ++m) acc[r][m] = Acc<C>{};
     if (DIR == 0) {
       const int j = r0 + r;
       ok[r] = j < ny && col <= nx && (p.px || (col >= 1 && col <= nx - 1));
@@ -459,34 +518,34 @@ k_gfaces1(GDevStep s, float* __restrict__ fb, float h, int kchunk) {
   for (int k = k0 + warp; k < k1; k += NW) {
     if (k + NW < k1) issue(k + NW, b ^ 1);
     cp_commit();
-    const float4 xq = __ldg(s.vq + k);             // xi_x hi, lo, xi_y hi, lo
-    const float cx = xq.x, cxl = xq.y, cy = xq.z, cyl = xq.w;
-    const float cn = DIR == 0 ? cx : cy;
+    const V4 xq = ld4(vq + k);                     // xi_x hi, lo, xi_y hi, lo
+    const C cx = xq.x, cxl = xq.y, cy = xq.z, cyl = xq.w;
+    const C cn = DIR == 0 ? cx : cy;
     // the upwind cell is the lower one (slab offset 0) for xi.n > 0 and the
     // upper one (one column / row on) for xi.n < 0; xi.n = 0 averages both
     // (uniform across the warp)
-    const bool up = cn < 0.f, tie = cn == 0.f;
-    const float sh = up ? -0.5f : 0.5f;
-    float Tw[9];
-    if (DIR == 0) taylor9f((sh * dx - cx * h) * idx_, -cy * h * idy, Tw);
-    else taylor9f(-cx * h * idx_, (sh * dy - cy * h) * idy, Tw);
+    const bool up = cn < C(0), tie = cn == C(0);
+    const C sh = up ? C(-0.5) : C(0.5);
+    C Tw[9];
+    if (DIR == 0) taylor9<C>((sh * dx - cx * h) * idx_, -cy * h * idy, Tw);
+    else taylor9<C>(-cx * h * idx_, (sh * dy - cy * h) * idy, Tw);
     cp_wait1();                                    // this velocity's slab has landed
     __syncwarp();
     // x faces: rows r..r+2 (cells j-1..j+1), columns lane+q (cells fi-2+q);
     // y faces: rows r+q (cells fj-2+q), columns lane+1+q (cells i-1+q)
     const T* sl = slab + b * S::ELEMS + lane + (DIR == 0 ? 0 : 1);
     const int uoff = DIR == 0 ? 1 : SW;            // lower -> upper cell
-    float* fbk = fb + (size_t)k * nf;
+    C* fbk = fb + (size_t)k * nf;
     if (!tie) {
       const T* sb = sl + (up ? uoff : 0);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const T* s0 = sb + r * SW;
-        float v = 0.f;
+        C v = C(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int q = 0; q < 3; ++q) v = fmaf(Tw[a * 3 + q], lds(s0 + a * SW + q), v);
+          for (int q = 0; q < 3; ++q) v = fmx(Tw[a * 3 + q], lds(s0 + a * SW + q), v);
         const int face = DIR == 0 ? (r0 + r) * (nx + 1) + col : (r0 + r) * nx + col;
         if (ok[r]) fbk[face] = v;
         acc_add(acc[r][0], v);                     // rows without a face are never stored
@@ -494,21 +553,21 @@ k_gfaces1(GDevStep s, float* __restrict__ fb, float h, int kchunk) {
         acc_addprod(acc[r][2], cy, cyl, v);
       }
     } else {
-      float Tu[9];
-      if (DIR == 0) taylor9f((-0.5f * dx - cx * h) * idx_, -cy * h * idy, Tu);
-      else taylor9f(-cx * h * idx_, (-0.5f * dy - cy * h) * idy, Tu);
+      C Tu[9];
+      if (DIR == 0) taylor9<C>((C(-0.5) * dx - cx * h) * idx_, -cy * h * idy, Tu);
+      else taylor9<C>(-cx * h * idx_, (C(-0.5) * dy - cy * h) * idy, Tu);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const T* s0 = sl + r * SW;
-        float vl = 0.f, vu = 0.f;
+        C vl = C(0), vu = C(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            vl = fmaf(Tw[a * 3 + q], lds(s0 + a * SW + q), vl);
-            vu = fmaf(Tu[a * 3 + q], lds(s0 + uoff + a * SW + q), vu);
+            vl = fmx(Tw[a * 3 + q], lds(s0 + a * SW + q), vl);
+            vu = fmx(Tu[a * 3 + q], lds(s0 + uoff + a * SW + q), vu);
           }
-        const float v = 0.5f * (vl + vu);
+        const C v = C(0.5) * (vl + vu);
         const int face = DIR == 0 ? (r0 + r) * (nx + 1) + col : (r0 + r) * nx + col;
         if (ok[r]) fbk[face] = v;
         acc_add(acc[r][0], v);
@@ -554,12 +613,12 @@ k_gfaces1(GDevStep s, float* __restrict__ fb, float h, int kchunk) {
 }
 
 // Face parameters of the interior faces: the face moments (FP64, velocity
-// chunks summed in order) and the FP32 assembly parameters of the face
+// chunks summed in order) and the assembly parameters of the face
 // equilibrium, fpar[5][nf] (eq. recover2f is applied where the update reads
 // the face values: f = alpha f-bar + beta feq).  Wall faces are skipped.
-template <int DIR>
+template <typename C, int DIR>
 __global__ void __launch_bounds__(256)
-k_gfacepar(GDevStep s, float* __restrict__ fpar, int nchunk) {
+k_gfacepar(GDevStep s, C* __restrict__ fpar, int nchunk) {
   const DevParams& p = s.p;
   const int nx = p.nx, ny = p.ny;
   const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
@@ -579,12 +638,7 @@ k_gfacepar(GDevStep s, float* __restrict__ fpar, int nchunk) {
     jx += pc[nf + face];
     jy += pc[2 * nf + face];
   }
-  const EqF q = eq_params_j(r, jx, jy, p.inv_RT, s.ref.rho0);
-  fpar[face] = q.vx;
-  fpar[nf + face] = q.vy;
-  fpar[2 * nf + face] = q.bm1;
-  fpar[3 * nf + face] = q.r;
-  fpar[4 * nf + face] = q.dr;
+  store_par(fpar, nf, face, eq_params_j<C>(r, jx, jy, p.inv_RT, s.ref.rho0));
 }
 
 // -------------------------------------------------------------- wall faces
@@ -593,30 +647,34 @@ k_gfacepar(GDevStep s, float* __restrict__ fpar, int nchunk) {
 // or along the wall), the wall rule of Sec. 2.3 for velocities entering the
 // fluid (bounce-back with the moving-wall term, or diffuse scattering with
 // the density that balances the outgoing flux), f-bar into fb, the face
-// moments (compensated FP32 partials per thread, FP64 across the block) and
-// the face's assembly parameters into fpar.  Per direction, face
+// moments (per-thread partials, FP64 across the block) and the face's
+// assembly parameters into fpar.  Per direction, face
 // id = 2 line + (0: W/S wall, 1: E/N).
-template <typename T>
-__device__ __forceinline__ float taylor_at(const GDevStep& s, const T* __restrict__ g, int k,
-                                           int ci, int cj, float X, float Y) {
-  float Tw[9];
-  taylor9f(X * (float)s.p.inv_dx, Y * (float)s.p.inv_dy, Tw);
-  float v = 0.f;
+template <typename T, typename C>
+__device__ __forceinline__ C taylor_at(const GDevStep& s, const T* __restrict__ g, int k, int ci,
+                                       int cj, C X, C Y) {
+  C Tw[9];
+  taylor9<C>(X * (C)s.p.inv_dx, Y * (C)s.p.inv_dy, Tw);
+  C v = C(0);
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx)
-      v = fmaf(Tw[(dy + 1) * 3 + dx + 1], ldv(g + gp_at(s, k, ci + dx, cj + dy)), v);
+      v = fmx(Tw[(dy + 1) * 3 + dx + 1], ldv(g + gp_at(s, k, ci + dx, cj + dy)), v);
   return v;
 }
 
 template <typename T, int DIR>
-__device__ __forceinline__ void wall_face(const GDevStep& s, int id, float h, double* sm) {
+__device__ __forceinline__ void wall_face(const GDevStep& s, int id, typename Prec<T>::C h,
+                                          double* sm) {
+  using C = typename Prec<T>::C;
+  using V4 = typename Prec<T>::V4;
   const DevParams& p = s.p;
   const GDevRef& ref = s.ref;
+  const V4* vq = (const V4*)s.vq;
   const T* __restrict__ g = (const T*)s.g;
-  float* __restrict__ fb = DIR == 0 ? s.fbx : s.fby;
-  float* __restrict__ fpar = DIR == 0 ? s.fpx : s.fpy;
+  C* __restrict__ fb = (C*)(DIR == 0 ? s.fbx : s.fby);
+  C* __restrict__ fpar = (C*)(DIR == 0 ? s.fpx : s.fpy);
   const int nx = p.nx, ny = p.ny, nv = p.nv;
   const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
   const bool upper_wall = id & 1;                 // east / north
@@ -627,39 +685,39 @@ __device__ __forceinline__ void wall_face(const GDevStep& s, int id, float h, do
   // the fluid cell lies on the +normal side of W/S walls; xi.n with n the
   // fluid's outward normal is -xi_n there and +xi_n at E/N walls
   const bool fluid_hi = !upper_wall;
-  const float nsg = fluid_hi ? -1.f : 1.f;
+  const C nsg = fluid_hi ? C(-1) : C(1);
   const int ci = DIR == 0 ? (fluid_hi ? 0 : nx - 1) : line;
   const int cj = DIR == 0 ? line : (fluid_hi ? 0 : ny - 1);
   const int kind = p.bc_kind[side];
-  const float half = 0.5f * (float)(DIR == 0 ? p.dx : p.dy);
-  const float off = fluid_hi ? -half : half;      // face centre from the fluid cell centre
-  const float rho_w = (float)s.mom[cj * nx + ci];
-  const float uwx = (float)p.uw_x[side], uwy = (float)p.uw_y[side];
-  const float irt = (float)p.inv_RT;
+  const C half = C(0.5) * (C)(DIR == 0 ? p.dx : p.dy);
+  const C off = fluid_hi ? -half : half;          // face centre from the fluid cell centre
+  const C rho_w = (C)s.mom[cj * nx + ci];
+  const C uwx = (C)p.uw_x[side], uwy = (C)p.uw_y[side];
+  const C irt = (C)p.inv_RT;
   auto recon = [&](int k) {
-    const float4 e4 = __ldg(s.vq + nv + k);
-    const float X = DIR == 0 ? off - e4.x * h : -e4.x * h;
-    const float Y = DIR == 0 ? -e4.y * h : off - e4.y * h;
-    return taylor_at(s, g, k, ci, cj, X, Y);
+    const V4 e4 = ld4(vq + nv + k);
+    const C X = DIR == 0 ? off - e4.x * h : -e4.x * h;
+    const C Y = DIR == 0 ? -e4.y * h : off - e4.y * h;
+    return taylor_at<T, C>(s, g, k, ci, cj, X, Y);
   };
-  // moments of f-bar (deviations) and the outgoing flux sum(xi.n f-bar_dev)
-  Acc a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+  // moments of f-bar and the outgoing flux sum(xi.n f-bar)
+  Acc<C> a0{}, a1{}, a2{}, a3{};
   for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-    const float4 xq = __ldg(s.vq + k);
-    const float cx = xq.x, cy = xq.z;
-    const float xn = nsg * (DIR == 0 ? cx : cy);
-    float fbar;
-    if (xn >= 0.f) {                               // hits the wall or runs along it
+    const V4 xq = ld4(vq + k);
+    const C cx = xq.x, cy = xq.z;
+    const C xn = nsg * (DIR == 0 ? cx : cy);
+    C fbar;
+    if (xn >= C(0)) {                              // hits the wall or runs along it
       fbar = recon(k);
-      if (xn > 0.f)
+      if (xn > C(0))
         acc_addprod(a3, DIR == 0 ? nsg * xq.x : nsg * xq.z, DIR == 0 ? nsg * xq.y : nsg * xq.w,
                     fbar);
     } else if (kind == BC_BOUNCEBACK) {
       const int kk = __ldg(p.opp + k);
-      const float wk = __ldg(s.vq + nv + k).z;
-      const float bbk = 2.f * wk * fmaf(cx, uwx, cy * uwy) * irt;
-      const float shift = (__ldg(s.vq + nv + kk).z - wk) * (float)ref.rho0;
-      fbar = fmaf(rho_w, bbk, recon(kk) + shift);
+      const C wk = ld4(vq + nv + k).z;
+      const C bbk = C(2) * wk * fmx(cx, uwx, cy * uwy) * irt;
+      const C shift = (ld4(vq + nv + kk).z - wk) * (C)ref.rho0;
+      fbar = fmx(rho_w, bbk, recon(kk) + shift);
     } else {
       continue;                                    // diffuse: after the reduction
     }
@@ -674,13 +732,13 @@ __device__ __forceinline__ void wall_face(const GDevStep& s, int id, float h, do
     // rho_ds: the outgoing flux of f = W rho0 + d over the wall's flux
     // normaliser (Sec. 2.3 diffuse scattering)
     const double rho_ds = (s.ds_out[side] + v[3]) / p.ds_den[side];
-    Acc b0{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f};
+    Acc<C> b0{}, b1{}, b2{};
     for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-      const float4 xq = __ldg(s.vq + k);
-      const float xn = nsg * (DIR == 0 ? xq.x : xq.z);
-      if (xn < 0.f) {
-        const float fbar =
-            d2f(fma(rho_ds, __ldg(p.feq_wall + side * nv + k), -__ldg(p.w + k) * ref.rho0));
+      const V4 xq = ld4(vq + k);
+      const C xn = nsg * (DIR == 0 ? xq.x : xq.z);
+      if (xn < C(0)) {
+        const C fbar =
+            to_c<C>(fma(rho_ds, __ldg(p.feq_wall + side * nv + k), -__ldg(p.w + k) * ref.rho0));
         fb[(size_t)k * nf + face] = fbar;
         acc_add(b0, fbar);
         acc_addprod(b1, xq.x, xq.y, fbar);
@@ -693,20 +751,15 @@ __device__ __forceinline__ void wall_face(const GDevStep& s, int id, float h, do
     v[1] += w2[1];
     v[2] += w2[2];
   }
-  if (threadIdx.x == 0) {
-    const EqF q = eq_params_j(ref.W + v[0], ref.Wx + v[1], ref.Wy + v[2], p.inv_RT, ref.rho0);
-    fpar[face] = q.vx;
-    fpar[nf + face] = q.vy;
-    fpar[2 * nf + face] = q.bm1;
-    fpar[3 * nf + face] = q.r;
-    fpar[4 * nf + face] = q.dr;
-  }
+  if (threadIdx.x == 0)
+    store_par(fpar, nf, face,
+              eq_params_j<C>(ref.W + v[0], ref.Wx + v[1], ref.Wy + v[2], p.inv_RT, ref.rho0));
 }
 
 // blocks [0, nwx): x-direction walls (W/E), then y-direction walls (S/N)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gwalls(GDevStep s, float h, int nwx) {
+k_gwalls(GDevStep s, typename Prec<T>::C h, int nwx) {
   __shared__ double sm[32 * 4];
   if ((int)blockIdx.x < nwx) wall_face<T, 0>(s, blockIdx.x, h, sm);
   else wall_face<T, 1>(s, blockIdx.x - nwx, h, sm);
@@ -717,69 +770,78 @@ k_gwalls(GDevStep s, float h, int nwx) {
 // flight).  Face values are f = alpha f-bar + beta feq (eq. recover2f) and
 // L = -(xi_x (f_e - f_w)/dx + xi_y (f_n - f_s)/dy) (eq. microflux).  Every
 // equilibrium entering the update -- the four faces' in L, and the cell's
-// in the collision term -- is W_k P(xi_k) with P quadratic in xi:
-// P = (r bm1 + dr) + r (u.xi/RT) + (r/2)(u.xi/RT)^2 from the assembly
-// parameters.  Their combination is W_k S(xi_k) with S a cubic in
-// (xi_x, xi_y), whose ten coefficients each thread forms once for its cell.
-constexpr int KB = 16, KH = 8;
+// in the collision term -- is W_k P(xi_k) with P quadratic in xi (Quad).
+// Their combination is W_k S(xi_k) with S a cubic in (xi_x, xi_y), whose ten
+// coefficients each thread forms once for its cell.
+constexpr int KB = 16;
 
-struct Cubic {                   // 1, x, y, xx, xy, yy, xxx, xxy, xyy, yyy
-  float c[10];
+template <typename C> struct Cubic {           // 1, x, y, xx, xy, yy, xxx, xxy, xyy, yyy
+  C c[10];
 };
-__device__ __forceinline__ float cubic(const Cubic& S, float x, float y) {
-  const float t1 = fmaf(x, S.c[6], fmaf(y, S.c[7], S.c[3]));
-  const float t2 = fmaf(y, S.c[8], S.c[4]);
-  const float t3 = fmaf(y, S.c[9], S.c[5]);
-  const float X = fmaf(x, t1, fmaf(y, t2, S.c[1]));
-  const float Y = fmaf(y, t3, S.c[2]);
-  return fmaf(x, X, fmaf(y, Y, S.c[0]));
+template <typename C>
+__device__ __forceinline__ C cubic(const Cubic<C>& S, C x, C y) {
+  const C t1 = fmx(x, S.c[6], fmx(y, S.c[7], S.c[3]));
+  const C t2 = fmx(y, S.c[8], S.c[4]);
+  const C t3 = fmx(y, S.c[9], S.c[5]);
+  const C X = fmx(x, t1, fmx(y, t2, S.c[1]));
+  const C Y = fmx(y, t3, S.c[2]);
+  return fmx(x, X, fmx(y, Y, S.c[0]));
 }
 // F(xi) = (x/dx)(P_E - P_W) + (y/dy)(P_N - P_S) for the faces of cell (i, j),
 // scaled by sc
-__device__ __forceinline__ Cubic flux_cubic(const GDevStep& s, int i, int j, float sc) {
+template <typename C>
+__device__ __forceinline__ Cubic<C> flux_cubic(const GDevStep& s, int i, int j, C sc) {
   const int nx = s.p.nx, ny = s.p.ny;
   const int nfx = ny * (nx + 1), nfy = (ny + 1) * nx;
   const int fx = j * (nx + 1) + i, fy = j * nx + i;
-  const Quad w = quad(s.fpx, nfx, fx), e = quad(s.fpx, nfx, fx + 1);
-  const Quad so = quad(s.fpy, nfy, fy), no = quad(s.fpy, nfy, fy + nx);
-  const float ax = sc * (float)s.p.inv_dx, ay = sc * (float)s.p.inv_dy;
-  Cubic F;
-  F.c[0] = 0.f;
+  const C* fpx = (const C*)s.fpx;
+  const C* fpy = (const C*)s.fpy;
+  const Quad<C> w = quad(fpx, nfx, fx), e = quad(fpx, nfx, fx + 1);
+  const Quad<C> so = quad(fpy, nfy, fy), no = quad(fpy, nfy, fy + nx);
+  const C ax = sc * (C)s.p.inv_dx, ay = sc * (C)s.p.inv_dy;
+  Cubic<C> F;
+  F.c[0] = C(0);
   F.c[1] = ax * (e.c0 - w.c0);
   F.c[2] = ay * (no.c0 - so.c0);
   F.c[3] = ax * (e.cx - w.cx);
-  F.c[4] = fmaf(ax, e.cy - w.cy, ay * (no.cx - so.cx));
+  F.c[4] = fmx(ax, e.cy - w.cy, ay * (no.cx - so.cx));
   F.c[5] = ay * (no.cy - so.cy);
   F.c[6] = ax * (e.cxx - w.cxx);
-  F.c[7] = fmaf(ax, e.cxy - w.cxy, ay * (no.cxx - so.cxx));
-  F.c[8] = fmaf(ax, e.cyy - w.cyy, ay * (no.cxy - so.cxy));
+  F.c[7] = fmx(ax, e.cxy - w.cxy, ay * (no.cxx - so.cxx));
+  F.c[8] = fmx(ax, e.cyy - w.cyy, ay * (no.cxy - so.cxy));
   F.c[9] = ay * (no.cyy - so.cyy);
   return F;
 }
 
 // kx (f-bar_e - f-bar_w) + ky (f-bar_n - f-bar_s) of velocity k
-__device__ __forceinline__ float lbar(const float (&f)[4], float kx, float ky) {
-  return fmaf(kx, f[1] - f[0], ky * (f[3] - f[2]));
+template <typename C>
+__device__ __forceinline__ C lbar(const C (&f)[4], C kx, C ky) {
+  return fmx(kx, f[1] - f[0], ky * (f[3] - f[2]));
 }
 
 // f~(t') = 5/4 g1 - 1/4 f^ + dt/3 L*,  acc = 1/4 f^ + 3/4 g1 + 3dt/7 L*,
 // L* = -alpha lbar + W S(xi), S = -beta F
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gupdate1(GDevStep s, float alpha, float beta, float dt3, float dt37) {
+k_gupdate1(GDevStep s, typename Prec<T>::C alpha, typename Prec<T>::C beta,
+           typename Prec<T>::C dt3, typename Prec<T>::C dt37) {
+  using C = typename Prec<T>::C;
+  using V4 = typename Prec<T>::V4;
+  constexpr int KH = Prec<T>::KH;
   const DevParams& p = s.p;
+  const V4* vq = (const V4*)s.vq;
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.N) return;
   const int nx = p.nx, ny = p.ny, nv = p.nv;
   const int j = cell / nx, i = cell - j * nx;
-  const Cubic S = flux_cubic(s, i, j, -beta);
+  const Cubic<C> S = flux_cubic<C>(s, i, j, -beta);
   const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
-  const float* fbx = s.fbx + (size_t)j * (nx + 1) + i;
-  const float* fby = s.fby + (size_t)j * nx + i;
-  for (int h = 0; h < KB; h += KH) {
-    const int kb = blockIdx.y * KB + h;
+  const C* fbx = (const C*)s.fbx + (size_t)j * (nx + 1) + i;
+  const C* fby = (const C*)s.fby + (size_t)j * nx + i;
+  for (int hb = 0; hb < KB; hb += KH) {
+    const int kb = blockIdx.y * KB + hb;
     T fh[KH], gg[KH];
-    float fv[KH][4];
+    C fv[KH][4];
 #pragma unroll
     for (int u = 0; u < KH; ++u) {
       const int k = kb + u;
@@ -796,13 +858,13 @@ k_gupdate1(GDevStep s, float alpha, float beta, float dt3, float dt37) {
     for (int u = 0; u < KH; ++u) {
       const int k = kb + u;
       if (k < nv) {
-        const float4 e4 = __ldg(s.vq + nv + k);
-        const float4 k4 = __ldg(s.vq + 2 * nv + k);
-        const float L = fmaf(-alpha, lbar(fv[u], k4.x, k4.y), e4.z * cubic(S, e4.x, e4.y));
+        const V4 e4 = ld4(vq + nv + k);
+        const V4 k4 = ld4(vq + 2 * nv + k);
+        const C L = fmx(-alpha, lbar<C>(fv[u], k4.x, k4.y), e4.z * cubic<C>(S, e4.x, e4.y));
         const size_t t = (size_t)k * p.N + cell;
-        const float f0 = tof(fh[u]), g0 = tof(gg[u]);
-        stv((T*)s.ftp + t, fmaf(1.25f, g0, fmaf(-0.25f, f0, dt3 * L)));
-        stv((T*)s.acc + t, fmaf(0.25f, f0, fmaf(0.75f, g0, dt37 * L)));
+        const C f0 = tof(fh[u]), g0 = tof(gg[u]);
+        stv((T*)s.ftp + t, fmx(C(1.25), g0, fmx(C(-0.25), f0, dt3 * L)));
+        stv((T*)s.acc + t, fmx(C(0.25), f0, fmx(C(0.75), g0, dt37 * L)));
       }
     }
   }
@@ -810,33 +872,38 @@ k_gupdate1(GDevStep s, float alpha, float beta, float dt3, float dt37) {
 
 // f^^{n+1} = acc + 3/4 dt Omega' + 4dt/7 L**,  dt Omega' = c_om (f~' - feq');
 // = acc + c34 f~' - (4dt/7) alpha lbar + W S(xi),
-// S = -c34 P_cell - (4dt/7) beta F
+// S = -c34 P_cell - (4dt/7) beta F  (P_cell with -rho0 for the deviations)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gupdate2(GDevStep s, float alpha, float beta, float c_om34, float dt47) {
+k_gupdate2(GDevStep s, typename Prec<T>::C alpha, typename Prec<T>::C beta,
+           typename Prec<T>::C c_om34, typename Prec<T>::C dt47) {
+  using C = typename Prec<T>::C;
+  using V4 = typename Prec<T>::V4;
+  constexpr int KH = Prec<T>::KH;
   const DevParams& p = s.p;
+  const V4* vq = (const V4*)s.vq;
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= p.N) return;
   const int nx = p.nx, ny = p.ny, nv = p.nv;
   const int j = cell / nx, i = cell - j * nx;
-  Cubic S = flux_cubic(s, i, j, -dt47 * beta);
+  Cubic<C> S = flux_cubic<C>(s, i, j, -dt47 * beta);
   {
-    const Quad c = quad(s.eqp, p.N, cell);
-    S.c[0] = fmaf(-c_om34, c.c0, S.c[0]);
-    S.c[1] = fmaf(-c_om34, c.cx, S.c[1]);
-    S.c[2] = fmaf(-c_om34, c.cy, S.c[2]);
-    S.c[3] = fmaf(-c_om34, c.cxx, S.c[3]);
-    S.c[4] = fmaf(-c_om34, c.cxy, S.c[4]);
-    S.c[5] = fmaf(-c_om34, c.cyy, S.c[5]);
+    const Quad<C> c = quad((const C*)s.eqp, p.N, cell);
+    S.c[0] = fmx(-c_om34, c.c0, S.c[0]);
+    S.c[1] = fmx(-c_om34, c.cx, S.c[1]);
+    S.c[2] = fmx(-c_om34, c.cy, S.c[2]);
+    S.c[3] = fmx(-c_om34, c.cxx, S.c[3]);
+    S.c[4] = fmx(-c_om34, c.cxy, S.c[4]);
+    S.c[5] = fmx(-c_om34, c.cyy, S.c[5]);
   }
-  const float adt = dt47 * alpha;
+  const C adt = dt47 * alpha;
   const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
-  const float* fbx = s.fbx + (size_t)j * (nx + 1) + i;
-  const float* fby = s.fby + (size_t)j * nx + i;
-  for (int h = 0; h < KB; h += KH) {
-    const int kb = blockIdx.y * KB + h;
+  const C* fbx = (const C*)s.fbx + (size_t)j * (nx + 1) + i;
+  const C* fby = (const C*)s.fby + (size_t)j * nx + i;
+  for (int hb = 0; hb < KB; hb += KH) {
+    const int kb = blockIdx.y * KB + hb;
     T ft[KH], ac[KH];
-    float fv[KH][4];
+    C fv[KH][4];
 #pragma unroll
     for (int u = 0; u < KH; ++u) {
       const int k = kb + u;
@@ -854,10 +921,10 @@ k_gupdate2(GDevStep s, float alpha, float beta, float c_om34, float dt47) {
     for (int u = 0; u < KH; ++u) {
       const int k = kb + u;
       if (k < nv) {
-        const float4 e4 = __ldg(s.vq + nv + k);
-        const float4 k4 = __ldg(s.vq + 2 * nv + k);
-        const float src = fmaf(-adt, lbar(fv[u], k4.x, k4.y), e4.z * cubic(S, e4.x, e4.y));
-        stv((T*)s.fhat + (size_t)k * p.N + cell, fmaf(c_om34, tof(ft[u]), tof(ac[u]) + src));
+        const V4 e4 = ld4(vq + nv + k);
+        const V4 k4 = ld4(vq + 2 * nv + k);
+        const C src = fmx(-adt, lbar<C>(fv[u], k4.x, k4.y), e4.z * cubic<C>(S, e4.x, e4.y));
+        stv((T*)s.fhat + (size_t)k * p.N + cell, fmx(c_om34, tof(ft[u]), tof(ac[u]) + src));
       }
     }
   }
@@ -865,20 +932,21 @@ k_gupdate2(GDevStep s, float alpha, float beta, float c_om34, float dt47) {
 
 template <typename T>
 cudaError_t cell_t(const GDevStep& s, const void* src, const StageCoef& c, cudaStream_t st) {
+  using C = typename Prec<T>::C;
   const DevParams& p = s.p;
   if (s.mch <= 1) {
-    k_gcell1<T><<<(p.N + kThreads - 1) / kThreads, kThreads, 0, st>>>(s, (const T*)src, (float)c.a,
-                                                                    (float)c.b);
+    k_gcell1<T><<<(p.N + kThreads - 1) / kThreads, kThreads, 0, st>>>(s, (const T*)src, (C)c.a,
+                                                                    (C)c.b);
   } else {
     const int kchunk = (p.nv + s.mch - 1) / s.mch;
     k_gmom<T><<<dim3((p.N + 31) / 32, s.mch), kThreads, 0, st>>>(s, (const T*)src, kchunk);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_gmomfin<<<(p.N + kThreads - 1) / kThreads, kThreads, 0, st>>>(s, s.mch);
+    k_gmomfin<C><<<(p.N + kThreads - 1) / kThreads, kThreads, 0, st>>>(s, s.mch);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_gcellg<T><<<dim3((p.N + kThreads - 1) / kThreads, (p.nv + 15) / 16), kThreads, 0, st>>>(
-        s, (const T*)src, (float)c.a, (float)c.b);
+        s, (const T*)src, (C)c.a, (C)c.b);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -889,41 +957,98 @@ cudaError_t cell_t(const GDevStep& s, const void* src, const StageCoef& c, cudaS
 
 template <typename T, int DIR>
 cudaError_t faces_t(const GDevStep& s, const StageCoef& c, cudaStream_t st) {
+  using C = typename Prec<T>::C;
   const DevParams& p = s.p;
-  float* fb = DIR == 0 ? s.fbx : s.fby;
-  float* fpar = DIR == 0 ? s.fpx : s.fpy;
+  C* fb = (C*)(DIR == 0 ? s.fbx : s.fby);
+  C* fpar = (C*)(DIR == 0 ? s.fpx : s.fpy);
   const int nch = DIR == 0 ? s.nchx : s.nchy;
   const int kchunk = (p.nv + nch - 1) / nch;
   const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
   const dim3 grid(DIR == 0 ? (p.nx + 1 + LANES - 1) / LANES : (p.nx + LANES - 1) / LANES,
                   DIR == 0 ? (p.ny + R - 1) / R : (p.ny + 1 + R - 1) / R, nch);
-  k_gfaces1<T, DIR><<<grid, LANES * NW, 0, st>>>(s, fb, (float)c.h, kchunk);
+  k_gfaces1<T, DIR><<<grid, LANES * NW, Slab<T, DIR>::BYTES, st>>>(s, fb, (C)c.h, kchunk);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_gfacepar<DIR><<<(nf + 255) / 256, 256, 0, st>>>(s, fpar, nch);
+  k_gfacepar<C, DIR><<<(nf + 255) / 256, 256, 0, st>>>(s, fpar, nch);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t walls_t(const GDevStep& s, int stage, cudaStream_t st) {
+  using C = typename Prec<T>::C;
+  const DevParams& p = s.p;
+  const int nwx = p.px ? 0 : 2 * p.ny, nwy = p.py ? 0 : 2 * p.nx;
+  if (nwx + nwy == 0) return cudaSuccess;
+  const C h = (C)(stage == 1 ? s.s1.h : s.s2.h);
+  const int threads = p.nv >= kThreads ? kThreads : ((p.nv + 31) / 32) * 32;
+  k_gwalls<T><<<nwx + nwy, threads, 0, st>>>(s, h, nwx);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t update_t(const GDevStep& s, int stage, cudaStream_t st) {
+  using C = typename Prec<T>::C;
+  const DevParams& p = s.p;
+  const dim3 grid((p.N + kThreads - 1) / kThreads, (p.nv + KB - 1) / KB);
+  const StageCoef& c = stage == 1 ? s.s1 : s.s2;
+  const C al = (C)c.alpha, be = (C)c.beta;
+  if (stage == 1) {
+    const C dt3 = (C)(p.dt / 3.0), dt37 = (C)(3.0 * p.dt / 7.0);
+    k_gupdate1<T><<<grid, kThreads, 0, st>>>(s, al, be, dt3, dt37);
+  } else {
+    const C c34 = (C)(0.75 * s.c_om), dt47 = (C)(4.0 * p.dt / 7.0);
+    k_gupdate2<T><<<grid, kThreads, 0, st>>>(s, al, be, c34, dt47);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int DIR>
+int occupancy() {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gfaces1<T, DIR>, LANES * NW,
+                                                    Slab<T, DIR>::BYTES) != cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  return occ;
+}
+
+template <typename T>
+cudaError_t allow_smem() {
+  cudaError_t e = cudaFuncSetAttribute(k_gfaces1<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Slab<T, 0>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gfaces1<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Slab<T, 1>::BYTES);
+  return e;
 }
 
 }  // namespace
 
 // Padded g layout: the row pitch leaves a whole 16-byte chunk (8 BF16 /
-// 4 FP32 elements) past the last ghost column nx + 1 and is a multiple of 8
-// elements, so every chunk the face kernels copy is aligned and in bounds.
+// 4 FP32 / 2 FP64 elements) past the last ghost column nx + 1 and is a
+// multiple of 8 elements, so every chunk the face kernels copy is aligned
+// and in bounds.
 int gdev_pitch(int nx) { return ((nx + 10 + 7) / 8) * 8; }
+
+// Shared-memory limits of the face kernels (the FP64 slabs exceed the
+// default 48 KiB).
+cudaError_t gdev_prepare(int store) {
+  if (store == 1) return allow_smem<float>();
+  if (store == 2) return allow_smem<__nv_bfloat16>();
+  return allow_smem<double>();
+}
 
 // Velocity chunks of the interior-face pass 1: the grid of (face columns x
 // face rows x chunks) blocks is sized to fill whole waves of resident blocks
 // (time ~ waves / chunks), with a small charge per chunk for the partial
 // moments that pass 2 reads back.
-int gdev_chunks(const DevParams& p, int dir, int sms) {
-  int occ = 0;
-  const cudaError_t e = dir == 0
-      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gfaces1<float, 0>, LANES * NW, 0)
-      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gfaces1<float, 1>, LANES * NW, 0);
-  if (e != cudaSuccess || occ < 1) {
-    cudaGetLastError();
-    occ = 1;
-  }
+int gdev_chunks(const DevParams& p, int dir, int sms, int store) {
+  int occ;
+  if (store == 1) occ = dir == 0 ? occupancy<float, 0>() : occupancy<float, 1>();
+  else if (store == 2) occ = dir == 0 ? occupancy<__nv_bfloat16, 0>() : occupancy<__nv_bfloat16, 1>();
+  else occ = dir == 0 ? occupancy<double, 0>() : occupancy<double, 1>();
   const long slots = (long)occ * (sms > 0 ? sms : 1);
   const long base = dir == 0 ? (long)((p.nx + LANES) / LANES) * ((p.ny + R - 1) / R)
                              : (long)((p.nx + LANES - 1) / LANES) * ((p.ny + R) / R);
@@ -944,42 +1069,30 @@ int gdev_chunks(const DevParams& p, int dir, int sms) {
 cudaError_t launch_gdev_cell(const GDevStep& s, int stage, cudaStream_t st) {
   const void* src = stage == 1 ? s.fhat : s.ftp;
   const StageCoef& c = stage == 1 ? s.s1 : s.s2;
-  return s.store == 1 ? cell_t<float>(s, src, c, st) : cell_t<__nv_bfloat16>(s, src, c, st);
+  if (s.store == 1) return cell_t<float>(s, src, c, st);
+  if (s.store == 2) return cell_t<__nv_bfloat16>(s, src, c, st);
+  return cell_t<double>(s, src, c, st);
 }
 
 cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_t st) {
   const StageCoef& c = stage == 1 ? s.s1 : s.s2;
   if (s.store == 1)
     return dir == 0 ? faces_t<float, 0>(s, c, st) : faces_t<float, 1>(s, c, st);
-  return dir == 0 ? faces_t<__nv_bfloat16, 0>(s, c, st) : faces_t<__nv_bfloat16, 1>(s, c, st);
+  if (s.store == 2)
+    return dir == 0 ? faces_t<__nv_bfloat16, 0>(s, c, st) : faces_t<__nv_bfloat16, 1>(s, c, st);
+  return dir == 0 ? faces_t<double, 0>(s, c, st) : faces_t<double, 1>(s, c, st);
 }
 
 cudaError_t launch_gdev_walls(const GDevStep& s, int stage, cudaStream_t st) {
-  const DevParams& p = s.p;
-  const int nwx = p.px ? 0 : 2 * p.ny, nwy = p.py ? 0 : 2 * p.nx;
-  if (nwx + nwy == 0) return cudaSuccess;
-  const float h = (float)(stage == 1 ? s.s1.h : s.s2.h);
-  const int threads = p.nv >= kThreads ? kThreads : ((p.nv + 31) / 32) * 32;
-  if (s.store == 1) k_gwalls<float><<<nwx + nwy, threads, 0, st>>>(s, h, nwx);
-  else k_gwalls<__nv_bfloat16><<<nwx + nwy, threads, 0, st>>>(s, h, nwx);
-  return cudaGetLastError();
+  if (s.store == 1) return walls_t<float>(s, stage, st);
+  if (s.store == 2) return walls_t<__nv_bfloat16>(s, stage, st);
+  return walls_t<double>(s, stage, st);
 }
 
 cudaError_t launch_gdev_update(const GDevStep& s, int stage, cudaStream_t st) {
-  const DevParams& p = s.p;
-  const dim3 grid((p.N + kThreads - 1) / kThreads, (p.nv + KB - 1) / KB);
-  const StageCoef& c = stage == 1 ? s.s1 : s.s2;
-  const float al = (float)c.alpha, be = (float)c.beta;
-  if (stage == 1) {
-    const float dt3 = (float)(p.dt / 3.0), dt37 = (float)(3.0 * p.dt / 7.0);
-    if (s.store == 1) k_gupdate1<float><<<grid, kThreads, 0, st>>>(s, al, be, dt3, dt37);
-    else k_gupdate1<__nv_bfloat16><<<grid, kThreads, 0, st>>>(s, al, be, dt3, dt37);
-  } else {
-    const float c34 = (float)(0.75 * s.c_om), dt47 = (float)(4.0 * p.dt / 7.0);
-    if (s.store == 1) k_gupdate2<float><<<grid, kThreads, 0, st>>>(s, al, be, c34, dt47);
-    else k_gupdate2<__nv_bfloat16><<<grid, kThreads, 0, st>>>(s, al, be, c34, dt47);
-  }
-  return cudaGetLastError();
+  if (s.store == 1) return update_t<float>(s, stage, st);
+  if (s.store == 2) return update_t<__nv_bfloat16>(s, stage, st);
+  return update_t<double>(s, stage, st);
 }
 
 }  // namespace dugks

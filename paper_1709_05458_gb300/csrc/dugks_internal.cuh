@@ -134,12 +134,13 @@ cudaError_t launch_dev_set_eq(const DevParams& p, int store, double rho0, const 
                               const double* ux, const double* uy, void* d, cudaStream_t st);
 cudaError_t d2q9m_prepare();
 
-// Deviation-storage form of the generic path (dugks_generic_mixed.cu), any
-// velocity set.  fhat/g/ftp/acc hold typed deviations d = f - W rho0 (store
-// 1 = FP32, 2 = BF16), fbx/fby FP32 face deviations of f-bar with the face
-// equilibrium parameters in fpx/fpy (the update forms f = alpha f-bar +
-// beta feq), mom FP64 (rho, ux, uy) of the last cell pass, eqp [5][N] its
-// FP32 equilibrium parameters.
+// Optimised generic path (dugks_generic_mixed.cu), any velocity set, in
+// three storage forms: store 0 = FP64 (rho0 = 0: the arrays hold f), 1 =
+// FP32, 2 = BF16 deviations d = f - W rho0.  fhat/ftp/acc [nv][ny][nx] of
+// the storage type; g padded; fbx/fby face values f-bar, eqp [5][N] the
+// cell equilibrium parameters of the last cell pass, fpx/fpy [5][nf] the
+// face ones, all in the compute type (FP64 for store 0, FP32 otherwise);
+// mom FP64 (rho, ux, uy).
 struct GDevRef {
   double rho0, W, Wx, Wy;       // rho0, rho0 sum W_k, rho0 sum W_k xi_x, rho0 sum W_k xi_y
 };
@@ -153,16 +154,18 @@ struct GDevStep {
   void* g;                      // stage field, padded: [nv][ny + 4][pitch], cell (i, j) at (j+2, i+2)
   int pitch;                    // gdev_pitch(nx)
   size_t plane;                 // (ny + 4) * pitch
-  float *fbx, *fby, *eqp;       // faces hold f-bar; eqp [5][N]
-  float *fpx, *fpy;             // face assembly parameters [5][nf] of x / y faces
-  const float4* vq;             // [3][nv]: (xh, xl, yh, yl), (xh, yh, W, 0), (kx, ky, 0, 0)
+  void *fbx, *fby, *eqp;        // compute type
+  void *fpx, *fpy;              // face assembly parameters [5][nf] of x / y faces
+  const void* vq;               // compute-type 4-vectors [3][nv]: (xi_x hi, lo, xi_y hi, lo),
+                                // (xi_x, xi_y, W, 0), (xi_x/dx, xi_y/dy, 0, 0); lo = 0 in FP64
   double *mom, *part;           // part: [nch][3][nf] partial face moments, or [mch][3][N] cell ones
   int nchx, nchy;
   int mch;                      // velocity chunks of the cell moments (1: one thread per cell)
   double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
 };
 int gdev_pitch(int nx);
-int gdev_chunks(const DevParams& p, int dir, int sms);
+cudaError_t gdev_prepare(int store);
+int gdev_chunks(const DevParams& p, int dir, int sms, int store);
 cudaError_t launch_gdev_cell(const GDevStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_t st);
 cudaError_t launch_gdev_walls(const GDevStep& s, int stage, cudaStream_t st);
