@@ -86,6 +86,7 @@ struct dugks_ctx {
   void* vf = nullptr;           // velocity table of that path (4-vector rows [3][nv])
   void* gpad = nullptr;         // padded stage field of that path
   void* fpar = nullptr;         // face equilibrium parameters of that path
+  double* twt = nullptr;        // FP64 Taylor weight tables of that path
   // time scheme (dugks_set_scheme): 0 T3S3; 1 T2S3, 2 T2S2 on the generic
   // kernels with the T2 stage coefficients below
   int scheme = DUGKS_T3S3;
@@ -208,6 +209,7 @@ void free_all(dugks_ctx* c) {
   if (c->vf) cudaFree(c->vf);
   if (c->gpad) cudaFree(c->gpad);
   if (c->fpar) cudaFree(c->fpar);
+  if (c->twt) cudaFree(c->twt);
   for (auto& q : c->pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -731,7 +733,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->eqp, 5 * (size_t)p.N * csz);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->fpar, 5 * 2 * nfmax * csz);
     // velocity table in the compute type, 4-vector rows [3][nv]:
-    // (xi_x hi, lo, xi_y hi, lo), (xi_x, xi_y, W_k, 0), (xi_x/dx, xi_y/dy, 0, 0);
+    // (xi_x hi, lo, xi_y hi, lo), (xi_x, xi_y, W_k, 0), flux factors (below);
     // FP32: hi = xi rounded to FP32, lo = the FP32 rounding of the remainder;
     // FP64: hi = xi, lo = 0
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->vf, 12 * (size_t)nv * csz);
@@ -750,8 +752,12 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
         r1[0] = xh;
         r1[1] = yh;
         r1[2] = vel->w[k];
-        r2[0] = x / mesh->dx;
-        r2[1] = y / mesh->dy;
+        // flux factors of the two stages: -(dt/3) alpha_1 xi/dx and
+        // -(4 dt/7) alpha_2 xi/dx (x and y)
+        r2[0] = -(dt / 3.0) * c->s1.alpha * x / mesh->dx;
+        r2[1] = -(dt / 3.0) * c->s1.alpha * y / mesh->dy;
+        r2[2] = -(4.0 * dt / 7.0) * c->s2.alpha * x / mesh->dx;
+        r2[3] = -(4.0 * dt / 7.0) * c->s2.alpha * y / mesh->dy;
       }
       if (f64) {
         e = cudaMemcpy(c->vf, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -760,6 +766,36 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
         e = cudaMemcpy(c->vf, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
       }
     }
+    // FP64: the quadratic Taylor weights of the upwind expansions per stage,
+    // direction and velocity (lower cell, upper cell), central differences
+    // on the 3x3 neighbourhood, foot offset (a dx, b dy) (eq. flux_DS)
+    if (e == cudaSuccess && f64) {
+      std::vector<double> w(4 * (size_t)nv * 18);
+      auto taylor = [](double a, double b, double* T) {
+        const double ab = 0.25 * a * b;
+        T[0] = ab;                T[1] = 0.5 * (b * b - b); T[2] = -ab;
+        T[3] = 0.5 * (a * a - a); T[4] = 1.0 - a * a - b * b; T[5] = 0.5 * (a * a + a);
+        T[6] = -ab;               T[7] = 0.5 * (b * b + b); T[8] = ab;
+      };
+      for (int st = 0; st < 2; ++st) {
+        const double h = st == 0 ? c->s1.h : c->s2.h;
+        for (int dir = 0; dir < 2; ++dir)
+          for (int k = 0; k < nv; ++k) {
+            const double x = vel->xi_x[k], y = vel->xi_y[k];
+            double* T = w.data() + ((size_t)(2 * st + dir) * nv + k) * 18;
+            if (dir == 0) {
+              taylor((0.5 * p.dx - x * h) * p.inv_dx, -y * h * p.inv_dy, T);
+              taylor((-0.5 * p.dx - x * h) * p.inv_dx, -y * h * p.inv_dy, T + 9);
+            } else {
+              taylor(-x * h * p.inv_dx, (0.5 * p.dy - y * h) * p.inv_dy, T);
+              taylor(-x * h * p.inv_dx, (-0.5 * p.dy - y * h) * p.inv_dy, T + 9);
+            }
+          }
+      }
+      e = cudaMalloc((void**)&c->twt, w.size() * sizeof(double));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(c->twt, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
       free_all(c);
       delete c;
@@ -767,6 +803,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
       return fail(e == cudaErrorMemoryAllocation ? DUGKS_ENOMEM : DUGKS_ECUDA,
                   std::string("generic path set-up: ") + cudaGetErrorString(e));
     }
+    g.tw = c->twt;
     g.fhat = c->fhat;
     g.g = c->gpad;
     g.ftp = c->ftp;

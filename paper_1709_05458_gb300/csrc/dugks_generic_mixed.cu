@@ -458,7 +458,8 @@ struct Slab {
 
 template <typename T, int DIR>
 __global__ void __launch_bounds__(LANES * NW, 2)
-k_gfaces1(GDevStep s, typename Prec<T>::C* __restrict__ fb, typename Prec<T>::C h, int kchunk) {
+k_gfaces1(GDevStep s, typename Prec<T>::C* __restrict__ fb, typename Prec<T>::C h, int kchunk,
+          const double* __restrict__ tws) {
   using C = typename Prec<T>::C;
   using V4 = typename Prec<T>::V4;
   using S = Slab<T, DIR>;
@@ -525,10 +526,17 @@ k_gfaces1(GDevStep s, typename Prec<T>::C* __restrict__ fb, typename Prec<T>::C 
     // upper one (one column / row on) for xi.n < 0; xi.n = 0 averages both
     // (uniform across the warp)
     const bool up = cn < C(0), tie = cn == C(0);
-    const C sh = up ? C(-0.5) : C(0.5);
     C Tw[9];
-    if (DIR == 0) taylor9<C>((sh * dx - cx * h) * idx_, -cy * h * idy, Tw);
-    else taylor9<C>(-cx * h * idx_, (sh * dy - cy * h) * idy, Tw);
+    if constexpr (sizeof(C) == 8) {
+      // FP64: the stage's weights from the table [k][lower 9, upper 9]
+      const double* w = tws + (size_t)k * 18 + (up ? 9 : 0);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) Tw[q] = __ldg(w + q);
+    } else {
+      const C sh = up ? C(-0.5) : C(0.5);
+      if (DIR == 0) taylor9<C>((sh * dx - cx * h) * idx_, -cy * h * idy, Tw);
+      else taylor9<C>(-cx * h * idx_, (sh * dy - cy * h) * idy, Tw);
+    }
     cp_wait1();                                    // this velocity's slab has landed
     __syncwarp();
     // x faces: rows r..r+2 (cells j-1..j+1), columns lane+q (cells fi-2+q);
@@ -554,8 +562,13 @@ k_gfaces1(GDevStep s, typename Prec<T>::C* __restrict__ fb, typename Prec<T>::C 
       }
     } else {
       C Tu[9];
-      if (DIR == 0) taylor9<C>((C(-0.5) * dx - cx * h) * idx_, -cy * h * idy, Tu);
-      else taylor9<C>(-cx * h * idx_, (C(-0.5) * dy - cy * h) * idy, Tu);
+      if constexpr (sizeof(C) == 8) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Tu[q] = __ldg(tws + (size_t)k * 18 + 9 + q);
+      } else {
+        if (DIR == 0) taylor9<C>((C(-0.5) * dx - cx * h) * idx_, -cy * h * idy, Tu);
+        else taylor9<C>(-cx * h * idx_, (C(-0.5) * dy - cy * h) * idy, Tu);
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const T* s0 = sl + r * SW;
@@ -813,18 +826,14 @@ __device__ __forceinline__ Cubic<C> flux_cubic(const GDevStep& s, int i, int j, 
   return F;
 }
 
-// kx (f-bar_e - f-bar_w) + ky (f-bar_n - f-bar_s) of velocity k
-template <typename C>
-__device__ __forceinline__ C lbar(const C (&f)[4], C kx, C ky) {
-  return fmx(kx, f[1] - f[0], ky * (f[3] - f[2]));
-}
 
 // f~(t') = 5/4 g1 - 1/4 f^ + dt/3 L*,  acc = 1/4 f^ + 3/4 g1 + 3dt/7 L*,
-// L* = -alpha lbar + W S(xi), S = -beta F
+// with dt/3 L* = k1 . (face differences of f-bar) + W S(xi), S = -(dt/3)
+// beta F and k1 = -(dt/3) alpha xi/dx (table row 2, x and y)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gupdate1(GDevStep s, typename Prec<T>::C alpha, typename Prec<T>::C beta,
-           typename Prec<T>::C dt3, typename Prec<T>::C dt37) {
+k_gupdate1(GDevStep s, typename Prec<T>::C beta, typename Prec<T>::C dt3,
+           typename Prec<T>::C r37) {
   using C = typename Prec<T>::C;
   using V4 = typename Prec<T>::V4;
   constexpr int KH = Prec<T>::KH;
@@ -834,7 +843,7 @@ k_gupdate1(GDevStep s, typename Prec<T>::C alpha, typename Prec<T>::C beta,
   if (cell >= p.N) return;
   const int nx = p.nx, ny = p.ny, nv = p.nv;
   const int j = cell / nx, i = cell - j * nx;
-  const Cubic<C> S = flux_cubic<C>(s, i, j, -beta);
+  const Cubic<C> S = flux_cubic<C>(s, i, j, -beta * dt3);
   const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
   const C* fbx = (const C*)s.fbx + (size_t)j * (nx + 1) + i;
   const C* fby = (const C*)s.fby + (size_t)j * nx + i;
@@ -860,23 +869,26 @@ k_gupdate1(GDevStep s, typename Prec<T>::C alpha, typename Prec<T>::C beta,
       if (k < nv) {
         const V4 e4 = ld4(vq + nv + k);
         const V4 k4 = ld4(vq + 2 * nv + k);
-        const C L = fmx(-alpha, lbar<C>(fv[u], k4.x, k4.y), e4.z * cubic<C>(S, e4.x, e4.y));
+        // Ls = dt/3 L*
+        const C Ls = fmx(k4.x, fv[u][1] - fv[u][0],
+                         fmx(k4.y, fv[u][3] - fv[u][2], e4.z * cubic<C>(S, e4.x, e4.y)));
         const size_t t = (size_t)k * p.N + cell;
         const C f0 = tof(fh[u]), g0 = tof(gg[u]);
-        stv((T*)s.ftp + t, fmx(C(1.25), g0, fmx(C(-0.25), f0, dt3 * L)));
-        stv((T*)s.acc + t, fmx(C(0.25), f0, fmx(C(0.75), g0, dt37 * L)));
+        stv((T*)s.ftp + t, fmx(C(1.25), g0, fmx(C(-0.25), f0, Ls)));
+        stv((T*)s.acc + t, fmx(C(0.25), f0, fmx(C(0.75), g0, r37 * Ls)));
       }
     }
   }
 }
 
 // f^^{n+1} = acc + 3/4 dt Omega' + 4dt/7 L**,  dt Omega' = c_om (f~' - feq');
-// = acc + c34 f~' - (4dt/7) alpha lbar + W S(xi),
-// S = -c34 P_cell - (4dt/7) beta F  (P_cell with -rho0 for the deviations)
+// = acc + c34 f~' + k2 . (face differences of f-bar) + W S(xi),
+// S = -c34 P_cell - (4dt/7) beta F  (P_cell with -rho0 for the deviations),
+// k2 = -(4dt/7) alpha xi/dx (table row 2, z and w)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_gupdate2(GDevStep s, typename Prec<T>::C alpha, typename Prec<T>::C beta,
-           typename Prec<T>::C c_om34, typename Prec<T>::C dt47) {
+k_gupdate2(GDevStep s, typename Prec<T>::C beta, typename Prec<T>::C c_om34,
+           typename Prec<T>::C dt47) {
   using C = typename Prec<T>::C;
   using V4 = typename Prec<T>::V4;
   constexpr int KH = Prec<T>::KH;
@@ -896,7 +908,6 @@ k_gupdate2(GDevStep s, typename Prec<T>::C alpha, typename Prec<T>::C beta,
     S.c[4] = fmx(-c_om34, c.cxy, S.c[4]);
     S.c[5] = fmx(-c_om34, c.cyy, S.c[5]);
   }
-  const C adt = dt47 * alpha;
   const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
   const C* fbx = (const C*)s.fbx + (size_t)j * (nx + 1) + i;
   const C* fby = (const C*)s.fby + (size_t)j * nx + i;
@@ -923,7 +934,8 @@ k_gupdate2(GDevStep s, typename Prec<T>::C alpha, typename Prec<T>::C beta,
       if (k < nv) {
         const V4 e4 = ld4(vq + nv + k);
         const V4 k4 = ld4(vq + 2 * nv + k);
-        const C src = fmx(-adt, lbar<C>(fv[u], k4.x, k4.y), e4.z * cubic<C>(S, e4.x, e4.y));
+        const C src = fmx(k4.z, fv[u][1] - fv[u][0],
+                          fmx(k4.w, fv[u][3] - fv[u][2], e4.z * cubic<C>(S, e4.x, e4.y)));
         stv((T*)s.fhat + (size_t)k * p.N + cell, fmx(c_om34, tof(ft[u]), tof(ac[u]) + src));
       }
     }
@@ -956,7 +968,8 @@ cudaError_t cell_t(const GDevStep& s, const void* src, const StageCoef& c, cudaS
 }
 
 template <typename T, int DIR>
-cudaError_t faces_t(const GDevStep& s, const StageCoef& c, cudaStream_t st) {
+cudaError_t faces_t(const GDevStep& s, int stage, cudaStream_t st) {
+  const StageCoef& c = stage == 1 ? s.s1 : s.s2;
   using C = typename Prec<T>::C;
   const DevParams& p = s.p;
   C* fb = (C*)(DIR == 0 ? s.fbx : s.fby);
@@ -966,7 +979,8 @@ cudaError_t faces_t(const GDevStep& s, const StageCoef& c, cudaStream_t st) {
   const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
   const dim3 grid(DIR == 0 ? (p.nx + 1 + LANES - 1) / LANES : (p.nx + LANES - 1) / LANES,
                   DIR == 0 ? (p.ny + R - 1) / R : (p.ny + 1 + R - 1) / R, nch);
-  k_gfaces1<T, DIR><<<grid, LANES * NW, Slab<T, DIR>::BYTES, st>>>(s, fb, (C)c.h, kchunk);
+  const double* tws = s.tw ? s.tw + ((size_t)(stage == 1 ? 0 : 2) + DIR) * p.nv * 18 : nullptr;
+  k_gfaces1<T, DIR><<<grid, LANES * NW, Slab<T, DIR>::BYTES, st>>>(s, fb, (C)c.h, kchunk, tws);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_gfacepar<C, DIR><<<(nf + 255) / 256, 256, 0, st>>>(s, fpar, nch);
@@ -991,13 +1005,12 @@ cudaError_t update_t(const GDevStep& s, int stage, cudaStream_t st) {
   const DevParams& p = s.p;
   const dim3 grid((p.N + kThreads - 1) / kThreads, (p.nv + KB - 1) / KB);
   const StageCoef& c = stage == 1 ? s.s1 : s.s2;
-  const C al = (C)c.alpha, be = (C)c.beta;
+  const C be = (C)c.beta;
   if (stage == 1) {
-    const C dt3 = (C)(p.dt / 3.0), dt37 = (C)(3.0 * p.dt / 7.0);
-    k_gupdate1<T><<<grid, kThreads, 0, st>>>(s, al, be, dt3, dt37);
+    k_gupdate1<T><<<grid, kThreads, 0, st>>>(s, be, (C)(p.dt / 3.0), (C)(9.0 / 7.0));
   } else {
     const C c34 = (C)(0.75 * s.c_om), dt47 = (C)(4.0 * p.dt / 7.0);
-    k_gupdate2<T><<<grid, kThreads, 0, st>>>(s, al, be, c34, dt47);
+    k_gupdate2<T><<<grid, kThreads, 0, st>>>(s, be, c34, dt47);
   }
   return cudaGetLastError();
 }
@@ -1075,12 +1088,12 @@ cudaError_t launch_gdev_cell(const GDevStep& s, int stage, cudaStream_t st) {
 }
 
 cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_t st) {
-  const StageCoef& c = stage == 1 ? s.s1 : s.s2;
   if (s.store == 1)
-    return dir == 0 ? faces_t<float, 0>(s, c, st) : faces_t<float, 1>(s, c, st);
+    return dir == 0 ? faces_t<float, 0>(s, stage, st) : faces_t<float, 1>(s, stage, st);
   if (s.store == 2)
-    return dir == 0 ? faces_t<__nv_bfloat16, 0>(s, c, st) : faces_t<__nv_bfloat16, 1>(s, c, st);
-  return dir == 0 ? faces_t<double, 0>(s, c, st) : faces_t<double, 1>(s, c, st);
+    return dir == 0 ? faces_t<__nv_bfloat16, 0>(s, stage, st)
+                    : faces_t<__nv_bfloat16, 1>(s, stage, st);
+  return dir == 0 ? faces_t<double, 0>(s, stage, st) : faces_t<double, 1>(s, stage, st);
 }
 
 cudaError_t launch_gdev_walls(const GDevStep& s, int stage, cudaStream_t st) {

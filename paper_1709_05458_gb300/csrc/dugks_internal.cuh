@@ -157,11 +157,13 @@ struct GDevStep {
   void *fbx, *fby, *eqp;        // compute type
   void *fpx, *fpy;              // face assembly parameters [5][nf] of x / y faces
   const void* vq;               // compute-type 4-vectors [3][nv]: (xi_x hi, lo, xi_y hi, lo),
-                                // (xi_x, xi_y, W, 0), (xi_x/dx, xi_y/dy, 0, 0); lo = 0 in FP64
+                                // (xi_x, xi_y, W, 0), stage flux factors (-(dt/3) alpha_1 xi/dx,
+                                // y, -(4dt/7) alpha_2 xi/dx, y); lo = 0 in FP64
   double *mom, *part;           // part: [nch][3][nf] partial face moments, or [mch][3][N] cell ones
   int nchx, nchy;
   int mch;                      // velocity chunks of the cell moments (1: one thread per cell)
   double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
+  const double* tw;             // FP64 storage: Taylor weights [stage][dir][nv][lower 9, upper 9]
 };
 int gdev_pitch(int nx);
 cudaError_t gdev_prepare(int store);
