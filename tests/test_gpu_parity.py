@@ -111,10 +111,14 @@ def test_cavity256_workload_full_compare(cuda):
     assert rel_linf(g.state(), fo) <= TOL
 
 
+@pytest.mark.parametrize("kernels", ["optimised", "first"])
 @pytest.mark.parametrize("walls", ["diffuse", "couette", "mixed"])
-def test_newton_cotes_walls(cuda, walls):
+def test_newton_cotes_walls(cuda, monkeypatch, walls, kernels):
     """Newton-Cotes velocity grid with diffuse-scattering walls (more than 32
-    velocities: the grouped-velocity kernels)."""
+    velocities), on the optimised generic kernels and on the first generic
+    kernels (DUGKS_LEGACY_GENERIC=1; they also serve the T2 schemes, the
+    adjoint's forward recomputation and the allocation-free entry)."""
+    monkeypatch.setenv("DUGKS_LEGACY_GENERIC", "1" if kernels == "first" else "0")
     uw = 0.16 * np.sqrt(5 / 3 * 0.5)
     bc = {"diffuse": [(P.DIFFUSE, 0, 0)] * 3 + [(P.DIFFUSE, uw, 0)],
           "couette": [(P.PERIODIC, 0, 0)] * 2 + [(P.DIFFUSE, -uw, 0), (P.DIFFUSE, uw, 0)],
