@@ -46,32 +46,38 @@ FLOPS_PER_UNIT = {
     # part (stage 1: L*, f~', moments, feq', dt Omega', g2, X = 25.9;
     # stage 2: L**, f^, moments, feq, g1 = 13.8)
     "d2q9_stage1": 72.3, "d2q9_stage2": 60.2,
-    # deviation forms: the same arithmetic, mostly in FP32; counted the same way
-    "d2q9m_stage1": 72.3, "d2q9m_stage2": 60.2,
-    # deviation forms on the generic kernels: the FP64 part is the moment
-    # sums (one add and two FMAs = 5 flops per cell- or face-velocity); at
-    # the FP64 peak it takes longer than the kernels' algorithmic bytes at
-    # the HBM peak, so it is their bound
-    "gdev_cell": 5, "gdev_face_x": 5, "gdev_face_y": 5,
     # T2 schemes on the generic kernels (counted as the T3S3 generic ones)
     "t2_cell": 17, "t2_face_x": 34, "t2_face_y": 34, "t2_update": 19,
 }
 SCHEMES = {"t3s3": 0, "t2s3": 1, "t2s2": 2}
 # The same kernels in FP64 (dugks_generic_mixed.cu with FP64 storage): all
-# their arithmetic is FP64 -- cell: moment sums 5 + g from the equilibrium
-# quadratic 12; face: 9-point stencil 18 + moment sums 5; updates: the
-# cubic equilibrium term 20 + face differences 5 + the stage maps 10 / 5.
+# their arithmetic is FP64 -- cell: moment sums 5 + g = a f + b W P(xi) with
+# P quadratic (5 FMAs) 14; face: 9-point stencil 18 + moment sums 5;
+# updates: the cubic equilibrium term W S(xi) (10 FMAs + 1) + face
+# differences 6 + the stage maps 9 (stage 1) / 3 (stage 2).
 FLOPS_PER_UNIT_GDEV_FP64 = {
-    "gdev_cell": 17, "gdev_face_x": 23, "gdev_face_y": 23,
-    "gdev_update_stage1": 35, "gdev_update_stage2": 30,
+    "gdev_cell": 19, "gdev_face_x": 23, "gdev_face_y": 23,
+    "gdev_update_stage1": 36, "gdev_update_stage2": 30,
 }
-# Kernels bound by HBM instead: algorithmic bytes per cell-velocity by
-# storage form (FP32 / BF16 per-cell arrays; face values are FP32 in both).
+# On a tensor velocity grid (Newton-Cotes n x n with n a multiple of 16) the
+# 16 velocities a thread takes share xi_x: P and S reduce, once per thread,
+# to polynomials in xi_y (2 and 3 FMAs per velocity).
+FLOPS_PER_UNIT_GDEV_FP64_TGRID = {
+    "gdev_cell": 13, "gdev_update_stage1": 22, "gdev_update_stage2": 16,
+}
+# The deviation forms (FP32 / BF16 per-cell arrays; face values FP32 in
+# both) against HBM: algorithmic bytes per cell- or face-velocity.
 HBM_BYTES_PER_UNIT = {
+    # moments: read d; g pass: read d, write g
+    "gdev_cell": {"fp32": 12, "bf16": 6},
+    # face pass: read g, write the face value f-bar (FP32)
+    "gdev_face_x": {"fp32": 8, "bf16": 6}, "gdev_face_y": {"fp32": 8, "bf16": 6},
     # read f^, g1, x and y faces; write f~', acc
     "gdev_update_stage1": {"fp32": 24, "bf16": 16},
     # read f~', acc, x and y faces; write f^
     "gdev_update_stage2": {"fp32": 20, "bf16": 14},
+    # fused D2Q9 stage kernels: read g and the cell's own array, write two arrays
+    "d2q9m_stage1": {"fp32": 16, "bf16": 8}, "d2q9m_stage2": {"fp32": 16, "bf16": 8},
 }
 # Algorithmic DRAM bytes per unit (FP64 values each kernel must read/write once).
 BYTES_PER_UNIT = {
@@ -420,8 +426,12 @@ def run_ours(args):
     hbm_per_unit = dict(HBM_BYTES_PER_UNIT)
     if args.storage == "fp64":
         flops_per_unit.update(FLOPS_PER_UNIT_GDEV_FP64)
-        for k in FLOPS_PER_UNIT_GDEV_FP64:
-            hbm_per_unit.pop(k, None)
+        if c.get("vel") == "nc" and c["nv1"] % 16 == 0:
+            flops_per_unit.update(FLOPS_PER_UNIT_GDEV_FP64_TGRID)
+        hbm_per_unit = {}
+    else:
+        for k in hbm_per_unit:
+            flops_per_unit.pop(k, None)
     name, (nl, kms) = max(((k, v) for k, v in prof.items()
                            if (k in flops_per_unit or k in hbm_per_unit)
                            and v[0] > 0 and v[1] > 0),

@@ -714,6 +714,14 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     g.s1 = c->s1;
     g.s2 = c->s2;
     g.c_om = c->c_om;
+    {   // tensor velocity grid with xi_x constant over runs of n >= 16 (n % 16 == 0)
+      int n = 0;
+      while ((long long)(n + 1) * (n + 1) <= nv) ++n;
+      bool tg = n * n == nv && n % 16 == 0;
+      for (int k = 0; tg && k < nv; ++k)
+        tg = vel->xi_x[k] == vel->xi_x[(k / n) * n] && vel->xi_y[k] == vel->xi_y[k % n];
+      g.tgrid = tg ? 1 : 0;
+    }
     e = gdev_prepare(storage);
     g.nchx = gdev_chunks(p, 0, sms, storage);
     g.nchy = gdev_chunks(p, 1, sms, storage);

@@ -339,7 +339,7 @@ k_gmomfin(GDevStep s, int nchunk) {
 // (3) g = a src + b W_k P(xi_k): one thread per cell and 16 consecutive
 // velocities (two batches of eight loads in flight), P the cell's
 // equilibrium quadratic in xi.
-template <typename T>
+template <typename T, bool TG>
 __global__ void __launch_bounds__(kThreads)
 k_gcellg(GDevStep s, const T* __restrict__ src, typename Prec<T>::C a, typename Prec<T>::C b) {
   using C = typename Prec<T>::C;
@@ -352,6 +352,9 @@ k_gcellg(GDevStep s, const T* __restrict__ src, typename Prec<T>::C a, typename 
   const int nv = p.nv;
   const int j = cell / p.nx, i = cell - j * p.nx;
   const Quad<C> P = quad((const C*)s.eqp, p.N, cell);   // W_k P: W_k (rho P_k - rho0)
+  // TG (tensor grid): the 16 velocities share xi_x, P(x, y) = a + y (b + y c)
+  const C x0 = TG ? ld4(vq + nv + blockIdx.y * CB).x : C(0);
+  const C pa = fmx(x0, fmx(x0, P.cxx, P.cx), P.c0), pb = fmx(x0, P.cxy, P.cy);
   T* __restrict__ g = (T*)s.g;
   for (int h = 0; h < CB; h += CH) {
     const int kb = blockIdx.y * CB + h;
@@ -365,7 +368,8 @@ k_gcellg(GDevStep s, const T* __restrict__ src, typename Prec<T>::C a, typename 
       if (k < nv) {
         const V4 e4 = ld4(vq + nv + k);
         const C x = e4.x, y = e4.y;
-        const C pk = fmx(x, fmx(x, P.cxx, fmx(y, P.cxy, P.cx)), fmx(y, fmx(y, P.cyy, P.cy), P.c0));
+        const C pk = TG ? fmx(y, fmx(y, P.cyy, pb), pa)
+                        : fmx(x, fmx(x, P.cxx, fmx(y, P.cxy, P.cx)), fmx(y, fmx(y, P.cyy, P.cy), P.c0));
         stv(g + gp_at(s, k, i, j), fmx(b * e4.z, pk, a * tof(d[u])));
       }
     }
@@ -800,6 +804,26 @@ __device__ __forceinline__ C cubic(const Cubic<C>& S, C x, C y) {
   const C Y = fmx(y, t3, S.c[2]);
   return fmx(x, X, fmx(y, Y, S.c[0]));
 }
+// On a tensor velocity grid whose 16 consecutive velocities share xi_x
+// (GDevStep::tgrid): the cubic at fixed x as a cubic in y, b0 + y (b1 +
+// y (b2 + y b3)), formed once per thread.
+template <typename C> struct CubicY {
+  C b0, b1, b2, b3;
+};
+template <typename C>
+__device__ __forceinline__ CubicY<C> cubic_at_x(const Cubic<C>& S, C x) {
+  CubicY<C> o;
+  o.b0 = fmx(x, fmx(x, fmx(x, S.c[6], S.c[3]), S.c[1]), S.c[0]);
+  o.b1 = fmx(x, fmx(x, S.c[7], S.c[4]), S.c[2]);
+  o.b2 = fmx(x, S.c[8], S.c[5]);
+  o.b3 = S.c[9];
+  return o;
+}
+template <typename C>
+__device__ __forceinline__ C cubic_y(const CubicY<C>& B, C y) {
+  return fmx(y, fmx(y, fmx(y, B.b3, B.b2), B.b1), B.b0);
+}
+
 // F(xi) = (x/dx)(P_E - P_W) + (y/dy)(P_N - P_S) for the faces of cell (i, j),
 // scaled by sc
 template <typename C>
@@ -830,7 +854,7 @@ __device__ __forceinline__ Cubic<C> flux_cubic(const GDevStep& s, int i, int j, 
 // f~(t') = 5/4 g1 - 1/4 f^ + dt/3 L*,  acc = 1/4 f^ + 3/4 g1 + 3dt/7 L*,
 // with dt/3 L* = k1 . (face differences of f-bar) + W S(xi), S = -(dt/3)
 // beta F and k1 = -(dt/3) alpha xi/dx (table row 2, x and y)
-template <typename T>
+template <typename T, bool TG>
 __global__ void __launch_bounds__(kThreads)
 k_gupdate1(GDevStep s, typename Prec<T>::C beta, typename Prec<T>::C dt3,
            typename Prec<T>::C r37) {
@@ -847,6 +871,8 @@ k_gupdate1(GDevStep s, typename Prec<T>::C beta, typename Prec<T>::C dt3,
   const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
   const C* fbx = (const C*)s.fbx + (size_t)j * (nx + 1) + i;
   const C* fby = (const C*)s.fby + (size_t)j * nx + i;
+  // TG (tensor grid): the 16 velocities of this thread share xi_x
+  const CubicY<C> SY = cubic_at_x<C>(S, TG ? ld4(vq + nv + blockIdx.y * KB).x : C(0));
   for (int hb = 0; hb < KB; hb += KH) {
     const int kb = blockIdx.y * KB + hb;
     T fh[KH], gg[KH];
@@ -870,8 +896,8 @@ k_gupdate1(GDevStep s, typename Prec<T>::C beta, typename Prec<T>::C dt3,
         const V4 e4 = ld4(vq + nv + k);
         const V4 k4 = ld4(vq + 2 * nv + k);
         // Ls = dt/3 L*
-        const C Ls = fmx(k4.x, fv[u][1] - fv[u][0],
-                         fmx(k4.y, fv[u][3] - fv[u][2], e4.z * cubic<C>(S, e4.x, e4.y)));
+        const C sk = TG ? cubic_y<C>(SY, e4.y) : cubic<C>(S, e4.x, e4.y);
+        const C Ls = fmx(k4.x, fv[u][1] - fv[u][0], fmx(k4.y, fv[u][3] - fv[u][2], e4.z * sk));
         const size_t t = (size_t)k * p.N + cell;
         const C f0 = tof(fh[u]), g0 = tof(gg[u]);
         stv((T*)s.ftp + t, fmx(C(1.25), g0, fmx(C(-0.25), f0, Ls)));
@@ -885,7 +911,7 @@ k_gupdate1(GDevStep s, typename Prec<T>::C beta, typename Prec<T>::C dt3,
 // = acc + c34 f~' + k2 . (face differences of f-bar) + W S(xi),
 // S = -c34 P_cell - (4dt/7) beta F  (P_cell with -rho0 for the deviations),
 // k2 = -(4dt/7) alpha xi/dx (table row 2, z and w)
-template <typename T>
+template <typename T, bool TG>
 __global__ void __launch_bounds__(kThreads)
 k_gupdate2(GDevStep s, typename Prec<T>::C beta, typename Prec<T>::C c_om34,
            typename Prec<T>::C dt47) {
@@ -911,6 +937,7 @@ k_gupdate2(GDevStep s, typename Prec<T>::C beta, typename Prec<T>::C c_om34,
   const size_t nfx = (size_t)ny * (nx + 1), nfy = (size_t)(ny + 1) * nx;
   const C* fbx = (const C*)s.fbx + (size_t)j * (nx + 1) + i;
   const C* fby = (const C*)s.fby + (size_t)j * nx + i;
+  const CubicY<C> SY = cubic_at_x<C>(S, TG ? ld4(vq + nv + blockIdx.y * KB).x : C(0));
   for (int hb = 0; hb < KB; hb += KH) {
     const int kb = blockIdx.y * KB + hb;
     T ft[KH], ac[KH];
@@ -934,8 +961,8 @@ k_gupdate2(GDevStep s, typename Prec<T>::C beta, typename Prec<T>::C c_om34,
       if (k < nv) {
         const V4 e4 = ld4(vq + nv + k);
         const V4 k4 = ld4(vq + 2 * nv + k);
-        const C src = fmx(k4.z, fv[u][1] - fv[u][0],
-                          fmx(k4.w, fv[u][3] - fv[u][2], e4.z * cubic<C>(S, e4.x, e4.y)));
+        const C sk = TG ? cubic_y<C>(SY, e4.y) : cubic<C>(S, e4.x, e4.y);
+        const C src = fmx(k4.z, fv[u][1] - fv[u][0], fmx(k4.w, fv[u][3] - fv[u][2], e4.z * sk));
         stv((T*)s.fhat + (size_t)k * p.N + cell, fmx(c_om34, tof(ft[u]), tof(ac[u]) + src));
       }
     }
@@ -957,8 +984,11 @@ cudaError_t cell_t(const GDevStep& s, const void* src, const StageCoef& c, cudaS
     k_gmomfin<C><<<(p.N + kThreads - 1) / kThreads, kThreads, 0, st>>>(s, s.mch);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_gcellg<T><<<dim3((p.N + kThreads - 1) / kThreads, (p.nv + 15) / 16), kThreads, 0, st>>>(
-        s, (const T*)src, (C)c.a, (C)c.b);
+    const dim3 grid((p.N + kThreads - 1) / kThreads, (p.nv + 15) / 16);
+    if (s.tgrid)
+      k_gcellg<T, true><<<grid, kThreads, 0, st>>>(s, (const T*)src, (C)c.a, (C)c.b);
+    else
+      k_gcellg<T, false><<<grid, kThreads, 0, st>>>(s, (const T*)src, (C)c.a, (C)c.b);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1007,10 +1037,13 @@ cudaError_t update_t(const GDevStep& s, int stage, cudaStream_t st) {
   const StageCoef& c = stage == 1 ? s.s1 : s.s2;
   const C be = (C)c.beta;
   if (stage == 1) {
-    k_gupdate1<T><<<grid, kThreads, 0, st>>>(s, be, (C)(p.dt / 3.0), (C)(9.0 / 7.0));
+    const C dt3 = (C)(p.dt / 3.0), r37 = (C)(9.0 / 7.0);
+    if (s.tgrid) k_gupdate1<T, true><<<grid, kThreads, 0, st>>>(s, be, dt3, r37);
+    else k_gupdate1<T, false><<<grid, kThreads, 0, st>>>(s, be, dt3, r37);
   } else {
     const C c34 = (C)(0.75 * s.c_om), dt47 = (C)(4.0 * p.dt / 7.0);
-    k_gupdate2<T><<<grid, kThreads, 0, st>>>(s, be, c34, dt47);
+    if (s.tgrid) k_gupdate2<T, true><<<grid, kThreads, 0, st>>>(s, be, c34, dt47);
+    else k_gupdate2<T, false><<<grid, kThreads, 0, st>>>(s, be, c34, dt47);
   }
   return cudaGetLastError();
 }

@@ -164,6 +164,8 @@ struct GDevStep {
   int mch;                      // velocity chunks of the cell moments (1: one thread per cell)
   double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
   const double* tw;             // FP64 storage: Taylor weights [stage][dir][nv][lower 9, upper 9]
+  int tgrid;                    // 1: xi_k = (X[k / n], Y[k % n]) with n a multiple of 16, so the
+                                // 16 velocities an update / g-pass thread takes share xi_x
 };
 int gdev_pitch(int nx);
 cudaError_t gdev_prepare(int store);
