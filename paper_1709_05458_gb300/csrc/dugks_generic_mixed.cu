@@ -445,6 +445,16 @@ __device__ __forceinline__ void taylor9(C a, C b, C (&T)[9]) {
 // double-buffered so the next velocity's slab loads while the current one
 // is used; stencils in C, per-thread partial face moments, combined in FP64
 // per velocity chunk into part[chunk][3][nf].
+// Face-pass grid: face columns 0 .. nx of the x faces (0 .. nx - 1 with
+// walls in x: faces 0 and nx are the wall kernel's), all nx columns of the
+// y faces; rows likewise.
+inline int face_blocks_x(const DevParams& p, int dir) {
+  return (p.nx + (dir == 0 && p.px ? 1 : 0) + LANES - 1) / LANES;
+}
+inline int face_blocks_y(const DevParams& p, int dir) {
+  return (p.ny + (dir == 1 && p.py ? 1 : 0) + R - 1) / R;
+}
+
 template <typename T, int DIR>
 struct Slab {
   static constexpr int SR = DIR == 0 ? R + 2 : R + 3;          // rows
@@ -550,14 +560,35 @@ k_gfaces1(GDevStep s, typename Prec<T>::C* __restrict__ fb, typename Prec<T>::C 
     C* fbk = fb + (size_t)k * nf;
     if (!tie) {
       const T* sb = sl + (up ? uoff : 0);
+      // FP32 arithmetic (issue-bound): a sliding window of three stencil
+      // rows reads each slab row once; FP64 (FP64-pipe-bound, at its
+      // register limit) reads the nine values per face
+      constexpr bool WIN = sizeof(C) == 4;
+      C wr[3][3];
+      if constexpr (WIN) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) wr[a + 1][q] = lds(sb + a * SW + q);
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const T* s0 = sb + r * SW;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            if constexpr (WIN) {
+              if (a < 2) wr[a][q] = wr[a + 1][q];
+              else wr[2][q] = lds(sb + (r + 2) * SW + q);
+            } else {
+              wr[a][q] = lds(sb + (r + a) * SW + q);
+            }
+          }
         C v = C(0);
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-          for (int q = 0; q < 3; ++q) v = fmx(Tw[a * 3 + q], lds(s0 + a * SW + q), v);
+          for (int q = 0; q < 3; ++q) v = fmx(Tw[a * 3 + q], wr[a][q], v);
         const int face = DIR == 0 ? (r0 + r) * (nx + 1) + col : (r0 + r) * nx + col;
         if (ok[r]) fbk[face] = v;
         acc_add(acc[r][0], v);                     // rows without a face are never stored
@@ -1007,8 +1038,7 @@ cudaError_t faces_t(const GDevStep& s, int stage, cudaStream_t st) {
   const int nch = DIR == 0 ? s.nchx : s.nchy;
   const int kchunk = (p.nv + nch - 1) / nch;
   const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
-  const dim3 grid(DIR == 0 ? (p.nx + 1 + LANES - 1) / LANES : (p.nx + LANES - 1) / LANES,
-                  DIR == 0 ? (p.ny + R - 1) / R : (p.ny + 1 + R - 1) / R, nch);
+  const dim3 grid(face_blocks_x(p, DIR), face_blocks_y(p, DIR), nch);
   const double* tws = s.tw ? s.tw + ((size_t)(stage == 1 ? 0 : 2) + DIR) * p.nv * 18 : nullptr;
   k_gfaces1<T, DIR><<<grid, LANES * NW, Slab<T, DIR>::BYTES, st>>>(s, fb, (C)c.h, kchunk, tws);
   cudaError_t e = cudaGetLastError();
@@ -1096,8 +1126,7 @@ int gdev_chunks(const DevParams& p, int dir, int sms, int store) {
   else if (store == 2) occ = dir == 0 ? occupancy<__nv_bfloat16, 0>() : occupancy<__nv_bfloat16, 1>();
   else occ = dir == 0 ? occupancy<double, 0>() : occupancy<double, 1>();
   const long slots = (long)occ * (sms > 0 ? sms : 1);
-  const long base = dir == 0 ? (long)((p.nx + LANES) / LANES) * ((p.ny + R - 1) / R)
-                             : (long)((p.nx + LANES - 1) / LANES) * ((p.ny + R) / R);
+  const long base = (long)face_blocks_x(p, dir) * face_blocks_y(p, dir);
   const int maxc = p.nv < 64 ? p.nv : 64;
   int best = 1;
   double bestc = 1e300;
