@@ -78,6 +78,8 @@ HBM_BYTES_PER_UNIT = {
     "gdev_update_stage2": {"fp32": 20, "bf16": 14},
     # fused D2Q9 stage kernels: read g and the cell's own array, write two arrays
     "d2q9m_stage1": {"fp32": 16, "bf16": 8}, "d2q9m_stage2": {"fp32": 16, "bf16": 8},
+    # the same in double-word arithmetic on FP64 arrays
+    "d2q9dw_stage1": {"f64dw": 32}, "d2q9dw_stage2": {"f64dw": 32},
 }
 # Algorithmic DRAM bytes per unit (FP64 values each kernel must read/write once).
 BYTES_PER_UNIT = {
@@ -337,7 +339,8 @@ def run_ours(args):
     dev_index = torch.cuda.current_device()
     stream = torch.cuda.Stream()
     P.load()
-    main_storage = {"fp64": P.FP64, "fp32": P.G_FP32, "bf16": P.G_BF16}[args.storage]
+    main_storage = {"fp64": P.FP64, "fp32": P.G_FP32, "bf16": P.G_BF16,
+                    "f64dw": P.F64_DW}[args.storage]
     solver, c, nv = make_solver(P, PV, WL, stream, storage=main_storage, scheme=args.scheme)
     units = c["nx"] * c["ny"] * nv
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -395,7 +398,8 @@ def run_ours(args):
     # protocol; E(u) against the FP64 run after the same W + K steps
     forms = {}
     if not args.no_forms and args.storage == "fp64" and args.scheme == "t3s3":
-        for label, st in (("fp32", P.G_FP32), ("bf16", P.G_BF16)):
+        extra = (("f64dw", P.F64_DW),) if c.get("vel") != "nc" else ()
+        for label, st in (("fp32", P.G_FP32), ("bf16", P.G_BF16)) + extra:
             s2, _, _ = make_solver(P, PV, WL, stream, storage=st)
             for _ in range(max(args.warmup, 0)):
                 s2.step(1)
@@ -461,7 +465,8 @@ def run_ours(args):
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32 deviation storage, f64 moment sums",
-                  "bf16": "bf16 deviation storage, f32 arithmetic, f64 moment sums"}[args.storage],
+                  "bf16": "bf16 deviation storage, f32 arithmetic, f64 moment sums",
+                  "f64dw": "f64 storage, double-word (f32 pair) arithmetic"}[args.storage],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": f"{nx}x{ny}", "scheme": args.scheme.upper(),
                    "velocities": ("D2Q9" if c.get("vel") != "nc"
@@ -510,7 +515,7 @@ def main():
     ap.add_argument("--scheme", default="t3s3", choices=list(SCHEMES),
                     help="time scheme (T2S3/T2S2: the second-order comparison schemes, "
                          "generic FP64 kernels; the step they time is a T2 step)")
-    ap.add_argument("--storage", default="fp64", choices=["fp64", "fp32", "bf16"],
+    ap.add_argument("--storage", default="fp64", choices=["fp64", "fp32", "bf16", "f64dw"],
                     help="storage form of the measured line (default FP64)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP32/BF16 deviation-storage forms")

@@ -59,15 +59,24 @@ enum { DUGKS_WEST = 0, DUGKS_EAST = 1, DUGKS_SOUTH = 2, DUGKS_NORTH = 3 };
  *                  magnitude (rho below ~18); larger ones turn the moment
  *                  into NaN, which dugks_check reports as DUGKS_EUNSTABLE.
  *   DUGKS_G_BF16 : as DUGKS_G_FP32 with the deviations stored in BF16.
+ *   DUGKS_F64_DW : FP64 storage; every operation of the step in double-word
+ *                  arithmetic (a value is an unevaluated sum of two FP32
+ *                  numbers, 48-bit significand, unit roundoff 2^-48; sums
+ *                  with a normwise error bound), which GB300 runs on its
+ *                  FP32 pipes.  Fused D2Q9 kernels only: other velocity
+ *                  sets, DUGKS_FORCE_GENERIC=1, the T2 schemes, the adjoint
+ *                  and the batched launch refuse it (DUGKS_ENOTIMPL; a batch
+ *                  steps such a context with its own launches).
  * The description above is that of the fused D2Q9 kernels, taken when the
  * set is in the D2Q9 listing order of Sec. 2.2 (xi_k = c (k/3 - 1, k%3 - 1)).
  * Any other velocity set (Newton-Cotes grids) runs the deviation forms on
  * the generic kernels: the same FP32/BF16 storage and FP32 stencils, FP32
- * face values, moment sums of every cell and face accumulated in FP64 from
- * the exactly converted FP32 terms (no magnitude limit; a non-finite
- * deviation gives a non-finite moment).  States cross the ABI in FP64 for
- * every form. */
-enum { DUGKS_FP64 = 0, DUGKS_G_FP32 = 1, DUGKS_G_BF16 = 2 };
+ * face values, moment sums of every cell and face accumulated as
+ * compensated FP32 pairs (each product and sum error-free transformed, the
+ * pair rounded once to FP64; no magnitude limit; a non-finite deviation
+ * gives a non-finite moment).  States cross the ABI in FP64 for every
+ * form. */
+enum { DUGKS_FP64 = 0, DUGKS_G_FP32 = 1, DUGKS_G_BF16 = 2, DUGKS_F64_DW = 3 };
 
 typedef struct dugks_ctx dugks_ctx;   /* opaque, owned by the library */
 
@@ -96,7 +105,8 @@ typedef struct { int kind; double uw_x, uw_y; } dugks_bc;
  *                 extrapolation uses three cells); bounce-back needs -xi_k in
  *                 the set for every velocity leaving that wall; diffuse walls
  *                 need at least one velocity leaving the wall.
- *   storage     : DUGKS_FP64, DUGKS_G_FP32 or DUGKS_G_BF16 (see above).
+ *   storage     : DUGKS_FP64, DUGKS_G_FP32, DUGKS_G_BF16 or DUGKS_F64_DW
+ *                 (see above).
  *   cuda_stream : cudaStream_t (may be NULL = legacy default stream) on which
  *                 every later call of this context runs.
  *   out         : receives the new context.

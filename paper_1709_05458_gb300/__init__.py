@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libdugks.so")
 DUGKS_OK, DUGKS_EINVAL, DUGKS_ECUDA, DUGKS_ENOMEM, DUGKS_EUNSTABLE, DUGKS_ENOTIMPL = 0, -1, -2, -3, -4, -5
 PERIODIC, BOUNCEBACK, DIFFUSE = 0, 1, 2
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
-FP64, G_FP32, G_BF16 = 0, 1, 2
+FP64, G_FP32, G_BF16, F64_DW = 0, 1, 2, 3
 T3S3, T2S3, T2S2 = 0, 1, 2
 
 # every symbol include/dugks.h declares

@@ -37,7 +37,8 @@ const char* kNames[K_NUM] = {
     "d2q9_prologue", "d2q9_stage1", "d2q9_stage2",
     "d2q9m_stage1", "d2q9m_stage2", "convert",
     "gdev_cell", "gdev_face_x", "gdev_face_y", "gdev_walls", "gdev_update_stage1",
-    "gdev_update_stage2", "t2_cell", "t2_face_x", "t2_face_y", "t2_update"};
+    "gdev_update_stage2", "t2_cell", "t2_face_x", "t2_face_y", "t2_update",
+    "d2q9dw_stage1", "d2q9dw_stage2"};
 
 struct Pending {
   int id;
@@ -73,6 +74,11 @@ struct dugks_ctx {
   bool g1_valid = false;
   D2Q9Params dp{};
   D2Q9Stage ds1{}, ds2{};
+  // DUGKS_F64_DW: the fused D2Q9 kernels in double-word arithmetic on the
+  // same FP64 arrays, with the parameters split into FP32 pairs
+  bool dwa = false;
+  D2Q9ParamsDW dwp{};
+  D2Q9StageDW dws1{}, dws2{};
   // deviation storage (store 1 = FP32, 2 = BF16): fhat, g, ftp, acc hold
   // typed deviations d = f - W rho0; fbx is the FP64 staging buffer
   int store = 0;
@@ -291,6 +297,18 @@ int one_step_d2q9(dugks_ctx* c) {
     TRY(launch(c, K_D2Q9_PROLOGUE, [&] { return launch_cell(c->p, 1, 1, c->fhat, c->g, c->mom, c->s1.a, c->s1.b, s); }));
     c->g1_valid = true;
   }
+  if (c->dwa) {
+    c->dwp.ty = c->dp.ty;                         // the tile height may have been retuned
+    TRY(launch(c, K_D2Q9DW_STAGE1, [&] {
+      return launch_d2q9dw_stage(c->dwp, c->dws1, 1, c->g, c->fhat, c->mom, c->ftp, c->acc,
+                                 c->mom + N, s);
+    }));
+    TRY(launch(c, K_D2Q9DW_STAGE2, [&] {
+      return launch_d2q9dw_stage(c->dwp, c->dws2, 2, c->ftp, c->acc, c->mom + N, c->fhat, c->g,
+                                 c->mom, s);
+    }));
+    return DUGKS_OK;
+  }
   TRY(launch(c, K_D2Q9_STAGE1, [&] {
     return launch_d2q9_stage(c->dp, c->ds1, 1, c->g, c->fhat, c->mom, c->ftp, c->acc, c->mom + N, s);
   }));
@@ -505,7 +523,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
   if (!out) return fail(DUGKS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!mesh || !vel || !bc) return fail(DUGKS_EINVAL, "NULL mesh, velocity set or bc");
-  if (storage < DUGKS_FP64 || storage > DUGKS_G_BF16) return fail(DUGKS_ENOTIMPL, "unknown storage form");
+  if (storage < DUGKS_FP64 || storage > DUGKS_F64_DW) return fail(DUGKS_ENOTIMPL, "unknown storage form");
   if (mesh->nx < 1 || mesh->ny < 1) return fail(DUGKS_EINVAL, "nx, ny must be >= 1");
   if ((long long)mesh->nx * mesh->ny > (1LL << 31) - 1)
     return fail(DUGKS_EINVAL, "too many cells");
@@ -519,6 +537,14 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
   for (int k = 0; k < nv; ++k)
     if (!std::isfinite(vel->xi_x[k]) || !std::isfinite(vel->xi_y[k]) || !std::isfinite(vel->w[k]))
       return fail(DUGKS_EINVAL, "non-finite velocity or weight");
+  // double-word arithmetic: FP64 arrays, taken by the fused D2Q9 kernels only
+  const bool dwa = storage == DUGKS_F64_DW;
+  if (dwa) {
+    const char* fg = std::getenv("DUGKS_FORCE_GENERIC");
+    if (!(d2q9_speed(vel) > 0.0) || (fg && fg[0] == '1'))
+      return fail(DUGKS_ENOTIMPL, "double-word arithmetic runs on the fused D2Q9 kernels only");
+    storage = DUGKS_FP64;
+  }
   for (int s = 0; s < 4; ++s) {
     if (bc[s].kind < 0 || bc[s].kind > 2) return fail(DUGKS_EINVAL, "unknown boundary kind");
     if (!std::isfinite(bc[s].uw_x) || !std::isfinite(bc[s].uw_y))
@@ -863,6 +889,12 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     }
     d2q9_stage_tables(c->ds1, cd, p.dx, p.dy, T, c->s1.h, dt / 3.0);
     d2q9_stage_tables(c->ds2, cd, p.dx, p.dy, T, c->s2.h, 4.0 * dt / 7.0);
+    if (dwa) {
+      c->dwa = true;
+      d2q9_params_to_dw(q, c->dwp);
+      d2q9_stage_to_dw(c->ds1, c->dws1);
+      d2q9_stage_to_dw(c->ds2, c->dws2);
+    }
     e = d2q9_prepare(q.ty);
     if (e == cudaSuccess && storage != DUGKS_FP64) {
       c->store = storage;
@@ -1002,7 +1034,7 @@ int dugks_profile_read(dugks_ctx* c, long long* launches, double* ms, int n) {
 int dugks_adjoint_step(dugks_ctx* c, const double* lam_in, double* lam_out, double* dJ_dtau,
                        double* dJ_duw, int on_device) {
   if (!c || !lam_in || !lam_out) return fail(DUGKS_EINVAL, "NULL argument");
-  if (c->store) return fail(DUGKS_ENOTIMPL, "the adjoint needs DUGKS_FP64 storage");
+  if (c->store || c->dwa) return fail(DUGKS_ENOTIMPL, "the adjoint needs DUGKS_FP64 storage");
   if (c->scheme != DUGKS_T3S3) return fail(DUGKS_ENOTIMPL, "the adjoint is that of the T3S3 step");
   TRY(ensure_adjoint(c));
   const size_t nvN = (size_t)c->p.nv * c->p.N;
@@ -1018,7 +1050,7 @@ int dugks_adjoint_run(dugks_ctx* c, const double* fhat0, int nsteps, int every,
                       int on_device) {
   if (!c || !fhat0 || !lam_final || !lam0) return fail(DUGKS_EINVAL, "NULL argument");
   if (nsteps < 0 || every < 1) return fail(DUGKS_EINVAL, "nsteps >= 0 and every >= 1 required");
-  if (c->store) return fail(DUGKS_ENOTIMPL, "the adjoint needs DUGKS_FP64 storage");
+  if (c->store || c->dwa) return fail(DUGKS_ENOTIMPL, "the adjoint needs DUGKS_FP64 storage");
   if (c->scheme != DUGKS_T3S3) return fail(DUGKS_ENOTIMPL, "the adjoint is that of the T3S3 step");
   TRY(ensure_adjoint(c));
   const size_t nvN = (size_t)c->p.nv * c->p.N;
@@ -1153,7 +1185,7 @@ int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
     dugks_ctx* c = ctxs[i];
     b->ctxs.push_back(c);
     c->batched += 1;
-    if (!(c->d2q9 && c->store == 0 && c->scheme == DUGKS_T3S3)) {
+    if (!(c->d2q9 && c->store == 0 && !c->dwa && c->scheme == DUGKS_T3S3)) {
       b->own.push_back(c);
       continue;
     }
@@ -1255,7 +1287,7 @@ int dugks_set_scheme(dugks_ctx* c, int scheme) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
   if (scheme < DUGKS_T3S3 || scheme > DUGKS_T2S2) return fail(DUGKS_EINVAL, "unknown scheme");
   if (c->batched) return fail(DUGKS_EINVAL, "the context belongs to a batch");
-  if (scheme != DUGKS_T3S3 && c->store)
+  if (scheme != DUGKS_T3S3 && (c->store || c->dwa))
     return fail(DUGKS_ENOTIMPL, "the T2 schemes run with DUGKS_FP64 storage");
   c->scheme = scheme;
   c->p.recon = scheme == DUGKS_T2S2 ? 1 : 0;

@@ -23,8 +23,14 @@
 // pattern of those weights is fixed at compile time per velocity.  The face
 // value is kept as f/alpha = f-bar + gamma feq (alpha is folded into the
 // flux scale), and equilibria use P = B +- e with B = base + e^2/2.
+//
+// The tile code is written once over its arithmetic type A: double (the
+// FP64 kernels) or dw, double-word FP32 pairs (dugks_dw.cuh), which keep FP64
+// arrays but run every operation on the FP32 pipes -- GB300 issues those at
+// 64 times its FP64 rate -- with a unit roundoff of 2^-48 instead of 2^-53.
 #include <type_traits>
 
+#include "dugks_dw.cuh"
 #include "dugks_fp.cuh"
 #include "dugks_internal.cuh"
 
@@ -44,37 +50,76 @@ template <int K> struct Vel {
   static constexpr int ey = K % 3 - 1;
 };
 
+// Arithmetic of the tile code.  Par / Stg: the parameter structs in that
+// arithmetic; load / store: FP64 memory <-> A; cst: an FP32-exact constant;
+// rcp: 1/x; diffuse: the diffuse wall density factor num c / ds_den.
+template <typename A> struct Arith;
+template <> struct Arith<double> {
+  using Par = D2Q9Params;
+  using Stg = D2Q9Stage;
+  using Acc = double;
+  static __device__ __forceinline__ double load(const double* p) { return __ldg(p); }
+  static __device__ __forceinline__ double store(double x) { return x; }
+  static __device__ __forceinline__ double cst(float x) { return (double)x; }
+  static __device__ __forceinline__ double coef(double x) { return x; }
+  static __device__ __forceinline__ double rcp(double x) { return rcp_fast(x); }
+  static __device__ __forceinline__ double diffuse(double num, const Par& P, int side) {
+    return num * P.c / P.ds_den[side];
+  }
+  static __device__ __forceinline__ void dot_first(double& a, double w, double v) { a = w * v; }
+  static __device__ __forceinline__ void dot_add(double& a, double w, double v) { a = fma(w, v, a); }
+  static __device__ __forceinline__ double dot_value(double a) { return a; }
+};
+template <> struct Arith<dw> {
+  using Par = D2Q9ParamsDW;
+  using Stg = D2Q9StageDW;
+  using Acc = dw_acc;
+  static __device__ __forceinline__ dw load(const double* p) { return dw_from_d(__ldg(p)); }
+  static __device__ __forceinline__ double store(dw x) { return dw_to_d(x); }
+  static __device__ __forceinline__ dw cst(float x) { return dw{x, 0.0f}; }
+  // ghost extrapolation coefficients (small integers, exact in FP32)
+  static __device__ __forceinline__ dw coef(double x) { return dw{d2f_bits(x), 0.0f}; }
+  static __device__ __forceinline__ dw rcp(dw x) { return dw_rcp(x); }
+  static __device__ __forceinline__ dw diffuse(dw num, const Par& P, int side) {
+    return num * P.c_ds[side];
+  }
+  static __device__ __forceinline__ void dot_first(dw_acc& a, dw w, dw v) { dw_acc_first(a, w, v); }
+  static __device__ __forceinline__ void dot_add(dw_acc& a, dw w, dw v) { dw_acc_add(a, w, v); }
+  static __device__ __forceinline__ dw dot_value(const dw_acc& a) { return dw_acc_value(a); }
+};
+
 // dot product of a weight block with the smem stencil, compile-time extents
-template <int R0, int R1, int Q0, int Q1, int NCOL>
-__device__ __forceinline__ double wdot(const double* __restrict__ s, const double* w) {
-  double acc = 0.0;
+template <typename A, int R0, int R1, int Q0, int Q1, int NCOL>
+__device__ __forceinline__ A wdot(const A* __restrict__ s, const A* w) {
+  typename Arith<A>::Acc acc;
 #pragma unroll
   for (int r = R0; r <= R1; ++r)
 #pragma unroll
     for (int q = Q0; q <= Q1; ++q) {
-      const double v = s[r * SW + q];
-      acc = (r == R0 && q == Q0) ? w[r * NCOL + q] * v : fma(w[r * NCOL + q], v, acc);
+      const A v = s[r * SW + q];
+      if (r == R0 && q == Q0) Arith<A>::dot_first(acc, w[r * NCOL + q], v);
+      else Arith<A>::dot_add(acc, w[r * NCOL + q], v);
     }
-  return acc;
+  return Arith<A>::dot_value(acc);
 }
 
 // interior x-face value of velocity K; s -> smem (row j-1, col fi-2)
-template <int K>
-__device__ __forceinline__ double xface_val(const double* __restrict__ s, const D2Q9Stage& S) {
+template <typename A, int K>
+__device__ __forceinline__ A xface_val(const A* __restrict__ s, const typename Arith<A>::Stg& S) {
   constexpr int ex = Vel<K>::ex, ey = Vel<K>::ey;
   constexpr int q0 = ex < 0 ? 1 : 0, q1 = ex > 0 ? 2 : 3;
   constexpr int r0 = ey == 0 ? 1 : 0, r1 = ey == 0 ? 1 : 2;
-  return wdot<r0, r1, q0, q1, 4>(s, &S.wx[K][0][0]);
+  return wdot<A, r0, r1, q0, q1, 4>(s, &S.wx[K][0][0]);
 }
 
 // interior y-face value of velocity K; s -> smem (row j-2, col i-1); the
 // weight block is [row q][col] so rows and columns swap roles
-template <int K>
-__device__ __forceinline__ double yface_val(const double* __restrict__ s, const D2Q9Stage& S) {
+template <typename A, int K>
+__device__ __forceinline__ A yface_val(const A* __restrict__ s, const typename Arith<A>::Stg& S) {
   constexpr int ex = Vel<K>::ex, ey = Vel<K>::ey;
   constexpr int q0 = ey < 0 ? 1 : 0, q1 = ey > 0 ? 2 : 3;
   constexpr int c0 = ex == 0 ? 1 : 0, c1 = ex == 0 ? 1 : 2;
-  return wdot<q0, q1, c0, c1, 3>(s, &S.wy[K][0][0]);
+  return wdot<A, q0, q1, c0, c1, 3>(s, &S.wy[K][0][0]);
 }
 
 // Equilibrium polynomials P_k = 1 + e + e^2/2 - |ut|^2 base_div for the nine
@@ -82,17 +127,19 @@ __device__ __forceinline__ double yface_val(const double* __restrict__ s, const 
 // the B of the four velocity pairs from uu = |ut|^2, xx = ut_x^2 and
 // p = ut_x ut_y:  B_x = base + xx/2, B_y = base + (uu - xx)/2,
 // B_(+-1,+-1) = base + uu/2 + p, B_(+-1,-+1) = base + uu/2 - p.
-__device__ __forceinline__ void d2q9_poly(double utx, double uty, const D2Q9Params& Q,
-                                          double (&P)[9]) {
-  const double xx = utx * utx;
-  const double uu = fma(uty, uty, xx);
-  const double base = fma(uu, -Q.base_div, 1.0);
-  const double bh = fma(uu, Q.half_mb, 1.0);            // base + uu/2
-  const double pxy = utx * uty;
-  const double bx = fma(0.5, xx, base);
-  const double by = fma(-0.5, xx, bh);
-  const double bs = bh + pxy, bd = bh - pxy;
-  const double sp = utx + uty, sm = utx - uty;
+template <typename A>
+__device__ __forceinline__ void d2q9_poly(A utx, A uty, const typename Arith<A>::Par& Q,
+                                          A (&P)[9]) {
+  using R = Arith<A>;
+  const A xx = utx * utx;
+  const A uu = fma(uty, uty, xx);
+  const A base = fma(uu, -Q.base_div, R::cst(1.0f));
+  const A bh = fma(uu, Q.half_mb, R::cst(1.0f));        // base + uu/2
+  const A pxy = utx * uty;
+  const A bx = fma(R::cst(0.5f), xx, base);
+  const A by = fma(R::cst(-0.5f), xx, bh);
+  const A bs = bh + pxy, bd = bh - pxy;
+  const A sp = utx + uty, sm = utx - uty;
   P[4] = base;
   P[7] = bx + utx;  P[1] = bx - utx;          // (+-1, 0)
   P[5] = by + uty;  P[3] = by - uty;          // (0, +-1)
@@ -103,19 +150,19 @@ __device__ __forceinline__ void d2q9_poly(double utx, double uty, const D2Q9Para
 // s W_k of velocity K.  WS: the weights depend only on |e_k|^2 (rest,
 // axis, diagonal), and ws = (s W_rest, s W_axis, s W_diagonal) precomputed;
 // otherwise one product per velocity.
-template <bool WS, int K>
-__device__ __forceinline__ double wk(const D2Q9Params& P, double s, const double (&ws)[3]) {
+template <bool WS, int K, typename A>
+__device__ __forceinline__ A wk(const typename Arith<A>::Par& P, A s, const A (&ws)[3]) {
   if constexpr (WS) return K == 4 ? ws[0] : ((K & 1) ? ws[1] : ws[2]);
   else return s * P.W[K];
 }
-template <bool WS>
-__device__ __forceinline__ void wclasses(const D2Q9Params& P, double s, double (&ws)[3]) {
+template <bool WS, typename A>
+__device__ __forceinline__ void wclasses(const typename Arith<A>::Par& P, A s, A (&ws)[3]) {
   if constexpr (WS) {
     ws[0] = s * P.W[4];
     ws[1] = s * P.W[1];
     ws[2] = s * P.W[0];
   } else {
-    ws[0] = ws[1] = ws[2] = 0.0;
+    ws[0] = ws[1] = ws[2] = Arith<A>::cst(0.0f);
   }
 }
 
@@ -129,33 +176,35 @@ __device__ __forceinline__ void for9(F&& f) {
 }
 
 // ut = c u / RT from the sums: (c^2/RT) (sx, sy) / rho
-__device__ __forceinline__ void d2q9_ut(double rho, double sx, double sy, const D2Q9Params& P,
-                                        double& utx, double& uty) {
-  const double rc = P.c3 * rcp_fast(rho);
+template <typename A>
+__device__ __forceinline__ void d2q9_ut(A rho, A sx, A sy, const typename Arith<A>::Par& P,
+                                        A& utx, A& uty) {
+  const A rc = P.c3 * Arith<A>::rcp(rho);
   utx = sx * rc;
   uty = sy * rc;
 }
 
 // rho, sx = sum_{ex=1} f - sum_{ex=-1} f, sy likewise
-__device__ __forceinline__ void d2q9_sums(const double (&f)[9], double& rho, double& sx, double& sy) {
-  const double a = f[0] + f[1] + f[2];     // ex = -1
-  const double b = f[6] + f[7] + f[8];     // ex = +1
+template <typename A>
+__device__ __forceinline__ void d2q9_sums(const A (&f)[9], A& rho, A& sx, A& sy) {
+  const A a = f[0] + f[1] + f[2];          // ex = -1
+  const A b = f[6] + f[7] + f[8];          // ex = +1
   rho = (a + b) + (f[3] + f[4] + f[5]);
   sx = b - a;
   sy = (f[2] + f[5] + f[8]) - (f[0] + f[3] + f[6]);
 }
 
 // f/alpha = f-bar + gamma feq(moments of f-bar) for one face, in place
-template <bool WS>
-__device__ __forceinline__ void face_recover(double (&fb)[9], const D2Q9Stage& S,
-                                             const D2Q9Params& P) {
-  double rho, sx, sy;
+template <bool WS, typename A>
+__device__ __forceinline__ void face_recover(A (&fb)[9], const typename Arith<A>::Stg& S,
+                                             const typename Arith<A>::Par& P) {
+  A rho, sx, sy;
   d2q9_sums(fb, rho, sx, sy);
-  double utx, uty;
+  A utx, uty;
   d2q9_ut(rho, sx, sy, P, utx, uty);
-  double Pk[9], ws[3];
+  A Pk[9], ws[3];
   d2q9_poly(utx, uty, P, Pk);
-  const double gr = S.gamma * rho;
+  const A gr = S.gamma * rho;
   wclasses<WS>(P, gr, ws);
   for9([&](auto kc) {
     constexpr int k = decltype(kc)::value;
@@ -180,22 +229,76 @@ __device__ __forceinline__ int resolve1(int x, int n, bool per, int (&i)[3], dou
   return 0;   // beyond the ghost band: never read by a computed face
 }
 
+// Cell part of a stage in double-word arithmetic.  The maps are written so
+// that a uniform equilibrium passes every one of them exactly whatever the
+// rounding of the coefficients: g = f + b (feq - f) instead of a f + b feq
+// (a + b = 1 holds in FP64 to 2^-53 but only to 2^-49 for coefficients
+// split into FP32 pairs, a bias that would accumulate step after step), and
+// X = f^/4 + 3 g1/4 + r37 (dt/3 L*) + c_om34 (f~' - feq') with the 3dt/7 L*
+// term taken from the flux itself (eq. fhp; 3dt/7 = r37 dt/3).
+template <int STAGE, bool WS>
+__device__ __forceinline__ void d2q9_cell_dw(const D2Q9ParamsDW& P, const dw (&L)[9],
+                                             const dw* __restrict__ sg,
+                                             const double* __restrict__ own,
+                                             double* __restrict__ out0, double* __restrict__ out1,
+                                             double* __restrict__ rho_out, int cell, int N,
+                                             int SH, int r, int c) {
+  using R = Arith<dw>;
+  dw f[9], X[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const dw fh = R::load(own + (size_t)k * N + cell);
+    if (STAGE == 1) {
+      // L[k] = dt/3 L*: f~' = 5/4 g1 - 1/4 f^ + dt/3 L*
+      const dw g1 = sg[(k * SH + r + HALO) * SW + c + HALO];
+      f[k] = fma(R::cst(1.25f), g1, fma(R::cst(-0.25f), fh, L[k]));
+      X[k] = fma(P.r37, L[k], fma(R::cst(0.25f), fh, R::cst(0.75f) * g1));
+    } else {
+      // L[k] = 4dt/7 L**: f^^{n+1} = X + 4dt/7 L**
+      f[k] = fh + L[k];
+    }
+  }
+  dw rho, sx, sy;
+  d2q9_sums(f, rho, sx, sy);
+  dw utx, uty;
+  d2q9_ut(rho, sx, sy, P, utx, uty);
+  dw Pk[9], rw[3];
+  d2q9_poly(utx, uty, P, Pk);
+  wclasses<WS>(P, rho, rw);
+  const dw b = STAGE == 1 ? P.b2 : P.b1;
+  for9([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    const dw d = wk<WS, k>(P, rho, rw) * Pk[k] - f[k];      // feq - f
+    const dw g = fma(b, d, f[k]);                           // g2 (stage 1) or g1
+    if (STAGE == 1) {
+      out0[(size_t)k * N + cell] = R::store(g);
+      out1[(size_t)k * N + cell] = R::store(fma(-P.c_om34, d, X[k]));
+    } else {
+      out0[(size_t)k * N + cell] = R::store(f[k]);
+      out1[(size_t)k * N + cell] = R::store(g);
+    }
+  });
+  rho_out[cell] = R::store(rho);
+}
+
 // ---------------------------------------------------------------- kernel
 // One 32 x P.ty tile of one stage (all phases); every thread of the block
 // takes part (blockDim.x >= 32 (P.ty + 1)).
-template <int STAGE, bool WS>
-__device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& S,
+template <int STAGE, bool WS, typename A>
+__device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
+                                          const typename Arith<A>::Stg& S,
                                           const double* __restrict__ gin,
                                           const double* __restrict__ own,
                                           const double* __restrict__ rho_in,
                                           double* __restrict__ out0, double* __restrict__ out1,
                                           double* __restrict__ rho_out, int x0, int y0,
-                                          double* __restrict__ smem) {
+                                          A* __restrict__ smem) {
+  using R = Arith<A>;
   const int TY = P.ty;
   const int SH = TY + 2 * HALO;
-  double* sg = smem;                               // [9][SH][SW]
-  double* sfx = sg + 9 * SH * SW;                  // [9][TY][TX+1]
-  double* sfy = sfx + 9 * TY * (TX + 1);           // [9][TY+1][TX]
+  A* sg = smem;                                    // [9][SH][SW]
+  A* sfx = sg + 9 * SH * SW;                       // [9][TY][TX+1]
+  A* sfy = sfx + 9 * TY * (TX + 1);                // [9][TY+1][TX]
   const int nx = P.nx, ny = P.ny, N = P.N;
   const int tid = threadIdx.x, nthr = blockDim.x;
 
@@ -209,14 +312,14 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
     if (nxr == 1 && nyr == 1) {
       const double* src = gin + iy[0] * nx + ix[0];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) sg[(k * SH + rr) * SW + cc] = __ldg(src + (size_t)k * N);
+      for (int k = 0; k < 9; ++k) sg[(k * SH + rr) * SW + cc] = R::load(src + (size_t)k * N);
     } else {
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        double v = 0.0;
+        A v = R::cst(0.0f);
         for (int a = 0; a < nyr; ++a)
           for (int b = 0; b < nxr; ++b)
-            v = fma(cy[a] * cx[b], __ldg(gin + (size_t)k * N + iy[a] * nx + ix[b]), v);
+            v = fma(R::coef(cy[a] * cx[b]), R::load(gin + (size_t)k * N + iy[a] * nx + ix[b]), v);
         sg[(k * SH + rr) * SW + cc] = v;
       }
     }
@@ -228,32 +331,32 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
     const int r = t / (TX + 1), fc = t - r * (TX + 1);
     const int j = y0 + r, fi = x0 + fc;
     if (j >= ny || fi > nx) continue;
-    double fb[9];
-    const double* s0 = sg + (r + 1) * SW + fc;   // row j-1, col fi-2
+    A fb[9];
+    const A* s0 = sg + (r + 1) * SW + fc;   // row j-1, col fi-2
     const int stride = SH * SW;
-    fb[0] = xface_val<0>(s0 + 0 * stride, S);
-    fb[1] = xface_val<1>(s0 + 1 * stride, S);
-    fb[2] = xface_val<2>(s0 + 2 * stride, S);
-    fb[3] = xface_val<3>(s0 + 3 * stride, S);
-    fb[4] = xface_val<4>(s0 + 4 * stride, S);
-    fb[5] = xface_val<5>(s0 + 5 * stride, S);
-    fb[6] = xface_val<6>(s0 + 6 * stride, S);
-    fb[7] = xface_val<7>(s0 + 7 * stride, S);
-    fb[8] = xface_val<8>(s0 + 8 * stride, S);
+    fb[0] = xface_val<A, 0>(s0 + 0 * stride, S);
+    fb[1] = xface_val<A, 1>(s0 + 1 * stride, S);
+    fb[2] = xface_val<A, 2>(s0 + 2 * stride, S);
+    fb[3] = xface_val<A, 3>(s0 + 3 * stride, S);
+    fb[4] = xface_val<A, 4>(s0 + 4 * stride, S);
+    fb[5] = xface_val<A, 5>(s0 + 5 * stride, S);
+    fb[6] = xface_val<A, 6>(s0 + 6 * stride, S);
+    fb[7] = xface_val<A, 7>(s0 + 7 * stride, S);
+    fb[8] = xface_val<A, 8>(s0 + 8 * stride, S);
     if (!P.px && (fi == 0 || fi == nx)) {
       const bool hi = fi == 0;                    // fluid cell on the +x side (west wall)
       const int side = hi ? SIDE_W : SIDE_E;
-      const double rw = rho_in[j * nx + (hi ? 0 : nx - 1)];
+      const A rw = R::load(rho_in + j * nx + (hi ? 0 : nx - 1));
       // per-velocity tangential rows need the velocity-k slice
-      double fw[9];
+      A fw[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) fw[k] = fb[k];
       // tangential (ex = 0) velocities are k = 3, 4, 5: recompute one-sided
 #pragma unroll
       for (int k = 3; k <= 5; ++k) {
-        const double(&w)[3][3] = hi ? S.wxR[k] : S.wxL[k];
-        const double* sk = s0 + k * stride + (hi ? 1 : 0);
-        double v = 0.0;
+        const A(&w)[3][3] = hi ? S.wxR[k] : S.wxL[k];
+        const A* sk = s0 + k * stride + (hi ? 1 : 0);
+        A v = R::cst(0.0f);
 #pragma unroll
         for (int rr2 = 0; rr2 < 3; ++rr2)
 #pragma unroll
@@ -266,11 +369,11 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
         for (int k = 0; k < 9; ++k)
           if (nsg * (k / 3 - 1) < 0) fw[k] = fma(rw, P.bb[side][k], fw[8 - k]);
       } else {
-        double num = 0.0;
+        A num = R::cst(0.0f);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-          if (nsg * (k / 3 - 1) > 0) num += fw[k];
-        const double rd = num * P.c / P.ds_den[side];
+          if (nsg * (k / 3 - 1) > 0) num = num + fw[k];
+        const A rd = R::diffuse(num, P, side);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
           if (nsg * (k / 3 - 1) < 0) fw[k] = rd * P.feq_wall[side][k];
@@ -288,31 +391,31 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
     const int fr = t / TX, c = t - fr * TX;
     const int fj = y0 + fr, i = x0 + c;
     if (i >= nx || fj > ny) continue;
-    double fb[9];
-    const double* s0 = sg + fr * SW + (c + 1);   // row fj-2, col i-1
+    A fb[9];
+    const A* s0 = sg + fr * SW + (c + 1);   // row fj-2, col i-1
     const int stride = SH * SW;
-    fb[0] = yface_val<0>(s0 + 0 * stride, S);
-    fb[1] = yface_val<1>(s0 + 1 * stride, S);
-    fb[2] = yface_val<2>(s0 + 2 * stride, S);
-    fb[3] = yface_val<3>(s0 + 3 * stride, S);
-    fb[4] = yface_val<4>(s0 + 4 * stride, S);
-    fb[5] = yface_val<5>(s0 + 5 * stride, S);
-    fb[6] = yface_val<6>(s0 + 6 * stride, S);
-    fb[7] = yface_val<7>(s0 + 7 * stride, S);
-    fb[8] = yface_val<8>(s0 + 8 * stride, S);
+    fb[0] = yface_val<A, 0>(s0 + 0 * stride, S);
+    fb[1] = yface_val<A, 1>(s0 + 1 * stride, S);
+    fb[2] = yface_val<A, 2>(s0 + 2 * stride, S);
+    fb[3] = yface_val<A, 3>(s0 + 3 * stride, S);
+    fb[4] = yface_val<A, 4>(s0 + 4 * stride, S);
+    fb[5] = yface_val<A, 5>(s0 + 5 * stride, S);
+    fb[6] = yface_val<A, 6>(s0 + 6 * stride, S);
+    fb[7] = yface_val<A, 7>(s0 + 7 * stride, S);
+    fb[8] = yface_val<A, 8>(s0 + 8 * stride, S);
     if (!P.py && (fj == 0 || fj == ny)) {
       const bool hi = fj == 0;                    // fluid cell above (south wall)
       const int side = hi ? SIDE_S : SIDE_N;
-      const double rw = rho_in[(hi ? 0 : ny - 1) * nx + i];
-      double fw[9];
+      const A rw = R::load(rho_in + (hi ? 0 : ny - 1) * nx + i);
+      A fw[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) fw[k] = fb[k];
       // tangential (ey = 0) velocities are k = 1, 4, 7
 #pragma unroll
       for (int k = 1; k <= 7; k += 3) {
-        const double(&w)[3][3] = hi ? S.wyT[k] : S.wyB[k];
-        const double* sk = s0 + k * stride + (hi ? SW : 0);
-        double v = 0.0;
+        const A(&w)[3][3] = hi ? S.wyT[k] : S.wyB[k];
+        const A* sk = s0 + k * stride + (hi ? SW : 0);
+        A v = R::cst(0.0f);
 #pragma unroll
         for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -325,11 +428,11 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
         for (int k = 0; k < 9; ++k)
           if (nsg * (k % 3 - 1) < 0) fw[k] = fma(rw, P.bb[side][k], fw[8 - k]);
       } else {
-        double num = 0.0;
+        A num = R::cst(0.0f);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-          if (nsg * (k % 3 - 1) > 0) num += fw[k];
-        const double rd = num * P.c / P.ds_den[side];
+          if (nsg * (k % 3 - 1) > 0) num = num + fw[k];
+        const A rd = R::diffuse(num, P, side);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
           if (nsg * (k % 3 - 1) < 0) fw[k] = rd * P.feq_wall[side][k];
@@ -349,84 +452,87 @@ __device__ __forceinline__ void d2q9_tile(const D2Q9Params& P, const D2Q9Stage& 
     const int j = y0 + r, i = x0 + c;
     if (j >= ny || i >= nx) continue;
     const int cell = j * nx + i;
-    double L[9];
+    A L[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const int ex = k / 3 - 1, ey = k % 3 - 1;
-      double v = 0.0;
+      A v = R::cst(0.0f);
       if (ex != 0)
         v = S.kx[k] * (sfx[(k * TY + r) * (TX + 1) + c + 1] - sfx[(k * TY + r) * (TX + 1) + c]);
       if (ey != 0) {
-        const double d = sfy[(k * (TY + 1) + r + 1) * TX + c] - sfy[(k * (TY + 1) + r) * TX + c];
+        const A d = sfy[(k * (TY + 1) + r + 1) * TX + c] - sfy[(k * (TY + 1) + r) * TX + c];
         v = (ex != 0) ? fma(S.ky[k], d, v) : S.ky[k] * d;
       }
       L[k] = v;
     }
-    if (STAGE == 1) {
+    if constexpr (std::is_same<A, dw>::value) {
+      d2q9_cell_dw<STAGE, WS>(P, L, sg, own, out0, out1, rho_out, cell, N, SH, r, c);
+    } else if (STAGE == 1) {
       // L[k] = dt/3 L*.  f~' = 5/4 g1 - 1/4 f^ + dt/3 L*;  X0 = 1/4 f^ + 3/4 g1 + 3dt/7 L*
       // X0 = f^+ + 3dt/7 L* with L* written through f~' (dt/3 L* = f~' -
       // 5/4 g1 + 1/4 f^):  X0 = r37 f~' + Xg,  Xg = (3/4 - 5/4 r37) g1 +
       // (1/4 + 1/4 r37) f^;  the r37 f~' part joins the c_om34 f~' term below
-      const double cg = 0.75 - 1.25 * P.r37, cf = 0.25 + 0.25 * P.r37;
-      const double cft = P.c_om34 + P.r37;
-      double ft[9], X[9];
+      const A cg = R::cst(0.75f) - R::cst(1.25f) * P.r37, cf = R::cst(0.25f) + R::cst(0.25f) * P.r37;
+      const A cft = P.c_om34 + P.r37;
+      A ft[9], X[9];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        const double g1 = sg[(k * SH + r + HALO) * SW + c + HALO];
-        const double fh = __ldg(own + (size_t)k * N + cell);
-        ft[k] = fma(1.25, g1, fma(-0.25, fh, L[k]));
+        const A g1 = sg[(k * SH + r + HALO) * SW + c + HALO];
+        const A fh = R::load(own + (size_t)k * N + cell);
+        ft[k] = fma(R::cst(1.25f), g1, fma(R::cst(-0.25f), fh, L[k]));
         X[k] = fma(cf, fh, cg * g1);
       }
-      double rho, sx, sy;
+      A rho, sx, sy;
       d2q9_sums(ft, rho, sx, sy);
-      double utx, uty;
+      A utx, uty;
       d2q9_ut(rho, sx, sy, P, utx, uty);
-      double Pk[9], rcw[3], rbw[3];
+      A Pk[9], rcw[3], rbw[3];
       d2q9_poly(utx, uty, P, Pk);
       // X += 3/4 dt Omega' = c_om34 (f~' - feq');  g2 = a2 f~' + b2 feq'
-      const double rc = -P.c_om34 * rho, rb = P.b2 * rho;
+      const A rc = -P.c_om34 * rho, rb = P.b2 * rho;
       wclasses<WS>(P, rc, rcw);
       wclasses<WS>(P, rb, rbw);
       for9([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        const double xk = fma(cft, ft[k], fma(wk<WS, k>(P, rc, rcw), Pk[k], X[k]));
-        const double g2 = fma(wk<WS, k>(P, rb, rbw), Pk[k], P.a2 * ft[k]);
-        out0[(size_t)k * N + cell] = g2;
-        out1[(size_t)k * N + cell] = xk;
+        const A xk = fma(cft, ft[k], fma(wk<WS, k>(P, rc, rcw), Pk[k], X[k]));
+        const A g2 = fma(wk<WS, k>(P, rb, rbw), Pk[k], P.a2 * ft[k]);
+        out0[(size_t)k * N + cell] = R::store(g2);
+        out1[(size_t)k * N + cell] = R::store(xk);
       });
-      rho_out[cell] = rho;
+      rho_out[cell] = R::store(rho);
     } else {
       // L[k] = 4dt/7 L**.  f^^{n+1} = X + 4dt/7 L**; then g1 of the next step
-      double fh[9];
+      A fh[9];
 #pragma unroll
-      for (int k = 0; k < 9; ++k) fh[k] = __ldg(own + (size_t)k * N + cell) + L[k];
-      double rho, sx, sy;
+      for (int k = 0; k < 9; ++k) fh[k] = R::load(own + (size_t)k * N + cell) + L[k];
+      A rho, sx, sy;
       d2q9_sums(fh, rho, sx, sy);
-      double utx, uty;
+      A utx, uty;
       d2q9_ut(rho, sx, sy, P, utx, uty);
-      double Pk[9], rbw[3];
+      A Pk[9], rbw[3];
       d2q9_poly(utx, uty, P, Pk);
-      const double rb = P.b1 * rho;
+      const A rb = P.b1 * rho;
       wclasses<WS>(P, rb, rbw);
       for9([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        const double g1 = fma(wk<WS, k>(P, rb, rbw), Pk[k], P.a1 * fh[k]);
-        out0[(size_t)k * N + cell] = fh[k];
-        out1[(size_t)k * N + cell] = g1;
+        const A g1 = fma(wk<WS, k>(P, rb, rbw), Pk[k], P.a1 * fh[k]);
+        out0[(size_t)k * N + cell] = R::store(fh[k]);
+        out1[(size_t)k * N + cell] = R::store(g1);
       });
-      rho_out[cell] = rho;
+      rho_out[cell] = R::store(rho);
     }
   }
 }
 
-template <int STAGE, bool WS>
+template <int STAGE, bool WS, typename A>
 __global__ void __launch_bounds__(kMaxThreads)
-k_d2q9(D2Q9Params P, D2Q9Stage S, const double* __restrict__ gin,
+k_d2q9(typename Arith<A>::Par P, typename Arith<A>::Stg S, const double* __restrict__ gin,
        const double* __restrict__ own, const double* __restrict__ rho_in,
        double* __restrict__ out0, double* __restrict__ out1, double* __restrict__ rho_out) {
   extern __shared__ double smem[];
-  d2q9_tile<STAGE, WS>(P, S, gin, own, rho_in, out0, out1, rho_out, blockIdx.x * TX,
-                       blockIdx.y * P.ty, smem);
+  static_assert(sizeof(A) == sizeof(double), "tile buffers are sized for 8-byte values");
+  d2q9_tile<STAGE, WS, A>(P, S, gin, own, rho_in, out0, out1, rho_out, blockIdx.x * TX,
+                          blockIdx.y * P.ty, reinterpret_cast<A*>(smem));
 }
 
 // Persistent batched stage kernel: blocks take (instance, tile) work items
@@ -459,11 +565,11 @@ k_d2q9_batch(const D2Q9BatchItem* __restrict__ items, const int* __restrict__ ti
     const int local = t - tile_start[it];
     const int bx = local % I.tiles_x, by = local / I.tiles_x;
     if constexpr (STAGE == 1)
-      d2q9_tile<1, false>(I.P, I.S1, I.g1, I.fhat, I.mom, I.g2, I.X, I.mom + I.P.N, bx * TX,
-                          by * I.P.ty, smem);
+      d2q9_tile<1, false, double>(I.P, I.S1, I.g1, I.fhat, I.mom, I.g2, I.X, I.mom + I.P.N,
+                                  bx * TX, by * I.P.ty, smem);
     else
-      d2q9_tile<2, false>(I.P, I.S2, I.g2, I.X, I.mom + I.P.N, I.fhat, I.g1, I.mom, bx * TX,
-                          by * I.P.ty, smem);
+      d2q9_tile<2, false, double>(I.P, I.S2, I.g2, I.X, I.mom + I.P.N, I.fhat, I.g1, I.mom,
+                                  bx * TX, by * I.P.ty, smem);
     __syncthreads();
   }
 }
@@ -474,18 +580,25 @@ size_t d2q9_smem_bytes(int ty) {
   return sizeof(double) * (9 * (ty + 2 * HALO) * SW + 9 * ty * (TX + 1) + 9 * (ty + 1) * TX);
 }
 
+template <typename A>
+cudaError_t allow_smem(int bytes) {
+  cudaError_t e = cudaFuncSetAttribute(k_d2q9<1, true, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_d2q9<2, true, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_d2q9<1, false, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_d2q9<2, false, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
 cudaError_t d2q9_prepare(int ty) {
   // the attribute is per function: always allow the largest tile so that
   // contexts with different tile heights can coexist
   (void)ty;
   const int bytes = (int)d2q9_smem_bytes(kMaxTY);
-  cudaError_t e = cudaFuncSetAttribute(k_d2q9<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_d2q9<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_d2q9<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_d2q9<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = allow_smem<double>(bytes);
+  if (e == cudaSuccess) e = allow_smem<dw>(bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_d2q9_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -509,25 +622,97 @@ int d2q9_batch_blocks_per_sm(int max_ty) {
   return n < 1 ? 1 : n;
 }
 
-cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage,
-                              const double* gin, const double* own, const double* rho_in,
-                              double* out0, double* out1, double* rho_out, cudaStream_t st) {
+namespace {
+template <typename A>
+cudaError_t launch_stage(const typename Arith<A>::Par& p, const typename Arith<A>::Stg& s,
+                         int stage, const double* gin, const double* own, const double* rho_in,
+                         double* out0, double* out1, double* rho_out, cudaStream_t st) {
   if (p.ty < 1 || p.ty > kMaxTY) return cudaErrorInvalidValue;
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + p.ty - 1) / p.ty);
   const int threads = TX * (p.ty + 1);
   const size_t bytes = d2q9_smem_bytes(p.ty);
   if (p.wsym) {
     if (stage == 1)
-      k_d2q9<1, true><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
+      k_d2q9<1, true, A><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
     else
-      k_d2q9<2, true><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
+      k_d2q9<2, true, A><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
   } else {
     if (stage == 1)
-      k_d2q9<1, false><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
+      k_d2q9<1, false, A><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
     else
-      k_d2q9<2, false><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
+      k_d2q9<2, false, A><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
   }
   return cudaGetLastError();
+}
+
+// x = h + l with h = x rounded to FP32 and l the FP32 rounding of x - h
+dw split(double x) {
+  const float h = (float)x;
+  return dw{h, (float)(x - (double)h)};
+}
+template <size_t N>
+void split_all(const double (&x)[N], dw (&d)[N]) {
+  for (size_t i = 0; i < N; ++i) d[i] = split(x[i]);
+}
+template <size_t N, size_t M>
+void split_all(const double (&x)[N][M], dw (&d)[N][M]) {
+  for (size_t i = 0; i < N; ++i) split_all(x[i], d[i]);
+}
+template <size_t N, size_t M, size_t L>
+void split_all(const double (&x)[N][M][L], dw (&d)[N][M][L]) {
+  for (size_t i = 0; i < N; ++i) split_all(x[i], d[i]);
+}
+}  // namespace
+
+cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage,
+                              const double* gin, const double* own, const double* rho_in,
+                              double* out0, double* out1, double* rho_out, cudaStream_t st) {
+  return launch_stage<double>(p, s, stage, gin, own, rho_in, out0, out1, rho_out, st);
+}
+
+cudaError_t launch_d2q9dw_stage(const D2Q9ParamsDW& p, const D2Q9StageDW& s, int stage,
+                                const double* gin, const double* own, const double* rho_in,
+                                double* out0, double* out1, double* rho_out, cudaStream_t st) {
+  return launch_stage<dw>(p, s, stage, gin, own, rho_in, out0, out1, rho_out, st);
+}
+
+void d2q9_params_to_dw(const D2Q9Params& p, D2Q9ParamsDW& d) {
+  d.nx = p.nx;
+  d.ny = p.ny;
+  d.N = p.N;
+  d.px = p.px;
+  d.py = p.py;
+  d.ty = p.ty;
+  split_all(p.W, d.W);
+  d.c3 = split(p.c3);
+  d.base_div = split(p.base_div);
+  d.half_mb = split(p.half_mb);
+  d.wsym = p.wsym;
+  d.c = split(p.c);
+  d.a1 = split(p.a1);
+  d.b1 = split(p.b1);
+  d.a2 = split(p.a2);
+  d.b2 = split(p.b2);
+  d.c_om34 = split(p.c_om34);
+  d.r37 = split(p.r37);
+  for (int s4 = 0; s4 < 4; ++s4) {
+    d.bc_kind[s4] = p.bc_kind[s4];
+    d.c_ds[s4] = split(p.ds_den[s4] > 0.0 ? p.c / p.ds_den[s4] : 0.0);
+  }
+  split_all(p.feq_wall, d.feq_wall);
+  split_all(p.bb, d.bb);
+}
+
+void d2q9_stage_to_dw(const D2Q9Stage& s, D2Q9StageDW& d) {
+  split_all(s.wx, d.wx);
+  split_all(s.wy, d.wy);
+  split_all(s.wxL, d.wxL);
+  split_all(s.wxR, d.wxR);
+  split_all(s.wyB, d.wyB);
+  split_all(s.wyT, d.wyT);
+  d.gamma = split(s.gamma);
+  split_all(s.kx, d.kx);
+  split_all(s.ky, d.ky);
 }
 
 }  // namespace dugks

@@ -41,6 +41,8 @@ enum KernelId {
   K_T2_FACE_X,
   K_T2_FACE_Y,
   K_T2_UPDATE,         // f~^{n+1} = f~^{+,n} + dt L
+  K_D2Q9DW_STAGE1,     // fused D2Q9 path in double-word arithmetic, stage 1
+  K_D2Q9DW_STAGE2,     // stage 2
   K_NUM
 };
 
@@ -191,6 +193,38 @@ cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage
                               double* out0, double* out1, double* rho_out, cudaStream_t st);
 size_t d2q9_smem_bytes(int ty);
 cudaError_t d2q9_prepare(int ty);
+
+// Double-word arithmetic form of the fused D2Q9 kernels: FP64 arrays, every
+// operation in double-word (FP32 pair) arithmetic (dugks_dw.cuh).  The
+// parameters are the FP64 ones split on the host into h + l pairs.
+struct dw {
+  float h, l;                   // value h + l, |l| <= ulp(h) / 2
+};
+struct D2Q9ParamsDW {
+  int nx, ny, N, px, py, ty;
+  dw W[9];
+  dw c3, base_div, half_mb;
+  int wsym;
+  dw c;
+  dw a1, b1, a2, b2;
+  dw c_om34, r37;
+  int bc_kind[4];
+  dw c_ds[4];                   // c / ds_den: the diffuse wall density factor
+  dw feq_wall[4][9];
+  dw bb[4][9];
+};
+struct D2Q9StageDW {
+  dw wx[9][3][4];
+  dw wy[9][4][3];
+  dw wxL[9][3][3], wxR[9][3][3], wyB[9][3][3], wyT[9][3][3];
+  dw gamma;
+  dw kx[9], ky[9];
+};
+void d2q9_params_to_dw(const D2Q9Params& p, D2Q9ParamsDW& d);
+void d2q9_stage_to_dw(const D2Q9Stage& s, D2Q9StageDW& d);
+cudaError_t launch_d2q9dw_stage(const D2Q9ParamsDW& p, const D2Q9StageDW& s, int stage,
+                                const double* gin, const double* own, const double* rho_in,
+                                double* out0, double* out1, double* rho_out, cudaStream_t st);
 
 // Adjoint kernels (dugks_adjoint.cu); grads = [tau, uw_x(W), uw_y(W), uw_x(E), ...].
 cudaError_t launch_flux_T(const DevParams& p, int dir, const double* A, double sa,

@@ -65,10 +65,20 @@ def test_bounceback_needs_opposite_velocities(lib):
     assert "bounce-back" in str(e.value)
 
 
-def test_storage_other_than_fp64_not_provided(lib):
+def test_unknown_storage_form_not_provided(lib):
     with pytest.raises(P.DugksError) as e:
-        _init(storage=3)
+        _init(storage=4)
     assert e.value.code == P.DUGKS_ENOTIMPL
+
+
+def test_double_word_form_needs_the_d2q9_set(lib):
+    """DUGKS_F64_DW runs on the fused D2Q9 kernels only; a Newton-Cotes set
+    is refused before any device work."""
+    xi, W, RT = PV.newton_cotes(4, 0.5)
+    with pytest.raises(P.DugksError) as e:
+        _init(xi=xi, W=W, RT=RT, storage=P.F64_DW)
+    assert e.value.code == P.DUGKS_ENOTIMPL
+    assert "D2Q9" in str(e.value)
 
 
 def test_product_velocity_sets_match_oracle():
