@@ -273,12 +273,13 @@ double d2q9_speed(const dugks_velset* v) {
   return c;
 }
 
-// Tile height: the number of 32 x ty tiles per SM wave times the work per
-// tile (ty + 1 face rows) is minimised over ty in [4, 16].
-int d2q9_tile_height(int nx, int ny, int sms) {
+// Tile height: the number of 32 x ty tiles per wave of resident blocks
+// times the work per tile (ty + 1 face rows) is minimised over ty in
+// [4, maxty].
+int d2q9_tile_height(int nx, int ny, int sms, int maxty) {
   int best = 8;
   double bestc = 1e300;
-  for (int ty = 4; ty <= 16; ++ty) {
+  for (int ty = 4; ty <= maxty; ++ty) {
     const long tiles = (long)((nx + 31) / 32) * ((ny + ty - 1) / ty);
     const long waves = (tiles + sms - 1) / sms;
     const double cost = (double)waves * (ty + 1);
@@ -863,7 +864,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     q.N = p.N;
     q.px = p.px;
     q.py = p.py;
-    q.ty = d2q9_tile_height(p.nx, p.ny, sms);
+    q.ty = d2q9_tile_height(p.nx, p.ny, sms * d2q9_blocks_per_sm(dwa), d2q9_max_ty(dwa));
     for (int k = 0; k < 9; ++k) q.W[k] = vel->w[k];
     q.c3 = cd * cd / vel->RT;
     q.base_div = 0.5 / q.c3;
@@ -1135,7 +1136,7 @@ int dugks_autotune(dugks_ctx* c, int trials, int* ty_out) {
   CK(cudaEventCreate(&b));
   int best = c->dp.ty;
   float best_ms = 1e30f;
-  for (int ty = 4; ty <= 16; ++ty) {
+  for (int ty = 4; ty <= d2q9_max_ty(c->dwa); ++ty) {
     c->dp.ty = ty;
     c->g1_valid = false;
     int rc = advance(c);                                  // warm-up incl. the prologue

@@ -55,6 +55,8 @@ template <int K> struct Vel {
 // rcp: 1/x; diffuse: the diffuse wall density factor num c / ds_den.
 template <typename A> struct Arith;
 template <> struct Arith<double> {
+  // tiles up to 32 x 16, one block per SM (no minimum given to the compiler)
+  static constexpr int kMaxTY = 16, kThreads = TX * (kMaxTY + 1), kMinBlocks = 0;
   using Par = D2Q9Params;
   using Stg = D2Q9Stage;
   using Acc = double;
@@ -71,6 +73,10 @@ template <> struct Arith<double> {
   static __device__ __forceinline__ double dot_value(double a) { return a; }
 };
 template <> struct Arith<dw> {
+  // tiles up to 32 x 12 so that two blocks share an SM (2 x 100 KB of
+  // shared memory, <= 72 registers per thread): one block's phase barriers
+  // and instruction fetches overlap the other's arithmetic
+  static constexpr int kMaxTY = 12, kThreads = TX * (kMaxTY + 1), kMinBlocks = 2;
   using Par = D2Q9ParamsDW;
   using Stg = D2Q9StageDW;
   using Acc = dw_acc;
@@ -525,7 +531,7 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
 }
 
 template <int STAGE, bool WS, typename A>
-__global__ void __launch_bounds__(kMaxThreads)
+__global__ void __launch_bounds__(Arith<A>::kThreads, Arith<A>::kMinBlocks)
 k_d2q9(typename Arith<A>::Par P, typename Arith<A>::Stg S, const double* __restrict__ gin,
        const double* __restrict__ own, const double* __restrict__ rho_in,
        double* __restrict__ out0, double* __restrict__ out1, double* __restrict__ rho_out) {
@@ -598,7 +604,7 @@ cudaError_t d2q9_prepare(int ty) {
   (void)ty;
   const int bytes = (int)d2q9_smem_bytes(kMaxTY);
   cudaError_t e = allow_smem<double>(bytes);
-  if (e == cudaSuccess) e = allow_smem<dw>(bytes);
+  if (e == cudaSuccess) e = allow_smem<dw>((int)d2q9_smem_bytes(Arith<dw>::kMaxTY));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_d2q9_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -627,7 +633,7 @@ template <typename A>
 cudaError_t launch_stage(const typename Arith<A>::Par& p, const typename Arith<A>::Stg& s,
                          int stage, const double* gin, const double* own, const double* rho_in,
                          double* out0, double* out1, double* rho_out, cudaStream_t st) {
-  if (p.ty < 1 || p.ty > kMaxTY) return cudaErrorInvalidValue;
+  if (p.ty < 1 || p.ty > Arith<A>::kMaxTY) return cudaErrorInvalidValue;
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + p.ty - 1) / p.ty);
   const int threads = TX * (p.ty + 1);
   const size_t bytes = d2q9_smem_bytes(p.ty);
@@ -663,6 +669,9 @@ void split_all(const double (&x)[N][M][L], dw (&d)[N][M][L]) {
   for (size_t i = 0; i < N; ++i) split_all(x[i], d[i]);
 }
 }  // namespace
+
+int d2q9_max_ty(bool dwa) { return dwa ? Arith<dw>::kMaxTY : Arith<double>::kMaxTY; }
+int d2q9_blocks_per_sm(bool dwa) { return dwa ? Arith<dw>::kMinBlocks : 1; }
 
 cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage,
                               const double* gin, const double* own, const double* rho_in,

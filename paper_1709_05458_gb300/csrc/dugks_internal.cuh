@@ -220,6 +220,9 @@ struct D2Q9StageDW {
   dw gamma;
   dw kx[9], ky[9];
 };
+// largest tile height and resident blocks per SM of the FP64 / double-word kernels
+int d2q9_max_ty(bool dwa);
+int d2q9_blocks_per_sm(bool dwa);
 void d2q9_params_to_dw(const D2Q9Params& p, D2Q9ParamsDW& d);
 void d2q9_stage_to_dw(const D2Q9Stage& s, D2Q9StageDW& d);
 cudaError_t launch_d2q9dw_stage(const D2Q9ParamsDW& p, const D2Q9StageDW& s, int stage,
