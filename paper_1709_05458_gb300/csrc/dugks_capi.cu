@@ -295,7 +295,7 @@ int one_step_d2q9(dugks_ctx* c) {
   cudaStream_t s = c->stream;
   const size_t N = c->p.N;
   if (!c->g1_valid) {
-    TRY(launch(c, K_D2Q9_PROLOGUE, [&] { return launch_cell(c->p, 1, 1, c->fhat, c->g, c->mom, c->s1.a, c->s1.b, s); }));
+    TRY(launch(c, K_D2Q9_PROLOGUE, [&] { return launch_d2q9_cell(c->dp, true, c->fhat, c->g, c->mom, s); }));
     c->g1_valid = true;
   }
   if (c->dwa) {
@@ -418,7 +418,7 @@ int ensure_g1(dugks_ctx* c) {
     }));
   else
     TRY(launch(c, K_D2Q9_PROLOGUE, [&] {
-      return launch_cell(c->p, 1, 1, c->fhat, c->g, c->mom, c->s1.a, c->s1.b, s);
+      return launch_d2q9_cell(c->dp, true, c->fhat, c->g, c->mom, s);
     }));
   c->g1_valid = true;
   return DUGKS_OK;
@@ -973,13 +973,25 @@ int dugks_step(dugks_ctx* c, int n) {
 int dugks_moments(dugks_ctx* c, double* rho, double* ux, double* uy, int on_device) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
   TRY(launch(c, K_MOMENTS, [&] {
-    return c->store ? launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, c->mom, 0.0, 0.0, 0, c->stream)
-                    : launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
+    if (c->store)
+      return launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, c->mom, 0.0, 0.0, 0, c->stream);
+    if (c->d2q9) return launch_d2q9_cell(c->dp, false, c->fhat, nullptr, c->mom, c->stream);
+    return launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
   }));
+  // the three copies are queued on the stream; one synchronisation for host buffers
   const size_t N = c->p.N;
-  if (rho) TRY(copy_out(c, rho, c->mom, N, on_device));
-  if (ux) TRY(copy_out(c, ux, c->mom + N, N, on_device));
-  if (uy) TRY(copy_out(c, uy, c->mom + 2 * N, N, on_device));
+  double* dst[3] = {rho, ux, uy};
+  for (int m = 0; m < 3; ++m) {
+    if (!dst[m]) continue;
+    cudaError_t e = cudaMemcpyAsync(dst[m], c->mom + m * N, N * sizeof(double),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy from device");
+  }
+  if (!on_device) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy from device");
+  }
   return DUGKS_OK;
 }
 

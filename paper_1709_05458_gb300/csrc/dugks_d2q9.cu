@@ -541,6 +541,40 @@ k_d2q9(typename Arith<A>::Par P, typename Arith<A>::Stg S, const double* __restr
                           blockIdx.y * P.ty, reinterpret_cast<A*>(smem));
 }
 
+// Cell pass of the fused path outside a step, one thread per cell: the
+// moments of f^ (rho, ux, uy; Sec. 2.2) into mom[3][N] and, with G, g1 =
+// f-bar^{+,dt/6} of eq. f_bar_1_6 in the stage-2 kernel's own arithmetic
+// (the prologue after a new state).
+template <bool G, bool WS>
+__global__ void __launch_bounds__(256)
+k_d2q9_cell(D2Q9Params P, const double* __restrict__ fhat, double* __restrict__ g1,
+            double* __restrict__ mom) {
+  const int N = P.N;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N) return;
+  double f[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) f[k] = __ldg(fhat + (size_t)k * N + cell);
+  double rho, sx, sy;
+  d2q9_sums(f, rho, sx, sy);
+  const double cr = P.c / rho;
+  mom[cell] = rho;
+  mom[N + cell] = sx * cr;
+  mom[2 * N + cell] = sy * cr;
+  if constexpr (G) {
+    double utx, uty;
+    d2q9_ut(rho, sx, sy, P, utx, uty);
+    double Pk[9], rbw[3];
+    d2q9_poly(utx, uty, P, Pk);
+    const double rb = P.b1 * rho;
+    wclasses<WS>(P, rb, rbw);
+    for9([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      g1[(size_t)k * N + cell] = fma(wk<WS, k>(P, rb, rbw), Pk[k], P.a1 * f[k]);
+    });
+  }
+}
+
 // Persistent batched stage kernel: blocks take (instance, tile) work items
 // from an atomic counter until all tiles of all instances are done (no
 // waiting on other blocks).  Instance parameters and stage tables are read
@@ -669,6 +703,18 @@ void split_all(const double (&x)[N][M][L], dw (&d)[N][M][L]) {
   for (size_t i = 0; i < N; ++i) split_all(x[i], d[i]);
 }
 }  // namespace
+
+cudaError_t launch_d2q9_cell(const D2Q9Params& p, bool write_g, const double* fhat, double* g1,
+                             double* mom, cudaStream_t st) {
+  const int blocks = (p.N + 255) / 256;
+  if (write_g) {
+    if (p.wsym) k_d2q9_cell<true, true><<<blocks, 256, 0, st>>>(p, fhat, g1, mom);
+    else k_d2q9_cell<true, false><<<blocks, 256, 0, st>>>(p, fhat, g1, mom);
+  } else {
+    k_d2q9_cell<false, false><<<blocks, 256, 0, st>>>(p, fhat, g1, mom);
+  }
+  return cudaGetLastError();
+}
 
 int d2q9_max_ty(bool dwa) { return dwa ? Arith<dw>::kMaxTY : Arith<double>::kMaxTY; }
 int d2q9_blocks_per_sm(bool dwa) { return dwa ? Arith<dw>::kMinBlocks : 1; }

@@ -193,6 +193,9 @@ cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage
                               double* out0, double* out1, double* rho_out, cudaStream_t st);
 size_t d2q9_smem_bytes(int ty);
 cudaError_t d2q9_prepare(int ty);
+// moments of f^ into mom[3][N] (rho, ux, uy) and, with write_g, g1 (FP64 fused path)
+cudaError_t launch_d2q9_cell(const D2Q9Params& p, bool write_g, const double* fhat, double* g1,
+                             double* mom, cudaStream_t st);
 
 // Double-word arithmetic form of the fused D2Q9 kernels: FP64 arrays, every
 // operation in double-word (FP32 pair) arithmetic (dugks_dw.cuh).  The
