@@ -125,7 +125,10 @@ int dugks_set_equilibrium(dugks_ctx* ctx, const double* rho, const double* ux,
                           const double* uy, int on_device);
 
 /* dugks_set_state -- copy f^ = f - dt/4 Omega (eq. feqIntD3rdHat2), array
- * [nv][ny][nx], into the context. */
+ * [nv][ny][nx], into the context.  With on_device = 0 the call returns once
+ * the host array has been copied (it may then be freed or reused); the
+ * work that follows the copy (the conversion of the deviation forms, the
+ * fused D2Q9 path's first pass, eq. f_bar_1_6) stays queued on the stream. */
 int dugks_set_state(dugks_ctx* ctx, const double* fhat, int on_device);
 
 /* dugks_get_state -- copy the current f^ [nv][ny][nx] out.  With

@@ -99,6 +99,7 @@ struct dugks_ctx {
   StageCoef t2{};               // g = a f~ + b feq, h = dt/2, f = alpha f-bar + beta feq
   double t2a = 0.0, t2b = 0.0;  // f~^+ = t2a f~ + t2b feq
   int batched = 0;              // number of batches holding this context
+  cudaEvent_t ev_copy = nullptr;  // end of dugks_set_state's host upload
   // adjoint (allocated on first use): forward intermediates and adjoint fields
   double *a_g1 = nullptr, *a_g2 = nullptr, *a_ftp = nullptr, *a_acc = nullptr;
   double *a_mom1 = nullptr, *a_mom2 = nullptr, *a_tbar = nullptr, *a_gbar = nullptr;
@@ -221,6 +222,7 @@ void free_all(dugks_ctx* c) {
     cudaEventDestroy(q.b);
   }
   for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->ev_copy) cudaEventDestroy(c->ev_copy);
 }
 
 // Quadratic Taylor weights about one cell centre for the foot offset
@@ -940,16 +942,35 @@ int dugks_set_equilibrium(dugks_ctx* c, const double* rho, const double* ux, con
 int dugks_set_state(dugks_ctx* c, const double* fhat, int on_device) {
   if (!c || !fhat) return fail(DUGKS_EINVAL, "NULL argument");
   c->g1_valid = false;
-  if (c->store) {
-    const double* src = fhat;
-    if (!on_device) {
-      TRY(copy_in(c, c->fbx, fhat, (size_t)c->p.nv * c->p.N, 0));
-      src = c->fbx;
+  if (!on_device && !c->ev_copy &&
+      cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming) != cudaSuccess)
+    return cuda_fail(cudaGetLastError(), "dugks_set_state");
+  const size_t n = (size_t)c->p.nv * c->p.N;
+  const double* src = fhat;
+  if (!on_device || !c->store) {                  // deviation forms convert from a staging copy
+    double* dst = c->store ? c->fbx : c->fhat;
+    cudaError_t e = cudaMemcpyAsync(dst, fhat, n * sizeof(double),
+                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess && !on_device) e = cudaEventRecord(c->ev_copy, c->stream);
+    if (e != cudaSuccess) {
+      cudaStreamSynchronize(c->stream);
+      return cuda_fail(e, "copy to device");
     }
-    TRY(launch(c, K_CONVERT, [&] { return launch_dev_from_f64(c->p, c->store, c->rho0, src, c->fhat, c->stream); }));
-    return DUGKS_OK;
+    src = dst;
   }
-  return copy_in(c, c->fhat, fhat, (size_t)c->p.nv * c->p.N, on_device);
+  // the conversion and the fused paths' g1 prologue are queued right behind
+  // the copy; the call returns once the copy itself is done (the caller may
+  // free or reuse a host buffer after return)
+  int rc = DUGKS_OK;
+  if (c->store)
+    rc = launch(c, K_CONVERT, [&] { return launch_dev_from_f64(c->p, c->store, c->rho0, src, c->fhat, c->stream); });
+  if (rc == DUGKS_OK && c->d2q9 && c->scheme == DUGKS_T3S3) rc = ensure_g1(c);
+  if (!on_device) {
+    const cudaError_t e = cudaEventSynchronize(c->ev_copy);
+    if (e != cudaSuccess && rc == DUGKS_OK) return cuda_fail(e, "copy to device");
+  }
+  return rc;
 }
 
 int dugks_get_state(dugks_ctx* c, double* fhat, int on_device) {
