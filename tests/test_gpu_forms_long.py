@@ -1,0 +1,67 @@
+"""The cavity256 workload over its full length (20 000 steps, 256^2 D2Q9,
+Re 1000, lid Ma 0.1, from rest): the FP32 and BF16 deviation forms and the
+double-word form against the FP64 kernels at 1k, 5k and 20k steps.
+
+The FP64 kernels match the oracle to 1e-12 (test_gpu_parity.py); the oracle
+itself would need about 40 minutes of one host core for 20 000 steps at
+this size, so the FP64 kernels stand in for it here.  E(u) is the L2
+velocity error of Sec. 3.1, mass drift |sum rho - sum rho_64| / sum rho_64.
+Bounds are 3-5x the values measured on GB300 (quoted per row):
+
+    steps   FP32 E(u)   BF16 E(u)   DW E(u)    DW state rel Linf
+    1000    1.5e-5      3.1e-2      2.7e-12    1.2e-13
+    5000    8.2e-5      0.105       7.4e-12    6.4e-13
+    20000   4.1e-4      0.246       3.6e-11    2.0e-12
+
+BF16 deviations (2^-9 relative rounding) drift to a quarter of the velocity
+field's norm by 20 000 steps; FP32 stays below 1e-3; the double-word form
+tracks FP64 to 1e-12 in the state for the first few thousand steps."""
+import numpy as np
+import pytest
+
+import paper_1709_05458_gb300 as P
+from paper_1709_05458_gb300 import velocity_sets as PV
+import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {      # steps: (FP32 E(u), mass), (BF16 E(u), mass), (DW E(u), DW state)
+    1000: ((5e-5, 2e-8), (0.1, 1e-4), (1e-11, 5e-13)),
+    5000: ((3e-4, 2e-7), (0.3, 5e-4), (3e-11, 3e-12)),
+    20000: ((2e-3, 1e-6), (0.6, 5e-3), (2e-10, 1e-11)),
+}
+
+
+def test_cavity256_full_length_forms(cuda):
+    c = WL.config("cavity256")
+    xi, W, RT = PV.d2q9(c["RT"])
+    forms = {"fp64": P.FP64, "fp32": P.G_FP32, "bf16": P.G_BF16, "dw": P.F64_DW}
+    sol = {}
+    for name, st in forms.items():
+        s = P.Solver(256, 256, 1 / 256, 1 / 256, xi, W, RT, c["tau"], c["dt"], c["bc"], storage=st)
+        s.set_equilibrium(*WL.rest_fields(256, 256))
+        sol[name] = s
+    done = 0
+    try:
+        for n in (1000, 5000, c["steps"]):
+            for s in sol.values():
+                s.step(n - done)
+            done = n
+            r0, u0, v0 = sol["fp64"].moments()
+            den = np.sqrt((u0 ** 2 + v0 ** 2).sum())
+            got = {}
+            for name in ("fp32", "bf16", "dw"):
+                r, u, v = sol[name].moments()
+                got[name] = (float(np.sqrt(((u - u0) ** 2 + (v - v0) ** 2).sum()) / den),
+                             float(abs(r.sum() - r0.sum()) / r0.sum()))
+            f64 = sol["fp64"].state()
+            dws = float(np.abs(sol["dw"].state() - f64).max() / np.abs(f64).max())
+            (e32, m32), (e16, m16), (edw, sdw) = BOUNDS[n]
+            assert got["fp32"][0] <= e32 and got["fp32"][1] <= m32, (n, got["fp32"])
+            assert got["bf16"][0] <= e16 and got["bf16"][1] <= m16, (n, got["bf16"])
+            assert got["dw"][0] <= edw and dws <= sdw, (n, got["dw"], dws)
+        for s in sol.values():
+            assert s.check() == P.DUGKS_OK
+    finally:
+        for s in sol.values():
+            s.close()
