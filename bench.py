@@ -182,6 +182,26 @@ def dist_setup():
     return world, rank, local
 
 
+def reduce_max(vals, world):
+    """Max over the ranks of a list of floats (the timing rule: the slowest
+    rank's time); one rank returns the list unchanged."""
+    vals = [float(v) for v in vals]
+    if world == 1:
+        return vals
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
+def whole_job_rate(units_per_rank, steps, world, seconds):
+    """G updates/s of the whole job: every rank advances its own replica of
+    units_per_rank cell-velocities per step (weak scaling)."""
+    return units_per_rank * steps * world / seconds / 1e9
+
+
 def make_solver(P, PV, WL, stream, storage=0, scheme="t3s3"):
     c = WL.config(WORKLOAD)
     if c.get("vel") == "nc":
@@ -425,16 +445,12 @@ def run_ours(args):
                                         for k, v in fprof.items() if v[0]}}
             s2.close()
 
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_s = float(t[0]), float(t[1])
+    ms, e2e_s = reduce_max([ms, e2e_s], world)
     if rank != 0:
         return 0
 
-    value = units * args.steps * world / (ms * 1e-3) / 1e9
-    e2e = units * e2e_steps * world / e2e_s / 1e9 if e2e_steps else None
+    value = whole_job_rate(units, args.steps, world, ms * 1e-3)
+    e2e = whole_job_rate(units, e2e_steps, world, e2e_s) if e2e_steps else None
 
     # roofline of the dominant kernel (largest share of device time)
     flops_per_unit = dict(FLOPS_PER_UNIT)
