@@ -294,7 +294,11 @@ def run_batched(args):
     from paper_1709_05458_gb300 import velocity_sets as PV
     import workloads as WL
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    world, rank, local = dist_setup()
+    if world > 1:                                 # one replica of the batch per rank
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     P.load()
     insts = WL.config("batched64")["instances"]
@@ -326,6 +330,8 @@ def run_batched(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
     with torch.cuda.stream(stream):
         for a, b in evs:
             flush.fill_(1.0)
@@ -333,25 +339,99 @@ def run_batched(args):
             batch.step(1)
             b.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     ms = sum(a.elapsed_time(b) for a, b in evs)
     ok = all(s.check() == P.DUGKS_OK for s in sols)
+    ms, = reduce_max([ms], world)
+    if rank != 0:
+        batch.close()
+        return 0
     n_d2q9 = sum(1 for it in insts if it["vel"] == "d2q9")
     d2q9_units = sum(it["N"] ** 2 * 9 for it in insts if it["vel"] == "d2q9")
     line = {
         "metric": "G cell-velocity updates/s (T3S3 step, batched instances)",
-        "value": units * args.steps / (ms * 1e-3) / 1e9, "unit": "G updates/s", "n_gpus": 1,
+        "value": whole_job_rate(units, args.steps, world, ms * 1e-3), "unit": "G updates/s",
+        "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "batched64", "instances": len(insts), "d2q9_instances": n_d2q9,
                    "units_per_step": units, "d2q9_units_per_step": d2q9_units,
                    "graph": "one CUDA graph per bench step",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
                    "tile_heights": sorted(set(tuned.values())),
                    "l2": "flushed (256 MiB write) before every timed step"},
         "stable": ok,
     }
     print(json.dumps(line))
     batch.close()
+    return 0
+
+
+def run_adjoint(args):
+    """The gradient workload (cavity 128^2 D2Q9 FP64, Re 1000, lid Ma 0.1,
+    CFL 0.25, checkpoints every 100 steps): one dugks_adjoint_run over K
+    forward steps -- the checkpointed forward sweep, then per segment the
+    recomputed forward states and the reverse steps -- timed with CUDA events
+    on the solver's stream; value = cells x velocities x K / time.  The
+    forward-only rate of the same solver is reported beside it."""
+    import numpy as np
+    import torch
+    import paper_1709_05458_gb300 as P
+    from paper_1709_05458_gb300 import velocity_sets as PV
+    import workloads as WL
+
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    P.load()
+    n = 128
+    c = WL.config("cavity128")
+    xi, W, RT = PV.d2q9(c["RT"])
+    dt = 0.5 * c["dt"]
+    s = P.Solver(n, n, 1.0 / n, 1.0 / n, xi, W, RT, c["tau"], dt, c["bc"], stream=stream)
+    s.set_equilibrium(*WL.rest_fields(n, n))
+    units = n * n * len(W)
+    every = 100
+    with torch.cuda.stream(stream):
+        f0 = torch.empty((len(W), n, n), dtype=torch.float64, device="cuda")
+        P.dugks_get_state(s.ctx, f0)
+        lam = torch.ones_like(f0)
+        lam0 = torch.empty_like(f0)
+        for _ in range(max(args.warmup, 0)):
+            P.dugks_adjoint_run(s.ctx, f0, every, every, lam, lam0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        P.dugks_adjoint_run(s.ctx, f0, args.steps, every, lam, lam0)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        P.dugks_set_state(s.ctx, f0)
+        fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fa.record(stream)
+        s.step(args.steps)
+        fb.record(stream)
+        fb.synchronize()
+        fms = fa.elapsed_time(fb)
+    ok = bool(torch.isfinite(lam0).all()) and s.check() == P.DUGKS_OK
+    line = {
+        "metric": "G cell-velocity updates/s (T3S3 gradient: checkpointed forward + reverse)",
+        "value": units * args.steps / (ms * 1e-3) / 1e9, "unit": "G updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "adjoint128", "cells": f"{n}x{n}", "velocities": "D2Q9",
+                   "bc": "bounce-back walls, moving lid", "checkpoint_every": every,
+                   "units_per_step": units, "l2": "not flushed (one call covers all steps)"},
+        "forward_only": {"value": units * args.steps / (fms * 1e-3) / 1e9,
+                         "ms_per_step": fms / args.steps},
+        "stable": ok,
+    }
+    print(json.dumps(line))
+    s.close()
     return 0
 
 
@@ -561,6 +641,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched64":
         return run_batched(args)
+    if args.workload == "adjoint128":
+        return run_adjoint(args)
     return run_ours(args)
 
 

@@ -31,6 +31,29 @@ namespace {
 
 constexpr int kT = 128;
 
+// Adds the block's sum of v[0..M) to dst[0..M): warp shuffles, then the
+// warps' partials in shared memory, one atomic per non-zero value (the
+// parameter gradients would otherwise see one same-address atomic per
+// thread).  Every thread of the block must call it.
+template <int M>
+__device__ __forceinline__ void block_add(double (&v)[M], double* __restrict__ dst) {
+  __shared__ double sm[kT / 32][M];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_xor_sync(0xffffffffu, v[m], o);
+  if (lane == 0)
+#pragma unroll
+    for (int m = 0; m < M; ++m) sm[warp][m] = v[m];
+  __syncthreads();
+  if (threadIdx.x < M) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w][threadIdx.x];
+    if (t != 0.0) atomicAdd(dst + threadIdx.x, t);
+  }
+}
+
 __device__ __forceinline__ void eq_terms(double cx, double cy, double ux, double uy,
                                          const DevParams& p, double& P, double& e) {
   e = (cx * ux + cy * uy) * p.inv_RT;
@@ -39,10 +62,10 @@ __device__ __forceinline__ void eq_terms(double cx, double cy, double ux, double
 }
 
 // add v * weight to g_bar at cell (i, j) of one velocity, mapping ghosts
-__device__ void add_cell(double* __restrict__ gb, const DevParams& p, int i, int j, double v) {
+__device__ __forceinline__ void add_cell(double* __restrict__ gb, const DevParams& p, int i, int j, double v) {
   // resolve x
-  int ix[3];
-  double cx[3];
+  int ix[3] = {0, 0, 0};
+  double cx[3] = {0.0, 0.0, 0.0};
   int nxr;
   if (i >= 0 && i < p.nx) { ix[0] = i; cx[0] = 1.0; nxr = 1; }
   else if (p.px) { ix[0] = (i < 0) ? i + p.nx : i - p.nx; cx[0] = 1.0; nxr = 1; }
@@ -50,8 +73,8 @@ __device__ void add_cell(double* __restrict__ gb, const DevParams& p, int i, int
     const int b = (i < 0) ? 0 : p.nx - 1, s = (i < 0) ? 1 : -1;
     ix[0] = b; ix[1] = b + s; ix[2] = b + 2 * s; cx[0] = 3.0; cx[1] = -3.0; cx[2] = 1.0; nxr = 3;
   }
-  int iy[3];
-  double cy[3];
+  int iy[3] = {0, 0, 0};
+  double cy[3] = {0.0, 0.0, 0.0};
   int nyr;
   if (j >= 0 && j < p.ny) { iy[0] = j; cy[0] = 1.0; nyr = 1; }
   else if (p.py) { iy[0] = (j < 0) ? j + p.ny : j - p.ny; cy[0] = 1.0; nyr = 1; }
@@ -59,12 +82,16 @@ __device__ void add_cell(double* __restrict__ gb, const DevParams& p, int i, int
     const int b = (j < 0) ? 0 : p.ny - 1, s = (j < 0) ? 1 : -1;
     iy[0] = b; iy[1] = b + s; iy[2] = b + 2 * s; cy[0] = 3.0; cy[1] = -3.0; cy[2] = 1.0; nyr = 3;
   }
-  for (int a = 0; a < nyr; ++a)
-    for (int b = 0; b < nxr; ++b) atomicAdd(gb + iy[a] * p.nx + ix[b], v * cy[a] * cx[b]);
+  // fixed trip counts keep the index arrays in registers
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      if (a < nyr && b < nxr) atomicAdd(gb + iy[a] * p.nx + ix[b], v * cy[a] * cx[b]);
 }
 
 // transpose of the Taylor expansion about cell (ci, cj) at offset (dX, dY)
-__device__ void scatter_taylor(double* __restrict__ gb, const DevParams& p, int ci, int cj,
+__device__ __forceinline__ void scatter_taylor(double* __restrict__ gb, const DevParams& p, int ci, int cj,
                                double dX, double dY, double v) {
   const double a = dX * p.inv_dx, b = dY * p.inv_dy;
   add_cell(gb, p, ci, cj, v * (1.0 - a * a - b * b));
@@ -79,15 +106,11 @@ __device__ void scatter_taylor(double* __restrict__ gb, const DevParams& p, int 
 }
 
 // g at any cell within one ghost layer (forward reconstruction, as in the
-// forward generic kernels)
-__device__ double g_at(const double* __restrict__ gk, const DevParams& p, int i, int j) {
-  if (i < 0 || i >= p.nx) {
-    if (p.px) i = (i < 0) ? i + p.nx : i - p.nx;
-    else {
-      const int b = (i < 0) ? 0 : p.nx - 1, s = (i < 0) ? 1 : -1;
-      return 3.0 * g_at(gk, p, b, j) - 3.0 * g_at(gk, p, b + s, j) + g_at(gk, p, b + 2 * s, j);
-    }
-  }
+// forward generic kernels): a wall ghost along x is the extrapolation
+// 3 g_0 - 3 g_1 + g_2 of the y-resolved values of its row's interior cells,
+// along y the same of the interior cells of its column
+__device__ __forceinline__ double g_col(const double* __restrict__ gk, const DevParams& p, int i,
+                                        int j) {
   if (j < 0 || j >= p.ny) {
     if (p.py) j = (j < 0) ? j + p.ny : j - p.ny;
     else {
@@ -97,8 +120,19 @@ __device__ double g_at(const double* __restrict__ gk, const DevParams& p, int i,
   }
   return gk[j * p.nx + i];
 }
+__device__ __forceinline__ double g_at(const double* __restrict__ gk, const DevParams& p, int i,
+                                       int j) {
+  if (i < 0 || i >= p.nx) {
+    if (p.px) i = (i < 0) ? i + p.nx : i - p.nx;
+    else {
+      const int b = (i < 0) ? 0 : p.nx - 1, s = (i < 0) ? 1 : -1;
+      return 3.0 * g_col(gk, p, b, j) - 3.0 * g_col(gk, p, b + s, j) + g_col(gk, p, b + 2 * s, j);
+    }
+  }
+  return g_col(gk, p, i, j);
+}
 
-__device__ double taylor(const double* __restrict__ gk, const DevParams& p, int ci, int cj,
+__device__ __forceinline__ double taylor(const double* __restrict__ gk, const DevParams& p, int ci, int cj,
                          double dX, double dY) {
   const double C = g_at(gk, p, ci, cj);
   const double E = g_at(gk, p, ci + 1, cj), W = g_at(gk, p, ci - 1, cj);
@@ -119,7 +153,7 @@ struct FaceGeo {
 };
 
 template <int DIR>
-__device__ FaceGeo face_geo(const DevParams& p, int face) {
+__device__ __forceinline__ FaceGeo face_geo(const DevParams& p, int face) {
   FaceGeo f{};
   f.side = -1;
   if (DIR == 0) {
@@ -143,7 +177,7 @@ __device__ FaceGeo face_geo(const DevParams& p, int face) {
 // forward f-bar of velocity k at a face (the fluid side or upwind rule),
 // without the outgoing wall rules
 template <int DIR>
-__device__ double fbar_recon(const double* __restrict__ g, const DevParams& p, const FaceGeo& f,
+__device__ __forceinline__ double fbar_recon(const double* __restrict__ g, const DevParams& p, const FaceGeo& f,
                              int k, double h) {
   const double cx = __ldg(p.xi_x + k), cy = __ldg(p.xi_y + k);
   const double cn = DIR == 0 ? cx : cy;
@@ -159,7 +193,7 @@ __device__ double fbar_recon(const double* __restrict__ g, const DevParams& p, c
 }
 
 template <int DIR>
-__device__ void fbar_scatter(double* __restrict__ gbar, const DevParams& p, const FaceGeo& f,
+__device__ __forceinline__ void fbar_scatter(double* __restrict__ gbar, const DevParams& p, const FaceGeo& f,
                              int k, double h, double v) {
   const double cx = __ldg(p.xi_x + k), cy = __ldg(p.xi_y + k);
   const double cn = DIR == 0 ? cx : cy;
@@ -217,16 +251,16 @@ k_flux_T(DevParams p, const double* __restrict__ A, double sa, const double* __r
 }
 
 // Face adjoint: phi (adjoint of f_b, overwritten) -> g_bar (scatter),
-// rho_bar of wall-adjacent cells (bounce-back rho_w), d/d tau, d/d u_w.
+// rho_bar of wall-adjacent cells (bounce-back rho_w), and this face's
+// contributions to d/d tau (gr[0]) and d/d u_w (gr[1 + 2 side], gr[2 + 2 side]).
 // One thread per face, looping over all velocities.
 template <int DIR>
-__global__ void __launch_bounds__(kT)
-k_face_T(DevParams p, const double* __restrict__ g, const double* __restrict__ mom,
-         double* __restrict__ phi, double* __restrict__ gbar, double* __restrict__ rhobar,
-         double* __restrict__ grads, double h, double alpha, double beta, double dalpha) {
-  const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
-  const int face = blockIdx.x * blockDim.x + threadIdx.x;
-  if (face >= nf) return;
+__device__ __forceinline__ void face_T(const DevParams& p, int face, int nf,
+                                       const double* __restrict__ g,
+                                       const double* __restrict__ mom, double* __restrict__ phi,
+                                       double* __restrict__ gbar, double* __restrict__ rhobar,
+                                       double h, double alpha, double beta, double dalpha,
+                                       double (&gr)[9]) {
   const FaceGeo f = face_geo<DIR>(p, face);
   const int nv = p.nv;
   const int kind = f.side >= 0 ? p.bc_kind[f.side] : -1;
@@ -329,10 +363,13 @@ k_face_T(DevParams p, const double* __restrict__ g, const double* __restrict__ m
     }
   }
   if (f.side >= 0 && kind >= 0) {
-    atomicAdd(grads + 1 + 2 * f.side, uwb_x);
-    atomicAdd(grads + 2 + 2 * f.side, uwb_y);
+#pragma unroll
+    for (int sd = 0; sd < 4; ++sd) {             // constant indices keep gr in registers
+      gr[1 + 2 * sd] += sd == f.side ? uwb_x : 0.0;
+      gr[2 + 2 * sd] += sd == f.side ? uwb_y : 0.0;
+    }
   }
-  atomicAdd(grads, tau_bar);
+  gr[0] += tau_bar;
   // transpose of the reconstruction
   for (int k = 0; k < nv; ++k) {
     const double ps = phi[(size_t)k * nf + face];
@@ -340,18 +377,30 @@ k_face_T(DevParams p, const double* __restrict__ g, const double* __restrict__ m
   }
 }
 
+// the parameter block stays in parameter space under the wall-side indexing
+template <int DIR>
+__global__ void __launch_bounds__(kT)
+k_face_T(const __grid_constant__ DevParams p, const double* __restrict__ g, const double* __restrict__ mom,
+         double* __restrict__ phi, double* __restrict__ gbar, double* __restrict__ rhobar,
+         double* __restrict__ grads, double h, double alpha, double beta, double dalpha) {
+  const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
+  const int face = blockIdx.x * blockDim.x + threadIdx.x;
+  double gr[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  if (face < nf) face_T<DIR>(p, face, nf, g, mom, phi, gbar, rhobar, h, alpha, beta, dalpha, gr);
+  block_add<9>(gr, grads);
+}
+
 // Cell adjoint of g = a x + b feq(x) and of an extra equilibrium use
 // c_extra * feq(x) weighted by `lam` (stage 2: f^^{n+1} contains c (f~' - feq')):
 //   xbar_k += a gbar_k + (extra direct c_direct lam_k) + rho_bar + xi_k.J_bar
 // with mu_k = b gbar_k - c_extra lam_k, rho_bar including wall uses.
 // d/d tau += sum gbar (a' x + b' feq) + c' sum lam (x - feq).
-__global__ void __launch_bounds__(kT)
-k_cell_T(DevParams p, const double* __restrict__ x, const double* __restrict__ gbar,
-         const double* __restrict__ lam, const double* __restrict__ rhobar_extra,
-         double* __restrict__ xbar, double a, double b, double c_extra, double da,
-         double dc, double* __restrict__ grads) {
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= p.N) return;
+__device__ __forceinline__ double cell_T(const DevParams& p, int cell, const double* __restrict__ x,
+                                         const double* __restrict__ gbar,
+                                         const double* __restrict__ lam,
+                                         const double* __restrict__ rhobar_extra,
+                                         double* __restrict__ xbar, double a, double b,
+                                         double c_extra, double da, double dc) {
   double r = 0.0, jx = 0.0, jy = 0.0;
   for (int k = 0; k < p.nv; ++k) {
     const double v = x[(size_t)k * p.N + cell];
@@ -380,7 +429,18 @@ k_cell_T(DevParams p, const double* __restrict__ x, const double* __restrict__ g
     const size_t idx = (size_t)k * p.N + cell;
     xbar[idx] += a * gbar[idx] + rb + __ldg(p.xi_x + k) * jbx + __ldg(p.xi_y + k) * jby;
   }
-  atomicAdd(grads, tb);
+  return tb;
+}
+
+__global__ void __launch_bounds__(kT)
+k_cell_T(DevParams p, const double* __restrict__ x, const double* __restrict__ gbar,
+         const double* __restrict__ lam, const double* __restrict__ rhobar_extra,
+         double* __restrict__ xbar, double a, double b, double c_extra, double da,
+         double dc, double* __restrict__ grads) {
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (cell < p.N) v[0] = cell_T(p, cell, x, gbar, lam, rhobar_extra, xbar, a, b, c_extra, da, dc);
+  block_add<1>(v, grads);
 }
 
 // out = sa * A + sb * B (elementwise over nv * N), either may be NULL
