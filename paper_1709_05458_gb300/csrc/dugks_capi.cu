@@ -277,15 +277,17 @@ double d2q9_speed(const dugks_velset* v) {
 
 // Tile height: the number of 32 x ty tiles per wave of resident blocks
 // times the work per tile (ty + 1 face rows) is minimised over ty in
-// [4, maxty].
-int d2q9_tile_height(int nx, int ny, int sms, int maxty) {
+// [4, maxty]; ties go to the lower height, or with prefer_tall (the
+// issue-bound double-word kernels, which gain from the smaller halo share of
+// taller tiles; measured by dugks_autotune) to the taller one.
+int d2q9_tile_height(int nx, int ny, int sms, int maxty, bool prefer_tall) {
   int best = 8;
   double bestc = 1e300;
   for (int ty = 4; ty <= maxty; ++ty) {
     const long tiles = (long)((nx + 31) / 32) * ((ny + ty - 1) / ty);
     const long waves = (tiles + sms - 1) / sms;
     const double cost = (double)waves * (ty + 1);
-    if (cost < bestc - 1e-9) {
+    if (cost < bestc - 1e-9 || (prefer_tall && cost <= bestc + 1e-9)) {
       bestc = cost;
       best = ty;
     }
@@ -866,7 +868,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     q.N = p.N;
     q.px = p.px;
     q.py = p.py;
-    q.ty = d2q9_tile_height(p.nx, p.ny, sms * d2q9_blocks_per_sm(dwa), d2q9_max_ty(dwa));
+    q.ty = d2q9_tile_height(p.nx, p.ny, sms * d2q9_blocks_per_sm(dwa), d2q9_max_ty(dwa), dwa);
     for (int k = 0; k < 9; ++k) q.W[k] = vel->w[k];
     q.c3 = cd * cd / vel->RT;
     q.base_div = 0.5 / q.c3;
