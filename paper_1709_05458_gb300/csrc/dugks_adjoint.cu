@@ -250,17 +250,46 @@ k_flux_T(DevParams p, const double* __restrict__ A, double sa, const double* __r
   phi[t] = v;
 }
 
-// Face adjoint: phi (adjoint of f_b, overwritten) -> g_bar (scatter),
-// rho_bar of wall-adjacent cells (bounce-back rho_w), and this face's
-// contributions to d/d tau (gr[0]) and d/d u_w (gr[1 + 2 side], gr[2 + 2 side]).
-// One thread per face, looping over all velocities.
+// Forward f-bar of every (face, velocity) of a stage, one thread each: the
+// upwind reconstruction, or at a bounce-back wall the reflected value
+// (eq. BB); the leaving velocities of a diffuse wall need the face's flux
+// sum and are formed by k_face_T (0 here).  fbs[k][face].
+template <int DIR>
+__global__ void __launch_bounds__(kT)
+k_fbar_T(const __grid_constant__ DevParams p, const double* __restrict__ g,
+         const double* __restrict__ mom, double* __restrict__ fbs, double h) {
+  const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)p.nv * nf) return;
+  const int k = (int)(t / nf), face = (int)(t - (size_t)k * nf);
+  const FaceGeo f = face_geo<DIR>(p, face);
+  const int kind = f.side >= 0 ? p.bc_kind[f.side] : -1;
+  const double xn = f.nsgn * (DIR == 0 ? __ldg(p.xi_x + k) : __ldg(p.xi_y + k));
+  double v = 0.0;
+  if (kind < 0 || xn >= 0.0) {
+    v = fbar_recon<DIR>(g, p, f, k, h);
+  } else if (kind == BC_BOUNCEBACK) {
+    const int wcell = f.fluid_upper ? f.uj * p.nx + f.ui : f.lj * p.nx + f.li;
+    const int kk = __ldg(p.opp + k);
+    v = fbar_recon<DIR>(g, p, f, kk, h) +
+        2.0 * mom[wcell] * __ldg(p.w + k) *
+            (__ldg(p.xi_x + k) * p.uw_x[f.side] + __ldg(p.xi_y + k) * p.uw_y[f.side]) * p.inv_RT;
+  }
+  fbs[t] = v;
+}
+
+// Face adjoint: phi (adjoint of f_b, overwritten with the adjoint of
+// f-bar), rho_bar of wall-adjacent cells (bounce-back rho_w), and this
+// face's contributions to d/d tau (gr[0]) and d/d u_w (gr[1 + 2 side],
+// gr[2 + 2 side]).  One thread per face, looping over all velocities; the
+// forward f-bar comes from k_fbar_T, the transposed reconstruction is
+// k_scatter_T's.
 template <int DIR>
 __device__ __forceinline__ void face_T(const DevParams& p, int face, int nf,
-                                       const double* __restrict__ g,
+                                       const double* __restrict__ fbs,
                                        const double* __restrict__ mom, double* __restrict__ phi,
-                                       double* __restrict__ gbar, double* __restrict__ rhobar,
-                                       double h, double alpha, double beta, double dalpha,
-                                       double (&gr)[9]) {
+                                       double* __restrict__ rhobar, double alpha, double beta,
+                                       double dalpha, double (&gr)[9]) {
   const FaceGeo f = face_geo<DIR>(p, face);
   const int nv = p.nv;
   const int kind = f.side >= 0 ? p.bc_kind[f.side] : -1;
@@ -271,20 +300,15 @@ __device__ __forceinline__ void face_T(const DevParams& p, int face, int nf,
     return f.nsgn * (DIR == 0 ? __ldg(p.xi_x + k) : __ldg(p.xi_y + k));
   };
   auto fbar = [&](int k, double rds) {   // forward f-bar of velocity k
-    if (kind < 0 || xn_of(k) >= 0.0) return fbar_recon<DIR>(g, p, f, k, h);
-    if (kind == BC_BOUNCEBACK) {
-      const int kk = __ldg(p.opp + k);
-      return fbar_recon<DIR>(g, p, f, kk, h) +
-             2.0 * rho_w * __ldg(p.w + k) * (__ldg(p.xi_x + k) * uwx + __ldg(p.xi_y + k) * uwy) * p.inv_RT;
-    }
-    return rds * p.feq_wall[f.side * nv + k];
+    if (kind == BC_DIFFUSE && xn_of(k) < 0.0) return rds * p.feq_wall[f.side * nv + k];
+    return fbs[(size_t)k * nf + face];
   };
   // diffuse rho_w
   double num = 0.0, rds = 0.0;
   if (kind == BC_DIFFUSE) {
     for (int k = 0; k < nv; ++k) {
       const double xn = xn_of(k);
-      if (xn > 0.0) num += xn * fbar_recon<DIR>(g, p, f, k, h);
+      if (xn > 0.0) num += xn * fbs[(size_t)k * nf + face];
     }
     rds = num / p.ds_den[f.side];
   }
@@ -370,24 +394,34 @@ __device__ __forceinline__ void face_T(const DevParams& p, int face, int nf,
     }
   }
   gr[0] += tau_bar;
-  // transpose of the reconstruction
-  for (int k = 0; k < nv; ++k) {
-    const double ps = phi[(size_t)k * nf + face];
-    if (ps != 0.0) fbar_scatter<DIR>(gbar, p, f, k, h, ps);
-  }
 }
 
 // the parameter block stays in parameter space under the wall-side indexing
 template <int DIR>
 __global__ void __launch_bounds__(kT)
-k_face_T(const __grid_constant__ DevParams p, const double* __restrict__ g, const double* __restrict__ mom,
-         double* __restrict__ phi, double* __restrict__ gbar, double* __restrict__ rhobar,
-         double* __restrict__ grads, double h, double alpha, double beta, double dalpha) {
+k_face_T(const __grid_constant__ DevParams p, const double* __restrict__ fbs,
+         const double* __restrict__ mom, double* __restrict__ phi, double* __restrict__ rhobar,
+         double* __restrict__ grads, double alpha, double beta, double dalpha) {
   const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
   const int face = blockIdx.x * blockDim.x + threadIdx.x;
   double gr[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  if (face < nf) face_T<DIR>(p, face, nf, g, mom, phi, gbar, rhobar, h, alpha, beta, dalpha, gr);
+  if (face < nf) face_T<DIR>(p, face, nf, fbs, mom, phi, rhobar, alpha, beta, dalpha, gr);
   block_add<9>(gr, grads);
+}
+
+// Transpose of the reconstruction: phi (the adjoint of f-bar) of every
+// (face, velocity) scattered onto g_bar, one thread each.
+template <int DIR>
+__global__ void __launch_bounds__(kT)
+k_scatter_T(const __grid_constant__ DevParams p, const double* __restrict__ phi,
+            double* __restrict__ gbar, double h) {
+  const int nf = DIR == 0 ? p.ny * (p.nx + 1) : (p.ny + 1) * p.nx;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)p.nv * nf) return;
+  const double ps = phi[t];
+  if (ps == 0.0) return;
+  const int k = (int)(t / nf), face = (int)(t - (size_t)k * nf);
+  fbar_scatter<DIR>(gbar, p, face_geo<DIR>(p, face), k, h, ps);
 }
 
 // Cell adjoint of g = a x + b feq(x) and of an extra equilibrium use
@@ -492,12 +526,18 @@ cudaError_t launch_flux_T(const DevParams& p, int dir, const double* A, double s
 
 cudaError_t launch_face_T(const DevParams& p, int dir, const double* g, const double* mom,
                           double* phi, double* gbar, double* rhobar, double* grads,
-                          const StageCoef& c, double dalpha, cudaStream_t s) {
+                          const StageCoef& c, double dalpha, double* fbs, cudaStream_t s) {
   const size_t nf = dir == 0 ? (size_t)p.ny * (p.nx + 1) : (size_t)(p.ny + 1) * p.nx;
-  if (dir == 0)
-    k_face_T<0><<<nb(nf), kT, 0, s>>>(p, g, mom, phi, gbar, rhobar, grads, c.h, c.alpha, c.beta, dalpha);
-  else
-    k_face_T<1><<<nb(nf), kT, 0, s>>>(p, g, mom, phi, gbar, rhobar, grads, c.h, c.alpha, c.beta, dalpha);
+  const size_t nk = nf * p.nv;
+  if (dir == 0) {
+    k_fbar_T<0><<<nb(nk), kT, 0, s>>>(p, g, mom, fbs, c.h);
+    k_face_T<0><<<nb(nf), kT, 0, s>>>(p, fbs, mom, phi, rhobar, grads, c.alpha, c.beta, dalpha);
+    k_scatter_T<0><<<nb(nk), kT, 0, s>>>(p, phi, gbar, c.h);
+  } else {
+    k_fbar_T<1><<<nb(nk), kT, 0, s>>>(p, g, mom, fbs, c.h);
+    k_face_T<1><<<nb(nf), kT, 0, s>>>(p, fbs, mom, phi, rhobar, grads, c.alpha, c.beta, dalpha);
+    k_scatter_T<1><<<nb(nk), kT, 0, s>>>(p, phi, gbar, c.h);
+  }
   return cudaGetLastError();
 }
 

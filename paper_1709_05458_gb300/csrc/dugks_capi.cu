@@ -105,6 +105,7 @@ struct dugks_ctx {
   double *a_mom1 = nullptr, *a_mom2 = nullptr, *a_tbar = nullptr, *a_gbar = nullptr;
   double *a_lam = nullptr, *a_out = nullptr, *a_phix = nullptr, *a_phiy = nullptr;
   double *a_rhob = nullptr, *a_grads = nullptr;
+  double* a_fbs = nullptr;      // forward f-bar of the faces of one direction [nv][nf]
   std::vector<double*> ckpt;    // checkpoint store for dugks_adjoint_run
   // profiling
   bool prof = false;
@@ -205,7 +206,8 @@ int copy_out(dugks_ctx* c, double* dst, const double* src, size_t n, int on_devi
 void free_all(dugks_ctx* c) {
   double* bufs[] = {c->fhat, c->ftp, c->acc, c->g, c->fbx, c->fby, c->mom, c->vel, c->part,
                     c->a_g1, c->a_g2, c->a_ftp, c->a_acc, c->a_mom1, c->a_mom2, c->a_tbar,
-                    c->a_gbar, c->a_lam, c->a_out, c->a_phix, c->a_phiy, c->a_rhob, c->a_grads};
+                    c->a_gbar, c->a_lam, c->a_out, c->a_phix, c->a_phiy, c->a_rhob, c->a_grads,
+                    c->a_fbs};
   for (double* b : bufs)
     if (b) cudaFree(b);
   for (double* b : c->ckpt)
@@ -440,7 +442,7 @@ int ensure_adjoint(dugks_ctx* c) {
   al(&c->a_g1, nvN); al(&c->a_g2, nvN); al(&c->a_ftp, nvN); al(&c->a_acc, nvN);
   al(&c->a_mom1, 3 * N); al(&c->a_mom2, 3 * N); al(&c->a_tbar, nvN); al(&c->a_gbar, nvN);
   al(&c->a_lam, nvN); al(&c->a_out, nvN); al(&c->a_phix, nfx); al(&c->a_phiy, nfy);
-  al(&c->a_rhob, N); al(&c->a_grads, 16);
+  al(&c->a_rhob, N); al(&c->a_grads, 16); al(&c->a_fbs, std::max(nfx, nfy));
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(e == cudaErrorMemoryAllocation ? DUGKS_ENOMEM : DUGKS_ECUDA,
@@ -484,8 +486,8 @@ int adjoint_core(dugks_ctx* c) {
   CK(launch_flux_T(p, 1, c->a_lam, 4.0 * dt / 7.0, nullptr, 0.0, c->a_phiy, s));
   CK(cudaMemsetAsync(c->a_gbar, 0, nvN * sizeof(double), s));
   CK(cudaMemsetAsync(c->a_rhob, 0, N * sizeof(double), s));
-  CK(launch_face_T(p, 0, c->a_g2, c->a_mom2, c->a_phix, c->a_gbar, c->a_rhob, c->a_grads, c->s2, dal2, s));
-  CK(launch_face_T(p, 1, c->a_g2, c->a_mom2, c->a_phiy, c->a_gbar, c->a_rhob, c->a_grads, c->s2, dal2, s));
+  CK(launch_face_T(p, 0, c->a_g2, c->a_mom2, c->a_phix, c->a_gbar, c->a_rhob, c->a_grads, c->s2, dal2, c->a_fbs, s));
+  CK(launch_face_T(p, 1, c->a_g2, c->a_mom2, c->a_phiy, c->a_gbar, c->a_rhob, c->a_grads, c->s2, dal2, c->a_fbs, s));
   CK(launch_cell_T(p, c->a_ftp, c->a_gbar, c->a_lam, c->a_rhob, c->a_tbar, c->s2.a, c->s2.b, c34,
                    da2, dc, c->a_grads, s));
   // stage 1: f~' = 5/4 g1 - 1/4 f^ + dt/3 L*,  X = 1/4 f^ + 3/4 g1 + 3dt/7 L*
@@ -494,8 +496,8 @@ int adjoint_core(dugks_ctx* c) {
   CK(launch_flux_T(p, 0, c->a_tbar, dt / 3.0, c->a_lam, 3.0 * dt / 7.0, c->a_phix, s));
   CK(launch_flux_T(p, 1, c->a_tbar, dt / 3.0, c->a_lam, 3.0 * dt / 7.0, c->a_phiy, s));
   CK(cudaMemsetAsync(c->a_rhob, 0, N * sizeof(double), s));
-  CK(launch_face_T(p, 0, c->a_g1, c->a_mom1, c->a_phix, c->a_gbar, c->a_rhob, c->a_grads, c->s1, dal1, s));
-  CK(launch_face_T(p, 1, c->a_g1, c->a_mom1, c->a_phiy, c->a_gbar, c->a_rhob, c->a_grads, c->s1, dal1, s));
+  CK(launch_face_T(p, 0, c->a_g1, c->a_mom1, c->a_phix, c->a_gbar, c->a_rhob, c->a_grads, c->s1, dal1, c->a_fbs, s));
+  CK(launch_face_T(p, 1, c->a_g1, c->a_mom1, c->a_phiy, c->a_gbar, c->a_rhob, c->a_grads, c->s1, dal1, c->a_fbs, s));
   CK(launch_cell_T(p, c->fhat, c->a_gbar, nullptr, c->a_rhob, c->a_out, c->s1.a, c->s1.b, 0.0,
                    da1, 0.0, c->a_grads, s));
   return DUGKS_OK;

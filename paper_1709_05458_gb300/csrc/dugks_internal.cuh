@@ -237,7 +237,7 @@ cudaError_t launch_flux_T(const DevParams& p, int dir, const double* A, double s
                           const double* B, double sb, double* phi, cudaStream_t s);
 cudaError_t launch_face_T(const DevParams& p, int dir, const double* g, const double* mom,
                           double* phi, double* gbar, double* rhobar, double* grads,
-                          const StageCoef& c, double dalpha, cudaStream_t s);
+                          const StageCoef& c, double dalpha, double* fbs, cudaStream_t s);
 cudaError_t launch_cell_T(const DevParams& p, const double* x, const double* gbar,
                           const double* lam, const double* rhobar, double* xbar, double a,
                           double b, double c_extra, double da, double dc, double* grads,
