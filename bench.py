@@ -10,10 +10,16 @@ before every timed step, and each step is timed with CUDA events on the
 solver's stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload W] [--storage fp64|fp32|bf16|f64dw] [--scheme t3s3|t2s3|t2s2]
 
 ``--impl reference`` times the CPU oracle (plain FP64 numpy restatement of
 the paper) on the host cores on the same workload; N > 1 runs independent
-replicas (one per rank, no data-path collective).
+replicas (one per rank, no data-path collective).  Other workloads:
+``cavityN`` (N^2 D2Q9 cavity), ``rarefied128_kn{0.1,1,10}_nv64`` (Newton-Cotes
+64 x 64, diffuse walls), ``batched64`` (64 uneven instances in one CUDA
+graph per step), ``adjoint128`` (the checkpointed gradient of the 128^2
+cavity).  The default line also reports the FP32, BF16 and double-word
+forms of the same workload (``forms``).
 """
 from __future__ import annotations
 

@@ -174,7 +174,8 @@ const char* dugks_kernel_name(int id);
 
 /*
  * dugks_autotune -- choose the tile height of the fused D2Q9 kernels for this
- * problem by timing `trials` steps for every height 4..16 on the context's
+ * problem by timing `trials` steps for every height 4..16 (4..12 for
+ * DUGKS_F64_DW, whose kernels keep two blocks per SM) on the context's
  * own stream and state (f^ is saved and restored; the state is unchanged on
  * return).  The chosen height is kept by the context and written to *ty_out.
  * Other velocity sets: DUGKS_ENOTIMPL.  Results of later steps are

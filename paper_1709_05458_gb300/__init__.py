@@ -225,8 +225,9 @@ def dugks_adjoint_equilibrium(ctx, rho, ux, uy, lam, drho=None, dux=None, duy=No
 
 
 def dugks_autotune(ctx, trials=3):
-    """Time tile heights 4..16 for this context's fused D2Q9 kernels and keep
-    the fastest (state unchanged); returns the chosen height."""
+    """Time tile heights 4..16 (4..12 for the double-word form) for this
+    context's fused D2Q9 kernels and keep the fastest (state unchanged);
+    returns the chosen height."""
     ty = C.c_int(0)
     _check(load().dugks_autotune(ctx, int(trials), C.byref(ty)))
     return ty.value
