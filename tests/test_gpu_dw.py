@@ -159,3 +159,26 @@ def test_batch_runs_double_word_instances_on_their_own_launches(cuda):
     bt.close()
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("storage", [P.FP64, P.F64_DW], ids=["fp64", "dw"])
+def test_unequal_weights_take_the_general_kernels(cuda, storage):
+    """D2Q9 velocities with weights that differ inside a class (W of +x and
+    -x moved by +-0.01, still summing to one): the fused kernels' general
+    instantiations (one weight per velocity) against the oracle with the
+    same weights, bounce-back cavity, 8 steps."""
+    pg, po = PV.d2q9(1 / 3), OV.d2q9(1 / 3)
+    W, Wo = np.array(pg[1], dtype=float), np.array(po[1], dtype=float)
+    for w in (W, Wo):     # each side perturbs its own set
+        w[7] += 0.01      # (+1, 0)
+        w[1] -= 0.01      # (-1, 0)
+    nx, ny = 45, 33
+    bc = [(P.BOUNCEBACK, 0, 0)] * 3 + [(P.BOUNCEBACK, 0.05, 0)]
+    g = P.Solver(nx, ny, 1 / nx, 1 / ny, pg[0], W, pg[2], 0.002, 0.004, bc, storage=storage)
+    o = O.Setup(nx, ny, 1 / nx, 1 / ny, po[0], Wo, po[2], 0.002, 0.004, bc)
+    f0 = WL.near_equilibrium_state(Wo, ny, nx, amp=0.1, seed=23)
+    g.set_state(f0)
+    g.step(8)
+    fg = g.state()
+    g.close()
+    assert rel_linf(fg, O.t3s3_run(f0, o, 8)) <= TOL
