@@ -466,11 +466,18 @@ int adjoint_core(dugks_ctx* c) {
   const int G = c->groups;
   const size_t nvN = (size_t)p.nv * p.N;
   const double tau = p.tau, dt = p.dt;
-  // forward recomputation
+  // forward recomputation: g1 and the moments of f^, f~(t') (the fused
+  // stage-1 kernel for D2Q9 sets, else the face and update kernels), g2 and
+  // the moments of f~(t')
   CK(launch_cell(p, G, 1, c->fhat, c->a_g1, c->a_mom1, c->s1.a, c->s1.b, s));
-  CK(launch_face(p, G, 0, c->a_g1, c->a_mom1, c->fbx, c->s1, s));
-  CK(launch_face(p, G, 1, c->a_g1, c->a_mom1, c->fby, c->s1, s));
-  CK(launch_update1(p, c->fhat, c->a_g1, c->fbx, c->fby, c->a_ftp, c->a_acc, s));
+  if (c->d2q9) {
+    CK(launch_d2q9_ftp(c->dp, c->ds1, c->a_g1, c->fhat, c->a_mom1, c->a_g2, c->a_ftp,
+                       c->a_mom2, s));
+  } else {
+    CK(launch_face(p, G, 0, c->a_g1, c->a_mom1, c->fbx, c->s1, s));
+    CK(launch_face(p, G, 1, c->a_g1, c->a_mom1, c->fby, c->s1, s));
+    CK(launch_update1(p, c->fhat, c->a_g1, c->fbx, c->fby, c->a_ftp, c->a_acc, s));
+  }
   CK(launch_cell(p, G, 2, c->a_ftp, c->a_g2, c->a_mom2, c->s2.a, c->s2.b, s));
   // tau-derivatives of the coefficients
   const double c34 = 0.75 * c->c_om;

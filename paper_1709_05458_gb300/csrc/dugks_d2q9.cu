@@ -290,7 +290,9 @@ __device__ __forceinline__ void d2q9_cell_dw(const D2Q9ParamsDW& P, const dw (&L
 // ---------------------------------------------------------------- kernel
 // One 32 x P.ty tile of one stage (all phases); every thread of the block
 // takes part (blockDim.x >= 32 (P.ty + 1)).
-template <int STAGE, bool WS, typename A>
+// FT (stage 1, FP64): out1 receives f~(t') itself instead of X (the
+// adjoint's recomputation of the forward intermediates).
+template <int STAGE, bool WS, typename A, bool FT = false>
 __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
                                           const typename Arith<A>::Stg& S,
                                           const double* __restrict__ gin,
@@ -503,7 +505,7 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
         const A xk = fma(cft, ft[k], fma(wk<WS, k>(P, rc, rcw), Pk[k], X[k]));
         const A g2 = fma(wk<WS, k>(P, rb, rbw), Pk[k], P.a2 * ft[k]);
         out0[(size_t)k * N + cell] = R::store(g2);
-        out1[(size_t)k * N + cell] = R::store(xk);
+        out1[(size_t)k * N + cell] = R::store(FT ? ft[k] : xk);
       });
       rho_out[cell] = R::store(rho);
     } else {
@@ -539,6 +541,17 @@ k_d2q9(typename Arith<A>::Par P, typename Arith<A>::Stg S, const double* __restr
   static_assert(sizeof(A) == sizeof(double), "tile buffers are sized for 8-byte values");
   d2q9_tile<STAGE, WS, A>(P, S, gin, own, rho_in, out0, out1, rho_out, blockIdx.x * TX,
                           blockIdx.y * P.ty, reinterpret_cast<A*>(smem));
+}
+
+// Stage 1 with f~(t') as the second output (see d2q9_tile's FT).
+template <bool WS>
+__global__ void __launch_bounds__(kMaxThreads)
+k_d2q9_ftp(D2Q9Params P, D2Q9Stage S, const double* __restrict__ gin,
+           const double* __restrict__ own, const double* __restrict__ rho_in,
+           double* __restrict__ out0, double* __restrict__ out1, double* __restrict__ rho_out) {
+  extern __shared__ double smem[];
+  d2q9_tile<1, WS, double, true>(P, S, gin, own, rho_in, out0, out1, rho_out, blockIdx.x * TX,
+                                 blockIdx.y * P.ty, smem);
 }
 
 // Cell pass of the fused path outside a step, one thread per cell: the
@@ -640,6 +653,10 @@ cudaError_t d2q9_prepare(int ty) {
   cudaError_t e = allow_smem<double>(bytes);
   if (e == cudaSuccess) e = allow_smem<dw>((int)d2q9_smem_bytes(Arith<dw>::kMaxTY));
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_d2q9_ftp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_d2q9_ftp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_d2q9_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_d2q9_batch<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
@@ -703,6 +720,20 @@ void split_all(const double (&x)[N][M][L], dw (&d)[N][M][L]) {
   for (size_t i = 0; i < N; ++i) split_all(x[i], d[i]);
 }
 }  // namespace
+
+cudaError_t launch_d2q9_ftp(const D2Q9Params& p, const D2Q9Stage& s, const double* g1,
+                            const double* fhat, const double* rho_fhat, double* g2, double* ftp,
+                            double* rho_ftp, cudaStream_t st) {
+  if (p.ty < 1 || p.ty > kMaxTY) return cudaErrorInvalidValue;
+  const dim3 grid((p.nx + TX - 1) / TX, (p.ny + p.ty - 1) / p.ty);
+  const int threads = TX * (p.ty + 1);
+  const size_t bytes = d2q9_smem_bytes(p.ty);
+  if (p.wsym)
+    k_d2q9_ftp<true><<<grid, threads, bytes, st>>>(p, s, g1, fhat, rho_fhat, g2, ftp, rho_ftp);
+  else
+    k_d2q9_ftp<false><<<grid, threads, bytes, st>>>(p, s, g1, fhat, rho_fhat, g2, ftp, rho_ftp);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_d2q9_cell(const D2Q9Params& p, bool write_g, const double* fhat, double* g1,
                              double* mom, cudaStream_t st) {

@@ -193,6 +193,10 @@ cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage
                               double* out0, double* out1, double* rho_out, cudaStream_t st);
 size_t d2q9_smem_bytes(int ty);
 cudaError_t d2q9_prepare(int ty);
+// stage 1 of the fused FP64 path writing g2 and f~(t') (the adjoint's recomputation)
+cudaError_t launch_d2q9_ftp(const D2Q9Params& p, const D2Q9Stage& s, const double* g1,
+                            const double* fhat, const double* rho_fhat, double* g2, double* ftp,
+                            double* rho_ftp, cudaStream_t st);
 // moments of f^ into mom[3][N] (rho, ux, uy) and, with write_g, g1 (FP64 fused path)
 cudaError_t launch_d2q9_cell(const D2Q9Params& p, bool write_g, const double* fhat, double* g1,
                              double* mom, cudaStream_t st);
