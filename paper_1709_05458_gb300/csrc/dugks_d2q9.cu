@@ -94,18 +94,33 @@ template <> struct Arith<dw> {
   static __device__ __forceinline__ dw dot_value(const dw_acc& a) { return dw_acc_value(a); }
 };
 
-// dot product of a weight block with the smem stencil, compile-time extents
+// dot product of a weight block with the smem stencil, compile-time extents.
+// The double-word form keeps the rows after the first in a loop: its
+// stage code is bound by instruction fetch, and a rolled row is a third of
+// the code for a few loop instructions.
 template <typename A, int R0, int R1, int Q0, int Q1, int NCOL>
 __device__ __forceinline__ A wdot(const A* __restrict__ s, const A* w) {
   typename Arith<A>::Acc acc;
-#pragma unroll
-  for (int r = R0; r <= R1; ++r)
+  if constexpr (std::is_same<A, dw>::value) {
 #pragma unroll
     for (int q = Q0; q <= Q1; ++q) {
-      const A v = s[r * SW + q];
-      if (r == R0 && q == Q0) Arith<A>::dot_first(acc, w[r * NCOL + q], v);
-      else Arith<A>::dot_add(acc, w[r * NCOL + q], v);
+      if (q == Q0) Arith<A>::dot_first(acc, w[R0 * NCOL + q], s[R0 * SW + q]);
+      else Arith<A>::dot_add(acc, w[R0 * NCOL + q], s[R0 * SW + q]);
     }
+#pragma unroll 1
+    for (int r = R0 + 1; r <= R1; ++r)
+#pragma unroll
+      for (int q = Q0; q <= Q1; ++q) Arith<A>::dot_add(acc, w[r * NCOL + q], s[r * SW + q]);
+  } else {
+#pragma unroll
+    for (int r = R0; r <= R1; ++r)
+#pragma unroll
+      for (int q = Q0; q <= Q1; ++q) {
+        const A v = s[r * SW + q];
+        if (r == R0 && q == Q0) Arith<A>::dot_first(acc, w[r * NCOL + q], v);
+        else Arith<A>::dot_add(acc, w[r * NCOL + q], v);
+      }
+  }
   return Arith<A>::dot_value(acc);
 }
 
@@ -532,9 +547,12 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
   }
 }
 
+// the stage tables stay in parameter space when the double-word stencil
+// indexes its rows at run time
 template <int STAGE, bool WS, typename A>
 __global__ void __launch_bounds__(Arith<A>::kThreads, Arith<A>::kMinBlocks)
-k_d2q9(typename Arith<A>::Par P, typename Arith<A>::Stg S, const double* __restrict__ gin,
+k_d2q9(typename Arith<A>::Par P, const __grid_constant__ typename Arith<A>::Stg S,
+       const double* __restrict__ gin,
        const double* __restrict__ own, const double* __restrict__ rho_in,
        double* __restrict__ out0, double* __restrict__ out1, double* __restrict__ rho_out) {
   extern __shared__ double smem[];
