@@ -301,7 +301,10 @@ int one_step_d2q9(dugks_ctx* c) {
   cudaStream_t s = c->stream;
   const size_t N = c->p.N;
   if (!c->g1_valid) {
-    TRY(launch(c, K_D2Q9_PROLOGUE, [&] { return launch_d2q9_cell(c->dp, true, c->fhat, c->g, c->mom, s); }));
+    TRY(launch(c, K_D2Q9_PROLOGUE, [&] {
+      return c->dwa ? launch_d2q9dw_cell(c->dwp, c->fhat, c->g, c->mom, s)
+                    : launch_d2q9_cell(c->dp, true, c->fhat, c->g, c->mom, s);
+    }));
     c->g1_valid = true;
   }
   if (c->dwa) {
@@ -424,7 +427,8 @@ int ensure_g1(dugks_ctx* c) {
     }));
   else
     TRY(launch(c, K_D2Q9_PROLOGUE, [&] {
-      return launch_d2q9_cell(c->dp, true, c->fhat, c->g, c->mom, s);
+      return c->dwa ? launch_d2q9dw_cell(c->dwp, c->fhat, c->g, c->mom, s)
+                    : launch_d2q9_cell(c->dp, true, c->fhat, c->g, c->mom, s);
     }));
   c->g1_valid = true;
   return DUGKS_OK;

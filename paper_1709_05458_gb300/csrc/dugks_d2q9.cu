@@ -561,6 +561,38 @@ k_d2q9(typename Arith<A>::Par P, const __grid_constant__ typename Arith<A>::Stg 
                           blockIdx.y * P.ty, reinterpret_cast<A*>(smem));
 }
 
+// The g1 prologue of the double-word form, in the arithmetic and order of
+// its stage-2 tail (d2q9_cell_dw), so that a run restarted from its state
+// continues as it would have: g1 = f + b1 (feq - f), and the moments.
+template <bool WS>
+__global__ void __launch_bounds__(256)
+k_d2q9dw_cell(D2Q9ParamsDW P, const double* __restrict__ fhat, double* __restrict__ g1,
+              double* __restrict__ mom) {
+  using R = Arith<dw>;
+  const int N = P.N;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N) return;
+  dw f[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) f[k] = R::load(fhat + (size_t)k * N + cell);
+  dw rho, sx, sy;
+  d2q9_sums(f, rho, sx, sy);
+  dw utx, uty;
+  d2q9_ut(rho, sx, sy, P, utx, uty);
+  dw Pk[9], rw[3];
+  d2q9_poly(utx, uty, P, Pk);
+  wclasses<WS>(P, rho, rw);
+  for9([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    const dw d = wk<WS, k>(P, rho, rw) * Pk[k] - f[k];
+    g1[(size_t)k * N + cell] = R::store(fma(P.b1, d, f[k]));
+  });
+  const dw cr = P.c * R::rcp(rho);
+  mom[cell] = R::store(rho);
+  mom[N + cell] = R::store(sx * cr);
+  mom[2 * N + cell] = R::store(sy * cr);
+}
+
 // Stage 1 with f~(t') as the second output (see d2q9_tile's FT).
 template <bool WS>
 __global__ void __launch_bounds__(kMaxThreads)
@@ -750,6 +782,14 @@ cudaError_t launch_d2q9_ftp(const D2Q9Params& p, const D2Q9Stage& s, const doubl
     k_d2q9_ftp<true><<<grid, threads, bytes, st>>>(p, s, g1, fhat, rho_fhat, g2, ftp, rho_ftp);
   else
     k_d2q9_ftp<false><<<grid, threads, bytes, st>>>(p, s, g1, fhat, rho_fhat, g2, ftp, rho_ftp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_d2q9dw_cell(const D2Q9ParamsDW& p, const double* fhat, double* g1,
+                               double* mom, cudaStream_t st) {
+  const int blocks = (p.N + 255) / 256;
+  if (p.wsym) k_d2q9dw_cell<true><<<blocks, 256, 0, st>>>(p, fhat, g1, mom);
+  else k_d2q9dw_cell<false><<<blocks, 256, 0, st>>>(p, fhat, g1, mom);
   return cudaGetLastError();
 }
 

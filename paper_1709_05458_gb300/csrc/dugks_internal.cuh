@@ -232,6 +232,9 @@ int d2q9_max_ty(bool dwa);
 int d2q9_blocks_per_sm(bool dwa);
 void d2q9_params_to_dw(const D2Q9Params& p, D2Q9ParamsDW& d);
 void d2q9_stage_to_dw(const D2Q9Stage& s, D2Q9StageDW& d);
+// the g1 prologue and moments of the double-word form (its stage-2 arithmetic)
+cudaError_t launch_d2q9dw_cell(const D2Q9ParamsDW& p, const double* fhat, double* g1,
+                               double* mom, cudaStream_t st);
 cudaError_t launch_d2q9dw_stage(const D2Q9ParamsDW& p, const D2Q9StageDW& s, int stage,
                                 const double* gin, const double* own, const double* rho_in,
                                 double* out0, double* out1, double* rho_out, cudaStream_t st);

@@ -182,3 +182,22 @@ def test_unequal_weights_take_the_general_kernels(cuda, storage):
     fg = g.state()
     g.close()
     assert rel_linf(fg, O.t3s3_run(f0, o, 8)) <= TOL
+
+
+def test_autotune_keeps_results_identical(cuda):
+    """dugks_autotune on a double-word context picks a height in 4..12 and
+    later steps equal those of an untuned context bit for bit (the tile
+    height changes no arithmetic)."""
+    c = WL.config("cavity128")
+    runs = []
+    for tune in (False, True):
+        g, _ = pair(128, 128, c["RT"], c["tau"], 0.5 * c["dt"], c["bc"])
+        g.set_equilibrium(*WL.rest_fields(128, 128))
+        g.step(3)
+        if tune:
+            ty = P.dugks_autotune(g.ctx, trials=1)
+            assert 4 <= ty <= 12
+        g.step(5)
+        runs.append(g.state())
+        g.close()
+    np.testing.assert_array_equal(runs[0], runs[1])
