@@ -325,6 +325,10 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
   const int nx = P.nx, ny = P.ny, N = P.N;
   const int tid = threadIdx.x, nthr = blockDim.x;
 
+  // launched as a programmatic dependent of the previous stage kernel: wait
+  // for it to complete (no-op otherwise) before reading its outputs
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+
   // phase 0: g tile with a 2-cell halo (wrap or wall ghosts)
   for (int p = tid; p < SH * SW; p += nthr) {
     const int rr = p / SW, cc = p - rr * SW;
@@ -348,6 +352,9 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
     }
   }
   __syncthreads();
+  // this block's inputs are in shared memory: the next stage kernel may
+  // begin launching (it waits for this grid's completion before reading)
+  asm volatile("griddepcontrol.launch_dependents;");
 
   // phase 1: x-faces fi = x0 + fc, fc = 0..TX, rows r < TY
   for (int t = tid; t < TY * (TX + 1); t += nthr) {
@@ -738,18 +745,23 @@ cudaError_t launch_stage(const typename Arith<A>::Par& p, const typename Arith<A
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + p.ty - 1) / p.ty);
   const int threads = TX * (p.ty + 1);
   const size_t bytes = d2q9_smem_bytes(p.ty);
-  if (p.wsym) {
-    if (stage == 1)
-      k_d2q9<1, true, A><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
-    else
-      k_d2q9<2, true, A><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
-  } else {
-    if (stage == 1)
-      k_d2q9<1, false, A><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
-    else
-      k_d2q9<2, false, A><<<grid, threads, bytes, st>>>(p, s, gin, own, rho_in, out0, out1, rho_out);
-  }
-  return cudaGetLastError();
+  // programmatic dependent launch: this grid may be scheduled while the
+  // previous kernel on the stream finishes; the tile code waits for that
+  // kernel's completion before its first global read
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const auto kern = p.wsym ? (stage == 1 ? k_d2q9<1, true, A> : k_d2q9<2, true, A>)
+                           : (stage == 1 ? k_d2q9<1, false, A> : k_d2q9<2, false, A>);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, p, s, gin, own, rho_in, out0, out1, rho_out);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // x = h + l with h = x rounded to FP32 and l the FP32 rounding of x - h
