@@ -124,11 +124,26 @@ __device__ __forceinline__ void acc_addprod(Acc<float>& a, float ah, float al, f
 __device__ __forceinline__ double acc_value(const Acc<float>& a) {
   return to_d(a.hi) + to_d(a.lo);
 }
+// a += b and a += (xh + xl) b for an accumulated pair b
+__device__ __forceinline__ void acc_add_acc(Acc<float>& a, const Acc<float>& b) {
+  acc_add(a, b.hi);
+  a.lo = __fadd_rn(a.lo, b.lo);
+}
+__device__ __forceinline__ void acc_addprod_acc(Acc<float>& a, float xh, float xl,
+                                                const Acc<float>& b) {
+  acc_addprod(a, xh, xl, b.hi);
+  a.lo = __fmaf_rn(xh, b.lo, a.lo);
+}
 __device__ __forceinline__ void acc_add(Acc<double>& a, double x) { a.s += x; }
 __device__ __forceinline__ void acc_addprod(Acc<double>& a, double ah, double, double x) {
   a.s = fma(ah, x, a.s);
 }
 __device__ __forceinline__ double acc_value(const Acc<double>& a) { return a.s; }
+__device__ __forceinline__ void acc_add_acc(Acc<double>& a, const Acc<double>& b) { a.s += b.s; }
+__device__ __forceinline__ void acc_addprod_acc(Acc<double>& a, double xh, double,
+                                                const Acc<double>& b) {
+  a.s = fma(xh, b.s, a.s);
+}
 
 // ---- equilibrium ----
 // assembly parameters of one cell or face
@@ -264,9 +279,12 @@ k_gcell1(GDevStep s, const T* __restrict__ src, typename Prec<T>::C a, typename 
 // Large velocity sets, three kernels.  (1) Partial moments: 32 cells per
 // block, 8 warps over a velocity chunk (eight loads in flight per thread),
 // per-thread partials combined in FP64, into part[chunk][3][N].
-template <typename T>
+// TG (tensor grid, chunks of whole rows of n velocities sharing xi_x): per
+// row a compensated sum S of the terms and their xi_y-weighted sum, then
+// rho += S and rho u_x += xi_x S once per row.
+template <typename T, bool TG>
 __global__ void __launch_bounds__(kThreads)
-k_gmom(GDevStep s, const T* __restrict__ src, int kchunk) {
+k_gmom(GDevStep s, const T* __restrict__ src, int kchunk, int n) {
   using C = typename Prec<T>::C;
   using V4 = typename Prec<T>::V4;
   constexpr int TX = 32, G = kThreads / TX, U = 8;
@@ -278,7 +296,29 @@ k_gmom(GDevStep s, const T* __restrict__ src, int kchunk) {
   const bool valid = cell < p.N;
   const int k0 = blockIdx.y * kchunk, k1 = min(p.nv, k0 + kchunk);
   Acc<C> s0{}, s1{}, s2{};
-  if (valid) {
+  if (valid && TG) {
+    for (int row = k0; row < k1; row += n) {
+      Acc<C> sr{};
+      for (int k = row + ty; k < row + n; k += U * G) {
+        T d[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (k + u * G < row + n) d[u] = ldr(src + (size_t)(k + u * G) * p.N + cell);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (k + u * G < row + n) {
+            const V4 xq = ld4(vq + k + u * G);
+            const C du = tof(d[u]);
+            acc_add(sr, du);
+            acc_addprod(s2, xq.z, xq.w, du);
+          }
+        }
+      }
+      const V4 xr = ld4(vq + row);                   // the row's xi_x (hi, lo)
+      acc_add_acc(s0, sr);
+      acc_addprod_acc(s1, xr.x, xr.y, sr);
+    }
+  } else if (valid) {
     int k = k0 + ty;
     for (; k + (U - 1) * G < k1; k += U * G) {
       T d[U];
@@ -1009,7 +1049,16 @@ cudaError_t cell_t(const GDevStep& s, const void* src, const StageCoef& c, cudaS
                                                                     (C)c.b);
   } else {
     const int kchunk = (p.nv + s.mch - 1) / s.mch;
-    k_gmom<T><<<dim3((p.N + 31) / 32, s.mch), kThreads, 0, st>>>(s, (const T*)src, kchunk);
+    const dim3 mgrid((p.N + 31) / 32, s.mch);
+    // tensor grid with chunks of whole rows (n = sqrt(nv), a multiple of 16),
+    // FP64 storage: one FP64 operation per cell-velocity fewer on the FP64
+    // pipe that bounds it (the FP32 / BF16 forms measured no gain, BF16 a loss)
+    int n = 0;
+    while ((long)(n + 1) * (n + 1) <= p.nv) ++n;
+    if (sizeof(T) == 8 && s.tgrid && kchunk % n == 0)
+      k_gmom<T, true><<<mgrid, kThreads, 0, st>>>(s, (const T*)src, kchunk, n);
+    else
+      k_gmom<T, false><<<mgrid, kThreads, 0, st>>>(s, (const T*)src, kchunk, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_gmomfin<C><<<(p.N + kThreads - 1) / kThreads, kThreads, 0, st>>>(s, s.mch);
