@@ -184,6 +184,18 @@ const char* dugks_kernel_name(int id);
 int dugks_autotune(dugks_ctx* ctx, int trials, int* ty_out);
 
 /*
+ * dugks_set_tile_height -- fix the tile height (rows of cells per block) of
+ * the fused D2Q9 kernels, e.g. one that dugks_autotune chose on an earlier
+ * run of the same problem, without timing anything.  ty must lie in 4..16
+ * (4..12 for DUGKS_F64_DW), else DUGKS_EINVAL and the height is unchanged;
+ * other velocity sets: DUGKS_ENOTIMPL.  Results of later steps are identical
+ * for every height.  A batch reads the height when it is created.
+ * dugks_tile_height writes the current height to *ty_out.
+ */
+int dugks_set_tile_height(dugks_ctx* ctx, int ty);
+int dugks_tile_height(dugks_ctx* ctx, int* ty_out);
+
+/*
  * Batched stepping of many independent problems (contexts) in one CUDA
  * graph.  All FP64 D2Q9 contexts of the batch advance together through one
  * persistent launch per stage whose blocks take (instance, tile) work items

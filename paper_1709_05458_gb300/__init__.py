@@ -32,7 +32,8 @@ EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_
            "dugks_step", "dugks_moments", "dugks_check", "dugks_synchronize",
            "dugks_profile", "dugks_profile_read", "dugks_kernel_name", "dugks_destroy",
            "dugks_last_error", "dugks_step_static", "dugks_adjoint_step", "dugks_adjoint_run",
-           "dugks_adjoint_equilibrium", "dugks_autotune", "dugks_batch_create",
+           "dugks_adjoint_equilibrium", "dugks_autotune", "dugks_set_tile_height",
+           "dugks_tile_height", "dugks_batch_create",
            "dugks_batch_step", "dugks_batch_destroy", "dugks_set_scheme")
 
 
@@ -86,6 +87,8 @@ def load(path: str = LIB_PATH):
         "dugks_adjoint_run": (I, [P, P, I, I, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double), I]),
         "dugks_adjoint_equilibrium": (I, [P, P, P, P, P, P, P, P, I]),
         "dugks_autotune": (I, [P, I, C.POINTER(C.c_int)]),
+        "dugks_set_tile_height": (I, [P, I]),
+        "dugks_tile_height": (I, [P, C.POINTER(C.c_int)]),
         "dugks_batch_create": (I, [C.POINTER(P), I, C.POINTER(P)]),
         "dugks_batch_step": (I, [P, I]),
         "dugks_batch_destroy": (I, [P]),
@@ -230,6 +233,17 @@ def dugks_autotune(ctx, trials=3):
     returns the chosen height."""
     ty = C.c_int(0)
     _check(load().dugks_autotune(ctx, int(trials), C.byref(ty)))
+    return ty.value
+
+
+def dugks_set_tile_height(ctx, ty):
+    """Fix the fused D2Q9 kernels' tile height (4..16; 4..12 double-word)."""
+    return _check(load().dugks_set_tile_height(ctx, int(ty)))
+
+
+def dugks_tile_height(ctx):
+    ty = C.c_int(0)
+    _check(load().dugks_tile_height(ctx, C.byref(ty)))
     return ty.value
 
 

@@ -1214,6 +1214,22 @@ int dugks_autotune(dugks_ctx* c, int trials, int* ty_out) {
   return dugks_synchronize(c);
 }
 
+int dugks_set_tile_height(dugks_ctx* c, int ty) {
+  if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  if (!c->d2q9) return fail(DUGKS_ENOTIMPL, "the tile height applies to the D2Q9 kernels");
+  if (ty < 4 || ty > d2q9_max_ty(c->dwa)) return fail(DUGKS_EINVAL, "tile height out of range");
+  c->dp.ty = ty;
+  c->dwp.ty = ty;
+  return DUGKS_OK;
+}
+
+int dugks_tile_height(dugks_ctx* c, int* ty_out) {
+  if (!c || !ty_out) return fail(DUGKS_EINVAL, "NULL argument");
+  if (!c->d2q9) return fail(DUGKS_ENOTIMPL, "the tile height applies to the D2Q9 kernels");
+  *ty_out = c->dp.ty;
+  return DUGKS_OK;
+}
+
 int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
   if (!out) return fail(DUGKS_EINVAL, "out is NULL");
   *out = nullptr;

@@ -28,6 +28,8 @@
 // FP64 kernels) or dw, double-word FP32 pairs (dugks_dw.cuh), which keep FP64
 // arrays but run every operation on the FP32 pipes -- GB300 issues those at
 // 64 times its FP64 rate -- with a unit roundoff of 2^-48 instead of 2^-53.
+#include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 #include "dugks_dw.cuh"
@@ -702,13 +704,32 @@ cudaError_t allow_smem(int bytes) {
   return e;
 }
 
+// Shared memory per SM, the part reserved per block and the opt-in maximum
+// per block of the current device.
+struct SmemLimits {
+  int per_sm = 0, reserved = 0, optin = 0, sms = 0;
+};
+SmemLimits smem_limits() {
+  SmemLimits l;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l.reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return SmemLimits{};
+  return l;
+}
+
 cudaError_t d2q9_prepare(int ty) {
-  // the attribute is per function: always allow the largest tile so that
-  // contexts with different tile heights can coexist
+  // the attribute is per function: allow the largest tile so that contexts
+  // with different tile heights can coexist, and for the stage kernels the
+  // device maximum, which the one-wave padding of stage_smem may use
   (void)ty;
   const int bytes = (int)d2q9_smem_bytes(kMaxTY);
-  cudaError_t e = allow_smem<double>(bytes);
-  if (e == cudaSuccess) e = allow_smem<dw>((int)d2q9_smem_bytes(Arith<dw>::kMaxTY));
+  const SmemLimits l = smem_limits();
+  cudaError_t e = allow_smem<double>(std::max(bytes, l.optin));
+  if (e == cudaSuccess) e = allow_smem<dw>(std::max((int)d2q9_smem_bytes(Arith<dw>::kMaxTY), l.optin));
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_d2q9_ftp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -737,6 +758,65 @@ int d2q9_batch_blocks_per_sm(int max_ty) {
 }
 
 namespace {
+// Dynamic shared memory of a stage launch.  A grid of at most one wave
+// (tiles <= SMs x resident blocks per SM) is not spread evenly by the block
+// scheduler: some SMs receive as many tiles as fit (three 32 x 7 tiles of the
+// double-word kernels at 256^2) while others receive one, and the wave lasts
+// as long as the fullest SM.  Padding the request so that no more than
+// ceil(tiles / SMs) blocks fit on an SM spreads the tiles evenly (measured
+// at 256^2: double-word 103.2 -> 97.2 us per step at ty = 7; FP64 at its
+// chosen height, one block per SM, unchanged).  The occupancy of each
+// (kernel, tile height, cap) is computed once.
+template <typename A>
+size_t stage_smem(int stage, bool wsym, int ty, long tiles) {
+  const size_t need = d2q9_smem_bytes(ty);
+  struct Entry {
+    int occ = -1, cap = -1;
+    size_t bytes = 0;
+  };
+  static std::mutex mu;
+  static Entry cache[2][2][kMaxTY + 1];
+  static SmemLimits lim;
+  static int lim_dev = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return need;
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev != lim_dev) {                       // (re)read the limits of this device
+    lim = smem_limits();
+    lim_dev = dev;
+    for (auto& a : cache)
+      for (auto& b : a)
+        for (auto& c : b) c = Entry{};
+  }
+  if (lim.sms <= 0 || ty < 1 || ty > kMaxTY) return need;
+  const auto kern = wsym ? (stage == 1 ? k_d2q9<1, true, A> : k_d2q9<2, true, A>)
+                         : (stage == 1 ? k_d2q9<1, false, A> : k_d2q9<2, false, A>);
+  const int threads = TX * (ty + 1);
+  Entry& en = cache[stage - 1][wsym ? 1 : 0][ty];
+  if (en.occ < 0 &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&en.occ, kern, threads, need) != cudaSuccess) {
+    en.occ = 0;
+    cudaGetLastError();
+  }
+  const long cap = (tiles + lim.sms - 1) / lim.sms;
+  if (en.occ <= 0 || cap >= en.occ) return need;
+  if (en.cap != cap) {
+    // (cap + 1) (bytes + reserved) > per_sm >= cap (bytes + reserved)
+    size_t pad = (size_t)(lim.per_sm / (cap + 1) - lim.reserved + 16);
+    pad = std::max(need, (pad + 15) & ~(size_t)15);
+    int got = 0;
+    if (pad > (size_t)lim.optin ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, kern, threads, pad) != cudaSuccess ||
+        got != cap) {
+      cudaGetLastError();
+      pad = need;
+    }
+    en.cap = (int)cap;
+    en.bytes = pad;
+  }
+  return en.bytes;
+}
+
 template <typename A>
 cudaError_t launch_stage(const typename Arith<A>::Par& p, const typename Arith<A>::Stg& s,
                          int stage, const double* gin, const double* own, const double* rho_in,
@@ -744,7 +824,7 @@ cudaError_t launch_stage(const typename Arith<A>::Par& p, const typename Arith<A
   if (p.ty < 1 || p.ty > Arith<A>::kMaxTY) return cudaErrorInvalidValue;
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + p.ty - 1) / p.ty);
   const int threads = TX * (p.ty + 1);
-  const size_t bytes = d2q9_smem_bytes(p.ty);
+  const size_t bytes = stage_smem<A>(stage, p.wsym, p.ty, (long)grid.x * grid.y);
   // programmatic dependent launch: this grid may be scheduled while the
   // previous kernel on the stream finishes; the tile code waits for that
   // kernel's completion before its first global read

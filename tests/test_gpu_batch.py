@@ -77,6 +77,30 @@ def test_autotune_keeps_state_and_results(cuda):
     np.testing.assert_array_equal(a.state(), ref.state())
 
 
+@pytest.mark.parametrize("storage", [P.FP64, P.F64_DW], ids=["fp64", "dw"])
+def test_fixed_tile_heights_give_identical_results(cuda, storage):
+    """Every height dugks_set_tile_height accepts gives the same state bit for
+    bit (a ragged bounce-back cavity, 70 x 45, 6 steps); out-of-range
+    heights are refused and leave the height unchanged."""
+    sp = specs()[1][:6] + (storage,)
+    runs = {}
+    top = 16 if storage == P.FP64 else 12
+    for ty in (4, 5, 7, 11, top):
+        a, _ = make(sp, None)
+        P.dugks_set_tile_height(a.ctx, ty)
+        assert P.dugks_tile_height(a.ctx) == ty
+        a.step(6)
+        runs[ty] = a.state()
+        for bad in (3, top + 1):
+            with pytest.raises(P.DugksError) as e:
+                P.dugks_set_tile_height(a.ctx, bad)
+            assert e.value.code == P.DUGKS_EINVAL
+        assert P.dugks_tile_height(a.ctx) == ty
+        a.close()
+    for ty, f in runs.items():
+        np.testing.assert_array_equal(f, runs[4])
+
+
 def test_batch_needs_a_stream(cuda):
     xi, W, RT = PV.d2q9(1 / 3)
     s = P.Solver(8, 8, 1 / 8, 1 / 8, xi, W, RT, 0.01, 0.01, [(P.PERIODIC, 0, 0)] * 4)
