@@ -65,7 +65,9 @@ template <> struct Arith<double> {
   static __device__ __forceinline__ double load(const double* p) { return __ldg(p); }
   static __device__ __forceinline__ double store(double x) { return x; }
   static __device__ __forceinline__ double cst(float x) { return (double)x; }
-  static __device__ __forceinline__ double coef(double x) { return x; }
+  // ghost extrapolation coefficients (small integers, exact in FP32),
+  // converted on the integer pipe
+  static __device__ __forceinline__ double coef(float x) { return f2d_bits(x); }
   static __device__ __forceinline__ double rcp(double x) { return rcp_fast(x); }
   static __device__ __forceinline__ double diffuse(double num, const Par& P, int side) {
     return num * P.c / P.ds_den[side];
@@ -86,7 +88,7 @@ template <> struct Arith<dw> {
   static __device__ __forceinline__ double store(dw x) { return dw_to_d(x); }
   static __device__ __forceinline__ dw cst(float x) { return dw{x, 0.0f}; }
   // ghost extrapolation coefficients (small integers, exact in FP32)
-  static __device__ __forceinline__ dw coef(double x) { return dw{d2f_bits(x), 0.0f}; }
+  static __device__ __forceinline__ dw coef(float x) { return dw{x, 0.0f}; }
   static __device__ __forceinline__ dw rcp(dw x) { return dw_rcp(x); }
   static __device__ __forceinline__ dw diffuse(dw num, const Par& P, int side) {
     return num * P.c_ds[side];
@@ -235,21 +237,33 @@ __device__ __forceinline__ void face_recover(A (&fb)[9], const typename Arith<A>
   });
 }
 
-// Resolve a (possibly ghost) cell to a combination of interior cells:
-// periodic wrap, or the quadratic extrapolation along the wall normal
-// (g_-1 = 3g_0 - 3g_1 + g_2, g_-2 = 6g_0 - 8g_1 + 3g_2), x then y.
-__device__ __forceinline__ int resolve1(int x, int n, bool per, int (&i)[3], double (&c)[3]) {
-  if (x >= 0 && x < n) { i[0] = x; c[0] = 1.0; return 1; }
-  if (per) { i[0] = ((x % n) + n) % n; c[0] = 1.0; return 1; }
-  if (x == -1 || x == n) {
-    const int b = x < 0 ? 0 : n - 1, s = x < 0 ? 1 : -1;
-    i[0] = b; i[1] = b + s; i[2] = b + 2 * s; c[0] = 3.0; c[1] = -3.0; c[2] = 1.0; return 3;
-  }
-  if (x == -2 || x == n + 1) {
-    const int b = x < 0 ? 0 : n - 1, s = x < 0 ? 1 : -1;
-    i[0] = b; i[1] = b + s; i[2] = b + 2 * s; c[0] = 6.0; c[1] = -8.0; c[2] = 3.0; return 3;
-  }
-  return 0;   // beyond the ghost band: never read by a computed face
+// A staged coordinate x of a tile with its 2-cell halo: >= 0 the cell it
+// holds (in the domain, or its periodic image); -1 a wall ghost; -2 beyond
+// the ghost band (never read by a computed face).
+__device__ __forceinline__ int stage_coord(int x, int n, bool per) {
+  if (x >= 0 && x < n) return x;
+  if (per) return ((x % n) + n) % n;
+  return (x >= -2 && x <= n + 1) ? -1 : -2;
+}
+
+// Taps of a staged coordinate for the ghost fill, as positions in the
+// staged tile (t0 = tile origin, s = this position): itself with weight 1
+// when it holds a cell, else the three cells next to the wall with the
+// weights of the quadratic extrapolation along the wall normal
+// (g_-1 = 3g_0 - 3g_1 + g_2, g_-2 = 6g_0 - 8g_1 + 3g_2).  Walls need three
+// cells across, and a tile holding a ghost holds those three cells too.
+// The weights and their products are exact in FP32.
+__device__ __forceinline__ int ghost_taps(int x, int ix, int n, int t0, int s, int (&pos)[3],
+                                          float (&c)[3]) {
+  if (ix >= 0) { pos[0] = s; c[0] = 1.0f; return 1; }
+  const int b = x < 0 ? 0 : n - 1, d = x < 0 ? 1 : -1;
+  const bool near = x == -1 || x == n;
+  c[0] = near ? 3.0f : 6.0f;
+  c[1] = near ? -3.0f : -8.0f;
+  c[2] = near ? 1.0f : 3.0f;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) pos[m] = b + m * d - t0 + HALO;
+  return 3;
 }
 
 // Cell part of a stage in double-word arithmetic.  The maps are written so
@@ -331,26 +345,60 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
   // for it to complete (no-op otherwise) before reading its outputs
   asm volatile("griddepcontrol.wait;" ::: "memory");
 
-  // phase 0: g tile with a 2-cell halo (wrap or wall ghosts)
+  // phase 0: g tile with a 2-cell halo.  (a) Cells of the domain and their
+  // periodic images from global memory (beyond the ghost band: zero);
+  // (b) wall ghosts, extrapolated from the cells staged in (a), so that no
+  // ghost waits on a chain of global loads (a wall tile otherwise spent
+  // 10 us of a 66 us stage here at 256^2, and the stage waits for it).
   for (int p = tid; p < SH * SW; p += nthr) {
     const int rr = p / SW, cc = p - rr * SW;
-    int ix[3], iy[3];
-    double cx[3], cy[3];
-    const int nxr = resolve1(x0 + cc - HALO, nx, P.px, ix, cx);
-    const int nyr = resolve1(y0 + rr - HALO, ny, P.py, iy, cy);
-    if (nxr == 1 && nyr == 1) {
-      const double* src = gin + iy[0] * nx + ix[0];
+    const int ix = stage_coord(x0 + cc - HALO, nx, P.px);
+    const int iy = stage_coord(y0 + rr - HALO, ny, P.py);
+    if (ix >= 0 && iy >= 0) {
+      const double* src = gin + iy * nx + ix;
 #pragma unroll
       for (int k = 0; k < 9; ++k) sg[(k * SH + rr) * SW + cc] = R::load(src + (size_t)k * N);
-    } else {
+    } else if (ix == -2 || iy == -2) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        A v = R::cst(0.0f);
-        for (int a = 0; a < nyr; ++a)
-          for (int b = 0; b < nxr; ++b)
-            v = fma(R::coef(cy[a] * cx[b]), R::load(gin + (size_t)k * N + iy[a] * nx + ix[b]), v);
-        sg[(k * SH + rr) * SW + cc] = v;
+      for (int k = 0; k < 9; ++k) sg[(k * SH + rr) * SW + cc] = R::cst(0.0f);
+    }
+  }
+  // (b) one (ghost, velocity) pair per thread, so that the FP64 work fills
+  // whole warps: ghost columns (x beyond a wall; every row of the band,
+  // corners included), then ghost rows (y beyond a wall; columns that hold
+  // a cell)
+  const bool gw = !P.px && x0 == 0, gs = !P.py && y0 == 0;
+  const int ce = nx - x0 + HALO, rn = ny - y0 + HALO;    // first east column, north row
+  const int ngc = (gw ? 2 : 0) + (P.px ? 0 : max(0, min(2, SW - ce)));
+  const int ngr = (gs ? 2 : 0) + (P.py ? 0 : max(0, min(2, SH - rn)));
+  if (ngc + ngr > 0) {
+    __syncthreads();
+    const int ncol = ngc * SH * 9;
+    for (int t = tid; t < ncol + ngr * SW * 9; t += nthr) {
+      int rr, cc, k;
+      if (t < ncol) {
+        const int q = t / 9, ci = q / SH;
+        k = t - q * 9;
+        rr = q - ci * SH;
+        cc = (gw && ci < 2) ? ci : ce + ci - (gw ? 2 : 0);
+      } else {
+        const int q = (t - ncol) / 9, ri = q / SW;
+        k = (t - ncol) - q * 9;
+        cc = q - ri * SW;
+        rr = (gs && ri < 2) ? ri : rn + ri - (gs ? 2 : 0);
       }
+      const int x = x0 + cc - HALO, y = y0 + rr - HALO;
+      const int ix = stage_coord(x, nx, P.px), iy = stage_coord(y, ny, P.py);
+      if (ix == -2 || iy == -2 || (t >= ncol && ix < 0)) continue;
+      int pc[3], pr[3];
+      float cx[3], cy[3];
+      const int nxr = ghost_taps(x, ix, nx, x0, cc, pc, cx);
+      const int nyr = ghost_taps(y, iy, ny, y0, rr, pr, cy);
+      A v = R::cst(0.0f);
+      for (int a = 0; a < nyr; ++a)
+        for (int b = 0; b < nxr; ++b)
+          v = fma(R::coef(cy[a] * cx[b]), sg[(k * SH + pr[a]) * SW + pc[b]], v);
+      sg[(k * SH + rr) * SW + cc] = v;
     }
   }
   __syncthreads();
@@ -358,9 +406,25 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
   // begin launching (it waits for this grid's completion before reading)
   asm volatile("griddepcontrol.launch_dependents;");
 
-  // phase 1: x-faces fi = x0 + fc, fc = 0..TX, rows r < TY
+  // phase 1: x-faces fi = x0 + fc, fc = 0..TX, rows r < TY.  Wall faces
+  // (fi = 0 or nx; more work) are taken by threads after all the others, so
+  // that with one wall column every other warp takes one row of 32
+  // interior faces and none diverges on a wall face.
+  const int wc0 = (!P.px && x0 == 0) ? 0 : -1;
+  const int wc1 = (!P.px && nx - x0 <= TX) ? nx - x0 : -1;
+  const int nmain = TX + 1 - (wc0 >= 0) - (wc1 >= 0);
   for (int t = tid; t < TY * (TX + 1); t += nthr) {
-    const int r = t / (TX + 1), fc = t - r * (TX + 1);
+    int r, fc;
+    if (t < TY * nmain) {
+      r = t / nmain;
+      fc = t - r * nmain;
+      if (wc0 >= 0) ++fc;
+      if (wc1 >= 0 && fc >= wc1) ++fc;
+    } else {
+      const int u = t - TY * nmain, w = u / TY;
+      r = u - w * TY;
+      fc = (w == 0 && wc0 >= 0) ? wc0 : wc1;
+    }
     const int j = y0 + r, fi = x0 + fc;
     if (j >= ny || fi > nx) continue;
     A fb[9];

@@ -160,18 +160,31 @@ __device__ __forceinline__ void dev_feq(double rho, double drho, double sx, doub
   for (int k = 0; k < 9; ++k) fe[k] = M.W[k] * fmaf(r, p1[k], dr);
 }
 
-__device__ __forceinline__ int resolve1(int x, int n, bool per, int (&i)[3], float (&c)[3]) {
-  if (x >= 0 && x < n) { i[0] = x; c[0] = 1.f; return 1; }
-  if (per) { i[0] = ((x % n) + n) % n; c[0] = 1.f; return 1; }
-  if (x == -1 || x == n) {
-    const int b = x < 0 ? 0 : n - 1, s = x < 0 ? 1 : -1;
-    i[0] = b; i[1] = b + s; i[2] = b + 2 * s; c[0] = 3.f; c[1] = -3.f; c[2] = 1.f; return 3;
-  }
-  if (x == -2 || x == n + 1) {
-    const int b = x < 0 ? 0 : n - 1, s = x < 0 ? 1 : -1;
-    i[0] = b; i[1] = b + s; i[2] = b + 2 * s; c[0] = 6.f; c[1] = -8.f; c[2] = 3.f; return 3;
-  }
-  return 0;
+// A staged coordinate of a tile with its 2-cell halo: >= 0 the cell it holds
+// (in the domain or its periodic image); -1 a wall ghost; -2 beyond the
+// ghost band (never read by a computed face).
+__device__ __forceinline__ int stage_coord(int x, int n, bool per) {
+  if (x >= 0 && x < n) return x;
+  if (per) return ((x % n) + n) % n;
+  return (x >= -2 && x <= n + 1) ? -1 : -2;
+}
+
+// Taps of a staged coordinate for the ghost fill, as positions in the
+// staged tile (t0 = tile origin, s = this position): itself when it holds a
+// cell, else the three cells next to the wall with the weights of the
+// quadratic extrapolation (3, -3, 1 and 6, -8, 3); a tile holding a ghost
+// holds those cells too (walls need three cells across).
+__device__ __forceinline__ int ghost_taps(int x, int ix, int n, int t0, int s, int (&pos)[3],
+                                          float (&c)[3]) {
+  if (ix >= 0) { pos[0] = s; c[0] = 1.f; return 1; }
+  const int b = x < 0 ? 0 : n - 1, d = x < 0 ? 1 : -1;
+  const bool near = x == -1 || x == n;
+  c[0] = near ? 3.f : 6.f;
+  c[1] = near ? -3.f : -8.f;
+  c[2] = near ? 1.f : 3.f;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) pos[m] = b + m * d - t0 + HALO;
+  return 3;
 }
 
 // Wall face in deviation form: tangential velocities from the fluid cell only,
@@ -244,31 +257,77 @@ k_d2q9m(D2Q9Params P, D2Q9StageF S, MixedConst M, const T* __restrict__ gin,
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int stride = SH * SW;
 
+  // staged tile: cells of the domain and their periodic images first, then
+  // the wall ghosts extrapolated from them (no chain of global loads)
   for (int p = tid; p < SH * SW; p += nthr) {
     const int rr = p / SW, cc = p - rr * SW;
-    int ix[3], iy[3];
-    float cx[3], cy[3];
-    const int nxr = resolve1(x0 + cc - HALO, nx, P.px, ix, cx);
-    const int nyr = resolve1(y0 + rr - HALO, ny, P.py, iy, cy);
-    if (nxr == 1 && nyr == 1) {
-      const T* src = gin + iy[0] * nx + ix[0];
+    const int ix = stage_coord(x0 + cc - HALO, nx, P.px);
+    const int iy = stage_coord(y0 + rr - HALO, ny, P.py);
+    if (ix >= 0 && iy >= 0) {
+      const T* src = gin + iy * nx + ix;
 #pragma unroll
       for (int k = 0; k < 9; ++k) sg[k * stride + rr * SW + cc] = ld(src + (size_t)k * N);
-    } else {
+    } else if (ix == -2 || iy == -2) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        float v = 0.f;
-        for (int a = 0; a < nyr; ++a)
-          for (int b = 0; b < nxr; ++b)
-            v = fmaf(cy[a] * cx[b], ld(gin + (size_t)k * N + iy[a] * nx + ix[b]), v);
-        sg[k * stride + rr * SW + cc] = v;
+      for (int k = 0; k < 9; ++k) sg[k * stride + rr * SW + cc] = 0.f;
+    }
+  }
+  // ghosts: one (ghost, velocity) pair per thread; ghost columns (every
+  // row of the band, corners included), then ghost rows (columns that hold
+  // a cell)
+  const bool gw = !P.px && x0 == 0, gs = !P.py && y0 == 0;
+  const int ce = nx - x0 + HALO, rn = ny - y0 + HALO;    // first east column, north row
+  const int ngc = (gw ? 2 : 0) + (P.px ? 0 : max(0, min(2, SW - ce)));
+  const int ngr = (gs ? 2 : 0) + (P.py ? 0 : max(0, min(2, SH - rn)));
+  if (ngc + ngr > 0) {
+    __syncthreads();
+    const int ncol = ngc * SH * 9;
+    for (int t = tid; t < ncol + ngr * SW * 9; t += nthr) {
+      int rr, cc, k;
+      if (t < ncol) {
+        const int q = t / 9, ci = q / SH;
+        k = t - q * 9;
+        rr = q - ci * SH;
+        cc = (gw && ci < 2) ? ci : ce + ci - (gw ? 2 : 0);
+      } else {
+        const int q = (t - ncol) / 9, ri = q / SW;
+        k = (t - ncol) - q * 9;
+        cc = q - ri * SW;
+        rr = (gs && ri < 2) ? ri : rn + ri - (gs ? 2 : 0);
       }
+      const int x = x0 + cc - HALO, y = y0 + rr - HALO;
+      const int ix = stage_coord(x, nx, P.px), iy = stage_coord(y, ny, P.py);
+      if (ix == -2 || iy == -2 || (t >= ncol && ix < 0)) continue;
+      int pc[3], pr[3];
+      float cx[3], cy[3];
+      const int nxr = ghost_taps(x, ix, nx, x0, cc, pc, cx);
+      const int nyr = ghost_taps(y, iy, ny, y0, rr, pr, cy);
+      float v = 0.f;
+      for (int a = 0; a < nyr; ++a)
+        for (int b = 0; b < nxr; ++b)
+          v = fmaf(cy[a] * cx[b], sg[k * stride + pr[a] * SW + pc[b]], v);
+      sg[k * stride + rr * SW + cc] = v;
     }
   }
   __syncthreads();
 
+  // x-faces; wall faces (fi = 0 or nx) after all the others, so that no
+  // warp of interior faces diverges on one
+  const int wc0 = (!P.px && x0 == 0) ? 0 : -1;
+  const int wc1 = (!P.px && nx - x0 <= TX) ? nx - x0 : -1;
+  const int nmain = TX + 1 - (wc0 >= 0) - (wc1 >= 0);
   for (int t = tid; t < TY * (TX + 1); t += nthr) {
-    const int r = t / (TX + 1), fc = t - r * (TX + 1);
+    int r, fc;
+    if (t < TY * nmain) {
+      r = t / nmain;
+      fc = t - r * nmain;
+      if (wc0 >= 0) ++fc;
+      if (wc1 >= 0 && fc >= wc1) ++fc;
+    } else {
+      const int u = t - TY * nmain, w = u / TY;
+      r = u - w * TY;
+      fc = (w == 0 && wc0 >= 0) ? wc0 : wc1;
+    }
     const int j = y0 + r, fi = x0 + fc;
     if (j >= ny || fi > nx) continue;
     float fb[9];
