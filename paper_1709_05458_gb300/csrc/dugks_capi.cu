@@ -282,13 +282,20 @@ double d2q9_speed(const dugks_velset* v) {
 // [4, maxty]; ties go to the lower height, or with prefer_tall (the
 // issue-bound double-word kernels, which gain from the smaller halo share of
 // taller tiles; measured by dugks_autotune) to the taller one.
-int d2q9_tile_height(int nx, int ny, int sms, int maxty, bool prefer_tall) {
+// Tile height of the fused D2Q9 kernels: the height whose tiles finish
+// soonest when an SM holds b = min(occ[ty], ceil(tiles / SMs)) blocks at a
+// time (a one-wave grid is spread evenly by the launch), at a cost of ty + 1
+// face rows per tile, with 6 % credited to b >= 2 resident blocks, which
+// overlap one another's barriers and loads (measured at 256^2 and 1024^2 for
+// both arithmetics).  occ[ty]: resident blocks per SM at height ty.
+int d2q9_tile_height(int nx, int ny, int sms, int maxty, bool prefer_tall, const int* occ) {
   int best = 8;
   double bestc = 1e300;
   for (int ty = 4; ty <= maxty; ++ty) {
     const long tiles = (long)((nx + 31) / 32) * ((ny + ty - 1) / ty);
-    const long waves = (tiles + sms - 1) / sms;
-    const double cost = (double)waves * (ty + 1);
+    const long b = std::max(1L, std::min<long>(std::max(1, occ[ty]), (tiles + sms - 1) / sms));
+    const long waves = (tiles + sms * b - 1) / (sms * b);
+    const double cost = (double)waves * b * (ty + 1) * (b >= 2 ? 0.94 : 1.0);
     if (cost < bestc - 1e-9 || (prefer_tall && cost <= bestc + 1e-9)) {
       bestc = cost;
       best = ty;
@@ -881,13 +888,21 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     q.N = p.N;
     q.px = p.px;
     q.py = p.py;
-    q.ty = d2q9_tile_height(p.nx, p.ny, sms * d2q9_blocks_per_sm(dwa), d2q9_max_ty(dwa), dwa);
+    q.wsym = vel->w[1] == vel->w[3] && vel->w[1] == vel->w[5] && vel->w[1] == vel->w[7] &&
+             vel->w[0] == vel->w[2] && vel->w[0] == vel->w[6] && vel->w[0] == vel->w[8];
+    e = d2q9_prepare(0);
+    {
+      // occupancy of the FP64 / double-word stage kernels at each height;
+      // the deviation-storage kernels keep the one-block model
+      int occ[17];
+      for (int t = 0; t <= 16; ++t)
+        occ[t] = (e == cudaSuccess && storage == DUGKS_FP64) ? d2q9_occupancy(dwa, q.wsym, t) : 1;
+      q.ty = d2q9_tile_height(p.nx, p.ny, sms, d2q9_max_ty(dwa), dwa, occ);
+    }
     for (int k = 0; k < 9; ++k) q.W[k] = vel->w[k];
     q.c3 = cd * cd / vel->RT;
     q.base_div = 0.5 / q.c3;
     q.half_mb = 0.5 - q.base_div;
-    q.wsym = vel->w[1] == vel->w[3] && vel->w[1] == vel->w[5] && vel->w[1] == vel->w[7] &&
-             vel->w[0] == vel->w[2] && vel->w[0] == vel->w[6] && vel->w[0] == vel->w[8];
     q.c_over_RT = cd / vel->RT;
     q.c = cd;
     q.a1 = c->s1.a;
@@ -913,7 +928,6 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
       d2q9_stage_to_dw(c->ds1, c->dws1);
       d2q9_stage_to_dw(c->ds2, c->dws2);
     }
-    e = d2q9_prepare(q.ty);
     if (e == cudaSuccess && storage != DUGKS_FP64) {
       c->store = storage;
       d2q9_stage_to_float(c->ds1, c->df1);

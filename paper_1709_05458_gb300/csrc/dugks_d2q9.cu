@@ -822,6 +822,56 @@ int d2q9_batch_blocks_per_sm(int max_ty) {
 }
 
 namespace {
+// Per-device cache of the stage kernels' occupancy (blocks per SM at each
+// tile height, unpadded) and of the one-wave padding of stage_smem.
+template <typename A>
+struct StageCache {
+  struct Entry {
+    int occ = -1, cap = -1;
+    size_t bytes = 0;
+  };
+  std::mutex mu;
+  Entry e[2][2][kMaxTY + 1];
+  SmemLimits lim;
+  int dev = -1;
+};
+
+template <typename A>
+StageCache<A>& stage_cache() {
+  static StageCache<A> c;
+  return c;
+}
+
+template <typename A>
+auto stage_kernel(int stage, bool wsym) {
+  return wsym ? (stage == 1 ? k_d2q9<1, true, A> : k_d2q9<2, true, A>)
+              : (stage == 1 ? k_d2q9<1, false, A> : k_d2q9<2, false, A>);
+}
+
+// the cache entry of (stage, wsym, ty) with its occupancy filled in, or
+// nullptr; the caller holds c.mu
+template <typename A>
+typename StageCache<A>::Entry* stage_entry(StageCache<A>& c, int stage, bool wsym, int ty) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (dev != c.dev) {                         // (re)read the limits of this device
+    c.lim = smem_limits();
+    c.dev = dev;
+    for (auto& a : c.e)
+      for (auto& b : a)
+        for (auto& x : b) x = typename StageCache<A>::Entry{};
+  }
+  if (c.lim.sms <= 0 || ty < 1 || ty > kMaxTY) return nullptr;
+  auto& en = c.e[stage - 1][wsym ? 1 : 0][ty];
+  if (en.occ < 0 && cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &en.occ, stage_kernel<A>(stage, wsym), TX * (ty + 1),
+                        d2q9_smem_bytes(ty)) != cudaSuccess) {
+    en.occ = 0;
+    cudaGetLastError();
+  }
+  return &en;
+}
+
 // Dynamic shared memory of a stage launch.  A grid of at most one wave
 // (tiles <= SMs x resident blocks per SM) is not spread evenly by the block
 // scheduler: some SMs receive as many tiles as fit (three 32 x 7 tiles of the
@@ -829,56 +879,44 @@ namespace {
 // as long as the fullest SM.  Padding the request so that no more than
 // ceil(tiles / SMs) blocks fit on an SM spreads the tiles evenly (measured
 // at 256^2: double-word 103.2 -> 97.2 us per step at ty = 7; FP64 at its
-// chosen height, one block per SM, unchanged).  The occupancy of each
-// (kernel, tile height, cap) is computed once.
+// chosen height, one block per SM, unchanged).
 template <typename A>
 size_t stage_smem(int stage, bool wsym, int ty, long tiles) {
   const size_t need = d2q9_smem_bytes(ty);
-  struct Entry {
-    int occ = -1, cap = -1;
-    size_t bytes = 0;
-  };
-  static std::mutex mu;
-  static Entry cache[2][2][kMaxTY + 1];
-  static SmemLimits lim;
-  static int lim_dev = -1;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return need;
-  std::lock_guard<std::mutex> lock(mu);
-  if (dev != lim_dev) {                       // (re)read the limits of this device
-    lim = smem_limits();
-    lim_dev = dev;
-    for (auto& a : cache)
-      for (auto& b : a)
-        for (auto& c : b) c = Entry{};
-  }
-  if (lim.sms <= 0 || ty < 1 || ty > kMaxTY) return need;
-  const auto kern = wsym ? (stage == 1 ? k_d2q9<1, true, A> : k_d2q9<2, true, A>)
-                         : (stage == 1 ? k_d2q9<1, false, A> : k_d2q9<2, false, A>);
-  const int threads = TX * (ty + 1);
-  Entry& en = cache[stage - 1][wsym ? 1 : 0][ty];
-  if (en.occ < 0 &&
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&en.occ, kern, threads, need) != cudaSuccess) {
-    en.occ = 0;
-    cudaGetLastError();
-  }
-  const long cap = (tiles + lim.sms - 1) / lim.sms;
-  if (en.occ <= 0 || cap >= en.occ) return need;
-  if (en.cap != cap) {
+  StageCache<A>& c = stage_cache<A>();
+  std::lock_guard<std::mutex> lock(c.mu);
+  auto* en = stage_entry(c, stage, wsym, ty);
+  if (!en) return need;
+  const long cap = (tiles + c.lim.sms - 1) / c.lim.sms;
+  if (en->occ <= 0 || cap >= en->occ) return need;
+  if (en->cap != cap) {
     // (cap + 1) (bytes + reserved) > per_sm >= cap (bytes + reserved)
-    size_t pad = (size_t)(lim.per_sm / (cap + 1) - lim.reserved + 16);
+    size_t pad = (size_t)(c.lim.per_sm / (cap + 1) - c.lim.reserved + 16);
     pad = std::max(need, (pad + 15) & ~(size_t)15);
     int got = 0;
-    if (pad > (size_t)lim.optin ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, kern, threads, pad) != cudaSuccess ||
+    if (pad > (size_t)c.lim.optin ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, stage_kernel<A>(stage, wsym),
+                                                      TX * (ty + 1), pad) != cudaSuccess ||
         got != cap) {
       cudaGetLastError();
       pad = need;
     }
-    en.cap = (int)cap;
-    en.bytes = pad;
+    en->cap = (int)cap;
+    en->bytes = pad;
   }
-  return en.bytes;
+  return en->bytes;
+}
+
+template <typename A>
+int stage_occupancy(bool wsym, int ty) {
+  StageCache<A>& c = stage_cache<A>();
+  std::lock_guard<std::mutex> lock(c.mu);
+  int occ = 1 << 30;
+  for (int stage = 1; stage <= 2; ++stage) {
+    auto* en = stage_entry(c, stage, wsym, ty);
+    occ = std::min(occ, en ? en->occ : 0);
+  }
+  return occ;
 }
 
 template <typename A>
@@ -962,7 +1000,10 @@ cudaError_t launch_d2q9_cell(const D2Q9Params& p, bool write_g, const double* fh
 }
 
 int d2q9_max_ty(bool dwa) { return dwa ? Arith<dw>::kMaxTY : Arith<double>::kMaxTY; }
-int d2q9_blocks_per_sm(bool dwa) { return dwa ? Arith<dw>::kMinBlocks : 1; }
+int d2q9_occupancy(bool dwa, bool wsym, int ty) {
+  if (ty < 1 || ty > d2q9_max_ty(dwa)) return 0;
+  return dwa ? stage_occupancy<dw>(wsym, ty) : stage_occupancy<double>(wsym, ty);
+}
 
 cudaError_t launch_d2q9_stage(const D2Q9Params& p, const D2Q9Stage& s, int stage,
                               const double* gin, const double* own, const double* rho_in,

@@ -227,9 +227,11 @@ struct D2Q9StageDW {
   dw gamma;
   dw kx[9], ky[9];
 };
-// largest tile height and resident blocks per SM of the FP64 / double-word kernels
+// largest tile height of the FP64 / double-word stage kernels, and their
+// resident blocks per SM at height ty (the smaller of the two stages; 0 if
+// the occupancy query fails)
 int d2q9_max_ty(bool dwa);
-int d2q9_blocks_per_sm(bool dwa);
+int d2q9_occupancy(bool dwa, bool wsym, int ty);
 void d2q9_params_to_dw(const D2Q9Params& p, D2Q9ParamsDW& d);
 void d2q9_stage_to_dw(const D2Q9Stage& s, D2Q9StageDW& d);
 // the g1 prologue and moments of the double-word form (its stage-2 arithmetic)
