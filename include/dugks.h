@@ -203,7 +203,9 @@ int dugks_tile_height(dugks_ctx* ctx, int* ty_out);
  * GPU; the other contexts (Newton-Cotes sets, deviation storage) run their
  * own launches inside the same graph.  The contexts must share one
  * non-default stream; their parameters and tile heights are read at
- * dugks_batch_create (autotune before creating the batch).
+ * dugks_batch_create, and the fused instances run with the largest of their
+ * tile heights (every block of the persistent launch has that many rows of
+ * threads; results do not depend on the height).
  *   dugks_batch_create  -- ctxs[n] (borrowed; keep them alive while the
  *                          batch exists) -> *out.
  *   dugks_batch_step    -- advance every context nsteps steps: the graph for

@@ -1260,16 +1260,25 @@ int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
   b->stream = ctxs[0]->stream;
   std::vector<D2Q9BatchItem> items;
   std::vector<int> start(1, 0);
+  auto fused = [](const dugks_ctx* c) {
+    return c->d2q9 && c->store == 0 && !c->dwa && c->scheme == DUGKS_T3S3;
+  };
+  // one tile height for all fused instances, the largest of theirs: every
+  // block of the persistent launch has that many rows of threads, and a
+  // shorter tile would leave some of them idle (results do not depend on it)
+  for (int i = 0; i < n; ++i)
+    if (fused(ctxs[i])) b->max_ty = std::max(b->max_ty, ctxs[i]->dp.ty);
   for (int i = 0; i < n; ++i) {
     dugks_ctx* c = ctxs[i];
     b->ctxs.push_back(c);
     c->batched += 1;
-    if (!(c->d2q9 && c->store == 0 && !c->dwa && c->scheme == DUGKS_T3S3)) {
+    if (!fused(c)) {
       b->own.push_back(c);
       continue;
     }
     D2Q9BatchItem it{};
     it.P = c->dp;
+    it.P.ty = b->max_ty;
     it.S1 = c->ds1;
     it.S2 = c->ds2;
     it.fhat = c->fhat;
@@ -1278,9 +1287,8 @@ int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
     it.X = c->acc;
     it.mom = c->mom;
     it.tiles_x = (c->p.nx + 31) / 32;
-    const int tiles = it.tiles_x * ((c->p.ny + c->dp.ty - 1) / c->dp.ty);
+    const int tiles = it.tiles_x * ((c->p.ny + b->max_ty - 1) / b->max_ty);
     start.push_back(start.back() + tiles);
-    b->max_ty = std::max(b->max_ty, c->dp.ty);
     items.push_back(it);
   }
   b->nitems = (int)items.size();

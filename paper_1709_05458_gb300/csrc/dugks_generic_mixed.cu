@@ -1051,11 +1051,13 @@ cudaError_t cell_t(const GDevStep& s, const void* src, const StageCoef& c, cudaS
     const int kchunk = (p.nv + s.mch - 1) / s.mch;
     const dim3 mgrid((p.N + 31) / 32, s.mch);
     // tensor grid with chunks of whole rows (n = sqrt(nv), a multiple of 16),
-    // FP64 storage: one FP64 operation per cell-velocity fewer on the FP64
-    // pipe that bounds it (the FP32 / BF16 forms measured no gain, BF16 a loss)
+    // FP64 storage, rows of 64 velocities or more: one FP64 operation per
+    // cell-velocity fewer on the FP64 pipe that bounds it (measured: 64 x 64
+    // sets gain 1.3 %, the 16 x 16 - 32 x 32 sets of the batched workload
+    // lose 3 %; the FP32 / BF16 forms no gain, BF16 a loss)
     int n = 0;
     while ((long)(n + 1) * (n + 1) <= p.nv) ++n;
-    if (sizeof(T) == 8 && s.tgrid && kchunk % n == 0)
+    if (sizeof(T) == 8 && s.tgrid && n >= 64 && kchunk % n == 0)
       k_gmom<T, true><<<mgrid, kThreads, 0, st>>>(s, (const T*)src, kchunk, n);
     else
       k_gmom<T, false><<<mgrid, kThreads, 0, st>>>(s, (const T*)src, kchunk, n);
