@@ -46,12 +46,13 @@ FLOPS_PER_UNIT = {
     "cell_stage1": 17, "cell_stage2": 17,
     "face_x_stage1": 34, "face_y_stage1": 34, "face_x_stage2": 34, "face_y_stage2": 34,
     "update_stage1": 17, "update_stage2": 21,
-    # fused D2Q9 kernels, per cell-velocity: two faces (2 x 23.2: the 70
+    # fused D2Q9 kernels, per cell-velocity: two faces (2 x 22.0: the 70
     # non-zero stencil products of the nine velocities, face moments, one
-    # reciprocal, the nine equilibrium polynomials, f-bar -> f) plus the cell
-    # part (stage 1: L*, f~', moments, feq', dt Omega', g2, X = 25.9;
-    # stage 2: L**, f^, moments, feq, g1 = 13.8)
-    "d2q9_stage1": 72.3, "d2q9_stage2": 60.2,
+    # reciprocal, the equilibrium polynomials and f-bar -> f of the six
+    # velocities that cross the face) plus the cell part (stage 1: L*, f~',
+    # moments, feq', dt Omega', g2, X = 25.9; stage 2: L**, f^, moments, feq,
+    # g1 = 13.8)
+    "d2q9_stage1": 69.9, "d2q9_stage2": 57.8,
     # T2 schemes on the generic kernels (counted as the T3S3 generic ones)
     "t2_cell": 17, "t2_face_x": 34, "t2_face_y": 34, "t2_update": 19,
 }
@@ -109,11 +110,11 @@ BYTES_PER_UNIT = {
 # from a capture of the 1024^2 D2Q9 cavity (scaled to a launch by the units
 # it processes); kept only while the kernel is unchanged.
 TRAFFIC_BYTES_PER_UNIT = {
-    "d2q9_stage1": (151.372032e6 + 110.503936e6) / (1024 * 1024 * 9),
-    "d2q9_stage2": (151.418880e6 + 115.414016e6) / (1024 * 1024 * 9),
+    "d2q9_stage1": (151.343360e6 + 110.597888e6) / (1024 * 1024 * 9),
+    "d2q9_stage2": (151.400960e6 + 115.464704e6) / (1024 * 1024 * 9),
     # the double-word instantiation, same capture
-    "d2q9dw_stage1": (151.427072e6 + 110.076416e6) / (1024 * 1024 * 9),
-    "d2q9dw_stage2": (151.416320e6 + 114.046720e6) / (1024 * 1024 * 9),
+    "d2q9dw_stage1": (151.418880e6 + 110.078208e6) / (1024 * 1024 * 9),
+    "d2q9dw_stage2": (151.412992e6 + 114.651648e6) / (1024 * 1024 * 9),
 }
 
 

@@ -200,6 +200,12 @@ __device__ __forceinline__ void for9(F&& f) {
   }
 }
 
+// velocity K crosses a face of direction DIR (0: x, 1: y)
+template <int DIR, int K>
+__device__ __forceinline__ constexpr bool crosses() {
+  return DIR == 0 ? (K / 3 != 1) : (K % 3 != 1);
+}
+
 // ut = c u / RT from the sums: (c^2/RT) (sx, sy) / rho
 template <typename A>
 __device__ __forceinline__ void d2q9_ut(A rho, A sx, A sy, const typename Arith<A>::Par& P,
@@ -219,8 +225,11 @@ __device__ __forceinline__ void d2q9_sums(const A (&f)[9], A& rho, A& sx, A& sy)
   sy = (f[2] + f[5] + f[8]) - (f[0] + f[3] + f[6]);
 }
 
-// f/alpha = f-bar + gamma feq(moments of f-bar) for one face, in place
-template <bool WS, typename A>
+// f/alpha = f-bar + gamma feq(moments of f-bar) for one face of direction
+// DIR (0: x-face, 1: y-face), in place.  The moments take all nine f-bar;
+// the flux through the face only the velocities that cross it, so the
+// tangential ones (e_x = 0 at an x-face, e_y = 0 at a y-face) keep f-bar.
+template <bool WS, int DIR, typename A>
 __device__ __forceinline__ void face_recover(A (&fb)[9], const typename Arith<A>::Stg& S,
                                              const typename Arith<A>::Par& P) {
   A rho, sx, sy;
@@ -233,7 +242,7 @@ __device__ __forceinline__ void face_recover(A (&fb)[9], const typename Arith<A>
   wclasses<WS>(P, gr, ws);
   for9([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    fb[k] = fma(wk<WS, k>(P, gr, ws), Pk[k], fb[k]);
+    if constexpr (crosses<DIR, k>()) fb[k] = fma(wk<WS, k>(P, gr, ws), Pk[k], fb[k]);
   });
 }
 
@@ -477,9 +486,12 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
 #pragma unroll
       for (int k = 0; k < 9; ++k) fb[k] = fw[k];
     }
-    face_recover<WS>(fb, S, P);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sfx[(k * TY + r) * (TX + 1) + fc] = fb[k];
+    face_recover<WS, 0>(fb, S, P);
+    // only the velocities that cross the face are read back (cell phase)
+    for9([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if constexpr (crosses<0, k>()) sfx[(k * TY + r) * (TX + 1) + fc] = fb[k];
+    });
   }
 
   // phase 2: y-faces fj = y0 + fr, fr = 0..TY, cols c < TX
@@ -536,9 +548,11 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
 #pragma unroll
       for (int k = 0; k < 9; ++k) fb[k] = fw[k];
     }
-    face_recover<WS>(fb, S, P);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sfy[(k * (TY + 1) + fr) * TX + c] = fb[k];
+    face_recover<WS, 1>(fb, S, P);
+    for9([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if constexpr (crosses<1, k>()) sfy[(k * (TY + 1) + fr) * TX + c] = fb[k];
+    });
   }
   __syncthreads();
 

@@ -231,6 +231,9 @@ __device__ __forceinline__ void wall_dev(float (&fb)[9], const float* __restrict
   }
 }
 
+// f/alpha = f-bar + gamma feq for one face of direction DIR (0: x, 1: y);
+// the tangential velocities (no flux through the face) keep f-bar
+template <int DIR>
 __device__ __forceinline__ void face_recover_dev(float (&fb)[9], const D2Q9StageF& S,
                                                  const D2Q9Params& P, const MixedConst& M) {
   double rho, dr, sx, sy;
@@ -238,7 +241,8 @@ __device__ __forceinline__ void face_recover_dev(float (&fb)[9], const D2Q9Stage
   float fe[9];
   dev_feq(rho, dr, sx, sy, P, M, fe);
 #pragma unroll
-  for (int k = 0; k < 9; ++k) fb[k] = fmaf(S.gamma, fe[k], fb[k]);
+  for (int k = 0; k < 9; ++k)
+    if (DIR == 0 ? (k / 3 != 1) : (k % 3 != 1)) fb[k] = fmaf(S.gamma, fe[k], fb[k]);
 }
 
 template <int STAGE, typename T>
@@ -346,9 +350,10 @@ k_d2q9m(D2Q9Params P, D2Q9StageF S, MixedConst M, const T* __restrict__ gin,
       wall_dev<0>(fb, s0, stride, S, P, M, hi ? SIDE_W : SIDE_E, hi,
                   rho_in[j * nx + (hi ? 0 : nx - 1)]);
     }
-    face_recover_dev(fb, S, P, M);
+    face_recover_dev<0>(fb, S, P, M);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) sfx[(k * TY + r) * (TX + 1) + fc] = fb[k];
+    for (int k = 0; k < 9; ++k)
+      if (k / 3 != 1) sfx[(k * TY + r) * (TX + 1) + fc] = fb[k];   // read back: e_x != 0 only
   }
 
   for (int t = tid; t < (TY + 1) * TX; t += nthr) {
@@ -371,9 +376,10 @@ k_d2q9m(D2Q9Params P, D2Q9StageF S, MixedConst M, const T* __restrict__ gin,
       wall_dev<1>(fb, s0, stride, S, P, M, hi ? SIDE_S : SIDE_N, hi,
                   rho_in[(hi ? 0 : ny - 1) * nx + i]);
     }
-    face_recover_dev(fb, S, P, M);
+    face_recover_dev<1>(fb, S, P, M);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) sfy[(k * (TY + 1) + fr) * TX + c] = fb[k];
+    for (int k = 0; k < 9; ++k)
+      if (k % 3 != 1) sfy[(k * (TY + 1) + fr) * TX + c] = fb[k];   // read back: e_y != 0 only
   }
   __syncthreads();
 
