@@ -439,24 +439,33 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
     A fb[9];
     const A* s0 = sg + (r + 1) * SW + fc;   // row j-1, col fi-2
     const int stride = SH * SW;
-    fb[0] = xface_val<A, 0>(s0 + 0 * stride, S);
-    fb[1] = xface_val<A, 1>(s0 + 1 * stride, S);
-    fb[2] = xface_val<A, 2>(s0 + 2 * stride, S);
-    fb[3] = xface_val<A, 3>(s0 + 3 * stride, S);
-    fb[4] = xface_val<A, 4>(s0 + 4 * stride, S);
-    fb[5] = xface_val<A, 5>(s0 + 5 * stride, S);
-    fb[6] = xface_val<A, 6>(s0 + 6 * stride, S);
-    fb[7] = xface_val<A, 7>(s0 + 7 * stride, S);
-    fb[8] = xface_val<A, 8>(s0 + 8 * stride, S);
-    if (!P.px && (fi == 0 || fi == nx)) {
+    if (P.px || (fi != 0 && fi != nx)) {
+      fb[0] = xface_val<A, 0>(s0 + 0 * stride, S);
+      fb[1] = xface_val<A, 1>(s0 + 1 * stride, S);
+      fb[2] = xface_val<A, 2>(s0 + 2 * stride, S);
+      fb[3] = xface_val<A, 3>(s0 + 3 * stride, S);
+      fb[4] = xface_val<A, 4>(s0 + 4 * stride, S);
+      fb[5] = xface_val<A, 5>(s0 + 5 * stride, S);
+      fb[6] = xface_val<A, 6>(s0 + 6 * stride, S);
+      fb[7] = xface_val<A, 7>(s0 + 7 * stride, S);
+      fb[8] = xface_val<A, 8>(s0 + 8 * stride, S);
+    } else {
+      // wall face: only the velocities that leave the fluid toward the wall
+      // take the interior stencil; the tangential ones (e_x = 0, k = 3..5)
+      // take the one-sided one on the fluid side, and the ones entering the
+      // fluid come from the wall condition (eq. BB or diffuse scattering)
       const bool hi = fi == 0;                    // fluid cell on the +x side (west wall)
       const int side = hi ? SIDE_W : SIDE_E;
       const A rw = R::load(rho_in + j * nx + (hi ? 0 : nx - 1));
-      // per-velocity tangential rows need the velocity-k slice
-      A fw[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) fw[k] = fb[k];
-      // tangential (ex = 0) velocities are k = 3, 4, 5: recompute one-sided
+      if (hi) {
+        fb[0] = xface_val<A, 0>(s0 + 0 * stride, S);
+        fb[1] = xface_val<A, 1>(s0 + 1 * stride, S);
+        fb[2] = xface_val<A, 2>(s0 + 2 * stride, S);
+      } else {
+        fb[6] = xface_val<A, 6>(s0 + 6 * stride, S);
+        fb[7] = xface_val<A, 7>(s0 + 7 * stride, S);
+        fb[8] = xface_val<A, 8>(s0 + 8 * stride, S);
+      }
 #pragma unroll
       for (int k = 3; k <= 5; ++k) {
         const A(&w)[3][3] = hi ? S.wxR[k] : S.wxL[k];
@@ -466,25 +475,23 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
         for (int rr2 = 0; rr2 < 3; ++rr2)
 #pragma unroll
           for (int q = 0; q < 3; ++q) v = fma(w[rr2][q], sk[rr2 * SW + q], v);
-        fw[k] = v;
+        fb[k] = v;
       }
-      const double nsg = hi ? -1.0 : 1.0;
+      const int nsg = hi ? -1 : 1;
       if (P.bc_kind[side] == BC_BOUNCEBACK) {
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-          if (nsg * (k / 3 - 1) < 0) fw[k] = fma(rw, P.bb[side][k], fw[8 - k]);
+          if (nsg * (k / 3 - 1) < 0) fb[k] = fma(rw, P.bb[side][k], fb[8 - k]);
       } else {
         A num = R::cst(0.0f);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-          if (nsg * (k / 3 - 1) > 0) num = num + fw[k];
+          if (nsg * (k / 3 - 1) > 0) num = num + fb[k];
         const A rd = R::diffuse(num, P, side);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-          if (nsg * (k / 3 - 1) < 0) fw[k] = rd * P.feq_wall[side][k];
+          if (nsg * (k / 3 - 1) < 0) fb[k] = rd * P.feq_wall[side][k];
       }
-#pragma unroll
-      for (int k = 0; k < 9; ++k) fb[k] = fw[k];
     }
     face_recover<WS, 0>(fb, S, P);
     // only the velocities that cross the face are read back (cell phase)
@@ -502,23 +509,32 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
     A fb[9];
     const A* s0 = sg + fr * SW + (c + 1);   // row fj-2, col i-1
     const int stride = SH * SW;
-    fb[0] = yface_val<A, 0>(s0 + 0 * stride, S);
-    fb[1] = yface_val<A, 1>(s0 + 1 * stride, S);
-    fb[2] = yface_val<A, 2>(s0 + 2 * stride, S);
-    fb[3] = yface_val<A, 3>(s0 + 3 * stride, S);
-    fb[4] = yface_val<A, 4>(s0 + 4 * stride, S);
-    fb[5] = yface_val<A, 5>(s0 + 5 * stride, S);
-    fb[6] = yface_val<A, 6>(s0 + 6 * stride, S);
-    fb[7] = yface_val<A, 7>(s0 + 7 * stride, S);
-    fb[8] = yface_val<A, 8>(s0 + 8 * stride, S);
-    if (!P.py && (fj == 0 || fj == ny)) {
+    if (P.py || (fj != 0 && fj != ny)) {
+      fb[0] = yface_val<A, 0>(s0 + 0 * stride, S);
+      fb[1] = yface_val<A, 1>(s0 + 1 * stride, S);
+      fb[2] = yface_val<A, 2>(s0 + 2 * stride, S);
+      fb[3] = yface_val<A, 3>(s0 + 3 * stride, S);
+      fb[4] = yface_val<A, 4>(s0 + 4 * stride, S);
+      fb[5] = yface_val<A, 5>(s0 + 5 * stride, S);
+      fb[6] = yface_val<A, 6>(s0 + 6 * stride, S);
+      fb[7] = yface_val<A, 7>(s0 + 7 * stride, S);
+      fb[8] = yface_val<A, 8>(s0 + 8 * stride, S);
+    } else {
+      // wall face (a whole warp: one row of faces): leaving velocities from
+      // the interior stencil, tangential ones (e_y = 0, k = 1, 4, 7)
+      // one-sided, entering ones from the wall condition
       const bool hi = fj == 0;                    // fluid cell above (south wall)
       const int side = hi ? SIDE_S : SIDE_N;
       const A rw = R::load(rho_in + (hi ? 0 : ny - 1) * nx + i);
-      A fw[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) fw[k] = fb[k];
-      // tangential (ey = 0) velocities are k = 1, 4, 7
+      if (hi) {
+        fb[0] = yface_val<A, 0>(s0 + 0 * stride, S);
+        fb[3] = yface_val<A, 3>(s0 + 3 * stride, S);
+        fb[6] = yface_val<A, 6>(s0 + 6 * stride, S);
+      } else {
+        fb[2] = yface_val<A, 2>(s0 + 2 * stride, S);
+        fb[5] = yface_val<A, 5>(s0 + 5 * stride, S);
+        fb[8] = yface_val<A, 8>(s0 + 8 * stride, S);
+      }
 #pragma unroll
       for (int k = 1; k <= 7; k += 3) {
         const A(&w)[3][3] = hi ? S.wyT[k] : S.wyB[k];
@@ -528,25 +544,23 @@ __device__ __forceinline__ void d2q9_tile(const typename Arith<A>::Par& P,
         for (int q = 0; q < 3; ++q)
 #pragma unroll
           for (int cc = 0; cc < 3; ++cc) v = fma(w[q][cc], sk[q * SW + cc], v);
-        fw[k] = v;
+        fb[k] = v;
       }
-      const double nsg = hi ? -1.0 : 1.0;
+      const int nsg = hi ? -1 : 1;
       if (P.bc_kind[side] == BC_BOUNCEBACK) {
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-          if (nsg * (k % 3 - 1) < 0) fw[k] = fma(rw, P.bb[side][k], fw[8 - k]);
+          if (nsg * (k % 3 - 1) < 0) fb[k] = fma(rw, P.bb[side][k], fb[8 - k]);
       } else {
         A num = R::cst(0.0f);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-          if (nsg * (k % 3 - 1) > 0) num = num + fw[k];
+          if (nsg * (k % 3 - 1) > 0) num = num + fb[k];
         const A rd = R::diffuse(num, P, side);
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-          if (nsg * (k % 3 - 1) < 0) fw[k] = rd * P.feq_wall[side][k];
+          if (nsg * (k % 3 - 1) < 0) fb[k] = rd * P.feq_wall[side][k];
       }
-#pragma unroll
-      for (int k = 0; k < 9; ++k) fb[k] = fw[k];
     }
     face_recover<WS, 1>(fb, S, P);
     for9([&](auto kc) {
