@@ -118,6 +118,28 @@ TRAFFIC_BYTES_PER_UNIT = {
 }
 
 
+def kernel_launch_units(name, nv, nx, ny):
+    """Units one launch of the named kernel processes: face-velocities for
+    the generic face kernels, cell-velocities for every other kernel."""
+    face = name.replace("gdev_", "")[:6]
+    return {"face_x": nv * ny * (nx + 1), "face_y": nv * (ny + 1) * nx}.get(face, nv * nx * ny)
+
+
+def hbm_view(prof, label, nv, nx, ny, peak_gbs):
+    """A form's dominant kernel (largest device time among those with an
+    algorithmic byte count for the form) against HBM: bytes per unit x
+    units per launch / mean launch time, and that over the copy bandwidth.
+    prof: kernel name -> (launches, total ms).  None if no kernel counts."""
+    cand = [(k, v) for k, v in prof.items()
+            if label in HBM_BYTES_PER_UNIT.get(k, {}) and v[0] > 0 and v[1] > 0]
+    if not cand:
+        return None
+    name, (nl, kms) = max(cand, key=lambda kv: kv[1][1])
+    bpu = HBM_BYTES_PER_UNIT[name][label]
+    gbs = bpu * kernel_launch_units(name, nv, nx, ny) / (kms * 1e-3 / nl) / 1e9
+    return {"kernel": name, "achieved_gbs": gbs, "frac": gbs / peak_gbs, "bytes_per_unit": bpu}
+
+
 def fp64_peak_tflops():
     """Nominal GB300 FP64 vector peak from unit counts and clock:
     152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz = 1.258 TFLOP/s."""
@@ -528,6 +550,8 @@ def run_ours(args):
             forms[label] = {"value": units * args.steps * world / (fms * 1e-3) / 1e9,
                             "ms_per_step": fms / args.steps,
                             "E_u_vs_fp64": float(num / den),
+                            "hbm": hbm_view(fprof, label, nv, c["nx"], c["ny"],
+                                            measured_peaks().get("hbm_gbs", 6800.0)),
                             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)}
                                         for k, v in fprof.items() if v[0]}}
             s2.close()
@@ -555,10 +579,7 @@ def run_ours(args):
                            and v[0] > 0 and v[1] > 0),
                           key=lambda kv: kv[1][1])
     nx, ny = c["nx"], c["ny"]
-    face = name.replace("gdev_", "")[:6]
-    per_launch_units = {
-        "face_x": nv * ny * (nx + 1), "face_y": nv * (ny + 1) * nx,
-    }.get(face, nv * nx * ny)
+    per_launch_units = kernel_launch_units(name, nv, nx, ny)
     # gdev face and cell entries cover both stages: two launches per step
     avg_s = kms * 1e-3 / max(nl, 1)
     if name in hbm_per_unit:

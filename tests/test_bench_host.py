@@ -56,6 +56,22 @@ def test_whole_job_rate_is_weak_scaling():
     assert bench.whole_job_rate(589824, 10, 4, 2e-3) == pytest.approx(589824 * 10 * 4 / 2e-3 / 1e9)
 
 
+def test_hbm_view_of_a_form():
+    """The dominant kernel with a byte count for the form, its GB/s from
+    bytes per unit x units per launch / mean launch time."""
+    sys.path.insert(0, ROOT)
+    import bench
+    prof = {"d2q9m_stage1": (10, 2.0), "d2q9m_stage2": (10, 1.5), "other": (5, 9.0)}
+    v = bench.hbm_view(prof, "fp32", 9, 256, 256, 6800.0)
+    want = 16 * 9 * 256 * 256 / (2.0e-3 / 10) / 1e9
+    assert v["kernel"] == "d2q9m_stage1" and v["bytes_per_unit"] == 16
+    assert v["achieved_gbs"] == pytest.approx(want) and v["frac"] == pytest.approx(want / 6800.0)
+    # generic face kernels count face-velocities
+    v = bench.hbm_view({"gdev_face_x": (2, 1.0)}, "bf16", 16, 10, 4, 1000.0)
+    assert v["achieved_gbs"] == pytest.approx(6 * 16 * 4 * 11 / 0.5e-3 / 1e9)
+    assert bench.hbm_view({"d2q9_stage1": (1, 1.0)}, "fp32", 9, 8, 8, 1.0) is None
+
+
 def _run_reference(env_extra):
     env = dict(os.environ, **env_extra)
     return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1",
