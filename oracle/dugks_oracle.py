@@ -29,8 +29,13 @@ Readings of the paper where it is silent, garbled or inconsistent (each
 marked ``Qn`` where it is used):
 
 * Q1  micro-flux sign: L = -(1/|V|) oint (xi.n) f dS, consistent with L = -xi.grad f.
-* Q2  the Taylor term of eq. flux_DS carries the factor 1/2 and the mixed
-      derivative: f + d.grad f + 1/2 d^T (grad grad f) d.
+* Q2p eq. flux_DS is taken as printed: f + d.grad f + d^2 : grad^2 f, the
+      second-order term the full double contraction (mixed derivative
+      included) without a factor 1/2.  Run on the Taylor vortex of Table 1
+      this reproduces the printed T3S3 and T2S3 errors on the finer meshes
+      (within 25 % for N >= 96 and 13 % for N >= 64); the corrected Taylor
+      series with the 1/2 (``recon="quadratic"``, reading Q2) is 40-90x above
+      every printed entry.
 * Q3  derivatives by second-order central differences on the 3x3
       neighbourhood of the upwind cell.
 * Q4  xi.n == 0 at an interior face: average of the two one-sided expansions.
@@ -53,12 +58,13 @@ marked ``Qn`` where it is used):
       [ - sum_{xi.n<0} (xi.n) feq(xi; 1, u_w) ].
 * Q16 stencil ghosts beyond a wall: quadratic extrapolation along the wall
       normal, g_{-1} = 3 g_0 - 3 g_1 + g_2 (corners: both directions).
-* Q26 T2S2 (Sec. 3, the second-order-in-space comparison method, whose
-      reconstruction is not printed): eq. flux_DS taken to first order, the
-      "desired order" its text allows -- f-bar^+(x_b - xi h) =
-      g_U + (x_b - xi h - x_U).grad g_U from the upwind cell U, gradient by
-      central differences (Q3), walls and ties as for T3S3.  T2S3 is the same
-      T2 step with the full quadratic expansion.
+* Q26 T2S2 (Sec. 3, the second-order comparison method that Remark I
+      identifies as the original DUGKS; its reconstruction is not printed):
+      the original DUGKS interpolation f-bar^+(x_b - xi h) = f-bar^+(x_b) -
+      xi h . grad f-bar^+(x_b), face value and gradient interpolated linearly
+      between the two cells of the face (``recon="central"``); beyond a wall
+      the cell is the Q16 ghost.  It reproduces Table 1's T2S2 row to 0.02 %.
+      T2S3 is the same T2 step with the reconstruction of eq. flux_DS (Q2p).
 """
 from __future__ import annotations
 
@@ -85,7 +91,8 @@ class Setup:
     west, east, south, north.  Periodic sides must come in pairs.
     """
 
-    def __init__(self, nx, ny, dx, dy, xi, W, RT, tau, dt, bc, fbp="derived"):
+    def __init__(self, nx, ny, dx, dy, xi, W, RT, tau, dt, bc, fbp="derived",
+                 recon="printed"):
         self.nx, self.ny = int(nx), int(ny)
         self.dx, self.dy = float(dx), float(dy)
         self.xi = np.asarray(xi, dtype=np.float64)
@@ -94,6 +101,7 @@ class Setup:
         self.tau, self.dt = float(tau), float(dt)
         self.bc = [(int(b[0]), float(b[1]), float(b[2])) for b in bc]
         self.fbp = fbp
+        self.recon = recon            # face reconstruction of the T3S3 step
         if (self.bc[WEST][0] == PERIODIC) != (self.bc[EAST][0] == PERIODIC):
             raise ValueError("periodic x needs both west and east periodic")
         if (self.bc[SOUTH][0] == PERIODIC) != (self.bc[NORTH][0] == PERIODIC):
@@ -168,10 +176,18 @@ def cell_derivatives(g, s: Setup):
 
 
 def taylor(d, dX, dY):
-    """Quadratic Taylor expansion about a cell centre (eq. flux_DS with Q2)."""
+    """Quadratic Taylor series about a cell centre (reading Q2: eq. flux_DS
+    with the factor 1/2), kept for comparison with Q2p."""
     C, gx, gy, gxx, gxy, gyy = d
     return C + dX * gx + dY * gy + 0.5 * (dX * dX * gxx + 2.0 * dX * dY * gxy
                                           + dY * dY * gyy)
+
+
+def taylor_printed(d, dX, dY):
+    """eq. flux_DS as printed (Q2p): the second-order term is the full double
+    contraction (x_b - xi h - x_j)^2 : grad^2 f, without a factor 1/2."""
+    C, gx, gy, gxx, gxy, gyy = d
+    return C + dX * gx + dY * gy + (dX * dX * gxx + 2.0 * dX * dY * gxy + dY * dY * gyy)
 
 
 def _feq_unit(s: Setup, uwx, uwy):
@@ -207,48 +223,76 @@ def _wall(fluid, rho_adj, xn, s: Setup, bc):
     return fb
 
 
-def taylor_linear(d, dX, dY):
-    """First-order Taylor expansion about a cell centre (eq. flux_DS to the
-    gradient term, Q26)."""
-    C, gx, gy = d[0], d[1], d[2]
-    return C + dX * gx + dY * gy
+RECONS = ("printed", "quadratic", "central")
 
 
-def interface_fbar(g, h, rho_base, s: Setup, recon="quadratic"):
+def _central_faces(g, h, s: Setup):
+    """Original DUGKS reconstruction (Remark I's second-order method, T2S2):
+    f-bar^+(x_b - xi h) = f-bar^+(x_b) - xi h . grad f-bar^+(x_b) with the
+    face value and gradient by linear interpolation between the two cells of
+    the face -- value (g_L + g_R)/2, normal derivative (g_R - g_L)/dx,
+    tangential derivative the mean of the two cells' central differences.
+    Beyond a wall the cell is the Q16 ghost.  Returns (fbx, fby) without the
+    wall rule applied."""
+    ge = _with_ghosts(g, s)                       # (nv, ny+2, nx+2)
+    # x-faces i = 0..nx between ghosted columns i and i+1, rows 1..ny
+    L, R = ge[:, 1:-1, :-1], ge[:, 1:-1, 1:]
+    gy_all = (ge[:, 2:, :] - ge[:, :-2, :]) / (2.0 * s.dy)   # (nv, ny, nx+2)
+    gt = 0.5 * (gy_all[:, :, :-1] + gy_all[:, :, 1:])
+    fbx = 0.5 * (L + R) - s.cx * h * (R - L) / s.dx - s.cy * h * gt
+    # y-faces j = 0..ny between ghosted rows j and j+1, columns 1..nx
+    B, T = ge[:, :-1, 1:-1], ge[:, 1:, 1:-1]
+    gx_all = (ge[:, :, 2:] - ge[:, :, :-2]) / (2.0 * s.dx)   # (nv, ny+2, nx)
+    gt = 0.5 * (gx_all[:, :-1, :] + gx_all[:, 1:, :])
+    fby = 0.5 * (B + T) - s.cy * h * (T - B) / s.dy - s.cx * h * gt
+    return fbx, fby
+
+
+def interface_fbar(g, h, rho_base, s: Setup, recon="printed"):
     """f-bar(x_b, t+h) = f-bar^{+,h}(x_b - xi h, t) on every face
     (eqs. interfaceEvof and flux_DS), given g = f-bar^{+,h}(t) at the cells.
 
     Returns (fbx, fby): x-faces (nv, ny, nx+1) at x = i dx and y-faces
-    (nv, ny+1, nx) at y = j dy.  The upwind cell is chosen by the sign of
-    xi.n (eq. flux_DS); Q4 for xi.n == 0.  ``recon="linear"``: the
-    expansion truncated after the gradient term instead (T2S2, Q26).
+    (nv, ny+1, nx) at y = j dy.  ``recon`` selects the reconstruction:
+
+    * ``"printed"`` (T3S3, T2S3): eq. flux_DS exactly as printed (Q2p),
+      expanded about the upwind cell chosen by the sign of xi.n; Q4 for
+      xi.n == 0.
+    * ``"quadratic"``: the same with the factor 1/2 on the second-order term
+      (reading Q2, for comparison).
+    * ``"central"``: the original DUGKS reconstruction (T2S2, Q26).
     """
     nx, ny = s.nx, s.ny
-    if recon not in ("quadratic", "linear"):
+    if recon not in RECONS:
         raise ValueError(recon)
-    taylor_ = taylor if recon == "quadratic" else taylor_linear
-    d = cell_derivatives(g, s)
+    if recon == "central":
+        fbx, fby = _central_faces(g, h, s)
+        fromL = fromR = fbx
+        fromB = fromT = fby
+    else:
+        taylor_ = {"quadratic": taylor, "printed": taylor_printed}[recon]
+        d = cell_derivatives(g, s)
 
-    # x-faces: face i lies between cell i-1 (left) and cell i (right)
-    li = (np.arange(nx + 1) - 1) % nx
-    ri = np.arange(nx + 1) % nx
-    dL = tuple(a[:, :, li] for a in d)
-    dR = tuple(a[:, :, ri] for a in d)
-    fromL = taylor_(dL, 0.5 * s.dx - s.cx * h, -s.cy * h)
-    fromR = taylor_(dR, -0.5 * s.dx - s.cx * h, -s.cy * h)
-    fbx = np.where(s.cx > 0, fromL, np.where(s.cx < 0, fromR, 0.5 * (fromL + fromR)))
+        # x-faces: face i lies between cell i-1 (left) and cell i (right)
+        li = (np.arange(nx + 1) - 1) % nx
+        ri = np.arange(nx + 1) % nx
+        dL = tuple(a[:, :, li] for a in d)
+        dR = tuple(a[:, :, ri] for a in d)
+        fromL = taylor_(dL, 0.5 * s.dx - s.cx * h, -s.cy * h)
+        fromR = taylor_(dR, -0.5 * s.dx - s.cx * h, -s.cy * h)
+        fbx = np.where(s.cx > 0, fromL, np.where(s.cx < 0, fromR, 0.5 * (fromL + fromR)))
+
+        # y-faces: face j lies between cell j-1 (below) and cell j (above)
+        lj = (np.arange(ny + 1) - 1) % ny
+        rj = np.arange(ny + 1) % ny
+        dB = tuple(a[:, lj, :] for a in d)
+        dT = tuple(a[:, rj, :] for a in d)
+        fromB = taylor_(dB, -s.cx * h, 0.5 * s.dy - s.cy * h)
+        fromT = taylor_(dT, -s.cx * h, -0.5 * s.dy - s.cy * h)
+        fby = np.where(s.cy > 0, fromB, np.where(s.cy < 0, fromT, 0.5 * (fromB + fromT)))
     if not s.periodic_x:
         fbx[:, :, 0] = _wall(fromR[:, :, 0], rho_base[:, 0], -s.xi[:, 0], s, s.bc[WEST])
         fbx[:, :, nx] = _wall(fromL[:, :, nx], rho_base[:, nx - 1], s.xi[:, 0], s, s.bc[EAST])
-
-    # y-faces: face j lies between cell j-1 (below) and cell j (above)
-    lj = (np.arange(ny + 1) - 1) % ny
-    rj = np.arange(ny + 1) % ny
-    dB = tuple(a[:, lj, :] for a in d)
-    dT = tuple(a[:, rj, :] for a in d)
-    fromB = taylor_(dB, -s.cx * h, 0.5 * s.dy - s.cy * h)
-    fromT = taylor_(dT, -s.cx * h, -0.5 * s.dy - s.cy * h)
-    fby = np.where(s.cy > 0, fromB, np.where(s.cy < 0, fromT, 0.5 * (fromB + fromT)))
     if not s.periodic_y:
         fby[:, 0, :] = _wall(fromT[:, 0, :], rho_base[0, :], -s.xi[:, 1], s, s.bc[SOUTH])
         fby[:, ny, :] = _wall(fromB[:, ny, :], rho_base[ny - 1, :], s.xi[:, 1], s, s.bc[NORTH])
@@ -268,7 +312,7 @@ def microflux(fx, fy, s: Setup):
              + s.cy * (fy[:, 1:, :] - fy[:, :-1, :]) / s.dy)
 
 
-def flux_from_g(g, h, rho_base, s: Setup, recon="quadratic"):
+def flux_from_g(g, h, rho_base, s: Setup, recon="printed"):
     """The DUGKS reconstruction chain: g -> f-bar(x_b) -> f(x_b) -> L."""
     fbx, fby = interface_fbar(g, h, rho_base, s, recon)
     return microflux(recover_f(fbx, h, s), recover_f(fby, h, s), s)
@@ -282,7 +326,7 @@ def t3s3_step(fhat, s: Setup, trace=None):
     # Step (1): L* at t* = t_n + dt/6
     feq_n, rho_n = equilibrium_of(fhat, s)
     g1 = ((12.0 * tau - dt) * fhat + 4.0 * dt * feq_n) / (12.0 * tau + 3.0 * dt)
-    L1 = flux_from_g(g1, dt / 6.0, rho_n, s)
+    L1 = flux_from_g(g1, dt / 6.0, rho_n, s, s.recon)
 
     # Step (2): T2 step of size dt/3 to t' = t_n + dt/3, then dt*Omega(f')
     ft_plus = 1.25 * g1 - 0.25 * fhat                       # Q5
@@ -295,7 +339,7 @@ def t3s3_step(fhat, s: Setup, trace=None):
         g2 = ((24.0 * tau - 5.0 * dt) * ft_prime + 9.0 * dt * feq_p) / (24.0 * tau + 4.0 * dt)
     else:
         g2 = ((24.0 * tau - 5.0 * dt) * ft_prime + 15.0 * dt * feq_p) / (24.0 * tau + 10.0 * dt)
-    L2 = flux_from_g(g2, 5.0 * dt / 12.0, rho_p, s)
+    L2 = flux_from_g(g2, 5.0 * dt / 12.0, rho_p, s, s.recon)
 
     # Step (4)
     fhat_plus = 0.25 * fhat + 0.75 * g1
@@ -315,11 +359,11 @@ def t3s3_run(fhat, s: Setup, nsteps: int):
 
 
 # ------------------------------------------------ T2 step (Remark I)
-def t2_step(ftilde, s: Setup, delta: float, recon="quadratic"):
+def t2_step(ftilde, s: Setup, delta: float, recon="printed"):
     """Original DUGKS time step of size ``delta`` (Remark I, eq.
     feqIntD2nd_Explicit with Q7) at h = delta/2:
-    f~^{n+1} = f~^{+,n} + delta * L(t_n + delta/2); the quadratic
-    reconstruction gives T2S3, ``recon="linear"`` (Q26) gives T2S2.
+    f~^{n+1} = f~^{+,n} + delta * L(t_n + delta/2); the reconstruction of
+    eq. flux_DS (Q2p) gives T2S3, ``recon="central"`` (Q26) gives T2S2.
 
     Works on f~ = f - delta/2 Omega.
     """
@@ -334,8 +378,8 @@ def t2_step(ftilde, s: Setup, delta: float, recon="quadratic"):
     return ft_plus + delta * L
 
 
-def t2_run(ftilde, s: Setup, nsteps: int, recon="quadratic"):
-    """nsteps T2 steps of size s.dt (T2S3, or T2S2 with recon="linear")."""
+def t2_run(ftilde, s: Setup, nsteps: int, recon="printed"):
+    """nsteps T2 steps of size s.dt (T2S3, or T2S2 with recon="central")."""
     f = np.array(ftilde, dtype=np.float64, copy=True)
     for _ in range(nsteps):
         f = t2_step(f, s, s.dt, recon)

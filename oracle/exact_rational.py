@@ -7,7 +7,8 @@ exact ``fractions.Fraction`` arithmetic.  It is used to pin the vectorised
 FP64 oracle (``dugks_oracle.py``) on 4x4 grids: any index, sign or
 coefficient slip in either restatement makes them disagree.
 
-It follows the same readings of the paper (Q1-Q16 in ``dugks_oracle.py``).
+It follows the same readings of the paper (Q1-Q16 and Q2p in
+``dugks_oracle.py``).
 Velocity sets must have rational velocities and weights (D2Q9 with RT = 1/3
 gives xi in {-1, 0, 1}).
 """
@@ -76,7 +77,8 @@ def _gval(s, g, k, j, i):
 
 
 def _expand(s, g, k, j, i, ddx, ddy):
-    """Quadratic Taylor value at centre(j, i) + (ddx, ddy)."""
+    """eq. flux_DS as printed (reading Q2p) at centre(j, i) + (ddx, ddy):
+    value + d.grad + d^2 : grad^2, no factor 1/2 on the second-order term."""
     G = lambda a, b: _gval(s, g, k, j + b, i + a)   # noqa: E731  (a: x offset)
     c = G(0, 0)
     gx = (G(1, 0) - G(-1, 0)) / (2 * s.dx)
@@ -85,7 +87,7 @@ def _expand(s, g, k, j, i, ddx, ddy):
     gyy = (G(0, 1) - 2 * c + G(0, -1)) / (s.dy * s.dy)
     gxy = (G(1, 1) - G(-1, 1) - G(1, -1) + G(-1, -1)) / (4 * s.dx * s.dy)
     return (c + ddx * gx + ddy * gy
-            + (ddx * ddx * gxx + 2 * ddx * ddy * gxy + ddy * ddy * gyy) / 2)
+            + (ddx * ddx * gxx + 2 * ddx * ddy * gxy + ddy * ddy * gyy))
 
 
 def _face_value(s, g, k, cell_a, cell_b, normal_axis, h):
