@@ -4,7 +4,7 @@
 // Forward step (Sec. 2.1.3; generic form of dugks_kernels.cu):
 //   stage s in {1, 2}, input x (x = f^ for s = 1, x = f~' for s = 2):
 //     rho = sum x, J = sum xi x, feq(rho, J), g = a x + b feq
-//     face b: fbar = T(g) (quadratic upwind reconstruction, walls), face
+//     face b: fbar = T(g) (upwind reconstruction of eq. flux_DS, walls), face
 //             moments -> feq_b, f_b = alpha fbar + beta feq_b
 //     L_k(cell) = -(xi_x (f_E - f_W)/dx + xi_y (f_N - f_S)/dy)
 //   f~' = 5/4 g1 - 1/4 f^ + dt/3 L*,  X = 1/4 f^ + 3/4 g1 + 3dt/7 L*
@@ -17,9 +17,9 @@
 // so with mu_k the adjoint of feq_k:  rho_bar = sum mu_k W_k (1 - e^2/2 + uu/2),
 // J_bar = sum mu_k W_k (xi_k (1 + e_k) - u)/RT, and x_bar_k += rho_bar + xi_k.J_bar.
 // Interface reconstruction weights of cell offset (dx, dy) for the foot
-// offset (a dx, b dy): centre 1 - a^2 - b^2, E/W (a^2 +- a)/2, N/S
-// (b^2 +- b)/2, NE = SW = ab/4, NW = SE = -ab/4 (central differences in
-// eq. flux_DS); their transpose scatters with atomicAdd (stencil ghosts
+// offset (a dx, b dy): centre 1 - 2a^2 - 2b^2, E/W a^2 +- a/2, N/S
+// b^2 +- b/2, NE = SW = ab/2, NW = SE = -ab/2 (eq. flux_DS as printed, central
+// differences); their transpose scatters with atomicAdd (stencil ghosts
 // beyond walls scatter through the extrapolation 3, -3, 1).
 // Parameter derivatives: tau enters a, b, alpha, beta and c; the wall
 // velocity enters the bounce-back term and the diffuse-wall Maxwellian.
@@ -93,16 +93,12 @@ __device__ __forceinline__ void add_cell(double* __restrict__ gb, const DevParam
 // transpose of the Taylor expansion about cell (ci, cj) at offset (dX, dY)
 __device__ __forceinline__ void scatter_taylor(double* __restrict__ gb, const DevParams& p, int ci, int cj,
                                double dX, double dY, double v) {
-  const double a = dX * p.inv_dx, b = dY * p.inv_dy;
-  add_cell(gb, p, ci, cj, v * (1.0 - a * a - b * b));
-  add_cell(gb, p, ci + 1, cj, v * 0.5 * (a * a + a));
-  add_cell(gb, p, ci - 1, cj, v * 0.5 * (a * a - a));
-  add_cell(gb, p, ci, cj + 1, v * 0.5 * (b * b + b));
-  add_cell(gb, p, ci, cj - 1, v * 0.5 * (b * b - b));
-  add_cell(gb, p, ci + 1, cj + 1, v * 0.25 * a * b);
-  add_cell(gb, p, ci - 1, cj - 1, v * 0.25 * a * b);
-  add_cell(gb, p, ci - 1, cj + 1, -v * 0.25 * a * b);
-  add_cell(gb, p, ci + 1, cj - 1, -v * 0.25 * a * b);
+  double T[9];
+  flux_ds_weights<double>(dX * p.inv_dx, dY * p.inv_dy, T);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) add_cell(gb, p, ci + q - 1, cj + r - 1, v * T[r * 3 + q]);
 }
 
 // g at any cell within one ghost layer (forward reconstruction, as in the
@@ -143,7 +139,7 @@ __device__ __forceinline__ double taylor(const double* __restrict__ gk, const De
   const double gxx = (E - 2.0 * C + W) * (p.inv_dx * p.inv_dx);
   const double gyy = (N - 2.0 * C + S) * (p.inv_dy * p.inv_dy);
   const double gxy = (NE - NW - SE + SW) * (0.25 * p.inv_dx * p.inv_dy);
-  return C + dX * gx + dY * gy + 0.5 * (dX * dX * gxx + 2.0 * dX * dY * gxy + dY * dY * gyy);
+  return C + dX * gx + dY * gy + (dX * dX * gxx + 2.0 * dX * dY * gxy + dY * dY * gyy);
 }
 
 struct FaceGeo {

@@ -9,6 +9,21 @@
 
 namespace dugks {
 
+// Face-value weights of eq. flux_DS as printed, f-bar^+(x_b - xi h) =
+// g + d.grad g + d^2 : grad^2 g with d = x_b - xi h - x_j = (a dx, b dy)
+// (no factor 1/2 on the second-order term, reading Q2p), derivatives by
+// second-order central differences on the 3x3 neighbourhood of cell j:
+// T[(dy + 1) * 3 + dx + 1] for the cell at offset (dx, dy) from j.  The
+// weights sum to one (the difference stencils sum to zero).
+template <typename C>
+__host__ __device__ __forceinline__ void flux_ds_weights(C a, C b, C (&T)[9]) {
+  const C ab = C(0.5) * a * b;
+  const C ha = C(0.5) * a, hb = C(0.5) * b;
+  T[0] = ab;          T[1] = b * b - hb;                  T[2] = -ab;
+  T[3] = a * a - ha;  T[4] = C(1) - C(2) * (a * a + b * b); T[5] = a * a + ha;
+  T[6] = -ab;         T[7] = b * b + hb;                  T[8] = ab;
+}
+
 enum { SIDE_W = 0, SIDE_E = 1, SIDE_S = 2, SIDE_N = 3 };
 enum { BC_PERIODIC = 0, BC_BOUNCEBACK = 1, BC_DIFFUSE = 2 };
 
@@ -61,7 +76,8 @@ struct DevParams {
   int bc_kind[4];
   double uw_x[4], uw_y[4];
   double ds_den[4];             // -sum_{xi.n<0} (xi.n) W_k P(xi_k; u_w) per side
-  int recon;                    // face expansion: 0 quadratic (eq. flux_DS), 1 first order (T2S2)
+  int recon;                    // face reconstruction: 0 eq. flux_DS as printed (T3S3, T2S3),
+                                // 1 the original DUGKS interpolation (T2S2)
 };
 
 // Per-stage scalar coefficients (host-computed once at init).

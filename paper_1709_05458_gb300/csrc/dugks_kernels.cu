@@ -68,10 +68,10 @@ __device__ __forceinline__ double g_at(const double* __restrict__ gk, const DevP
   return g_col(gk, p, i, j);
 }
 
-// Quadratic Taylor expansion of g about the centre of cell (ci, cj), evaluated
-// at offset (dX, dY): value + d.grad + 1/2 d^T H d, derivatives by central
-// differences on the 3x3 neighbourhood (eq. flux_DS).  p.recon = 1: the
-// expansion stops after the gradient term (the T2S2 reconstruction).
+// eq. flux_DS as printed: the expansion of g about the centre of cell
+// (ci, cj), evaluated at offset d = (dX, dY): value + d.grad + d^T H d (no
+// factor 1/2 on the second-order term, reading Q2p), derivatives by central
+// differences on the 3x3 neighbourhood.
 __device__ __forceinline__ double taylor(const double* __restrict__ gk, const DevParams& p,
                                          int ci, int cj, double dX, double dY) {
   double C, E, W, N, S, NE, NW, SE, SW;
@@ -91,11 +91,32 @@ __device__ __forceinline__ double taylor(const double* __restrict__ gk, const De
   }
   const double gx = (E - W) * (0.5 * p.inv_dx);
   const double gy = (N - S) * (0.5 * p.inv_dy);
-  if (p.recon) return C + dX * gx + dY * gy;   // first order (T2S2)
   const double gxx = (E - 2.0 * C + W) * (p.inv_dx * p.inv_dx);
   const double gyy = (N - 2.0 * C + S) * (p.inv_dy * p.inv_dy);
   const double gxy = (NE - NW - SE + SW) * (0.25 * p.inv_dx * p.inv_dy);
-  return C + dX * gx + dY * gy + 0.5 * (dX * dX * gxx + 2.0 * dX * dY * gxy + dY * dY * gyy);
+  return C + dX * gx + dY * gy + (dX * dX * gxx + 2.0 * dX * dY * gxy + dY * dY * gyy);
+}
+
+// The original DUGKS reconstruction (T2S2, p.recon = 1): f-bar^+(x_b - xi h)
+// = f-bar^+(x_b) - xi h . grad f-bar^+(x_b), the face value and gradient by
+// linear interpolation between the two cells of the face (lo = left / below,
+// up = right / above; a cell beyond a wall is the ghost of g_at): value
+// (g_lo + g_up)/2, normal derivative (g_up - g_lo)/d, tangential derivative
+// the mean of the two cells' central differences.
+template <int DIR>
+__device__ __forceinline__ double central_face(const double* __restrict__ gk, const DevParams& p,
+                                               int li, int lj, int ui, int uj, double cxh,
+                                               double cyh) {
+  const double lo = g_at(gk, p, li, lj), up = g_at(gk, p, ui, uj);
+  double tn;
+  if (DIR == 0) {
+    tn = (g_at(gk, p, li, lj + 1) - g_at(gk, p, li, lj - 1) + g_at(gk, p, ui, uj + 1) -
+          g_at(gk, p, ui, uj - 1)) * (0.25 * p.inv_dy);
+    return 0.5 * (lo + up) - cxh * (up - lo) * p.inv_dx - cyh * tn;
+  }
+  tn = (g_at(gk, p, li + 1, lj) - g_at(gk, p, li - 1, lj) + g_at(gk, p, ui + 1, uj) -
+        g_at(gk, p, ui - 1, uj)) * (0.25 * p.inv_dx);
+  return 0.5 * (lo + up) - cyh * (up - lo) * p.inv_dy - cxh * tn;
 }
 
 // Combine M per-thread partial sums across the G velocity groups of a block;
@@ -238,7 +259,25 @@ k_face(DevParams p, const double* __restrict__ g, const double* __restrict__ mom
       const double uX = (DIR == 0) ? (-half - cx * h) : (-cx * h);
       const double uY = (DIR == 0) ? (-cy * h) : (-half - cy * h);
       double fbar;
-      if (!wall) {
+      if (p.recon == 1) {                      // T2S2: both cells of the face
+        const int kk = (wall && nsgn * cn < 0.0 && kind == BC_BOUNCEBACK) ? __ldg(p.opp + k) : k;
+        const double* gq = g + (size_t)kk * N;
+        const double qx = __ldg(p.xi_x + kk), qy = __ldg(p.xi_y + kk);
+        const double cf = central_face<DIR>(gq, p, li, lj, ui, uj, qx * h, qy * h);
+        if (!wall) {
+          fbar = cf;
+        } else {
+          const double xn = nsgn * cn;
+          if (xn >= 0.0) {
+            fbar = cf;
+            if (xn > 0.0) v[3] += xn * fbar;
+          } else if (kind == BC_BOUNCEBACK) {
+            fbar = cf + 2.0 * rho_w * __ldg(p.w + k) * (cx * uwx + cy * uwy) * p.inv_RT;
+          } else {
+            continue;                          // diffuse: after the reduction
+          }
+        }
+      } else if (!wall) {
         if (cn > 0.0) {
           fbar = taylor(gk, p, li, lj, lX, lY);
         } else if (cn < 0.0) {

@@ -52,20 +52,38 @@ __device__ __forceinline__ double slab_fetch(const double* __restrict__ gk, cons
 // Taylor weights about one cell for the foot offset (a dx, b dy):
 // T[(dy+1)*3 + dx+1]
 __device__ __forceinline__ void taylor9(double a, double b, double (&T)[9]) {
-  const double ab = 0.25 * a * b;
-  T[0] = ab;                  T[1] = 0.5 * (b * b - b); T[2] = -ab;
-  T[3] = 0.5 * (a * a - a);   T[4] = 1.0 - a * a - b * b; T[5] = 0.5 * (a * a + a);
-  T[6] = -ab;                 T[7] = 0.5 * (b * b + b); T[8] = ab;
+  flux_ds_weights<double>(a, b, T);
 }
 
-// the expansion's weights: quadratic (eq. flux_DS), or stopped after the
-// gradient term when p.recon = 1 (the T2S2 reconstruction)
-__device__ __forceinline__ void weights9(const DevParams& p, double a, double b,
-                                         double (&T)[9]) {
-  if (p.recon) {
-    T[0] = 0.0;      T[1] = -0.5 * b; T[2] = 0.0;
-    T[3] = -0.5 * a; T[4] = 1.0;      T[5] = 0.5 * a;
-    T[6] = 0.0;      T[7] = 0.5 * b;  T[8] = 0.0;
+// the face-value weights about the lower (left / below) or upper cell of
+// the face, foot offset (a dx, b dy): eq. flux_DS as printed (p.recon = 0);
+// p.recon = 1, the original DUGKS reconstruction (T2S2): face value and
+// gradient interpolated linearly between the two cells of the face, written
+// on the 3x3 neighbourhood of either of them (the same value from both)
+__device__ __forceinline__ void weights9(const DevParams& p, int dir, bool upper, double a,
+                                         double b, double (&T)[9]) {
+  if (p.recon == 1) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) T[i] = 0.0;
+    if (dir == 0) {        // normal x: a = +-1/2 - xi_x h/dx, tangential b = -xi_y h/dy
+      const double q = 0.25 * b;
+      if (!upper) {        // cells C (lower) and E (upper)
+        T[4] = 1.0 - a; T[5] = a;
+        T[7] = q; T[1] = -q; T[8] = q; T[2] = -q;
+      } else {             // cells W (lower) and C (upper)
+        T[3] = -a; T[4] = 1.0 + a;
+        T[7] = q; T[1] = -q; T[6] = q; T[0] = -q;
+      }
+    } else {               // normal y: b = +-1/2 - xi_y h/dy, tangential a = -xi_x h/dx
+      const double q = 0.25 * a;
+      if (!upper) {        // cells C (lower) and N (upper)
+        T[4] = 1.0 - b; T[7] = b;
+        T[5] = q; T[3] = -q; T[8] = q; T[6] = -q;
+      } else {             // cells S (lower) and C (upper)
+        T[1] = -b; T[4] = 1.0 + b;
+        T[5] = q; T[3] = -q; T[2] = q; T[0] = -q;
+      }
+    }
   } else {
     taylor9(a, b, T);
   }
@@ -118,12 +136,12 @@ k_nc_faces1(DevParams p, const double* __restrict__ g, double* __restrict__ fb,
     const bool lo = cn >= 0.0, hi = cn <= 0.0;     // uniform across the warp
     if (DIR == 0) {
       const double b = -cy * h * p.inv_dy;
-      if (lo) weights9(p, (0.5 * p.dx - cx * h) * p.inv_dx, b, TL);
-      if (hi) weights9(p, (-0.5 * p.dx - cx * h) * p.inv_dx, b, TU);
+      if (lo) weights9(p, 0, false, (0.5 * p.dx - cx * h) * p.inv_dx, b, TL);
+      if (hi) weights9(p, 0, true, (-0.5 * p.dx - cx * h) * p.inv_dx, b, TU);
     } else {
       const double a = -cx * h * p.inv_dx;
-      if (lo) weights9(p, a, (0.5 * p.dy - cy * h) * p.inv_dy, TL);
-      if (hi) weights9(p, a, (-0.5 * p.dy - cy * h) * p.inv_dy, TU);
+      if (lo) weights9(p, 1, false, a, (0.5 * p.dy - cy * h) * p.inv_dy, TL);
+      if (hi) weights9(p, 1, true, a, (-0.5 * p.dy - cy * h) * p.inv_dy, TU);
     }
     const double* gk = g + (size_t)k * p.N;
     __syncwarp();

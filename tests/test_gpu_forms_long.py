@@ -84,11 +84,12 @@ def test_rarefied128_kn1_500_steps_forms(cuda):
             s.step(500)
         r0, u0, v0 = sol["fp64"].moments()
         den = np.sqrt((u0 ** 2 + v0 ** 2).sum())
-        bounds = {"fp32": (5e-6, 2e-11), "bf16": (0.3, 2e-4)}
+        bounds = {"fp32": (5e-6, 2e-10), "bf16": (0.3, 5e-4)}
         for name, (eb, mb) in bounds.items():
             r, u, v = sol[name].moments()
             e = float(np.sqrt(((u - u0) ** 2 + (v - v0) ** 2).sum()) / den)
             m = float(abs(r.sum() - r0.sum()) / r0.sum())
+            print(f"rarefied128 Kn 1, 500 steps, {name}: E(u) {e:.3e}, mass drift {m:.3e}")
             assert e <= eb and m <= mb, (name, e, m)
             assert sol[name].check() == P.DUGKS_OK
     finally:

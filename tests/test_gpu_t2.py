@@ -12,7 +12,7 @@ import workloads as WL
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-12
-SCHEMES = [(P.T2S3, "quadratic"), (P.T2S2, "linear")]
+SCHEMES = [(P.T2S3, "printed"), (P.T2S2, "central")]
 IDS = ["t2s3", "t2s2"]
 
 
@@ -68,7 +68,7 @@ def test_scheme_switch_and_back(cuda):
     P.dugks_set_scheme(g.ctx, P.T2S2)
     g.step(4)
     f2 = g.state()
-    assert rel_linf(f2, O.t2_run(f1, o, 4, "linear")) <= TOL
+    assert rel_linf(f2, O.t2_run(f1, o, 4, "central")) <= TOL
     P.dugks_set_scheme(g.ctx, P.T3S3)
     g.step(2)
     assert rel_linf(g.state(), O.t3s3_run(f2, o, 2)) <= TOL
