@@ -16,6 +16,9 @@
 //   - Its device address is looked up once per device, on the first call
 //     made with that device current (cudaGetSymbolAddress); make that first
 //     call before any stream capture.
+//   - Every call uploads the velocity tables from host vectors that live only
+//     for the call, so a call made while its stream is capturing a CUDA graph
+//     is refused (DUGKS_EINVAL): a captured copy would point at freed memory.
 //   - All calls share the one array and it keeps the last call's contents.
 //     Nothing in it needs to start at zero: every intermediate is fully
 //     written before it is read within a step.  Calls that overlap on the GPU
@@ -164,11 +167,31 @@ extern "C" int dugks_step_static(const dugks_mesh* mesh, const dugks_velset* vel
     if (bc[s].kind == DUGKS_BC_DIFFUSE) p.has_ds = 1;
   }
 
+  // fhat_in and fhat_out: the same array, or two arrays that do not overlap
+  {
+    const size_t bytes = nvN * sizeof(double);
+    const char* a = reinterpret_cast<const char*>(fhat_in);
+    const char* b = reinterpret_cast<const char*>(fhat_out);
+    if (a != b && a < b + bytes && b < a + bytes)
+      return sfail(DUGKS_EINVAL, "dugks_step_static: fhat_in and fhat_out overlap without being equal");
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(st, &cs);
+    if (ce != cudaSuccess)
+      return sfail(DUGKS_ECUDA, std::string("dugks_step_static: cudaStreamIsCapturing: ") +
+                                    cudaGetErrorString(ce));
+    if (cs != cudaStreamCaptureStatusNone)
+      return sfail(DUGKS_EINVAL,
+                   "dugks_step_static: the stream is capturing a graph; this call uploads "
+                   "its velocity tables from call-local host memory and cannot be captured");
+  }
+
   void* base_v = nullptr;
   int rc = scratch_base(&base_v);
   if (rc != DUGKS_OK) return rc;
   unsigned char* base = static_cast<unsigned char*>(base_v);
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   double* dvel = reinterpret_cast<double*>(base + o_vel);
   int* dopp = reinterpret_cast<int*>(base + o_opp);
   double* mom = reinterpret_cast<double*>(base + o_mom);
