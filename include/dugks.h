@@ -131,9 +131,17 @@ int dugks_set_equilibrium(dugks_ctx* ctx, const double* rho, const double* ux,
  * fused D2Q9 path's first pass, eq. f_bar_1_6) stays queued on the stream. */
 int dugks_set_state(dugks_ctx* ctx, const double* fhat, int on_device);
 
-/* dugks_get_state -- copy the current f^ [nv][ny][nx] out.  With
- * on_device = 0 the call waits for the context's stream. */
-int dugks_get_state(dugks_ctx* ctx, double* fhat, int on_device);
+/* dugks_get_state -- copy a distribution [nv][ny][nx] of the current state
+ * out.  which = DUGKS_STATE_SCHEME: the scheme's own variable, the one
+ * dugks_set_state takes (f^ = f - dt/4 Omega under T3S3, eq.
+ * feqIntD3rdHat2; f~ = f - dt/2 Omega under a T2 scheme, eq.
+ * feqIntD2nd_Explicit).  which = DUGKS_STATE_F: the distribution f itself,
+ * f = (4 tau f^ + dt feq)/(4 tau + dt) (T3S3; (2 tau f~ + dt feq)/(2 tau + dt)
+ * under T2), feq from the moments of the state (the collision conserves
+ * them), computed on the device in FP64.  With on_device = 0 the call waits
+ * for the context's stream.  Errors: EINVAL (NULL, unknown which), ECUDA. */
+enum { DUGKS_STATE_SCHEME = 0, DUGKS_STATE_F = 1 };
+int dugks_get_state(dugks_ctx* ctx, double* out, int which, int on_device);
 
 /*
  * dugks_step -- advance n >= 0 T3S3 steps (Sec. 2.1.3, Steps (1)-(4)):
@@ -258,8 +266,12 @@ int dugks_adjoint_equilibrium(dugks_ctx* ctx, const double* rho, const double* u
                               double* duy, int on_device);
 
 /*
- * dugks_step_static -- advance nsteps T3S3 steps exactly as dugks_step does,
- * without allocating any device memory.  The paper has no counterpart: this
+ * dugks_step_static -- advance nsteps T3S3 steps without allocating any device
+ * memory.  It takes the same T3S3 step (Sec. 2.1.3) on the generic FP64
+ * kernels and matches dugks_step to the FP64 parity tolerance (for D2Q9 sets
+ * dugks_step runs the fused kernels, which agree to about 1e-12, not bit for
+ * bit); there is no context, so a storage form or time scheme does not apply.
+ * The paper has no counterpart: this
  * is a facility for callers that may not allocate device memory, such as a
  * plugin inside an application that owns all device memory through its own
  * pool, or a latency-critical loop that cannot accept the implicit device
@@ -279,9 +291,13 @@ int dugks_adjoint_equilibrium(dugks_ctx* ctx, const double* rho, const double* u
  * 5 * nv * nx * ny doubles, e.g. more than a 256^2 D2Q9 grid) is rejected
  * with DUGKS_EINVAL and a message giving the size.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make it before any stream capture.  Calls share the
- * array and it keeps the last call's contents (nothing needs to start at
- * zero); calls that overlap on the GPU race on it and must be serialised.
+ * that device current; make it before any stream capture.  Every call
+ * uploads the velocity tables from call-local host memory, so a call made
+ * while cuda_stream is capturing a CUDA graph is refused with DUGKS_EINVAL.
+ * fhat_in and fhat_out must be the same array or not overlap at all
+ * (DUGKS_EINVAL otherwise).  Calls share the array and it keeps the last
+ * call's contents (nothing needs to start at zero); calls that overlap on the
+ * GPU race on it and must be serialised.
  * Errors: EINVAL, ECUDA (message in dugks_last_error).
  */
 int dugks_step_static(const dugks_mesh* mesh, const dugks_velset* vel, double tau, double dt,
@@ -308,6 +324,23 @@ enum { DUGKS_T3S3 = 0, DUGKS_T2S3 = 1, DUGKS_T2S2 = 2 };
  * scheme.  A context that belongs to a batch cannot change scheme.
  * Errors: EINVAL (unknown scheme, NULL, batched context), ENOTIMPL. */
 int dugks_set_scheme(dugks_ctx* ctx, int scheme);
+
+/*
+ * dugks_alu_peak -- arithmetic-throughput microbenchmark.  The paper has no
+ * counterpart: it measures the denominator of the ALU roofline that bounds
+ * the FP64 form of the step.  One launch of SMs x blocks_per_sm blocks of
+ * 256 threads; every thread runs 8 independent fused multiply-add chains
+ * for iters x 16 rounds.  kind: 0 FP64 (DFMA), 1 FP32 (FFMA), 2 packed FP32
+ * pairs (fma.rn.f32x2, two FMAs per instruction).
+ *   out, out_len : device buffer of out_len >= SMs x blocks_per_sm x 256
+ *                  doubles; receives the chains' final values.
+ *   flops, ms    : host outputs: the launch's flops (an FMA counts 2) and
+ *                  its device time from CUDA events on cuda_stream.
+ * Waits for cuda_stream.  Errors: EINVAL (bad kind, iters < 1,
+ * blocks_per_sm outside 1..32, short buffer), ECUDA.
+ */
+int dugks_alu_peak(int kind, int iters, int blocks_per_sm, double* out, long long out_len,
+                   double* flops, float* ms, void* cuda_stream);
 
 /* dugks_destroy -- free the context (NULL is accepted). */
 int dugks_destroy(dugks_ctx* ctx);

@@ -34,7 +34,7 @@ EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_
            "dugks_last_error", "dugks_step_static", "dugks_adjoint_step", "dugks_adjoint_run",
            "dugks_adjoint_equilibrium", "dugks_autotune", "dugks_set_tile_height",
            "dugks_tile_height", "dugks_batch_create",
-           "dugks_batch_step", "dugks_batch_destroy", "dugks_set_scheme")
+           "dugks_batch_step", "dugks_batch_destroy", "dugks_set_scheme", "dugks_alu_peak")
 
 
 class DugksError(RuntimeError):
@@ -72,7 +72,7 @@ def load(path: str = LIB_PATH):
         "dugks_init": (I, [C.POINTER(Mesh), C.POINTER(VelSet), D, D, C.POINTER(BC), I, P, C.POINTER(P)]),
         "dugks_set_equilibrium": (I, [P, P, P, P, I]),
         "dugks_set_state": (I, [P, P, I]),
-        "dugks_get_state": (I, [P, P, I]),
+        "dugks_get_state": (I, [P, P, I, I]),
         "dugks_step": (I, [P, I]),
         "dugks_moments": (I, [P, P, P, P, I]),
         "dugks_check": (I, [P]),
@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         "dugks_batch_step": (I, [P, I]),
         "dugks_batch_destroy": (I, [P]),
         "dugks_set_scheme": (I, [P, I]),
+        "dugks_alu_peak": (I, [I, I, I, P, C.c_longlong, C.POINTER(C.c_double),
+                               C.POINTER(C.c_float), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -153,8 +155,14 @@ def dugks_set_state(ctx, fhat):
     return _check(load().dugks_set_state(ctx, _ptr(fhat), _on_device(fhat)))
 
 
-def dugks_get_state(ctx, out):
-    return _check(load().dugks_get_state(ctx, _ptr(out), _on_device(out)))
+STATE_SCHEME, STATE_F = 0, 1
+
+
+def dugks_get_state(ctx, out, which=STATE_SCHEME):
+    """Copy the state into ``out``: the scheme's variable (f^ under T3S3,
+    f~ under T2; ``which=STATE_SCHEME``) or the distribution f itself
+    (``which=STATE_F``)."""
+    return _check(load().dugks_get_state(ctx, _ptr(out), int(which), _on_device(out)))
 
 
 def dugks_step(ctx, n=1):
@@ -262,6 +270,23 @@ def dugks_batch_destroy(batch):
     return _check(load().dugks_batch_destroy(batch))
 
 
+ALU_FP64, ALU_FP32, ALU_FP32X2 = 0, 1, 2
+
+
+def dugks_alu_peak(kind, iters, blocks_per_sm, out, stream=None):
+    """One launch of the FMA-throughput microbenchmark; ``out`` is a CUDA
+    float64 tensor of at least SMs x blocks_per_sm x 256 elements.  Returns
+    (flops, ms)."""
+    import torch
+    if not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.float64:
+        raise ValueError("out must be a CUDA float64 tensor")
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
+    fl, ms = C.c_double(0.0), C.c_float(0.0)
+    _check(load().dugks_alu_peak(int(kind), int(iters), int(blocks_per_sm), _ptr(out),
+                                 out.numel(), C.byref(fl), C.byref(ms), C.c_void_p(s)))
+    return fl.value, float(ms.value)
+
+
 class Batch:
     """Many Solvers advanced together (one persistent launch per stage for
     the FP64 D2Q9 ones, everything inside one CUDA graph per step count).
@@ -286,6 +311,23 @@ class Batch:
             pass
 
 
+def _check_static_tensor(name, t, numel):
+    """dugks_step_static takes raw device pointers: refuse anything but a
+    contiguous float64 CUDA tensor of the right size on the current device."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, the problem needs {numel}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index}, not the current device "
+                         f"cuda:{torch.cuda.current_device()}")
+
+
 def dugks_step_static(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, fhat_in, fhat_out, nsteps,
                       stream=None):
     """T3S3 steps with no device allocation (library-internal fixed 32 MiB
@@ -296,6 +338,8 @@ def dugks_step_static(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, fhat_in, fhat_out,
     xi = np.ascontiguousarray(xi, dtype=np.float64)
     xx, xy = np.ascontiguousarray(xi[:, 0]), np.ascontiguousarray(xi[:, 1])
     w = np.ascontiguousarray(W, dtype=np.float64)
+    _check_static_tensor("fhat_in", fhat_in, len(w) * int(ny) * int(nx))
+    _check_static_tensor("fhat_out", fhat_out, len(w) * int(ny) * int(nx))
     vs = VelSet(len(w), xx.ctypes.data_as(C.POINTER(C.c_double)),
                 xy.ctypes.data_as(C.POINTER(C.c_double)),
                 w.ctypes.data_as(C.POINTER(C.c_double)), float(RT))
@@ -328,10 +372,10 @@ class Solver:
             fhat = np.ascontiguousarray(fhat, dtype=np.float64)
         dugks_set_state(self.ctx, fhat)
 
-    def state(self, out=None):
+    def state(self, out=None, which=STATE_SCHEME):
         if out is None:
             out = np.empty((self.nv, self.ny, self.nx))
-        dugks_get_state(self.ctx, out)
+        dugks_get_state(self.ctx, out, which)
         return out
 
     def step(self, n=1):

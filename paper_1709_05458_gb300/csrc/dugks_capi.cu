@@ -63,6 +63,7 @@ struct dugks_ctx {
   double* fbx = nullptr;        // x-face f [nv][ny][nx+1]
   double* fby = nullptr;        // y-face f [nv][ny+1][nx]
   double* mom = nullptr;        // rho, ux, uy [3][N]
+  double* mom_aux = nullptr;    // moments written by dugks_get_state(DUGKS_STATE_F) [3][N]
   double* vel = nullptr;        // xi_x, xi_y, w, feq_wall[4]  ([7][nv])
   int* opp = nullptr;           // [nv]
   double* part = nullptr;       // partial face moments of the large-set face kernels
@@ -204,7 +205,7 @@ int copy_out(dugks_ctx* c, double* dst, const double* src, size_t n, int on_devi
 }
 
 void free_all(dugks_ctx* c) {
-  double* bufs[] = {c->fhat, c->ftp, c->acc, c->g, c->fbx, c->fby, c->mom, c->vel, c->part,
+  double* bufs[] = {c->fhat, c->ftp, c->acc, c->g, c->fbx, c->fby, c->mom, c->mom_aux, c->vel, c->part,
                     c->a_g1, c->a_g2, c->a_ftp, c->a_acc, c->a_mom1, c->a_mom2, c->a_tbar,
                     c->a_gbar, c->a_lam, c->a_out, c->a_phix, c->a_phiy, c->a_rhob, c->a_grads,
                     c->a_fbs};
@@ -227,12 +228,13 @@ void free_all(dugks_ctx* c) {
   if (c->ev_copy) cudaEventDestroy(c->ev_copy);
 }
 
-// Quadratic Taylor weights about one cell centre for the foot offset
-// (a dx, b dy): T[dy+1][dx+1] (eq. flux_DS with central differences).
+// Face-value weights about one cell centre for the foot offset (a dx, b dy):
+// T[dy+1][dx+1] (eq. flux_DS as printed, central differences).
 void taylor_weights(double a, double b, double T[3][3]) {
-  T[0][0] = a * b / 4;  T[0][1] = (b * b - b) / 2;  T[0][2] = -a * b / 4;
-  T[1][0] = (a * a - a) / 2;  T[1][1] = 1 - a * a - b * b;  T[1][2] = (a * a + a) / 2;
-  T[2][0] = -a * b / 4;  T[2][1] = (b * b + b) / 2;  T[2][2] = a * b / 4;
+  double w[9];
+  flux_ds_weights<double>(a, b, w);
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) T[r][q] = w[r * 3 + q];
 }
 
 // Interface weight tables of one stage (interface step h, flux factor fac).
@@ -662,6 +664,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
   alloc(&c->fbx, nfx);
   alloc(&c->fby, nfy);
   alloc(&c->mom, 3 * (size_t)p.N);
+  alloc(&c->mom_aux, 3 * (size_t)p.N);
   if (c->groups > 1) {          // large velocity sets: interior-face kernels of dugks_nc.cu
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
@@ -825,16 +828,15 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
         e = cudaMemcpy(c->vf, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
       }
     }
-    // FP64: the quadratic Taylor weights of the upwind expansions per stage,
+    // FP64: the face-value weights of the upwind expansions per stage,
     // direction and velocity (lower cell, upper cell), central differences
     // on the 3x3 neighbourhood, foot offset (a dx, b dy) (eq. flux_DS)
     if (e == cudaSuccess && f64) {
       std::vector<double> w(4 * (size_t)nv * 18);
       auto taylor = [](double a, double b, double* T) {
-        const double ab = 0.25 * a * b;
-        T[0] = ab;                T[1] = 0.5 * (b * b - b); T[2] = -ab;
-        T[3] = 0.5 * (a * a - a); T[4] = 1.0 - a * a - b * b; T[5] = 0.5 * (a * a + a);
-        T[6] = -ab;               T[7] = 0.5 * (b * b + b); T[8] = ab;
+        double w[9];
+        flux_ds_weights<double>(a, b, w);
+        for (int q = 0; q < 9; ++q) T[q] = w[q];
       };
       for (int st = 0; st < 2; ++st) {
         const double h = st == 0 ? c->s1.h : c->s2.h;
@@ -1002,8 +1004,29 @@ int dugks_set_state(dugks_ctx* c, const double* fhat, int on_device) {
   return rc;
 }
 
-int dugks_get_state(dugks_ctx* c, double* fhat, int on_device) {
+int dugks_get_state(dugks_ctx* c, double* fhat, int which, int on_device) {
   if (!c || !fhat) return fail(DUGKS_EINVAL, "NULL argument");
+  if (which != DUGKS_STATE_SCHEME && which != DUGKS_STATE_F)
+    return fail(DUGKS_EINVAL, "which must be DUGKS_STATE_SCHEME or DUGKS_STATE_F");
+  if (which == DUGKS_STATE_F) {
+    // f from the scheme's variable x = f - c dt Omega(f): f = (tau x + c dt
+    // feq)/(tau + c dt) with c = 1/4 (T3S3, eq. feqIntD3rdHat2) or 1/2 (T2,
+    // eq. feqIntD2nd_Explicit); feq from the moments of x (the collision
+    // conserves them)
+    const double cdt = (c->scheme == DUGKS_T3S3 ? 0.25 : 0.5) * c->p.dt;
+    const double a = c->p.tau / (c->p.tau + cdt), b = cdt / (c->p.tau + cdt);
+    const double* src = c->fhat;
+    if (c->store) {
+      TRY(launch(c, K_CONVERT, [&] { return launch_f64_from_dev(c->p, c->store, c->rho0, c->fhat, c->fbx, c->stream); }));
+      src = c->fbx;
+    }
+    double* dst = on_device ? fhat : c->fby;
+    TRY(launch(c, K_MOMENTS, [&] {
+      return launch_cell(c->p, c->groups, 1, src, dst, c->mom_aux, a, b, c->stream);
+    }));
+    if (on_device) return DUGKS_OK;
+    return copy_out(c, fhat, c->fby, (size_t)c->p.nv * c->p.N, 0);
+  }
   if (c->store) {
     double* dst = on_device ? fhat : c->fbx;
     TRY(launch(c, K_CONVERT, [&] { return launch_f64_from_dev(c->p, c->store, c->rho0, c->fhat, dst, c->stream); }));

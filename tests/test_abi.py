@@ -98,3 +98,13 @@ def test_set_scheme_needs_a_context(lib):
     with pytest.raises(P.DugksError) as e:
         P.dugks_set_scheme(None, P.T2S2)
     assert e.value.code == P.DUGKS_EINVAL
+
+
+def test_alu_peak_rejects_bad_arguments_on_the_host(lib):
+    """Argument checks run before any CUDA call (no GPU needed)."""
+    import ctypes as C
+    fl, ms = C.c_double(0.0), C.c_float(0.0)
+    for kind, iters, bps in ((3, 10, 4), (0, 0, 4), (0, 10, 0), (0, 10, 33)):
+        rc = lib.dugks_alu_peak(kind, iters, bps, C.c_void_p(1), 1 << 20, C.byref(fl),
+                                C.byref(ms), None)
+        assert rc == P.DUGKS_EINVAL

@@ -1,7 +1,7 @@
 """Host logic of bench.py without a GPU: the max-over-ranks reduction of the
 multi-rank (torchrun, one replica per rank) path on two gloo ranks, the
-whole-job rate, and the reference arm's JSON line (the oracle on one
-host core; other ranks exit without output)."""
+whole-job rate, and the reference arm's JSON line (the oracle on every
+host core, one spawned process each; other ranks exit without output)."""
 import json
 import os
 import socket
@@ -85,7 +85,9 @@ def test_reference_arm_line():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference"
     assert line["value"] > 0 and line["unit"] == "G updates/s"
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["cores"] == (os.cpu_count() or 1)
+    assert line["cpu_baseline"]["cpu_model"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     assert line["config"]["workload"] == "cavity256"
 

@@ -237,3 +237,37 @@ def test_fused_d2q9_matches_generic_path(cuda, monkeypatch, bcname):
     fo = O.t3s3_run(f0, o, 6)
     assert rel_linf(out["0"], fo) <= TOL
     assert rel_linf(out["1"], fo) <= TOL
+
+
+@pytest.mark.parametrize("form", ["fp64_fused", "fp64_nc", "fp32_fused", "t2s3"])
+def test_get_state_of_f(cuda, form):
+    """dugks_get_state(which = DUGKS_STATE_F) returns the distribution f
+    itself: f = (4 tau f^ + dt feq)/(4 tau + dt) under T3S3 and
+    (2 tau f~ + dt feq)/(2 tau + dt) under a T2 scheme (feq of the state's
+    moments), against the oracle's conversion of its own state."""
+    nx, ny = 37, 23
+    bc = [(P.BOUNCEBACK, 0, 0)] * 3 + [(P.BOUNCEBACK, 0.05, 0)]
+    if form == "fp64_nc":
+        g, o = pair(nx, ny, 8, 0.5, 0.05, 0.004,
+                    [(P.DIFFUSE, 0, 0)] * 3 + [(P.DIFFUSE, 0.1, 0)])
+    else:
+        g, o = pair(nx, ny, "d2q9", 1 / 3, 0.003, 0.006, bc)
+        if form == "fp32_fused":
+            g.close()
+            pg = PV.d2q9(1 / 3)
+            g = P.Solver(nx, ny, 1 / nx, 1 / ny, *pg, 0.003, 0.006, bc, storage=P.G_FP32)
+        elif form == "t2s3":
+            P.dugks_set_scheme(g.ctx, P.T2S3)
+    f0 = WL.near_equilibrium_state(o.W, ny, nx, amp=0.1, seed=8)
+    g.set_state(f0)
+    g.step(2)
+    x = g.state()
+    f = g.state(which=P.STATE_F)
+    feq, _ = O.equilibrium_of(x, o)
+    cdt = (0.5 if form == "t2s3" else 0.25) * o.dt
+    fo = (o.tau * x + cdt * feq) / (o.tau + cdt)
+    assert rel_linf(f, fo) <= TOL
+    if form == "fp64_fused":
+        fs = O.t3s3_run(f0, o, 2)
+        assert rel_linf(f, O.f_from_fhat(fs, o)) <= TOL
+    g.close()
