@@ -189,13 +189,13 @@ def dugks_profile(ctx, enable=True):
 def dugks_profile_read(ctx):
     """{kernel name: (launches, total ms)} since profiling was enabled."""
     lib = load()
-    n = 32
+    n = 128
     la = (C.c_longlong * n)()
     ms = (C.c_double * n)()
     k = lib.dugks_profile_read(ctx, la, ms, n)
     if k < 0:
         _check(k)
-    return {lib.dugks_kernel_name(i).decode(): (int(la[i]), float(ms[i])) for i in range(k)}
+    return {lib.dugks_kernel_name(i).decode(): (int(la[i]), float(ms[i])) for i in range(min(k, n))}
 
 
 def dugks_destroy(ctx):

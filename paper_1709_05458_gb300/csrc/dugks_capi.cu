@@ -38,7 +38,8 @@ const char* kNames[K_NUM] = {
     "d2q9m_stage1", "d2q9m_stage2", "convert",
     "gdev_cell", "gdev_face_x", "gdev_face_y", "gdev_walls", "gdev_update_stage1",
     "gdev_update_stage2", "t2_cell", "t2_face_x", "t2_face_y", "t2_update",
-    "d2q9dw_stage1", "d2q9dw_stage2"};
+    "d2q9dw_stage1", "d2q9dw_stage2", "gnc_moments", "gnc_faces", "gnc_walls", "gnc_facefin",
+    "gnc_update_stage1", "gnc_update_stage2"};
 
 struct Pending {
   int id;
@@ -90,6 +91,14 @@ struct dugks_ctx {
   bool gdev = false;
   GDevStep gs{};
   void* eqp = nullptr;
+  // the staged-tile generic path (dugks_gnc.cu), which steps every generic
+  // context: its step descriptor and the buffers it adds to those above
+  bool gnc = false;
+  GncStep gn{};
+  void* gn_eq2 = nullptr;       // equilibrium parameters at t' [5][N]
+  double* gn_mom2 = nullptr;    // rho, u at t' [3][N]
+  void* gn_wf = nullptr;        // wall faces' f-bar
+  double* gn_part = nullptr;    // partial moments
   void* vf = nullptr;           // velocity table of that path (4-vector rows [3][nv])
   void* gpad = nullptr;         // padded stage field of that path
   void* fpar = nullptr;         // face equilibrium parameters of that path
@@ -220,6 +229,10 @@ void free_all(dugks_ctx* c) {
   if (c->gpad) cudaFree(c->gpad);
   if (c->fpar) cudaFree(c->fpar);
   if (c->twt) cudaFree(c->twt);
+  if (c->gn_eq2) cudaFree(c->gn_eq2);
+  if (c->gn_mom2) cudaFree(c->gn_mom2);
+  if (c->gn_wf) cudaFree(c->gn_wf);
+  if (c->gn_part) cudaFree(c->gn_part);
   for (auto& q : c->pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -403,6 +416,27 @@ int one_step_gdev(dugks_ctx* c) {
   return DUGKS_OK;
 }
 
+// The staged-tile generic path: per stage the face moments, the wall faces,
+// the face parameters and the update with its cell moments; the cell
+// moments of a new state first.
+int one_step_gnc(dugks_ctx* c) {
+  const GncStep& g = c->gn;
+  cudaStream_t s = c->stream;
+  if (!c->g1_valid) {
+    TRY(launch(c, K_GNC_MOMENTS, [&] { return launch_gnc_moments(g, s); }));
+    c->g1_valid = true;
+  }
+  const bool walls = !(c->p.px && c->p.py);
+  for (int stage = 1; stage <= 2; ++stage) {
+    TRY(launch(c, K_GNC_FACES, [&] { return launch_gnc_faces(g, stage, s); }));
+    if (walls) TRY(launch(c, K_GNC_WALLS, [&] { return launch_gnc_walls(g, stage, s); }));
+    TRY(launch(c, K_GNC_FACEFIN, [&] { return launch_gnc_facefin(g, s); }));
+    TRY(launch(c, stage == 1 ? K_GNC_UPDATE1 : K_GNC_UPDATE2,
+               [&] { return launch_gnc_update(g, stage, s); }));
+  }
+  return DUGKS_OK;
+}
+
 // One T2 step of size dt (Remark I, eq. feqIntD2nd_Explicit with Q7) on the
 // generic kernels: g = f-bar^{+,dt/2} from f~, faces at t_n + dt/2 with the
 // quadratic (T2S3) or first-order (T2S2) expansion, f~^{n+1} = f~^+ + dt L.
@@ -421,6 +455,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 int advance(dugks_ctx* c) {
   if (c->scheme != DUGKS_T3S3) return one_step_t2(c);
+  if (c->gnc) return one_step_gnc(c);
   if (c->gdev) return one_step_gdev(c);
   if (c->store) return one_step_d2q9m(c);
   return c->d2q9 ? one_step_d2q9(c) : one_step(c);
@@ -428,6 +463,11 @@ int advance(dugks_ctx* c) {
 
 // g1 of the current state for the fused paths (run eagerly before capture)
 int ensure_g1(dugks_ctx* c) {
+  if (c->gnc && !c->g1_valid && c->scheme == DUGKS_T3S3) {
+    TRY(launch(c, K_GNC_MOMENTS, [&] { return launch_gnc_moments(c->gn, c->stream); }));
+    c->g1_valid = true;
+    return DUGKS_OK;
+  }
   if (!c->d2q9 || c->g1_valid) return DUGKS_OK;
   cudaStream_t s = c->stream;
   if (c->store)
@@ -791,7 +831,14 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, (size_t)pch * 3 * nfmax * sizeof(double));
     g.pitch = gdev_pitch(p.nx);
     g.plane = (size_t)(p.ny + 4) * g.pitch;
-    if (e == cudaSuccess) e = cudaMalloc(&c->gpad, g.plane * nv * csz);
+    // The deviation forms take the staged-tile path (below), which forms the
+    // stage field and the face values on chip and moves about 28 bytes of the
+    // stored type per update: they are bound by bytes and instruction issue.
+    // FP64 storage is bound by the 2-lane FP64 pipe instead, and keeps the
+    // kernels of this file, which store g and the face values but need about
+    // 160 FP64 flops per update against about 365 for the recomputing path.
+    const bool use_gnc = !f64;
+    if (e == cudaSuccess && !use_gnc) e = cudaMalloc(&c->gpad, g.plane * nv * csz);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->eqp, 5 * (size_t)p.N * csz);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->fpar, 5 * 2 * nfmax * csz);
     // velocity table in the compute type, 4-vector rows [3][nv]:
@@ -877,6 +924,53 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     g.vq = c->vf;
     g.mom = c->mom;
     g.part = c->part;
+    if (use_gnc) {
+      // the staged-tile path: its descriptor shares the velocity table, the
+      // t_n parameters and moments and the face parameters with the above
+      GncStep& n = c->gn;
+      n.p = c->p;
+      n.ref = g.ref;
+      n.store = storage;
+      n.s1 = c->s1;
+      n.s2 = c->s2;
+      n.c_om = c->c_om;
+      n.fhat = c->fhat;
+      n.ftp = c->ftp;
+      n.eqn = c->eqp;
+      n.mom_n = c->mom;
+      n.fpx = c->fpar;
+      n.fpy = (char*)c->fpar + 5 * nfmax * csz;
+      n.vq = c->vf;
+      for (int sd = 0; sd < 4; ++sd) n.ds_out[sd] = g.ds_out[sd];
+      n.tiles_x = (p.nx + 31) / 32;
+      n.tiles_y = (p.ny + 15) / 16;
+      n.nch = gnc_chunks(p, sms);
+      n.kc = (nv + n.nch - 1) / n.nch;
+      n.nch = (nv + n.kc - 1) / n.kc;
+      const size_t nfx1 = (size_t)p.ny * (p.nx + 1), nfy1 = (size_t)(p.ny + 1) * p.nx;
+      const size_t nwall = (size_t)nv * 2 * (p.nx + p.ny);
+      if (e == cudaSuccess) e = cudaMalloc(&c->gn_eq2, 5 * (size_t)p.N * csz);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&c->gn_mom2, 3 * (size_t)p.N * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&c->gn_wf, nwall * csz);
+      if (e == cudaSuccess)
+        e = cudaMalloc((void**)&c->gn_part, (size_t)n.nch * 3 * (nfx1 + nfy1 + p.N) * sizeof(double));
+      if (e == cudaSuccess) e = gnc_prepare(storage);
+      if (e != cudaSuccess) {
+        free_all(c);
+        delete c;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? DUGKS_ENOMEM : DUGKS_ECUDA,
+                    std::string("staged-tile path set-up: ") + cudaGetErrorString(e));
+      }
+      n.eqp = c->gn_eq2;
+      n.mom_p = c->gn_mom2;
+      n.wfx = c->gn_wf;
+      n.wfy = (char*)c->gn_wf + (size_t)nv * 2 * p.ny * csz;
+      n.pfx = c->gn_part;
+      n.pfy = n.pfx + (size_t)n.nch * 3 * nfx1;
+      n.pc = n.pfy + (size_t)n.nch * 3 * nfy1;
+      c->gnc = true;
+    }
     c->store = storage;
     c->gdev = true;
   }
@@ -1045,18 +1139,21 @@ int dugks_step(dugks_ctx* c, int n) {
 
 int dugks_moments(dugks_ctx* c, double* rho, double* ux, double* uy, int on_device) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
+  // the staged-tile path keeps the state's moments from its last update in
+  // c->mom (the next step's walls read them): compute into the aside buffer
+  double* mom = c->gnc ? c->mom_aux : c->mom;
   TRY(launch(c, K_MOMENTS, [&] {
     if (c->store)
-      return launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, c->mom, 0.0, 0.0, 0, c->stream);
-    if (c->d2q9) return launch_d2q9_cell(c->dp, false, c->fhat, nullptr, c->mom, c->stream);
-    return launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
+      return launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, mom, 0.0, 0.0, 0, c->stream);
+    if (c->d2q9) return launch_d2q9_cell(c->dp, false, c->fhat, nullptr, mom, c->stream);
+    return launch_cell(c->p, c->groups, 0, c->fhat, nullptr, mom, 0.0, 0.0, c->stream);
   }));
   // the three copies are queued on the stream; one synchronisation for host buffers
   const size_t N = c->p.N;
   double* dst[3] = {rho, ux, uy};
   for (int m = 0; m < 3; ++m) {
     if (!dst[m]) continue;
-    cudaError_t e = cudaMemcpyAsync(dst[m], c->mom + m * N, N * sizeof(double),
+    cudaError_t e = cudaMemcpyAsync(dst[m], mom + m * N, N * sizeof(double),
                                     on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                     c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "copy from device");
@@ -1072,11 +1169,12 @@ int dugks_check(dugks_ctx* c) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
   cudaError_t e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "dugks_check");
+  double* mom = c->gnc ? c->mom_aux : c->mom;
   TRY(launch(c, K_MOMENTS, [&] {
-    return c->store ? launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, c->mom, 0.0, 0.0, 0, c->stream)
-                    : launch_cell(c->p, c->groups, 0, c->fhat, nullptr, c->mom, 0.0, 0.0, c->stream);
+    return c->store ? launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, mom, 0.0, 0.0, 0, c->stream)
+                    : launch_cell(c->p, c->groups, 0, c->fhat, nullptr, mom, 0.0, 0.0, c->stream);
   }));
-  TRY(launch(c, K_CHECK, [&] { return launch_check(c->p, c->mom, c->flag, c->stream); }));
+  TRY(launch(c, K_CHECK, [&] { return launch_check(c->p, mom, c->flag, c->stream); }));
   int h = 0;
   e = cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

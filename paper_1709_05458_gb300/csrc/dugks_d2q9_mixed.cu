@@ -53,6 +53,7 @@ struct MixedConst {
   float bb[4][9];       // bounce-back: rho_w * bb + (W_opp - W_k) rho0
   float bbc[4][9];
   float r37, com, a1, b1, a2, b2;   // FP32 copies of the stage coefficients
+  float c3f, base_divf;             // FP32 copies of c^2/RT and 1/(2 c^2/RT)
 };
 
 template <int K> struct Vel {
@@ -137,6 +138,62 @@ __device__ __forceinline__ void dev_sums(const float (&d)[9], const MixedConst& 
   sy = fix2d(y + M.fsyW);
 }
 
+
+// fixed point (56 fraction bits) -> FP32, round to nearest, integer pipe only
+__device__ __forceinline__ float fix2f(long long v) {
+  const unsigned s = v < 0 ? 0x80000000u : 0u;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll((long long)a);
+  const unsigned long long n = a << (lz & 63);    // leading one at bit 63
+  const unsigned bits = ((unsigned)(127 + 7 - lz) << 23) + (unsigned)((n >> 40) & 0x7fffffull) +
+                        (unsigned)((n >> 39) & 1ull);
+  return __uint_as_float(a == 0 ? 0u : (bits | s));
+}
+
+// The face moments of f-bar rounded once to FP32 (the sums themselves are
+// exact, as in dev_sums); a NaN density marks a deviation beyond the range.
+__device__ __forceinline__ void dev_sums_f(const float (&d)[9], const MixedConst& M, float& rho,
+                                           float& dr, float& sx, float& sy) {
+  unsigned bad = 0u;
+  long long v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = f2fix(d[k], bad);
+  const long long a = v[0] + v[1] + v[2];
+  const long long b = v[6] + v[7] + v[8];
+  const long long r = a + b + (v[3] + v[4] + v[5]);
+  const long long y = (v[2] + v[5] + v[8]) - (v[0] + v[3] + v[6]);
+  rho = bad ? __uint_as_float(0x7fc00000u) : fix2f(r + M.fr0W);
+  dr = fix2f(r + M.fdr0);
+  sx = fix2f(b - a + M.fsxW);
+  sy = fix2f(y + M.fsyW);
+}
+
+// Face equilibrium deviations W_k (rho P_k - rho0) in FP32 from the FP32
+// moments: 1/rho from the hardware reciprocal approximation refined by one
+// Newton step (relative error ~2^-23), u/RT and the constant part in FP32.
+// The per-velocity assembly is FP32 in either form; its parameters here
+// carry a few units in the last place of FP32 instead of one rounding.
+__device__ __forceinline__ void dev_feq_f(float rho, float dr, float sx, float sy,
+                                          const MixedConst& M, float (&fe)[9]) {
+  float rr;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rr) : "f"(rho));
+  rr = fmaf(rr, fmaf(-rho, rr, 1.0f), rr);
+  const float rc = M.c3f * rr;
+  const float ux = sx * rc, uy = sy * rc;
+  const float b1 = -fmaf(ux, ux, uy * uy) * M.base_divf;
+  const float r = rho;
+  const float sp = ux + uy, sm = ux - uy;
+  float p1[9];                                                  // P_k - 1
+  p1[4] = b1;
+  const float bx = fmaf(0.5f * ux, ux, b1), by = fmaf(0.5f * uy, uy, b1);
+  const float bs = fmaf(0.5f * sp, sp, b1), bd = fmaf(0.5f * sm, sm, b1);
+  p1[7] = bx + ux; p1[1] = bx - ux;
+  p1[5] = by + uy; p1[3] = by - uy;
+  p1[8] = bs + sp; p1[0] = bs - sp;
+  p1[6] = bd + sm; p1[2] = bd - sm;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) fe[k] = M.W[k] * fmaf(r, p1[k], dr);
+}
 
 // Equilibrium deviations W_k (rho P_k - rho0) from FP64 moments: u/RT and the
 // constant part in FP64, per-velocity assembly in FP32.
@@ -236,10 +293,11 @@ __device__ __forceinline__ void wall_dev(float (&fb)[9], const float* __restrict
 template <int DIR>
 __device__ __forceinline__ void face_recover_dev(float (&fb)[9], const D2Q9StageF& S,
                                                  const D2Q9Params& P, const MixedConst& M) {
-  double rho, dr, sx, sy;
-  dev_sums(fb, M, rho, dr, sx, sy);
+  float rho, dr, sx, sy;
+  dev_sums_f(fb, M, rho, dr, sx, sy);
   float fe[9];
-  dev_feq(rho, dr, sx, sy, P, M, fe);
+  dev_feq_f(rho, dr, sx, sy, M, fe);
+  (void)P;
 #pragma unroll
   for (int k = 0; k < 9; ++k)
     if (DIR == 0 ? (k / 3 != 1) : (k % 3 != 1)) fb[k] = fmaf(S.gamma, fe[k], fb[k]);
@@ -520,6 +578,8 @@ MixedConst mixed_const(const D2Q9Params& P, double rho0) {
   M.fdr0 = llrint(std::ldexp(rho0 * (sw - 1.0), 56));
   M.fsxW = llrint(std::ldexp(rho0 * sxp, 56));
   M.fsyW = llrint(std::ldexp(rho0 * syp, 56));
+  M.c3f = (float)P.c3;
+  M.base_divf = (float)P.base_div;
   M.r37 = (float)P.r37;
   M.com = (float)P.c_om34;
   M.a1 = (float)P.a1;

@@ -58,6 +58,12 @@ enum KernelId {
   K_T2_UPDATE,         // f~^{n+1} = f~^{+,n} + dt L
   K_D2Q9DW_STAGE1,     // fused D2Q9 path in double-word arithmetic, stage 1
   K_D2Q9DW_STAGE2,     // stage 2
+  K_GNC_MOMENTS,       // staged-tile generic path: cell moments of a new state
+  K_GNC_FACES,         // face moments of a stage (both directions)
+  K_GNC_WALLS,         // wall faces of a stage
+  K_GNC_FACEFIN,       // face equilibrium parameters
+  K_GNC_UPDATE1,       // f~(t') and its cell moments
+  K_GNC_UPDATE2,       // f^^{n+1} and its cell moments
   K_NUM
 };
 
@@ -192,6 +198,40 @@ cudaError_t launch_gdev_cell(const GDevStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_t st);
 cudaError_t launch_gdev_walls(const GDevStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gdev_update(const GDevStep& s, int stage, cudaStream_t st);
+
+// Staged-tile stage kernels for any velocity set (dugks_gnc.cu), in the three
+// storage forms of GDevStep.  Per stage: a face pass reduces the interface
+// moments of a velocity chunk (the stage field g and the face values are
+// formed in shared memory from the stored state and never stored), a wall
+// pass forms the wall faces, two small passes finalise face and cell
+// moments, and an update pass recomputes the four face values of every cell
+// from the same staged tile and writes the stage's output with its cell
+// moments.  Arrays per (cell, velocity) are [nv][ny][nx] of the storage
+// type; parameters [5][n] of the compute type; partial moments FP64.
+struct GncStep {
+  DevParams p;
+  GDevRef ref;
+  int store;                    // 0 FP64, 1 FP32, 2 BF16
+  StageCoef s1, s2;
+  double c_om;
+  void *fhat, *ftp;             // state f^ and f~(t')
+  void *eqn, *eqp;              // cell equilibrium parameters of f^ (t_n) and of f~' (t')
+  double *mom_n, *mom_p;        // rho, ux, uy [3][N] at t_n and t'
+  void *fpx, *fpy;              // face parameters [5][nf] (interior faces and walls)
+  void *wfx, *wfy;              // wall faces' f-bar [nv][2][ny] (W, E) and [nv][2][nx] (S, N)
+  double *pfx, *pfy, *pc;       // partial moments [nch][3][nfx], [nch][3][nfy], [nch][3][N]
+  const void* vq;               // velocity table of GDevStep::vq
+  int nch, kc;                  // velocity chunks and velocities per chunk
+  int tiles_x, tiles_y;         // 32 x 16 cell tiles
+  double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
+};
+int gnc_chunks(const DevParams& p, int sms);
+cudaError_t gnc_prepare(int store);
+cudaError_t launch_gnc_moments(const GncStep& s, cudaStream_t st);   // cell moments of f^ -> t_n
+cudaError_t launch_gnc_faces(const GncStep& s, int stage, cudaStream_t st);
+cudaError_t launch_gnc_walls(const GncStep& s, int stage, cudaStream_t st);
+cudaError_t launch_gnc_facefin(const GncStep& s, cudaStream_t st);
+cudaError_t launch_gnc_update(const GncStep& s, int stage, cudaStream_t st);
 
 // One instance of a batched D2Q9 FP64 launch (device memory).
 struct D2Q9BatchItem {

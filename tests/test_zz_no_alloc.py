@@ -128,13 +128,21 @@ def test_static_refuses_a_capturing_stream(cuda):
     xi, W, RT = PV.d2q9(1 / 3)
     bc = [(P.PERIODIC, 0, 0)] * 4
     f = torch.zeros((9, ny, nx), dtype=torch.float64, device="cuda")
+    import gc
     s = torch.cuda.Stream()
     P.dugks_step_static(nx, ny, 1 / nx, 1 / ny, xi, W, RT, 0.01, 0.01, bc, f, f, 0, stream=s)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
-    with pytest.raises(P.DugksError) as e:
-        with torch.cuda.graph(g, stream=s):
-            P.dugks_step_static(nx, ny, 1 / nx, 1 / ny, xi, W, RT, 0.01, 0.01, bc, f, f, 1,
-                                stream=s)
+    # no garbage collection during the capture: a collected object of an
+    # earlier test (a solver freeing its buffers) would invalidate it
+    gc.collect()
+    gc.disable()
+    try:
+        with pytest.raises(P.DugksError) as e:
+            with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+                P.dugks_step_static(nx, ny, 1 / nx, 1 / ny, xi, W, RT, 0.01, 0.01, bc, f, f, 1,
+                                    stream=s)
+    finally:
+        gc.enable()
     assert e.value.code == P.DUGKS_EINVAL and "capturing" in str(e.value)
     torch.cuda.synchronize()
