@@ -99,6 +99,7 @@ struct dugks_ctx {
   double* gn_mom2 = nullptr;    // rho, u at t' [3][N]
   void* gn_wf = nullptr;        // wall faces' f-bar
   double* gn_part = nullptr;    // partial moments
+  float* gn_fwt = nullptr;      // face-value weights per stage and velocity
   void* vf = nullptr;           // velocity table of that path (4-vector rows [3][nv])
   void* gpad = nullptr;         // padded stage field of that path
   void* fpar = nullptr;         // face equilibrium parameters of that path
@@ -233,6 +234,7 @@ void free_all(dugks_ctx* c) {
   if (c->gn_mom2) cudaFree(c->gn_mom2);
   if (c->gn_wf) cudaFree(c->gn_wf);
   if (c->gn_part) cudaFree(c->gn_part);
+  if (c->gn_fwt) cudaFree(c->gn_fwt);
   for (auto& q : c->pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -954,6 +956,13 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
       if (e == cudaSuccess) e = cudaMalloc(&c->gn_wf, nwall * csz);
       if (e == cudaSuccess)
         e = cudaMalloc((void**)&c->gn_part, (size_t)n.nch * 3 * (nfx1 + nfy1 + p.N) * sizeof(double));
+      if (e == cudaSuccess) {
+        std::vector<float> wt(2 * (size_t)nv * 48);
+        gnc_weight_table(p, vel->xi_x, vel->xi_y, c->s1, c->s2, wt.data());
+        e = cudaMalloc((void**)&c->gn_fwt, wt.size() * sizeof(float));
+        if (e == cudaSuccess)
+          e = cudaMemcpy(c->gn_fwt, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice);
+      }
       if (e == cudaSuccess) e = gnc_prepare(storage);
       if (e != cudaSuccess) {
         free_all(c);
@@ -962,6 +971,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
         return fail(e == cudaErrorMemoryAllocation ? DUGKS_ENOMEM : DUGKS_ECUDA,
                     std::string("staged-tile path set-up: ") + cudaGetErrorString(e));
       }
+      n.fwt = c->gn_fwt;
       n.eqp = c->gn_eq2;
       n.mom_p = c->gn_mom2;
       n.wfx = c->gn_wf;

@@ -117,6 +117,21 @@ __device__ __forceinline__ void acc_addprod_acc(Acc<double>& a, double xh, doubl
   a.s = fma(xh, b.s, a.s);
 }
 
+// Kahan-compensated FP32 sum (Kahan 1965): s is the running sum, c the
+// negated low-order part lost by the last addition.  Four operations per
+// term; a product x xi is rounded once before it is added (relative 2^-24,
+// the level of the FP32 values it weighs).  The value is s - c in FP64.
+struct Kah {
+  float s, c;
+};
+__device__ __forceinline__ void kah_add(Kah& a, float x) {
+  const float y = __fsub_rn(x, a.c);
+  const float t = __fadd_rn(a.s, y);
+  a.c = __fsub_rn(__fsub_rn(t, a.s), y);
+  a.s = t;
+}
+__device__ __forceinline__ double kah_value(const Kah& a) { return to_d(a.s) - to_d(a.c); }
+
 // ---- equilibrium ----
 // assembly parameters of one cell or face
 template <typename C> struct EqF {

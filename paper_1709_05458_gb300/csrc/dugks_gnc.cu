@@ -79,44 +79,97 @@ __device__ __forceinline__ C dot9(const C (&T)[9], C s00, C s01, C s02, C s10, C
   W[(y) - 1][(x) - 1], W[(y) - 1][(x)], W[(y) - 1][(x) + 1], W[(y)][(x) - 1], W[(y)][(x)], \
       W[(y)][(x) + 1], W[(y) + 1][(x) - 1], W[(y) + 1][(x)], W[(y) + 1][(x) + 1]
 
-// Per-velocity face-value weights (eq. flux_DS as printed): x-faces about
-// the lower (left) and upper (right) cell, y-faces about the lower (below)
-// and upper cell; the sign of xi.n picks one, a tie averages both (Q4).
-template <typename C>
+// Per-velocity face-value weights (eq. flux_DS as printed), formed on the
+// host per stage and velocity (gnc_weight_table) and read by every block for
+// its chunk into shared memory: x-faces about the lower (left) and upper
+// (right) cell, y-faces about the lower (below) and upper cell, each nine
+// weights padded to twelve for 16-byte reads.  The sign of xi.n picks one
+// set; a tie averages both (Q4).
+constexpr int KCMAX = 128;            // velocities per chunk at most
+constexpr int WPV = 48;               // weights per velocity in the table
 struct FaceW {
-  C xl[9], xu[9], yl[9], yu[9];
-  int sx, sy;                      // sign of xi_x, xi_y
+  float x[9], y[9];                   // the set each direction's sign picks
+  const float* row;                   // the velocity's row of the table (ties)
+  int sx, sy;                         // sign of xi_x, xi_y
 };
-template <typename C>
-__device__ __forceinline__ void face_weights(FaceW<C>& w, C cx, C cy, C h, C idx, C idy) {
-  const C ax = -cx * h * idx, by = -cy * h * idy;
-  w.sx = cx > C(0) ? 1 : (cx < C(0) ? -1 : 0);
-  w.sy = cy > C(0) ? 1 : (cy < C(0) ? -1 : 0);
-  if (w.sx >= 0) flux_ds_weights<C>(C(0.5) + ax, by, w.xl);
-  if (w.sx <= 0) flux_ds_weights<C>(C(-0.5) + ax, by, w.xu);
-  if (w.sy >= 0) flux_ds_weights<C>(ax, C(0.5) + by, w.yl);
-  if (w.sy <= 0) flux_ds_weights<C>(ax, C(-0.5) + by, w.yu);
+__device__ __forceinline__ void read9(const float* __restrict__ w, float (&T)[9]) {
+  const float4 a = *reinterpret_cast<const float4*>(w);
+  const float4 b = *reinterpret_cast<const float4*>(w + 4);
+  T[0] = a.x; T[1] = a.y; T[2] = a.z; T[3] = a.w;
+  T[4] = b.x; T[5] = b.y; T[6] = b.z; T[7] = b.w;
+  T[8] = w[8];
+}
+__device__ __forceinline__ void face_weights(FaceW& w, const float* __restrict__ row, float cx,
+                                             float cy) {
+  w.row = row;
+  w.sx = cx > 0.f ? 1 : (cx < 0.f ? -1 : 0);
+  w.sy = cy > 0.f ? 1 : (cy < 0.f ? -1 : 0);
+  read9(row + (w.sx >= 0 ? 0 : 12), w.x);
+  read9(row + (w.sy >= 0 ? 24 : 36), w.y);
 }
 
 // x-face value between the cells centred at window columns xl and xl + 1
-// (row y); y-face value between window rows yl and yl + 1 (column x)
-template <typename C, int NR, int NC>
-__device__ __forceinline__ C xface(const FaceW<C>& w, const C (&W)[NR][NC], int xl, int y) {
-  if (w.sx > 0) return dot9(w.xl, STEN(W, xl, y));
-  if (w.sx < 0) return dot9(w.xu, STEN(W, xl + 1, y));
-  return C(0.5) * (dot9(w.xl, STEN(W, xl, y)) + dot9(w.xu, STEN(W, xl + 1, y)));
+// (row y); y-face value between window rows yl and yl + 1 (column x); a tie
+// averages the expansions from both cells (Q4)
+template <int NR, int NC>
+__device__ __forceinline__ float xface(const FaceW& w, const float (&W)[NR][NC], int xl, int y) {
+  if (w.sx > 0) return dot9(w.x, STEN(W, xl, y));
+  if (w.sx < 0) return dot9(w.x, STEN(W, xl + 1, y));
+  float u[9];
+  read9(w.row + 12, u);
+  return 0.5f * (dot9(w.x, STEN(W, xl, y)) + dot9(u, STEN(W, xl + 1, y)));
 }
-template <typename C, int NR, int NC>
-__device__ __forceinline__ C yface(const FaceW<C>& w, const C (&W)[NR][NC], int x, int yl) {
-  if (w.sy > 0) return dot9(w.yl, STEN(W, x, yl));
-  if (w.sy < 0) return dot9(w.yu, STEN(W, x, yl + 1));
-  return C(0.5) * (dot9(w.yl, STEN(W, x, yl)) + dot9(w.yu, STEN(W, x, yl + 1)));
+template <int NR, int NC>
+__device__ __forceinline__ float yface(const FaceW& w, const float (&W)[NR][NC], int x, int yl) {
+  if (w.sy > 0) return dot9(w.y, STEN(W, x, yl));
+  if (w.sy < 0) return dot9(w.y, STEN(W, x, yl + 1));
+  float u[9];
+  read9(w.row + 36, u);
+  return 0.5f * (dot9(w.y, STEN(W, x, yl)) + dot9(u, STEN(W, x, yl + 1)));
+}
+// the same from the staged plane directly: x-face left of staged column cx
+// (staged row cy), y-face below staged row cy (staged column cx)
+__device__ __forceinline__ float stencil_at(const float* __restrict__ g, const float (&T)[9], int cx,
+                                            int cy) {
+  const float* b = g + (cy - 1) * HXT + cx - 1;
+  float v = T[0] * b[0];
+  v = fmaf(T[1], b[1], v);
+  v = fmaf(T[2], b[2], v);
+  v = fmaf(T[3], b[HXT], v);
+  v = fmaf(T[4], b[HXT + 1], v);
+  v = fmaf(T[5], b[HXT + 2], v);
+  v = fmaf(T[6], b[2 * HXT], v);
+  v = fmaf(T[7], b[2 * HXT + 1], v);
+  return fmaf(T[8], b[2 * HXT + 2], v);
+}
+__device__ __forceinline__ float xface_at(const FaceW& w, const float* __restrict__ g, int cx,
+                                          int cy) {
+  if (w.sx > 0) return stencil_at(g, w.x, cx - 1, cy);
+  if (w.sx < 0) return stencil_at(g, w.x, cx, cy);
+  float u[9];
+  read9(w.row + 12, u);
+  return 0.5f * (stencil_at(g, w.x, cx - 1, cy) + stencil_at(g, u, cx, cy));
+}
+__device__ __forceinline__ float yface_at(const FaceW& w, const float* __restrict__ g, int cx,
+                                          int cy) {
+  if (w.sy > 0) return stencil_at(g, w.y, cx, cy - 1);
+  if (w.sy < 0) return stencil_at(g, w.y, cx, cy);
+  float u[9];
+  read9(w.row + 36, u);
+  return 0.5f * (stencil_at(g, w.y, cx, cy - 1) + stencil_at(g, u, cx, cy));
+}
+
+// the chunk's rows of the weight table into shared memory (the caller syncs
+// before the first use)
+__device__ __forceinline__ void load_weights(float* __restrict__ wts, const GncStep& s, int stage,
+                                             int k0, int k1) {
+  const float* src = s.fwt + ((size_t)(stage - 1) * s.p.nv + k0) * WPV;
+  const int n = (k1 - k0) * WPV;
+  for (int t = threadIdx.x; t < n; t += NTH) wts[t] = __ldg(src + t);
 }
 
 // a compute-type value as the storage type holds it
-template <typename T> __device__ __forceinline__ typename Prec<T>::C stored_value(typename Prec<T>::C v) {
-  return v;
-}
+template <typename T> __device__ __forceinline__ float stored_value(float v) { return v; }
 template <> __device__ __forceinline__ float stored_value<__nv_bfloat16>(float v) {
   return __bfloat162float(__float2bfloat16_rn(v));
 }
@@ -125,12 +178,14 @@ template <> __device__ __forceinline__ float stored_value<__nv_bfloat16>(float v
 // fixed for the whole chunk: their source offsets (periodic wrap; clamped
 // across a wall, where the ghost replaces the value) and the equilibrium
 // parameters of their cells stay in registers.
+constexpr int PD = 3;                 // velocity planes loaded ahead
+
 template <typename T>
 struct Stager {
   using C = typename Prec<T>::C;
   int off[EPT];
   EqF<C> q[EPT];
-  T raw[EPT];
+  T raw[PD][EPT];
   __device__ void init(const GncStep& s, const C* __restrict__ eq, int i0, int j0) {
     const DevParams& p = s.p;
 #pragma unroll
@@ -151,19 +206,20 @@ struct Stager {
       q[m].dr = eq[4 * p.N + off[m]];
     }
   }
-  __device__ __forceinline__ void load(const T* __restrict__ src, int k, int N) {
+  // slot u must be a compile-time constant after unrolling (registers)
+  __device__ __forceinline__ void load(int u, const T* __restrict__ src, int k, int N) {
 #pragma unroll
     for (int m = 0; m < EPT; ++m)
-      if (threadIdx.x + NTH * m < NST) raw[m] = ldr(src + (size_t)k * N + off[m]);
+      if (threadIdx.x + NTH * m < NST) raw[u][m] = ldr(src + (size_t)k * N + off[m]);
   }
   // g = a src + b feq = src + b (feq - src) (a + b = 1; this form keeps a
   // uniform equilibrium exact whatever the rounding of b) into the buffer
-  __device__ __forceinline__ void store(C* __restrict__ buf, C b, C cx, C cy, C w) {
+  __device__ __forceinline__ void store(int u, C* __restrict__ buf, C b, C cx, C cy, C w) {
 #pragma unroll
     for (int m = 0; m < EPT; ++m) {
       const int e = threadIdx.x + NTH * m;
       if (e < NST) {
-        const C r = tof(raw[m]);
+        const C r = tof(raw[u][m]);
         buf[e] = fmx(b, feq_dev<C>(q[m], cx, cy, w) - r, r);
       }
     }
@@ -219,12 +275,15 @@ __device__ __forceinline__ bool tile_touches_walls_y(const DevParams& p, int j0)
 // ------------------------------------------------------------------ faces
 // Face pass of a stage: partial moments over the chunk of the x-face at the
 // left and the y-face below every cell of the tile (interior faces only).
+// Velocity planes are loaded PD velocities ahead into registers; one block
+// barrier per velocity (two more on tiles with wall ghosts).
 template <typename T>
 __global__ void __launch_bounds__(NTH, 2)
 k_gnc_faces(GncStep s, int stage) {
-  using C = typename Prec<T>::C;
-  using V4 = typename Prec<T>::V4;
+  using C = float;
+  using V4 = float4;
   __shared__ C gs[2][NST];
+  __shared__ __align__(16) float wts[KCMAX * WPV];
   const DevParams& p = s.p;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tiles = s.tiles_x * s.tiles_y;
@@ -234,8 +293,7 @@ k_gnc_faces(GncStep s, int stage) {
   const StageCoef& sc = stage == 1 ? s.s1 : s.s2;
   const T* __restrict__ src = (const T*)(stage == 1 ? s.fhat : s.ftp);
   const C* __restrict__ eq = (const C*)(stage == 1 ? s.eqn : s.eqp);
-  const C a = (C)sc.a, b = (C)sc.b, h = (C)sc.h;
-  const C idx = (C)p.inv_dx, idy = (C)p.inv_dy;
+  const C b = (C)sc.b;
   const V4* vq = (const V4*)s.vq;
   const bool wx = tile_touches_walls_x(p, i0), wy = tile_touches_walls_y(p, j0);
 
@@ -249,45 +307,52 @@ k_gnc_faces(GncStep s, int stage) {
     fx[q] = cell && (p.px || i >= 1);
     fy[q] = cell && (p.py || j >= 1);
   }
-  Acc<C> ax[2][3] = {}, ay[2][3] = {};
+  Kah ax[2][3] = {}, ay[2][3] = {};
 
+  load_weights(wts, s, stage, k0, k1);
   Stager<T> st;
   st.init(s, eq, i0, j0);
-  if (k0 < k1) st.load(src, k0, p.N);
+#pragma unroll
+  for (int u = 0; u < PD; ++u)
+    if (k0 + u < k1) st.load(u, src, k0 + u, p.N);
   int buf = 0;
-  for (int k = k0; k < k1; ++k) {
-    const V4 e4 = ld4(vq + p.nv + k);
-    st.store(gs[buf], b, e4.x, e4.y, e4.z);
-    if (k + 1 < k1) st.load(src, k + 1, p.N);
-    __syncthreads();
-    stage_ghosts<C>(p, gs[buf], i0, j0, wx, wy);
-    FaceW<C> fw;
-    face_weights<C>(fw, e4.x, e4.y, h, idx, idy);
-    // window: staged rows 2w .. 2w + 4, columns lane .. lane + 3
-    C Wn[5][4];
-    const C* g0 = gs[buf] + (2 * warp) * HXT + lane;
+  for (int kb = k0; kb < k1; kb += PD) {
 #pragma unroll
-    for (int r = 0; r < 5; ++r)
+    for (int u = 0; u < PD; ++u) {
+      const int k = kb + u;
+      if (k >= k1) break;                            // uniform over the block
+      const V4 e4 = ld4(vq + p.nv + k);
+      st.store(u, gs[buf], b, e4.x, e4.y, e4.z);
+      if (k + PD < k1) st.load(u, src, k + PD, p.N);
+      __syncthreads();
+      stage_ghosts<C>(p, gs[buf], i0, j0, wx, wy);
+      FaceW fw;
+      face_weights(fw, wts + (k - k0) * WPV, e4.x, e4.y);
+      // window: staged rows 2w .. 2w + 4, columns lane .. lane + 3
+      C Wn[5][4];
+      const C* g0 = gs[buf] + (2 * warp) * HXT + lane;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) Wn[r][c] = g0[r * HXT + c];
-    const V4 xq = ld4(vq + k);
+      for (int r = 0; r < 5; ++r)
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      // cell q sits at window (2, 2 + q)
-      if (fx[q]) {
-        const C v = xface<C>(fw, Wn, 1, 2 + q);
-        acc_add(ax[q][0], v);
-        acc_addprod(ax[q][1], xq.x, xq.y, v);
-        acc_addprod(ax[q][2], xq.z, xq.w, v);
+        for (int c = 0; c < 4; ++c) Wn[r][c] = g0[r * HXT + c];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        // cell q sits at window (2, 2 + q)
+        if (fx[q]) {
+          const C v = xface(fw, Wn, 1, 2 + q);
+          kah_add(ax[q][0], v);
+          kah_add(ax[q][1], e4.x * v);
+          kah_add(ax[q][2], e4.y * v);
+        }
+        if (fy[q]) {
+          const C v = yface(fw, Wn, 2, 1 + q);
+          kah_add(ay[q][0], v);
+          kah_add(ay[q][1], e4.x * v);
+          kah_add(ay[q][2], e4.y * v);
+        }
       }
-      if (fy[q]) {
-        const C v = yface<C>(fw, Wn, 2, 1 + q);
-        acc_add(ay[q][0], v);
-        acc_addprod(ay[q][1], xq.x, xq.y, v);
-        acc_addprod(ay[q][2], xq.z, xq.w, v);
-      }
+      buf ^= 1;
     }
-    buf ^= 1;
   }
   const int nfx = p.ny * (p.nx + 1), nfy = (p.ny + 1) * p.nx;
   double* px = s.pfx + (size_t)chunk * 3 * nfx;
@@ -298,12 +363,12 @@ k_gnc_faces(GncStep s, int stage) {
     if (fx[q]) {
       const int f = j * (p.nx + 1) + i;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) px[(size_t)m * nfx + f] = acc_value(ax[q][m]);
+      for (int m = 0; m < 3; ++m) px[(size_t)m * nfx + f] = kah_value(ax[q][m]);
     }
     if (fy[q]) {
       const int f = j * p.nx + i;
 #pragma unroll
-      for (int m = 0; m < 3; ++m) py[(size_t)m * nfy + f] = acc_value(ay[q][m]);
+      for (int m = 0; m < 3; ++m) py[(size_t)m * nfy + f] = kah_value(ay[q][m]);
     }
   }
 }
@@ -649,11 +714,13 @@ __device__ __forceinline__ void add_quad(Cubic<C>& S, const Quad<C>& q, C sc) {
 // pc.
 template <typename T, int STAGE>
 __global__ void __launch_bounds__(NTH, 2)
-k_gnc_update(GncStep s, typename Prec<T>::C cA, typename Prec<T>::C cB,
-             typename Prec<T>::C sP, typename Prec<T>::C sQ, typename Prec<T>::C sF) {
-  using C = typename Prec<T>::C;
-  using V4 = typename Prec<T>::V4;
+k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
+  using C = float;
+  using V4 = float4;
   __shared__ C gs[2][NST];
+  __shared__ C fxs[TYT][TXT + 1];       // x-faces fi = i0 .. i0 + 32 of the tile's rows
+  __shared__ C fys[TYT + 1][TXT];       // y-faces fj = j0 .. j0 + 16 of its columns
+  __shared__ __align__(16) float wts[KCMAX * WPV];
   const DevParams& p = s.p;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tiles = s.tiles_x * s.tiles_y;
@@ -667,8 +734,7 @@ k_gnc_update(GncStep s, typename Prec<T>::C cA, typename Prec<T>::C cB,
   // the read is a plain load issued before the store
   T* dst = (T*)(STAGE == 1 ? s.ftp : s.fhat);
   const T* fh = (const T*)s.fhat;
-  const C a = (C)sc.a, b = (C)sc.b, h = (C)sc.h;
-  const C idx = (C)p.inv_dx, idy = (C)p.inv_dy;
+  const C b = (C)sc.b;
   const V4* vq = (const V4*)s.vq;
   const C* wfx = (const C*)s.wfx;
   const C* wfy = (const C*)s.wfy;
@@ -689,77 +755,108 @@ k_gnc_update(GncStep s, typename Prec<T>::C cA, typename Prec<T>::C cB,
       if (STAGE == 2) add_quad(S[q], quad((const C*)s.eqp, p.N, cell[q]), sQ);
     }
   }
-  // wall faces of the thread's cells
-  const bool wW = !p.px && i == 0, wE = !p.px && i == p.nx - 1;
-  bool wS[2], wN[2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int j = j0 + 2 * warp + q;
-    wS[q] = !p.py && j == 0;
-    wN[q] = !p.py && j == p.ny - 1;
-  }
-  Acc<C> am[2][3] = {};
+  // faces this thread computes: the x-face left of and the y-face below
+  // each of its two cells; wall faces come from the wall pass's arrays.  The
+  // tile's last x-face column (i0 + 32) and y-face row (j0 + 16) are taken
+  // by warps 0 and 1 (extra index e < 48).
+  const int ex_id = warp * 32 + lane;
+  const bool extra = ex_id < 48;
+  Kah am[2][3] = {};
 
+  load_weights(wts, s, STAGE, k0, k1);
   Stager<T> st;
   st.init(s, eq, i0, j0);
-  if (k0 < k1) st.load(src, k0, p.N);
+#pragma unroll
+  for (int u = 0; u < PD; ++u)
+    if (k0 + u < k1) st.load(u, src, k0 + u, p.N);
   int buf = 0;
-  for (int k = k0; k < k1; ++k) {
-    const V4 e4 = ld4(vq + p.nv + k);
-    st.store(gs[buf], b, e4.x, e4.y, e4.z);
-    if (k + 1 < k1) st.load(src, k + 1, p.N);
-    // the cells' own values (L1 / L2 hits: the plane was just staged)
-    C own[2], fown[2];
+  for (int kb = k0; kb < k1; kb += PD) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      own[q] = ok[q] ? ldv(src + (size_t)k * p.N + cell[q]) : C(0);
-      fown[q] = (STAGE == 2 && ok[q]) ? lds(fh + (size_t)k * p.N + cell[q]) : C(0);
-    }
-    __syncthreads();
-    stage_ghosts<C>(p, gs[buf], i0, j0, wx, wy);
-    FaceW<C> fw;
-    face_weights<C>(fw, e4.x, e4.y, h, idx, idy);
-    // window: staged rows 2w .. 2w + 5, columns lane .. lane + 4
-    C Wn[6][5];
-    const C* g0 = gs[buf] + (2 * warp) * HXT + lane;
+    for (int u = 0; u < PD; ++u) {
+      const int k = kb + u;
+      if (k >= k1) break;                            // uniform over the block
+      const V4 e4 = ld4(vq + p.nv + k);
+      st.store(u, gs[buf], b, e4.x, e4.y, e4.z);
+      if (k + PD < k1) st.load(u, src, k + PD, p.N);
+      // the cells' own values (L1 / L2 hits: the plane is being staged)
+      C own[2], fown[2];
 #pragma unroll
-    for (int r = 0; r < 6; ++r)
-#pragma unroll
-      for (int c = 0; c < 5; ++c) Wn[r][c] = g0[r * HXT + c];
-    const V4 k4 = ld4(vq + 2 * p.nv + k);
-    const C kx = STAGE == 1 ? k4.x : k4.z, ky = STAGE == 1 ? k4.y : k4.w;
-    const V4 xq = ld4(vq + k);
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      if (!ok[q]) continue;
-      const int j = j0 + 2 * warp + q;
-      // cell q sits at window (2, 2 + q)
-      const C fW = wW ? wfx[(size_t)k * 2 * p.ny + j] : xface<C>(fw, Wn, 1, 2 + q);
-      const C fE = wE ? wfx[(size_t)k * 2 * p.ny + p.ny + j] : xface<C>(fw, Wn, 2, 2 + q);
-      const C fS = wS[q] ? wfy[(size_t)k * 2 * p.nx + i] : yface<C>(fw, Wn, 2, 1 + q);
-      const C fN = wN[q] ? wfy[(size_t)k * 2 * p.nx + p.nx + i] : yface<C>(fw, Wn, 2, 2 + q);
-      const C df = fmx(kx, fE - fW, ky * (fN - fS));
-      const C ws = fmx(e4.z, cubic<C>(S[q], e4.x, e4.y), df);
-      C out;
-      if (STAGE == 1) {
-        out = fmx(-cB, own[q], own[q] + ws);                 // cB = sP
-      } else {
-        out = fmx(cA, fown[q] - own[q], fmx(-cB, own[q], own[q] + ws));   // cB = sP + sQ
+      for (int q = 0; q < 2; ++q) {
+        own[q] = ok[q] ? ldv(src + (size_t)k * p.N + cell[q]) : C(0);
+        fown[q] = (STAGE == 2 && ok[q]) ? lds(fh + (size_t)k * p.N + cell[q]) : C(0);
       }
-      const C ov = stored_value<T>(out);    // the moments are those of the stored value
-      stv(dst + (size_t)k * p.N + cell[q], ov);
-      acc_add(am[q][0], ov);
-      acc_addprod(am[q][1], xq.x, xq.y, ov);
-      acc_addprod(am[q][2], xq.z, xq.w, ov);
+      __syncthreads();
+      stage_ghosts<C>(p, gs[buf], i0, j0, wx, wy);
+      FaceW fw;
+      face_weights(fw, wts + (k - k0) * WPV, e4.x, e4.y);
+      {
+        // window: staged rows 2w .. 2w + 4, columns lane .. lane + 3
+        C Wn[5][4];
+        const C* g0 = gs[buf] + (2 * warp) * HXT + lane;
+#pragma unroll
+        for (int r = 0; r < 5; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) Wn[r][c] = g0[r * HXT + c];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int r = 2 * warp + q, j = j0 + r;
+          // cell (lane, r) sits at window (2, 2 + q)
+          C vx = xface(fw, Wn, 1, 2 + q);
+          if (!p.px && i == 0 && j < p.ny) vx = wfx[(size_t)k * 2 * p.ny + j];
+          if (!p.px && i == p.nx && j < p.ny) vx = wfx[(size_t)k * 2 * p.ny + p.ny + j];
+          fxs[r][lane] = vx;
+          C vy = yface(fw, Wn, 2, 1 + q);
+          if (!p.py && j == 0 && i < p.nx) vy = wfy[(size_t)k * 2 * p.nx + i];
+          if (!p.py && j == p.ny && i < p.nx) vy = wfy[(size_t)k * 2 * p.nx + p.nx + i];
+          fys[r][lane] = vy;
+        }
+      }
+      if (extra) {
+        const C* g = gs[buf];
+        if (ex_id < TYT) {                           // x-face i0 + 32 of row ex_id
+          const int r = ex_id, ii = i0 + TXT, j = j0 + r;
+          C v = xface_at(fw, g, TXT + 2, r + 2);
+          if (!p.px && ii == p.nx && j < p.ny) v = wfx[(size_t)k * 2 * p.ny + p.ny + j];
+          fxs[r][TXT] = v;
+        } else {                                     // y-face j0 + 16 of column ex_id - 16
+          const int c = ex_id - TYT, ii = i0 + c, j = j0 + TYT;
+          C v = yface_at(fw, g, c + 2, TYT + 2);
+          if (!p.py && j == p.ny && ii < p.nx) v = wfy[(size_t)k * 2 * p.nx + p.nx + ii];
+          fys[TYT][c] = v;
+        }
+      }
+      __syncthreads();
+      const V4 k4 = ld4(vq + 2 * p.nv + k);
+      const C kx = STAGE == 1 ? k4.x : k4.z, ky = STAGE == 1 ? k4.y : k4.w;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (!ok[q]) continue;
+        const int r = 2 * warp + q;
+        const C fW = fxs[r][lane], fE = fxs[r][lane + 1];
+        const C fS = fys[r][lane], fN = fys[r + 1][lane];
+        const C df = fmx(kx, fE - fW, ky * (fN - fS));
+        const C ws = fmx(e4.z, cubic<C>(S[q], e4.x, e4.y), df);
+        C out;
+        if (STAGE == 1) {
+          out = fmx(-cB, own[q], own[q] + ws);                 // cB = sP
+        } else {
+          out = fmx(cA, fown[q] - own[q], fmx(-cB, own[q], own[q] + ws));   // cB = sP + sQ
+        }
+        const C ov = stored_value<T>(out);    // the moments are those of the stored value
+        stv(dst + (size_t)k * p.N + cell[q], ov);
+        kah_add(am[q][0], ov);
+        kah_add(am[q][1], e4.x * ov);
+        kah_add(am[q][2], e4.y * ov);
+      }
+      buf ^= 1;
     }
-    buf ^= 1;
   }
   double* pc = s.pc + (size_t)chunk * 3 * p.N;
 #pragma unroll
   for (int q = 0; q < 2; ++q)
     if (ok[q])
 #pragma unroll
-      for (int m = 0; m < 3; ++m) pc[(size_t)m * p.N + cell[q]] = acc_value(am[q][m]);
+      for (int m = 0; m < 3; ++m) pc[(size_t)m * p.N + cell[q]] = kah_value(am[q][m]);
 }
 
 template <typename T>
@@ -774,10 +871,28 @@ int items(const GncStep& s) { return s.tiles_x * s.tiles_y * s.nch; }
 
 }  // namespace
 
+void gnc_weight_table(const DevParams& p, const double* xi_x, const double* xi_y,
+                      const StageCoef& s1, const StageCoef& s2, float* out) {
+  for (int st = 0; st < 2; ++st) {
+    const double h = st == 0 ? s1.h : s2.h;
+    for (int k = 0; k < p.nv; ++k) {
+      const double ax = -xi_x[k] * h * p.inv_dx, by = -xi_y[k] * h * p.inv_dy;
+      const double ab[4][2] = {{0.5 + ax, by}, {-0.5 + ax, by}, {ax, 0.5 + by}, {ax, -0.5 + by}};
+      float* row = out + ((size_t)st * p.nv + k) * WPV;
+      for (int set = 0; set < 4; ++set) {
+        double w[9];
+        flux_ds_weights<double>(ab[set][0], ab[set][1], w);
+        for (int q = 0; q < 12; ++q) row[set * 12 + q] = q < 9 ? (float)w[q] : 0.0f;
+      }
+    }
+  }
+}
+
 int gnc_chunks(const DevParams& p, int sms) {
   const int tiles = ((p.nx + TXT - 1) / TXT) * ((p.ny + TYT - 1) / TYT);
   const int want = (4 * 2 * sms + tiles - 1) / tiles;        // about four waves of two blocks per SM
-  return std::max(1, std::min(p.nv, want));
+  const int cap = (p.nv + KCMAX - 1) / KCMAX;                 // at most KCMAX velocities per chunk
+  return std::max(1, std::min(p.nv, std::max(want, cap)));
 }
 
 cudaError_t gnc_prepare(int store) {

@@ -224,7 +224,13 @@ struct GncStep {
   int nch, kc;                  // velocity chunks and velocities per chunk
   int tiles_x, tiles_y;         // 32 x 16 cell tiles
   double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
+  const float* fwt;             // face-value weights [2 stages][nv][48] (gnc_weight_table)
 };
+// Face-value weights of eq. flux_DS (as printed) per stage and velocity for
+// the staged-tile kernels: x-faces about the lower and upper cell, y-faces
+// about the lower and upper cell, nine weights each padded to twelve.
+void gnc_weight_table(const DevParams& p, const double* xi_x, const double* xi_y,
+                      const StageCoef& s1, const StageCoef& s2, float* out);
 int gnc_chunks(const DevParams& p, int sms);
 cudaError_t gnc_prepare(int store);
 cudaError_t launch_gnc_moments(const GncStep& s, cudaStream_t st);   // cell moments of f^ -> t_n
