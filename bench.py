@@ -87,11 +87,11 @@ HBM_BYTES_PER_UNIT = {
     "d2q9m_stage1": {"fp32": 16, "bf16": 8}, "d2q9m_stage2": {"fp32": 16, "bf16": 8},
     # the same in double-word arithmetic on FP64 arrays
     "d2q9dw_stage1": {"f64dw": 32}, "d2q9dw_stage2": {"f64dw": 32},
-    # staged-tile generic path (deviation forms): the face pass reads the
+    # class-moment generic path (deviation forms): the sums pass reads the
     # stage source once; update 1 reads f^ and writes f~'; update 2 reads
     # f~' and f^ and writes f^ (per cell-velocity; halo re-reads and the
-    # O(cells) partial moments are not counted)
-    "gnc_faces": {"fp32": 4, "bf16": 2},
+    # O(cells) finaliser data are not counted)
+    "gnc_sums": {"fp32": 4, "bf16": 2},
     "gnc_update_stage1": {"fp32": 8, "bf16": 4},
     "gnc_update_stage2": {"fp32": 12, "bf16": 6},
 }

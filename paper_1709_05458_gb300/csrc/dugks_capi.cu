@@ -38,7 +38,7 @@ const char* kNames[K_NUM] = {
     "d2q9m_stage1", "d2q9m_stage2", "convert",
     "gdev_cell", "gdev_face_x", "gdev_face_y", "gdev_walls", "gdev_update_stage1",
     "gdev_update_stage2", "t2_cell", "t2_face_x", "t2_face_y", "t2_update",
-    "d2q9dw_stage1", "d2q9dw_stage2", "gnc_moments", "gnc_faces", "gnc_walls", "gnc_facefin",
+    "d2q9dw_stage1", "d2q9dw_stage2", "gnc_sums", "gnc_cellfin", "gnc_walls", "gnc_facefin",
     "gnc_update_stage1", "gnc_update_stage2"};
 
 struct Pending {
@@ -91,15 +91,18 @@ struct dugks_ctx {
   bool gdev = false;
   GDevStep gs{};
   void* eqp = nullptr;
-  // the staged-tile generic path (dugks_gnc.cu), which steps every generic
-  // context: its step descriptor and the buffers it adds to those above
+  // the class-moment generic path (dugks_gnc.cu), which steps the generic
+  // contexts with FP32 / BF16 storage: its step descriptor and the buffers
+  // it adds to those above
   bool gnc = false;
   GncStep gn{};
   void* gn_eq2 = nullptr;       // equilibrium parameters at t' [5][N]
   double* gn_mom2 = nullptr;    // rho, u at t' [3][N]
-  void* gn_wf = nullptr;        // wall faces' f-bar
-  double* gn_part = nullptr;    // partial moments
-  float* gn_fwt = nullptr;      // face-value weights per stage and velocity
+  void* gn_wf = nullptr;        // wall faces' f-bar [nv][nw]
+  double* gn_wrho = nullptr;    // wall densities [nw]
+  double* gn_sums = nullptr;    // class sums [ncls][10][N]
+  float* gn_nu = nullptr;       // stencil moments [ncombo][18][N]
+  void* gn_tab = nullptr;       // class tables, quadrature and face weights
   void* vf = nullptr;           // velocity table of that path (4-vector rows [3][nv])
   void* gpad = nullptr;         // padded stage field of that path
   void* fpar = nullptr;         // face equilibrium parameters of that path
@@ -233,8 +236,10 @@ void free_all(dugks_ctx* c) {
   if (c->gn_eq2) cudaFree(c->gn_eq2);
   if (c->gn_mom2) cudaFree(c->gn_mom2);
   if (c->gn_wf) cudaFree(c->gn_wf);
-  if (c->gn_part) cudaFree(c->gn_part);
-  if (c->gn_fwt) cudaFree(c->gn_fwt);
+  if (c->gn_wrho) cudaFree(c->gn_wrho);
+  if (c->gn_sums) cudaFree(c->gn_sums);
+  if (c->gn_nu) cudaFree(c->gn_nu);
+  if (c->gn_tab) cudaFree(c->gn_tab);
   for (auto& q : c->pending) {
     cudaEventDestroy(q.a);
     cudaEventDestroy(q.b);
@@ -418,21 +423,17 @@ int one_step_gdev(dugks_ctx* c) {
   return DUGKS_OK;
 }
 
-// The staged-tile generic path: per stage the face moments, the wall faces,
-// the face parameters and the update with its cell moments; the cell
-// moments of a new state first.
+// The class-moment generic path: per stage the class sums of the source,
+// the cell and face finalisers, the wall faces and the update.
 int one_step_gnc(dugks_ctx* c) {
   const GncStep& g = c->gn;
   cudaStream_t s = c->stream;
-  if (!c->g1_valid) {
-    TRY(launch(c, K_GNC_MOMENTS, [&] { return launch_gnc_moments(g, s); }));
-    c->g1_valid = true;
-  }
   const bool walls = !(c->p.px && c->p.py);
   for (int stage = 1; stage <= 2; ++stage) {
-    TRY(launch(c, K_GNC_FACES, [&] { return launch_gnc_faces(g, stage, s); }));
+    TRY(launch(c, K_GNC_SUMS, [&] { return launch_gnc_sums(g, stage, s); }));
+    TRY(launch(c, K_GNC_CELLFIN, [&] { return launch_gnc_cellfin(g, stage, s); }));
+    TRY(launch(c, K_GNC_FACEFIN, [&] { return launch_gnc_facefin(g, stage, s); }));
     if (walls) TRY(launch(c, K_GNC_WALLS, [&] { return launch_gnc_walls(g, stage, s); }));
-    TRY(launch(c, K_GNC_FACEFIN, [&] { return launch_gnc_facefin(g, s); }));
     TRY(launch(c, stage == 1 ? K_GNC_UPDATE1 : K_GNC_UPDATE2,
                [&] { return launch_gnc_update(g, stage, s); }));
   }
@@ -465,11 +466,7 @@ int advance(dugks_ctx* c) {
 
 // g1 of the current state for the fused paths (run eagerly before capture)
 int ensure_g1(dugks_ctx* c) {
-  if (c->gnc && !c->g1_valid && c->scheme == DUGKS_T3S3) {
-    TRY(launch(c, K_GNC_MOMENTS, [&] { return launch_gnc_moments(c->gn, c->stream); }));
-    c->g1_valid = true;
-    return DUGKS_OK;
-  }
+  if (c->gnc) return DUGKS_OK;                     // every step starts from the sums
   if (!c->d2q9 || c->g1_valid) return DUGKS_OK;
   cudaStream_t s = c->stream;
   if (c->store)
@@ -927,7 +924,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
     g.mom = c->mom;
     g.part = c->part;
     if (use_gnc) {
-      // the staged-tile path: its descriptor shares the velocity table, the
+      // the class-moment path: its descriptor shares the velocity table, the
       // t_n parameters and moments and the face parameters with the above
       GncStep& n = c->gn;
       n.p = c->p;
@@ -938,30 +935,47 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
       n.c_om = c->c_om;
       n.fhat = c->fhat;
       n.ftp = c->ftp;
-      n.eqn = c->eqp;
+      n.eqn = (float*)c->eqp;
       n.mom_n = c->mom;
-      n.fpx = c->fpar;
-      n.fpy = (char*)c->fpar + 5 * nfmax * csz;
+      n.fpx = (float*)c->fpar;
+      n.fpy = (float*)((char*)c->fpar + 5 * nfmax * csz);
       n.vq = c->vf;
       for (int sd = 0; sd < 4; ++sd) n.ds_out[sd] = g.ds_out[sd];
-      n.tiles_x = (p.nx + 31) / 32;
-      n.tiles_y = (p.ny + 15) / 16;
-      n.nch = gnc_chunks(p, sms);
+      GncTables tb;
+      if (e == cudaSuccess &&
+          !gnc_tables(n, vel->xi_x, vel->xi_y, vel->w, host.data() + 3 * (size_t)nv, opp.data(), tb))
+        e = cudaErrorInvalidValue;
+      n.nch = gnc_chunks(n, sms);
       n.kc = (nv + n.nch - 1) / n.nch;
       n.nch = (nv + n.kc - 1) / n.kc;
-      const size_t nfx1 = (size_t)p.ny * (p.nx + 1), nfy1 = (size_t)(p.ny + 1) * p.nx;
-      const size_t nwall = (size_t)nv * 2 * (p.nx + p.ny);
+      // one device block for the tables: ints, then floats (16-byte aligned)
+      const size_t ni = tb.cls_off.size() + tb.cls_k.size() + tb.wsrc.size();
+      const size_t ioff = 0, foff = ((ni * sizeof(int) + 15) / 16) * 16;
+      const size_t nf1 = tb.cls_mono.size(), nf2 = tb.zc.size(), nf3 = tb.fwt.size();
+      const size_t nf4 = tb.wbb.size();
+      const size_t tab_bytes = foff + (nf1 + nf2 + nf3 + nf4) * sizeof(float);
       if (e == cudaSuccess) e = cudaMalloc(&c->gn_eq2, 5 * (size_t)p.N * csz);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->gn_mom2, 3 * (size_t)p.N * sizeof(double));
-      if (e == cudaSuccess) e = cudaMalloc(&c->gn_wf, nwall * csz);
+      if (e == cudaSuccess) e = cudaMalloc(&c->gn_wf, (size_t)nv * n.nw * csz);
+      if (e == cudaSuccess) e = cudaMalloc((void**)&c->gn_wrho, (size_t)n.nw * sizeof(double));
       if (e == cudaSuccess)
-        e = cudaMalloc((void**)&c->gn_part, (size_t)n.nch * 3 * (nfx1 + nfy1 + p.N) * sizeof(double));
+        e = cudaMalloc((void**)&c->gn_sums, (size_t)n.ncls * 10 * p.N * sizeof(double));
+      if (e == cudaSuccess)
+        e = cudaMalloc((void**)&c->gn_nu, (size_t)n.ncombo * 18 * p.N * sizeof(float));
+      if (e == cudaSuccess) e = cudaMalloc(&c->gn_tab, tab_bytes);
       if (e == cudaSuccess) {
-        std::vector<float> wt(2 * (size_t)nv * 48);
-        gnc_weight_table(p, vel->xi_x, vel->xi_y, c->s1, c->s2, wt.data());
-        e = cudaMalloc((void**)&c->gn_fwt, wt.size() * sizeof(float));
-        if (e == cudaSuccess)
-          e = cudaMemcpy(c->gn_fwt, wt.data(), wt.size() * sizeof(float), cudaMemcpyHostToDevice);
+        std::vector<char> blob(tab_bytes, 0);
+        std::memcpy(blob.data() + ioff, tb.cls_off.data(), tb.cls_off.size() * sizeof(int));
+        std::memcpy(blob.data() + ioff + tb.cls_off.size() * sizeof(int), tb.cls_k.data(),
+                    tb.cls_k.size() * sizeof(int));
+        std::memcpy(blob.data() + ioff + (tb.cls_off.size() + tb.cls_k.size()) * sizeof(int),
+                    tb.wsrc.data(), tb.wsrc.size() * sizeof(int));
+        std::memcpy(blob.data() + foff, tb.cls_mono.data(), nf1 * sizeof(float));
+        std::memcpy(blob.data() + foff + nf1 * sizeof(float), tb.zc.data(), nf2 * sizeof(float));
+        std::memcpy(blob.data() + foff + (nf1 + nf2) * sizeof(float), tb.fwt.data(), nf3 * sizeof(float));
+        std::memcpy(blob.data() + foff + (nf1 + nf2 + nf3) * sizeof(float), tb.wbb.data(),
+                    nf4 * sizeof(float));
+        e = cudaMemcpy(c->gn_tab, blob.data(), tab_bytes, cudaMemcpyHostToDevice);
       }
       if (e == cudaSuccess) e = gnc_prepare(storage);
       if (e != cudaSuccess) {
@@ -969,16 +983,22 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
         delete c;
         cudaGetLastError();
         return fail(e == cudaErrorMemoryAllocation ? DUGKS_ENOMEM : DUGKS_ECUDA,
-                    std::string("staged-tile path set-up: ") + cudaGetErrorString(e));
+                    std::string("class-moment path set-up: ") + cudaGetErrorString(e));
       }
-      n.fwt = c->gn_fwt;
-      n.eqp = c->gn_eq2;
+      const char* tab = (const char*)c->gn_tab;
+      n.cls_off = (const int*)(tab + ioff);
+      n.cls_k = n.cls_off + tb.cls_off.size();
+      n.wsrc = n.cls_k + tb.cls_k.size();
+      n.cls_mono = (const float*)(tab + foff);
+      n.zc = n.cls_mono + nf1;
+      n.fwt = n.zc + nf2;
+      n.wbb = (const float2*)(n.fwt + nf3);
+      n.eqp = (float*)c->gn_eq2;
       n.mom_p = c->gn_mom2;
-      n.wfx = c->gn_wf;
-      n.wfy = (char*)c->gn_wf + (size_t)nv * 2 * p.ny * csz;
-      n.pfx = c->gn_part;
-      n.pfy = n.pfx + (size_t)n.nch * 3 * nfx1;
-      n.pc = n.pfy + (size_t)n.nch * 3 * nfy1;
+      n.wf = (float*)c->gn_wf;
+      n.wrho = c->gn_wrho;
+      n.sums = c->gn_sums;
+      n.nu = c->gn_nu;
       c->gnc = true;
     }
     c->store = storage;

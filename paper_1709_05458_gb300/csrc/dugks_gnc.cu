@@ -1,48 +1,54 @@
-// Staged-tile kernels of the T3S3 step for any velocity set (Newton-Cotes
+// Class-moment kernels of the T3S3 step for any velocity set (Newton-Cotes
 // grids in particular), periodic / bounce-back / diffuse walls, for the
 // deviation storage forms of the generic path (FP32 / BF16 deviations
-// d = f - W_k rho0, FP32 arithmetic, compensated moment sums; see
-// dugks_gcommon.cuh).  The kernels are written for any compute type, but
-// FP64 storage keeps the generic kernels of dugks_generic_mixed.cu: it is
-// bound by the FP64 pipe, and recomputing g and the face values costs more
-// FP64 operations than storing them.
+// d = f - W_k rho0, FP32 arithmetic; helpers in dugks_gcommon.cuh).  FP64
+// storage keeps the kernels of dugks_generic_mixed.cu, which are bound by the
+// FP64 pipe rather than by bytes.
 //
-// One stage (Sec. 2.1.3, Steps (1)-(4)) reads its source array -- f^ in
-// stage 1, f~(t') in stage 2 -- twice and writes one array:
+// The face equilibria of a stage (eqs. recover2f, feqIntD3rdHat2_DS) need
+// only the moments (1, xi_x, xi_y) of the interface values f-bar over the
+// velocities.  An interface value is a 3 x 3 stencil of the stage field
+// g = a src + b feq around the upwind cell with weights T(a, b) (eq. flux_DS
+// as printed) that are quadratic in the foot offset (a, b) = (a0, b0) -
+// (xi_x h/dx, xi_y h/dy); so xi^m T(a, b) is a cubic polynomial in xi and
+// every face moment is a fixed combination, over the stencil's nine cells,
+// of the cell moments of g up to third degree taken over the velocities with
+// one sign of xi_x (x-faces) or xi_y (y-faces).  A stage is then
 //
-//   faces   per (32 x 16 cell tile, velocity chunk): every velocity plane of
-//           the tile plus a two-cell halo is staged in shared memory as the
-//           stage field g = a src + b feq (eqs. f_bar_1_6, fbp_5_12 derived),
-//           wall ghosts extrapolated there (reading Q16); the interface
-//           values f-bar of the tile's interior faces follow from the
-//           upwind 3 x 3 stencils (eqs. interfaceEvof, flux_DS as printed)
-//           and only their moments over the chunk leave the chip
-//           (partial sums, FP64);
-//   walls   per wall face: the wall rules of Sec. 2.3 on f-bar (bounce-back
-//           with a moving wall, diffuse scattering), the face's moments and
-//           equilibrium parameters; the wall faces' f-bar is stored (a few
-//           MB);
-//   facefin interior faces: chunk sums -> the face equilibrium's parameters;
-//   update  per (tile, chunk): the same staging; the four face values of
-//           every cell recomputed from the staged g (or read at walls),
-//           f = alpha f-bar + beta feq (eq. recover2f) and the micro-flux
-//           (eq. microflux) enter
+//   sums    a streaming pass over the stage's source array: per cell and
+//           sign class (sign xi_x, sign xi_y) the ten moments of degree <= 3
+//           (the cell's rho and j among them) -- one read of the state;
+//   cellfin per cell: rho, u and the equilibrium's parameters; the class
+//           moments of g (the equilibrium's part by exact quadrature); the
+//           18 stencil moments nu_{m,u} = sum xi^m u(a, b) g of every
+//           class combination the faces use (u = 1, a, b, a^2, ab, b^2);
+//   facefin per face: M_m = sum over the stencil cells and u of t_u(s)
+//           nu_{m,u}, T = sum_u t_u u(a, b), wall ghosts by the quadratic
+//           extrapolation of Q16 (linear, so it applies to nu), and at a wall
+//           the leaving velocities by the wall rule: bounce-back mirrors the
+//           incoming moments (eq. BB), diffuse scattering adds rho_w times
+//           the wall equilibrium's moments with rho_w from the incoming
+//           flux (Sec. 2.3, Q13-Q15);
+//   walls   per wall face and velocity: f-bar (fluid side, or the wall rule);
+//   update  per (32 x 16 cell tile, velocity chunk): each velocity plane of
+//           the tile plus a two-cell halo is staged in shared memory as g
+//           (wall ghosts extrapolated there), the x- and y-face values of
+//           the tile follow from the upwind stencils (wall faces from the
+//           walls pass), and f = alpha f-bar + beta feq (eq. recover2f)
+//           enters
 //             stage 1: f~(t') = 5/4 g1 - 1/4 f^ + dt/3 L*
 //             stage 2: f^^{n+1} = X + 3/4 dt Omega' + 4dt/7 L**,
 //                      X = f^+ + 3dt/7 L* = 4/7 f^ - 6/7 g1 + 9/7 f~(t')
 //           (eqs. f_tilde_1_3, fhp, collisionterm, feqIntD3rdHat2_DS; X is
-//           recovered from f^ and f~(t') instead of being stored); the
-//           output's cell moments over the chunk are written as partial
-//           sums;
-//   cellfin cell moments -> rho, u (FP64) and the next stage's equilibrium
-//           parameters.
+//           recovered from f^ and f~(t') instead of being stored).
 //
-// Every equilibrium that enters an update is W_k P(xi_k) with P quadratic;
-// with the flux factors they combine into W_k S(xi_k), S a cubic per cell
-// (Cubic in dugks_gcommon.cuh).  Per (cell, velocity) and step the path
-// moves four reads and two writes of the stored type plus the halo
-// re-reads, which the 126 MB L2 mostly serves.
+// Per (cell, velocity) and step the path reads the stored type four times
+// (sums and update of each stage, stage 2 also f^) and writes it twice: 24
+// bytes in FP32, 12 in BF16, plus the halo re-reads of the updates, which
+// the L2 serves.  The finalisers touch O(cells) data.
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "dugks_gcommon.cuh"
 
@@ -52,648 +58,592 @@ namespace {
 
 constexpr int TXT = 32;                 // tile columns (one lane each)
 constexpr int TYT = 16;                 // tile rows
-constexpr int NWP = 8;                  // warps per block; warp w takes rows 2w, 2w + 1
+constexpr int UNW = 4;                  // warps per update block
+constexpr int RPW = TYT / UNW;          // rows per warp: warp w takes rows 4w .. 4w + 3
+constexpr int UNT = 32 * UNW;           // 128 threads
 constexpr int HXT = TXT + 4;            // staged columns i0 - 2 .. i0 + 33
 constexpr int HYT = TYT + 4;            // staged rows    j0 - 2 .. j0 + 17
 constexpr int NST = HXT * HYT;          // 720 staged cells
-constexpr int NTH = 32 * NWP;           // 256 threads
-constexpr int EPT = (NST + NTH - 1) / NTH;   // staged cells per thread (3)
+constexpr int NHALO = NST - TXT * TYT;  // 208 of them outside the tile
+constexpr int HPT = (NHALO + UNT - 1) / UNT;   // halo cells per thread (2)
+constexpr int EPT = RPW + HPT;          // staged cells per thread: 4 own + 2 halo
+constexpr int WPV = 72;                 // face weights per velocity in the table
+constexpr int NMONO = 10;               // monomials of degree <= 3
+constexpr int NNU = 18;                 // stencil moments nu_{m,u}: 3 m x 6 u
+constexpr int SBLK = 16;                // velocities per plain FP32 block in the sums
 
-template <typename C>
-__device__ __forceinline__ C dot9(const C (&T)[9], C s00, C s01, C s02, C s10, C s11, C s12,
-                                  C s20, C s21, C s22) {
-  C v = T[0] * s00;
-  v = fmx(T[1], s01, v);
-  v = fmx(T[2], s02, v);
-  v = fmx(T[3], s10, v);
-  v = fmx(T[4], s11, v);
-  v = fmx(T[5], s12, v);
-  v = fmx(T[6], s20, v);
-  v = fmx(T[7], s21, v);
-  return fmx(T[8], s22, v);
-}
+// index of the monomial x^i y^j among 1, x, y, xx, xy, yy, xxx, xxy, xyy, yyy
+__host__ __device__ constexpr int mono_ix(int i, int j) { return (i + j) * (i + j + 1) / 2 + j; }
 
-// the 3 x 3 stencil of window W centred at (x, y): rows y-1..y+1 (south to
-// north), columns x-1..x+1
-#define STEN(W, x, y)                                                                   \
-  W[(y) - 1][(x) - 1], W[(y) - 1][(x)], W[(y) - 1][(x) + 1], W[(y)][(x) - 1], W[(y)][(x)], \
-      W[(y)][(x) + 1], W[(y) + 1][(x) - 1], W[(y) + 1][(x)], W[(y) + 1][(x) + 1]
+// ------------------------------------------------------------------ sums
+// Per cell and sign class: the moments sum_k pi_p(xi_k) src_k of the
+// class's velocities for the ten monomials pi_p.  p = 0, 1, 2 (the cell's
+// rho and j, which the collision must conserve) are Kahan-compensated per
+// term; the others add SBLK terms in plain FP32 and fold each block into a
+// compensated sum.  The table row of a velocity holds pi_0 .. pi_9.
+//
 
-// Per-velocity face-value weights (eq. flux_DS as printed), formed on the
-// host per stage and velocity (gnc_weight_table) and read by every block for
-// its chunk into shared memory: x-faces about the lower (left) and upper
-// (right) cell, y-faces about the lower (below) and upper cell, each nine
-// weights padded to twelve for 16-byte reads.  The sign of xi.n picks one
-// set; a tie averages both (Q4).
-constexpr int KCMAX = 128;            // velocities per chunk at most
-constexpr int WPV = 48;               // weights per velocity in the table
-struct FaceW {
-  float x[9], y[9];                   // the set each direction's sign picks
-  const float* row;                   // the velocity's row of the table (ties)
-  int sx, sy;                         // sign of xi_x, xi_y
-};
-__device__ __forceinline__ void read9(const float* __restrict__ w, float (&T)[9]) {
-  const float4 a = *reinterpret_cast<const float4*>(w);
-  const float4 b = *reinterpret_cast<const float4*>(w + 4);
-  T[0] = a.x; T[1] = a.y; T[2] = a.z; T[3] = a.w;
-  T[4] = b.x; T[5] = b.y; T[6] = b.z; T[7] = b.w;
-  T[8] = w[8];
-}
-__device__ __forceinline__ void face_weights(FaceW& w, const float* __restrict__ row, float cx,
-                                             float cy) {
-  w.row = row;
-  w.sx = cx > 0.f ? 1 : (cx < 0.f ? -1 : 0);
-  w.sy = cy > 0.f ? 1 : (cy < 0.f ? -1 : 0);
-  read9(row + (w.sx >= 0 ? 0 : 12), w.x);
-  read9(row + (w.sy >= 0 ? 24 : 36), w.y);
-}
-
-// x-face value between the cells centred at window columns xl and xl + 1
-// (row y); y-face value between window rows yl and yl + 1 (column x); a tie
-// averages the expansions from both cells (Q4)
-template <int NR, int NC>
-__device__ __forceinline__ float xface(const FaceW& w, const float (&W)[NR][NC], int xl, int y) {
-  if (w.sx > 0) return dot9(w.x, STEN(W, xl, y));
-  if (w.sx < 0) return dot9(w.x, STEN(W, xl + 1, y));
-  float u[9];
-  read9(w.row + 12, u);
-  return 0.5f * (dot9(w.x, STEN(W, xl, y)) + dot9(u, STEN(W, xl + 1, y)));
-}
-template <int NR, int NC>
-__device__ __forceinline__ float yface(const FaceW& w, const float (&W)[NR][NC], int x, int yl) {
-  if (w.sy > 0) return dot9(w.y, STEN(W, x, yl));
-  if (w.sy < 0) return dot9(w.y, STEN(W, x, yl + 1));
-  float u[9];
-  read9(w.row + 36, u);
-  return 0.5f * (dot9(w.y, STEN(W, x, yl)) + dot9(u, STEN(W, x, yl + 1)));
-}
-// the same from the staged plane directly: x-face left of staged column cx
-// (staged row cy), y-face below staged row cy (staged column cx)
-__device__ __forceinline__ float stencil_at(const float* __restrict__ g, const float (&T)[9], int cx,
-                                            int cy) {
-  const float* b = g + (cy - 1) * HXT + cx - 1;
-  float v = T[0] * b[0];
-  v = fmaf(T[1], b[1], v);
-  v = fmaf(T[2], b[2], v);
-  v = fmaf(T[3], b[HXT], v);
-  v = fmaf(T[4], b[HXT + 1], v);
-  v = fmaf(T[5], b[HXT + 2], v);
-  v = fmaf(T[6], b[2 * HXT], v);
-  v = fmaf(T[7], b[2 * HXT + 1], v);
-  return fmaf(T[8], b[2 * HXT + 2], v);
-}
-__device__ __forceinline__ float xface_at(const FaceW& w, const float* __restrict__ g, int cx,
-                                          int cy) {
-  if (w.sx > 0) return stencil_at(g, w.x, cx - 1, cy);
-  if (w.sx < 0) return stencil_at(g, w.x, cx, cy);
-  float u[9];
-  read9(w.row + 12, u);
-  return 0.5f * (stencil_at(g, w.x, cx - 1, cy) + stencil_at(g, u, cx, cy));
-}
-__device__ __forceinline__ float yface_at(const FaceW& w, const float* __restrict__ g, int cx,
-                                          int cy) {
-  if (w.sy > 0) return stencil_at(g, w.y, cx, cy - 1);
-  if (w.sy < 0) return stencil_at(g, w.y, cx, cy);
-  float u[9];
-  read9(w.row + 36, u);
-  return 0.5f * (stencil_at(g, w.y, cx, cy - 1) + stencil_at(g, u, cx, cy));
-}
-
-// the chunk's rows of the weight table into shared memory (the caller syncs
-// before the first use)
-__device__ __forceinline__ void load_weights(float* __restrict__ wts, const GncStep& s, int stage,
-                                             int k0, int k1) {
-  const float* src = s.fwt + ((size_t)(stage - 1) * s.p.nv + k0) * WPV;
-  const int n = (k1 - k0) * WPV;
-  for (int t = threadIdx.x; t < n; t += NTH) wts[t] = __ldg(src + t);
-}
-
-// a compute-type value as the storage type holds it
-template <typename T> __device__ __forceinline__ float stored_value(float v) { return v; }
-template <> __device__ __forceinline__ float stored_value<__nv_bfloat16>(float v) {
-  return __bfloat162float(__float2bfloat16_rn(v));
-}
-
-// Staging of one velocity plane of a tile.  The staged cells of a thread are
-// fixed for the whole chunk: their source offsets (periodic wrap; clamped
-// across a wall, where the ghost replaces the value) and the equilibrium
-// parameters of their cells stay in registers.
-constexpr int PD = 3;                 // velocity planes loaded ahead
+// Block: SPL velocity subsets x 32 threads, one cell per thread (CPB cells
+// per block); a subset takes every SPL-th velocity of the class; the
+// subsets' compensated sums are added in FP64 in a fixed order.  The loads
+// of SU velocities are issued before their sums.
+constexpr int SPL = 8;
+constexpr int CPB = 256 / SPL;           // 32 cells per block
+constexpr int SU = 8;                    // velocities in flight per thread
 
 template <typename T>
-struct Stager {
-  using C = typename Prec<T>::C;
-  int off[EPT];
-  EqF<C> q[EPT];
-  T raw[PD][EPT];
-  __device__ void init(const GncStep& s, const C* __restrict__ eq, int i0, int j0) {
-    const DevParams& p = s.p;
+__global__ void __launch_bounds__(256)
+k_gnc_sums(GncStep s, int stage) {
+  __shared__ double red[SPL][NMONO][CPB];
+  const DevParams& p = s.p;
+  const int cls = blockIdx.y;
+  const int sub = threadIdx.x / CPB, tl = threadIdx.x % CPB;
+  const int cb0 = blockIdx.x * CPB;
+  const int c = cb0 + tl;
+  const bool have = c < p.N;
+  const T* __restrict__ src = (const T*)(stage == 1 ? s.fhat : s.ftp) + (have ? c : 0);
+  const int e0 = __ldg(s.cls_off + cls), e1 = __ldg(s.cls_off + cls + 1);
+  Kah lo[3] = {}, hi[7] = {};
+  int e = e0 + sub;
+  while (e < e1) {
+    float part[7] = {};
+    // a block of up to SBLK of this subset's velocities, SU loads at a time
+    const int eend = min(e1, e + SPL * SBLK);
+    for (; e < eend; e += SPL * SU) {
+      float v[SU];
+      int ee[SU];
 #pragma unroll
-    for (int m = 0; m < EPT; ++m) {
-      const int e = threadIdx.x + NTH * m;
-      const int ee = e < NST ? e : NST - 1;
-      const int ex = ee % HXT, ey = ee / HXT;
-      int gi = i0 - 2 + ex, gj = j0 - 2 + ey;
-      if (p.px) gi = ((gi % p.nx) + p.nx) % p.nx;
-      else gi = min(max(gi, 0), p.nx - 1);
-      if (p.py) gj = ((gj % p.ny) + p.ny) % p.ny;
-      else gj = min(max(gj, 0), p.ny - 1);
-      off[m] = gj * p.nx + gi;
-      q[m].vx = eq[off[m]];
-      q[m].vy = eq[p.N + off[m]];
-      q[m].bm1 = eq[2 * p.N + off[m]];
-      q[m].r = eq[3 * p.N + off[m]];
-      q[m].dr = eq[4 * p.N + off[m]];
+      for (int u = 0; u < SU; ++u) {
+        ee[u] = e + SPL * u;
+        v[u] = 0.f;
+        if (ee[u] < eend && have) v[u] = ldv(src + (size_t)__ldg(s.cls_k + ee[u]) * p.N);
+      }
+#pragma unroll
+      for (int u = 0; u < SU; ++u) {
+        if (ee[u] >= eend) break;
+        const float4* mp = reinterpret_cast<const float4*>(s.cls_mono) + 3 * (size_t)ee[u];
+        const float4 m0 = __ldg(mp), m1 = __ldg(mp + 1), m2 = __ldg(mp + 2);
+        const float x = v[u];
+        kah_add(lo[0], x);
+        kah_add(lo[1], m0.y * x);
+        kah_add(lo[2], m0.z * x);
+        part[0] = fmaf(m0.w, x, part[0]);
+        part[1] = fmaf(m1.x, x, part[1]);
+        part[2] = fmaf(m1.y, x, part[2]);
+        part[3] = fmaf(m1.z, x, part[3]);
+        part[4] = fmaf(m1.w, x, part[4]);
+        part[5] = fmaf(m2.x, x, part[5]);
+        part[6] = fmaf(m2.y, x, part[6]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 7; ++t) kah_add(hi[t], part[t]);
+  }
+#pragma unroll
+  for (int t = 0; t < 3; ++t) red[sub][t][tl] = kah_value(lo[t]);
+#pragma unroll
+  for (int t = 0; t < 7; ++t) red[sub][3 + t][tl] = kah_value(hi[t]);
+  __syncthreads();
+  double* out = s.sums + (size_t)cls * NMONO * p.N;
+  for (int o = threadIdx.x; o < NMONO * CPB; o += 256) {
+    const int t = o / CPB, cc = o % CPB;
+    if (cb0 + cc >= p.N) continue;
+    double v = 0.0;
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) v += red[q][t][cc];
+    out[(size_t)t * p.N + cb0 + cc] = v;
+  }
+}
+
+// --------------------------------------------------------------- cellfin
+// nu_{m,u} = sum xi^m u(a, b) g over a class combination, from its moments
+// mu of g, with a = a0 - hx xi_x, b = b0 - hy xi_y
+__device__ __forceinline__ void stencil_moments(const float (&mu)[NMONO], float a0, float b0,
+                                                float hx, float hy, float (&nu)[NNU]) {
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int mi = m == 1 ? 1 : 0, mj = m == 2 ? 1 : 0;
+    const float M00 = mu[mono_ix(mi, mj)];
+    const float M10 = mu[mono_ix(mi + 1, mj)], M01 = mu[mono_ix(mi, mj + 1)];
+    const float M20 = mu[mono_ix(mi + 2, mj)], M11 = mu[mono_ix(mi + 1, mj + 1)];
+    const float M02 = mu[mono_ix(mi, mj + 2)];
+    nu[6 * m + 0] = M00;
+    nu[6 * m + 1] = fmaf(a0, M00, -hx * M10);
+    nu[6 * m + 2] = fmaf(b0, M00, -hy * M01);
+    nu[6 * m + 3] = fmaf(a0 * a0, M00, fmaf(-2.f * a0 * hx, M10, hx * hx * M20));
+    nu[6 * m + 4] = fmaf(a0 * b0, M00, fmaf(-a0 * hy, M01, fmaf(-b0 * hx, M10, hx * hy * M11)));
+    nu[6 * m + 5] = fmaf(b0 * b0, M00, fmaf(-2.f * b0 * hy, M01, hy * hy * M02));
+  }
+}
+
+// Per cell: rho, u (FP64, from the class sums) into mom, the equilibrium's
+// assembly parameters into eq (FP32), and nu of every combination.
+__global__ void __launch_bounds__(256)
+k_gnc_cellfin(GncStep s, int stage) {
+  const DevParams& p = s.p;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= p.N) return;
+  const size_t N = p.N;
+  double r = s.ref.W, jx = s.ref.Wx, jy = s.ref.Wy;
+  for (int c = 0; c < s.ncls; ++c) {
+    const double* sc = s.sums + (size_t)c * NMONO * N + cell;
+    r += sc[0];
+    jx += sc[N];
+    jy += sc[2 * N];
+  }
+  const double ux = jx / r, uy = jy / r;
+  double* mom = stage == 1 ? s.mom_n : s.mom_p;
+  mom[cell] = r;
+  mom[N + cell] = ux;
+  mom[2 * N + cell] = uy;
+  store_par(stage == 1 ? s.eqn : s.eqp, p.N, cell, eq_params_u<float>(r, ux, uy, p.inv_RT, s.ref.rho0));
+  // W_k (rho P(xi_k) - rho0) = W_k sum_q qd_q pi_q(xi_k), q over 1, x, y, xx, xy, yy
+  const double vx = ux * p.inv_RT, vy = uy * p.inv_RT;
+  float qd[6];
+  qd[0] = (float)((r - s.ref.rho0) - 0.5 * r * (ux * vx + uy * vy));
+  qd[1] = (float)(r * vx);
+  qd[2] = (float)(r * vy);
+  qd[3] = (float)(0.5 * r * vx * vx);
+  qd[4] = (float)(r * vx * vy);
+  qd[5] = (float)(0.5 * r * vy * vy);
+  const StageCoef& sc = stage == 1 ? s.s1 : s.s2;
+  const float b = (float)sc.b, omb = (float)(1.0 - sc.b);
+  const float hx = (float)(sc.h * p.inv_dx), hy = (float)(sc.h * p.inv_dy);
+  for (int cb = 0; cb < s.ncombo; ++cb) {
+    const GncCombo& C = s.cmb[cb];
+    float mu[NMONO];
+#pragma unroll
+    for (int t = 0; t < NMONO; ++t) mu[t] = 0.f;
+    for (int c = 0; c < s.ncls; ++c) {
+      const float lam = C.lam[c];
+      if (lam == 0.f) continue;
+      const double* sc2 = s.sums + (size_t)c * NMONO * N + cell;
+#pragma unroll
+      for (int t = 0; t < NMONO; ++t) mu[t] = fmaf(lam, (float)sc2[(size_t)t * N], mu[t]);
+    }
+    // g = (1 - b) src + b feq: the equilibrium's part by the combination's
+    // quadrature table zc[p][q] = sum lam W_k pi_p pi_q
+    const float* z = s.zc + (size_t)cb * NMONO * 6;
+#pragma unroll
+    for (int t = 0; t < NMONO; ++t) {
+      float e = 0.f;
+#pragma unroll
+      for (int q = 0; q < 6; ++q) e = fmaf(__ldg(z + 6 * t + q), qd[q], e);
+      mu[t] = fmaf(omb, mu[t], b * e);
+    }
+    float nu[NNU];
+    stencil_moments(mu, C.a0, C.b0, hx, hy, nu);
+    float* o = s.nu + (size_t)cb * NNU * N + cell;
+#pragma unroll
+    for (int t = 0; t < NNU; ++t) o[(size_t)t * N] = nu[t];
+  }
+}
+
+// ---------------------------------------------------------------- ghosts
+// A cell (ci, cj) at most one layer outside the mesh as a combination of
+// cells inside it: periodic wrap, or the quadratic extrapolation across a
+// wall (Q16) -- along x on rows inside the mesh, then along y, so a corner
+// is the y-extrapolation of x-ghosts (as in the oracle).  Writes up to nine
+// (cell index, coefficient) pairs and returns their number.
+__device__ __forceinline__ int ghost_terms_x(const DevParams& p, int ci, int cj, float cf,
+                                             int* idx, float* co) {
+  if (ci < 0 || ci >= p.nx) {
+    if (p.px) {
+      ci = ci < 0 ? ci + p.nx : ci - p.nx;
+    } else {
+      const int i1 = ci < 0 ? 0 : p.nx - 1, sx = ci < 0 ? 1 : -1;
+      idx[0] = cj * p.nx + i1;
+      idx[1] = cj * p.nx + i1 + sx;
+      idx[2] = cj * p.nx + i1 + 2 * sx;
+      co[0] = 3.f * cf;
+      co[1] = -3.f * cf;
+      co[2] = cf;
+      return 3;
     }
   }
-  // slot u must be a compile-time constant after unrolling (registers)
-  __device__ __forceinline__ void load(int u, const T* __restrict__ src, int k, int N) {
-#pragma unroll
-    for (int m = 0; m < EPT; ++m)
-      if (threadIdx.x + NTH * m < NST) raw[u][m] = ldr(src + (size_t)k * N + off[m]);
+  idx[0] = cj * p.nx + ci;
+  co[0] = cf;
+  return 1;
+}
+__device__ __forceinline__ int ghost_terms(const DevParams& p, int ci, int cj, int (&idx)[9],
+                                           float (&co)[9]) {
+  if (cj < 0 || cj >= p.ny) {
+    if (p.py) {
+      cj = cj < 0 ? cj + p.ny : cj - p.ny;
+    } else {
+      const int j1 = cj < 0 ? 0 : p.ny - 1, sy = cj < 0 ? 1 : -1;
+      int n = ghost_terms_x(p, ci, j1, 3.f, idx, co);
+      n += ghost_terms_x(p, ci, j1 + sy, -3.f, idx + n, co + n);
+      n += ghost_terms_x(p, ci, j1 + 2 * sy, 1.f, idx + n, co + n);
+      return n;
+    }
   }
-  // g = a src + b feq = src + b (feq - src) (a + b = 1; this form keeps a
-  // uniform equilibrium exact whatever the rounding of b) into the buffer
-  __device__ __forceinline__ void store(int u, C* __restrict__ buf, C b, C cx, C cy, C w) {
+  return ghost_terms_x(p, ci, cj, 1.f, idx, co);
+}
+
+// --------------------------------------------------------------- facefin
+// Face moments of combination cb for the stencil about cell (ci, cj):
+// M_m = sum_s sum_u t_u(s) nu_{m,u}(cell + s); cells outside the mesh by
+// their ghost terms, the stencil of a cell away from the walls directly
+__device__ void face_moments(const GncStep& s, int cb, int ci, int cj, float (&M)[3]) {
+  const DevParams& p = s.p;
+  const float* base = s.nu + (size_t)cb * NNU * p.N;
+  M[0] = M[1] = M[2] = 0.f;
+  const bool inside = ci >= 1 && ci + 1 < p.nx && cj >= 1 && cj + 1 < p.ny;
+  if (inside) {
+    const float* c0 = base + cj * p.nx + ci;
 #pragma unroll
-    for (int m = 0; m < EPT; ++m) {
-      const int e = threadIdx.x + NTH * m;
-      if (e < NST) {
-        const C r = tof(raw[u][m]);
-        buf[e] = fmx(b, feq_dev<C>(q[m], cx, cy, w) - r, r);
+    for (int t = 0; t < 9; ++t) {
+      const int off = (t / 3 - 1) * p.nx + t % 3 - 1;
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        const float w = s.tu[u][t];
+        if (w == 0.f) continue;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) M[m] = fmaf(w, __ldg(c0 + (size_t)(6 * m + u) * p.N + off), M[m]);
+      }
+    }
+    return;
+  }
+#pragma unroll 1
+  for (int t = 0; t < 9; ++t) {
+    int idx[9];
+    float co[9];
+    const int n = ghost_terms(p, ci + t % 3 - 1, cj + t / 3 - 1, idx, co);
+#pragma unroll 1
+    for (int u = 0; u < 6; ++u) {
+      const float w = s.tu[u][t];
+      if (w == 0.f) continue;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const float* b = base + (size_t)(6 * m + u) * p.N;
+        float v = 0.f;
+        for (int q = 0; q < n; ++q) v = fmaf(co[q], __ldg(b + idx[q]), v);
+        M[m] = fmaf(w, v, M[m]);
       }
     }
   }
-};
+}
+
+// Every face of both directions: the face moments -> the face equilibrium's
+// assembly parameters; at a wall, the leaving velocities by the wall rule
+// and the wall density (bounce-back: the fluid cell's rho; diffuse: from the
+// incoming flux, Q15) into wrho for the walls pass.
+__global__ void __launch_bounds__(256)
+k_gnc_facefin(GncStep s, int stage) {
+  const DevParams& p = s.p;
+  const int nfx = p.ny * (p.nx + 1), nfy = (p.ny + 1) * p.nx;
+  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nfx + nfy) return;
+  const bool xdir = f < nfx;
+  if (!xdir) f -= nfx;
+  const int nf = xdir ? nfx : nfy;
+  // face position: x-face fi between cells (fi - 1, j) and (fi, j); y-face
+  // fj between (i, fj - 1) and (i, fj)
+  const int a = xdir ? f % (p.nx + 1) : f / p.nx;      // fi or fj
+  const int l = xdir ? f / (p.nx + 1) : f % p.nx;      // j or i
+  const int n = xdir ? p.nx : p.ny;
+  const bool per = xdir ? p.px : p.py;
+  if (per && a == n) return;                           // face n is face 0
+  float M[3];
+  int side = -1;
+  if (!per && (a == 0 || a == n)) {
+    side = xdir ? (a == 0 ? SIDE_W : SIDE_E) : (a == 0 ? SIDE_S : SIDE_N);
+    const int ci = xdir ? (a == 0 ? 0 : p.nx - 1) : l;
+    const int cj = xdir ? l : (a == 0 ? 0 : p.ny - 1);
+    face_moments(s, s.c_wf[side], ci, cj, M);
+    double d[3] = {M[0], M[1], M[2]};
+    const double* mom = stage == 1 ? s.mom_n : s.mom_p;
+    double rw;
+    if (p.bc_kind[side] == BC_BOUNCEBACK) {
+      float Mi[3] = {M[0], M[1], M[2]};
+      if (s.c_win[side] != s.c_wf[side]) face_moments(s, s.c_win[side], ci, cj, Mi);
+      rw = mom[cj * p.nx + ci];
+      d[0] += (double)Mi[0] + rw * s.wB[side][0] + s.wH[side][0];
+      d[1] += -(double)Mi[1] + rw * s.wB[side][1] + s.wH[side][1];
+      d[2] += -(double)Mi[2] + rw * s.wB[side][2] + s.wH[side][2];
+    } else {
+      // incoming normal flux sum_{xi.n > 0} (xi.n) f-bar, n the fluid's
+      // outward normal
+      const double qn = (a == 0 ? -1.0 : 1.0) * (xdir ? d[1] : d[2]);
+      rw = (s.ds_out[side] + qn) / p.ds_den[side];
+      for (int m = 0; m < 3; ++m) d[m] += rw * s.wMo[side][m] - s.wWo[side][m];
+    }
+    const int slot = side == SIDE_W ? l : side == SIDE_E ? p.ny + l
+                   : side == SIDE_S ? 2 * p.ny + l : 2 * p.ny + p.nx + l;
+    s.wrho[slot] = rw;
+    store_par(xdir ? s.fpx : s.fpy, nf, f,
+              eq_params_j<float>(s.ref.W + d[0], s.ref.Wx + d[1], s.ref.Wy + d[2], p.inv_RT, s.ref.rho0));
+    return;
+  }
+  // interior: the class with xi.n > 0 about the lower cell, xi.n < 0 about
+  // the upper cell (a tie enters both combinations with weight 1/2, Q4)
+  float Ml[3], Mu[3];
+  if (xdir) {
+    face_moments(s, s.c_lo[0], a - 1, l, Ml);
+    face_moments(s, s.c_up[0], a, l, Mu);
+  } else {
+    face_moments(s, s.c_lo[1], l, a - 1, Ml);
+    face_moments(s, s.c_up[1], l, a, Mu);
+  }
+  const EqF<float> q = eq_params_j<float>(s.ref.W + ((double)Ml[0] + Mu[0]),
+                                          s.ref.Wx + ((double)Ml[1] + Mu[1]),
+                                          s.ref.Wy + ((double)Ml[2] + Mu[2]), p.inv_RT, s.ref.rho0);
+  float* fp = xdir ? s.fpx : s.fpy;
+  store_par(fp, nf, f, q);
+  if (per && a == 0) store_par(fp, nf, xdir ? f + p.nx : f + p.ny * p.nx, q);
+}
+
+// ----------------------------------------------------------------- walls
+
+// Wall faces: f-bar per velocity.  Block: one wall side, WSEG consecutive
+// wall faces, WCH velocities.  Per velocity the strip of cells at distance
+// 0-2 from the wall along the segment (plus three cells on either end) is
+// staged as g in shared memory, the ghosts are extrapolated there (Q16: the
+// x-direction first, on rows inside the mesh, then the y-direction), and
+// each thread forms one face's upwind stencil about the fluid cell.  Written
+// are the fluid-side values of the velocities hitting or running along the
+// wall, and diffuse scattering's f-bar_k = rho_w W_k P(xi_k; u_w) - W_k rho0
+// for the leaving ones; bounce-back's leaving values (eq. BB) are formed by
+// the update from the mirrored velocity's entry.
+constexpr int WSEG = 128;                // wall faces per block
+constexpr int WCH = 32;                  // velocities per block
+constexpr int WTW = WSEG + 6;            // strip positions along the wall
+constexpr int WEPT = (3 * WTW + 127) / 128;   // staged cells per thread
+
+__device__ __forceinline__ int wall_segments(int n) { return (n + WSEG - 1) / WSEG; }
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_gnc_walls(GncStep s, int stage) {
+  __shared__ float st[2][4 * WTW];       // [depth 0 (ghost) .. 3][position]
+  const DevParams& p = s.p;
+  // block -> wall side and segment (walled sides only, in the order W, E, S, N)
+  int id = blockIdx.x, side = -1, seg = 0;
+  for (int sd = 0; sd < 4 && side < 0; ++sd) {
+    const bool xw = sd <= SIDE_E;
+    if (xw ? p.px : p.py) continue;
+    const int ns = wall_segments(xw ? p.ny : p.nx);
+    if (id < ns) side = sd, seg = id;
+    else id -= ns;
+  }
+  if (side < 0) return;
+  const bool xw = side <= SIDE_E;
+  const int nt = xw ? p.ny : p.nx;       // faces along the wall
+  const bool tper = xw ? p.py : p.px;    // the direction along the wall is periodic
+  const int t0 = seg * WSEG, t1 = min(nt, t0 + WSEG);
+  const int k0 = blockIdx.y * WCH, k1 = min(p.nv, k0 + WCH);
+  const T* __restrict__ src = (const T*)(stage == 1 ? s.fhat : s.ftp);
+  const float* __restrict__ eq = stage == 1 ? s.eqn : s.eqp;
+  const float b = (float)(stage == 1 ? s.s1.b : s.s2.b);
+  const float4* vq = (const float4*)s.vq;
+  // cell (depth d = 1..3 from the wall, position tt) of the strip
+  auto cell_of = [&](int d, int tt) {
+    const int i = side == SIDE_W ? d - 1 : side == SIDE_E ? p.nx - d : tt;
+    const int j = side == SIDE_S ? d - 1 : side == SIDE_N ? p.ny - d : tt;
+    return j * p.nx + i;
+  };
+  int sidx[WEPT], soff[WEPT];
+  bool sin_[WEPT];
+  EqF<float> sq[WEPT];
+#pragma unroll
+  for (int m = 0; m < WEPT; ++m) {
+    const int e = threadIdx.x + 128 * m;
+    const int d = 1 + e / WTW, x = e % WTW;
+    int tt = t0 - 3 + x;
+    bool in = e < 3 * WTW;
+    if (tper) tt = ((tt % nt) + nt) % nt;
+    else in = in && tt >= 0 && tt < nt;
+    sin_[m] = in;
+    sidx[m] = e < 3 * WTW ? d * WTW + x : -1;
+    soff[m] = in ? cell_of(d, tt) : 0;
+    if (in) {
+      sq[m].vx = __ldg(eq + soff[m]);
+      sq[m].vy = __ldg(eq + p.N + soff[m]);
+      sq[m].bm1 = __ldg(eq + 2 * p.N + soff[m]);
+      sq[m].r = __ldg(eq + 3 * p.N + soff[m]);
+      sq[m].dr = __ldg(eq + 4 * p.N + soff[m]);
+    }
+  }
+  const int set = side == SIDE_W ? 1 : side == SIDE_E ? 0 : side == SIDE_S ? 3 : 2;
+  const int tt = t0 + threadIdx.x;       // this thread's face
+  const int slot = (side == SIDE_W ? 0 : side == SIDE_E ? p.ny : side == SIDE_S ? 2 * p.ny
+                                                                 : 2 * p.ny + p.nx) + tt;
+  const double rw = tt < t1 ? s.wrho[slot] : 0.0;
+  T raw[WEPT];
+#pragma unroll
+  for (int m = 0; m < WEPT; ++m)
+    if (sin_[m] && k0 < k1) raw[m] = ldr(src + (size_t)k0 * p.N + soff[m]);
+  for (int k = k0; k < k1; ++k) {
+    float* g = st[(k - k0) & 1];
+    const float4 e4 = ld4(vq + p.nv + k);
+#pragma unroll
+    for (int m = 0; m < WEPT; ++m)
+      if (sidx[m] >= 0) {
+        float v = 0.f;
+        if (sin_[m]) {
+          const float r = tof(raw[m]);
+          v = fmaf(b, feq_dev<float>(sq[m], e4.x, e4.y, e4.z) - r, r);
+        }
+        g[sidx[m]] = v;
+      }
+    if (k + 1 < k1) {
+#pragma unroll
+      for (int m = 0; m < WEPT; ++m)
+        if (sin_[m]) raw[m] = ldr(src + (size_t)(k + 1) * p.N + soff[m]);
+    }
+    __syncthreads();
+    // ghosts: across the x-direction first (rows inside the mesh), then y
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool normal = (pass == 0) == xw;   // this pass extrapolates across the wall
+      if (normal) {
+        for (int x = threadIdx.x; x < WTW; x += 128) {
+          const int t = t0 - 3 + x;
+          if (xw && !tper && (t < 0 || t >= nt)) continue;     // corner: filled by the y pass
+          g[x] = 3.f * g[WTW + x] - 3.f * g[2 * WTW + x] + g[3 * WTW + x];
+        }
+      } else if (!tper) {
+        for (int q = threadIdx.x; q < 8; q += 128) {
+          const int d = q & 3, lowend = q < 4;
+          if (!xw && d == 0) continue;         // the y-ghost row is formed after
+          const int xg = (lowend ? -1 : nt) - (t0 - 3);        // ghost position
+          const int s1 = lowend ? 1 : -1;
+          if (xg < 0 || xg >= WTW || xg + 3 * s1 < 0 || xg + 3 * s1 >= WTW) continue;
+          float* r = g + d * WTW;
+          r[xg] = 3.f * r[xg + s1] - 3.f * r[xg + 2 * s1] + r[xg + 3 * s1];
+        }
+      }
+      __syncthreads();
+    }
+    if (tt < t1) {
+      const float* w = s.fwt + ((size_t)(stage - 1) * p.nv + k) * WPV + 12 * set;
+      float v = 0.f;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int dy = t / 3 - 1, dx = t % 3 - 1;
+        const int d = side == SIDE_W ? dx + 1 : side == SIDE_E ? 1 - dx : side == SIDE_S ? dy + 1 : 1 - dy;
+        const int q = xw ? dy : dx;
+        v = fmaf(__ldg(w + t), g[d * WTW + (tt + q - t0 + 3)], v);
+      }
+      const float xn = side == SIDE_W ? -e4.x : side == SIDE_E ? e4.x : side == SIDE_S ? -e4.y : e4.y;
+      if (xn < 0.f && p.bc_kind[side] == BC_DIFFUSE)
+        v = (float)fma(rw, __ldg(p.feq_wall + (size_t)side * p.nv + k), -__ldg(p.w + k) * s.ref.rho0);
+      s.wf[(size_t)k * s.nw + slot] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- update
+// F(xi) = (x/dx)(P_E - P_W) + (y/dy)(P_N - P_S) over the faces of cell
+// (i, j), scaled by sc (the face equilibria's part of the micro-flux)
+__device__ __forceinline__ Cubic<float> gnc_flux_cubic(const GncStep& s, int i, int j, float sc) {
+  const int nx = s.p.nx, ny = s.p.ny;
+  const int nfx = ny * (nx + 1), nfy = (ny + 1) * nx;
+  const int fx = j * (nx + 1) + i, fy = j * nx + i;
+  const Quad<float> w = quad(s.fpx, nfx, fx), e = quad(s.fpx, nfx, fx + 1);
+  const Quad<float> so = quad(s.fpy, nfy, fy), no = quad(s.fpy, nfy, fy + nx);
+  const float ax = sc * (float)s.p.inv_dx, ay = sc * (float)s.p.inv_dy;
+  Cubic<float> F;
+  F.c[0] = 0.f;
+  F.c[1] = ax * (e.c0 - w.c0);
+  F.c[2] = ay * (no.c0 - so.c0);
+  F.c[3] = ax * (e.cx - w.cx);
+  F.c[4] = fmaf(ax, e.cy - w.cy, ay * (no.cx - so.cx));
+  F.c[5] = ay * (no.cy - so.cy);
+  F.c[6] = ax * (e.cxx - w.cxx);
+  F.c[7] = fmaf(ax, e.cxy - w.cxy, ay * (no.cxx - so.cxx));
+  F.c[8] = fmaf(ax, e.cyy - w.cyy, ay * (no.cxy - so.cxy));
+  F.c[9] = ay * (no.cyy - so.cyy);
+  return F;
+}
+__device__ __forceinline__ void add_quad(Cubic<float>& S, const Quad<float>& q, float sc) {
+  S.c[0] = fmaf(sc, q.c0, S.c[0]);
+  S.c[1] = fmaf(sc, q.cx, S.c[1]);
+  S.c[2] = fmaf(sc, q.cy, S.c[2]);
+  S.c[3] = fmaf(sc, q.cxx, S.c[3]);
+  S.c[4] = fmaf(sc, q.cxy, S.c[4]);
+  S.c[5] = fmaf(sc, q.cyy, S.c[5]);
+}
+
+__device__ __forceinline__ float dot9(const float (&T)[9], float s00, float s01, float s02,
+                                      float s10, float s11, float s12, float s20, float s21,
+                                      float s22) {
+  float v = T[0] * s00;
+  v = fmaf(T[1], s01, v);
+  v = fmaf(T[2], s02, v);
+  v = fmaf(T[3], s10, v);
+  v = fmaf(T[4], s11, v);
+  v = fmaf(T[5], s12, v);
+  v = fmaf(T[6], s20, v);
+  v = fmaf(T[7], s21, v);
+  return fmaf(T[8], s22, v);
+}
+// the 3 x 3 window of W with lower-left corner (row r, column c): rows
+// south to north, columns west to east (the order of eq. flux_DS's weights)
+#define WIN3(W, r, c)                                                                      \
+  W[r][c], W[r][(c) + 1], W[r][(c) + 2], W[(r) + 1][c], W[(r) + 1][(c) + 1],                 \
+      W[(r) + 1][(c) + 2], W[(r) + 2][c], W[(r) + 2][(c) + 1], W[(r) + 2][(c) + 2]
+
+__device__ __forceinline__ void read9(const float* __restrict__ w, float (&T)[9]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(w));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(w) + 1);
+  T[0] = a.x; T[1] = a.y; T[2] = a.z; T[3] = a.w;
+  T[4] = b.x; T[5] = b.y; T[6] = b.z; T[7] = b.w;
+  T[8] = __ldg(w + 8);
+}
 
 // Wall ghosts of a staged plane (reading Q16): first across x-walls on the
-// rows inside the mesh, then across y-walls on every staged column, so a
-// corner ghost is the y-extrapolation of x-ghosts (as in the oracle).
-// Uniform per block: every thread calls it, syncs included.
-template <typename C>
-__device__ __forceinline__ void stage_ghosts(const DevParams& p, C* __restrict__ buf, int i0,
+// rows inside the mesh, then across y-walls on every staged column.  Uniform
+// per block: every thread calls it, syncs included.
+__device__ __forceinline__ void stage_ghosts(const DevParams& p, float* __restrict__ g, int i0,
                                              int j0, bool wx, bool wy) {
   if (wx) {
-    const int xw = 1 - i0;                 // column of the west ghost (gi = -1)
-    const int xe = p.nx - i0 + 2;          // column of the east ghost (gi = nx)
-    for (int t = threadIdx.x; t < 2 * HYT; t += NTH) {
+    const int xw = 1 - i0;                 // staged column of the west ghost (gi = -1)
+    const int xe = p.nx - i0 + 2;          // staged column of the east ghost (gi = nx)
+    for (int t = threadIdx.x; t < 2 * HYT; t += UNT) {
       const int ey = t % HYT;
       const int gj = j0 - 2 + ey;
       if (!p.py && (gj < 0 || gj >= p.ny)) continue;
-      C* r = buf + ey * HXT;
+      float* r = g + ey * HXT;
       if (t < HYT) {
-        if (xw >= 0 && xw + 3 < HXT) r[xw] = C(3) * r[xw + 1] - C(3) * r[xw + 2] + r[xw + 3];
+        if (xw >= 0 && xw + 3 < HXT) r[xw] = 3.f * r[xw + 1] - 3.f * r[xw + 2] + r[xw + 3];
       } else if (xe >= 3 && xe < HXT) {
-        r[xe] = C(3) * r[xe - 1] - C(3) * r[xe - 2] + r[xe - 3];
+        r[xe] = 3.f * r[xe - 1] - 3.f * r[xe - 2] + r[xe - 3];
       }
     }
     __syncthreads();
   }
   if (wy) {
     const int ys = 1 - j0, yn = p.ny - j0 + 2;
-    for (int t = threadIdx.x; t < 2 * HXT; t += NTH) {
+    for (int t = threadIdx.x; t < 2 * HXT; t += UNT) {
       const int ex = t % HXT;
-      C* c = buf + ex;
+      float* c = g + ex;
       if (t < HXT) {
         if (ys >= 0 && ys + 3 < HYT)
-          c[ys * HXT] = C(3) * c[(ys + 1) * HXT] - C(3) * c[(ys + 2) * HXT] + c[(ys + 3) * HXT];
+          c[ys * HXT] = 3.f * c[(ys + 1) * HXT] - 3.f * c[(ys + 2) * HXT] + c[(ys + 3) * HXT];
       } else if (yn >= 3 && yn < HYT) {
-        c[yn * HXT] = C(3) * c[(yn - 1) * HXT] - C(3) * c[(yn - 2) * HXT] + c[(yn - 3) * HXT];
+        c[yn * HXT] = 3.f * c[(yn - 1) * HXT] - 3.f * c[(yn - 2) * HXT] + c[(yn - 3) * HXT];
       }
     }
     __syncthreads();
   }
 }
 
-__device__ __forceinline__ bool tile_touches_walls_x(const DevParams& p, int i0) {
-  return !p.px && (i0 == 0 || i0 + TXT + 2 >= p.nx);
-}
-__device__ __forceinline__ bool tile_touches_walls_y(const DevParams& p, int j0) {
-  return !p.py && (j0 == 0 || j0 + TYT + 2 >= p.ny);
-}
-
-// ------------------------------------------------------------------ faces
-// Face pass of a stage: partial moments over the chunk of the x-face at the
-// left and the y-face below every cell of the tile (interior faces only).
-// Velocity planes are loaded PD velocities ahead into registers; one block
-// barrier per velocity (two more on tiles with wall ghosts).
-template <typename T>
-__global__ void __launch_bounds__(NTH, 2)
-k_gnc_faces(GncStep s, int stage) {
-  using C = float;
-  using V4 = float4;
-  __shared__ C gs[2][NST];
-  __shared__ __align__(16) float wts[KCMAX * WPV];
-  const DevParams& p = s.p;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int tiles = s.tiles_x * s.tiles_y;
-  const int tile = blockIdx.x % tiles, chunk = blockIdx.x / tiles;
-  const int i0 = (tile % s.tiles_x) * TXT, j0 = (tile / s.tiles_x) * TYT;
-  const int k0 = chunk * s.kc, k1 = min(p.nv, k0 + s.kc);
-  const StageCoef& sc = stage == 1 ? s.s1 : s.s2;
-  const T* __restrict__ src = (const T*)(stage == 1 ? s.fhat : s.ftp);
-  const C* __restrict__ eq = (const C*)(stage == 1 ? s.eqn : s.eqp);
-  const C b = (C)sc.b;
-  const V4* vq = (const V4*)s.vq;
-  const bool wx = tile_touches_walls_x(p, i0), wy = tile_touches_walls_y(p, j0);
-
-  // the thread's cells (column i, rows j, j + 1) and which of their faces count
-  const int i = i0 + lane;
-  bool fx[2], fy[2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int j = j0 + 2 * warp + q;
-    const bool cell = i < p.nx && j < p.ny;
-    fx[q] = cell && (p.px || i >= 1);
-    fy[q] = cell && (p.py || j >= 1);
-  }
-  Kah ax[2][3] = {}, ay[2][3] = {};
-
-  load_weights(wts, s, stage, k0, k1);
-  Stager<T> st;
-  st.init(s, eq, i0, j0);
-#pragma unroll
-  for (int u = 0; u < PD; ++u)
-    if (k0 + u < k1) st.load(u, src, k0 + u, p.N);
-  int buf = 0;
-  for (int kb = k0; kb < k1; kb += PD) {
-#pragma unroll
-    for (int u = 0; u < PD; ++u) {
-      const int k = kb + u;
-      if (k >= k1) break;                            // uniform over the block
-      const V4 e4 = ld4(vq + p.nv + k);
-      st.store(u, gs[buf], b, e4.x, e4.y, e4.z);
-      if (k + PD < k1) st.load(u, src, k + PD, p.N);
-      __syncthreads();
-      stage_ghosts<C>(p, gs[buf], i0, j0, wx, wy);
-      FaceW fw;
-      face_weights(fw, wts + (k - k0) * WPV, e4.x, e4.y);
-      // window: staged rows 2w .. 2w + 4, columns lane .. lane + 3
-      C Wn[5][4];
-      const C* g0 = gs[buf] + (2 * warp) * HXT + lane;
-#pragma unroll
-      for (int r = 0; r < 5; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) Wn[r][c] = g0[r * HXT + c];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        // cell q sits at window (2, 2 + q)
-        if (fx[q]) {
-          const C v = xface(fw, Wn, 1, 2 + q);
-          kah_add(ax[q][0], v);
-          kah_add(ax[q][1], e4.x * v);
-          kah_add(ax[q][2], e4.y * v);
-        }
-        if (fy[q]) {
-          const C v = yface(fw, Wn, 2, 1 + q);
-          kah_add(ay[q][0], v);
-          kah_add(ay[q][1], e4.x * v);
-          kah_add(ay[q][2], e4.y * v);
-        }
-      }
-      buf ^= 1;
-    }
-  }
-  const int nfx = p.ny * (p.nx + 1), nfy = (p.ny + 1) * p.nx;
-  double* px = s.pfx + (size_t)chunk * 3 * nfx;
-  double* py = s.pfy + (size_t)chunk * 3 * nfy;
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int j = j0 + 2 * warp + q;
-    if (fx[q]) {
-      const int f = j * (p.nx + 1) + i;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) px[(size_t)m * nfx + f] = kah_value(ax[q][m]);
-    }
-    if (fy[q]) {
-      const int f = j * p.nx + i;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) py[(size_t)m * nfy + f] = kah_value(ay[q][m]);
-    }
-  }
-}
-
-// --------------------------------------------------------------- facefin
-// Interior faces of both directions: chunk sums (in chunk order) -> the face
-// equilibrium's assembly parameters.
-template <typename C>
-__global__ void __launch_bounds__(256)
-k_gnc_facefin(GncStep s) {
-  const DevParams& p = s.p;
-  const int nfx = p.ny * (p.nx + 1), nfy = (p.ny + 1) * p.nx;
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= nfx + nfy) return;
-  const bool xdir = f < nfx;
-  const int nf = xdir ? nfx : nfy;
-  if (!xdir) f -= nfx;
-  if (xdir) {
-    const int fi = f % (p.nx + 1);
-    if ((!p.px && (fi == 0 || fi == p.nx)) || (p.px && fi == p.nx)) return;
+// staged position (column, row) of halo cell h of a tile: rows 0-1, rows
+// 18-19, then columns 0, 1, 34, 35 of rows 2-17
+__device__ __forceinline__ void halo_pos(int h, int& sx, int& sy) {
+  if (h < 2 * HXT) {
+    sy = h / HXT;
+    sx = h % HXT;
+  } else if (h < 4 * HXT) {
+    sy = TYT + 2 + (h - 2 * HXT) / HXT;
+    sx = (h - 2 * HXT) % HXT;
   } else {
-    const int fj = f / p.nx;
-    if ((!p.py && (fj == 0 || fj == p.ny)) || (p.py && fj == p.ny)) return;
+    const int t = h - 4 * HXT;
+    sy = 2 + t / 4;
+    const int c = t % 4;
+    sx = c < 2 ? c : TXT + c;
   }
-  const double* part = xdir ? s.pfx : s.pfy;
-  double r = s.ref.W, jx = s.ref.Wx, jy = s.ref.Wy;
-  for (int c = 0; c < s.nch; ++c) {
-    const double* pc = part + (size_t)c * 3 * nf;
-    r += pc[f];
-    jx += pc[nf + f];
-    jy += pc[2 * nf + f];
-  }
-  C* fp = (C*)(xdir ? s.fpx : s.fpy);
-  const EqF<C> q = eq_params_j<C>(r, jx, jy, p.inv_RT, s.ref.rho0);
-  store_par(fp, nf, f, q);
-  // a periodic direction's face n is face 0
-  if (xdir && p.px && f % (p.nx + 1) == 0) store_par(fp, nf, f + p.nx, q);
-  if (!xdir && p.py && f / p.nx == 0) store_par(fp, nf, f + p.ny * p.nx, q);
-}
-
-// --------------------------------------------------------------- cellfin
-// Cell moments from the chunk partials: rho, u (FP64) and the equilibrium
-// parameters of the stage that reads them (which 0: f^ at t_n, 1: f~(t')).
-template <typename C>
-__global__ void __launch_bounds__(256)
-k_gnc_cellfin(GncStep s, int which) {
-  const DevParams& p = s.p;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= p.N) return;
-  double r = s.ref.W, jx = s.ref.Wx, jy = s.ref.Wy;
-  for (int c = 0; c < s.nch; ++c) {
-    const double* pc = s.pc + (size_t)c * 3 * p.N;
-    r += pc[cell];
-    jx += pc[p.N + cell];
-    jy += pc[2 * p.N + cell];
-  }
-  const double rinv = 1.0 / r;
-  const double ux = jx * rinv, uy = jy * rinv;
-  double* mom = which == 0 ? s.mom_n : s.mom_p;
-  mom[cell] = r;
-  mom[p.N + cell] = ux;
-  mom[2 * p.N + cell] = uy;
-  store_par((C*)(which == 0 ? s.eqn : s.eqp), p.N, cell,
-            eq_params_u<C>(r, ux, uy, p.inv_RT, s.ref.rho0));
-}
-
-// Cell moments of the stored state over the chunks (the state's first
-// step, or after it was set): one thread per cell.
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_gnc_moments(GncStep s) {
-  using C = typename Prec<T>::C;
-  using V4 = typename Prec<T>::V4;
-  const DevParams& p = s.p;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= p.N) return;
-  const V4* vq = (const V4*)s.vq;
-  const int chunk = blockIdx.y;
-  const int k0 = chunk * s.kc, k1 = min(p.nv, k0 + s.kc);
-  Acc<C> a0{}, a1{}, a2{};
-  const T* src = (const T*)s.fhat;
-  for (int k = k0; k < k1; ++k) {
-    const C d = ldv(src + (size_t)k * p.N + cell);
-    const V4 xq = ld4(vq + k);
-    acc_add(a0, d);
-    acc_addprod(a1, xq.x, xq.y, d);
-    acc_addprod(a2, xq.z, xq.w, d);
-  }
-  double* pc = s.pc + (size_t)chunk * 3 * p.N;
-  pc[cell] = acc_value(a0);
-  pc[p.N + cell] = acc_value(a1);
-  pc[2 * p.N + cell] = acc_value(a2);
-}
-
-// ----------------------------------------------------------------- walls
-// g of velocity k at cell (ci, cj) inside the mesh, from the stage source
-template <typename T>
-__device__ __forceinline__ typename Prec<T>::C g_cell(const GncStep& s, const T* __restrict__ src,
-                                                      const typename Prec<T>::C* __restrict__ eq,
-                                                      int k, int ci, int cj,
-                                                      typename Prec<T>::C a,
-                                                      typename Prec<T>::C b) {
-  using C = typename Prec<T>::C;
-  using V4 = typename Prec<T>::V4;
-  const DevParams& p = s.p;
-  const int c = cj * p.nx + ci;
-  EqF<C> q;
-  q.vx = eq[c];
-  q.vy = eq[p.N + c];
-  q.bm1 = eq[2 * p.N + c];
-  q.r = eq[3 * p.N + c];
-  q.dr = eq[4 * p.N + c];
-  const V4 e4 = ld4((const V4*)s.vq + p.nv + k);
-  const C r = ldv(src + (size_t)k * p.N + c);
-  (void)a;
-  return fmx(b, feq_dev<C>(q, e4.x, e4.y, e4.z) - r, r);     // src + b (feq - src)
-}
-// g within one ghost layer: periodic wrap, or the quadratic extrapolation
-// across a wall -- along x on rows inside the mesh, then along y (Q16)
-template <typename T>
-__device__ typename Prec<T>::C g_ghost(const GncStep& s, const T* __restrict__ src,
-                                       const typename Prec<T>::C* __restrict__ eq, int k,
-                                       int ci, int cj, typename Prec<T>::C a,
-                                       typename Prec<T>::C b) {
-  using C = typename Prec<T>::C;
-  const DevParams& p = s.p;
-  if (cj < 0 || cj >= p.ny) {
-    if (p.py) {
-      cj = (cj < 0) ? cj + p.ny : cj - p.ny;
-    } else {
-      const int j0 = cj < 0 ? 0 : p.ny - 1, sg = cj < 0 ? 1 : -1;
-      C v[3];
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        int ii = ci;
-        if (ii < 0 || ii >= p.nx) {
-          if (p.px) {
-            ii = ii < 0 ? ii + p.nx : ii - p.nx;
-            v[t] = g_cell<T>(s, src, eq, k, ii, j0 + t * sg, a, b);
-          } else {
-            const int i1 = ii < 0 ? 0 : p.nx - 1, sx = ii < 0 ? 1 : -1;
-            v[t] = C(3) * g_cell<T>(s, src, eq, k, i1, j0 + t * sg, a, b) -
-                   C(3) * g_cell<T>(s, src, eq, k, i1 + sx, j0 + t * sg, a, b) +
-                   g_cell<T>(s, src, eq, k, i1 + 2 * sx, j0 + t * sg, a, b);
-          }
-        } else {
-          v[t] = g_cell<T>(s, src, eq, k, ii, j0 + t * sg, a, b);
-        }
-      }
-      return C(3) * v[0] - C(3) * v[1] + v[2];
-    }
-  }
-  if (ci < 0 || ci >= p.nx) {
-    if (p.px) {
-      ci = ci < 0 ? ci + p.nx : ci - p.nx;
-    } else {
-      const int i1 = ci < 0 ? 0 : p.nx - 1, sx = ci < 0 ? 1 : -1;
-      return C(3) * g_cell<T>(s, src, eq, k, i1, cj, a, b) -
-             C(3) * g_cell<T>(s, src, eq, k, i1 + sx, cj, a, b) +
-             g_cell<T>(s, src, eq, k, i1 + 2 * sx, cj, a, b);
-    }
-  }
-  return g_cell<T>(s, src, eq, k, ci, cj, a, b);
-}
-// f-bar of velocity k at a wall face from the fluid cell (ci, cj): eq.
-// flux_DS about that cell, foot offset (X, Y) from its centre
-template <typename T>
-__device__ typename Prec<T>::C wall_recon(const GncStep& s, const T* __restrict__ src,
-                                          const typename Prec<T>::C* __restrict__ eq, int k,
-                                          int ci, int cj, typename Prec<T>::C X,
-                                          typename Prec<T>::C Y, typename Prec<T>::C a,
-                                          typename Prec<T>::C b) {
-  using C = typename Prec<T>::C;
-  C w[9];
-  flux_ds_weights<C>(X * (C)s.p.inv_dx, Y * (C)s.p.inv_dy, w);
-  C v = C(0);
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx)
-      v = fmx(w[(dy + 1) * 3 + dx + 1], g_ghost<T>(s, src, eq, k, ci + dx, cj + dy, a, b), v);
-  return v;
-}
-
-// One wall face per block (both directions in one launch), threads over the
-// velocities: fluid-side f-bar for velocities hitting or running along the
-// wall, the wall rule for those leaving it, the face's moments and
-// equilibrium parameters; f-bar into the wall arrays.  Face id per
-// direction = 2 line + (0: W/S, 1: E/N).
-template <typename T, int DIR>
-__device__ __forceinline__ void gnc_wall_face(const GncStep& s, int stage, int id, double* sm) {
-  using C = typename Prec<T>::C;
-  using V4 = typename Prec<T>::V4;
-  const DevParams& p = s.p;
-  const GDevRef& ref = s.ref;
-  const V4* vq = (const V4*)s.vq;
-  const StageCoef& sc = stage == 1 ? s.s1 : s.s2;
-  const T* __restrict__ src = (const T*)(stage == 1 ? s.fhat : s.ftp);
-  const C* __restrict__ eq = (const C*)(stage == 1 ? s.eqn : s.eqp);
-  const double* mom = stage == 1 ? s.mom_n : s.mom_p;
-  const C a = (C)sc.a, b = (C)sc.b, h = (C)sc.h;
-  const int nx = p.nx, ny = p.ny, nv = p.nv;
-  const int nf = DIR == 0 ? ny * (nx + 1) : (ny + 1) * nx;
-  const int nl = DIR == 0 ? ny : nx;
-  const bool upper_wall = id & 1;
-  const int line = id >> 1;
-  const int face = DIR == 0 ? line * (nx + 1) + (upper_wall ? nx : 0)
-                            : (upper_wall ? ny : 0) * nx + line;
-  const int side = DIR == 0 ? (upper_wall ? SIDE_E : SIDE_W) : (upper_wall ? SIDE_N : SIDE_S);
-  const bool fluid_hi = !upper_wall;
-  const C nsg = fluid_hi ? C(-1) : C(1);
-  const int ci = DIR == 0 ? (fluid_hi ? 0 : nx - 1) : line;
-  const int cj = DIR == 0 ? line : (fluid_hi ? 0 : ny - 1);
-  const int kind = p.bc_kind[side];
-  const C half = C(0.5) * (C)(DIR == 0 ? p.dx : p.dy);
-  const C off = fluid_hi ? -half : half;
-  const C rho_w = (C)mom[cj * nx + ci];
-  const C uwx = (C)p.uw_x[side], uwy = (C)p.uw_y[side];
-  const C irt = (C)p.inv_RT;
-  C* wf = (C*)(DIR == 0 ? s.wfx : s.wfy);
-  const size_t wstride = 2 * (size_t)nl;
-  const int wslot = (upper_wall ? 1 : 0) * nl + line;
-  auto recon = [&](int k) {
-    const V4 e4 = ld4(vq + nv + k);
-    const C X = DIR == 0 ? off - e4.x * h : -e4.x * h;
-    const C Y = DIR == 0 ? -e4.y * h : off - e4.y * h;
-    return wall_recon<T>(s, src, eq, k, ci, cj, X, Y, a, b);
-  };
-  Acc<C> a0{}, a1{}, a2{}, a3{};
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-    const V4 xq = ld4(vq + k);
-    const C cx = xq.x, cy = xq.z;
-    const C xn = nsg * (DIR == 0 ? cx : cy);
-    C fbar;
-    if (xn >= C(0)) {
-      fbar = recon(k);
-      if (xn > C(0))
-        acc_addprod(a3, DIR == 0 ? nsg * xq.x : nsg * xq.z, DIR == 0 ? nsg * xq.y : nsg * xq.w,
-                    fbar);
-    } else if (kind == BC_BOUNCEBACK) {            // eq. BB on f-bar
-      const int kk = __ldg(p.opp + k);
-      const C wk = ld4(vq + nv + k).z;
-      const C bbk = C(2) * wk * fmx(cx, uwx, cy * uwy) * irt;
-      const C shift = (ld4(vq + nv + kk).z - wk) * (C)ref.rho0;
-      fbar = fmx(rho_w, bbk, recon(kk) + shift);
-    } else {
-      continue;                                    // diffuse: after the reduction
-    }
-    wf[(size_t)k * wstride + wslot] = fbar;
-    acc_add(a0, fbar);
-    acc_addprod(a1, xq.x, xq.y, fbar);
-    acc_addprod(a2, xq.z, xq.w, fbar);
-  }
-  double v[4] = {acc_value(a0), acc_value(a1), acc_value(a2), acc_value(a3)};
-  block_sum<4>(v, sm);
-  if (kind == BC_DIFFUSE) {                        // uniform over the block
-    // rho_w balances the outgoing flux of f = W rho0 + d (Sec. 2.3, Q15)
-    const double rho_ds = (s.ds_out[side] + v[3]) / p.ds_den[side];
-    Acc<C> b0{}, b1{}, b2{};
-    for (int k = threadIdx.x; k < nv; k += blockDim.x) {
-      const V4 xq = ld4(vq + k);
-      const C xn = nsg * (DIR == 0 ? xq.x : xq.z);
-      if (xn < C(0)) {
-        const C fbar =
-            to_c<C>(fma(rho_ds, __ldg(p.feq_wall + side * nv + k), -__ldg(p.w + k) * ref.rho0));
-        wf[(size_t)k * wstride + wslot] = fbar;
-        acc_add(b0, fbar);
-        acc_addprod(b1, xq.x, xq.y, fbar);
-        acc_addprod(b2, xq.z, xq.w, fbar);
-      }
-    }
-    double w2[3] = {acc_value(b0), acc_value(b1), acc_value(b2)};
-    block_sum<3>(w2, sm);
-    v[0] += w2[0];
-    v[1] += w2[1];
-    v[2] += w2[2];
-  }
-  if (threadIdx.x == 0)
-    store_par((C*)(DIR == 0 ? s.fpx : s.fpy), nf, face,
-              eq_params_j<C>(ref.W + v[0], ref.Wx + v[1], ref.Wy + v[2], p.inv_RT, ref.rho0));
-}
-
-// blocks [0, nwx): x-direction walls (W/E), then y-direction walls (S/N)
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_gnc_walls(GncStep s, int stage, int nwx) {
-  __shared__ double sm[32 * 4];
-  if ((int)blockIdx.x < nwx) gnc_wall_face<T, 0>(s, stage, blockIdx.x, sm);
-  else gnc_wall_face<T, 1>(s, stage, blockIdx.x - nwx, sm);
-}
-
-// ---------------------------------------------------------------- update
-// F(xi) = (x/dx)(P_E - P_W) + (y/dy)(P_N - P_S) over the faces of cell
-// (i, j), scaled by sc (the face equilibria's part of the micro-flux)
-template <typename C>
-__device__ __forceinline__ Cubic<C> gnc_flux_cubic(const GncStep& s, int i, int j, C sc) {
-  const int nx = s.p.nx, ny = s.p.ny;
-  const int nfx = ny * (nx + 1), nfy = (ny + 1) * nx;
-  const int fx = j * (nx + 1) + i, fy = j * nx + i;
-  const C* fpx = (const C*)s.fpx;
-  const C* fpy = (const C*)s.fpy;
-  const Quad<C> w = quad(fpx, nfx, fx), e = quad(fpx, nfx, fx + 1);
-  const Quad<C> so = quad(fpy, nfy, fy), no = quad(fpy, nfy, fy + nx);
-  const C ax = sc * (C)s.p.inv_dx, ay = sc * (C)s.p.inv_dy;
-  Cubic<C> F;
-  F.c[0] = C(0);
-  F.c[1] = ax * (e.c0 - w.c0);
-  F.c[2] = ay * (no.c0 - so.c0);
-  F.c[3] = ax * (e.cx - w.cx);
-  F.c[4] = fmx(ax, e.cy - w.cy, ay * (no.cx - so.cx));
-  F.c[5] = ay * (no.cy - so.cy);
-  F.c[6] = ax * (e.cxx - w.cxx);
-  F.c[7] = fmx(ax, e.cxy - w.cxy, ay * (no.cxx - so.cxx));
-  F.c[8] = fmx(ax, e.cyy - w.cyy, ay * (no.cxy - so.cxy));
-  F.c[9] = ay * (no.cyy - so.cyy);
-  return F;
-}
-template <typename C>
-__device__ __forceinline__ void add_quad(Cubic<C>& S, const Quad<C>& q, C sc) {
-  S.c[0] = fmx(sc, q.c0, S.c[0]);
-  S.c[1] = fmx(sc, q.cx, S.c[1]);
-  S.c[2] = fmx(sc, q.cy, S.c[2]);
-  S.c[3] = fmx(sc, q.cxx, S.c[3]);
-  S.c[4] = fmx(sc, q.cxy, S.c[4]);
-  S.c[5] = fmx(sc, q.cyy, S.c[5]);
 }
 
 // Update pass.  With Df = kx (fbar_E - fbar_W) + ky (fbar_N - fbar_S),
@@ -710,189 +660,579 @@ __device__ __forceinline__ void add_quad(Cubic<C>& S, const Quad<C>& q, C sc) {
 // coefficient on both sides of each difference, the maps keep a uniform
 // equilibrium exact whatever the rounding of the coefficients (their exact
 // sum is one; written as a plain sum of terms an FP32 step would scale the
-// deviations by 1 + O(2^-24) every step).  The output's chunk moments go to
-// pc.
-template <typename T, int STAGE>
-__global__ void __launch_bounds__(NTH, 2)
+// deviations by 1 + O(2^-24) every step).
+//
+// Warp w takes rows 4w .. 4w + 3 of the tile, lane l column i0 + l.  Each
+// lane forms the x-face west of each of its cells and the y-faces south of
+// them and north of the last; the east face comes from the next lane, and
+// lanes 0-3 form the east faces of the tile's last column (for lane 31).
+// One barrier per velocity plane (the planes are double-buffered), two more
+// on tiles whose halo reaches a wall.
+// Ring of per-velocity inputs of the update, NRING planes deep, filled by
+// asynchronous copies NRING - 1 planes ahead: the staged plane (FP32
+// storage; BF16 arrives through registers), the face weights, the velocity's
+// table rows, its bounce-back coefficients, f^ of the tile's cells (stage 2,
+// FP32) and the tile's wall-face values.  Offsets in floats, 16-byte aligned.
+constexpr int NRING = 4;
+constexpr int NWALL = 2 * TYT + 2 * TXT;          // W rows, E rows, S columns, N columns
+constexpr int RG = 0;                             // g (source values until converted)
+constexpr int RW = RG + NST;                      // face weights (WPV)
+constexpr int RV = RW + WPV;                      // (xi_x, xi_y, W, 0), flux factors
+constexpr int RC = RV + 8;                        // bounce-back (c_k, shift_k) per side
+constexpr int RF = RC + 8;                        // f^ of the tile's cells
+constexpr int RB = RF + TXT * TYT;                // wall-face f-bar
+constexpr int RPL = RB + NWALL;
+static_assert(RW % 4 == 0 && RV % 4 == 0 && RC % 4 == 0 && RF % 4 == 0 && RPL % 4 == 0,
+              "ring regions must be 16-byte aligned");
+
+// two partial chains: the dependent-FMA depth of a 3 x 3 stencil halves
+__device__ __forceinline__ float dot9s(const float* __restrict__ T, float s00, float s01, float s02,
+                                       float s10, float s11, float s12, float s20, float s21,
+                                       float s22) {
+  float u = T[0] * s00;
+  float v = T[1] * s01;
+  u = fmaf(T[2], s02, u);
+  v = fmaf(T[3], s10, v);
+  u = fmaf(T[4], s11, u);
+  v = fmaf(T[5], s12, v);
+  u = fmaf(T[6], s20, u);
+  v = fmaf(T[7], s21, v);
+  u = fmaf(T[8], s22, u);
+  return u + v;
+}
+
+// Update pass.  With Df = kx (fbar_E - fbar_W) + ky (fbar_N - fbar_S),
+// k = -(flux scale) alpha xi / dx (velocity table row 2), P_n and P' the
+// cell equilibria at t_n and t', F the faces' equilibria in the flux:
+//   stage 1: f~' = 5/4 g1 - 1/4 f^ + dt/3 L*
+//                = f^ + W S(xi) - sP f^ + Df,
+//            S = sP P_n + sF F, sP = 5/4 b1, sF = -(dt/3) beta1;
+//   stage 2: f^^{n+1} = 4/7 f^ - 6/7 g1 + 9/7 f~' + c34 (f~' - feq') + 4dt/7 L**
+//                = f~' + cA (f^ - f~') + W S(xi) - (sP + sQ) f~' + Df,
+//            S = sP P_n + sQ P' + sF F, cA = 4/7 - 6/7 a1, sP = -6/7 b1,
+//            sQ = -c34, sF = -(4dt/7) beta2.
+// Written around f^ (stage 1) or f~' (stage 2) with the same rounded
+// coefficient on both sides of each difference, the maps keep a uniform
+// equilibrium exact whatever the rounding of the coefficients (their exact
+// sum is one; written as a plain sum of terms an FP32 step would scale the
+// deviations by 1 + O(2^-24) every step).
+//
+// Warp w takes rows 4w .. 4w + 3 of the tile, lane l column i0 + l.  Each
+// lane forms the x-face west of each of its cells and the y-faces south of
+// them and north of the last; the east face comes from the next lane, and
+// lanes 0-3 form the east faces of the tile's last column (for lane 31).
+// Without tie velocities the upwind side is a uniform offset of the window
+// loads; with them (TIES) every face is a 12-point stencil whose weights
+// carry both sides.  One barrier per velocity, two more on tiles whose halo
+// reaches a wall.  At a wall face the value comes from the walls pass, for
+// a velocity leaving a bounce-back wall as the mirrored velocity's entry
+// plus rho_w c_k + shift_k (eq. BB in deviations).
+template <typename T, int STAGE, bool TIES>
+__global__ void __launch_bounds__(UNT, 3)
 k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
-  using C = float;
-  using V4 = float4;
-  __shared__ C gs[2][NST];
-  __shared__ C fxs[TYT][TXT + 1];       // x-faces fi = i0 .. i0 + 32 of the tile's rows
-  __shared__ C fys[TYT + 1][TXT];       // y-faces fj = j0 .. j0 + 16 of its columns
-  __shared__ __align__(16) float wts[KCMAX * WPV];
+  constexpr bool ASYNC = sizeof(T) == 4;       // FP32: the plane arrives by copies
+  __shared__ __align__(16) float ring[NRING][RPL];
+  __shared__ float rwb[NWALL];                 // wall densities of the tile's wall faces
   const DevParams& p = s.p;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tiles = s.tiles_x * s.tiles_y;
   const int tile = blockIdx.x % tiles, chunk = blockIdx.x / tiles;
   const int i0 = (tile % s.tiles_x) * TXT, j0 = (tile / s.tiles_x) * TYT;
   const int k0 = chunk * s.kc, k1 = min(p.nv, k0 + s.kc);
+  if (k0 >= k1) return;                                     // uniform per block
   const StageCoef& sc = STAGE == 1 ? s.s1 : s.s2;
   const T* __restrict__ src = (const T*)(STAGE == 1 ? s.fhat : s.ftp);
-  const C* __restrict__ eq = (const C*)(STAGE == 1 ? s.eqn : s.eqp);
-  // stage 2 reads f^ of its own cells and overwrites them: no restrict, and
-  // the read is a plain load issued before the store
+  const float* __restrict__ eq = STAGE == 1 ? s.eqn : s.eqp;
+  // stage 2 reads f^ of its own cells and overwrites them: no restrict
   T* dst = (T*)(STAGE == 1 ? s.ftp : s.fhat);
   const T* fh = (const T*)s.fhat;
-  const C b = (C)sc.b;
-  const V4* vq = (const V4*)s.vq;
-  const C* wfx = (const C*)s.wfx;
-  const C* wfy = (const C*)s.wfy;
-  const bool wx = tile_touches_walls_x(p, i0), wy = tile_touches_walls_y(p, j0);
+  const float b = (float)sc.b;
+  const float4* vq = (const float4*)s.vq;
+  const float* __restrict__ fwt = s.fwt + (size_t)(STAGE - 1) * p.nv * WPV;
+  const bool wx = !p.px && (i0 == 0 || i0 + TXT + 2 >= p.nx);
+  const bool wy = !p.py && (j0 == 0 || j0 + TYT + 2 >= p.ny);
+  const bool wall_tile = (!p.px && (i0 == 0 || i0 + TXT >= p.nx)) ||
+                         (!p.py && (j0 == 0 || j0 + TYT >= p.ny));
+  const int N = p.N;
 
   const int i = i0 + lane;
-  bool ok[2];
-  int cell[2];
-  Cubic<C> S[2];
+  const int jr = j0 + RPW * warp;                           // the warp's first row
+  bool ok[RPW];
+  int cell[RPW];
+  Cubic<float> S[RPW];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int j = j0 + 2 * warp + q;
-    ok[q] = i < p.nx && j < p.ny;
-    cell[q] = ok[q] ? j * p.nx + i : 0;
-    if (ok[q]) {
-      S[q] = gnc_flux_cubic<C>(s, i, j, sF);
-      add_quad(S[q], quad((const C*)s.eqn, p.N, cell[q]), sP);
-      if (STAGE == 2) add_quad(S[q], quad((const C*)s.eqp, p.N, cell[q]), sQ);
+  for (int m = 0; m < RPW; ++m) {
+    const int j = jr + m;
+    ok[m] = i < p.nx && j < p.ny;
+    cell[m] = ok[m] ? j * p.nx + i : 0;
+    if (ok[m]) {
+      S[m] = gnc_flux_cubic(s, i, j, sF);
+      add_quad(S[m], quad(s.eqn, N, cell[m]), sP);
+      if (STAGE == 2) add_quad(S[m], quad(s.eqp, N, cell[m]), sQ);
     }
   }
-  // faces this thread computes: the x-face left of and the y-face below
-  // each of its two cells; wall faces come from the wall pass's arrays.  The
-  // tile's last x-face column (i0 + 32) and y-face row (j0 + 16) are taken
-  // by warps 0 and 1 (extra index e < 48).
-  const int ex_id = warp * 32 + lane;
-  const bool extra = ex_id < 48;
-  Kah am[2][3] = {};
+  // this thread's wall face in the ring's wall region (thread t < NWALL):
+  // W row t, E row t - 16, S column t - 32, N column t - 64 of the tile
+  int wside = -1, wslot = -1;
+  if (threadIdx.x < NWALL) {
+    const int t = threadIdx.x;
+    if (t < 2 * TYT) {
+      const int j = j0 + t % TYT;
+      wside = t < TYT ? SIDE_W : SIDE_E;
+      const bool here = !p.px && j < p.ny && (t < TYT ? i0 == 0 : i0 + TXT >= p.nx);
+      if (here) wslot = (t < TYT ? 0 : p.ny) + j;
+    } else {
+      const int c = (t - 2 * TYT) % TXT, ii = i0 + c;
+      const bool south = t < 2 * TYT + TXT;
+      wside = south ? SIDE_S : SIDE_N;
+      const bool here = !p.py && ii < p.nx && (south ? j0 == 0 : j0 + TYT >= p.ny);
+      if (here) wslot = (south ? 2 * p.ny : 2 * p.ny + p.nx) + ii;
+    }
+    rwb[t] = wslot >= 0 ? (float)s.wrho[wslot] : 0.f;
+  }
 
-  load_weights(wts, s, STAGE, k0, k1);
-  Stager<T> st;
-  st.init(s, eq, i0, j0);
+  // staging: cells (sx, sy) of the 36 x 20 plane, own cells first
+  int soff[EPT], sidx[EPT];
+  bool sact[EPT];
+  EqF<float> sq[EPT];
 #pragma unroll
-  for (int u = 0; u < PD; ++u)
-    if (k0 + u < k1) st.load(u, src, k0 + u, p.N);
-  int buf = 0;
-  for (int kb = k0; kb < k1; kb += PD) {
+  for (int m = 0; m < EPT; ++m) {
+    int sx, sy;
+    if (m < RPW) {
+      sx = lane + 2;
+      sy = RPW * warp + m + 2;
+      sact[m] = true;
+    } else {
+      const int h = threadIdx.x + UNT * (m - RPW);
+      sact[m] = h < NHALO;
+      halo_pos(sact[m] ? h : 0, sx, sy);
+    }
+    sidx[m] = sy * HXT + sx;
+    int gi = i0 - 2 + sx, gj = j0 - 2 + sy;
+    if (p.px) gi = ((gi % p.nx) + p.nx) % p.nx;
+    else gi = min(max(gi, 0), p.nx - 1);
+    if (p.py) gj = ((gj % p.ny) + p.ny) % p.ny;
+    else gj = min(max(gj, 0), p.ny - 1);
+    soff[m] = gj * p.nx + gi;
+    sq[m].vx = __ldg(eq + soff[m]);
+    sq[m].vy = __ldg(eq + N + soff[m]);
+    sq[m].bm1 = __ldg(eq + 2 * N + soff[m]);
+    sq[m].r = __ldg(eq + 3 * N + soff[m]);
+    sq[m].dr = __ldg(eq + 4 * N + soff[m]);
+  }
+
+  // copies of velocity kq's inputs into ring buffer q; one commit group per
+  // plane, also when empty, so the group count stays uniform
+  int ksrc = 0;                                   // wall value's source velocity for the next issue
+  if (wslot >= 0 && k0 + NRING - 1 < k1) ksrc = __ldg(s.wsrc + (size_t)wside * p.nv + k0 + NRING - 1);
+  auto issue = [&](int kq, int q, int ks) {
+    if (kq < k1) {
+      float* R = ring[q];
+      if constexpr (ASYNC) {
 #pragma unroll
-    for (int u = 0; u < PD; ++u) {
-      const int k = kb + u;
-      if (k >= k1) break;                            // uniform over the block
-      const V4 e4 = ld4(vq + p.nv + k);
-      st.store(u, gs[buf], b, e4.x, e4.y, e4.z);
-      if (k + PD < k1) st.load(u, src, k + PD, p.N);
-      // the cells' own values (L1 / L2 hits: the plane is being staged)
-      C own[2], fown[2];
+        for (int m = 0; m < EPT; ++m)
+          if (sact[m]) cp4(&R[RG + sidx[m]], src + (size_t)kq * N + soff[m]);
+        if (STAGE == 2) {
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        own[q] = ok[q] ? ldv(src + (size_t)k * p.N + cell[q]) : C(0);
-        fown[q] = (STAGE == 2 && ok[q]) ? lds(fh + (size_t)k * p.N + cell[q]) : C(0);
-      }
-      __syncthreads();
-      stage_ghosts<C>(p, gs[buf], i0, j0, wx, wy);
-      FaceW fw;
-      face_weights(fw, wts + (k - k0) * WPV, e4.x, e4.y);
-      {
-        // window: staged rows 2w .. 2w + 4, columns lane .. lane + 3
-        C Wn[5][4];
-        const C* g0 = gs[buf] + (2 * warp) * HXT + lane;
-#pragma unroll
-        for (int r = 0; r < 5; ++r)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) Wn[r][c] = g0[r * HXT + c];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int r = 2 * warp + q, j = j0 + r;
-          // cell (lane, r) sits at window (2, 2 + q)
-          C vx = xface(fw, Wn, 1, 2 + q);
-          if (!p.px && i == 0 && j < p.ny) vx = wfx[(size_t)k * 2 * p.ny + j];
-          if (!p.px && i == p.nx && j < p.ny) vx = wfx[(size_t)k * 2 * p.ny + p.ny + j];
-          fxs[r][lane] = vx;
-          C vy = yface(fw, Wn, 2, 1 + q);
-          if (!p.py && j == 0 && i < p.nx) vy = wfy[(size_t)k * 2 * p.nx + i];
-          if (!p.py && j == p.ny && i < p.nx) vy = wfy[(size_t)k * 2 * p.nx + p.nx + i];
-          fys[r][lane] = vy;
+          for (int m = 0; m < RPW; ++m)
+            if (ok[m]) cp4(&R[RF + (RPW * warp + m) * TXT + lane], fh + (size_t)kq * N + cell[m]);
         }
       }
-      if (extra) {
-        const C* g = gs[buf];
-        if (ex_id < TYT) {                           // x-face i0 + 32 of row ex_id
-          const int r = ex_id, ii = i0 + TXT, j = j0 + r;
-          C v = xface_at(fw, g, TXT + 2, r + 2);
-          if (!p.px && ii == p.nx && j < p.ny) v = wfx[(size_t)k * 2 * p.ny + p.ny + j];
-          fxs[r][TXT] = v;
-        } else {                                     // y-face j0 + 16 of column ex_id - 16
-          const int c = ex_id - TYT, ii = i0 + c, j = j0 + TYT;
-          C v = yface_at(fw, g, c + 2, TYT + 2);
-          if (!p.py && j == p.ny && ii < p.nx) v = wfy[(size_t)k * 2 * p.nx + p.nx + ii];
-          fys[TYT][c] = v;
-        }
-      }
-      __syncthreads();
-      const V4 k4 = ld4(vq + 2 * p.nv + k);
-      const C kx = STAGE == 1 ? k4.x : k4.z, ky = STAGE == 1 ? k4.y : k4.w;
+      const int t = threadIdx.x;
+      if (t < WPV / 4) cp16(&R[RW + 4 * t], fwt + (size_t)kq * WPV + 4 * t);
+      else if (t == WPV / 4) cp16(&R[RV], vq + p.nv + kq);
+      else if (t == WPV / 4 + 1) cp16(&R[RV + 4], vq + 2 * p.nv + kq);
+      else if (t < WPV / 4 + 4) cp16(&R[RC + 4 * (t - WPV / 4 - 2)], s.wbb + 4 * (size_t)kq + 2 * (t - WPV / 4 - 2));
+      if (wslot >= 0) cp4(&R[RB + t], s.wf + (size_t)ks * s.nw + wslot);
+    }
+    cp_commit();
+  };
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (!ok[q]) continue;
-        const int r = 2 * warp + q;
-        const C fW = fxs[r][lane], fE = fxs[r][lane + 1];
-        const C fS = fys[r][lane], fN = fys[r + 1][lane];
-        const C df = fmx(kx, fE - fW, ky * (fN - fS));
-        const C ws = fmx(e4.z, cubic<C>(S[q], e4.x, e4.y), df);
-        C out;
-        if (STAGE == 1) {
-          out = fmx(-cB, own[q], own[q] + ws);                 // cB = sP
-        } else {
-          out = fmx(cA, fown[q] - own[q], fmx(-cB, own[q], own[q] + ws));   // cB = sP + sQ
-        }
-        const C ov = stored_value<T>(out);    // the moments are those of the stored value
-        stv(dst + (size_t)k * p.N + cell[q], ov);
-        kah_add(am[q][0], ov);
-        kah_add(am[q][1], e4.x * ov);
-        kah_add(am[q][2], e4.y * ov);
+  for (int q = 0; q < NRING - 1; ++q) {
+    const int ks = wslot >= 0 && k0 + q < k1 ? __ldg(s.wsrc + (size_t)wside * p.nv + k0 + q) : 0;
+    issue(k0 + q, q, ks);
+  }
+  T raw[EPT];
+  if constexpr (!ASYNC) {
+#pragma unroll
+    for (int m = 0; m < EPT; ++m)
+      if (sact[m]) raw[m] = ldr(src + (size_t)k0 * N + soff[m]);
+  }
+
+  for (int k = k0; k < k1; ++k) {
+    float* R = ring[(k - k0) % NRING];
+    float* g = R + RG;
+    cp_wait<NRING - 2>();                                   // this thread's copies of velocity k
+    // the velocity row is another thread's copy: read after the barrier,
+    // except xi and W for the conversion, which come from the table
+    const float4 e4 = ld4(vq + p.nv + k);
+    float own[RPW], fown[RPW];
+#pragma unroll
+    for (int m = 0; m < EPT; ++m)
+      if (sact[m]) {
+        const float r = ASYNC ? g[sidx[m]] : tof(raw[m]);
+        if (m < RPW) own[m] = r;
+        g[sidx[m]] = fmaf(b, feq_dev<float>(sq[m], e4.x, e4.y, e4.z) - r, r);
       }
-      buf ^= 1;
+    if constexpr (!ASYNC) {
+#pragma unroll
+      for (int m = 0; m < RPW; ++m) fown[m] = (STAGE == 2 && ok[m]) ? lds(fh + (size_t)k * N + cell[m]) : 0.f;
+      if (k + 1 < k1) {
+#pragma unroll
+        for (int m = 0; m < EPT; ++m)
+          if (sact[m]) raw[m] = ldr(src + (size_t)(k + 1) * N + soff[m]);
+      }
+    }
+    __syncthreads();
+    // the ring buffer of velocity k - 1 is free once every thread is here
+    {
+      const int kq = k + NRING - 1;
+      const int ks = ksrc;
+      if (wslot >= 0 && kq + 1 < k1) ksrc = __ldg(s.wsrc + (size_t)wside * p.nv + kq + 1);
+      issue(kq, (k - k0 + NRING - 1) % NRING, ks);
+    }
+    stage_ghosts(p, g, i0, j0, wx, wy);
+    if constexpr (ASYNC) {
+#pragma unroll
+      for (int m = 0; m < RPW; ++m) fown[m] = STAGE == 2 ? R[RF + (RPW * warp + m) * TXT + lane] : 0.f;
+    }
+
+    const float* wk = R + RW;
+    const int sgx = e4.x > 0.f ? 1 : (e4.x < 0.f ? -1 : 0);
+    const int sgy = e4.y > 0.f ? 1 : (e4.y < 0.f ? -1 : 0);
+    const float* g0 = g + (RPW * warp) * HXT + lane;       // window row 0, column 0 (cell i - 2)
+    float fx[RPW], fy[RPW + 1], ext = 0.f;
+    if constexpr (!TIES) {
+      // x-faces: about cell i - 1 (window columns 0-2) or i (1-3); y-faces:
+      // about the cell below (window rows m .. m + 2) or the cell (m + 1 ..)
+      const int ox = sgx > 0 ? 0 : 1, oy = sgy > 0 ? 0 : 1;
+      const float* Tx = wk + (sgx > 0 ? 0 : 12);
+      const float* Ty = wk + (sgy > 0 ? 24 : 36);
+      float X[RPW + 2][3], Y[RPW + 3][3];
+#pragma unroll
+      for (int q = 0; q < RPW + 2; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) X[q][c] = g0[(q + 1) * HXT + ox + c];
+#pragma unroll
+      for (int q = 0; q < RPW + 3; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Y[q][c] = g0[(q + oy) * HXT + 1 + c];
+#pragma unroll
+      for (int m = 0; m < RPW; ++m) fx[m] = dot9s(Tx, WIN3(X, m, 0));
+#pragma unroll
+      for (int m = 0; m <= RPW; ++m) fy[m] = dot9s(Ty, WIN3(Y, m, 0));
+      if (lane < RPW) {
+        const float* ge = g + (RPW * warp + lane + 1) * HXT + TXT + ox;
+        ext = dot9s(Tx, ge[0], ge[1], ge[2], ge[HXT], ge[HXT + 1], ge[HXT + 2], ge[2 * HXT],
+                    ge[2 * HXT + 1], ge[2 * HXT + 2]);
+      }
+    } else {
+      // 12-point stencils: x 3 rows x 4 columns, y 4 rows x 3 columns
+      const float* Cx = wk + 48;
+      const float* Cy = wk + 60;
+      float Wn[2 * RPW][4];
+#pragma unroll
+      for (int q = 0; q < 2 * RPW; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) Wn[q][c] = g0[q * HXT + c];
+#pragma unroll
+      for (int m = 0; m < RPW; ++m) {
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) v = fmaf(Cx[4 * r + c], Wn[m + 1 + r][c], v);
+        fx[m] = v;
+      }
+#pragma unroll
+      for (int m = 0; m <= RPW; ++m) {
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) v = fmaf(Cy[3 * r + c], Wn[m + r][1 + c], v);
+        fy[m] = v;
+      }
+      if (lane < RPW) {
+        const float* ge = g + (RPW * warp + lane + 1) * HXT + TXT;
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) v = fmaf(Cx[4 * r + c], ge[r * HXT + c], v);
+        ext = v;
+      }
+    }
+    if (wall_tile) {
+      // the walls pass's values; bounce-back mirrors for leaving velocities
+      const float* rc = R + RC;                             // (c_k, shift_k) per side
+      auto wv = [&](int t, int side, bool leaving) {
+        float v = R[RB + t];
+        if (leaving && p.bc_kind[side] == BC_BOUNCEBACK) v = fmaf(rwb[t], rc[2 * side], v + rc[2 * side + 1]);
+        return v;
+      };
+#pragma unroll
+      for (int m = 0; m < RPW; ++m) {
+        const int j = jr + m;
+        if (!p.px && j < p.ny) {
+          if (i == 0) fx[m] = wv(RPW * warp + m, SIDE_W, sgx > 0);
+          else if (i == p.nx) fx[m] = wv(TYT + RPW * warp + m, SIDE_E, sgx < 0);
+        }
+      }
+      if (!p.px && lane < RPW && i0 + TXT == p.nx && jr + lane < p.ny)
+        ext = wv(TYT + RPW * warp + lane, SIDE_E, sgx < 0);
+#pragma unroll
+      for (int m = 0; m <= RPW; ++m) {
+        const int j = jr + m;
+        if (!p.py && i < p.nx) {
+          if (j == 0) fy[m] = wv(2 * TYT + lane, SIDE_S, sgy > 0);
+          else if (j == p.ny) fy[m] = wv(2 * TYT + TXT + lane, SIDE_N, sgy < 0);
+        }
+      }
+    }
+
+    const float4 k4 = *reinterpret_cast<const float4*>(R + RV + 4);
+    const float kx = STAGE == 1 ? k4.x : k4.z, ky = STAGE == 1 ? k4.y : k4.w;
+#pragma unroll
+    for (int m = 0; m < RPW; ++m) {
+      float fE = __shfl_down_sync(0xffffffffu, fx[m], 1);
+      const float fEx = __shfl_sync(0xffffffffu, ext, m);
+      if (lane == 31) fE = fEx;
+      if (!ok[m]) continue;
+      const float df = fmaf(kx, fE - fx[m], ky * (fy[m + 1] - fy[m]));
+      const float ws = fmaf(e4.z, cubic<float>(S[m], e4.x, e4.y), df);
+      float out;
+      if (STAGE == 1) out = fmaf(-cB, own[m], own[m] + ws);                          // cB = sP
+      else out = fmaf(cA, fown[m] - own[m], fmaf(-cB, own[m], own[m] + ws));         // cB = sP + sQ
+      stv(dst + (size_t)k * N + cell[m], out);
     }
   }
-  double* pc = s.pc + (size_t)chunk * 3 * p.N;
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-    if (ok[q])
-#pragma unroll
-      for (int m = 0; m < 3; ++m) pc[(size_t)m * p.N + cell[q]] = kah_value(am[q][m]);
 }
 
 template <typename T>
 cudaError_t allow_gnc() {
-  cudaError_t e = cudaFuncSetAttribute(k_gnc_faces<T>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gnc_update<T, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gnc_update<T, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  cudaError_t e = cudaSuccess;
+  for (void* f : {(void*)k_gnc_update<T, 1, false>, (void*)k_gnc_update<T, 2, false>,
+                  (void*)k_gnc_update<T, 1, true>, (void*)k_gnc_update<T, 2, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   return e;
 }
 
 int items(const GncStep& s) { return s.tiles_x * s.tiles_y * s.nch; }
 
+// polynomial in (x, y) of degree <= 3 as coefficients of the ten monomials
+struct Poly {
+  double c[NMONO] = {};
+};
+
 }  // namespace
 
-void gnc_weight_table(const DevParams& p, const double* xi_x, const double* xi_y,
-                      const StageCoef& s1, const StageCoef& s2, float* out) {
-  for (int st = 0; st < 2; ++st) {
-    const double h = st == 0 ? s1.h : s2.h;
-    for (int k = 0; k < p.nv; ++k) {
-      const double ax = -xi_x[k] * h * p.inv_dx, by = -xi_y[k] * h * p.inv_dy;
-      const double ab[4][2] = {{0.5 + ax, by}, {-0.5 + ax, by}, {ax, 0.5 + by}, {ax, -0.5 + by}};
-      float* row = out + ((size_t)st * p.nv + k) * WPV;
-      for (int set = 0; set < 4; ++set) {
-        double w[9];
-        flux_ds_weights<double>(ab[set][0], ab[set][1], w);
-        for (int q = 0; q < 12; ++q) row[set * 12 + q] = q < 9 ? (float)w[q] : 0.0f;
+bool gnc_tables(GncStep& g, const double* xi_x, const double* xi_y, const double* w,
+                const double* feq_wall, const int* opp, GncTables& t) {
+  const DevParams& p = g.p;
+  const int nv = p.nv;
+  const double rho0 = g.ref.rho0;
+  auto sgn = [](double v) { return v > 0.0 ? 1 : (v < 0.0 ? -1 : 0); };
+  auto mono = [&](int k, int idx) {
+    static const int ex[NMONO][2] = {{0, 0}, {1, 0}, {0, 1}, {2, 0}, {1, 1},
+                                     {0, 2}, {3, 0}, {2, 1}, {1, 2}, {0, 3}};
+    double v = 1.0;
+    for (int q = 0; q < ex[idx][0]; ++q) v *= xi_x[k];
+    for (int q = 0; q < ex[idx][1]; ++q) v *= xi_y[k];
+    return v;
+  };
+  // sign classes, in the order (sx, sy) = (-1,-1), (-1,0), ... (1,1)
+  g.ncls = 0;
+  t.cls_off.assign(1, 0);
+  t.cls_k.clear();
+  t.cls_mono.clear();
+  int cls_sx[9], cls_sy[9];
+  for (int sx = -1; sx <= 1; ++sx)
+    for (int sy = -1; sy <= 1; ++sy) {
+      int n = 0;
+      for (int k = 0; k < nv; ++k)
+        if (sgn(xi_x[k]) == sx && sgn(xi_y[k]) == sy) {
+          t.cls_k.push_back(k);
+          for (int q = 0; q < 12; ++q) t.cls_mono.push_back(q < NMONO ? (float)mono(k, q) : 0.f);
+          ++n;
+        }
+      if (n) {
+        cls_sx[g.ncls] = sx;
+        cls_sy[g.ncls] = sy;
+        ++g.ncls;
+        t.cls_off.push_back((int)t.cls_k.size());
+      }
+    }
+  // class combinations: interior faces (ties with weight 1/2, Q4), and per
+  // wall the fluid side (ties with weight 1) and the strictly incoming
+  // velocities (for the bounce-back mirror)
+  g.ncombo = 0;
+  auto combo = [&](double a0, double b0, auto lam_of) {
+    GncCombo C{};
+    C.a0 = (float)a0;
+    C.b0 = (float)b0;
+    for (int c = 0; c < 9; ++c) C.lam[c] = c < g.ncls ? (float)lam_of(cls_sx[c], cls_sy[c]) : 0.f;
+    for (int q = 0; q < g.ncombo; ++q) {
+      const GncCombo& D = g.cmb[q];
+      bool same = D.a0 == C.a0 && D.b0 == C.b0;
+      for (int c = 0; c < 9 && same; ++c) same = D.lam[c] == C.lam[c];
+      if (same) return q;
+    }
+    g.cmb[g.ncombo] = C;
+    return g.ncombo++;
+  };
+  auto half = [](int s, int want) { return s == want ? 1.0 : (s == 0 ? 0.5 : 0.0); };
+  g.c_lo[0] = combo(0.5, 0.0, [&](int sx, int) { return half(sx, 1); });
+  g.c_up[0] = combo(-0.5, 0.0, [&](int sx, int) { return half(sx, -1); });
+  g.c_lo[1] = combo(0.0, 0.5, [&](int, int sy) { return half(sy, 1); });
+  g.c_up[1] = combo(0.0, -0.5, [&](int, int sy) { return half(sy, -1); });
+  for (int sd = 0; sd < 4; ++sd) g.c_wf[sd] = g.c_win[sd] = 0;
+  if (!p.px) {
+    g.c_wf[SIDE_W] = combo(-0.5, 0.0, [](int sx, int) { return sx <= 0 ? 1.0 : 0.0; });
+    g.c_win[SIDE_W] = combo(-0.5, 0.0, [](int sx, int) { return sx < 0 ? 1.0 : 0.0; });
+    g.c_wf[SIDE_E] = combo(0.5, 0.0, [](int sx, int) { return sx >= 0 ? 1.0 : 0.0; });
+    g.c_win[SIDE_E] = combo(0.5, 0.0, [](int sx, int) { return sx > 0 ? 1.0 : 0.0; });
+  }
+  if (!p.py) {
+    g.c_wf[SIDE_S] = combo(0.0, -0.5, [](int, int sy) { return sy <= 0 ? 1.0 : 0.0; });
+    g.c_win[SIDE_S] = combo(0.0, -0.5, [](int, int sy) { return sy < 0 ? 1.0 : 0.0; });
+    g.c_wf[SIDE_N] = combo(0.0, 0.5, [](int, int sy) { return sy >= 0 ? 1.0 : 0.0; });
+    g.c_win[SIDE_N] = combo(0.0, 0.5, [](int, int sy) { return sy > 0 ? 1.0 : 0.0; });
+  }
+  // equilibrium quadrature per combination: zc[p][q] = sum lam W_k pi_p pi_q
+  t.zc.assign((size_t)g.ncombo * NMONO * 6, 0.f);
+  for (int cb = 0; cb < g.ncombo; ++cb)
+    for (int pp = 0; pp < NMONO; ++pp)
+      for (int q = 0; q < 6; ++q) {
+        double z = 0.0;
+        for (int c = 0; c < g.ncls; ++c) {
+          const double lam = g.cmb[cb].lam[c];
+          if (lam == 0.0) continue;
+          for (int e = t.cls_off[c]; e < t.cls_off[c + 1]; ++e) {
+            const int k = t.cls_k[e];
+            z += lam * w[k] * mono(k, pp) * mono(k, q);
+          }
+        }
+        t.zc[((size_t)cb * NMONO + pp) * 6 + q] = (float)z;
+      }
+  // T(a, b) = sum_u t_u u(a, b), u = 1, a, b, a^2, ab, b^2 (T is quadratic
+  // in (a, b)): the coefficients from six evaluations, checked at a seventh
+  double T00[9], Tp0[9], Tm0[9], T0p[9], T0m[9], Tpp[9], Tx[9];
+  flux_ds_weights<double>(0.0, 0.0, T00);
+  flux_ds_weights<double>(1.0, 0.0, Tp0);
+  flux_ds_weights<double>(-1.0, 0.0, Tm0);
+  flux_ds_weights<double>(0.0, 1.0, T0p);
+  flux_ds_weights<double>(0.0, -1.0, T0m);
+  flux_ds_weights<double>(1.0, 1.0, Tpp);
+  flux_ds_weights<double>(0.3, -0.7, Tx);
+  for (int q = 0; q < 9; ++q) {
+    const double t1 = T00[q], ta = 0.5 * (Tp0[q] - Tm0[q]), taa = 0.5 * (Tp0[q] + Tm0[q]) - T00[q];
+    const double tb = 0.5 * (T0p[q] - T0m[q]), tbb = 0.5 * (T0p[q] + T0m[q]) - T00[q];
+    const double tab = Tpp[q] - t1 - ta - tb - taa - tbb;
+    const double a = 0.3, bb = -0.7;
+    const double chk = t1 + ta * a + tb * bb + taa * a * a + tab * a * bb + tbb * bb * bb;
+    if (std::fabs(chk - Tx[q]) > 1e-12) return false;
+    g.tu[0][q] = (float)t1;
+    g.tu[1][q] = (float)ta;
+    g.tu[2][q] = (float)tb;
+    g.tu[3][q] = (float)taa;
+    g.tu[4][q] = (float)tab;
+    g.tu[5][q] = (float)tbb;
+  }
+  // wall tables: sums over the leaving velocities (xi.n < 0, n the fluid's
+  // outward normal) of pi_m times the bounce-back coefficient, the
+  // deviation shift, the wall equilibrium and the reference state
+  for (int sd = 0; sd < 4; ++sd) {
+    for (int m = 0; m < 3; ++m) g.wB[sd][m] = g.wH[sd][m] = g.wMo[sd][m] = g.wWo[sd][m] = 0.0;
+    if (p.bc_kind[sd] == BC_PERIODIC) continue;
+    const double nxs = sd == SIDE_W ? -1.0 : sd == SIDE_E ? 1.0 : 0.0;
+    const double nys = sd == SIDE_S ? -1.0 : sd == SIDE_N ? 1.0 : 0.0;
+    for (int k = 0; k < nv; ++k) {
+      const double xn = xi_x[k] * nxs + xi_y[k] * nys;
+      if (!(xn < 0.0)) continue;
+      const double pm[3] = {1.0, xi_x[k], xi_y[k]};
+      const double ck = 2.0 * w[k] * (xi_x[k] * p.uw_x[sd] + xi_y[k] * p.uw_y[sd]) * p.inv_RT;
+      const double sh = opp[k] >= 0 ? (w[opp[k]] - w[k]) * rho0 : 0.0;
+      for (int m = 0; m < 3; ++m) {
+        g.wB[sd][m] += pm[m] * ck;
+        g.wH[sd][m] += pm[m] * sh;
+        g.wMo[sd][m] += pm[m] * feq_wall[(size_t)sd * nv + k];
+        g.wWo[sd][m] += pm[m] * w[k] * rho0;
       }
     }
   }
+  // per velocity and side: bounce-back's c_k = 2 W_k xi_k.u_w / RT and
+  // shift_k = (W_opp(k) - W_k) rho0 ([nv][4] pairs, FP32), and the velocity
+  // whose wall-face entry the update reads (the mirror for a velocity
+  // leaving a bounce-back wall)
+  t.wbb.assign((size_t)nv * 8, 0.f);
+  t.wsrc.assign(4 * (size_t)nv, 0);
+  for (int sd = 0; sd < 4; ++sd) {
+    const double nxs = sd == SIDE_W ? -1.0 : sd == SIDE_E ? 1.0 : 0.0;
+    const double nys = sd == SIDE_S ? -1.0 : sd == SIDE_N ? 1.0 : 0.0;
+    for (int k = 0; k < nv; ++k) {
+      const bool leaving = xi_x[k] * nxs + xi_y[k] * nys < 0.0;
+      const bool bb = p.bc_kind[sd] == BC_BOUNCEBACK;
+      t.wsrc[(size_t)sd * nv + k] = (bb && leaving && opp[k] >= 0) ? opp[k] : k;
+      if (!bb) continue;
+      const double ck = 2.0 * w[k] * (xi_x[k] * p.uw_x[sd] + xi_y[k] * p.uw_y[sd]) * p.inv_RT;
+      const double sh = opp[k] >= 0 ? (w[opp[k]] - w[k]) * rho0 : 0.0;
+      t.wbb[8 * (size_t)k + 2 * sd] = (float)ck;
+      t.wbb[8 * (size_t)k + 2 * sd + 1] = (float)sh;
+    }
+  }
+  g.nw = 2 * (p.nx + p.ny);
+  // face weights of eq. flux_DS per stage and velocity: four sets of 12 (x
+  // about the lower / upper cell, y likewise; nine used), then the
+  // 12-point x- and y-stencils with the upwind choice built in (a tie
+  // velocity, Q4: half of each side)
+  g.ties = 0;
+  for (int k = 0; k < nv; ++k)
+    if (xi_x[k] == 0.0 || xi_y[k] == 0.0) g.ties = 1;
+  t.fwt.assign(2 * (size_t)nv * WPV, 0.f);
+  for (int st = 0; st < 2; ++st) {
+    const double h = st == 0 ? g.s1.h : g.s2.h;
+    for (int k = 0; k < nv; ++k) {
+      const double ax = -xi_x[k] * h * p.inv_dx, by = -xi_y[k] * h * p.inv_dy;
+      const double ab[4][2] = {{0.5 + ax, by}, {-0.5 + ax, by}, {ax, 0.5 + by}, {ax, -0.5 + by}};
+      double wv[4][9];
+      float* row = t.fwt.data() + ((size_t)st * nv + k) * WPV;
+      for (int set = 0; set < 4; ++set) {
+        flux_ds_weights<double>(ab[set][0], ab[set][1], wv[set]);
+        for (int q = 0; q < 9; ++q) row[set * 12 + q] = (float)wv[set][q];
+      }
+      const double lx = xi_x[k] > 0.0 ? 1.0 : xi_x[k] < 0.0 ? 0.0 : 0.5;   // weight of the lower side
+      const double ly = xi_y[k] > 0.0 ? 1.0 : xi_y[k] < 0.0 ? 0.0 : 0.5;
+      double cx[3][4] = {}, cy[4][3] = {};
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+          cx[r][c] += lx * wv[0][3 * r + c];
+          cx[r][c + 1] += (1.0 - lx) * wv[1][3 * r + c];
+          cy[r][c] += ly * wv[2][3 * r + c];
+          cy[r + 1][c] += (1.0 - ly) * wv[3][3 * r + c];
+        }
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 4; ++c) row[48 + 4 * r + c] = (float)cx[r][c];
+      for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 3; ++c) row[60 + 3 * r + c] = (float)cy[r][c];
+    }
+  }
+  g.tiles_x = (p.nx + TXT - 1) / TXT;
+  g.tiles_y = (p.ny + TYT - 1) / TYT;
+  return true;
 }
 
-int gnc_chunks(const DevParams& p, int sms) {
-  const int tiles = ((p.nx + TXT - 1) / TXT) * ((p.ny + TYT - 1) / TYT);
-  const int want = (4 * 2 * sms + tiles - 1) / tiles;        // about four waves of two blocks per SM
-  const int cap = (p.nv + KCMAX - 1) / KCMAX;                 // at most KCMAX velocities per chunk
-  return std::max(1, std::min(p.nv, std::max(want, cap)));
+// velocity chunks per tile: about one wave of update blocks
+int gnc_chunks(const GncStep& g, int sms) {
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_gnc_update<float, 2, false>, UNT, 0) != cudaSuccess ||
+      bps < 1) {
+    cudaGetLastError();
+    bps = 3;
+  }
+  const int tiles = g.tiles_x * g.tiles_y;
+  const int want = std::max(1, (bps * sms) / tiles);
+  return std::max(1, std::min(g.p.nv, want));
 }
 
 cudaError_t gnc_prepare(int store) {
@@ -901,67 +1241,62 @@ cudaError_t gnc_prepare(int store) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_gnc_moments(const GncStep& s, cudaStream_t st) {
-  const dim3 grid((s.p.N + 255) / 256, s.nch);
-  if (s.store == 1) k_gnc_moments<float><<<grid, 256, 0, st>>>(s);
-  else k_gnc_moments<__nv_bfloat16><<<grid, 256, 0, st>>>(s);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_gnc_cellfin<float><<<(s.p.N + 255) / 256, 256, 0, st>>>(s, 0);
+// class sums of the stage's source, then the cell finaliser
+cudaError_t launch_gnc_sums(const GncStep& s, int stage, cudaStream_t st) {
+  const dim3 grid((s.p.N + CPB - 1) / CPB, s.ncls);
+  if (s.store == 1) k_gnc_sums<float><<<grid, 256, 0, st>>>(s, stage);
+  else k_gnc_sums<__nv_bfloat16><<<grid, 256, 0, st>>>(s, stage);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gnc_faces(const GncStep& s, int stage, cudaStream_t st) {
-  if (s.store == 1) k_gnc_faces<float><<<items(s), NTH, 0, st>>>(s, stage);
-  else k_gnc_faces<__nv_bfloat16><<<items(s), NTH, 0, st>>>(s, stage);
+cudaError_t launch_gnc_cellfin(const GncStep& s, int stage, cudaStream_t st) {
+  k_gnc_cellfin<<<(s.p.N + 255) / 256, 256, 0, st>>>(s, stage);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gnc_facefin(const GncStep& s, int stage, cudaStream_t st) {
+  const int nf = s.p.ny * (s.p.nx + 1) + (s.p.ny + 1) * s.p.nx;
+  k_gnc_facefin<<<(nf + 255) / 256, 256, 0, st>>>(s, stage);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gnc_walls(const GncStep& s, int stage, cudaStream_t st) {
-  const int nwx = s.p.px ? 0 : 2 * s.p.ny, nwy = s.p.py ? 0 : 2 * s.p.nx;
-  if (nwx + nwy == 0) return cudaSuccess;
-  if (s.store == 1) k_gnc_walls<float><<<nwx + nwy, 256, 0, st>>>(s, stage, nwx);
-  else k_gnc_walls<__nv_bfloat16><<<nwx + nwy, 256, 0, st>>>(s, stage, nwx);
+  const int nseg = (s.p.px ? 0 : 2 * ((s.p.ny + WSEG - 1) / WSEG)) +
+                   (s.p.py ? 0 : 2 * ((s.p.nx + WSEG - 1) / WSEG));
+  if (nseg == 0) return cudaSuccess;
+  const dim3 grid(nseg, (s.p.nv + WCH - 1) / WCH);
+  if (s.store == 1) k_gnc_walls<float><<<grid, 128, 0, st>>>(s, stage);
+  else k_gnc_walls<__nv_bfloat16><<<grid, 128, 0, st>>>(s, stage);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gnc_facefin(const GncStep& s, cudaStream_t st) {
-  const int nf = s.p.ny * (s.p.nx + 1) + (s.p.ny + 1) * s.p.nx;
-  k_gnc_facefin<float><<<(nf + 255) / 256, 256, 0, st>>>(s);
-  return cudaGetLastError();
-}
-
-// the update of a stage followed by the cell moments of its output
 cudaError_t launch_gnc_update(const GncStep& s, int stage, cudaStream_t st) {
   const double a1 = s.s1.a, b1 = s.s1.b, dt = s.p.dt;
   const double c34 = 0.75 * s.c_om;
   // cB: the coefficient subtracted from the base (sP, or sP + sQ), formed
-  // from the values the kernel puts into S, in the compute type
-  double cA = 0.0, cB, sP, sQ = 0.0, sF;
-  auto rc = [](double x) { return (double)(float)x; };
+  // from the values the kernel puts into S, in FP32
+  float cA = 0.f, cB, sP, sQ = 0.f, sF;
   if (stage == 1) {
-    sP = rc(1.25 * b1);
-    sF = -(dt / 3.0) * s.s1.beta;
+    sP = (float)(1.25 * b1);
+    sF = (float)(-(dt / 3.0) * s.s1.beta);
     cB = sP;
   } else {
-    cA = 4.0 / 7.0 - 6.0 / 7.0 * a1;
-    sP = rc(-6.0 / 7.0 * b1);
-    sQ = rc(-c34);
-    sF = -(4.0 * dt / 7.0) * s.s2.beta;
-    cB = (double)((float)sP + (float)sQ);
+    cA = (float)(4.0 / 7.0 - 6.0 / 7.0 * a1);
+    sP = (float)(-6.0 / 7.0 * b1);
+    sQ = (float)(-c34);
+    sF = (float)(-(4.0 * dt / 7.0) * s.s2.beta);
+    cB = sP + sQ;
   }
   const int n = items(s);
+#define GNC_UPD(T, ST, TI) k_gnc_update<T, ST, TI><<<n, UNT, 0, st>>>(s, cA, cB, sP, sQ, sF)
   if (s.store == 1) {
-    if (stage == 1) k_gnc_update<float, 1><<<n, NTH, 0, st>>>(s, (float)cA, (float)cB, (float)sP, (float)sQ, (float)sF);
-    else k_gnc_update<float, 2><<<n, NTH, 0, st>>>(s, (float)cA, (float)cB, (float)sP, (float)sQ, (float)sF);
+    if (s.ties) { if (stage == 1) GNC_UPD(float, 1, true); else GNC_UPD(float, 2, true); }
+    else { if (stage == 1) GNC_UPD(float, 1, false); else GNC_UPD(float, 2, false); }
   } else {
-    if (stage == 1) k_gnc_update<__nv_bfloat16, 1><<<n, NTH, 0, st>>>(s, (float)cA, (float)cB, (float)sP, (float)sQ, (float)sF);
-    else k_gnc_update<__nv_bfloat16, 2><<<n, NTH, 0, st>>>(s, (float)cA, (float)cB, (float)sP, (float)sQ, (float)sF);
+    if (s.ties) { if (stage == 1) GNC_UPD(__nv_bfloat16, 1, true); else GNC_UPD(__nv_bfloat16, 2, true); }
+    else { if (stage == 1) GNC_UPD(__nv_bfloat16, 1, false); else GNC_UPD(__nv_bfloat16, 2, false); }
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int which = stage == 1 ? 1 : 0;
-  k_gnc_cellfin<float><<<(s.p.N + 255) / 256, 256, 0, st>>>(s, which);
+#undef GNC_UPD
   return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 namespace dugks {
 
@@ -58,12 +59,12 @@ enum KernelId {
   K_T2_UPDATE,         // f~^{n+1} = f~^{+,n} + dt L
   K_D2Q9DW_STAGE1,     // fused D2Q9 path in double-word arithmetic, stage 1
   K_D2Q9DW_STAGE2,     // stage 2
-  K_GNC_MOMENTS,       // staged-tile generic path: cell moments of a new state
-  K_GNC_FACES,         // face moments of a stage (both directions)
-  K_GNC_WALLS,         // wall faces of a stage
-  K_GNC_FACEFIN,       // face equilibrium parameters
-  K_GNC_UPDATE1,       // f~(t') and its cell moments
-  K_GNC_UPDATE2,       // f^^{n+1} and its cell moments
+  K_GNC_SUMS,          // class-moment generic path: class sums of a stage's source
+  K_GNC_CELLFIN,       // cell moments, equilibrium parameters, stencil moments
+  K_GNC_WALLS,         // wall faces' f-bar of a stage
+  K_GNC_FACEFIN,       // face equilibrium parameters, wall densities
+  K_GNC_UPDATE1,       // f~(t')
+  K_GNC_UPDATE2,       // f^^{n+1}
   K_NUM
 };
 
@@ -199,44 +200,68 @@ cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_
 cudaError_t launch_gdev_walls(const GDevStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gdev_update(const GDevStep& s, int stage, cudaStream_t st);
 
-// Staged-tile stage kernels for any velocity set (dugks_gnc.cu), in the three
-// storage forms of GDevStep.  Per stage: a face pass reduces the interface
-// moments of a velocity chunk (the stage field g and the face values are
-// formed in shared memory from the stored state and never stored), a wall
-// pass forms the wall faces, two small passes finalise face and cell
-// moments, and an update pass recomputes the four face values of every cell
-// from the same staged tile and writes the stage's output with its cell
-// moments.  Arrays per (cell, velocity) are [nv][ny][nx] of the storage
-// type; parameters [5][n] of the compute type; partial moments FP64.
+// Class-moment stage kernels for any velocity set (dugks_gnc.cu), FP32 and
+// BF16 deviation storage.  Per stage: a streaming pass sums the moments of
+// degree <= 3 of the stage's source per cell and sign class of xi; a cell
+// pass forms rho, u, the equilibrium's parameters and the stencil moments
+// of g; a face pass forms the face equilibria (and the wall densities) from
+// them; a wall pass the wall faces' f-bar per velocity; and an update pass
+// stages g tile by tile, forms the face values on chip and writes the
+// stage's output.  Arrays per (cell, velocity) are [nv][ny][nx] of the
+// storage type.
+struct GncCombo {               // a sum over sign classes, weights lam, with the face's
+  float lam[9];                 // offset (a0, b0) from the upwind cell's centre (cell units)
+  float a0, b0;
+};
 struct GncStep {
   DevParams p;
   GDevRef ref;
-  int store;                    // 0 FP64, 1 FP32, 2 BF16
+  int store;                    // 1 FP32, 2 BF16
   StageCoef s1, s2;
   double c_om;
   void *fhat, *ftp;             // state f^ and f~(t')
-  void *eqn, *eqp;              // cell equilibrium parameters of f^ (t_n) and of f~' (t')
+  float *eqn, *eqp;             // cell equilibrium parameters [5][N] at t_n and t'
   double *mom_n, *mom_p;        // rho, ux, uy [3][N] at t_n and t'
-  void *fpx, *fpy;              // face parameters [5][nf] (interior faces and walls)
-  void *wfx, *wfy;              // wall faces' f-bar [nv][2][ny] (W, E) and [nv][2][nx] (S, N)
-  double *pfx, *pfy, *pc;       // partial moments [nch][3][nfx], [nch][3][nfy], [nch][3][N]
-  const void* vq;               // velocity table of GDevStep::vq
+  float *fpx, *fpy;             // face equilibrium parameters [5][nfx], [5][nfy]
+  float* wf;                    // wall faces' f-bar [nv][nw]
+  double* wrho;                 // wall density per wall face [nw]
+  double* sums;                 // class sums [ncls][10][N]
+  float* nu;                    // stencil moments [ncombo][18][N]
+  const void* vq;               // velocity table of GDevStep::vq (FP32)
+  const float* fwt;             // face-value weights [2 stages][nv][48]
+  const int* cls_off;           // [ncls + 1] first table entry of each class
+  const int* cls_k;             // velocity of each entry
+  const float* cls_mono;        // [entries][12]: the ten monomials of the velocity
+  const float* zc;              // [ncombo][10][6] equilibrium quadrature per combination
+  const float2* wbb;            // [nv][4] bounce-back (c_k, shift_k) per side
+  const int* wsrc;              // [4][nv] velocity whose wall-face entry the update reads
+  int ncls, ncombo;
+  int ties;                     // some velocity has xi_x = 0 or xi_y = 0
+  GncCombo cmb[12];
+  int c_lo[2], c_up[2];         // interior faces of x and y: xi.n > 0 / < 0 combinations
+  int c_wf[4], c_win[4];        // per wall: fluid side (ties too), strictly incoming
+  float tu[6][9];               // T(a, b) = sum_u tu[u] u(a, b), u = 1, a, b, a^2, ab, b^2
+  double wB[4][3], wH[4][3];    // per wall, sums over the leaving velocities of (1, xi) x
+  double wMo[4][3], wWo[4][3];  // bounce-back coefficient, shift, wall equilibrium, W rho0
+  double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
+  int nw;                       // wall face slots: W rows, E rows, S columns, N columns
   int nch, kc;                  // velocity chunks and velocities per chunk
   int tiles_x, tiles_y;         // 32 x 16 cell tiles
-  double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side
-  const float* fwt;             // face-value weights [2 stages][nv][48] (gnc_weight_table)
 };
-// Face-value weights of eq. flux_DS (as printed) per stage and velocity for
-// the staged-tile kernels: x-faces about the lower and upper cell, y-faces
-// about the lower and upper cell, nine weights each padded to twelve.
-void gnc_weight_table(const DevParams& p, const double* xi_x, const double* xi_y,
-                      const StageCoef& s1, const StageCoef& s2, float* out);
-int gnc_chunks(const DevParams& p, int sms);
+struct GncTables {              // host tables of GncStep's device arrays
+  std::vector<int> cls_off, cls_k, wsrc;
+  std::vector<float> cls_mono, zc, fwt, wbb;
+};
+// Fill g's by-value tables and t from the velocity set (host arrays) and the
+// wall data; false if the stencil weights are not quadratic in (a, b).
+bool gnc_tables(GncStep& g, const double* xi_x, const double* xi_y, const double* w,
+                const double* feq_wall, const int* opp, GncTables& t);
+int gnc_chunks(const GncStep& g, int sms);
 cudaError_t gnc_prepare(int store);
-cudaError_t launch_gnc_moments(const GncStep& s, cudaStream_t st);   // cell moments of f^ -> t_n
-cudaError_t launch_gnc_faces(const GncStep& s, int stage, cudaStream_t st);
+cudaError_t launch_gnc_sums(const GncStep& s, int stage, cudaStream_t st);
+cudaError_t launch_gnc_cellfin(const GncStep& s, int stage, cudaStream_t st);
+cudaError_t launch_gnc_facefin(const GncStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gnc_walls(const GncStep& s, int stage, cudaStream_t st);
-cudaError_t launch_gnc_facefin(const GncStep& s, cudaStream_t st);
 cudaError_t launch_gnc_update(const GncStep& s, int stage, cudaStream_t st);
 
 // One instance of a batched D2Q9 FP64 launch (device memory).
