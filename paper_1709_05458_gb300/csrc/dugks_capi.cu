@@ -100,7 +100,7 @@ struct dugks_ctx {
   double* gn_mom2 = nullptr;    // rho, u at t' [3][N]
   void* gn_wf = nullptr;        // wall faces' f-bar [nv][nw]
   double* gn_wrho = nullptr;    // wall densities [nw]
-  double* gn_sums = nullptr;    // class sums [ncls][10][N]
+  double* gn_sums = nullptr;    // class sums [nsplit][ncls][10][N]
   float* gn_nu = nullptr;       // stencil moments [ncombo][18][N]
   void* gn_tab = nullptr;       // class tables, quadrature and face weights
   void* vf = nullptr;           // velocity table of that path (4-vector rows [3][nv])
@@ -946,6 +946,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
           !gnc_tables(n, vel->xi_x, vel->xi_y, vel->w, host.data() + 3 * (size_t)nv, opp.data(), tb))
         e = cudaErrorInvalidValue;
       n.nch = gnc_chunks(n, sms);
+      n.nsplit = gnc_splits(n, tb, sms);
       n.kc = (nv + n.nch - 1) / n.nch;
       n.nch = (nv + n.kc - 1) / n.kc;
       // one device block for the tables: ints, then floats (16-byte aligned)
@@ -959,7 +960,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
       if (e == cudaSuccess) e = cudaMalloc(&c->gn_wf, (size_t)nv * n.nw * csz);
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->gn_wrho, (size_t)n.nw * sizeof(double));
       if (e == cudaSuccess)
-        e = cudaMalloc((void**)&c->gn_sums, (size_t)n.ncls * 10 * p.N * sizeof(double));
+        e = cudaMalloc((void**)&c->gn_sums, (size_t)n.nsplit * n.ncls * 10 * p.N * sizeof(double));
       if (e == cudaSuccess)
         e = cudaMalloc((void**)&c->gn_nu, (size_t)n.ncombo * 18 * p.N * sizeof(float));
       if (e == cudaSuccess) e = cudaMalloc(&c->gn_tab, tab_bytes);

@@ -70,89 +70,85 @@ constexpr int EPT = RPW + HPT;          // staged cells per thread: 4 own + 2 ha
 constexpr int WPV = 72;                 // face weights per velocity in the table
 constexpr int NMONO = 10;               // monomials of degree <= 3
 constexpr int NNU = 18;                 // stencil moments nu_{m,u}: 3 m x 6 u
-constexpr int SBLK = 16;                // velocities per plain FP32 block in the sums
 
 // index of the monomial x^i y^j among 1, x, y, xx, xy, yy, xxx, xxy, xyy, yyy
 __host__ __device__ constexpr int mono_ix(int i, int j) { return (i + j) * (i + j + 1) / 2 + j; }
 
 // ------------------------------------------------------------------ sums
 // Per cell and sign class: the moments sum_k pi_p(xi_k) src_k of the
-// class's velocities for the ten monomials pi_p.  p = 0, 1, 2 (the cell's
-// rho and j, which the collision must conserve) are Kahan-compensated per
-// term; the others add SBLK terms in plain FP32 and fold each block into a
-// compensated sum.  The table row of a velocity holds pi_0 .. pi_9.
-//
+// class's velocities for the ten monomials pi_p (pi_0 .. pi_9 in the table
+// row of a velocity).  A block takes SCB consecutive cells (one per thread)
+// and one split of one class's velocities, whose indices and monomials it
+// first copies to shared memory; each thread then reads its cell's values
+// SBLK velocities at a time (the next block's loads issued before the
+// current block is summed), adds each block in plain FP32 and folds it into
+// a Kahan-compensated sum (the cell's rho and j among them, which the
+// collision must conserve: the blocked sum keeps their error at the level
+// of the FP32 storage itself).
+constexpr int SCB = 256;                 // cells per block
+constexpr int SBLK = 16;                 // velocities per plain FP32 block
+constexpr int SMAXE = 512;               // velocities per split at most
 
-// Block: SPL velocity subsets x 32 threads, one cell per thread (CPB cells
-// per block); a subset takes every SPL-th velocity of the class; the
-// subsets' compensated sums are added in FP64 in a fixed order.  The loads
-// of SU velocities are issued before their sums.
-constexpr int SPL = 8;
-constexpr int CPB = 256 / SPL;           // 32 cells per block
-constexpr int SU = 8;                    // velocities in flight per thread
+// velocity split z of class cls: table entries [ea, eb)
+__device__ __forceinline__ void split_range(const GncStep& s, int cls, int z, int& ea, int& eb) {
+  const int c0 = __ldg(s.cls_off + cls), c1 = __ldg(s.cls_off + cls + 1);
+  ea = c0 + (int)((long long)(c1 - c0) * z / s.nsplit);
+  eb = c0 + (int)((long long)(c1 - c0) * (z + 1) / s.nsplit);
+}
 
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(SCB)
 k_gnc_sums(GncStep s, int stage) {
-  __shared__ double red[SPL][NMONO][CPB];
+  __shared__ float4 mono[SMAXE][3];
+  __shared__ int kof[SMAXE];
   const DevParams& p = s.p;
   const int cls = blockIdx.y;
-  const int sub = threadIdx.x / CPB, tl = threadIdx.x % CPB;
-  const int cb0 = blockIdx.x * CPB;
-  const int c = cb0 + tl;
-  const bool have = c < p.N;
-  const T* __restrict__ src = (const T*)(stage == 1 ? s.fhat : s.ftp) + (have ? c : 0);
-  const int e0 = __ldg(s.cls_off + cls), e1 = __ldg(s.cls_off + cls + 1);
-  Kah lo[3] = {}, hi[7] = {};
-  int e = e0 + sub;
-  while (e < e1) {
-    float part[7] = {};
-    // a block of up to SBLK of this subset's velocities, SU loads at a time
-    const int eend = min(e1, e + SPL * SBLK);
-    for (; e < eend; e += SPL * SU) {
-      float v[SU];
-      int ee[SU];
+  int ea, eb;
+  split_range(s, cls, blockIdx.z, ea, eb);
+  const int cnt = min(eb - ea, SMAXE);
+  const float4* mt = reinterpret_cast<const float4*>(s.cls_mono);
+  for (int t = threadIdx.x; t < 3 * cnt; t += SCB) mono[t / 3][t % 3] = __ldg(mt + 3 * (size_t)ea + t);
+  for (int t = threadIdx.x; t < cnt; t += SCB) kof[t] = __ldg(s.cls_k + ea + t);
+  __syncthreads();
+  const int c = blockIdx.x * SCB + threadIdx.x;
+  if (c >= p.N) return;
+  const T* __restrict__ col = (const T*)(stage == 1 ? s.fhat : s.ftp) + c;
+  Kah acc[NMONO] = {};
+  float v[SBLK];
 #pragma unroll
-      for (int u = 0; u < SU; ++u) {
-        ee[u] = e + SPL * u;
-        v[u] = 0.f;
-        if (ee[u] < eend && have) v[u] = ldv(src + (size_t)__ldg(s.cls_k + ee[u]) * p.N);
-      }
+  for (int u = 0; u < SBLK; ++u) v[u] = u < cnt ? ldv(col + (size_t)kof[u] * p.N) : 0.f;
+  for (int n = 0; n < cnt; n += SBLK) {
+    float w[SBLK];
 #pragma unroll
-      for (int u = 0; u < SU; ++u) {
-        if (ee[u] >= eend) break;
-        const float4* mp = reinterpret_cast<const float4*>(s.cls_mono) + 3 * (size_t)ee[u];
-        const float4 m0 = __ldg(mp), m1 = __ldg(mp + 1), m2 = __ldg(mp + 2);
-        const float x = v[u];
-        kah_add(lo[0], x);
-        kah_add(lo[1], m0.y * x);
-        kah_add(lo[2], m0.z * x);
-        part[0] = fmaf(m0.w, x, part[0]);
-        part[1] = fmaf(m1.x, x, part[1]);
-        part[2] = fmaf(m1.y, x, part[2]);
-        part[3] = fmaf(m1.z, x, part[3]);
-        part[4] = fmaf(m1.w, x, part[4]);
-        part[5] = fmaf(m2.x, x, part[5]);
-        part[6] = fmaf(m2.y, x, part[6]);
-      }
+    for (int u = 0; u < SBLK; ++u) {
+      const int e = n + SBLK + u;
+      w[u] = e < cnt ? ldv(col + (size_t)kof[e] * p.N) : 0.f;
+    }
+    float part[NMONO] = {};
+#pragma unroll
+    for (int u = 0; u < SBLK; ++u) {
+      if (n + u >= cnt) break;
+      const float x = v[u];
+      const float4 m0 = mono[n + u][0], m1 = mono[n + u][1], m2 = mono[n + u][2];
+      part[0] += x;
+      part[1] = fmaf(m0.y, x, part[1]);
+      part[2] = fmaf(m0.z, x, part[2]);
+      part[3] = fmaf(m0.w, x, part[3]);
+      part[4] = fmaf(m1.x, x, part[4]);
+      part[5] = fmaf(m1.y, x, part[5]);
+      part[6] = fmaf(m1.z, x, part[6]);
+      part[7] = fmaf(m1.w, x, part[7]);
+      part[8] = fmaf(m2.x, x, part[8]);
+      part[9] = fmaf(m2.y, x, part[9]);
     }
 #pragma unroll
-    for (int t = 0; t < 7; ++t) kah_add(hi[t], part[t]);
+    for (int t = 0; t < NMONO; ++t) kah_add(acc[t], part[t]);
+#pragma unroll
+    for (int u = 0; u < SBLK; ++u) v[u] = w[u];
   }
+  double* out = s.sums + ((size_t)blockIdx.z * s.ncls + cls) * NMONO * p.N + c;
 #pragma unroll
-  for (int t = 0; t < 3; ++t) red[sub][t][tl] = kah_value(lo[t]);
-#pragma unroll
-  for (int t = 0; t < 7; ++t) red[sub][3 + t][tl] = kah_value(hi[t]);
-  __syncthreads();
-  double* out = s.sums + (size_t)cls * NMONO * p.N;
-  for (int o = threadIdx.x; o < NMONO * CPB; o += 256) {
-    const int t = o / CPB, cc = o % CPB;
-    if (cb0 + cc >= p.N) continue;
-    double v = 0.0;
-#pragma unroll
-    for (int q = 0; q < SPL; ++q) v += red[q][t][cc];
-    out[(size_t)t * p.N + cb0 + cc] = v;
-  }
+  for (int t = 0; t < NMONO; ++t) out[(size_t)t * p.N] = kah_value(acc[t]);
 }
 
 // --------------------------------------------------------------- cellfin
@@ -176,27 +172,32 @@ __device__ __forceinline__ void stencil_moments(const float (&mu)[NMONO], float 
   }
 }
 
-// Per cell: rho, u (FP64, from the class sums) into mom, the equilibrium's
-// assembly parameters into eq (FP32), and nu of every combination.
-__global__ void __launch_bounds__(256)
+// Per cell and combination (grid y): rho, u (FP64, from the class sums),
+// with the first combination writing them into mom and the equilibrium's
+// assembly parameters into eq (FP32); nu of the combination.
+__global__ void __launch_bounds__(64)
 k_gnc_cellfin(GncStep s, int stage) {
   const DevParams& p = s.p;
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cb = blockIdx.y;                       // this thread's combination
   if (cell >= p.N) return;
   const size_t N = p.N;
   double r = s.ref.W, jx = s.ref.Wx, jy = s.ref.Wy;
-  for (int c = 0; c < s.ncls; ++c) {
-    const double* sc = s.sums + (size_t)c * NMONO * N + cell;
-    r += sc[0];
-    jx += sc[N];
-    jy += sc[2 * N];
-  }
+  for (int z = 0; z < s.nsplit; ++z)
+    for (int c = 0; c < s.ncls; ++c) {
+      const double* sc = s.sums + ((size_t)z * s.ncls + c) * NMONO * N + cell;
+      r += sc[0];
+      jx += sc[N];
+      jy += sc[2 * N];
+    }
   const double ux = jx / r, uy = jy / r;
-  double* mom = stage == 1 ? s.mom_n : s.mom_p;
-  mom[cell] = r;
-  mom[N + cell] = ux;
-  mom[2 * N + cell] = uy;
-  store_par(stage == 1 ? s.eqn : s.eqp, p.N, cell, eq_params_u<float>(r, ux, uy, p.inv_RT, s.ref.rho0));
+  if (cb == 0) {
+    double* mom = stage == 1 ? s.mom_n : s.mom_p;
+    mom[cell] = r;
+    mom[N + cell] = ux;
+    mom[2 * N + cell] = uy;
+    store_par(stage == 1 ? s.eqn : s.eqp, p.N, cell, eq_params_u<float>(r, ux, uy, p.inv_RT, s.ref.rho0));
+  }
   // W_k (rho P(xi_k) - rho0) = W_k sum_q qd_q pi_q(xi_k), q over 1, x, y, xx, xy, yy
   const double vx = ux * p.inv_RT, vy = uy * p.inv_RT;
   float qd[6];
@@ -209,7 +210,7 @@ k_gnc_cellfin(GncStep s, int stage) {
   const StageCoef& sc = stage == 1 ? s.s1 : s.s2;
   const float b = (float)sc.b, omb = (float)(1.0 - sc.b);
   const float hx = (float)(sc.h * p.inv_dx), hy = (float)(sc.h * p.inv_dy);
-  for (int cb = 0; cb < s.ncombo; ++cb) {
+  {
     const GncCombo& C = s.cmb[cb];
     float mu[NMONO];
 #pragma unroll
@@ -217,9 +218,12 @@ k_gnc_cellfin(GncStep s, int stage) {
     for (int c = 0; c < s.ncls; ++c) {
       const float lam = C.lam[c];
       if (lam == 0.f) continue;
-      const double* sc2 = s.sums + (size_t)c * NMONO * N + cell;
 #pragma unroll
-      for (int t = 0; t < NMONO; ++t) mu[t] = fmaf(lam, (float)sc2[(size_t)t * N], mu[t]);
+      for (int t = 0; t < NMONO; ++t) {
+        double v = 0.0;
+        for (int z = 0; z < s.nsplit; ++z) v += s.sums[(((size_t)z * s.ncls + c) * NMONO + t) * N + cell];
+        mu[t] = fmaf(lam, (float)v, mu[t]);
+      }
     }
     // g = (1 - b) src + b feq: the equilibrium's part by the combination's
     // quadrature table zc[p][q] = sum lam W_k pi_p pi_q
@@ -292,7 +296,7 @@ __device__ void face_moments(const GncStep& s, int cb, int ci, int cj, float (&M
   const bool inside = ci >= 1 && ci + 1 < p.nx && cj >= 1 && cj + 1 < p.ny;
   if (inside) {
     const float* c0 = base + cj * p.nx + ci;
-#pragma unroll
+#pragma unroll 1
     for (int t = 0; t < 9; ++t) {
       const int off = (t / 3 - 1) * p.nx + t % 3 - 1;
 #pragma unroll
@@ -329,7 +333,7 @@ __device__ void face_moments(const GncStep& s, int cb, int ci, int cj, float (&M
 // assembly parameters; at a wall, the leaving velocities by the wall rule
 // and the wall density (bounce-back: the fluid cell's rho; diffuse: from the
 // incoming flux, Q15) into wrho for the walls pass.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(64)
 k_gnc_facefin(GncStep s, int stage) {
   const DevParams& p = s.p;
   const int nfx = p.ny * (p.nx + 1), nfy = (p.ny + 1) * p.nx;
@@ -407,7 +411,7 @@ k_gnc_facefin(GncStep s, int stage) {
 // for the leaving ones; bounce-back's leaving values (eq. BB) are formed by
 // the update from the mirrored velocity's entry.
 constexpr int WSEG = 128;                // wall faces per block
-constexpr int WCH = 32;                  // velocities per block
+constexpr int WCH = 8;                   // velocities per block (their loads issued at once)
 constexpr int WTW = WSEG + 6;            // strip positions along the wall
 constexpr int WEPT = (3 * WTW + 127) / 128;   // staged cells per thread
 
@@ -470,28 +474,28 @@ k_gnc_walls(GncStep s, int stage) {
   const int slot = (side == SIDE_W ? 0 : side == SIDE_E ? p.ny : side == SIDE_S ? 2 * p.ny
                                                                  : 2 * p.ny + p.nx) + tt;
   const double rw = tt < t1 ? s.wrho[slot] : 0.0;
-  T raw[WEPT];
+  T raw[WCH][WEPT];
 #pragma unroll
-  for (int m = 0; m < WEPT; ++m)
-    if (sin_[m] && k0 < k1) raw[m] = ldr(src + (size_t)k0 * p.N + soff[m]);
-  for (int k = k0; k < k1; ++k) {
-    float* g = st[(k - k0) & 1];
+  for (int q = 0; q < WCH; ++q)
+#pragma unroll
+    for (int m = 0; m < WEPT; ++m)
+      if (sin_[m] && k0 + q < k1) raw[q][m] = ldr(src + (size_t)(k0 + q) * p.N + soff[m]);
+#pragma unroll
+  for (int kq = 0; kq < WCH; ++kq) {
+    const int k = k0 + kq;
+    if (k >= k1) break;                  // uniform per block
+    float* g = st[kq & 1];
     const float4 e4 = ld4(vq + p.nv + k);
 #pragma unroll
     for (int m = 0; m < WEPT; ++m)
       if (sidx[m] >= 0) {
         float v = 0.f;
         if (sin_[m]) {
-          const float r = tof(raw[m]);
+          const float r = tof(raw[kq][m]);
           v = fmaf(b, feq_dev<float>(sq[m], e4.x, e4.y, e4.z) - r, r);
         }
         g[sidx[m]] = v;
       }
-    if (k + 1 < k1) {
-#pragma unroll
-      for (int m = 0; m < WEPT; ++m)
-        if (sin_[m]) raw[m] = ldr(src + (size_t)(k + 1) * p.N + soff[m]);
-    }
     __syncthreads();
     // ghosts: across the x-direction first (rows inside the mesh), then y
     for (int pass = 0; pass < 2; ++pass) {
@@ -1222,6 +1226,22 @@ bool gnc_tables(GncStep& g, const double* xi_x, const double* xi_y, const double
   return true;
 }
 
+// velocity splits of the class sums: at most SMAXE velocities per split,
+// and about four blocks per SM where the classes have 64 velocities per
+// split to spare
+int gnc_splits(const GncStep& g, const GncTables& t, int sms) {
+  int smallest = g.p.nv, largest = 1;
+  for (int c = 0; c < g.ncls; ++c) {
+    const int n = t.cls_off[c + 1] - t.cls_off[c];
+    smallest = std::min(smallest, n);
+    largest = std::max(largest, n);
+  }
+  const int need = (largest + SMAXE - 1) / SMAXE;
+  const int blocks = ((g.p.N + SCB - 1) / SCB) * g.ncls;
+  const int want = std::min((4 * sms + blocks - 1) / blocks, std::max(1, smallest / 64));
+  return std::max(need, want);
+}
+
 // velocity chunks per tile: about one wave of update blocks
 int gnc_chunks(const GncStep& g, int sms) {
   int bps = 0;
@@ -1243,20 +1263,20 @@ cudaError_t gnc_prepare(int store) {
 
 // class sums of the stage's source, then the cell finaliser
 cudaError_t launch_gnc_sums(const GncStep& s, int stage, cudaStream_t st) {
-  const dim3 grid((s.p.N + CPB - 1) / CPB, s.ncls);
-  if (s.store == 1) k_gnc_sums<float><<<grid, 256, 0, st>>>(s, stage);
-  else k_gnc_sums<__nv_bfloat16><<<grid, 256, 0, st>>>(s, stage);
+  const dim3 grid((s.p.N + SCB - 1) / SCB, s.ncls, s.nsplit);
+  if (s.store == 1) k_gnc_sums<float><<<grid, SCB, 0, st>>>(s, stage);
+  else k_gnc_sums<__nv_bfloat16><<<grid, SCB, 0, st>>>(s, stage);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gnc_cellfin(const GncStep& s, int stage, cudaStream_t st) {
-  k_gnc_cellfin<<<(s.p.N + 255) / 256, 256, 0, st>>>(s, stage);
+  k_gnc_cellfin<<<dim3((s.p.N + 63) / 64, s.ncombo), 64, 0, st>>>(s, stage);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gnc_facefin(const GncStep& s, int stage, cudaStream_t st) {
   const int nf = s.p.ny * (s.p.nx + 1) + (s.p.ny + 1) * s.p.nx;
-  k_gnc_facefin<<<(nf + 255) / 256, 256, 0, st>>>(s, stage);
+  k_gnc_facefin<<<(nf + 63) / 64, 64, 0, st>>>(s, stage);
   return cudaGetLastError();
 }
 

@@ -225,7 +225,7 @@ struct GncStep {
   float *fpx, *fpy;             // face equilibrium parameters [5][nfx], [5][nfy]
   float* wf;                    // wall faces' f-bar [nv][nw]
   double* wrho;                 // wall density per wall face [nw]
-  double* sums;                 // class sums [ncls][10][N]
+  double* sums;                 // class sums [nsplit][ncls][10][N]
   float* nu;                    // stencil moments [ncombo][18][N]
   const void* vq;               // velocity table of GDevStep::vq (FP32)
   const float* fwt;             // face-value weights [2 stages][nv][48]
@@ -235,7 +235,7 @@ struct GncStep {
   const float* zc;              // [ncombo][10][6] equilibrium quadrature per combination
   const float2* wbb;            // [nv][4] bounce-back (c_k, shift_k) per side
   const int* wsrc;              // [4][nv] velocity whose wall-face entry the update reads
-  int ncls, ncombo;
+  int ncls, ncombo, nsplit;      // classes, combinations, velocity splits of the sums
   int ties;                     // some velocity has xi_x = 0 or xi_y = 0
   GncCombo cmb[12];
   int c_lo[2], c_up[2];         // interior faces of x and y: xi.n > 0 / < 0 combinations
@@ -257,6 +257,7 @@ struct GncTables {              // host tables of GncStep's device arrays
 bool gnc_tables(GncStep& g, const double* xi_x, const double* xi_y, const double* w,
                 const double* feq_wall, const int* opp, GncTables& t);
 int gnc_chunks(const GncStep& g, int sms);
+int gnc_splits(const GncStep& g, const GncTables& t, int sms);
 cudaError_t gnc_prepare(int store);
 cudaError_t launch_gnc_sums(const GncStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gnc_cellfin(const GncStep& s, int stage, cudaStream_t st);
