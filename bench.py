@@ -57,6 +57,7 @@ FLOPS_PER_UNIT = {
     "t2_cell": 17, "t2_face_x": 34, "t2_face_y": 34, "t2_update": 19,
 }
 SCHEMES = {"t3s3": 0, "t2s3": 1, "t2s2": 2}
+PATHS = {"auto": 0, "generic": 1, "reference": 2}
 # The same kernels in FP64 (dugks_generic_mixed.cu with FP64 storage): all
 # their arithmetic is FP64 -- cell: moment sums 5 + g = a f + b W P(xi) with
 # P quadratic (5 FMAs) 14; face: 9-point stencil 18 + moment sums 5;
@@ -285,7 +286,7 @@ def whole_job_rate(units_per_rank, steps, world, seconds):
     return units_per_rank * steps * world / seconds / 1e9
 
 
-def make_solver(P, PV, WL, stream, storage=0, scheme="t3s3"):
+def make_solver(P, PV, WL, stream, storage=0, scheme="t3s3", path=0):
     c = WL.config(WORKLOAD)
     if c.get("vel") == "nc":
         xi, W, RT = PV.newton_cotes(c["nv1"], c["RT"])
@@ -293,7 +294,7 @@ def make_solver(P, PV, WL, stream, storage=0, scheme="t3s3"):
         xi, W, RT = PV.d2q9(c["RT"])
     n = c["nx"]
     s = P.Solver(n, n, 1.0 / n, 1.0 / n, xi, W, RT, c["tau"], c["dt"], c["bc"], stream=stream,
-                 storage=storage, scheme=SCHEMES[scheme])
+                 storage=storage, scheme=SCHEMES[scheme], path=path)
     s.set_equilibrium(*WL.rest_fields(n, n))
     return s, c, len(W)
 
@@ -643,7 +644,8 @@ def run_ours(args):
     P.load()
     main_storage = {"fp64": P.FP64, "fp32": P.G_FP32, "bf16": P.G_BF16,
                     "f64dw": P.F64_DW}[args.storage]
-    solver, c, nv = make_solver(P, PV, WL, stream, storage=main_storage, scheme=args.scheme)
+    solver, c, nv = make_solver(P, PV, WL, stream, storage=main_storage, scheme=args.scheme,
+                                path=PATHS[args.path])
     units = c["nx"] * c["ny"] * nv
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -789,9 +791,9 @@ def run_ours(args):
         "unit": "G updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp32": "f32 deviation storage, f64 moment sums",
-                  "bf16": "bf16 deviation storage, f32 arithmetic, f64 moment sums",
-                  "f64dw": "f64 storage, double-word (f32 pair) arithmetic"}[args.storage],
+        "dtype": {"fp64": "f64", "fp32": "f32 (f32 deviation storage)",
+                  "bf16": "f32 (bf16 deviation storage)",
+                  "f64dw": "f32 pairs (f64 storage, double-word arithmetic)"}[args.storage],
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "cells": f"{nx}x{ny}", "scheme": args.scheme.upper(),
                    "velocities": ("D2Q9" if c.get("vel") != "nc"
@@ -800,7 +802,8 @@ def run_ours(args):
                           else "diffuse walls, moving lid"),
                    **({"Re": 1000, "Ma": 0.1} if c.get("vel") != "nc" else {"Kn": c.get("Kn")}),
                    "units_per_step": units, "l2": "flushed (256 MiB write) before every timed step",
-                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   **({"kernel_path": args.path} if args.path != "auto" else {})},
         "roofline": {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,
                      "traffic": (TRAFFIC_BYTES_PER_UNIT[name] * per_launch_units
@@ -846,6 +849,10 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD,
                     help="cavityN (N^2 D2Q9 cavity); the default is the reported workload")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--path", default="auto", choices=list(PATHS),
+                    help="kernel path of dugks_init_ex (auto: fused D2Q9 or optimised "
+                         "generic; generic: optimised generic for every set; reference: the "
+                         "FP64 kernels that also run the T2 schemes)")
     ap.add_argument("--scheme", default="t3s3", choices=list(SCHEMES),
                     help="time scheme (T2S3/T2S2: the second-order comparison schemes, "
                          "generic FP64 kernels; the step they time is a T2 step)")

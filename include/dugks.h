@@ -64,7 +64,7 @@ enum { DUGKS_WEST = 0, DUGKS_EAST = 1, DUGKS_SOUTH = 2, DUGKS_NORTH = 3 };
  *                  numbers, 48-bit significand, unit roundoff 2^-48; sums
  *                  with a normwise error bound), which GB300 runs on its
  *                  FP32 pipes.  Fused D2Q9 kernels only: other velocity
- *                  sets, DUGKS_FORCE_GENERIC=1, the T2 schemes, the adjoint
+ *                  sets, DUGKS_PATH_GENERIC, the T2 schemes, the adjoint
  *                  and the batched launch refuse it (DUGKS_ENOTIMPL; a batch
  *                  steps such a context with its own launches).
  * The description above is that of the fused D2Q9 kernels, taken when the
@@ -115,6 +115,27 @@ typedef struct { int kind; double uw_x, uw_y; } dugks_bc;
  */
 int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, double dt,
                const dugks_bc bc[4], int storage, void* cuda_stream, dugks_ctx** out);
+
+/* Kernel paths of dugks_init_ex.  dugks_init takes DUGKS_PATH_AUTO: the
+ * fused D2Q9 kernels for a set in the D2Q9 listing order of Sec. 2.2, the
+ * optimised generic kernels for any other set.  DUGKS_PATH_GENERIC takes the
+ * optimised generic kernels for every set (a D2Q9 set included);
+ * DUGKS_PATH_REFERENCE the reference FP64 kernels that also run the T2
+ * schemes, the adjoint's forward recomputation and dugks_step_static (FP64
+ * storage only).  All paths compute the same step; the selector exists so
+ * that one problem can be run on each of them and compared. */
+enum { DUGKS_PATH_AUTO = 0, DUGKS_PATH_GENERIC = 1, DUGKS_PATH_REFERENCE = 2 };
+
+/*
+ * dugks_init_ex -- dugks_init with an explicit kernel path.
+ *   path : DUGKS_PATH_AUTO, DUGKS_PATH_GENERIC or DUGKS_PATH_REFERENCE.
+ * Errors: those of dugks_init; EINVAL for an unknown path; ENOTIMPL for
+ * DUGKS_PATH_REFERENCE with a deviation storage form, and for
+ * DUGKS_F64_DW on any path but DUGKS_PATH_AUTO with a D2Q9 set.
+ */
+int dugks_init_ex(const dugks_mesh* mesh, const dugks_velset* vel, double tau, double dt,
+                  const dugks_bc bc[4], int storage, int path, void* cuda_stream,
+                  dugks_ctx** out);
 
 /*
  * dugks_set_equilibrium -- f^ = feq(rho, u) in every cell (the paper's

@@ -26,9 +26,10 @@ PERIODIC, BOUNCEBACK, DIFFUSE = 0, 1, 2
 WEST, EAST, SOUTH, NORTH = 0, 1, 2, 3
 FP64, G_FP32, G_BF16, F64_DW = 0, 1, 2, 3
 T3S3, T2S3, T2S2 = 0, 1, 2
+PATH_AUTO, PATH_GENERIC, PATH_REFERENCE = 0, 1, 2
 
 # every symbol include/dugks.h declares
-EXPORTS = ("dugks_init", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_state",
+EXPORTS = ("dugks_init", "dugks_init_ex", "dugks_set_equilibrium", "dugks_set_state", "dugks_get_state",
            "dugks_step", "dugks_moments", "dugks_check", "dugks_synchronize",
            "dugks_profile", "dugks_profile_read", "dugks_kernel_name", "dugks_destroy",
            "dugks_last_error", "dugks_step_static", "dugks_adjoint_step", "dugks_adjoint_run",
@@ -70,6 +71,8 @@ def load(path: str = LIB_PATH):
     P, I, D = C.c_void_p, C.c_int, C.c_double
     sig = {
         "dugks_init": (I, [C.POINTER(Mesh), C.POINTER(VelSet), D, D, C.POINTER(BC), I, P, C.POINTER(P)]),
+        "dugks_init_ex": (I, [C.POINTER(Mesh), C.POINTER(VelSet), D, D, C.POINTER(BC), I, I, P,
+                              C.POINTER(P)]),
         "dugks_set_equilibrium": (I, [P, P, P, P, I]),
         "dugks_set_state": (I, [P, P, I]),
         "dugks_get_state": (I, [P, P, I, I]),
@@ -126,10 +129,12 @@ def _on_device(a):
 
 
 # ------------------------------------------------- C-ABI mirrors
-def dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, storage=FP64, stream=None):
+def dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, storage=FP64, stream=None,
+               path=PATH_AUTO):
     """Returns an opaque context handle (int).  ``bc``: four (kind, uw_x, uw_y)
     in the order west, east, south, north; ``stream``: a torch.cuda.Stream,
-    a raw cudaStream_t int, or None."""
+    a raw cudaStream_t int, or None; ``path``: the kernel path of
+    ``dugks_init_ex`` (PATH_AUTO, PATH_GENERIC, PATH_REFERENCE)."""
     lib = load()
     xi = np.ascontiguousarray(xi, dtype=np.float64)
     xx = np.ascontiguousarray(xi[:, 0])
@@ -142,8 +147,12 @@ def dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, storage=FP64, stream=None
     mesh = Mesh(int(nx), int(ny), float(dx), float(dy))
     s = stream.cuda_stream if hasattr(stream, "cuda_stream") else (stream or 0)
     out = C.c_void_p()
-    _check(lib.dugks_init(C.byref(mesh), C.byref(vs), float(tau), float(dt), bcs, int(storage),
-                          C.c_void_p(s), C.byref(out)))
+    if path == PATH_AUTO:
+        _check(lib.dugks_init(C.byref(mesh), C.byref(vs), float(tau), float(dt), bcs, int(storage),
+                              C.c_void_p(s), C.byref(out)))
+    else:
+        _check(lib.dugks_init_ex(C.byref(mesh), C.byref(vs), float(tau), float(dt), bcs,
+                                 int(storage), int(path), C.c_void_p(s), C.byref(out)))
     return out.value
 
 
@@ -354,10 +363,10 @@ class Solver:
     """One DUGKS context: ``Solver(nx, ny, dx, dy, xi, W, RT, tau, dt, bc)``."""
 
     def __init__(self, nx, ny, dx, dy, xi, W, RT, tau, dt, bc, stream=None, storage=FP64,
-                 scheme=T3S3):
+                 scheme=T3S3, path=PATH_AUTO):
         self.nx, self.ny, self.nv = int(nx), int(ny), len(W)
         self.ctx = None
-        self.ctx = dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, storage, stream)
+        self.ctx = dugks_init(nx, ny, dx, dy, xi, W, RT, tau, dt, bc, storage, stream, path)
         self.warning = dugks_last_error()
         if scheme != T3S3:
             dugks_set_scheme(self.ctx, scheme)

@@ -585,9 +585,17 @@ const char* dugks_kernel_name(int id) {
 
 int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, double dt,
                const dugks_bc bc[4], int storage, void* cuda_stream, dugks_ctx** out) {
+  return dugks_init_ex(mesh, vel, tau, dt, bc, storage, DUGKS_PATH_AUTO, cuda_stream, out);
+}
+
+int dugks_init_ex(const dugks_mesh* mesh, const dugks_velset* vel, double tau, double dt,
+                  const dugks_bc bc[4], int storage, int path, void* cuda_stream, dugks_ctx** out) {
   g_err.clear();
   if (!out) return fail(DUGKS_EINVAL, "out is NULL");
   *out = nullptr;
+  if (path < DUGKS_PATH_AUTO || path > DUGKS_PATH_REFERENCE) return fail(DUGKS_EINVAL, "unknown kernel path");
+  if (path == DUGKS_PATH_REFERENCE && storage != DUGKS_FP64)
+    return fail(DUGKS_ENOTIMPL, "the reference kernels store FP64");
   if (!mesh || !vel || !bc) return fail(DUGKS_EINVAL, "NULL mesh, velocity set or bc");
   if (storage < DUGKS_FP64 || storage > DUGKS_F64_DW) return fail(DUGKS_ENOTIMPL, "unknown storage form");
   if (mesh->nx < 1 || mesh->ny < 1) return fail(DUGKS_EINVAL, "nx, ny must be >= 1");
@@ -606,8 +614,7 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
   // double-word arithmetic: FP64 arrays, taken by the fused D2Q9 kernels only
   const bool dwa = storage == DUGKS_F64_DW;
   if (dwa) {
-    const char* fg = std::getenv("DUGKS_FORCE_GENERIC");
-    if (!(d2q9_speed(vel) > 0.0) || (fg && fg[0] == '1'))
+    if (!(d2q9_speed(vel) > 0.0) || path != DUGKS_PATH_AUTO)
       return fail(DUGKS_ENOTIMPL, "double-word arithmetic runs on the fused D2Q9 kernels only");
     storage = DUGKS_FP64;
   }
@@ -769,16 +776,15 @@ int dugks_init(const dugks_mesh* mesh, const dugks_velset* vel, double tau, doub
 
   // fused D2Q9 path
   const double cd = d2q9_speed(vel);
-  const char* force = std::getenv("DUGKS_FORCE_GENERIC");
-  const bool forced = force && force[0] == '1';
-  // The optimised generic kernels (dugks_generic_mixed.cu) step every
-  // context that the fused D2Q9 kernels do not take: any velocity set, FP64
-  // or deviation storage.  DUGKS_LEGACY_GENERIC=1 keeps FP64 contexts on the
-  // first generic kernels (dugks_kernels.cu, dugks_nc.cu), which also run
-  // the T2 schemes.
-  const char* legacy = std::getenv("DUGKS_LEGACY_GENERIC");
+  const bool forced = path != DUGKS_PATH_AUTO;
+  // The optimised generic kernels (dugks_generic_mixed.cu for FP64,
+  // dugks_gnc.cu for the deviation forms) step every context that the fused
+  // D2Q9 kernels do not take: any velocity set, any storage.
+  // DUGKS_PATH_REFERENCE keeps an FP64 context on the reference kernels
+  // (dugks_kernels.cu, dugks_nc.cu), which also run the T2 schemes, the
+  // adjoint's recomputation and the allocation-free entry.
   const bool generic = !(cd > 0.0 && !forced);
-  if (generic && (storage != DUGKS_FP64 || !(legacy && legacy[0] == '1'))) {
+  if (generic && path != DUGKS_PATH_REFERENCE) {
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -287,44 +287,38 @@ __device__ __forceinline__ int ghost_terms(const DevParams& p, int ci, int cj, i
 
 // --------------------------------------------------------------- facefin
 // Face moments of combination cb for the stencil about cell (ci, cj):
-// M_m = sum_s sum_u t_u(s) nu_{m,u}(cell + s); cells outside the mesh by
-// their ghost terms, the stencil of a cell away from the walls directly
+// M_m = sum over the nonzero t_u(s) of t_u(s) nu_{m,u}(cell + s) (the
+// list tl of GncStep); cells outside the mesh by their ghost terms, the
+// stencil of a cell away from the walls directly
 __device__ void face_moments(const GncStep& s, int cb, int ci, int cj, float (&M)[3]) {
   const DevParams& p = s.p;
   const float* base = s.nu + (size_t)cb * NNU * p.N;
   M[0] = M[1] = M[2] = 0.f;
   const bool inside = ci >= 1 && ci + 1 < p.nx && cj >= 1 && cj + 1 < p.ny;
-  if (inside) {
-    const float* c0 = base + cj * p.nx + ci;
+  const size_t plane = (size_t)6 * p.N;            // from nu_{m,u} to nu_{m+1,u}
 #pragma unroll 1
-    for (int t = 0; t < 9; ++t) {
-      const int off = (t / 3 - 1) * p.nx + t % 3 - 1;
-#pragma unroll
-      for (int u = 0; u < 6; ++u) {
-        const float w = s.tu[u][t];
-        if (w == 0.f) continue;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) M[m] = fmaf(w, __ldg(c0 + (size_t)(6 * m + u) * p.N + off), M[m]);
+  for (int q = 0; q < s.ntl; ++q) {
+    const int t = s.tl_s[q], u = s.tl_u[q];
+    const float w = s.tl_w[q];
+    const float* b = base + (size_t)u * p.N;
+    if (inside) {
+      const int c = (cj + t / 3 - 1) * p.nx + ci + t % 3 - 1;
+      M[0] = fmaf(w, __ldg(b + c), M[0]);
+      M[1] = fmaf(w, __ldg(b + plane + c), M[1]);
+      M[2] = fmaf(w, __ldg(b + 2 * plane + c), M[2]);
+    } else {
+      int idx[9];
+      float co[9];
+      const int n = ghost_terms(p, ci + t % 3 - 1, cj + t / 3 - 1, idx, co);
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      for (int r = 0; r < n; ++r) {
+        v0 = fmaf(co[r], __ldg(b + idx[r]), v0);
+        v1 = fmaf(co[r], __ldg(b + plane + idx[r]), v1);
+        v2 = fmaf(co[r], __ldg(b + 2 * plane + idx[r]), v2);
       }
-    }
-    return;
-  }
-#pragma unroll 1
-  for (int t = 0; t < 9; ++t) {
-    int idx[9];
-    float co[9];
-    const int n = ghost_terms(p, ci + t % 3 - 1, cj + t / 3 - 1, idx, co);
-#pragma unroll 1
-    for (int u = 0; u < 6; ++u) {
-      const float w = s.tu[u][t];
-      if (w == 0.f) continue;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const float* b = base + (size_t)(6 * m + u) * p.N;
-        float v = 0.f;
-        for (int q = 0; q < n; ++q) v = fmaf(co[q], __ldg(b + idx[q]), v);
-        M[m] = fmaf(w, v, M[m]);
-      }
+      M[0] = fmaf(w, v0, M[0]);
+      M[1] = fmaf(w, v1, M[1]);
+      M[2] = fmaf(w, v2, M[2]);
     }
   }
 }
@@ -1143,6 +1137,15 @@ bool gnc_tables(GncStep& g, const double* xi_x, const double* xi_y, const double
     g.tu[4][q] = (float)tab;
     g.tu[5][q] = (float)tbb;
   }
+  g.ntl = 0;
+  for (int q = 0; q < 9; ++q)
+    for (int u = 0; u < 6; ++u)
+      if (g.tu[u][q] != 0.f) {
+        g.tl_s[g.ntl] = (unsigned char)q;
+        g.tl_u[g.ntl] = (unsigned char)u;
+        g.tl_w[g.ntl] = g.tu[u][q];
+        ++g.ntl;
+      }
   // wall tables: sums over the leaving velocities (xi.n < 0, n the fluid's
   // outward normal) of pi_m times the bounce-back coefficient, the
   // deviation shift, the wall equilibrium and the reference state

@@ -241,6 +241,9 @@ struct GncStep {
   int c_lo[2], c_up[2];         // interior faces of x and y: xi.n > 0 / < 0 combinations
   int c_wf[4], c_win[4];        // per wall: fluid side (ties too), strictly incoming
   float tu[6][9];               // T(a, b) = sum_u tu[u] u(a, b), u = 1, a, b, a^2, ab, b^2
+  int ntl;                      // the nonzero tu as a list: stencil cell, u, weight
+  unsigned char tl_s[54], tl_u[54];
+  float tl_w[54];
   double wB[4][3], wH[4][3];    // per wall, sums over the leaving velocities of (1, xi) x
   double wMo[4][3], wWo[4][3];  // bounce-back coefficient, shift, wall equilibrium, W rho0
   double ds_out[4];             // rho0 sum over xi.n > 0 of (xi.n) W_k per wall side

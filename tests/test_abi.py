@@ -81,6 +81,20 @@ def test_double_word_form_needs_the_d2q9_set(lib):
     assert "D2Q9" in str(e.value)
 
 
+def test_kernel_path_is_checked_on_the_host(lib):
+    """dugks_init_ex refuses an unknown kernel path (EINVAL) and the
+    reference kernels with a deviation storage form (ENOTIMPL) before any
+    device work; the double-word form needs the automatic path."""
+    xi, W, RT = PV.d2q9(1 / 3)
+    for path, storage, code in ((7, P.FP64, P.DUGKS_EINVAL), (-1, P.FP64, P.DUGKS_EINVAL),
+                                (P.PATH_REFERENCE, P.G_FP32, P.DUGKS_ENOTIMPL),
+                                (P.PATH_GENERIC, P.F64_DW, P.DUGKS_ENOTIMPL)):
+        with pytest.raises(P.DugksError) as e:
+            P.dugks_init(8, 8, .1, .1, xi, W, RT, .1, .1, [(P.PERIODIC, 0, 0)] * 4,
+                         storage=storage, path=path)
+        assert e.value.code == code
+
+
 def test_product_velocity_sets_match_oracle():
     """The product and oracle velocity sets are built independently."""
     from oracle import velocity_sets as V

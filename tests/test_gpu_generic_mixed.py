@@ -1,10 +1,13 @@
 """Deviation-storage forms (DUGKS_G_FP32, DUGKS_G_BF16) on the generic
-kernels -- Newton-Cotes velocity grids, and D2Q9 with the generic kernels
-forced -- against the FP64 oracle.
+kernels -- Newton-Cotes velocity grids, and D2Q9 on the generic path
+(DUGKS_PATH_GENERIC) -- against the FP64 oracle.
 
-These forms store d = f - W_k rho0 in FP32 or BF16, compute stencils, face
-values and the equilibrium assembly in FP32 and accumulate every moment sum
-in FP64.  They are not bit-for-bit; the bounds are on the relative
+These forms store d = f - W_k rho0 in FP32 or BF16 and compute stencils,
+face values and the equilibrium assembly in FP32.  The moment sums over the
+velocities add blocks of 16 terms in FP32 and fold each block into a
+Kahan-compensated FP32 sum, which is rounded to FP64; the splits of a sum
+and the face moments built from the cell sums are added in FP64 and FP32
+respectively.  They are not bit-for-bit; the bounds are on the relative
 L-infinity state error max|f - f_oracle| / max|f_oracle|, the L2 velocity
 error E(u) (Sec. 3.1 definition) and the relative mass drift, after the
 stated number of steps, each a few times the value measured on GB300
@@ -114,15 +117,15 @@ def test_rarefied128_fp32_corner_window(cuda):
 
 
 @pytest.mark.parametrize("storage", FORMS, ids=IDS)
-def test_d2q9_on_generic_deviation_kernels(cuda, monkeypatch, storage):
-    """D2Q9 with the generic kernels forced (DUGKS_FORCE_GENERIC=1): the
-    Taylor-Green vortex on 32^2, 200 steps, within the bounds of the fused
-    deviation kernels."""
-    monkeypatch.setenv("DUGKS_FORCE_GENERIC", "1")
+def test_d2q9_on_generic_deviation_kernels(cuda, storage):
+    """D2Q9 on the generic kernels (dugks_init_ex with DUGKS_PATH_GENERIC):
+    the Taylor-Green vortex on 32^2, 200 steps, within the bounds of the
+    fused deviation kernels."""
     c = WL.config("tgv32")
     xi, W, RT = PV.d2q9(c["RT"])
     fields = WL.tgv_fields(32, 32, c["u0"], c["RT"])
-    g = P.Solver(32, 32, 1 / 32, 1 / 32, xi, W, RT, c["tau"], c["dt"], c["bc"], storage=storage)
+    g = P.Solver(32, 32, 1 / 32, 1 / 32, xi, W, RT, c["tau"], c["dt"], c["bc"], storage=storage,
+                 path=P.PATH_GENERIC)
     g.set_equilibrium(*fields)
     m0 = g.moments()[0].sum()
     g.step(200)

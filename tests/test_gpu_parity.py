@@ -22,14 +22,15 @@ def rel_linf(a, b):
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
-def pair(nx, ny, vel, RT, tau, dt, bc, Lx=1.0, Ly=1.0, **vkw):
-    """(GPU solver, oracle setup) for the same problem."""
+def pair(nx, ny, vel, RT, tau, dt, bc, Lx=1.0, Ly=1.0, path=P.PATH_AUTO, **vkw):
+    """(GPU solver, oracle setup) for the same problem; ``path`` the kernel
+    path of dugks_init_ex."""
     if vel == "d2q9":
         pg, po = PV.d2q9(RT), OV.d2q9(RT)
     else:
         pg, po = PV.newton_cotes(vel, RT, **vkw), OV.newton_cotes_2d(vel, RT, **vkw)
     dx, dy = Lx / nx, Ly / ny
-    g = P.Solver(nx, ny, dx, dy, pg[0], pg[1], pg[2], tau, dt, bc)
+    g = P.Solver(nx, ny, dx, dy, pg[0], pg[1], pg[2], tau, dt, bc, path=path)
     o = O.Setup(nx, ny, dx, dy, po[0], po[1], po[2], tau, dt, bc)
     return g, o
 
@@ -113,12 +114,12 @@ def test_cavity256_workload_full_compare(cuda):
 
 @pytest.mark.parametrize("kernels", ["optimised", "first"])
 @pytest.mark.parametrize("walls", ["diffuse", "couette", "mixed"])
-def test_newton_cotes_walls(cuda, monkeypatch, walls, kernels):
+def test_newton_cotes_walls(cuda, walls, kernels):
     """Newton-Cotes velocity grid with diffuse-scattering walls (more than 32
-    velocities), on the optimised generic kernels and on the first generic
-    kernels (DUGKS_LEGACY_GENERIC=1; they also serve the T2 schemes, the
+    velocities), on the optimised generic kernels and on the reference
+    kernels (DUGKS_PATH_REFERENCE; they also serve the T2 schemes, the
     adjoint's forward recomputation and the allocation-free entry)."""
-    monkeypatch.setenv("DUGKS_LEGACY_GENERIC", "1" if kernels == "first" else "0")
+    path = P.PATH_REFERENCE if kernels == "first" else P.PATH_AUTO
     uw = 0.16 * np.sqrt(5 / 3 * 0.5)
     bc = {"diffuse": [(P.DIFFUSE, 0, 0)] * 3 + [(P.DIFFUSE, uw, 0)],
           "couette": [(P.PERIODIC, 0, 0)] * 2 + [(P.DIFFUSE, -uw, 0), (P.DIFFUSE, uw, 0)],
@@ -127,7 +128,7 @@ def test_newton_cotes_walls(cuda, monkeypatch, walls, kernels):
     nx, ny = 21, 18
     tau = 1.0 / np.sqrt(np.pi * 0.5 / 2)
     dt = 0.25 * (1 / 21) / (4 * np.sqrt(0.5))
-    g, o = pair(nx, ny, 16, 0.5, tau, dt, bc)
+    g, o = pair(nx, ny, 16, 0.5, tau, dt, bc, path=path)
     f0 = WL.near_equilibrium_state(o.W, ny, nx, amp=0.1, seed=3)
     err, fg, _ = compare_from_state(g, o, f0, 4)
     assert err <= TOL
@@ -215,10 +216,10 @@ def test_unstable_run_is_detected_on_the_host(cuda):
 
 
 @pytest.mark.parametrize("bcname", ["periodic", "cavity", "diffuse"])
-def test_fused_d2q9_matches_generic_path(cuda, monkeypatch, bcname):
+def test_fused_d2q9_matches_generic_path(cuda, bcname):
     """The fused D2Q9 kernels (default for D2Q9) and the generic kernels
-    (forced with DUGKS_FORCE_GENERIC=1) agree with each other and with the
-    oracle, on a grid that spans several 32 x ty tiles with ragged edges."""
+    (DUGKS_PATH_GENERIC) agree with each other and with the oracle, on a grid
+    that spans several 32 x ty tiles with ragged edges."""
     bc = {"periodic": PER,
           "cavity": [(P.BOUNCEBACK, 0, 0)] * 3 + [(P.BOUNCEBACK, 0.05, 0)],
           "diffuse": [(P.DIFFUSE, 0.0, 0.02), (P.DIFFUSE, 0, 0), (P.DIFFUSE, -0.03, 0),
@@ -227,9 +228,8 @@ def test_fused_d2q9_matches_generic_path(cuda, monkeypatch, bcname):
     _, W, _ = OV.d2q9(1 / 3)
     f0 = WL.near_equilibrium_state(W, ny, nx, amp=0.15, seed=17)
     out = {}
-    for mode in ("0", "1"):
-        monkeypatch.setenv("DUGKS_FORCE_GENERIC", mode)
-        g, o = pair(nx, ny, "d2q9", 1 / 3, 0.003, 0.006, bc)
+    for mode, path in (("0", P.PATH_AUTO), ("1", P.PATH_GENERIC)):
+        g, o = pair(nx, ny, "d2q9", 1 / 3, 0.003, 0.006, bc, path=path)
         g.set_state(f0)
         g.step(6)
         out[mode] = g.state()
