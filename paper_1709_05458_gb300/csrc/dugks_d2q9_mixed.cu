@@ -9,10 +9,12 @@
 // O(1) W_k, which keeps FP32/BF16 rounding small relative to f.
 //
 // Precision split: stencil dot products, fluxes, the per-velocity assembly
-// of the equilibrium deviation W_k((rho - rho0) + rho (P_k - 1)) and all
-// combinations run in FP32; the moment sums (rho, rho u) of every face and
-// cell, the reciprocal 1/rho and the equilibrium parameters u / RT and
-// |u|^2 / (2 RT) run in FP64 (Sec. 2.2 moments; Sec. 2.1.1 equilibrium).
+// of the equilibrium deviation W_k((rho - rho0) + rho (P_k - 1)), the face
+// moments and the face equilibria, and all combinations run in FP32; the
+// cell moment sums (rho, rho u), which the collision conserves, are exact
+// (fixed point) and rounded to FP64, and the cell's 1/rho and equilibrium
+// parameters u / RT and |u|^2 / (2 RT) are FP64 (Sec. 2.2 moments;
+// Sec. 2.1.1 equilibrium).
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -54,6 +56,7 @@ struct MixedConst {
   float bbc[4][9];
   float r37, com, a1, b1, a2, b2;   // FP32 copies of the stage coefficients
   float c3f, base_divf;             // FP32 copies of c^2/RT and 1/(2 c^2/RT)
+  float r0Wf, dr0f, sxWf, syWf;     // FP32 copies of rho0W, rho0 (sum W - 1), sxW, syW
 };
 
 template <int K> struct Vel {
@@ -139,33 +142,20 @@ __device__ __forceinline__ void dev_sums(const float (&d)[9], const MixedConst& 
 }
 
 
-// fixed point (56 fraction bits) -> FP32, round to nearest, integer pipe only
-__device__ __forceinline__ float fix2f(long long v) {
-  const unsigned s = v < 0 ? 0x80000000u : 0u;
-  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-  const int lz = __clzll((long long)a);
-  const unsigned long long n = a << (lz & 63);    // leading one at bit 63
-  const unsigned bits = ((unsigned)(127 + 7 - lz) << 23) + (unsigned)((n >> 40) & 0x7fffffull) +
-                        (unsigned)((n >> 39) & 1ull);
-  return __uint_as_float(a == 0 ? 0u : (bits | s));
-}
 
-// The face moments of f-bar rounded once to FP32 (the sums themselves are
-// exact, as in dev_sums); a NaN density marks a deviation beyond the range.
+// The face moments of f-bar, summed in FP32: they set only the face
+// equilibrium, which is assembled in FP32 (the cell moments, which the
+// collision conserves, keep the exact sums of dev_sums).
 __device__ __forceinline__ void dev_sums_f(const float (&d)[9], const MixedConst& M, float& rho,
                                            float& dr, float& sx, float& sy) {
-  unsigned bad = 0u;
-  long long v[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) v[k] = f2fix(d[k], bad);
-  const long long a = v[0] + v[1] + v[2];
-  const long long b = v[6] + v[7] + v[8];
-  const long long r = a + b + (v[3] + v[4] + v[5]);
-  const long long y = (v[2] + v[5] + v[8]) - (v[0] + v[3] + v[6]);
-  rho = bad ? __uint_as_float(0x7fc00000u) : fix2f(r + M.fr0W);
-  dr = fix2f(r + M.fdr0);
-  sx = fix2f(b - a + M.fsxW);
-  sy = fix2f(y + M.fsyW);
+  const float a = (d[0] + d[1]) + d[2];
+  const float b = (d[6] + d[7]) + d[8];
+  const float r = (a + b) + ((d[3] + d[4]) + d[5]);
+  const float y = ((d[2] + d[5]) + d[8]) - ((d[0] + d[3]) + d[6]);
+  rho = r + M.r0Wf;
+  dr = r + M.dr0f;
+  sx = (b - a) + M.sxWf;
+  sy = y + M.syWf;
 }
 
 // Face equilibrium deviations W_k (rho P_k - rho0) in FP32 from the FP32
@@ -578,6 +568,10 @@ MixedConst mixed_const(const D2Q9Params& P, double rho0) {
   M.fdr0 = llrint(std::ldexp(rho0 * (sw - 1.0), 56));
   M.fsxW = llrint(std::ldexp(rho0 * sxp, 56));
   M.fsyW = llrint(std::ldexp(rho0 * syp, 56));
+  M.r0Wf = (float)(rho0 * sw);
+  M.dr0f = (float)(rho0 * (sw - 1.0));
+  M.sxWf = (float)(rho0 * sxp);
+  M.syWf = (float)(rho0 * syp);
   M.c3f = (float)P.c3;
   M.base_divf = (float)P.base_div;
   M.r37 = (float)P.r37;
