@@ -410,7 +410,7 @@ def timed_steps(P, solver, stream, flush, steps):
     return sum(a.elapsed_time(b) for a, b in evs), prof
 
 
-def batched_measure(P, PV, WL, stream, steps, warmup, world=1, individual=True):
+def batched_measure(P, PV, WL, stream, steps, warmup, world=1, individual=True, storage=0):
     """The batched workload: 64 seeded uneven instances advanced together
     (one persistent launch per stage for the D2Q9 ones, one CUDA graph per
     bench step); per step: sum of cells x velocities over all instances.
@@ -430,7 +430,8 @@ def batched_measure(P, PV, WL, stream, steps, warmup, world=1, individual=True):
         else:
             kw = P.BOUNCEBACK if it["vel"] == "d2q9" else P.DIFFUSE
             bc = [(kw, 0, 0)] * 3 + [(kw, it["U"], 0)]
-        s = P.Solver(N, N, 1.0 / N, 1.0 / N, xi, W, RT, it["tau"], it["dt"], bc, stream=stream)
+        s = P.Solver(N, N, 1.0 / N, 1.0 / N, xi, W, RT, it["tau"], it["dt"], bc, stream=stream,
+                     storage=storage)
         if it["kind"] == "tgv":
             s.set_equilibrium(*WL.tgv_fields(N, N, it["U"] * 2 * 3.141592653589793, RT))
         else:
@@ -440,6 +441,7 @@ def batched_measure(P, PV, WL, stream, steps, warmup, world=1, individual=True):
         sols.append(s)
         units += N * N * len(W)
     batch = P.Batch(sols)
+    batch_ty = batch.autotune(2)              # tile height of the persistent D2Q9 launch
     for _ in range(max(warmup, 0)):
         batch.step(1)
     torch.cuda.synchronize()
@@ -481,7 +483,8 @@ def batched_measure(P, PV, WL, stream, steps, warmup, world=1, individual=True):
         sv.close()
     out = {"ms": ms, "units": units, "steps": steps, "instances": len(insts),
            "d2q9_instances": n_d2q9, "d2q9_units_per_step": d2q9_units,
-           "tile_heights": sorted(set(tuned.values())), "stable": ok}
+           "tile_heights": sorted(set(tuned.values())), "batch_tile_height": batch_ty,
+           "stable": ok}
     if ind_ms is not None:
         out["individual_ms"] = ind_ms
     return out
@@ -501,7 +504,8 @@ def run_batched(args):
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
     P.load()
-    m = batched_measure(P, PV, WL, stream, args.steps, args.warmup, world)
+    st = {"fp64": 0, "fp32": 1, "bf16": 2}[args.storage]
+    m = batched_measure(P, PV, WL, stream, args.steps, args.warmup, world, storage=st)
     ms, = reduce_max([m["ms"]], world)
     if rank != 0:
         return 0
@@ -511,7 +515,9 @@ def run_batched(args):
         "value": whole_job_rate(units, args.steps, world, ms * 1e-3), "unit": "G updates/s",
         "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp32": "f32 (f32 deviation storage)",
+                  "bf16": "f32 (bf16 deviation storage)"}[args.storage],
         "data": "synthetic",
         "config": {"workload": "batched64", "instances": m["instances"],
                    "d2q9_instances": m["d2q9_instances"],
@@ -519,6 +525,7 @@ def run_batched(args):
                    "graph": "one CUDA graph per bench step",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "tile_heights": m["tile_heights"],
+                   "batch_tile_height": m["batch_tile_height"],
                    "l2": "flushed (256 MiB write) before every timed step"},
         "individual": {"ms_per_step": m["individual_ms"] / args.steps,
                        "value": units * args.steps / (m["individual_ms"] * 1e-3) / 1e9},
@@ -729,15 +736,18 @@ def run_ours(args):
     if not args.no_extra and WORKLOAD == "cavity256":
         extra["rarefied128_fp32"] = rarefied_measure(P, PV, WL, stream, flush, 20, 3, P.G_FP32,
                                                      "fp32")
-        b = batched_measure(P, PV, WL, stream, 3, 2, world)
-        extra["batched64"] = {
-            "value": b["units"] * b["steps"] / (b["ms"] * 1e-3) / 1e9, "unit": "G updates/s",
-            "ms_per_step": b["ms"] / b["steps"], "steps": b["steps"],
-            "units_per_step": b["units"], "instances": b["instances"],
-            "d2q9_instances": b["d2q9_instances"], "tile_heights": b["tile_heights"],
-            "individual": {"ms_per_step": b["individual_ms"] / b["steps"],
-                           "value": b["units"] * b["steps"] / (b["individual_ms"] * 1e-3) / 1e9},
-            "graph": "one CUDA graph per step", "stable": b["stable"]}
+        for key, st in (("batched64", P.FP64), ("batched64_fp32", P.G_FP32)):
+            b = batched_measure(P, PV, WL, stream, 3, 2, world, storage=st)
+            extra[key] = {
+                "value": b["units"] * b["steps"] / (b["ms"] * 1e-3) / 1e9, "unit": "G updates/s",
+                "ms_per_step": b["ms"] / b["steps"], "steps": b["steps"],
+                "storage": {P.FP64: "fp64", P.G_FP32: "fp32"}[st],
+                "units_per_step": b["units"], "instances": b["instances"],
+                "d2q9_instances": b["d2q9_instances"], "tile_heights": b["tile_heights"],
+                "batch_tile_height": b["batch_tile_height"],
+                "individual": {"ms_per_step": b["individual_ms"] / b["steps"],
+                               "value": b["units"] * b["steps"] / (b["individual_ms"] * 1e-3) / 1e9},
+                "graph": "one CUDA graph per step", "stable": b["stable"]}
 
     ms, e2e_s = reduce_max([ms, e2e_s], world)
     if rank != 0:

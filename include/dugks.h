@@ -230,21 +230,28 @@ int dugks_tile_height(dugks_ctx* ctx, int* ty_out);
  * persistent launch per stage whose blocks take (instance, tile) work items
  * from an atomic counter, so uneven grid sizes and parameters share the
  * GPU; the other contexts (Newton-Cotes sets, deviation storage) run their
- * own launches inside the same graph.  The contexts must share one
- * non-default stream; their parameters and tile heights are read at
- * dugks_batch_create, and the fused instances run with the largest of their
- * tile heights (every block of the persistent launch has that many rows of
- * threads; results do not depend on the height).
- *   dugks_batch_create  -- ctxs[n] (borrowed; keep them alive while the
- *                          batch exists) -> *out.
- *   dugks_batch_step    -- advance every context nsteps steps: the graph for
- *                          this nsteps is captured on first use and replayed
- *                          afterwards (asynchronous on the stream).
- *   dugks_batch_destroy -- free the batch (not the contexts).
+ * own launches inside the same graph, in up to eight concurrent branches
+ * (largest first into the branch with the least cells x velocities).  The
+ * contexts must share one non-default stream; their parameters and tile
+ * heights are read at dugks_batch_create, and the fused instances run with
+ * the largest of their tile heights (every block of the persistent launch
+ * has that many rows of threads; results do not depend on the height).
+ *   dugks_batch_create   -- ctxs[n] (borrowed; keep them alive while the
+ *                           batch exists) -> *out.
+ *   dugks_batch_step     -- advance every context nsteps steps: the graph for
+ *                           this nsteps is captured on first use and replayed
+ *                           afterwards (asynchronous on the stream).
+ *   dugks_batch_autotune -- time `trials` steps of the persistent launch at
+ *                           every tile height and keep the fastest (*ty_out,
+ *                           0 without fused instances); the fused instances'
+ *                           states are restored, results do not change, and
+ *                           graphs captured before are dropped.  Synchronous.
+ *   dugks_batch_destroy  -- free the batch (not the contexts).
  */
 typedef struct dugks_batch dugks_batch;
 int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out);
 int dugks_batch_step(dugks_batch* batch, int nsteps);
+int dugks_batch_autotune(dugks_batch* batch, int trials, int* ty_out);
 int dugks_batch_destroy(dugks_batch* batch);
 
 /*

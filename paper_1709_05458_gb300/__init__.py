@@ -35,7 +35,8 @@ EXPORTS = ("dugks_init", "dugks_init_ex", "dugks_set_equilibrium", "dugks_set_st
            "dugks_last_error", "dugks_step_static", "dugks_adjoint_step", "dugks_adjoint_run",
            "dugks_adjoint_equilibrium", "dugks_autotune", "dugks_set_tile_height",
            "dugks_tile_height", "dugks_batch_create",
-           "dugks_batch_step", "dugks_batch_destroy", "dugks_set_scheme", "dugks_alu_peak")
+           "dugks_batch_step", "dugks_batch_autotune", "dugks_batch_destroy", "dugks_set_scheme",
+           "dugks_alu_peak")
 
 
 class DugksError(RuntimeError):
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
         "dugks_tile_height": (I, [P, C.POINTER(C.c_int)]),
         "dugks_batch_create": (I, [C.POINTER(P), I, C.POINTER(P)]),
         "dugks_batch_step": (I, [P, I]),
+        "dugks_batch_autotune": (I, [P, I, C.POINTER(I)]),
         "dugks_batch_destroy": (I, [P]),
         "dugks_set_scheme": (I, [P, I]),
         "dugks_alu_peak": (I, [I, I, I, P, C.c_longlong, C.POINTER(C.c_double),
@@ -275,6 +277,14 @@ def dugks_batch_step(batch, nsteps=1):
     return _check(load().dugks_batch_step(batch, int(nsteps)))
 
 
+def dugks_batch_autotune(batch, trials=3):
+    """Tile height of the batch's persistent launch: the fastest over
+    ``trials`` timed steps (0 without fused instances)."""
+    ty = C.c_int(0)
+    _check(load().dugks_batch_autotune(batch, int(trials), C.byref(ty)))
+    return ty.value
+
+
 def dugks_batch_destroy(batch):
     return _check(load().dugks_batch_destroy(batch))
 
@@ -307,6 +317,10 @@ class Batch:
 
     def step(self, n=1):
         dugks_batch_step(self.handle, n)
+
+    def autotune(self, trials=3):
+        """Tile height of the persistent launch (see dugks_batch_autotune)."""
+        return dugks_batch_autotune(self.handle, trials)
 
     def close(self):
         if self.handle:

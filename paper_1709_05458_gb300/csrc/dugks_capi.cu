@@ -155,6 +155,12 @@ struct dugks_ctx {
 struct dugks_batch {
   std::vector<dugks_ctx*> ctxs;
   std::vector<dugks_ctx*> own;      // instances run by their own launches
+  // the own instances in branches of the captured graph: branch streams,
+  // the instances of each branch, fork and join events
+  std::vector<cudaStream_t> bstreams;
+  std::vector<std::vector<dugks_ctx*>> branches;
+  std::vector<cudaEvent_t> bevents;
+  std::vector<dugks_ctx*> fused;    // instances of the persistent D2Q9 launch
   cudaStream_t stream = nullptr;
   D2Q9BatchItem* items = nullptr;   // device
   int* tile_start = nullptr;        // device, nitems + 1
@@ -1402,6 +1408,45 @@ int dugks_tile_height(dugks_ctx* c, int* ty_out) {
   return DUGKS_OK;
 }
 
+namespace {
+// The persistent launch's work items for tile height ty: per fused instance
+// its parameters and arrays and its first tile; device tables (re)written.
+cudaError_t batch_items(dugks_batch* b, int ty) {
+  std::vector<D2Q9BatchItem> items;
+  std::vector<int> start(1, 0);
+  for (dugks_ctx* c : b->fused) {
+    D2Q9BatchItem it{};
+    it.P = c->dp;
+    it.P.ty = ty;
+    it.S1 = c->ds1;
+    it.S2 = c->ds2;
+    it.fhat = c->fhat;
+    it.g1 = c->g;
+    it.g2 = c->ftp;
+    it.X = c->acc;
+    it.mom = c->mom;
+    it.tiles_x = (c->p.nx + 31) / 32;
+    start.push_back(start.back() + it.tiles_x * ((c->p.ny + ty - 1) / ty));
+    items.push_back(it);
+  }
+  cudaError_t e = cudaSuccess;
+  if (!b->items) e = cudaMalloc((void**)&b->items, items.size() * sizeof(D2Q9BatchItem));
+  if (e == cudaSuccess && !b->tile_start) e = cudaMalloc((void**)&b->tile_start, start.size() * sizeof(int));
+  if (e == cudaSuccess && !b->counters) e = cudaMalloc((void**)&b->counters, 2 * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->items, items.data(), items.size() * sizeof(D2Q9BatchItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->tile_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice);
+  int dev = 0, sms = 152;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  b->nitems = (int)items.size();
+  b->max_ty = ty;
+  b->blocks = sms * d2q9_batch_blocks_per_sm(ty);
+  return e;
+}
+}  // namespace
+
 int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
   if (!out) return fail(DUGKS_EINVAL, "out is NULL");
   *out = nullptr;
@@ -1416,54 +1461,52 @@ int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
   if (!ctxs[0]->stream) return fail(DUGKS_EINVAL, "batching needs a non-default stream (graph capture)");
   dugks_batch* b = new dugks_batch();
   b->stream = ctxs[0]->stream;
-  std::vector<D2Q9BatchItem> items;
-  std::vector<int> start(1, 0);
   auto fused = [](const dugks_ctx* c) {
     return c->d2q9 && c->store == 0 && !c->dwa && c->scheme == DUGKS_T3S3;
   };
   // one tile height for all fused instances, the largest of theirs: every
   // block of the persistent launch has that many rows of threads, and a
-  // shorter tile would leave some of them idle (results do not depend on it)
+  // shorter tile would leave some of them idle (results do not depend on it;
+  // dugks_batch_autotune times the others)
   for (int i = 0; i < n; ++i)
     if (fused(ctxs[i])) b->max_ty = std::max(b->max_ty, ctxs[i]->dp.ty);
   for (int i = 0; i < n; ++i) {
     dugks_ctx* c = ctxs[i];
     b->ctxs.push_back(c);
     c->batched += 1;
-    if (!fused(c)) {
-      b->own.push_back(c);
-      continue;
-    }
-    D2Q9BatchItem it{};
-    it.P = c->dp;
-    it.P.ty = b->max_ty;
-    it.S1 = c->ds1;
-    it.S2 = c->ds2;
-    it.fhat = c->fhat;
-    it.g1 = c->g;
-    it.g2 = c->ftp;
-    it.X = c->acc;
-    it.mom = c->mom;
-    it.tiles_x = (c->p.nx + 31) / 32;
-    const int tiles = it.tiles_x * ((c->p.ny + b->max_ty - 1) / b->max_ty);
-    start.push_back(start.back() + tiles);
-    items.push_back(it);
+    if (fused(c)) b->fused.push_back(c);
+    else b->own.push_back(c);
   }
-  b->nitems = (int)items.size();
   cudaError_t e = cudaSuccess;
-  if (b->nitems) {
-    e = cudaMalloc((void**)&b->items, items.size() * sizeof(D2Q9BatchItem));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->tile_start, start.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->counters, 2 * sizeof(int));
-    if (e == cudaSuccess)
-      e = cudaMemcpy(b->items, items.data(), items.size() * sizeof(D2Q9BatchItem), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-      e = cudaMemcpy(b->tile_start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice);
-    int dev = 0, sms = 152;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    b->blocks = sms * d2q9_batch_blocks_per_sm(b->max_ty);
+  // Own instances go into up to kBranches graph branches, largest first into
+  // the branch with the least work (cells x velocities), so that their
+  // kernels run concurrently with each other and with the persistent launch.
+  {
+    constexpr int kBranches = 8;
+    const int nb = std::min<int>(kBranches, (int)b->own.size());
+    std::vector<dugks_ctx*> order = b->own;
+    std::stable_sort(order.begin(), order.end(), [](const dugks_ctx* x, const dugks_ctx* y) {
+      return (double)x->p.N * x->p.nv > (double)y->p.N * y->p.nv;
+    });
+    b->branches.assign(nb, {});
+    std::vector<double> load(nb, 0.0);
+    for (dugks_ctx* c : order) {
+      const int q = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      b->branches[q].push_back(c);
+      load[q] += (double)c->p.N * c->p.nv;
+    }
+    for (int q = 0; q < nb && e == cudaSuccess; ++q) {
+      cudaStream_t bs = nullptr;
+      e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+      if (e == cudaSuccess) b->bstreams.push_back(bs);
+    }
+    for (int q = 0; q < nb + 1 && e == cudaSuccess; ++q) {   // fork + one join per branch
+      cudaEvent_t ev = nullptr;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) b->bevents.push_back(ev);
+    }
   }
+  if (e == cudaSuccess && !b->fused.empty()) e = batch_items(b, b->max_ty);
   if (e != cudaSuccess) {
     dugks_batch_destroy(b);
     return cuda_fail(e, "dugks_batch_create");
@@ -1496,7 +1539,29 @@ int dugks_batch_step(dugks_batch* b, int nsteps) {
           e = launch_d2q9_batch(2, b->items, b->tile_start, b->nitems, b->max_ty, b->counters + 1, b->blocks, s);
         if (e != cudaSuccess) rc = cuda_fail(e, "batched launch");
       }
-      for (size_t k = 0; k < b->own.size() && rc == DUGKS_OK; ++k) rc = advance(b->own[k]);
+    }
+    // the own instances: each branch forks from the capturing stream, runs
+    // its instances' steps on its stream and joins back
+    if (rc == DUGKS_OK && !b->branches.empty()) {
+      e = cudaEventRecord(b->bevents[0], s);
+      if (e != cudaSuccess) rc = cuda_fail(e, "batch fork");
+      for (size_t q = 0; q < b->branches.size() && rc == DUGKS_OK; ++q) {
+        cudaStream_t bs = b->bstreams[q];
+        e = cudaStreamWaitEvent(bs, b->bevents[0], 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batch fork");
+        for (dugks_ctx* c : b->branches[q]) c->stream = bs;
+        for (int i = 0; i < nsteps && rc == DUGKS_OK; ++i)
+          for (dugks_ctx* c : b->branches[q]) {
+            rc = advance(c);
+            if (rc != DUGKS_OK) break;
+          }
+        for (dugks_ctx* c : b->branches[q]) c->stream = s;
+        if (rc == DUGKS_OK) {
+          e = cudaEventRecord(b->bevents[q + 1], bs);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->bevents[q + 1], 0);
+          if (e != cudaSuccess) rc = cuda_fail(e, "batch join");
+        }
+      }
     }
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
@@ -1516,6 +1581,68 @@ int dugks_batch_step(dugks_batch* b, int nsteps) {
   return DUGKS_OK;
 }
 
+int dugks_batch_autotune(dugks_batch* b, int trials, int* ty_out) {
+  if (!b) return fail(DUGKS_EINVAL, "NULL batch");
+  if (b->fused.empty()) {
+    if (ty_out) *ty_out = 0;
+    return DUGKS_OK;
+  }
+  if (trials < 1) trials = 3;
+  cudaStream_t s = b->stream;
+  // save f^ of the fused instances (their face arrays are free between steps)
+  for (dugks_ctx* c : b->fused)
+    CK(cudaMemcpyAsync(c->fbx, c->fhat, (size_t)c->p.nv * c->p.N * sizeof(double),
+                       cudaMemcpyDeviceToDevice, s));
+  cudaEvent_t ea, eb;
+  CK(cudaEventCreate(&ea));
+  CK(cudaEventCreate(&eb));
+  int best = b->max_ty;
+  float best_ms = 1e30f;
+  int rc = DUGKS_OK;
+  for (int ty = 4; ty <= d2q9_max_ty(false) && rc == DUGKS_OK; ++ty) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = batch_items(b, ty);
+    for (dugks_ctx* c : b->fused) c->g1_valid = false;
+    for (dugks_ctx* c : b->fused)
+      if (rc == DUGKS_OK && e == cudaSuccess) rc = ensure_g1(c);
+    auto step = [&] {
+      cudaError_t x = cudaMemsetAsync(b->counters, 0, 2 * sizeof(int), s);
+      if (x == cudaSuccess)
+        x = launch_d2q9_batch(1, b->items, b->tile_start, b->nitems, b->max_ty, b->counters, b->blocks, s);
+      if (x == cudaSuccess)
+        x = launch_d2q9_batch(2, b->items, b->tile_start, b->nitems, b->max_ty, b->counters + 1, b->blocks, s);
+      return x;
+    };
+    if (e == cudaSuccess && rc == DUGKS_OK) e = step();            // warm-up
+    if (e == cudaSuccess && rc == DUGKS_OK) e = cudaEventRecord(ea, s);
+    for (int i = 0; i < trials && e == cudaSuccess && rc == DUGKS_OK; ++i) e = step();
+    if (e == cudaSuccess && rc == DUGKS_OK) e = cudaEventRecord(eb, s);
+    float ms = 0.f;
+    if (e == cudaSuccess && rc == DUGKS_OK) e = cudaEventSynchronize(eb);
+    if (e == cudaSuccess && rc == DUGKS_OK) e = cudaEventElapsedTime(&ms, ea, eb);
+    if (e == cudaSuccess && rc == DUGKS_OK && ms < best_ms) {
+      best_ms = ms;
+      best = ty;
+    }
+    for (dugks_ctx* c : b->fused)                                  // restore f^
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->fhat, c->fbx, (size_t)c->p.nv * c->p.N * sizeof(double),
+                            cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess && rc == DUGKS_OK) rc = cuda_fail(e, "dugks_batch_autotune");
+  }
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  if (rc != DUGKS_OK) return rc;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = batch_items(b, best);
+  if (e != cudaSuccess) return cuda_fail(e, "dugks_batch_autotune");
+  for (dugks_ctx* c : b->fused) c->g1_valid = false;
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);    // captured with the old shape
+  b->graphs.clear();
+  if (ty_out) *ty_out = best;
+  return DUGKS_OK;
+}
+
 int dugks_batch_destroy(dugks_batch* b) {
   if (!b) return DUGKS_OK;
   cudaStreamSynchronize(b->stream);
@@ -1524,6 +1651,8 @@ int dugks_batch_destroy(dugks_batch* b) {
   if (b->items) cudaFree(b->items);
   if (b->tile_start) cudaFree(b->tile_start);
   if (b->counters) cudaFree(b->counters);
+  for (cudaEvent_t ev : b->bevents) cudaEventDestroy(ev);
+  for (cudaStream_t bs : b->bstreams) cudaStreamDestroy(bs);
   delete b;
   return DUGKS_OK;
 }

@@ -107,3 +107,71 @@ def test_batch_needs_a_stream(cuda):
     with pytest.raises(P.DugksError) as e:
         P.Batch([s])
     assert e.value.code == P.DUGKS_EINVAL
+
+
+def recipe_problem(it):
+    """Boundaries and initial fields of one instance of the seeded
+    64-instance recipe (workloads.batched_instances), as the benchmark builds
+    it: TGV (periodic) or lid cavity (bounce-back for D2Q9, diffuse for
+    Newton-Cotes), from equilibrium."""
+    N = it["N"]
+    if it["kind"] == "tgv":
+        return [(P.PERIODIC, 0, 0)] * 4, WL.tgv_fields(N, N, it["U"] * 2 * np.pi, it["RT"])
+    kw = P.BOUNCEBACK if it["vel"] == "d2q9" else P.DIFFUSE
+    return [(kw, 0, 0)] * 3 + [(kw, it["U"], 0)], WL.rest_fields(N, N)
+
+
+def recipe_solver(it, stream):
+    N = it["N"]
+    if it["vel"] == "d2q9":
+        xi, W, RT = PV.d2q9(it["RT"])
+    else:
+        xi, W, RT = PV.newton_cotes(it["nv1"], it["RT"])
+    bc, fields = recipe_problem(it)
+    s = P.Solver(N, N, 1.0 / N, 1.0 / N, xi, W, RT, it["tau"], it["dt"], bc, stream=stream)
+    s.set_equilibrium(*fields)
+    return s
+
+
+def test_batched64_recipe_matches_individual_runs_and_oracle(cuda):
+    """The full 64-instance recipe (seeded grids 32^2-512^2, D2Q9 and
+    Newton-Cotes 16^2-32^2 sets) in one batch with its tile height
+    autotuned: two batched steps equal, bit for bit, each instance stepped
+    alone, and the smallest D2Q9 and the smallest Newton-Cotes instance
+    match the FP64 oracle."""
+    torch = cuda
+    stream = torch.cuda.Stream()
+    insts = WL.config("batched64")["instances"]
+    sols = [recipe_solver(it, stream) for it in insts]
+    b = P.Batch(sols)
+    ty = b.autotune(1)
+    assert ty == 0 or 4 <= ty <= 16
+    b.step(2)
+    torch.cuda.synchronize()
+    for it, s in zip(insts, sols):
+        got = torch.empty((s.nv, s.ny, s.nx), dtype=torch.float64, device="cuda")
+        s.state(got)
+        ref = recipe_solver(it, stream)
+        ref.step(2)
+        want = torch.empty_like(got)
+        ref.state(want)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want), (it["vel"], it["N"])
+        ref.close()
+        del got, want
+    for vel in ("d2q9", "nc"):
+        i = min((k for k, it in enumerate(insts) if it["vel"] == vel), key=lambda k: insts[k]["N"])
+        it = insts[i]
+        bc, fields = recipe_problem(it)
+        if vel == "d2q9":
+            po = OV.d2q9(it["RT"])
+        else:
+            po = OV.newton_cotes_2d(it["nv1"], it["RT"])
+        N = it["N"]
+        o = O.Setup(N, N, 1.0 / N, 1.0 / N, po[0], po[1], po[2], it["tau"], it["dt"], bc)
+        fo = O.t3s3_run(O.equilibrium_state(*fields, o), o, 2)
+        fg = sols[i].state()
+        assert np.abs(fg - fo).max() <= 1e-12 * np.abs(fo).max(), (vel, N)
+    b.close()
+    for s in sols:
+        s.close()
