@@ -158,8 +158,8 @@ STATED_BOUNDS = {
         "f64dw": {"steps": 20000, "E_u_bound": 2e-10, "E_u_measured": 3.6e-11},
     },
     "rarefied128_kn1_nv64": {
-        "fp32": {"steps": 500, "E_u_bound": 5e-6, "E_u_measured": 1.2e-6},
-        "bf16": {"steps": 500, "E_u_bound": 0.3, "E_u_measured": 0.109},
+        "fp32": {"steps": 500, "E_u_bound": 2e-7, "E_u_measured": 4.6e-8},
+        "bf16": {"steps": 500, "E_u_bound": 0.3, "E_u_measured": 0.083},
     },
 }
 

@@ -446,6 +446,13 @@ int one_step_gnc(dugks_ctx* c) {
   return DUGKS_OK;
 }
 
+// rho, u of the current f^ into c->mom on the class-moment path
+int gnc_moments(dugks_ctx* c) {
+  TRY(launch(c, K_GNC_SUMS, [&] { return launch_gnc_sums(c->gn, 1, c->stream); }));
+  TRY(launch(c, K_GNC_CELLFIN, [&] { return launch_gnc_cellfin(c->gn, 1, c->stream); }));
+  return DUGKS_OK;
+}
+
 // One T2 step of size dt (Remark I, eq. feqIntD2nd_Explicit with Q7) on the
 // generic kernels: g = f-bar^{+,dt/2} from f~, faces at t_n + dt/2 with the
 // quadratic (T2S3) or first-order (T2S2) expansion, f~^{n+1} = f~^+ + dt L.
@@ -827,9 +834,16 @@ int dugks_init_ex(const dugks_mesh* mesh, const dugks_velset* vel, double tau, d
         tg = vel->xi_x[k] == vel->xi_x[(k / n) * n] && vel->xi_y[k] == vel->xi_y[k % n];
       g.tgrid = tg ? 1 : 0;
     }
-    e = gdev_prepare(storage);
-    g.nchx = gdev_chunks(p, 0, sms, storage);
-    g.nchy = gdev_chunks(p, 1, sms, storage);
+    // the FP64 generic kernels (dugks_generic_mixed.cu); the deviation forms
+    // take the class-moment kernels (below) and share this descriptor's
+    // tables and buffers
+    if (f64) {
+      e = gdev_prepare(storage);
+      g.nchx = gdev_chunks(p, 0, sms, storage);
+      g.nchy = gdev_chunks(p, 1, sms, storage);
+    } else {
+      g.nchx = g.nchy = 1;
+    }
     g.mch = nv > 32 ? 4 : 1;
     // partial moments: this path's face and cell passes and (FP64) the
     // first generic kernels share one buffer, used at different times
@@ -842,12 +856,12 @@ int dugks_init_ex(const dugks_mesh* mesh, const dugks_velset* vel, double tau, d
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->part, (size_t)pch * 3 * nfmax * sizeof(double));
     g.pitch = gdev_pitch(p.nx);
     g.plane = (size_t)(p.ny + 4) * g.pitch;
-    // The deviation forms take the staged-tile path (below), which forms the
-    // stage field and the face values on chip and moves about 28 bytes of the
-    // stored type per update: they are bound by bytes and instruction issue.
-    // FP64 storage is bound by the 2-lane FP64 pipe instead, and keeps the
-    // kernels of this file, which store g and the face values but need about
-    // 160 FP64 flops per update against about 365 for the recomputing path.
+    // The deviation forms take the class-moment path (below): one streaming
+    // pass per stage for the moments, and an update that forms g and the
+    // face values on chip, about 24 bytes of the stored type per update and
+    // bound by instruction issue.  FP64 storage is bound by the 2-lane FP64
+    // pipe instead, and keeps the kernels of dugks_generic_mixed.cu, which
+    // store g and the face values but need about 160 FP64 flops per update.
     const bool use_gnc = !f64;
     if (e == cudaSuccess && !use_gnc) e = cudaMalloc(&c->gpad, g.plane * nv * csz);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->eqp, 5 * (size_t)p.N * csz);
@@ -1182,10 +1196,11 @@ int dugks_step(dugks_ctx* c, int n) {
 
 int dugks_moments(dugks_ctx* c, double* rho, double* ux, double* uy, int on_device) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
-  // the staged-tile path keeps the state's moments from its last update in
-  // c->mom (the next step's walls read them): compute into the aside buffer
-  double* mom = c->gnc ? c->mom_aux : c->mom;
-  TRY(launch(c, K_MOMENTS, [&] {
+  // the class-moment path: the class sums of f^ and the cell finaliser of
+  // stage 1 (which the next step recomputes anyway) give rho, u in c->mom
+  double* mom = c->mom;
+  if (c->gnc) TRY(gnc_moments(c));
+  else TRY(launch(c, K_MOMENTS, [&] {
     if (c->store)
       return launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, mom, 0.0, 0.0, 0, c->stream);
     if (c->d2q9) return launch_d2q9_cell(c->dp, false, c->fhat, nullptr, mom, c->stream);
@@ -1212,8 +1227,9 @@ int dugks_check(dugks_ctx* c) {
   if (!c) return fail(DUGKS_EINVAL, "NULL context");
   cudaError_t e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
   if (e != cudaSuccess) return cuda_fail(e, "dugks_check");
-  double* mom = c->gnc ? c->mom_aux : c->mom;
-  TRY(launch(c, K_MOMENTS, [&] {
+  double* mom = c->mom;
+  if (c->gnc) TRY(gnc_moments(c));
+  else TRY(launch(c, K_MOMENTS, [&] {
     return c->store ? launch_dev_cell(c->p, c->store, c->rho0, c->fhat, nullptr, mom, 0.0, 0.0, 0, c->stream)
                     : launch_cell(c->p, c->groups, 0, c->fhat, nullptr, mom, 0.0, 0.0, c->stream);
   }));

@@ -1,10 +1,13 @@
 // Optimised generic path of the T3S3 step for any velocity set (Newton-Cotes
-// grids in particular), periodic / bounce-back / diffuse walls, in three
-// storage forms: FP64, and the FP32 / BF16 deviation forms.  Per stage:
+// grids in particular), periodic / bounce-back / diffuse walls, FP64
+// storage (the FP32 / BF16 deviation forms run on the class-moment kernels
+// of dugks_gnc.cu).  Per stage:
 //   cell pass -> ghosts -> interior faces x, y (stencils + face moments)
 //   -> face parameters -> wall faces -> update.
 //
-// Storage T and compute type C: T = double computes in FP64 (plain FP64
+// The kernels are templated on the storage type T and compute type C (the
+// deviation forms ran on them until the class-moment kernels replaced them
+// and are no longer instantiated): T = double computes in FP64 (plain FP64
 // sums; reference density rho0 = 0, so the arrays hold f itself).  T =
 // float / bf16 hold the deviation d = f - W_k rho0 and compute stencils,
 // face values, stage transforms and the per-velocity equilibrium assembly
@@ -937,8 +940,7 @@ int gdev_pitch(int nx) { return ((nx + 10 + 7) / 8) * 8; }
 // Shared-memory limits of the face kernels (the FP64 slabs exceed the
 // default 48 KiB).
 cudaError_t gdev_prepare(int store) {
-  if (store == 1) return allow_smem<float>();
-  if (store == 2) return allow_smem<__nv_bfloat16>();
+  if (store != 0) return cudaErrorInvalidValue;
   return allow_smem<double>();
 }
 
@@ -947,10 +949,8 @@ cudaError_t gdev_prepare(int store) {
 // (time ~ waves / chunks), with a small charge per chunk for the partial
 // moments that pass 2 reads back.
 int gdev_chunks(const DevParams& p, int dir, int sms, int store) {
-  int occ;
-  if (store == 1) occ = dir == 0 ? occupancy<float, 0>() : occupancy<float, 1>();
-  else if (store == 2) occ = dir == 0 ? occupancy<__nv_bfloat16, 0>() : occupancy<__nv_bfloat16, 1>();
-  else occ = dir == 0 ? occupancy<double, 0>() : occupancy<double, 1>();
+  (void)store;
+  const int occ = dir == 0 ? occupancy<double, 0>() : occupancy<double, 1>();
   const long slots = (long)occ * (sms > 0 ? sms : 1);
   const long base = (long)face_blocks_x(p, dir) * face_blocks_y(p, dir);
   const int maxc = p.nv < 64 ? p.nv : 64;
@@ -970,29 +970,22 @@ int gdev_chunks(const DevParams& p, int dir, int sms, int store) {
 cudaError_t launch_gdev_cell(const GDevStep& s, int stage, cudaStream_t st) {
   const void* src = stage == 1 ? s.fhat : s.ftp;
   const StageCoef& c = stage == 1 ? s.s1 : s.s2;
-  if (s.store == 1) return cell_t<float>(s, src, c, st);
-  if (s.store == 2) return cell_t<__nv_bfloat16>(s, src, c, st);
+  if (s.store != 0) return cudaErrorInvalidValue;
   return cell_t<double>(s, src, c, st);
 }
 
 cudaError_t launch_gdev_faces(const GDevStep& s, int stage, int dir, cudaStream_t st) {
-  if (s.store == 1)
-    return dir == 0 ? faces_t<float, 0>(s, stage, st) : faces_t<float, 1>(s, stage, st);
-  if (s.store == 2)
-    return dir == 0 ? faces_t<__nv_bfloat16, 0>(s, stage, st)
-                    : faces_t<__nv_bfloat16, 1>(s, stage, st);
+  if (s.store != 0) return cudaErrorInvalidValue;
   return dir == 0 ? faces_t<double, 0>(s, stage, st) : faces_t<double, 1>(s, stage, st);
 }
 
 cudaError_t launch_gdev_walls(const GDevStep& s, int stage, cudaStream_t st) {
-  if (s.store == 1) return walls_t<float>(s, stage, st);
-  if (s.store == 2) return walls_t<__nv_bfloat16>(s, stage, st);
+  if (s.store != 0) return cudaErrorInvalidValue;
   return walls_t<double>(s, stage, st);
 }
 
 cudaError_t launch_gdev_update(const GDevStep& s, int stage, cudaStream_t st) {
-  if (s.store == 1) return update_t<float>(s, stage, st);
-  if (s.store == 2) return update_t<__nv_bfloat16>(s, stage, st);
+  if (s.store != 0) return cudaErrorInvalidValue;
   return update_t<double>(s, stage, st);
 }
 

@@ -56,6 +56,9 @@ def test_cavity256_full_length_forms(cuda):
                              float(abs(r.sum() - r0.sum()) / r0.sum()))
             f64 = sol["fp64"].state()
             dws = float(np.abs(sol["dw"].state() - f64).max() / np.abs(f64).max())
+            print(f"cavity256 {n} steps: fp32 E(u) {got['fp32'][0]:.3e} mass {got['fp32'][1]:.3e}; "
+                  f"bf16 E(u) {got['bf16'][0]:.3e} mass {got['bf16'][1]:.3e}; "
+                  f"dw E(u) {got['dw'][0]:.3e} state {dws:.3e}")
             (e32, m32), (e16, m16), (edw, sdw) = BOUNDS[n]
             assert got["fp32"][0] <= e32 and got["fp32"][1] <= m32, (n, got["fp32"])
             assert got["bf16"][0] <= e16 and got["bf16"][1] <= m16, (n, got["bf16"])
@@ -70,8 +73,9 @@ def test_cavity256_full_length_forms(cuda):
 def test_rarefied128_kn1_500_steps_forms(cuda):
     """rarefied128 (128^2 cells, 64 x 64 Newton-Cotes, Kn 1, diffuse walls
     with a moving lid) from rest, 500 steps: FP32 and BF16 deviation forms
-    against the FP64 kernels.  Measured: FP32 E(u) 1.2e-6, mass drift
-    3.6e-12; BF16 E(u) 0.109, mass drift 3.7e-5."""
+    against the FP64 kernels.  Measured on GB300 (class-moment kernels):
+    FP32 E(u) 4.6e-8, mass drift 5.5e-11; BF16 E(u) 8.3e-2, mass drift
+    4.3e-5."""
     c = WL.config("rarefied128_kn1_nv64")
     pg = PV.newton_cotes(64, c["RT"])
     sol = {}
@@ -84,7 +88,7 @@ def test_rarefied128_kn1_500_steps_forms(cuda):
             s.step(500)
         r0, u0, v0 = sol["fp64"].moments()
         den = np.sqrt((u0 ** 2 + v0 ** 2).sum())
-        bounds = {"fp32": (5e-6, 2e-10), "bf16": (0.3, 5e-4)}
+        bounds = {"fp32": (2e-7, 2e-10), "bf16": (0.3, 5e-4)}
         for name, (eb, mb) in bounds.items():
             r, u, v = sol[name].moments()
             e = float(np.sqrt(((u - u0) ** 2 + (v - v0) ** 2).sum()) / den)
