@@ -726,11 +726,12 @@ __device__ __forceinline__ float dot9s(const float* __restrict__ T, float s00, f
 // a velocity leaving a bounce-back wall as the mirrored velocity's entry
 // plus rho_w c_k + shift_k (eq. BB in deviations).
 template <typename T, int STAGE, bool TIES>
-__global__ void __launch_bounds__(UNT, 3)
+__global__ void __launch_bounds__(UNT, 4)
 k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
   constexpr bool ASYNC = sizeof(T) == 4;       // FP32: the plane arrives by copies
   __shared__ __align__(16) float ring[NRING][RPL];
   __shared__ float rwb[NWALL];                 // wall densities of the tile's wall faces
+  __shared__ float prm[5][NST];                // equilibrium parameters of the staged cells
   const DevParams& p = s.p;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tiles = s.tiles_x * s.tiles_y;
@@ -792,7 +793,6 @@ k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
   // staging: cells (sx, sy) of the 36 x 20 plane, own cells first
   int soff[EPT], sidx[EPT];
   bool sact[EPT];
-  EqF<float> sq[EPT];
 #pragma unroll
   for (int m = 0; m < EPT; ++m) {
     int sx, sy;
@@ -812,11 +812,11 @@ k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
     if (p.py) gj = ((gj % p.ny) + p.ny) % p.ny;
     else gj = min(max(gj, 0), p.ny - 1);
     soff[m] = gj * p.nx + gi;
-    sq[m].vx = __ldg(eq + soff[m]);
-    sq[m].vy = __ldg(eq + N + soff[m]);
-    sq[m].bm1 = __ldg(eq + 2 * N + soff[m]);
-    sq[m].r = __ldg(eq + 3 * N + soff[m]);
-    sq[m].dr = __ldg(eq + 4 * N + soff[m]);
+    // each thread reads back only the entries it writes: no barrier
+    if (sact[m]) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) prm[q][sidx[m]] = __ldg(eq + (size_t)q * N + soff[m]);
+    }
   }
 
   // copies of velocity kq's inputs into ring buffer q; one commit group per
@@ -870,7 +870,13 @@ k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
       if (sact[m]) {
         const float r = ASYNC ? g[sidx[m]] : tof(raw[m]);
         if (m < RPW) own[m] = r;
-        g[sidx[m]] = fmaf(b, feq_dev<float>(sq[m], e4.x, e4.y, e4.z) - r, r);
+        EqF<float> q;
+        q.vx = prm[0][sidx[m]];
+        q.vy = prm[1][sidx[m]];
+        q.bm1 = prm[2][sidx[m]];
+        q.r = prm[3][sidx[m]];
+        q.dr = prm[4][sidx[m]];
+        g[sidx[m]] = fmaf(b, feq_dev<float>(q, e4.x, e4.y, e4.z) - r, r);
       }
     if constexpr (!ASYNC) {
 #pragma unroll
