@@ -161,6 +161,10 @@ struct dugks_batch {
   std::vector<std::vector<dugks_ctx*>> branches;
   std::vector<cudaEvent_t> bevents;
   std::vector<dugks_ctx*> fused;    // instances of the persistent D2Q9 launch
+  // class-moment instances, grouped by storage and tie flag: one batched
+  // launch per kernel and stage for each group, in a branch of its own
+  std::vector<GncBatch> gnc;
+  std::vector<cudaStream_t> gstreams;
   cudaStream_t stream = nullptr;
   D2Q9BatchItem* items = nullptr;   // device
   int* tile_start = nullptr;        // device, nitems + 1
@@ -1494,6 +1498,25 @@ int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
     else b->own.push_back(c);
   }
   cudaError_t e = cudaSuccess;
+  // class-moment instances (T3S3) run batched: one group per (storage, ties)
+  {
+    std::map<std::pair<int, int>, std::vector<const GncStep*>> groups;
+    std::vector<dugks_ctx*> rest;
+    for (dugks_ctx* c : b->own) {
+      if (c->gnc && c->scheme == DUGKS_T3S3) groups[{c->gn.store, c->gn.ties}].push_back(&c->gn);
+      else rest.push_back(c);
+    }
+    b->own = rest;
+    for (auto& kv : groups) {
+      if (e != cudaSuccess) break;
+      GncBatch gb;
+      e = gnc_batch_init(kv.second.data(), (int)kv.second.size(), gb);
+      if (e == cudaSuccess) b->gnc.push_back(gb);
+      cudaStream_t gs = nullptr;
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+      if (e == cudaSuccess) b->gstreams.push_back(gs);
+    }
+  }
   // Own instances go into up to kBranches graph branches, largest first into
   // the branch with the least work (cells x velocities), so that their
   // kernels run concurrently with each other and with the persistent launch.
@@ -1516,7 +1539,7 @@ int dugks_batch_create(dugks_ctx* const* ctxs, int n, dugks_batch** out) {
       e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
       if (e == cudaSuccess) b->bstreams.push_back(bs);
     }
-    for (int q = 0; q < nb + 1 && e == cudaSuccess; ++q) {   // fork + one join per branch
+    for (int q = 0; q < nb + (int)b->gnc.size() + 1 && e == cudaSuccess; ++q) {   // fork + joins
       cudaEvent_t ev = nullptr;
       e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
       if (e == cudaSuccess) b->bevents.push_back(ev);
@@ -1557,10 +1580,22 @@ int dugks_batch_step(dugks_batch* b, int nsteps) {
       }
     }
     // the own instances: each branch forks from the capturing stream, runs
-    // its instances' steps on its stream and joins back
-    if (rc == DUGKS_OK && !b->branches.empty()) {
+    // its instances' steps on its stream and joins back; a class-moment
+    // group is one branch that steps all its instances with batched launches
+    if (rc == DUGKS_OK && (!b->branches.empty() || !b->gnc.empty())) {
       e = cudaEventRecord(b->bevents[0], s);
       if (e != cudaSuccess) rc = cuda_fail(e, "batch fork");
+      for (size_t q = 0; q < b->gnc.size() && rc == DUGKS_OK; ++q) {
+        cudaStream_t gs = b->gstreams[q];
+        e = cudaStreamWaitEvent(gs, b->bevents[0], 0);
+        for (int i = 0; i < nsteps && e == cudaSuccess; ++i)
+          for (int stage = 1; stage <= 2 && e == cudaSuccess; ++stage)
+            e = launch_gnc_batch_stage(b->gnc[q], stage, gs);
+        cudaEvent_t ev = b->bevents[b->branches.size() + 1 + q];
+        if (e == cudaSuccess) e = cudaEventRecord(ev, gs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+        if (e != cudaSuccess) rc = cuda_fail(e, "batched class-moment launch");
+      }
       for (size_t q = 0; q < b->branches.size() && rc == DUGKS_OK; ++q) {
         cudaStream_t bs = b->bstreams[q];
         e = cudaStreamWaitEvent(bs, b->bevents[0], 0);
@@ -1669,6 +1704,8 @@ int dugks_batch_destroy(dugks_batch* b) {
   if (b->counters) cudaFree(b->counters);
   for (cudaEvent_t ev : b->bevents) cudaEventDestroy(ev);
   for (cudaStream_t bs : b->bstreams) cudaStreamDestroy(bs);
+  for (GncBatch& gb : b->gnc) gnc_batch_free(gb);
+  for (cudaStream_t gs : b->gstreams) cudaStreamDestroy(gs);
   delete b;
   return DUGKS_OK;
 }

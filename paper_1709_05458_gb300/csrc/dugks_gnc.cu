@@ -97,20 +97,19 @@ __device__ __forceinline__ void split_range(const GncStep& s, int cls, int z, in
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCB)
-k_gnc_sums(GncStep s, int stage) {
+__device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int bx, int by, int bz) {
   __shared__ float4 mono[SMAXE][3];
   __shared__ int kof[SMAXE];
   const DevParams& p = s.p;
-  const int cls = blockIdx.y;
+  const int cls = by;
   int ea, eb;
-  split_range(s, cls, blockIdx.z, ea, eb);
+  split_range(s, cls, bz, ea, eb);
   const int cnt = min(eb - ea, SMAXE);
   const float4* mt = reinterpret_cast<const float4*>(s.cls_mono);
   for (int t = threadIdx.x; t < 3 * cnt; t += SCB) mono[t / 3][t % 3] = __ldg(mt + 3 * (size_t)ea + t);
   for (int t = threadIdx.x; t < cnt; t += SCB) kof[t] = __ldg(s.cls_k + ea + t);
   __syncthreads();
-  const int c = blockIdx.x * SCB + threadIdx.x;
+  const int c = bx * SCB + threadIdx.x;
   if (c >= p.N) return;
   const T* __restrict__ col = (const T*)(stage == 1 ? s.fhat : s.ftp) + c;
   Kah acc[NMONO] = {};
@@ -146,10 +145,17 @@ k_gnc_sums(GncStep s, int stage) {
 #pragma unroll
     for (int u = 0; u < SBLK; ++u) v[u] = w[u];
   }
-  double* out = s.sums + ((size_t)blockIdx.z * s.ncls + cls) * NMONO * p.N + c;
+  double* out = s.sums + ((size_t)bz * s.ncls + cls) * NMONO * p.N + c;
 #pragma unroll
   for (int t = 0; t < NMONO; ++t) out[(size_t)t * p.N] = kah_value(acc[t]);
 }
+
+template <typename T>
+__global__ void __launch_bounds__(SCB)
+k_gnc_sums(GncStep s, int stage) {
+  gnc_sums_body<T>(s, stage, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 
 // --------------------------------------------------------------- cellfin
 // nu_{m,u} = sum xi^m u(a, b) g over a class combination, from its moments
@@ -175,11 +181,10 @@ __device__ __forceinline__ void stencil_moments(const float (&mu)[NMONO], float 
 // Per cell and combination (grid y): rho, u (FP64, from the class sums),
 // with the first combination writing them into mom and the equilibrium's
 // assembly parameters into eq (FP32); nu of the combination.
-__global__ void __launch_bounds__(64)
-k_gnc_cellfin(GncStep s, int stage) {
+__device__ __forceinline__ void gnc_cellfin_body(const GncStep& s, int stage, int bx, int by) {
   const DevParams& p = s.p;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-  const int cb = blockIdx.y;                       // this thread's combination
+  const int cell = bx * 64 + threadIdx.x;
+  const int cb = by;                       // this thread's combination
   if (cell >= p.N) return;
   const size_t N = p.N;
   double r = s.ref.W, jx = s.ref.Wx, jy = s.ref.Wy;
@@ -242,6 +247,12 @@ k_gnc_cellfin(GncStep s, int stage) {
     for (int t = 0; t < NNU; ++t) o[(size_t)t * N] = nu[t];
   }
 }
+
+__global__ void __launch_bounds__(64)
+k_gnc_cellfin(GncStep s, int stage) {
+  gnc_cellfin_body(s, stage, blockIdx.x, blockIdx.y);
+}
+
 
 // ---------------------------------------------------------------- ghosts
 // A cell (ci, cj) at most one layer outside the mesh as a combination of
@@ -327,11 +338,10 @@ __device__ void face_moments(const GncStep& s, int cb, int ci, int cj, float (&M
 // assembly parameters; at a wall, the leaving velocities by the wall rule
 // and the wall density (bounce-back: the fluid cell's rho; diffuse: from the
 // incoming flux, Q15) into wrho for the walls pass.
-__global__ void __launch_bounds__(64)
-k_gnc_facefin(GncStep s, int stage) {
+__device__ __forceinline__ void gnc_facefin_body(const GncStep& s, int stage, int bx) {
   const DevParams& p = s.p;
   const int nfx = p.ny * (p.nx + 1), nfy = (p.ny + 1) * p.nx;
-  int f = blockIdx.x * blockDim.x + threadIdx.x;
+  int f = bx * 64 + threadIdx.x;
   if (f >= nfx + nfy) return;
   const bool xdir = f < nfx;
   if (!xdir) f -= nfx;
@@ -392,6 +402,12 @@ k_gnc_facefin(GncStep s, int stage) {
   if (per && a == 0) store_par(fp, nf, xdir ? f + p.nx : f + p.ny * p.nx, q);
 }
 
+__global__ void __launch_bounds__(64)
+k_gnc_facefin(GncStep s, int stage) {
+  gnc_facefin_body(s, stage, blockIdx.x);
+}
+
+
 // ----------------------------------------------------------------- walls
 
 // Wall faces: f-bar per velocity.  Block: one wall side, WSEG consecutive
@@ -412,12 +428,11 @@ constexpr int WEPT = (3 * WTW + 127) / 128;   // staged cells per thread
 __device__ __forceinline__ int wall_segments(int n) { return (n + WSEG - 1) / WSEG; }
 
 template <typename T>
-__global__ void __launch_bounds__(128)
-k_gnc_walls(GncStep s, int stage) {
+__device__ __forceinline__ void gnc_walls_body(const GncStep& s, int stage, int bx, int by) {
   __shared__ float st[2][4 * WTW];       // [depth 0 (ghost) .. 3][position]
   const DevParams& p = s.p;
   // block -> wall side and segment (walled sides only, in the order W, E, S, N)
-  int id = blockIdx.x, side = -1, seg = 0;
+  int id = bx, side = -1, seg = 0;
   for (int sd = 0; sd < 4 && side < 0; ++sd) {
     const bool xw = sd <= SIDE_E;
     if (xw ? p.px : p.py) continue;
@@ -430,7 +445,7 @@ k_gnc_walls(GncStep s, int stage) {
   const int nt = xw ? p.ny : p.nx;       // faces along the wall
   const bool tper = xw ? p.py : p.px;    // the direction along the wall is periodic
   const int t0 = seg * WSEG, t1 = min(nt, t0 + WSEG);
-  const int k0 = blockIdx.y * WCH, k1 = min(p.nv, k0 + WCH);
+  const int k0 = by * WCH, k1 = min(p.nv, k0 + WCH);
   const T* __restrict__ src = (const T*)(stage == 1 ? s.fhat : s.ftp);
   const float* __restrict__ eq = stage == 1 ? s.eqn : s.eqp;
   const float b = (float)(stage == 1 ? s.s1.b : s.s2.b);
@@ -530,6 +545,13 @@ k_gnc_walls(GncStep s, int stage) {
     }
   }
 }
+
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_gnc_walls(GncStep s, int stage) {
+  gnc_walls_body<T>(s, stage, blockIdx.x, blockIdx.y);
+}
+
 
 // ---------------------------------------------------------------- update
 // F(xi) = (x/dx)(P_E - P_W) + (y/dy)(P_N - P_S) over the faces of cell
@@ -726,16 +748,17 @@ __device__ __forceinline__ float dot9s(const float* __restrict__ T, float s00, f
 // a velocity leaving a bounce-back wall as the mirrored velocity's entry
 // plus rho_w c_k + shift_k (eq. BB in deviations).
 template <typename T, int STAGE, bool TIES>
-__global__ void __launch_bounds__(UNT, 4)
-k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
+__device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, float cB, float sP,
+                                                float sQ, float sF, int bx) {
   constexpr bool ASYNC = sizeof(T) == 4;       // FP32: the plane arrives by copies
   __shared__ __align__(16) float ring[NRING][RPL];
   __shared__ float rwb[NWALL];                 // wall densities of the tile's wall faces
-  __shared__ float prm[5][NST];                // equilibrium parameters of the staged cells
+  __shared__ float4 prm4[NST];                 // equilibrium parameters of the staged cells:
+  __shared__ float prmd[NST];                  // (u_x/RT, u_y/RT, -|u|^2/2RT, rho), rho - rho0
   const DevParams& p = s.p;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tiles = s.tiles_x * s.tiles_y;
-  const int tile = blockIdx.x % tiles, chunk = blockIdx.x / tiles;
+  const int tile = bx % tiles, chunk = bx / tiles;
   const int i0 = (tile % s.tiles_x) * TXT, j0 = (tile / s.tiles_x) * TYT;
   const int k0 = chunk * s.kc, k1 = min(p.nv, k0 + s.kc);
   if (k0 >= k1) return;                                     // uniform per block
@@ -814,8 +837,9 @@ k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
     soff[m] = gj * p.nx + gi;
     // each thread reads back only the entries it writes: no barrier
     if (sact[m]) {
-#pragma unroll
-      for (int q = 0; q < 5; ++q) prm[q][sidx[m]] = __ldg(eq + (size_t)q * N + soff[m]);
+      prm4[sidx[m]] = make_float4(__ldg(eq + soff[m]), __ldg(eq + N + soff[m]),
+                                  __ldg(eq + 2 * (size_t)N + soff[m]), __ldg(eq + 3 * (size_t)N + soff[m]));
+      prmd[sidx[m]] = __ldg(eq + 4 * (size_t)N + soff[m]);
     }
   }
 
@@ -870,12 +894,13 @@ k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
       if (sact[m]) {
         const float r = ASYNC ? g[sidx[m]] : tof(raw[m]);
         if (m < RPW) own[m] = r;
+        const float4 q4 = prm4[sidx[m]];
         EqF<float> q;
-        q.vx = prm[0][sidx[m]];
-        q.vy = prm[1][sidx[m]];
-        q.bm1 = prm[2][sidx[m]];
-        q.r = prm[3][sidx[m]];
-        q.dr = prm[4][sidx[m]];
+        q.vx = q4.x;
+        q.vy = q4.y;
+        q.bm1 = q4.z;
+        q.r = q4.w;
+        q.dr = prmd[sidx[m]];
         g[sidx[m]] = fmaf(b, feq_dev<float>(q, e4.x, e4.y, e4.z) - r, r);
       }
     if constexpr (!ASYNC) {
@@ -1013,11 +1038,85 @@ k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
   }
 }
 
+template <typename T, int STAGE, bool TIES>
+__global__ void __launch_bounds__(UNT, 4)
+k_gnc_update(GncStep s, float cA, float cB, float sP, float sQ, float sF) {
+  gnc_update_body<T, STAGE, TIES>(s, cA, cB, sP, sQ, sF, blockIdx.x);
+}
+
+
+// ------------------------------------------------------------ batched
+// The same kernels over many instances in one launch: the instances'
+// descriptors in device memory, and per kernel the prefix sum of their
+// blocks; a block finds its instance, copies the descriptor into shared
+// memory and runs the instance's block of the same body, so each instance
+// computes exactly what its own launch would.
+__device__ __forceinline__ int batch_item(const int* __restrict__ start, int n, int b) {
+  int lo = 0, hi = n;                      // start[lo] <= b < start[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(start + mid) <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int batch_enter(GncStep& ss, const GncStep* __restrict__ steps,
+                                           const int* __restrict__ start, int n) {
+  const int i = batch_item(start, n, blockIdx.x);
+  const int* a = reinterpret_cast<const int*>(steps + i);
+  int* d = reinterpret_cast<int*>(&ss);
+  for (int t = threadIdx.x; t < (int)(sizeof(GncStep) / 4); t += blockDim.x) d[t] = __ldg(a + t);
+  __syncthreads();
+  return blockIdx.x - __ldg(start + i);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCB)
+k_gnc_sums_b(const GncStep* steps, const int* start, int n, int stage) {
+  __shared__ GncStep ss;
+  const int l = batch_enter(ss, steps, start, n);
+  const int gx = (ss.p.N + SCB - 1) / SCB, gy = ss.ncls;
+  gnc_sums_body<T>(ss, stage, l % gx, (l / gx) % gy, l / (gx * gy));
+}
+__global__ void __launch_bounds__(64)
+k_gnc_cellfin_b(const GncStep* steps, const int* start, int n, int stage) {
+  __shared__ GncStep ss;
+  const int l = batch_enter(ss, steps, start, n);
+  const int gx = (ss.p.N + 63) / 64;
+  gnc_cellfin_body(ss, stage, l % gx, l / gx);
+}
+__global__ void __launch_bounds__(64)
+k_gnc_facefin_b(const GncStep* steps, const int* start, int n, int stage) {
+  __shared__ GncStep ss;
+  const int l = batch_enter(ss, steps, start, n);
+  gnc_facefin_body(ss, stage, l);
+}
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_gnc_walls_b(const GncStep* steps, const int* start, int n, int stage) {
+  __shared__ GncStep ss;
+  const int l = batch_enter(ss, steps, start, n);
+  int nseg = 0;
+  if (!ss.p.px) nseg += 2 * wall_segments(ss.p.ny);
+  if (!ss.p.py) nseg += 2 * wall_segments(ss.p.nx);
+  gnc_walls_body<T>(ss, stage, l % nseg, l / nseg);
+}
+template <typename T, int STAGE, bool TIES>
+__global__ void __launch_bounds__(UNT, 4)
+k_gnc_update_b(const GncStep* steps, const int* start, int n, const float* coef) {
+  __shared__ GncStep ss;
+  const int l = batch_enter(ss, steps, start, n);
+  const float* c = coef + (batch_item(start, n, blockIdx.x) * 2 + (STAGE - 1)) * 5;
+  gnc_update_body<T, STAGE, TIES>(ss, __ldg(c), __ldg(c + 1), __ldg(c + 2), __ldg(c + 3), __ldg(c + 4), l);
+}
+
 template <typename T>
 cudaError_t allow_gnc() {
   cudaError_t e = cudaSuccess;
   for (void* f : {(void*)k_gnc_update<T, 1, false>, (void*)k_gnc_update<T, 2, false>,
-                  (void*)k_gnc_update<T, 1, true>, (void*)k_gnc_update<T, 2, true>})
+                  (void*)k_gnc_update<T, 1, true>, (void*)k_gnc_update<T, 2, true>,
+                  (void*)k_gnc_update_b<T, 1, false>, (void*)k_gnc_update_b<T, 2, false>,
+                  (void*)k_gnc_update_b<T, 1, true>, (void*)k_gnc_update_b<T, 2, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   return e;
 }
@@ -1299,11 +1398,12 @@ cudaError_t launch_gnc_walls(const GncStep& s, int stage, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_gnc_update(const GncStep& s, int stage, cudaStream_t st) {
+// the update's coefficients of stage `stage`: cA, cB, sP, sQ, sF (see the
+// update's comment; cB, the coefficient subtracted from the base, sP or
+// sP + sQ, is formed from the values the kernel puts into S, in FP32)
+void update_coefs(const GncStep& s, int stage, float (&o)[5]) {
   const double a1 = s.s1.a, b1 = s.s1.b, dt = s.p.dt;
   const double c34 = 0.75 * s.c_om;
-  // cB: the coefficient subtracted from the base (sP, or sP + sQ), formed
-  // from the values the kernel puts into S, in FP32
   float cA = 0.f, cB, sP, sQ = 0.f, sF;
   if (stage == 1) {
     sP = (float)(1.25 * b1);
@@ -1316,6 +1416,17 @@ cudaError_t launch_gnc_update(const GncStep& s, int stage, cudaStream_t st) {
     sF = (float)(-(4.0 * dt / 7.0) * s.s2.beta);
     cB = sP + sQ;
   }
+  o[0] = cA;
+  o[1] = cB;
+  o[2] = sP;
+  o[3] = sQ;
+  o[4] = sF;
+}
+
+cudaError_t launch_gnc_update(const GncStep& s, int stage, cudaStream_t st) {
+  float cf[5];
+  update_coefs(s, stage, cf);
+  const float cA = cf[0], cB = cf[1], sP = cf[2], sQ = cf[3], sF = cf[4];
   const int n = items(s);
 #define GNC_UPD(T, ST, TI) k_gnc_update<T, ST, TI><<<n, UNT, 0, st>>>(s, cA, cB, sP, sQ, sF)
   if (s.store == 1) {
@@ -1327,6 +1438,103 @@ cudaError_t launch_gnc_update(const GncStep& s, int stage, cudaStream_t st) {
   }
 #undef GNC_UPD
   return cudaGetLastError();
+}
+
+
+// ------------------------------------------------------------ batched
+namespace {
+// blocks of each kernel for one instance: sums, cellfin, facefin, walls, update
+void batch_blocks(const GncStep& s, int (&nb)[5]) {
+  const DevParams& p = s.p;
+  nb[0] = ((p.N + SCB - 1) / SCB) * s.ncls * s.nsplit;
+  nb[1] = ((p.N + 63) / 64) * s.ncombo;
+  nb[2] = (p.ny * (p.nx + 1) + (p.ny + 1) * p.nx + 63) / 64;
+  const int nseg = (p.px ? 0 : 2 * ((p.ny + WSEG - 1) / WSEG)) + (p.py ? 0 : 2 * ((p.nx + WSEG - 1) / WSEG));
+  nb[3] = nseg * ((p.nv + WCH - 1) / WCH);
+  nb[4] = items(s);
+}
+}  // namespace
+
+cudaError_t gnc_batch_init(const GncStep* const* steps, int n, GncBatch& b) {
+  gnc_batch_free(b);
+  if (n < 1) return cudaErrorInvalidValue;
+  b.n = n;
+  b.store = steps[0]->store;
+  b.ties = steps[0]->ties;
+  std::vector<GncStep> host(n);
+  std::vector<int> start(5 * (size_t)(n + 1), 0);
+  std::vector<float> coef(10 * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    if (steps[i]->store != b.store || steps[i]->ties != b.ties) return cudaErrorInvalidValue;
+    host[i] = *steps[i];
+    int nb[5];
+    batch_blocks(host[i], nb);
+    for (int k = 0; k < 5; ++k) start[k * (size_t)(n + 1) + i + 1] = start[k * (size_t)(n + 1) + i] + nb[k];
+    for (int st = 1; st <= 2; ++st) {
+      float cf[5];
+      update_coefs(host[i], st, cf);
+      for (int q = 0; q < 5; ++q) coef[(size_t)(2 * i + st - 1) * 5 + q] = cf[q];
+    }
+  }
+  for (int k = 0; k < 5; ++k) b.total[k] = start[k * (size_t)(n + 1) + n];
+  cudaError_t e = cudaMalloc((void**)&b.steps, host.size() * sizeof(GncStep));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b.start, start.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b.coef, coef.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(b.steps, host.data(), host.size() * sizeof(GncStep), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b.start, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b.coef, coef.data(), coef.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) gnc_batch_free(b);
+  return e;
+}
+
+void gnc_batch_free(GncBatch& b) {
+  if (b.steps) cudaFree(b.steps);
+  if (b.start) cudaFree(b.start);
+  if (b.coef) cudaFree(b.coef);
+  b.steps = nullptr;
+  b.start = nullptr;
+  b.coef = nullptr;
+  b.n = 0;
+}
+
+// One stage of every instance: five launches, each over all instances.
+cudaError_t launch_gnc_batch_stage(const GncBatch& b, int stage, cudaStream_t st) {
+  const int n = b.n;
+  const int* s0 = b.start;
+  auto at = [&](int k) { return s0 + (size_t)k * (n + 1); };
+  cudaError_t e = cudaSuccess;
+  const bool f32 = b.store == 1;
+  if (b.total[0]) {
+    if (f32) k_gnc_sums_b<float><<<b.total[0], SCB, 0, st>>>(b.steps, at(0), n, stage);
+    else k_gnc_sums_b<__nv_bfloat16><<<b.total[0], SCB, 0, st>>>(b.steps, at(0), n, stage);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && b.total[1]) {
+    k_gnc_cellfin_b<<<b.total[1], 64, 0, st>>>(b.steps, at(1), n, stage);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && b.total[2]) {
+    k_gnc_facefin_b<<<b.total[2], 64, 0, st>>>(b.steps, at(2), n, stage);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && b.total[3]) {
+    if (f32) k_gnc_walls_b<float><<<b.total[3], 128, 0, st>>>(b.steps, at(3), n, stage);
+    else k_gnc_walls_b<__nv_bfloat16><<<b.total[3], 128, 0, st>>>(b.steps, at(3), n, stage);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && b.total[4]) {
+#define GNC_UPB(T, ST, TI) k_gnc_update_b<T, ST, TI><<<b.total[4], UNT, 0, st>>>(b.steps, at(4), n, b.coef)
+    if (f32) {
+      if (b.ties) { if (stage == 1) GNC_UPB(float, 1, true); else GNC_UPB(float, 2, true); }
+      else { if (stage == 1) GNC_UPB(float, 1, false); else GNC_UPB(float, 2, false); }
+    } else {
+      if (b.ties) { if (stage == 1) GNC_UPB(__nv_bfloat16, 1, true); else GNC_UPB(__nv_bfloat16, 2, true); }
+      else { if (stage == 1) GNC_UPB(__nv_bfloat16, 1, false); else GNC_UPB(__nv_bfloat16, 2, false); }
+    }
+#undef GNC_UPB
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace dugks

@@ -268,6 +268,20 @@ cudaError_t launch_gnc_facefin(const GncStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gnc_walls(const GncStep& s, int stage, cudaStream_t st);
 cudaError_t launch_gnc_update(const GncStep& s, int stage, cudaStream_t st);
 
+// Many class-moment instances (one storage type and tie flag) stepped by
+// one launch per kernel and stage: descriptors and per-kernel block
+// prefixes in device memory.
+struct GncBatch {
+  GncStep* steps = nullptr;     // device [n]
+  int* start = nullptr;         // device [5][n + 1]: blocks of sums, cellfin, facefin, walls, update
+  float* coef = nullptr;        // device [n][2][5]: the update's coefficients per stage
+  int n = 0, store = 1, ties = 0;
+  int total[5] = {};
+};
+cudaError_t gnc_batch_init(const GncStep* const* steps, int n, GncBatch& b);
+cudaError_t launch_gnc_batch_stage(const GncBatch& b, int stage, cudaStream_t st);
+void gnc_batch_free(GncBatch& b);
+
 // One instance of a batched D2Q9 FP64 launch (device memory).
 struct D2Q9BatchItem {
   D2Q9Params P;
