@@ -12,8 +12,9 @@
 // of the equilibrium deviation W_k((rho - rho0) + rho (P_k - 1)), the face
 // moments and the face equilibria, and all combinations run in FP32; the
 // cell moment sums (rho, rho u), which the collision conserves, are exact
-// (fixed point) and rounded to FP64, and the cell's 1/rho and equilibrium
-// parameters u / RT and |u|^2 / (2 RT) are FP64 (Sec. 2.2 moments;
+// (fixed point), rounded to FP64 for the stored density and once more to
+// FP32 for the cell's equilibrium parameters 1/rho, u / RT and
+// |u|^2 / (2 RT), formed in FP32 like the faces' (Sec. 2.2 moments;
 // Sec. 2.1.1 equilibrium).
 #include <cuda_bf16.h>
 
@@ -185,27 +186,6 @@ __device__ __forceinline__ void dev_feq_f(float rho, float dr, float sx, float s
   for (int k = 0; k < 9; ++k) fe[k] = M.W[k] * fmaf(r, p1[k], dr);
 }
 
-// Equilibrium deviations W_k (rho P_k - rho0) from FP64 moments: u/RT and the
-// constant part in FP64, per-velocity assembly in FP32.
-__device__ __forceinline__ void dev_feq(double rho, double drho, double sx, double sy,
-                                        const D2Q9Params& P, const MixedConst& M, float (&fe)[9]) {
-  const double rc = P.c3 * rcp64(rho);
-  const double utx = sx * rc, uty = sy * rc;
-  const double bm1 = -fma(utx, utx, uty * uty) * P.base_div;     // P - 1 at rest velocity
-  const float ux = d2f_bits(utx), uy = d2f_bits(uty), b1 = d2f_bits(bm1);
-  const float r = d2f_bits(rho), dr = d2f_bits(drho);
-  const float sp = ux + uy, sm = ux - uy;
-  float p1[9];                                                  // P_k - 1
-  p1[4] = b1;
-  const float bx = fmaf(0.5f * ux, ux, b1), by = fmaf(0.5f * uy, uy, b1);
-  const float bs = fmaf(0.5f * sp, sp, b1), bd = fmaf(0.5f * sm, sm, b1);
-  p1[7] = bx + ux; p1[1] = bx - ux;
-  p1[5] = by + uy; p1[3] = by - uy;
-  p1[8] = bs + sp; p1[0] = bs - sp;
-  p1[6] = bd + sm; p1[2] = bd - sm;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) fe[k] = M.W[k] * fmaf(r, p1[k], dr);
-}
 
 // A staged coordinate of a tile with its 2-cell halo: >= 0 the cell it holds
 // (in the domain or its periodic image); -1 a wall ghost; -2 beyond the
@@ -461,7 +441,7 @@ k_d2q9m(D2Q9Params P, D2Q9StageF S, MixedConst M, const T* __restrict__ gin,
       double rho, dr, sx, sy;
       dev_sums(ft, M, rho, dr, sx, sy);
       float fe[9];
-      dev_feq(rho, dr, sx, sy, P, M, fe);
+      dev_feq_f(d2f_bits(rho), d2f_bits(dr), d2f_bits(sx), d2f_bits(sy), M, fe);
       const float com = M.com, a2 = M.a2, b2 = M.b2;
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
@@ -476,7 +456,7 @@ k_d2q9m(D2Q9Params P, D2Q9StageF S, MixedConst M, const T* __restrict__ gin,
       double rho, dr, sx, sy;
       dev_sums(fh, M, rho, dr, sx, sy);
       float fe[9];
-      dev_feq(rho, dr, sx, sy, P, M, fe);
+      dev_feq_f(d2f_bits(rho), d2f_bits(dr), d2f_bits(sx), d2f_bits(sy), M, fe);
       const float a1 = M.a1, b1 = M.b1;
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
