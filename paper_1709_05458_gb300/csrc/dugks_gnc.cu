@@ -612,41 +612,53 @@ __device__ __forceinline__ void read9(const float* __restrict__ w, float (&T)[9]
   T[8] = __ldg(w + 8);
 }
 
-// Wall ghosts of a staged plane (reading Q16): first across x-walls on the
-// rows inside the mesh, then across y-walls on every staged column.  Uniform
-// per block: every thread calls it, syncs included.
+// g at the x-wall ghost in staged column sx, row sy, extrapolated from the
+// three cells inwards (dx = +1 west, -1 east) by the quadratic of Q16
+__device__ __forceinline__ float ghost_x(const float* __restrict__ g, int sx, int sy, int dx) {
+  const float* r = g + sy * HXT + sx;
+  return 3.f * r[dx] - 3.f * r[2 * dx] + r[3 * dx];
+}
+
+// Wall ghosts of a staged plane (reading Q16: across x on the mesh rows,
+// then across y on every column) in one pass: a corner is the
+// y-extrapolation of three x-extrapolated values, i.e. nine mesh cells, so
+// no ghost reads another and one barrier ends the pass.  Uniform per block:
+// every thread calls it.
 __device__ __forceinline__ void stage_ghosts(const DevParams& p, float* __restrict__ g, int i0,
                                              int j0, bool wx, bool wy) {
-  if (wx) {
-    const int xw = 1 - i0;                 // staged column of the west ghost (gi = -1)
-    const int xe = p.nx - i0 + 2;          // staged column of the east ghost (gi = nx)
-    for (int t = threadIdx.x; t < 2 * HYT; t += UNT) {
-      const int ey = t % HYT;
-      const int gj = j0 - 2 + ey;
-      if (!p.py && (gj < 0 || gj >= p.ny)) continue;
-      float* r = g + ey * HXT;
-      if (t < HYT) {
-        if (xw >= 0 && xw + 3 < HXT) r[xw] = 3.f * r[xw + 1] - 3.f * r[xw + 2] + r[xw + 3];
-      } else if (xe >= 3 && xe < HXT) {
-        r[xe] = 3.f * r[xe - 1] - 3.f * r[xe - 2] + r[xe - 3];
+  if (!wx && !wy) return;
+  const int t = threadIdx.x;
+  const int xw = i0 == 0 ? 1 : -64;                   // staged column of gi = -1
+  const int xe = p.nx - i0 + 2 < HXT ? p.nx - i0 + 2 : -64;    // of gi = nx
+  int idx = -1;
+  float v = 0.f;
+  if (t < 2 * HYT) {
+    const int sy = t % HYT, gj = j0 - 2 + sy;
+    const int sx = t < HYT ? xw : xe, d = t < HYT ? 1 : -1;
+    if (wx && sx >= 0 && (p.py || (gj >= 0 && gj < p.ny))) {
+      idx = sy * HXT + sx;
+      v = ghost_x(g, sx, sy, d);
+    }
+  } else if (t < 2 * HYT + 2 * HXT) {
+    const int u = t - 2 * HYT, sx = u % HXT, gi = i0 - 2 + sx;
+    const int ys = j0 == 0 ? 1 : -64, yn = p.ny - j0 + 2 < HYT ? p.ny - j0 + 2 : -64;
+    const int sy = u < HXT ? ys : yn, d = u < HXT ? 1 : -1;
+    if (wy && sy >= 0) {
+      const float* c = g + sy * HXT + sx;
+      if (p.px || (gi >= 0 && gi < p.nx)) {
+        idx = sy * HXT + sx;
+        v = 3.f * c[d * HXT] - 3.f * c[2 * d * HXT] + c[3 * d * HXT];
+      } else if ((gi == -1 || gi == p.nx) && sx + 3 * (gi < 0 ? 1 : -1) >= 0 &&
+                 sx + 3 * (gi < 0 ? 1 : -1) < HXT) {
+        const int dx = gi < 0 ? 1 : -1;
+        idx = sy * HXT + sx;
+        v = 3.f * ghost_x(g, sx, sy + d, dx) - 3.f * ghost_x(g, sx, sy + 2 * d, dx) +
+            ghost_x(g, sx, sy + 3 * d, dx);
       }
     }
-    __syncthreads();
   }
-  if (wy) {
-    const int ys = 1 - j0, yn = p.ny - j0 + 2;
-    for (int t = threadIdx.x; t < 2 * HXT; t += UNT) {
-      const int ex = t % HXT;
-      float* c = g + ex;
-      if (t < HXT) {
-        if (ys >= 0 && ys + 3 < HYT)
-          c[ys * HXT] = 3.f * c[(ys + 1) * HXT] - 3.f * c[(ys + 2) * HXT] + c[(ys + 3) * HXT];
-      } else if (yn >= 3 && yn < HYT) {
-        c[yn * HXT] = 3.f * c[(yn - 1) * HXT] - 3.f * c[(yn - 2) * HXT] + c[(yn - 3) * HXT];
-      }
-    }
-    __syncthreads();
-  }
+  if (idx >= 0) g[idx] = v;
+  __syncthreads();
 }
 
 // staged position (column, row) of halo cell h of a tile: rows 0-1, rows
@@ -666,28 +678,6 @@ __device__ __forceinline__ void halo_pos(int h, int& sx, int& sy) {
   }
 }
 
-// Update pass.  With Df = kx (fbar_E - fbar_W) + ky (fbar_N - fbar_S),
-// k = -(flux scale) alpha xi / dx (velocity table row 2), P_n and P' the
-// cell equilibria at t_n and t', F the faces' equilibria in the flux:
-//   stage 1: f~' = 5/4 g1 - 1/4 f^ + dt/3 L*
-//                = f^ + W S(xi) - sP f^ + Df,
-//            S = sP P_n + sF F, sP = 5/4 b1, sF = -(dt/3) beta1;
-//   stage 2: f^^{n+1} = 4/7 f^ - 6/7 g1 + 9/7 f~' + c34 (f~' - feq') + 4dt/7 L**
-//                = f~' + cA (f^ - f~') + W S(xi) - (sP + sQ) f~' + Df,
-//            S = sP P_n + sQ P' + sF F, cA = 4/7 - 6/7 a1, sP = -6/7 b1,
-//            sQ = -c34, sF = -(4dt/7) beta2.
-// Written around f^ (stage 1) or f~' (stage 2) with the same rounded
-// coefficient on both sides of each difference, the maps keep a uniform
-// equilibrium exact whatever the rounding of the coefficients (their exact
-// sum is one; written as a plain sum of terms an FP32 step would scale the
-// deviations by 1 + O(2^-24) every step).
-//
-// Warp w takes rows 4w .. 4w + 3 of the tile, lane l column i0 + l.  Each
-// lane forms the x-face west of each of its cells and the y-faces south of
-// them and north of the last; the east face comes from the next lane, and
-// lanes 0-3 form the east faces of the tile's last column (for lane 31).
-// One barrier per velocity plane (the planes are double-buffered), two more
-// on tiles whose halo reaches a wall.
 // Ring of per-velocity inputs of the update, NRING planes deep, filled by
 // asynchronous copies NRING - 1 planes ahead: the staged plane (FP32
 // storage; BF16 arrives through registers), the face weights, the velocity's
@@ -743,8 +733,8 @@ __device__ __forceinline__ float dot9s(const float* __restrict__ T, float s00, f
 // lanes 0-3 form the east faces of the tile's last column (for lane 31).
 // Without tie velocities the upwind side is a uniform offset of the window
 // loads; with them (TIES) every face is a 12-point stencil whose weights
-// carry both sides.  One barrier per velocity, two more on tiles whose halo
-// reaches a wall.  At a wall face the value comes from the walls pass, for
+// carry both sides.  One barrier per velocity, one more on tiles whose halo
+// reaches a wall (the ghost pass).  At a wall face the value comes from the walls pass, for
 // a velocity leaving a bounce-back wall as the mirrored velocity's entry
 // plus rho_w c_k + shift_k (eq. BB in deviations).
 template <typename T, int STAGE, bool TIES>
@@ -793,6 +783,33 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
       if (STAGE == 2) add_quad(S[m], quad(s.eqp, N, cell[m]), sQ);
     }
   }
+  // the tile's wall faces, the same for every velocity, packed in one word:
+  // bits 0-3 the rows m whose x-face west of this lane's cell is on the W or
+  // E wall, 4-8 the rows m (0..RPW) whose south face is on a y-wall, 9-13
+  // those on the north wall, 14 the tile's last east face (lanes < RPW) on
+  // the E wall, 15 a bounce-back wall, 16-23 the RB index of the lane's
+  // first x-wall row; kept in shared memory, read once per velocity on wall
+  // tiles only
+  __shared__ unsigned wbits_s[UNT];
+  unsigned wb0 = 0u;
+  if (!p.px && (i == 0 || i == p.nx)) {
+    wb0 |= (unsigned)((i == 0 ? 0 : TYT) + RPW * warp) << 16;
+#pragma unroll
+    for (int m = 0; m < RPW; ++m)
+      if (jr + m < p.ny) wb0 |= 1u << m;
+  }
+  if (!p.px && lane < RPW && i0 + TXT == p.nx && jr + lane < p.ny) wb0 |= 1u << 14;
+  if (!p.py && i < p.nx) {
+#pragma unroll
+    for (int m = 0; m <= RPW; ++m) {
+      if (jr + m == 0) wb0 |= 1u << (4 + m);
+      else if (jr + m == p.ny) wb0 |= (1u << (4 + m)) | (1u << (9 + m));
+    }
+  }
+  if ((!p.px && (p.bc_kind[SIDE_W] == BC_BOUNCEBACK || p.bc_kind[SIDE_E] == BC_BOUNCEBACK)) ||
+      (!p.py && (p.bc_kind[SIDE_S] == BC_BOUNCEBACK || p.bc_kind[SIDE_N] == BC_BOUNCEBACK)))
+    wb0 |= 1u << 15;
+  wbits_s[threadIdx.x] = wb0;
   // this thread's wall face in the ring's wall region (thread t < NWALL):
   // W row t, E row t - 16, S column t - 32, N column t - 64 of the tile
   int wside = -1, wslot = -1;
@@ -992,7 +1009,18 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
         ext = v;
       }
     }
-    if (wall_tile) {
+    const unsigned wbits = wall_tile ? wbits_s[threadIdx.x] : 0u;
+    if (wall_tile && !((wbits >> 15) & 1u)) {
+      // the walls pass's values (fluid side, or diffuse scattering)
+      const float* rb = R + RB;
+#pragma unroll
+      for (int m = 0; m < RPW; ++m)
+        if ((wbits >> m) & 1u) fx[m] = rb[(wbits >> 16) + m];
+      if ((wbits >> 14) & 1u) ext = rb[TYT + RPW * warp + lane];
+#pragma unroll
+      for (int m = 0; m <= RPW; ++m)
+        if ((wbits >> (4 + m)) & 1u) fy[m] = rb[2 * TYT + ((wbits >> (9 + m)) & 1u ? TXT : 0) + lane];
+    } else if (wall_tile) {
       // the walls pass's values; bounce-back mirrors for leaving velocities
       const float* rc = R + RC;                             // (c_k, shift_k) per side
       auto wv = [&](int t, int side, bool leaving) {
