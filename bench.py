@@ -796,6 +796,10 @@ def run_ours(args):
         hbm_extra = {"hbm_achieved_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm_peak,
                      "hbm_bytes_per_unit": BYTES_PER_UNIT[name]}
     launches = sum(v[0] for k, v in prof.items())
+    try:                                         # fused D2Q9 kernels only
+        tile_height = P.dugks_tile_height(solver.ctx)
+    except Exception:
+        tile_height = None
     line = {
         "metric": "G cell-velocity updates/s (T3S3 step)", "value": value,
         "unit": "G updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -813,6 +817,7 @@ def run_ours(args):
                    **({"Re": 1000, "Ma": 0.1} if c.get("vel") != "nc" else {"Kn": c.get("Kn")}),
                    "units_per_step": units, "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
+                   **({"tile_height": tile_height} if tile_height else {}),
                    **({"kernel_path": args.path} if args.path != "auto" else {})},
         "roofline": {"bound": bound, "kernel": name, "achieved": achieved, "peak": peak,
                      "unit": unit, "frac": achieved / peak,

@@ -309,25 +309,29 @@ double d2q9_speed(const dugks_velset* v) {
   return c;
 }
 
-// Tile height: the number of 32 x ty tiles per wave of resident blocks
-// times the work per tile (ty + 1 face rows) is minimised over ty in
-// [4, maxty]; ties go to the lower height, or with prefer_tall (the
-// issue-bound double-word kernels, which gain from the smaller halo share of
-// taller tiles; measured by dugks_autotune) to the taller one.
 // Tile height of the fused D2Q9 kernels: the height whose tiles finish
 // soonest when an SM holds b = min(occ[ty], ceil(tiles / SMs)) blocks at a
 // time (a one-wave grid is spread evenly by the launch), at a cost of ty + 1
-// face rows per tile, with 6 % credited to b >= 2 resident blocks, which
-// overlap one another's barriers and loads (measured at 256^2 and 1024^2 for
-// both arithmetics).  occ[ty]: resident blocks per SM at height ty.
-int d2q9_tile_height(int nx, int ny, int sms, int maxty, bool prefer_tall, const int* occ) {
+// face rows per tile scaled by the throughput gained from co-resident
+// blocks, which overlap one another's barriers and loads.  FP64 and
+// double-word kernels (bound by the FP64 pipe or by issue): 6 % for b >= 2
+// (measured at 256^2 and 1024^2 for both arithmetics).  FP32 / BF16
+// deviation kernels (latency-bound at 2-3 blocks): b^(-1/4), fitted to
+// heights 4..16 at 1024^2, where 7 resident blocks of height 4 ran 17 %
+// faster than 2 of height 13.  Ties go to the lower height, or with
+// prefer_tall (the issue-bound double-word kernels, which gain from the
+// smaller halo share of taller tiles) to the taller one.  occ[ty]: resident
+// blocks per SM at height ty.
+int d2q9_tile_height(int nx, int ny, int sms, int maxty, bool prefer_tall, const int* occ,
+                     bool dev_kernels) {
   int best = 8;
   double bestc = 1e300;
   for (int ty = 4; ty <= maxty; ++ty) {
     const long tiles = (long)((nx + 31) / 32) * ((ny + ty - 1) / ty);
     const long b = std::max(1L, std::min<long>(std::max(1, occ[ty]), (tiles + sms - 1) / sms));
     const long waves = (tiles + sms * b - 1) / (sms * b);
-    const double cost = (double)waves * b * (ty + 1) * (b >= 2 ? 0.94 : 1.0);
+    const double eff = dev_kernels ? std::pow((double)b, -0.25) : (b >= 2 ? 0.94 : 1.0);
+    const double cost = (double)waves * b * (ty + 1) * eff;
     if (cost < bestc - 1e-9 || (prefer_tall && cost <= bestc + 1e-9)) {
       bestc = cost;
       best = ty;
@@ -1048,13 +1052,17 @@ int dugks_init_ex(const dugks_mesh* mesh, const dugks_velset* vel, double tau, d
     q.wsym = vel->w[1] == vel->w[3] && vel->w[1] == vel->w[5] && vel->w[1] == vel->w[7] &&
              vel->w[0] == vel->w[2] && vel->w[0] == vel->w[6] && vel->w[0] == vel->w[8];
     e = d2q9_prepare(0);
+    const bool devk = storage == DUGKS_G_FP32 || storage == DUGKS_G_BF16;
+    if (e == cudaSuccess && devk) e = d2q9m_prepare();
     {
-      // occupancy of the FP64 / double-word stage kernels at each height;
-      // the deviation-storage kernels keep the one-block model
+      // resident blocks of the context's stage kernels at each height (the
+      // double-word kernels keep the one-block model)
       int occ[17];
       for (int t = 0; t <= 16; ++t)
-        occ[t] = (e == cudaSuccess && storage == DUGKS_FP64) ? d2q9_occupancy(dwa, q.wsym, t) : 1;
-      q.ty = d2q9_tile_height(p.nx, p.ny, sms, d2q9_max_ty(dwa), dwa, occ);
+        occ[t] = e != cudaSuccess ? 1
+                 : storage == DUGKS_FP64 ? d2q9_occupancy(dwa, q.wsym, t)
+                 : devk ? d2q9m_occupancy(storage == DUGKS_G_FP32 ? 1 : 2, t) : 1;
+      q.ty = d2q9_tile_height(p.nx, p.ny, sms, d2q9_max_ty(dwa), dwa, occ, devk);
     }
     for (int k = 0; k < 9; ++k) q.W[k] = vel->w[k];
     q.c3 = cd * cd / vel->RT;
@@ -1089,7 +1097,6 @@ int dugks_init_ex(const dugks_mesh* mesh, const dugks_velset* vel, double tau, d
       c->store = storage;
       d2q9_stage_to_float(c->ds1, c->df1);
       d2q9_stage_to_float(c->ds2, c->df2);
-      e = d2q9m_prepare();
     }
     if (e != cudaSuccess) {
       free_all(c);

@@ -617,6 +617,27 @@ cudaError_t d2q9m_prepare() {
   return e;
 }
 
+// Resident blocks per SM of the deviation-storage stage kernels at tile
+// height ty (the smaller of the two stages'; store 1 FP32, else BF16), after
+// d2q9m_prepare; 0 on error.
+int d2q9m_occupancy(int store, int ty) {
+  if (ty < 1 || ty > kMaxTY) return 0;
+  const int threads = TX * (ty + 1);
+  const size_t bytes = smem_bytes(ty);
+  int a = 0, b = 0;
+  cudaError_t e;
+  if (store == 1) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_d2q9m<1, float>, threads, bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_d2q9m<2, float>, threads, bytes);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_d2q9m<1, __nv_bfloat16>, threads, bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_d2q9m<2, __nv_bfloat16>, threads, bytes);
+  }
+  return e == cudaSuccess ? (a < b ? a : b) : 0;
+}
+
 cudaError_t launch_d2q9m_stage(const D2Q9Params& p, const D2Q9StageF& s, int store, int stage,
                                double rho0, const void* gin, const void* own,
                                const double* rho_in, void* out0, void* out1, double* rho_out,

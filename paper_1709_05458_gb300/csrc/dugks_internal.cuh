@@ -158,6 +158,7 @@ cudaError_t launch_dev_cell(const DevParams& p, int store, double rho0, const vo
 cudaError_t launch_dev_set_eq(const DevParams& p, int store, double rho0, const double* rho,
                               const double* ux, const double* uy, void* d, cudaStream_t st);
 cudaError_t d2q9m_prepare();
+int d2q9m_occupancy(int store, int ty);
 
 // Optimised generic path (dugks_generic_mixed.cu), any velocity set, in
 // three storage forms: store 0 = FP64 (rho0 = 0: the arrays hold f), 1 =
