@@ -506,28 +506,36 @@ __device__ __forceinline__ void gnc_walls_body(const GncStep& s, int stage, int 
         g[sidx[m]] = v;
       }
     __syncthreads();
-    // ghosts: across the x-direction first (rows inside the mesh), then y
-    for (int pass = 0; pass < 2; ++pass) {
-      const bool normal = (pass == 0) == xw;   // this pass extrapolates across the wall
-      if (normal) {
-        for (int x = threadIdx.x; x < WTW; x += 128) {
-          const int t = t0 - 3 + x;
-          if (xw && !tper && (t < 0 || t >= nt)) continue;     // corner: filled by the y pass
-          g[x] = 3.f * g[WTW + x] - 3.f * g[2 * WTW + x] + g[3 * WTW + x];
+    // ghosts (reading Q16: across x on the mesh rows, then across y) in one
+    // pass, each from mesh cells only: depth 0 across the wall at the mesh
+    // positions; where the direction along the wall has walls, depths 1-3
+    // along it beyond the strip's ends, and depth 0 there (the corner) as
+    // the nine-cell product of the two extrapolations
+    for (int q = threadIdx.x; q < WTW + 8; q += 128) {
+      int at = -1;
+      float v = 0.f;
+      if (q < WTW) {
+        const int t = t0 - 3 + q;
+        if (tper || (t >= 0 && t < nt)) {
+          at = q;
+          v = 3.f * g[WTW + q] - 3.f * g[2 * WTW + q] + g[3 * WTW + q];
         }
       } else if (!tper) {
-        for (int q = threadIdx.x; q < 8; q += 128) {
-          const int d = q & 3, lowend = q < 4;
-          if (!xw && d == 0) continue;         // the y-ghost row is formed after
-          const int xg = (lowend ? -1 : nt) - (t0 - 3);        // ghost position
-          const int s1 = lowend ? 1 : -1;
-          if (xg < 0 || xg >= WTW || xg + 3 * s1 < 0 || xg + 3 * s1 >= WTW) continue;
-          float* r = g + d * WTW;
-          r[xg] = 3.f * r[xg + s1] - 3.f * r[xg + 2 * s1] + r[xg + 3 * s1];
+        const int u = q - WTW, d = u & 3, lowend = u < 4;
+        const int xg = (lowend ? -1 : nt) - (t0 - 3);        // ghost position
+        const int s1 = lowend ? 1 : -1;
+        if (xg >= 0 && xg < WTW && xg + 3 * s1 >= 0 && xg + 3 * s1 < WTW) {
+          auto along = [&](int dd) {
+            const float* r = g + dd * WTW;
+            return 3.f * r[xg + s1] - 3.f * r[xg + 2 * s1] + r[xg + 3 * s1];
+          };
+          at = d * WTW + xg;
+          v = d > 0 ? along(d) : 3.f * along(1) - 3.f * along(2) + along(3);
         }
       }
-      __syncthreads();
+      if (at >= 0) g[at] = v;
     }
+    __syncthreads();
     if (tt < t1) {
       const float* w = s.fwt + ((size_t)(stage - 1) * p.nv + k) * WPV + 12 * set;
       float v = 0.f;
@@ -585,32 +593,11 @@ __device__ __forceinline__ void add_quad(Cubic<float>& S, const Quad<float>& q, 
   S.c[5] = fmaf(sc, q.cyy, S.c[5]);
 }
 
-__device__ __forceinline__ float dot9(const float (&T)[9], float s00, float s01, float s02,
-                                      float s10, float s11, float s12, float s20, float s21,
-                                      float s22) {
-  float v = T[0] * s00;
-  v = fmaf(T[1], s01, v);
-  v = fmaf(T[2], s02, v);
-  v = fmaf(T[3], s10, v);
-  v = fmaf(T[4], s11, v);
-  v = fmaf(T[5], s12, v);
-  v = fmaf(T[6], s20, v);
-  v = fmaf(T[7], s21, v);
-  return fmaf(T[8], s22, v);
-}
 // the 3 x 3 window of W with lower-left corner (row r, column c): rows
 // south to north, columns west to east (the order of eq. flux_DS's weights)
 #define WIN3(W, r, c)                                                                      \
   W[r][c], W[r][(c) + 1], W[r][(c) + 2], W[(r) + 1][c], W[(r) + 1][(c) + 1],                 \
       W[(r) + 1][(c) + 2], W[(r) + 2][c], W[(r) + 2][(c) + 1], W[(r) + 2][(c) + 2]
-
-__device__ __forceinline__ void read9(const float* __restrict__ w, float (&T)[9]) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(w));
-  const float4 b = __ldg(reinterpret_cast<const float4*>(w) + 1);
-  T[0] = a.x; T[1] = a.y; T[2] = a.z; T[3] = a.w;
-  T[4] = b.x; T[5] = b.y; T[6] = b.z; T[7] = b.w;
-  T[8] = __ldg(w + 8);
-}
 
 // g at the x-wall ghost in staged column sx, row sy, extrapolated from the
 // three cells inwards (dx = +1 west, -1 east) by the quadratic of Q16
