@@ -670,7 +670,7 @@ __device__ __forceinline__ void halo_pos(int h, int& sx, int& sy) {
 // storage; BF16 arrives through registers), the face weights, the velocity's
 // table rows, its bounce-back coefficients, f^ of the tile's cells (stage 2,
 // FP32) and the tile's wall-face values.  Offsets in floats, 16-byte aligned.
-constexpr int NRING = 4;
+constexpr int NRING = 4;                          // a power of two
 constexpr int NWALL = 2 * TYT + 2 * TXT;          // W rows, E rows, S columns, N columns
 constexpr int RG = 0;                             // g (source values until converted)
 constexpr int RW = RG + NST;                      // face weights (WPV)
@@ -696,6 +696,35 @@ __device__ __forceinline__ float dot9s(const float* __restrict__ T, float s00, f
   v = fmaf(T[7], s21, v);
   u = fmaf(T[8], s22, u);
   return u + v;
+}
+
+// The x- and y-face values of a lane's cells from its stencil windows
+// (window row 0, column 0 at g0): x-faces read rows 1..RPW+2, columns
+// OX..OX+2, y-faces rows OY..OY+RPW+2, columns 1..3.  The x-faces' entries
+// in columns 1..3 are the y-faces', so each is read once: 21 shared loads
+// (27 with OX = 0) instead of 39.
+template <int OX, int OY>
+__device__ __forceinline__ void window_faces(const float* __restrict__ g0, const float* Tx,
+                                             const float* Ty, float (&fx)[RPW],
+                                             float (&fy)[RPW + 1]) {
+  float Y[RPW + 3][3], X0[RPW + 2];
+#pragma unroll
+  for (int q = 0; q < RPW + 3; ++q)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Y[q][c] = g0[(q + OY) * HXT + 1 + c];
+  if (!OX) {
+#pragma unroll
+    for (int q = 0; q < RPW + 2; ++q) X0[q] = g0[(q + 1) * HXT];
+  }
+  // entry (q, c) of the x-face window
+#define XW(q, c) (OX ? Y[(q) + 1 - OY][c] : ((c) == 0 ? X0[q] : Y[(q) + 1 - OY][(c) - 1]))
+#pragma unroll
+  for (int m = 0; m < RPW; ++m)
+    fx[m] = dot9s(Tx, XW(m, 0), XW(m, 1), XW(m, 2), XW(m + 1, 0), XW(m + 1, 1), XW(m + 1, 2),
+                  XW(m + 2, 0), XW(m + 2, 1), XW(m + 2, 2));
+#undef XW
+#pragma unroll
+  for (int m = 0; m <= RPW; ++m) fy[m] = dot9s(Ty, WIN3(Y, m, 0));
 }
 
 // Update pass.  With Df = kx (fbar_E - fbar_W) + ky (fbar_N - fbar_S),
@@ -730,8 +759,10 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
   constexpr bool ASYNC = sizeof(T) == 4;       // FP32: the plane arrives by copies
   __shared__ __align__(16) float ring[NRING][RPL];
   __shared__ float rwb[NWALL];                 // wall densities of the tile's wall faces
-  __shared__ float4 prm4[NST];                 // equilibrium parameters of the staged cells:
-  __shared__ float prmd[NST];                  // (u_x/RT, u_y/RT, -|u|^2/2RT, rho), rho - rho0
+  // equilibrium of the staged cells as W (c0 + E + h E^2), E = xi . (A, B):
+  // (c0, A, B, h) = (rho - rho0 - rho |u|^2/2RT, rho u_x/RT, rho u_y/RT,
+  // 1/(2 rho)), the assembly of feq_dev regrouped around E = rho xi.u/RT
+  __shared__ float4 prm4[NST];
   const DevParams& p = s.p;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int tiles = s.tiles_x * s.tiles_y;
@@ -841,9 +872,10 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
     soff[m] = gj * p.nx + gi;
     // each thread reads back only the entries it writes: no barrier
     if (sact[m]) {
-      prm4[sidx[m]] = make_float4(__ldg(eq + soff[m]), __ldg(eq + N + soff[m]),
-                                  __ldg(eq + 2 * (size_t)N + soff[m]), __ldg(eq + 3 * (size_t)N + soff[m]));
-      prmd[sidx[m]] = __ldg(eq + 4 * (size_t)N + soff[m]);
+      const float vx = __ldg(eq + soff[m]), vy = __ldg(eq + N + soff[m]);
+      const float bm1 = __ldg(eq + 2 * (size_t)N + soff[m]), r = __ldg(eq + 3 * (size_t)N + soff[m]);
+      const float dr = __ldg(eq + 4 * (size_t)N + soff[m]);
+      prm4[sidx[m]] = make_float4(fmaf(r, bm1, dr), r * vx, r * vy, 0.5f / r);
     }
   }
 
@@ -886,7 +918,7 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
   }
 
   for (int k = k0; k < k1; ++k) {
-    float* R = ring[(k - k0) % NRING];
+    float* R = ring[(k - k0) & (NRING - 1)];
     float* g = R + RG;
     cp_wait<NRING - 2>();                                   // this thread's copies of velocity k
     // the velocity row is another thread's copy: read after the barrier,
@@ -899,13 +931,9 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
         const float r = ASYNC ? g[sidx[m]] : tof(raw[m]);
         if (m < RPW) own[m] = r;
         const float4 q4 = prm4[sidx[m]];
-        EqF<float> q;
-        q.vx = q4.x;
-        q.vy = q4.y;
-        q.bm1 = q4.z;
-        q.r = q4.w;
-        q.dr = prmd[sidx[m]];
-        g[sidx[m]] = fmaf(b, feq_dev<float>(q, e4.x, e4.y, e4.z) - r, r);
+        const float E = fmaf(e4.x, q4.y, e4.y * q4.z);
+        const float fe = e4.z * (fmaf(q4.w * E, E, E) + q4.x);
+        g[sidx[m]] = fmaf(b, fe - r, r);
       }
     if constexpr (!ASYNC) {
 #pragma unroll
@@ -922,7 +950,7 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
       const int kq = k + NRING - 1;
       const int ks = ksrc;
       if (wslot >= 0 && kq + 1 < k1) ksrc = __ldg(s.wsrc + (size_t)wside * p.nv + kq + 1);
-      issue(kq, (k - k0 + NRING - 1) % NRING, ks);
+      issue(kq, (k - k0 + NRING - 1) & (NRING - 1), ks);
     }
     stage_ghosts(p, g, i0, j0, wx, wy);
     if constexpr (ASYNC) {
