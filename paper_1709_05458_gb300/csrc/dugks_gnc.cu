@@ -105,45 +105,52 @@ __device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int b
   int ea, eb;
   split_range(s, cls, bz, ea, eb);
   const int cnt = min(eb - ea, SMAXE);
+  // the split padded to whole blocks of SBLK: padding entries read velocity
+  // 0 and carry zero monomials (pi_0 = 1 included), so they add nothing
+  const int cntp = (cnt + SBLK - 1) / SBLK * SBLK;
   const float4* mt = reinterpret_cast<const float4*>(s.cls_mono);
-  for (int t = threadIdx.x; t < 3 * cnt; t += SCB) mono[t / 3][t % 3] = __ldg(mt + 3 * (size_t)ea + t);
-  for (int t = threadIdx.x; t < cnt; t += SCB) kof[t] = __ldg(s.cls_k + ea + t);
+  for (int t = threadIdx.x; t < 3 * cntp; t += SCB)
+    mono[t / 3][t % 3] = t < 3 * cnt ? __ldg(mt + 3 * (size_t)ea + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int t = threadIdx.x; t < cntp; t += SCB) kof[t] = t < cnt ? __ldg(s.cls_k + ea + t) : 0;
   __syncthreads();
   const int c = bx * SCB + threadIdx.x;
   if (c >= p.N) return;
   const T* __restrict__ col = (const T*)(stage == 1 ? s.fhat : s.ftp) + c;
   Kah acc[NMONO] = {};
-  float v[SBLK];
-#pragma unroll
-  for (int u = 0; u < SBLK; ++u) v[u] = u < cnt ? ldv(col + (size_t)kof[u] * p.N) : 0.f;
-  for (int n = 0; n < cnt; n += SBLK) {
-    float w[SBLK];
-#pragma unroll
-    for (int u = 0; u < SBLK; ++u) {
-      const int e = n + SBLK + u;
-      w[u] = e < cnt ? ldv(col + (size_t)kof[e] * p.N) : 0.f;
-    }
+  // block n of the split, summed in FP32 and folded into the Kahan sums
+  auto add_block = [&](const float (&x)[SBLK], int n) {
     float part[NMONO] = {};
 #pragma unroll
     for (int u = 0; u < SBLK; ++u) {
-      if (n + u >= cnt) break;
-      const float x = v[u];
       const float4 m0 = mono[n + u][0], m1 = mono[n + u][1], m2 = mono[n + u][2];
-      part[0] += x;
-      part[1] = fmaf(m0.y, x, part[1]);
-      part[2] = fmaf(m0.z, x, part[2]);
-      part[3] = fmaf(m0.w, x, part[3]);
-      part[4] = fmaf(m1.x, x, part[4]);
-      part[5] = fmaf(m1.y, x, part[5]);
-      part[6] = fmaf(m1.z, x, part[6]);
-      part[7] = fmaf(m1.w, x, part[7]);
-      part[8] = fmaf(m2.x, x, part[8]);
-      part[9] = fmaf(m2.y, x, part[9]);
+      part[0] = fmaf(m0.x, x[u], part[0]);
+      part[1] = fmaf(m0.y, x[u], part[1]);
+      part[2] = fmaf(m0.z, x[u], part[2]);
+      part[3] = fmaf(m0.w, x[u], part[3]);
+      part[4] = fmaf(m1.x, x[u], part[4]);
+      part[5] = fmaf(m1.y, x[u], part[5]);
+      part[6] = fmaf(m1.z, x[u], part[6]);
+      part[7] = fmaf(m1.w, x[u], part[7]);
+      part[8] = fmaf(m2.x, x[u], part[8]);
+      part[9] = fmaf(m2.y, x[u], part[9]);
     }
 #pragma unroll
     for (int t = 0; t < NMONO; ++t) kah_add(acc[t], part[t]);
+  };
+  auto load_block = [&](float (&x)[SBLK], int n) {
 #pragma unroll
-    for (int u = 0; u < SBLK; ++u) v[u] = w[u];
+    for (int u = 0; u < SBLK; ++u) x[u] = ldv(col + (size_t)kof[n + u] * p.N);
+  };
+  // two register blocks in turn: the next block's loads are in flight while
+  // the current one is summed
+  float v[SBLK], w[SBLK];
+  if (cntp > 0) load_block(v, 0);
+  for (int n = 0; n < cntp; n += 2 * SBLK) {
+    if (n + SBLK < cntp) load_block(w, n + SBLK);
+    add_block(v, n);
+    if (n + SBLK >= cntp) break;
+    if (n + 2 * SBLK < cntp) load_block(v, n + 2 * SBLK);
+    add_block(w, n + SBLK);
   }
   double* out = s.sums + ((size_t)bz * s.ncls + cls) * NMONO * p.N + c;
 #pragma unroll
@@ -151,7 +158,7 @@ __device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int b
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCB)
+__global__ void __launch_bounds__(SCB, 3)
 k_gnc_sums(GncStep s, int stage) {
   gnc_sums_body<T>(s, stage, blockIdx.x, blockIdx.y, blockIdx.z);
 }
@@ -1114,7 +1121,7 @@ __device__ __forceinline__ int batch_enter(GncStep& ss, const GncStep* __restric
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCB)
+__global__ void __launch_bounds__(SCB, 3)
 k_gnc_sums_b(const GncStep* steps, const int* start, int n, int stage) {
   __shared__ GncStep ss;
   const int l = batch_enter(ss, steps, start, n);
