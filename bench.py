@@ -153,12 +153,12 @@ def hbm_view(prof, label, nv, nx, ny, peak_gbs):
 # from those runs on GB300): the metric's "at stated L2 error".
 STATED_BOUNDS = {
     "cavity256": {
-        "fp32": {"steps": 20000, "E_u_bound": 2e-3, "E_u_measured": 4.1e-4},
-        "bf16": {"steps": 20000, "E_u_bound": 0.6, "E_u_measured": 0.246},
+        "fp32": {"steps": 20000, "E_u_bound": 2e-3, "E_u_measured": 4.4e-4},
+        "bf16": {"steps": 20000, "E_u_bound": 0.6, "E_u_measured": 0.281},
         "f64dw": {"steps": 20000, "E_u_bound": 2e-10, "E_u_measured": 3.6e-11},
     },
     "rarefied128_kn1_nv64": {
-        "fp32": {"steps": 500, "E_u_bound": 2e-7, "E_u_measured": 4.6e-8},
+        "fp32": {"steps": 500, "E_u_bound": 2e-7, "E_u_measured": 4.9e-8},
         "bf16": {"steps": 500, "E_u_bound": 0.3, "E_u_measured": 0.083},
     },
 }
