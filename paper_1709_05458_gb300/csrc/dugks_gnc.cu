@@ -185,79 +185,97 @@ __device__ __forceinline__ void stencil_moments(const float (&mu)[NMONO], float 
   }
 }
 
-// Per cell and combination (grid y): rho, u (FP64, from the class sums),
-// with the first combination writing them into mom and the equilibrium's
-// assembly parameters into eq (FP32); nu of the combination.
-__device__ __forceinline__ void gnc_cellfin_body(const GncStep& s, int stage, int bx, int by) {
+// A block takes CFC cells with CFC threads per class combination (thread
+// t: cell t % CFC, combination t / CFC).  The cells' FP64 work is done once:
+// the first CFC threads form rho, u from the class sums (FP64), write them
+// into mom and the equilibrium's assembly parameters into eq (FP32), and
+// the equilibrium polynomial's coefficients into shared memory; all threads
+// round the class sums (added over the velocity splits in FP64) to FP32 in
+// shared memory.  Then each (cell, combination) forms nu in FP32.
+constexpr int CFC = 64;                  // cells per cellfin block
+constexpr int NCLS_MAX = 9;              // sign classes: (sign xi_x, sign xi_y)
+constexpr int NCMB_MAX = 12;             // class combinations at most
+__device__ __forceinline__ void gnc_cellfin_body(const GncStep& s, int stage, int bx) {
+  __shared__ float cs[NCLS_MAX * NMONO][CFC];   // class sums, FP32
+  __shared__ float qds[6][CFC];                 // equilibrium polynomial
   const DevParams& p = s.p;
-  const int cell = bx * 64 + threadIdx.x;
-  const int cb = by;                       // this thread's combination
-  if (cell >= p.N) return;
   const size_t N = p.N;
-  double r = s.ref.W, jx = s.ref.Wx, jy = s.ref.Wy;
-  for (int z = 0; z < s.nsplit; ++z)
-    for (int c = 0; c < s.ncls; ++c) {
-      const double* sc = s.sums + ((size_t)z * s.ncls + c) * NMONO * N + cell;
-      r += sc[0];
-      jx += sc[N];
-      jy += sc[2 * N];
-    }
-  const double ux = jx / r, uy = jy / r;
-  if (cb == 0) {
+  const int cl = threadIdx.x % CFC, cb = threadIdx.x / CFC;
+  const int cell = bx * CFC + cl;
+  const bool in = cell < p.N;
+#pragma unroll 1
+  for (int t = threadIdx.x; t < s.ncls * NMONO * CFC; t += blockDim.x) {
+    const int cm = t / CFC, q = t % CFC, ce = bx * CFC + q;
+    double v = 0.0;
+    if (ce < p.N)
+#pragma unroll 1
+      for (int z = 0; z < s.nsplit; ++z) v += s.sums[((size_t)z * s.ncls * NMONO + cm) * N + ce];
+    cs[cm][q] = (float)v;
+  }
+  if (cb == 0 && in) {
+    double r = s.ref.W, jx = s.ref.Wx, jy = s.ref.Wy;
+#pragma unroll 1
+    for (int z = 0; z < s.nsplit; ++z)
+#pragma unroll 3
+      for (int c = 0; c < s.ncls; ++c) {
+        const double* sc = s.sums + ((size_t)z * s.ncls + c) * NMONO * N + cell;
+        r += sc[0];
+        jx += sc[N];
+        jy += sc[2 * N];
+      }
+    const double ux = jx / r, uy = jy / r;
     double* mom = stage == 1 ? s.mom_n : s.mom_p;
     mom[cell] = r;
     mom[N + cell] = ux;
     mom[2 * N + cell] = uy;
     store_par(stage == 1 ? s.eqn : s.eqp, p.N, cell, eq_params_u<float>(r, ux, uy, p.inv_RT, s.ref.rho0));
+    // W_k (rho P(xi_k) - rho0) = W_k sum_q qd_q pi_q(xi_k), q over 1, x, y, xx, xy, yy
+    const double vx = ux * p.inv_RT, vy = uy * p.inv_RT;
+    qds[0][cl] = (float)((r - s.ref.rho0) - 0.5 * r * (ux * vx + uy * vy));
+    qds[1][cl] = (float)(r * vx);
+    qds[2][cl] = (float)(r * vy);
+    qds[3][cl] = (float)(0.5 * r * vx * vx);
+    qds[4][cl] = (float)(r * vx * vy);
+    qds[5][cl] = (float)(0.5 * r * vy * vy);
   }
-  // W_k (rho P(xi_k) - rho0) = W_k sum_q qd_q pi_q(xi_k), q over 1, x, y, xx, xy, yy
-  const double vx = ux * p.inv_RT, vy = uy * p.inv_RT;
-  float qd[6];
-  qd[0] = (float)((r - s.ref.rho0) - 0.5 * r * (ux * vx + uy * vy));
-  qd[1] = (float)(r * vx);
-  qd[2] = (float)(r * vy);
-  qd[3] = (float)(0.5 * r * vx * vx);
-  qd[4] = (float)(r * vx * vy);
-  qd[5] = (float)(0.5 * r * vy * vy);
+  __syncthreads();
+  if (!in || cb >= s.ncombo) return;
   const StageCoef& sc = stage == 1 ? s.s1 : s.s2;
   const float b = (float)sc.b, omb = (float)(1.0 - sc.b);
   const float hx = (float)(sc.h * p.inv_dx), hy = (float)(sc.h * p.inv_dy);
-  {
-    const GncCombo& C = s.cmb[cb];
-    float mu[NMONO];
+  const GncCombo& C = s.cmb[cb];
+  float mu[NMONO];
 #pragma unroll
-    for (int t = 0; t < NMONO; ++t) mu[t] = 0.f;
-    for (int c = 0; c < s.ncls; ++c) {
-      const float lam = C.lam[c];
-      if (lam == 0.f) continue;
+  for (int t = 0; t < NMONO; ++t) mu[t] = 0.f;
+  for (int c = 0; c < s.ncls; ++c) {
+    const float lam = C.lam[c];
+    if (lam == 0.f) continue;
 #pragma unroll
-      for (int t = 0; t < NMONO; ++t) {
-        double v = 0.0;
-        for (int z = 0; z < s.nsplit; ++z) v += s.sums[(((size_t)z * s.ncls + c) * NMONO + t) * N + cell];
-        mu[t] = fmaf(lam, (float)v, mu[t]);
-      }
-    }
-    // g = (1 - b) src + b feq: the equilibrium's part by the combination's
-    // quadrature table zc[p][q] = sum lam W_k pi_p pi_q
-    const float* z = s.zc + (size_t)cb * NMONO * 6;
-#pragma unroll
-    for (int t = 0; t < NMONO; ++t) {
-      float e = 0.f;
-#pragma unroll
-      for (int q = 0; q < 6; ++q) e = fmaf(__ldg(z + 6 * t + q), qd[q], e);
-      mu[t] = fmaf(omb, mu[t], b * e);
-    }
-    float nu[NNU];
-    stencil_moments(mu, C.a0, C.b0, hx, hy, nu);
-    float* o = s.nu + (size_t)cb * NNU * N + cell;
-#pragma unroll
-    for (int t = 0; t < NNU; ++t) o[(size_t)t * N] = nu[t];
+    for (int t = 0; t < NMONO; ++t) mu[t] = fmaf(lam, cs[c * NMONO + t][cl], mu[t]);
   }
+  // g = (1 - b) src + b feq: the equilibrium's part by the combination's
+  // quadrature table zc[p][q] = sum lam W_k pi_p pi_q
+  const float* z = s.zc + (size_t)cb * NMONO * 6;
+  float qd[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) qd[q] = qds[q][cl];
+#pragma unroll
+  for (int t = 0; t < NMONO; ++t) {
+    float e = 0.f;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) e = fmaf(__ldg(z + 6 * t + q), qd[q], e);
+    mu[t] = fmaf(omb, mu[t], b * e);
+  }
+  float nu[NNU];
+  stencil_moments(mu, C.a0, C.b0, hx, hy, nu);
+  float* o = s.nu + (size_t)cb * NNU * N + cell;
+#pragma unroll
+  for (int t = 0; t < NNU; ++t) o[(size_t)t * N] = nu[t];
 }
 
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(CFC * NCMB_MAX)
 k_gnc_cellfin(GncStep s, int stage) {
-  gnc_cellfin_body(s, stage, blockIdx.x, blockIdx.y);
+  gnc_cellfin_body(s, stage, blockIdx.x);
 }
 
 
@@ -490,6 +508,23 @@ __device__ __forceinline__ void gnc_walls_body(const GncStep& s, int stage, int 
   const int slot = (side == SIDE_W ? 0 : side == SIDE_E ? p.ny : side == SIDE_S ? 2 * p.ny
                                                                  : 2 * p.ny + p.nx) + tt;
   const double rw = tt < t1 ? s.wrho[slot] : 0.0;
+  // the block's velocities: their face weights for this side, and for
+  // diffuse scattering W_k and the wall Maxwellian's deviation from it,
+  // f_wall,k - W_k (FP64 difference, rounded once)
+  __shared__ float wts[WCH][9], wdev[WCH], wwk[WCH];
+  for (int t = threadIdx.x; t < WCH * 9; t += 128) {
+    const int q = t / 9, k = min(k0 + q, p.nv - 1);
+    wts[q][t % 9] = __ldg(s.fwt + ((size_t)(stage - 1) * p.nv + k) * WPV + 12 * set + t % 9);
+  }
+  if (threadIdx.x < WCH) {
+    const int k = min(k0 + (int)threadIdx.x, p.nv - 1);
+    const double wk = __ldg(p.w + k);
+    wdev[threadIdx.x] = (float)(__ldg(p.feq_wall + (size_t)side * p.nv + k) - wk);
+    wwk[threadIdx.x] = (float)wk;
+  }
+  // diffuse leaving values rho_w f_wall,k - W_k rho0 = W_k (rho_w - rho0) +
+  // rho_w (f_wall,k - W_k): FP32 terms of the result's own size
+  const float rwf = (float)rw, drw = (float)(rw - s.ref.rho0);
   T raw[WCH][WEPT];
 #pragma unroll
   for (int q = 0; q < WCH; ++q)
@@ -544,18 +579,17 @@ __device__ __forceinline__ void gnc_walls_body(const GncStep& s, int stage, int 
     }
     __syncthreads();
     if (tt < t1) {
-      const float* w = s.fwt + ((size_t)(stage - 1) * p.nv + k) * WPV + 12 * set;
+      const float* w = wts[kq];
       float v = 0.f;
 #pragma unroll
       for (int t = 0; t < 9; ++t) {
         const int dy = t / 3 - 1, dx = t % 3 - 1;
         const int d = side == SIDE_W ? dx + 1 : side == SIDE_E ? 1 - dx : side == SIDE_S ? dy + 1 : 1 - dy;
         const int q = xw ? dy : dx;
-        v = fmaf(__ldg(w + t), g[d * WTW + (tt + q - t0 + 3)], v);
+        v = fmaf(w[t], g[d * WTW + (tt + q - t0 + 3)], v);
       }
       const float xn = side == SIDE_W ? -e4.x : side == SIDE_E ? e4.x : side == SIDE_S ? -e4.y : e4.y;
-      if (xn < 0.f && p.bc_kind[side] == BC_DIFFUSE)
-        v = (float)fma(rw, __ldg(p.feq_wall + (size_t)side * p.nv + k), -__ldg(p.w + k) * s.ref.rho0);
+      if (xn < 0.f && p.bc_kind[side] == BC_DIFFUSE) v = fmaf(rwf, wdev[kq], drw * wwk[kq]);
       s.wf[(size_t)k * s.nw + slot] = v;
     }
   }
@@ -1128,12 +1162,11 @@ k_gnc_sums_b(const GncStep* steps, const int* start, int n, int stage) {
   const int gx = (ss.p.N + SCB - 1) / SCB, gy = ss.ncls;
   gnc_sums_body<T>(ss, stage, l % gx, (l / gx) % gy, l / (gx * gy));
 }
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(CFC * NCMB_MAX)
 k_gnc_cellfin_b(const GncStep* steps, const int* start, int n, int stage) {
   __shared__ GncStep ss;
   const int l = batch_enter(ss, steps, start, n);
-  const int gx = (ss.p.N + 63) / 64;
-  gnc_cellfin_body(ss, stage, l % gx, l / gx);
+  gnc_cellfin_body(ss, stage, l);
 }
 __global__ void __launch_bounds__(64)
 k_gnc_facefin_b(const GncStep* steps, const int* start, int n, int stage) {
@@ -1428,7 +1461,7 @@ cudaError_t launch_gnc_sums(const GncStep& s, int stage, cudaStream_t st) {
 }
 
 cudaError_t launch_gnc_cellfin(const GncStep& s, int stage, cudaStream_t st) {
-  k_gnc_cellfin<<<dim3((s.p.N + 63) / 64, s.ncombo), 64, 0, st>>>(s, stage);
+  k_gnc_cellfin<<<(s.p.N + CFC - 1) / CFC, CFC * s.ncombo, 0, st>>>(s, stage);
   return cudaGetLastError();
 }
 
@@ -1497,7 +1530,7 @@ namespace {
 void batch_blocks(const GncStep& s, int (&nb)[5]) {
   const DevParams& p = s.p;
   nb[0] = ((p.N + SCB - 1) / SCB) * s.ncls * s.nsplit;
-  nb[1] = ((p.N + 63) / 64) * s.ncombo;
+  nb[1] = (p.N + CFC - 1) / CFC;
   nb[2] = (p.ny * (p.nx + 1) + (p.ny + 1) * p.nx + 63) / 64;
   const int nseg = (p.px ? 0 : 2 * ((p.ny + WSEG - 1) / WSEG)) + (p.py ? 0 : 2 * ((p.nx + WSEG - 1) / WSEG));
   nb[3] = nseg * ((p.nv + WCH - 1) / WCH);
@@ -1509,6 +1542,7 @@ cudaError_t gnc_batch_init(const GncStep* const* steps, int n, GncBatch& b) {
   gnc_batch_free(b);
   if (n < 1) return cudaErrorInvalidValue;
   b.n = n;
+  b.ncombo_max = 1;
   b.store = steps[0]->store;
   b.ties = steps[0]->ties;
   std::vector<GncStep> host(n);
@@ -1517,6 +1551,7 @@ cudaError_t gnc_batch_init(const GncStep* const* steps, int n, GncBatch& b) {
   for (int i = 0; i < n; ++i) {
     if (steps[i]->store != b.store || steps[i]->ties != b.ties) return cudaErrorInvalidValue;
     host[i] = *steps[i];
+    b.ncombo_max = std::max(b.ncombo_max, host[i].ncombo);
     int nb[5];
     batch_blocks(host[i], nb);
     for (int k = 0; k < 5; ++k) start[k * (size_t)(n + 1) + i + 1] = start[k * (size_t)(n + 1) + i] + nb[k];
@@ -1560,7 +1595,7 @@ cudaError_t launch_gnc_batch_stage(const GncBatch& b, int stage, cudaStream_t st
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && b.total[1]) {
-    k_gnc_cellfin_b<<<b.total[1], 64, 0, st>>>(b.steps, at(1), n, stage);
+    k_gnc_cellfin_b<<<b.total[1], CFC * b.ncombo_max, 0, st>>>(b.steps, at(1), n, stage);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && b.total[2]) {

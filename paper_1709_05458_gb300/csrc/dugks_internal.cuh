@@ -277,6 +277,7 @@ struct GncBatch {
   int* start = nullptr;         // device [5][n + 1]: blocks of sums, cellfin, facefin, walls, update
   float* coef = nullptr;        // device [n][2][5]: the update's coefficients per stage
   int n = 0, store = 1, ties = 0;
+  int ncombo_max = 1;           // the instances' largest class-combination count
   int total[5] = {};
 };
 cudaError_t gnc_batch_init(const GncStep* const* steps, int n, GncBatch& b);
