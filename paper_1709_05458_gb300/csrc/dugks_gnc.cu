@@ -203,7 +203,7 @@ __device__ __forceinline__ void gnc_cellfin_body(const GncStep& s, int stage, in
   const int cl = threadIdx.x % CFC, cb = threadIdx.x / CFC;
   const int cell = bx * CFC + cl;
   const bool in = cell < p.N;
-#pragma unroll 1
+#pragma unroll 4
   for (int t = threadIdx.x; t < s.ncls * NMONO * CFC; t += blockDim.x) {
     const int cm = t / CFC, q = t % CFC, ce = bx * CFC + q;
     double v = 0.0;
@@ -332,17 +332,26 @@ __device__ void face_moments(const GncStep& s, int cb, int ci, int cj, float (&M
   M[0] = M[1] = M[2] = 0.f;
   const bool inside = ci >= 1 && ci + 1 < p.nx && cj >= 1 && cj + 1 < p.ny;
   const size_t plane = (size_t)6 * p.N;            // from nu_{m,u} to nu_{m+1,u}
+  if (inside) {
+    // five terms' loads in flight at a time
+#pragma unroll 5
+    for (int q = 0; q < s.ntl; ++q) {
+      const int t = s.tl_s[q], u = s.tl_u[q];
+      const float w = s.tl_w[q];
+      const float* b = base + (size_t)u * p.N;
+      const int c = (cj + t / 3 - 1) * p.nx + ci + t % 3 - 1;
+      M[0] = fmaf(w, __ldg(b + c), M[0]);
+      M[1] = fmaf(w, __ldg(b + plane + c), M[1]);
+      M[2] = fmaf(w, __ldg(b + 2 * plane + c), M[2]);
+    }
+    return;
+  }
 #pragma unroll 1
   for (int q = 0; q < s.ntl; ++q) {
     const int t = s.tl_s[q], u = s.tl_u[q];
     const float w = s.tl_w[q];
     const float* b = base + (size_t)u * p.N;
-    if (inside) {
-      const int c = (cj + t / 3 - 1) * p.nx + ci + t % 3 - 1;
-      M[0] = fmaf(w, __ldg(b + c), M[0]);
-      M[1] = fmaf(w, __ldg(b + plane + c), M[1]);
-      M[2] = fmaf(w, __ldg(b + 2 * plane + c), M[2]);
-    } else {
+    {
       int idx[9];
       float co[9];
       const int n = ghost_terms(p, ci + t % 3 - 1, cj + t / 3 - 1, idx, co);
