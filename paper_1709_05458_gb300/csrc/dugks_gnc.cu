@@ -659,8 +659,8 @@ __device__ __forceinline__ float ghost_x(const float* __restrict__ g, int sx, in
 // Wall ghosts of a staged plane (reading Q16: across x on the mesh rows,
 // then across y on every column) in one pass: a corner is the
 // y-extrapolation of three x-extrapolated values, i.e. nine mesh cells, so
-// no ghost reads another and one barrier ends the pass.  Uniform per block:
-// every thread calls it.
+// no ghost reads another; the caller's barrier ends the pass (one for
+// several planes).
 __device__ __forceinline__ void stage_ghosts(const DevParams& p, float* __restrict__ g, int i0,
                                              int j0, bool wx, bool wy) {
   if (!wx && !wy) return;
@@ -695,7 +695,6 @@ __device__ __forceinline__ void stage_ghosts(const DevParams& p, float* __restri
     }
   }
   if (idx >= 0) g[idx] = v;
-  __syncthreads();
 }
 
 // staged position (column, row) of halo cell h of a tile: rows 0-1, rows
@@ -799,8 +798,9 @@ __device__ __forceinline__ void window_faces(const float* __restrict__ g0, const
 // lanes 0-3 form the east faces of the tile's last column (for lane 31).
 // Without tie velocities the upwind side is a uniform offset of the window
 // loads; with them (TIES) every face is a 12-point stencil whose weights
-// carry both sides.  One barrier per velocity, one more on tiles whose halo
-// reaches a wall (the ghost pass).  At a wall face the value comes from the walls pass, for
+// carry both sides.  FP32: one barrier per two velocities (both planes
+// converted before it, both planes' faces after it); BF16: one per velocity;
+// one more on tiles whose halo reaches a wall (the ghost pass).  At a wall face the value comes from the walls pass, for
 // a velocity leaving a bounce-back wall as the mirrored velocity's entry
 // plus rho_w c_k + shift_k (eq. BB in deviations).
 template <typename T, int STAGE, bool TIES>
@@ -930,9 +930,11 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
   }
 
   // copies of velocity kq's inputs into ring buffer q; one commit group per
-  // plane, also when empty, so the group count stays uniform
-  int ksrc = 0;                                   // wall value's source velocity for the next issue
-  if (wslot >= 0 && k0 + NRING - 1 < k1) ksrc = __ldg(s.wsrc + (size_t)wside * p.nv + k0 + NRING - 1);
+  // plane, also when empty, so the group count stays uniform.  FP32: the
+  // planes go in pairs, one barrier for two (AHEAD = 2 planes in flight);
+  // BF16 (values through registers): one plane per barrier, three ahead.
+  constexpr int PAIR = ASYNC ? 2 : 1;
+  constexpr int AHEAD = NRING - PAIR;
   auto issue = [&](int kq, int q, int ks) {
     if (kq < k1) {
       float* R = ring[q];
@@ -955,11 +957,14 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
     }
     cp_commit();
   };
+  auto wall_src = [&](int kq) {                   // wall value's source velocity
+    return wslot >= 0 && kq < k1 ? __ldg(s.wsrc + (size_t)wside * p.nv + kq) : 0;
+  };
+  int ksrc[PAIR];                                 // for the next iteration's issues
 #pragma unroll
-  for (int q = 0; q < NRING - 1; ++q) {
-    const int ks = wslot >= 0 && k0 + q < k1 ? __ldg(s.wsrc + (size_t)wside * p.nv + k0 + q) : 0;
-    issue(k0 + q, q, ks);
-  }
+  for (int h = 0; h < PAIR; ++h) ksrc[h] = wall_src(k0 + AHEAD + h);
+#pragma unroll
+  for (int q = 0; q < AHEAD; ++q) issue(k0 + q, q, wall_src(k0 + q));
   T raw[EPT];
   if constexpr (!ASYNC) {
 #pragma unroll
@@ -967,47 +972,11 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
       if (sact[m]) raw[m] = ldr(src + (size_t)k0 * N + soff[m]);
   }
 
-  for (int k = k0; k < k1; ++k) {
-    float* R = ring[(k - k0) & (NRING - 1)];
-    float* g = R + RG;
-    cp_wait<NRING - 2>();                                   // this thread's copies of velocity k
-    // the velocity row is another thread's copy: read after the barrier,
-    // except xi and W for the conversion, which come from the table
-    const float4 e4 = ld4(vq + p.nv + k);
-    float own[RPW], fown[RPW];
-#pragma unroll
-    for (int m = 0; m < EPT; ++m)
-      if (sact[m]) {
-        const float r = ASYNC ? g[sidx[m]] : tof(raw[m]);
-        if (m < RPW) own[m] = r;
-        const float4 q4 = prm4[sidx[m]];
-        const float E = fmaf(e4.x, q4.y, e4.y * q4.z);
-        const float fe = e4.z * (fmaf(q4.w * E, E, E) + q4.x);
-        g[sidx[m]] = fmaf(b, fe - r, r);
-      }
-    if constexpr (!ASYNC) {
-#pragma unroll
-      for (int m = 0; m < RPW; ++m) fown[m] = (STAGE == 2 && ok[m]) ? lds(fh + (size_t)k * N + cell[m]) : 0.f;
-      if (k + 1 < k1) {
-#pragma unroll
-        for (int m = 0; m < EPT; ++m)
-          if (sact[m]) raw[m] = ldr(src + (size_t)(k + 1) * N + soff[m]);
-      }
-    }
-    __syncthreads();
-    // the ring buffer of velocity k - 1 is free once every thread is here
-    {
-      const int kq = k + NRING - 1;
-      const int ks = ksrc;
-      if (wslot >= 0 && kq + 1 < k1) ksrc = __ldg(s.wsrc + (size_t)wside * p.nv + kq + 1);
-      issue(kq, (k - k0 + NRING - 1) & (NRING - 1), ks);
-    }
-    stage_ghosts(p, g, i0, j0, wx, wy);
-    if constexpr (ASYNC) {
-#pragma unroll
-      for (int m = 0; m < RPW; ++m) fown[m] = STAGE == 2 ? R[RF + (RPW * warp + m) * TXT + lane] : 0.f;
-    }
-
+  // the faces of velocity k's plane (staged as g in ring slot R) and the
+  // update of the tile's cells from their source (own) and f^ (fown) values
+  auto plane_out = [&](int k, const float* R, const float4 e4, const float (&ownv)[RPW],
+                       const float (&fownv)[RPW]) {
+    const float* g = R + RG;
     const float* wk = R + RW;
     const int sgx = e4.x > 0.f ? 1 : (e4.x < 0.f ? -1 : 0);
     const int sgy = e4.y > 0.f ? 1 : (e4.y < 0.f ? -1 : 0);
@@ -1124,9 +1093,101 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
       const float df = fmaf(kx, fE - fx[m], ky * (fy[m + 1] - fy[m]));
       const float ws = fmaf(e4.z, cubic<float>(S[m], e4.x, e4.y), df);
       float out;
-      if (STAGE == 1) out = fmaf(-cB, own[m], own[m] + ws);                          // cB = sP
-      else out = fmaf(cA, fown[m] - own[m], fmaf(-cB, own[m], own[m] + ws));         // cB = sP + sQ
+      const float o = ownv[m];
+      if (STAGE == 1) out = fmaf(-cB, o, o + ws);                                    // cB = sP
+      else out = fmaf(cA, fownv[m] - o, fmaf(-cB, o, o + ws));                     // cB = sP + sQ
       stv(dst + (size_t)k * N + cell[m], out);
+    }
+  };
+
+  if constexpr (ASYNC) {
+    for (int kp = k0; kp < k1; kp += PAIR) {
+      const int np = min(PAIR, k1 - kp);
+      cp_wait<AHEAD - PAIR>();                                // this thread's copies of the pair
+      float own[PAIR][RPW], fown[PAIR][RPW];
+#pragma unroll
+      for (int h = 0; h < PAIR; ++h) {
+        if (h >= np) break;
+        const int k = kp + h;
+        float* g = ring[(k - k0) & (NRING - 1)] + RG;
+        // the velocity row is another thread's copy: read after the barrier,
+        // except xi and W for the conversion, which come from the table
+        const float4 e4 = ld4(vq + p.nv + k);
+#pragma unroll
+        for (int m = 0; m < EPT; ++m)
+          if (sact[m]) {
+            const float r = g[sidx[m]];
+            if (m < RPW) own[h][m] = r;
+            const float4 q4 = prm4[sidx[m]];
+            const float E = fmaf(e4.x, q4.y, e4.y * q4.z);
+            const float fe = e4.z * (fmaf(q4.w * E, E, E) + q4.x);
+            g[sidx[m]] = fmaf(b, fe - r, r);
+          }
+      }
+      __syncthreads();
+      // the ring buffers of the previous pair are free once every thread is here
+#pragma unroll
+      for (int h = 0; h < PAIR; ++h) {
+        const int kq = kp + AHEAD + h;
+        const int ks = ksrc[h];
+        ksrc[h] = wall_src(kq + PAIR);
+        issue(kq, (kq - k0) & (NRING - 1), ks);
+      }
+      if (wx || wy) {
+#pragma unroll
+        for (int h = 0; h < PAIR; ++h)
+          if (h < np) stage_ghosts(p, ring[(kp + h - k0) & (NRING - 1)] + RG, i0, j0, wx, wy);
+        __syncthreads();
+      }
+#pragma unroll
+      for (int h = 0; h < PAIR; ++h) {
+        if (h >= np) break;
+        const int k = kp + h;
+        const float* R = ring[(k - k0) & (NRING - 1)];
+#pragma unroll
+        for (int m = 0; m < RPW; ++m) fown[h][m] = STAGE == 2 ? R[RF + (RPW * warp + m) * TXT + lane] : 0.f;
+        plane_out(k, R, ld4(vq + p.nv + k), own[h], fown[h]);
+      }
+    }
+  } else {
+    for (int k = k0; k < k1; ++k) {
+      float* R = ring[(k - k0) & (NRING - 1)];
+      float* g = R + RG;
+      cp_wait<NRING - 2>();                                   // this thread's copies of velocity k
+      // the velocity row is another thread's copy: read after the barrier,
+      // except xi and W for the conversion, which come from the table
+      const float4 e4 = ld4(vq + p.nv + k);
+      float own[RPW], fown[RPW];
+#pragma unroll
+      for (int m = 0; m < EPT; ++m)
+        if (sact[m]) {
+          const float r = tof(raw[m]);
+          if (m < RPW) own[m] = r;
+          const float4 q4 = prm4[sidx[m]];
+          const float E = fmaf(e4.x, q4.y, e4.y * q4.z);
+          const float fe = e4.z * (fmaf(q4.w * E, E, E) + q4.x);
+          g[sidx[m]] = fmaf(b, fe - r, r);
+        }
+#pragma unroll
+      for (int m = 0; m < RPW; ++m) fown[m] = (STAGE == 2 && ok[m]) ? lds(fh + (size_t)k * N + cell[m]) : 0.f;
+      if (k + 1 < k1) {
+#pragma unroll
+        for (int m = 0; m < EPT; ++m)
+          if (sact[m]) raw[m] = ldr(src + (size_t)(k + 1) * N + soff[m]);
+      }
+      __syncthreads();
+      // the ring buffer of velocity k - 1 is free once every thread is here
+      {
+        const int kq = k + AHEAD;
+        const int ks = ksrc[0];
+        ksrc[0] = wall_src(kq + 1);
+        issue(kq, (kq - k0) & (NRING - 1), ks);
+      }
+      if (wx || wy) {
+        stage_ghosts(p, g, i0, j0, wx, wy);
+        __syncthreads();
+      }
+      plane_out(k, R, e4, own, fown);
     }
   }
 }
