@@ -685,10 +685,11 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: upload f^ from pinned
     # host memory, one step, read the moments back, every step
     f_host = torch.empty((nv, c["ny"], c["nx"]), dtype=torch.float64).pin_memory()
-    mom_host = [torch.empty((c["ny"], c["nx"]), dtype=torch.float64).pin_memory() for _ in range(3)]
+    # rho, ux, uy as the three planes of one pinned buffer: one read-back copy
+    mom_host = torch.empty((3, c["ny"], c["nx"]), dtype=torch.float64).pin_memory()
     P.dugks_get_state(solver.ctx, f_host.numpy())
     fh = f_host.numpy()
-    mh = [m.numpy() for m in mom_host]
+    mh = list(mom_host.numpy())
     for _ in range(0 if args.no_e2e else 2):
         P.dugks_set_state(solver.ctx, fh)
         solver.step(1)

@@ -179,7 +179,9 @@ int dugks_step(dugks_ctx* ctx, int n);
 
 /* dugks_moments -- rho = sum_k f_k, (ux, uy) = sum_k xi_k f_k / rho of the
  * current state (Sec. 2.2; the moments of f^ equal those of f because the
- * collision conserves them).  Any output pointer may be NULL.  With
+ * collision conserves them).  Each output is [ny][nx] FP64; any output
+ * pointer may be NULL.  When ux = rho + nx*ny and uy = rho + 2*nx*ny (one
+ * [3][ny][nx] buffer) the three arrays arrive in a single copy.  With
  * on_device = 0 the call waits for the context's stream. */
 int dugks_moments(dugks_ctx* ctx, double* rho, double* ux, double* uy, int on_device);
 

@@ -1217,15 +1217,20 @@ int dugks_moments(dugks_ctx* c, double* rho, double* ux, double* uy, int on_devi
     if (c->d2q9) return launch_d2q9_cell(c->dp, false, c->fhat, nullptr, mom, c->stream);
     return launch_cell(c->p, c->groups, 0, c->fhat, nullptr, mom, 0.0, 0.0, c->stream);
   }));
-  // the three copies are queued on the stream; one synchronisation for host buffers
+  // the copies are queued on the stream; one synchronisation for host buffers.
+  // rho, ux, uy consecutive in one buffer (the layout of mom): one copy
   const size_t N = c->p.N;
   double* dst[3] = {rho, ux, uy};
-  for (int m = 0; m < 3; ++m) {
-    if (!dst[m]) continue;
-    cudaError_t e = cudaMemcpyAsync(dst[m], mom + m * N, N * sizeof(double),
-                                    on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                    c->stream);
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (rho && ux == rho + N && uy == rho + 2 * N) {
+    cudaError_t e = cudaMemcpyAsync(rho, mom, 3 * N * sizeof(double), kind, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "copy from device");
+  } else {
+    for (int m = 0; m < 3; ++m) {
+      if (!dst[m]) continue;
+      cudaError_t e = cudaMemcpyAsync(dst[m], mom + m * N, N * sizeof(double), kind, c->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "copy from device");
+    }
   }
   if (!on_device) {
     cudaError_t e = cudaStreamSynchronize(c->stream);

@@ -183,6 +183,36 @@ def test_device_pointer_path(cuda):
     assert np.abs(rho.cpu().numpy() - fo.sum(axis=0)).max() <= 1e-12
 
 
+def test_moments_into_one_buffer(cuda):
+    """rho, ux, uy as the three planes of one [3][ny][nx] buffer (read back in
+    one copy) equal the three separate arrays, on the host and on the device,
+    and the oracle's moments (Sec. 2.2)."""
+    torch = cuda
+    xi, W, RT = PV.d2q9(1 / 3)
+    nx, ny = 37, 21
+    bc = [(P.BOUNCEBACK, 0, 0)] * 3 + [(P.BOUNCEBACK, 0.05, 0)]
+    g = P.Solver(nx, ny, 1 / nx, 1 / ny, xi, W, RT, 0.01, 0.02, bc)
+    f0 = WL.near_equilibrium_state(W, ny, nx, amp=0.2, seed=6)
+    g.set_state(f0)
+    g.step(2)
+    r, u, v = g.moments()
+    packed = np.empty((3, ny, nx))
+    P.dugks_moments(g.ctx, packed[0], packed[1], packed[2])
+    for a, b in zip(packed, (r, u, v)):
+        np.testing.assert_array_equal(a, b)
+    dev = torch.empty((3, ny, nx), dtype=torch.float64, device="cuda")
+    P.dugks_moments(g.ctx, dev[0], dev[1], dev[2])
+    g.synchronize()
+    np.testing.assert_array_equal(dev.cpu().numpy(), packed)
+    po = OV.d2q9(1 / 3)
+    o = O.Setup(nx, ny, 1 / nx, 1 / ny, po[0], po[1], po[2], 0.01, 0.02, bc)
+    fo = O.t3s3_run(f0, o, 2)
+    ro, uo, vo = O.velocity(fo, o)
+    assert np.abs(r - fo.sum(axis=0)).max() <= 1e-12
+    assert max(np.abs(u - uo).max(), np.abs(v - vo).max()) <= 1e-11
+    g.close()
+
+
 def test_zero_steps_and_state_roundtrip(cuda):
     xi, W, RT = PV.d2q9(1 / 3)
     g = P.Solver(5, 4, .2, .25, xi, W, RT, 0.1, 0.1, PER)
