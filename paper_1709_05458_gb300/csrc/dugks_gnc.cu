@@ -117,25 +117,32 @@ __device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int b
   if (c >= p.N) return;
   const T* __restrict__ col = (const T*)(stage == 1 ? s.fhat : s.ftp) + c;
   Kah acc[NMONO] = {};
-  // block n of the split, summed in FP32 and folded into the Kahan sums
+  // block n of the split, summed in FP32 and folded into the Kahan sums.
+  // The ten products of a value go as five packed pairs (one fma.rn.f32x2
+  // is two FP32 fused multiply-adds, each rounded as fmaf): monomials
+  // (pi_0, pi_1) .. (pi_8, pi_9) against (x, x)
   auto add_block = [&](const float (&x)[SBLK], int n) {
-    float part[NMONO] = {};
+    unsigned long long part[NMONO / 2] = {};
 #pragma unroll
     for (int u = 0; u < SBLK; ++u) {
-      const float4 m0 = mono[n + u][0], m1 = mono[n + u][1], m2 = mono[n + u][2];
-      part[0] = fmaf(m0.x, x[u], part[0]);
-      part[1] = fmaf(m0.y, x[u], part[1]);
-      part[2] = fmaf(m0.z, x[u], part[2]);
-      part[3] = fmaf(m0.w, x[u], part[3]);
-      part[4] = fmaf(m1.x, x[u], part[4]);
-      part[5] = fmaf(m1.y, x[u], part[5]);
-      part[6] = fmaf(m1.z, x[u], part[6]);
-      part[7] = fmaf(m1.w, x[u], part[7]);
-      part[8] = fmaf(m2.x, x[u], part[8]);
-      part[9] = fmaf(m2.y, x[u], part[9]);
+      const ulonglong2 m0 = *reinterpret_cast<const ulonglong2*>(&mono[n + u][0]);
+      const ulonglong2 m1 = *reinterpret_cast<const ulonglong2*>(&mono[n + u][1]);
+      const unsigned long long m2 = *reinterpret_cast<const unsigned long long*>(&mono[n + u][2]);
+      unsigned long long xx;
+      asm("mov.b64 %0, {%1, %1};" : "=l"(xx) : "f"(x[u]));
+      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(part[0]) : "l"(m0.x), "l"(xx));
+      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(part[1]) : "l"(m0.y), "l"(xx));
+      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(part[2]) : "l"(m1.x), "l"(xx));
+      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(part[3]) : "l"(m1.y), "l"(xx));
+      asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(part[4]) : "l"(m2), "l"(xx));
     }
 #pragma unroll
-    for (int t = 0; t < NMONO; ++t) kah_add(acc[t], part[t]);
+    for (int t = 0; t < NMONO / 2; ++t) {
+      float lo, hi;
+      asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(part[t]));
+      kah_add(acc[2 * t], lo);
+      kah_add(acc[2 * t + 1], hi);
+    }
   };
   auto load_block = [&](float (&x)[SBLK], int n) {
 #pragma unroll
