@@ -78,6 +78,43 @@ def test_newton_cotes_deviation_forms(cuda, walls, storage):
     assert err <= b[0] and e <= b[1] and dm <= b[2], (err, e, dm)
 
 
+# (nx, ny): three-cell walls (a wall ghost's sources span the mesh), a
+# two-column last tile, ragged tiles in both directions
+TINY = [(3, 3), (3, 5), (34, 4), (33, 17)]
+TINY_BC = {
+    "mixed": [(P.BOUNCEBACK, 0, 0), (P.DIFFUSE, 0, 0), (P.DIFFUSE, 0, 0), (P.BOUNCEBACK, 0.05, 0)],
+    "xper": [(P.PERIODIC, 0, 0)] * 2 + [(P.DIFFUSE, 0, 0), (P.DIFFUSE, 0.05, 0)],
+}
+
+
+@pytest.mark.parametrize("storage", FORMS, ids=IDS)
+@pytest.mark.parametrize("nv1", [5, 6])
+@pytest.mark.parametrize("bcname", list(TINY_BC))
+@pytest.mark.parametrize("nx,ny", TINY)
+def test_class_moment_path_tiny_meshes(cuda, nx, ny, bcname, nv1, storage):
+    """The class-moment kernels on meshes of a few cells: wall ghosts whose
+    corners take all nine nearest mesh cells, tiles narrower than 32 x 16,
+    an odd (25, with tie velocities) and an even (36) velocity count (the
+    FP32 update takes the velocities in pairs), mixed wall kinds; 6 steps
+    against the oracle.  Bounds as for the 37 x 21 cases above."""
+    RT = 0.5
+    bc = TINY_BC[bcname]
+    tau, dt = 0.2, 0.25 * (1 / max(nx, ny)) / (4 * np.sqrt(RT))
+    pg, po = PV.newton_cotes(nv1, RT), OV.newton_cotes_2d(nv1, RT)
+    g = P.Solver(nx, ny, 1 / nx, 1 / ny, pg[0], pg[1], pg[2], tau, dt, bc, storage=storage)
+    o = O.Setup(nx, ny, 1 / nx, 1 / ny, po[0], po[1], po[2], tau, dt, bc)
+    f0 = WL.near_equilibrium_state(po[1], ny, nx, amp=0.1, seed=11 * nx + ny)
+    g.set_state(f0)
+    g.step(6)
+    fg = g.state()
+    assert g.check() == P.DUGKS_OK
+    g.close()
+    fo = O.t3s3_run(f0, o, 6)
+    err = rel_linf(fg, fo)
+    assert err <= {P.G_FP32: 5e-7, P.G_BF16: 2e-2}[storage], err
+    assert abs(fg.sum() - fo.sum()) <= {P.G_FP32: 1e-8, P.G_BF16: 1e-3}[storage] * fo.sum()
+
+
 @pytest.mark.parametrize("storage", FORMS, ids=IDS)
 def test_small_velocity_set_deviation_forms(cuda, storage):
     """5 x 5 Newton-Cotes grid (25 velocities; an odd grid, with tie
