@@ -738,6 +738,32 @@ constexpr int RPL = RB + NWALL;
 static_assert(RW % 4 == 0 && RV % 4 == 0 && RC % 4 == 0 && RF % 4 == 0 && RPL % 4 == 0,
               "ring regions must be 16-byte aligned");
 
+// packed FP32 pairs (lo, hi) in one 64-bit register, for fma.rn.f32x2
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// cubic() of two cells at once (the same operations, lane by lane)
+__device__ __forceinline__ unsigned long long cubic2(const unsigned long long (&S)[10],
+                                                     unsigned long long x, unsigned long long y) {
+  const unsigned long long t1 = fma2(x, S[6], fma2(y, S[7], S[3]));
+  const unsigned long long t2 = fma2(y, S[8], S[4]);
+  const unsigned long long t3 = fma2(y, S[9], S[5]);
+  const unsigned long long X = fma2(x, t1, fma2(y, t2, S[1]));
+  const unsigned long long Y = fma2(y, t3, S[2]);
+  return fma2(x, X, fma2(y, Y, S[0]));
+}
+
 // two partial chains: the dependent-FMA depth of a 3 x 3 stencil halves
 __device__ __forceinline__ float dot9s(const float* __restrict__ T, float s00, float s01, float s02,
                                        float s10, float s11, float s12, float s20, float s21,
@@ -846,7 +872,7 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
   const int jr = j0 + RPW * warp;                           // the warp's first row
   bool ok[RPW];
   int cell[RPW];
-  Cubic<float> S[RPW];
+  Cubic<float> S[RPW] = {};
 #pragma unroll
   for (int m = 0; m < RPW; ++m) {
     const int j = jr + m;
@@ -858,6 +884,14 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
       if (STAGE == 2) add_quad(S[m], quad(s.eqp, N, cell[m]), sQ);
     }
   }
+  // the cubics of cells (2q, 2q + 1) as packed FP32 pairs: both are
+  // evaluated at the same xi, two per fma.rn.f32x2 (each lane rounded as
+  // fmaf, so the values are those of cubic())
+  unsigned long long SP[RPW / 2][10];
+#pragma unroll
+  for (int q = 0; q < RPW / 2; ++q)
+#pragma unroll
+    for (int t = 0; t < 10; ++t) SP[q][t] = pack2(S[2 * q].c[t], S[2 * q + 1].c[t]);
   // the tile's wall faces, the same for every velocity, packed in one word:
   // bits 0-3 the rows m whose x-face west of this lane's cell is on the W or
   // E wall, 4-8 the rows m (0..RPW) whose south face is on a y-wall, 9-13
@@ -1091,6 +1125,12 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
 
     const float4 k4 = *reinterpret_cast<const float4*>(R + RV + 4);
     const float kx = STAGE == 1 ? k4.x : k4.z, ky = STAGE == 1 ? k4.y : k4.w;
+    float cw[RPW];                                          // the cells' cubics at xi
+    {
+      const unsigned long long xx = pack2(e4.x, e4.x), yy = pack2(e4.y, e4.y);
+#pragma unroll
+      for (int q = 0; q < RPW / 2; ++q) unpack2(cubic2(SP[q], xx, yy), cw[2 * q], cw[2 * q + 1]);
+    }
 #pragma unroll
     for (int m = 0; m < RPW; ++m) {
       float fE = __shfl_down_sync(0xffffffffu, fx[m], 1);
@@ -1098,7 +1138,7 @@ __device__ __forceinline__ void gnc_update_body(const GncStep& s, float cA, floa
       if (lane == 31) fE = fEx;
       if (!ok[m]) continue;
       const float df = fmaf(kx, fE - fx[m], ky * (fy[m + 1] - fy[m]));
-      const float ws = fmaf(e4.z, cubic<float>(S[m], e4.x, e4.y), df);
+      const float ws = fmaf(e4.z, cw[m], df);
       float out;
       const float o = ownv[m];
       if (STAGE == 1) out = fmaf(-cB, o, o + ws);                                    // cB = sP
