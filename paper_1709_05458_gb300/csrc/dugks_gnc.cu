@@ -74,6 +74,43 @@ constexpr int NNU = 18;                 // stencil moments nu_{m,u}: 3 m x 6 u
 // index of the monomial x^i y^j among 1, x, y, xx, xy, yy, xxx, xxy, xyy, yyy
 __host__ __device__ constexpr int mono_ix(int i, int j) { return (i + j) * (i + j + 1) / 2 + j; }
 
+// packed FP32 pairs (lo, hi) in one 64-bit register, for fma.rn.f32x2
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// the Kahan-compensated sums of two accumulators at once (kah_add lane by
+// lane: each operation rounded to nearest in FP32); s and c packed as pairs
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+struct Kah2 {
+  unsigned long long s, c;
+};
+__device__ __forceinline__ void kah_add2(Kah2& a, unsigned long long x) {
+  const unsigned long long y = sub2(x, a.c);
+  const unsigned long long t = add2(a.s, y);
+  a.c = sub2(sub2(t, a.s), y);
+  a.s = t;
+}
+
 // ------------------------------------------------------------------ sums
 // Per cell and sign class: the moments sum_k pi_p(xi_k) src_k of the
 // class's velocities for the ten monomials pi_p (pi_0 .. pi_9 in the table
@@ -116,7 +153,7 @@ __device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int b
   const int c = bx * SCB + threadIdx.x;
   if (c >= p.N) return;
   const T* __restrict__ col = (const T*)(stage == 1 ? s.fhat : s.ftp) + c;
-  Kah acc[NMONO] = {};
+  Kah2 acc[NMONO / 2] = {};                      // monomials (2t, 2t + 1)
   // block n of the split, summed in FP32 and folded into the Kahan sums.
   // The ten products of a value go as five packed pairs (one fma.rn.f32x2
   // is two FP32 fused multiply-adds, each rounded as fmaf): monomials
@@ -137,12 +174,7 @@ __device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int b
       asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(part[4]) : "l"(m2), "l"(xx));
     }
 #pragma unroll
-    for (int t = 0; t < NMONO / 2; ++t) {
-      float lo, hi;
-      asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(part[t]));
-      kah_add(acc[2 * t], lo);
-      kah_add(acc[2 * t + 1], hi);
-    }
+    for (int t = 0; t < NMONO / 2; ++t) kah_add2(acc[t], part[t]);
   };
   auto load_block = [&](float (&x)[SBLK], int n) {
 #pragma unroll
@@ -161,7 +193,13 @@ __device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int b
   }
   double* out = s.sums + ((size_t)bz * s.ncls + cls) * NMONO * p.N + c;
 #pragma unroll
-  for (int t = 0; t < NMONO; ++t) out[(size_t)t * p.N] = kah_value(acc[t]);
+  for (int t = 0; t < NMONO / 2; ++t) {
+    Kah lo, hi;
+    unpack2(acc[t].s, lo.s, hi.s);
+    unpack2(acc[t].c, lo.c, hi.c);
+    out[(size_t)(2 * t) * p.N] = kah_value(lo);
+    out[(size_t)(2 * t + 1) * p.N] = kah_value(hi);
+  }
 }
 
 template <typename T>
@@ -738,21 +776,6 @@ constexpr int RPL = RB + NWALL;
 static_assert(RW % 4 == 0 && RV % 4 == 0 && RC % 4 == 0 && RF % 4 == 0 && RPL % 4 == 0,
               "ring regions must be 16-byte aligned");
 
-// packed FP32 pairs (lo, hi) in one 64-bit register, for fma.rn.f32x2
-__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void unpack2(unsigned long long v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
-                                                   unsigned long long c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
 // cubic() of two cells at once (the same operations, lane by lane)
 __device__ __forceinline__ unsigned long long cubic2(const unsigned long long (&S)[10],
                                                      unsigned long long x, unsigned long long y) {
