@@ -125,6 +125,15 @@ __device__ __forceinline__ void kah_add2(Kah2& a, unsigned long long x) {
 constexpr int SCB = 256;                 // cells per block
 constexpr int SBLK = 16;                 // velocities per plain FP32 block
 constexpr int SMAXE = 512;               // velocities per split at most
+constexpr int SRING = 3;                 // streamed form: blocks of SBLK planes in the ring
+// streamed form (BF16): dynamic shared memory holding the split's
+// monomials and velocity indices, then the ring of its planes' values
+constexpr size_t SUMS_TAB = (size_t)SMAXE * 3 * sizeof(float4) + SMAXE * sizeof(int);
+template <typename T> constexpr bool sums_streamed() { return sizeof(T) == 2; }
+template <typename T> constexpr size_t sums_smem() {
+  return sums_streamed<T>() ? SUMS_TAB + (size_t)SRING * SBLK * SCB * sizeof(T) : 0;
+}
+static_assert(SUMS_TAB % 16 == 0, "the ring must start 16-byte aligned");
 
 // velocity split z of class cls: table entries [ea, eb)
 __device__ __forceinline__ void split_range(const GncStep& s, int cls, int z, int& ea, int& eb) {
@@ -135,8 +144,13 @@ __device__ __forceinline__ void split_range(const GncStep& s, int cls, int z, in
 
 template <typename T>
 __device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int bx, int by, int bz) {
-  __shared__ float4 mono[SMAXE][3];
-  __shared__ int kof[SMAXE];
+  // FP32: static tables; BF16: the tables and the ring in dynamic memory
+  __shared__ float4 mono_s[sums_streamed<T>() ? 1 : SMAXE][3];
+  __shared__ int kof_s[sums_streamed<T>() ? 1 : SMAXE];
+  extern __shared__ __align__(16) unsigned char sdyn[];
+  float4 (*mono)[3] = sums_streamed<T>() ? reinterpret_cast<float4 (*)[3]>(sdyn) : mono_s;
+  int* kof = sums_streamed<T>() ? reinterpret_cast<int*>(sdyn + (size_t)SMAXE * 3 * sizeof(float4)) : kof_s;
+  T* ring = reinterpret_cast<T*>(sdyn + SUMS_TAB);          // [SRING][SBLK][SCB]
   const DevParams& p = s.p;
   const int cls = by;
   int ea, eb;
@@ -151,8 +165,6 @@ __device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int b
   for (int t = threadIdx.x; t < cntp; t += SCB) kof[t] = t < cnt ? __ldg(s.cls_k + ea + t) : 0;
   __syncthreads();
   const int c = bx * SCB + threadIdx.x;
-  if (c >= p.N) return;
-  const T* __restrict__ col = (const T*)(stage == 1 ? s.fhat : s.ftp) + c;
   Kah2 acc[NMONO / 2] = {};                      // monomials (2t, 2t + 1)
   // block n of the split, summed in FP32 and folded into the Kahan sums.
   // The ten products of a value go as five packed pairs (one fma.rn.f32x2
@@ -176,21 +188,61 @@ __device__ __forceinline__ void gnc_sums_body(const GncStep& s, int stage, int b
 #pragma unroll
     for (int t = 0; t < NMONO / 2; ++t) kah_add2(acc[t], part[t]);
   };
-  auto load_block = [&](float (&x)[SBLK], int n) {
+  constexpr int VPC = 16 / (int)sizeof(T);       // values per 16-byte copy
+  if (sums_streamed<T>() && p.N % VPC == 0) {
+    // streamed (BF16, the cell count a multiple of 8): the planes of the
+    // block's cells arrive by 16-byte asynchronous copies into a ring of
+    // SRING blocks of SBLK planes, two blocks ahead of the one being summed;
+    // one barrier per block.  FP32 keeps the loads through registers, which
+    // measured faster there (77 against 80 us at 128^2 x 4096; BF16 76
+    // against 80)
+    constexpr int CPP = SCB / VPC;               // copies per plane
+    const int c0 = bx * SCB, ncell = min(SCB, p.N - c0);   // a multiple of VPC
+    const T* __restrict__ base = (const T*)(stage == 1 ? s.fhat : s.ftp) + c0;
+    const int nblk = cntp / SBLK;
+    auto issue = [&](int b) {
+      if (b < nblk) {
+        T* dst = ring + (size_t)(b % SRING) * SBLK * SCB;
+        for (int q = threadIdx.x; q < SBLK * CPP; q += SCB) {
+          const int u = q / CPP, ch = q % CPP;
+          if (ch * VPC < ncell)
+            cp16(dst + u * SCB + ch * VPC, base + (size_t)kof[b * SBLK + u] * p.N + ch * VPC);
+        }
+      }
+      cp_commit();
+    };
+    issue(0);
+    issue(1);
+    for (int b = 0; b < nblk; ++b) {
+      cp_wait<1>();                              // this thread's copies of block b
+      __syncthreads();                           // everyone's; block b - 1 read by all
+      issue(b + 2);                              // into block b - 1's slot
+      const T* src = ring + (size_t)(b % SRING) * SBLK * SCB + threadIdx.x;
+      float x[SBLK];
 #pragma unroll
-    for (int u = 0; u < SBLK; ++u) x[u] = ldv(col + (size_t)kof[n + u] * p.N);
-  };
-  // two register blocks in turn: the next block's loads are in flight while
-  // the current one is summed
-  float v[SBLK], w[SBLK];
-  if (cntp > 0) load_block(v, 0);
-  for (int n = 0; n < cntp; n += 2 * SBLK) {
-    if (n + SBLK < cntp) load_block(w, n + SBLK);
-    add_block(v, n);
-    if (n + SBLK >= cntp) break;
-    if (n + 2 * SBLK < cntp) load_block(v, n + 2 * SBLK);
-    add_block(w, n + SBLK);
+      for (int u = 0; u < SBLK; ++u) x[u] = tof(src[u * SCB]);
+      add_block(x, b * SBLK);
+    }
+  } else {
+    // each thread's loads through registers, the next block's in flight
+    // while the current one is summed
+    if (c >= p.N) return;                        // no barrier follows
+    const T* __restrict__ col = (const T*)(stage == 1 ? s.fhat : s.ftp) + c;
+    auto load_block = [&](float (&x)[SBLK], int n) {
+#pragma unroll
+      for (int u = 0; u < SBLK; ++u) x[u] = ldv(col + (size_t)kof[n + u] * p.N);
+    };
+    float v[SBLK], w[SBLK];
+    if (cntp > 0) load_block(v, 0);
+    for (int n = 0; n < cntp; n += 2 * SBLK) {
+      if (n + SBLK < cntp) load_block(w, n + SBLK);
+      add_block(v, n);
+      if (n + SBLK >= cntp) break;
+      if (n + 2 * SBLK < cntp) load_block(v, n + 2 * SBLK);
+      add_block(w, n + SBLK);
+    }
   }
+  if (c >= p.N) return;
   double* out = s.sums + ((size_t)bz * s.ncls + cls) * NMONO * p.N + c;
 #pragma unroll
   for (int t = 0; t < NMONO / 2; ++t) {
@@ -1341,6 +1393,15 @@ cudaError_t allow_gnc() {
                   (void*)k_gnc_update_b<T, 1, false>, (void*)k_gnc_update_b<T, 2, false>,
                   (void*)k_gnc_update_b<T, 1, true>, (void*)k_gnc_update_b<T, 2, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  // the streamed sums (BF16) hold their ring in shared memory; the FP32
+  // sums keep the default split, whose L1 takes their loads in flight (a
+  // full shared-memory carveout slowed them from 77 to 87 us)
+  if (sums_streamed<T>())
+    for (void* f : {(void*)k_gnc_sums<T>, (void*)k_gnc_sums_b<T>}) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sums_smem<T>());
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
   return e;
 }
 
@@ -1595,8 +1656,8 @@ cudaError_t gnc_prepare(int store) {
 // class sums of the stage's source, then the cell finaliser
 cudaError_t launch_gnc_sums(const GncStep& s, int stage, cudaStream_t st) {
   const dim3 grid((s.p.N + SCB - 1) / SCB, s.ncls, s.nsplit);
-  if (s.store == 1) k_gnc_sums<float><<<grid, SCB, 0, st>>>(s, stage);
-  else k_gnc_sums<__nv_bfloat16><<<grid, SCB, 0, st>>>(s, stage);
+  if (s.store == 1) k_gnc_sums<float><<<grid, SCB, sums_smem<float>(), st>>>(s, stage);
+  else k_gnc_sums<__nv_bfloat16><<<grid, SCB, sums_smem<__nv_bfloat16>(), st>>>(s, stage);
   return cudaGetLastError();
 }
 
@@ -1730,8 +1791,8 @@ cudaError_t launch_gnc_batch_stage(const GncBatch& b, int stage, cudaStream_t st
   cudaError_t e = cudaSuccess;
   const bool f32 = b.store == 1;
   if (b.total[0]) {
-    if (f32) k_gnc_sums_b<float><<<b.total[0], SCB, 0, st>>>(b.steps, at(0), n, stage);
-    else k_gnc_sums_b<__nv_bfloat16><<<b.total[0], SCB, 0, st>>>(b.steps, at(0), n, stage);
+    if (f32) k_gnc_sums_b<float><<<b.total[0], SCB, sums_smem<float>(), st>>>(b.steps, at(0), n, stage);
+    else k_gnc_sums_b<__nv_bfloat16><<<b.total[0], SCB, sums_smem<__nv_bfloat16>(), st>>>(b.steps, at(0), n, stage);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && b.total[1]) {
