@@ -1413,7 +1413,12 @@ cudaError_t allow_gnc() {
     for (void* f : {(void*)k_gnc_sums<T>, (void*)k_gnc_sums_b<T>}) {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sums_smem<T>());
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncAttributes a{};
+      if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, f);
+      if (e != cudaSuccess) break;
+      const long need = 3L * ((long)a.sharedSizeBytes + (long)sums_smem<T>() + 1024);   // three blocks
+      const int carve = smem_sm > 0 ? (int)std::min(100L, (need * 100 + smem_sm - 1) / smem_sm) : 100;
+      e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
     }
   return e;
 }
