@@ -535,13 +535,15 @@ def run_batched(args):
     return 0
 
 
-def rarefied_measure(P, PV, WL, stream, flush, steps, warmup, storage, label):
-    """rarefied128 (128^2 cells, 64 x 64 Newton-Cotes, Kn 1, diffuse walls)
-    in one storage form: device-timed steps, the dominant kernel against HBM
-    and the whole step against the algorithmic bytes of one read and one
-    write of the stored state per update."""
+def workload_measure(P, PV, WL, stream, flush, steps, warmup, storage, label,
+                     workload="rarefied128_kn1_nv64"):
+    """Another workload (default rarefied128: 128^2 cells, 64 x 64
+    Newton-Cotes, Kn 1, diffuse walls) in one storage form: device-timed
+    steps, the dominant kernel against HBM and the whole step against the
+    algorithmic bytes of one read and one write of the stored state per
+    update."""
     saved = globals()["WORKLOAD"]
-    globals()["WORKLOAD"] = "rarefied128_kn1_nv64"
+    globals()["WORKLOAD"] = workload
     try:
         s, c, nv = make_solver(P, PV, WL, stream, storage=storage)
     finally:
@@ -551,11 +553,15 @@ def rarefied_measure(P, PV, WL, stream, flush, steps, warmup, storage, label):
         s.step(1)
     ms, prof = timed_steps(P, s, stream, flush, steps)
     ok = s.check() == P.DUGKS_OK
+    try:                                          # fused D2Q9 kernels only
+        tile_height = P.dugks_tile_height(s.ctx)
+    except Exception:
+        tile_height = None
     s.close()
     peak = measured_peaks().get("hbm_gbs", 6800.0)
     sbytes = {"fp32": 4, "bf16": 2, "fp64": 8}[label]
     step_s = ms * 1e-3 / steps
-    return {"workload": "rarefied128_kn1_nv64", "storage": label,
+    return {"workload": workload, "storage": label,
             "value": units / step_s / 1e9, "unit": "G updates/s", "ms_per_step": step_s * 1e3,
             "steps": steps, "units_per_step": units,
             "step_hbm": {"bytes_per_update": 2 * sbytes,
@@ -563,7 +569,8 @@ def rarefied_measure(P, PV, WL, stream, flush, steps, warmup, storage, label):
                          "frac": 2 * sbytes * units / step_s / 1e9 / peak,
                          "basis": "one read and one write of the stored state per update"},
             "hbm": hbm_view(prof, label, nv, c["nx"], c["ny"], peak),
-            "stated_bound": STATED_BOUNDS["rarefied128_kn1_nv64"].get(label),
+            "stated_bound": STATED_BOUNDS.get(workload, {}).get(label),
+            **({"tile_height": tile_height} if tile_height else {}),
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in prof.items() if v[0]},
             "stable": ok}
 
@@ -735,8 +742,10 @@ def run_ours(args):
     # the rarefied (Newton-Cotes) and batched workloads beside the headline
     extra = {}
     if not args.no_extra and WORKLOAD == "cavity256":
-        extra["rarefied128_fp32"] = rarefied_measure(P, PV, WL, stream, flush, 20, 3, P.G_FP32,
+        extra["rarefied128_fp32"] = workload_measure(P, PV, WL, stream, flush, 20, 3, P.G_FP32,
                                                      "fp32")
+        extra["cavity1024_fp32"] = workload_measure(P, PV, WL, stream, flush, 50, 3, P.G_FP32,
+                                                    "fp32", workload="cavity1024")
         for key, st in (("batched64", P.FP64), ("batched64_fp32", P.G_FP32)):
             b = batched_measure(P, PV, WL, stream, 3, 2, world, storage=st)
             extra[key] = {
