@@ -812,7 +812,8 @@ __device__ __forceinline__ void halo_pos(int h, int& sx, int& sy) {
 }
 
 // Ring of per-velocity inputs of the update, NRING planes deep, filled by
-// asynchronous copies NRING - 1 planes ahead: the staged plane (FP32
+// asynchronous copies ahead of use (FP32: the next pair of planes while a
+// pair is formed; BF16: three planes ahead): the staged plane (FP32
 // storage; BF16 arrives through registers), the face weights, the velocity's
 // table rows, its bounce-back coefficients, f^ of the tile's cells (stage 2,
 // FP32) and the tile's wall-face values.  Offsets in floats, 16-byte aligned.
