@@ -288,6 +288,9 @@ k_d2q9m(D2Q9Params P, D2Q9StageF S, MixedConst M, const T* __restrict__ gin,
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int stride = SH * SW;
+  // launched as a programmatic dependent of the previous stage kernel when
+  // the grid is one wave: wait for it (a no-op otherwise) before any read
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   // staged tile: cells of the domain and their periodic images first, then
   // the wall ghosts extrapolated from them (no chain of global loads)
@@ -342,6 +345,8 @@ k_d2q9m(D2Q9Params P, D2Q9StageF S, MixedConst M, const T* __restrict__ gin,
     }
   }
   __syncthreads();
+  // the tile is staged: the next stage kernel may begin launching
+  asm volatile("griddepcontrol.launch_dependents;");
 
   // x-faces; wall faces (fi = 0 or nx) after all the others, so that no
   // warp of interior faces diverges on one
@@ -646,20 +651,44 @@ cudaError_t launch_d2q9m_stage(const D2Q9Params& p, const D2Q9StageF& s, int sto
   dim3 grid((p.nx + TX - 1) / TX, (p.ny + p.ty - 1) / p.ty);
   const int threads = TX * (p.ty + 1);
   const size_t bytes = smem_bytes(p.ty);
+  // one-wave grids launch as programmatic dependents of the previous kernel
+  // (its tail overlaps this grid's launch); multi-wave grids plainly
+  // resident blocks per GPU at this form and height, queried once
+  static int slots[2][kMaxTY + 1] = {};
+  int& sl = slots[store == 1 ? 0 : 1][p.ty];
+  if (sl == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int occ = d2q9m_occupancy(store, p.ty);
+    sl = sms > 0 && occ > 0 ? sms * occ : -1;
+  }
+  const bool one_wave = sl > 0 && (long)grid.x * grid.y <= (long)sl;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = bytes;
+  cfg.stream = st_;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = one_wave ? 1 : 0;
+  cudaError_t e;
   if (store == 1) {
     const MixedConst M = mixed_const<float>(p, rho0);
     auto* g = (const float*)gin; auto* o = (const float*)own;
     auto* a = (float*)out0; auto* b = (float*)out1;
-    if (stage == 1) k_d2q9m<1, float><<<grid, threads, bytes, st_>>>(p, s, M, g, o, rho_in, a, b, rho_out);
-    else k_d2q9m<2, float><<<grid, threads, bytes, st_>>>(p, s, M, g, o, rho_in, a, b, rho_out);
+    e = cudaLaunchKernelEx(&cfg, stage == 1 ? k_d2q9m<1, float> : k_d2q9m<2, float>, p, s, M, g, o,
+                           rho_in, a, b, rho_out);
   } else {
     const MixedConst M = mixed_const<__nv_bfloat16>(p, rho0);
     auto* g = (const __nv_bfloat16*)gin; auto* o = (const __nv_bfloat16*)own;
     auto* a = (__nv_bfloat16*)out0; auto* b = (__nv_bfloat16*)out1;
-    if (stage == 1) k_d2q9m<1, __nv_bfloat16><<<grid, threads, bytes, st_>>>(p, s, M, g, o, rho_in, a, b, rho_out);
-    else k_d2q9m<2, __nv_bfloat16><<<grid, threads, bytes, st_>>>(p, s, M, g, o, rho_in, a, b, rho_out);
+    e = cudaLaunchKernelEx(&cfg, stage == 1 ? k_d2q9m<1, __nv_bfloat16> : k_d2q9m<2, __nv_bfloat16>,
+                           p, s, M, g, o, rho_in, a, b, rho_out);
   }
-  return cudaGetLastError();
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_dev_from_f64(const DevParams& p, int store, double rho0, const double* f,
